@@ -1,0 +1,166 @@
+"""Seeded synthetic inputs shaped like the paper's workloads (Sec. IV-B).
+
+This module holds input generators only: velocity models, off-grid source
+and receiver coordinates, and the source time function.  It contains none of
+the propagator's arithmetic (no stencil, no injection, no CFL, no damping),
+so that the CUDA path and the FP64 oracle can both be fed from it without
+sharing any of the method.
+
+The paper evaluates synthetic 512^3 velocity models with grid spacing 10 m,
+one spatially localised source wavelet, damping layers and zero initial
+conditions (Sec. IV-B); it names no public dataset.  The recipes below stand
+in for those models:
+
+* ``constant``  homogeneous vp (the 64^3 so4 parity case);
+* ``layered``   ``nlayers`` horizontal layers along axis 2 (depth), vp rising
+                from ``vmin`` to ``vmax`` with depth, seeded interface depths,
+                plus ``nblobs`` seeded Gaussian perturbations of +-5 % with
+                sigma 20-60 cells (scaled with the grid), clipped to
+                [vmin, vmax].
+
+Coordinates are in metres with the origin at grid index 0 (axis order
+x, y, z with z the contiguous depth axis).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BASE_SEED = 2010_10248
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def ricker(f0: float, dt: float, nt: int, t0: float | None = None) -> np.ndarray:
+    """Ricker wavelet (amplitude 1) sampled at t_n = n dt, peak at t0 = 1/f0."""
+    t0 = 1.0 / f0 if t0 is None else t0
+    tau = np.arange(nt, dtype=np.float64) * dt - t0
+    a = (math.pi * f0 * tau) ** 2
+    return (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def constant_vp(shape, v: float) -> np.ndarray:
+    return np.full(tuple(shape), v, dtype=np.float32)
+
+
+def layered_vp(shape, seed: int, vmin: float = 1500.0, vmax: float = 4500.0,
+               nlayers: int = 8, nblobs: int = 16, blob_sigma=(20.0, 60.0),
+               blob_amp: float = 0.05) -> np.ndarray:
+    """Layered model along depth (axis 2) with smooth Gaussian perturbations."""
+    n0, n1, n2 = (int(s) for s in shape)
+    g = rng(seed)
+    # interface depths: sorted seeded fractions of the depth axis
+    cuts = np.sort(g.uniform(0.05, 0.95, size=nlayers - 1)) * n2
+    vel = np.linspace(vmin, vmax, nlayers)
+    z = np.arange(n2)
+    layer = np.searchsorted(cuts, z, side="right")
+    prof = vel[layer].astype(np.float32)
+    vp = np.broadcast_to(prof[None, None, :], (n0, n1, n2)).copy()
+    # sigma range is quoted for 512^3; scale it with the grid
+    scale = min(n0, n1, n2) / 512.0
+    for _ in range(nblobs):
+        c = g.uniform(0, 1, size=3) * np.array([n0, n1, n2])
+        sig = g.uniform(*blob_sigma) * scale
+        amp = g.choice([-1.0, 1.0]) * blob_amp
+        lo = [max(0, int(c[d] - 3 * sig)) for d in range(3)]
+        hi = [min((n0, n1, n2)[d], int(c[d] + 3 * sig) + 1) for d in range(3)]
+        if any(hi[d] <= lo[d] for d in range(3)):
+            continue
+        gx = np.exp(-0.5 * ((np.arange(lo[0], hi[0]) - c[0]) / sig) ** 2).astype(np.float32)
+        gy = np.exp(-0.5 * ((np.arange(lo[1], hi[1]) - c[1]) / sig) ** 2).astype(np.float32)
+        gz = np.exp(-0.5 * ((np.arange(lo[2], hi[2]) - c[2]) / sig) ** 2).astype(np.float32)
+        box = vp[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]
+        box *= 1.0 + amp * (gx[:, None, None] * gy[None, :, None] * gz[None, None, :])
+    np.clip(vp, vmin, vmax, out=vp)
+    return vp
+
+
+def offgrid_point(shape, spacing, seed: int, lo_frac=0.3, hi_frac=0.7) -> np.ndarray:
+    """One seeded off-grid point inside the given fraction of the box."""
+    g = rng(seed)
+    ext = np.array([(shape[d] - 1) * spacing[d] for d in range(3)])
+    return g.uniform(lo_frac, hi_frac, size=3) * ext
+
+
+def receiver_line(shape, spacing, seed: int, nrec: int, margin_cells: float = 2.0) -> np.ndarray:
+    """nrec receivers on a line along x at a seeded off-grid (y, z)."""
+    g = rng(seed)
+    ext = np.array([(shape[d] - 1) * spacing[d] for d in range(3)])
+    y = g.uniform(0.3, 0.7) * ext[1]
+    z = g.uniform(0.2, 0.5) * ext[2]
+    x0 = margin_cells * spacing[0] + g.uniform(0.0, 1.0) * spacing[0]
+    x1 = ext[0] - margin_cells * spacing[0]
+    xs = np.linspace(x0, x1, nrec)
+    return np.stack([xs, np.full(nrec, y), np.full(nrec, z)], axis=1)
+
+
+def receiver_plane(shape, spacing, seed: int, nx: int, ny: int, depth_cells: float,
+                   step_cells: float = 2.0) -> np.ndarray:
+    """nx * ny receivers on a horizontal plane at an off-grid depth, spacing
+    step_cells grid cells, with a seeded sub-cell offset."""
+    g = rng(seed)
+    off = g.uniform(0.05, 0.95, size=3)
+    ext = np.array([(shape[d] - 1) * spacing[d] for d in range(3)])
+    xs = (off[0] + step_cells * np.arange(nx)) * spacing[0]
+    ys = (off[1] + step_cells * np.arange(ny)) * spacing[1]
+    xs = xs[xs <= ext[0]]
+    ys = ys[ys <= ext[1]]
+    z = (depth_cells + off[2]) * spacing[2]
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], axis=1)
+
+
+@dataclass
+class Workload:
+    """One propagation problem: grid, model, geometry and wavelet recipe."""
+    name: str
+    shape: tuple
+    spacing: tuple
+    so: int
+    nt: int
+    nbl: int
+    f0: float
+    vp: np.ndarray
+    src_xyz: np.ndarray
+    rec_xyz: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    def wavelets(self, dt: float) -> np.ndarray:
+        """[nsrc, nt] source time functions sampled with the step dt."""
+        w = ricker(self.f0, dt, self.nt)
+        return np.repeat(w[None, :], len(self.src_xyz), axis=0)
+
+
+def acoustic_64_so4(seed: int = BASE_SEED + 0) -> Workload:
+    """64^3, h = 10 m, so4, 100 steps, vp = 1.5 km/s, 10-cell sponge, one
+    10 Hz Ricker at a seeded off-grid interior point, 64 receivers on an
+    off-grid line along x."""
+    shape, h = (64, 64, 64), (10.0, 10.0, 10.0)
+    src = offgrid_point(shape, h, seed + 1)[None, :]
+    rec = receiver_line(shape, h, seed + 2, 64)
+    return Workload("acoustic 64^3 so4 100 steps", shape, h, 4, 100, 10, 10.0,
+                    constant_vp(shape, 1500.0), src, rec)
+
+
+def acoustic_512_so8(seed: int = BASE_SEED + 1, shape=(512, 512, 512), nt: int = 1000,
+                     nbl: int = 40) -> Workload:
+    """512^3, h = 10 m, so8, 1000 steps, 40-cell sponge, seeded layered vp
+    1.5-4.5 km/s with Gaussian perturbations, one 15 Hz Ricker near the top,
+    256 x 256 receiver plane (spacing 2h) at a fixed off-grid depth.
+    ``shape`` / ``nt`` / ``nbl`` may be reduced for parity runs that keep
+    the same recipe."""
+    h = (10.0, 10.0, 10.0)
+    g = rng(seed + 7)
+    src = np.array([[(0.5 * (shape[0] - 1) + g.uniform(-0.5, 0.5)) * h[0],
+                     (0.5 * (shape[1] - 1) + g.uniform(-0.5, 0.5)) * h[1],
+                     (nbl + 10 + g.uniform(0.05, 0.95)) * h[2]]])
+    nrx = min(256, (shape[0] - 1) // 2)
+    nry = min(256, (shape[1] - 1) // 2)
+    rec = receiver_plane(shape, h, seed + 3, nrx, nry, depth_cells=nbl + 20)
+    vp = layered_vp(shape, seed + 4)
+    return Workload(f"acoustic {shape[0]}x{shape[1]}x{shape[2]} so8 {nt} steps", tuple(shape), h,
+                    8, nt, nbl, 15.0, vp, src, rec)

@@ -1,0 +1,363 @@
+"""Benchmark: temporally blocked acoustic propagation, 512^3, space order 8.
+
+One bench step is one whole shot through the C ABI: model setup (CFL step,
+sponge, c2), the source and receiver inspectors, and tb_forward over 1000
+time steps with the blocked schedule (receiver traces included).  The metric
+is grid-point updates per second (N * nt / step time).  The one-step
+spatially blocked kernel is timed in the same run for comparison.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+this method; there is no reference code) on a bounded sample of the same
+workload.  Under torchrun (N > 1) every rank runs an independent replica of
+the shot on its own GPU (the path has no data exchange between shots).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GPts/s blocked vs spatial-blocked at rel-L2<=1e-4; shot p50/p99 latency"
+UNIT = "GPts/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--size", type=int, default=512, help="cube edge (512 = the benchmark)")
+    ap.add_argument("--nt", type=int, default=1000)
+    ap.add_argument("--time-tile", type=int, default=4)
+    ap.add_argument("--no-onestep", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("tb_sweep.cuh",):
+        h.update(open(os.path.join(ROOT, "paper_2010_10248_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch_full_size")
+
+
+def cpu_oracle_rate(w, dt, steps_a, steps_b):
+    """GPts/s of the FP64 oracle on the host, from the difference of two runs
+    (removes its serial setup); returns (rate, seconds, threads)."""
+    import oracle
+    oracle.build()
+    wav = w.wavelets(dt)
+    vp64 = w.vp.astype(np.float64)
+    N = int(np.prod(w.shape))
+    t = []
+    for s in (steps_a, steps_b):
+        t0 = time.perf_counter()
+        oracle.acoustic_forward(w.shape, w.spacing, w.so, dt, s, vp64, nbl=w.nbl,
+                                src_xyz=w.src_xyz, src_wav=wav[:, :s], rec_xyz=w.rec_xyz)
+        t.append(time.perf_counter() - t0)
+    dtime = max(t[1] - t[0], 1e-9)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return N * (steps_b - steps_a) / dtime / 1e9, t[0] + t[1], threads
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2010_10248_gb300 import workloads as wl
+    import oracle
+    w = wl.acoustic_512_so8(shape=(args.size,) * 3, nt=args.nt)
+    dt = 0.8 * oracle.cfl_dt_max(w.so, w.spacing, float(w.vp.max()))
+    sample_steps = 2
+    rates = []
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    N = int(np.prod(w.shape))
+    wav = w.wavelets(dt)
+    vp64 = w.vp.astype(np.float64)
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.acoustic_forward(w.shape, w.spacing, w.so, dt, sample_steps, vp64, nbl=w.nbl,
+                                src_xyz=w.src_xyz, src_wav=wav[:, :sample_steps],
+                                rec_xyz=w.rec_xyz)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            rates.append(N * sample_steps / el / 1e9)
+    v = float(np.median(rates))
+    sample = (f"{w.shape[0]}^3 so8, {sample_steps} of {w.nt} steps per bench step, FP64 oracle "
+              f"(Listing 1 form, all {len(w.rec_xyz)} receivers), setup included")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": N * w.nt / (v * 1e9) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.shape), "space_order": w.so,
+                       "nt": w.nt, "receivers": len(w.rec_xyz)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import torch
+    import paper_2010_10248_gb300 as tb
+    from paper_2010_10248_gb300 import build as tbbuild
+    from paper_2010_10248_gb300 import workloads as wl
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    if rank == 0:
+        tbbuild.build()
+    if dist:
+        dist.barrier()
+    tb.load()
+    dev = torch.device("cuda", local)
+
+    w = wl.acoustic_512_so8(shape=(args.size,) * 3, nt=args.nt)
+    N = int(np.prod(w.shape))
+    nt = w.nt
+    vp_dev = torch.from_numpy(w.vp).to(dev)
+    src_dev = torch.from_numpy(w.src_xyz).to(dev)
+    rec_dev = torch.from_numpy(w.rec_xyz).to(dev)
+    nrec = len(w.rec_xyz)
+
+    prop = tb.Propagator(w.shape, w.spacing, w.so, nbl=w.nbl, time_tile=args.time_tile,
+                         profile=True)
+    stream = torch.cuda.current_stream()
+    prop.set_model(vp_dev)
+    dt = prop.dt
+    wav_dev = torch.from_numpy(w.wavelets(dt).astype(np.float32)).to(dev)
+    traces = torch.empty((nt, nrec), dtype=torch.float32, device=dev)
+
+    def shot(schedule, traces_out=traces, vp=vp_dev, src=src_dev, wav=wav_dev, rec=rec_dev):
+        h = prop.h
+        tb.tb_set_model(h, vp, None, None, 0.0, stream)
+        tb.tb_set_sources(h, len(w.src_xyz), src, nt, wav, stream)
+        tb.tb_set_receivers(h, nrec, rec, stream)
+        tb.tb_forward(h, nt, traces_out, tb.TB_BLOCKED if schedule == "blocked" else tb.TB_ONESTEP,
+                      stream)
+
+    def timed(schedule, k, warm, **kw):
+        for _ in range(warm):
+            shot(schedule, **kw)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = tb.tb_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kt_ms, kt_n = 0.0, 0
+        e0.record(stream)
+        for _ in range(k):
+            shot(schedule, **kw)
+            n, ms = prop.kernel_time(0)  # sweep launches of this shot (synchronises)
+            kt_ms += ms
+            kt_n += n
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms = e0.elapsed_time(e1) / k
+        launches = tb.tb_launch_count() - l0
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, kt_ms / max(kt_n, 1), kt_n // k, launches
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_b, kms_b, kl_b, launches = timed("blocked", args.steps, args.warmup)
+    clk = clocks.stop()
+    tr_blocked = traces.clone()
+    value = ws * N * nt / (ms_b * 1e-3) / 1e9
+
+    out = {}
+    if not args.no_onestep:
+        ms_1, kms_1, kl_1, _ = timed("onestep", args.steps, args.warmup)
+        out["onestep"] = {"value": N * nt / (ms_1 * 1e-3) / 1e9, "ms_per_step": ms_1,
+                          "kernel_ms_per_launch": kms_1, "launches_per_step": kl_1}
+        out["blocked_equals_onestep"] = bool(torch.equal(tr_blocked, traces))
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    e2e = None
+    if not args.no_e2e:
+        vp_h = torch.from_numpy(w.vp).pin_memory()
+        src_h = torch.from_numpy(w.src_xyz).pin_memory()
+        rec_h = torch.from_numpy(w.rec_xyz).pin_memory()
+        wav_h = torch.from_numpy(w.wavelets(dt).astype(np.float32)).pin_memory()
+        tr_h = torch.empty((nt, nrec), dtype=torch.float32).pin_memory()
+        ms_e, _, _, _ = timed("blocked", max(1, args.steps // 2), 1, traces_out=tr_h, vp=vp_h,
+                              src=src_h, wav=wav_h, rec=rec_h)
+        h2d = vp_h.numel() * 4 + src_h.numel() * 8 + rec_h.numel() * 8 + wav_h.numel() * 4
+        d2h = tr_h.numel() * 4
+        e2e = {"value": ws * N * nt / (ms_e * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": ms_e}
+
+    # roofline of the dominant kernel (the blocked sweep)
+    T = args.time_tile
+    peak, peak_kind = measured_peaks()
+    launches_per_shot = kl_b
+    # algorithmic bytes: per sweep, u^n, u^{n-1}, c2 read and u^{n+T}, u^{n+T-1}
+    # written once per owned point: 20 B per point per launch
+    full_sweeps = nt // T
+    points_per_launch = N * full_sweeps / max(launches_per_shot, 1)
+    bytes_per_launch = 20.0 * points_per_launch
+    achieved = bytes_per_launch / (kms_b * 1e-3) / 1e9
+    traffic = ncu_traffic(f"sweep_R{w.so // 2}_T{T}")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+            "kernel": f"sweep_kernel<R={w.so // 2},T={T}>",
+            "bytes_per_launch": bytes_per_launch, "kernel_ms_per_launch": kms_b,
+            "point_updates_per_s_in_kernel": points_per_launch * T / (kms_b * 1e-3) / 1e9}
+    if "onestep" in out:
+        o = out["onestep"]
+        bpl1 = 16.0 * N * nt / max(o["launches_per_step"], 1)
+        roof["onestep_kernel"] = {"achieved": bpl1 / (o["kernel_ms_per_launch"] * 1e-3) / 1e9,
+                                  "frac": bpl1 / (o["kernel_ms_per_launch"] * 1e-3) / 1e9 / peak,
+                                  "bytes_per_launch": bpl1,
+                                  "kernel_ms_per_launch": o["kernel_ms_per_launch"]}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        try:
+            rate, secs, threads = cpu_oracle_rate(w, dt, 2, 2 + args.cpu_steps)
+            cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                   "sample": f"{w.shape[0]}^3 so8, {args.cpu_steps} steps (difference of a 2- "
+                             f"and a {2 + args.cpu_steps}-step FP64 oracle run, {secs:.1f} s total)"}
+        except Exception as e:  # the baseline is reported, not required
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                   "sample": f"failed: {e}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "grid": list(w.shape), "space_order": w.so,
+                           "nt": nt, "time_tile": T, "receivers": nrec, "sources": len(w.src_xyz),
+                           "schedule": "blocked", "parallelism": f"replicas x{ws}",
+                           "l2": "inputs larger than L2 (512 MiB per field, 5 fields)",
+                           "step": "set_model + set_sources + set_receivers + forward(nt)"},
+                "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
+                "cpu_baseline": cpu, **out}
+        if out.get("onestep"):
+            line["speedup_vs_onestep"] = value / (ws * out["onestep"]["value"])
+        print(json.dumps(line), flush=True)
+    prop.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * tb.h -- C ABI of the GB300 temporally blocked finite-difference wave
+ * propagator with off-the-grid sources (arXiv 2010.10248).
+ *
+ * Problem (Sec. III-A, Eq. 1): isotropic acoustic wave equation
+ *     m(x) u_tt - Lap u = delta(x - x_s) q(t),  m = 1/vp^2,
+ *     zero initial conditions, receivers d(t, .) = u(t, x_r),
+ * discretised 2nd order in time and space order 4/8/12, with absorbing
+ * damping layers (Sec. IV-B).  Sources and receivers sit off the grid and
+ * act through trilinear weights (Sec. I, Fig. 3).  Before propagation an
+ * inspector rewrites them into grid-aligned form (Sec. II-A: affected-point
+ * mask and unique IDs, decomposed source table src_dcmp, per-column reduced
+ * iteration space), which lets the propagator fuse several time steps into
+ * one temporally blocked sweep (Sec. II-B).
+ *
+ * Conventions for every call:
+ *   - Grid shape n[3] with axis 2 contiguous (the paper's u[t][x][y][z] with
+ *     z innermost).  A "field" argument is a dense float array [n0][n1][n2].
+ *   - Coordinates are FP64 metres with the origin at grid index 0; a point
+ *     must lie in [0, (n_d - 1) h_d] on every axis, else TB_EINVAL.
+ *   - Array pointers may point to host or device memory; the library tells
+ *     them apart with cudaPointerGetAttributes.  Host inputs are copied to
+ *     the device on `stream` before the call returns (pageable host memory
+ *     makes the copy synchronous).  The caller keeps ownership of every
+ *     pointer it passes; the library never frees or retains them after the
+ *     call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL: the legacy default
+ *     stream).  Device work is enqueued asynchronously on it unless stated.
+ *   - Every function returns a tb_status.  The library never aborts or
+ *     exits; on error the handle keeps a message readable with
+ *     tb_last_error().  A failing call leaves the handle usable.
+ *   - One handle must not be used from two host threads at once.
+ */
+#ifndef TB_H
+#define TB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TB_OK = 0,
+  TB_EINVAL = 1,     /* invalid argument (shape, order, coordinate, size)   */
+  TB_ENOMEM = 2,     /* device allocation failed                            */
+  TB_ECUDA = 3,      /* a CUDA runtime call failed                          */
+  TB_EUNSTABLE = 4,  /* dt above the CFL limit of the model                 */
+  TB_ETIMEOUT = 5,   /* a bounded device-side wait ran out (blocked sweep)  */
+  TB_EDIVERGED = 6,  /* NaN/Inf found in the receiver traces                */
+  TB_ESTATE = 7      /* call order violated (e.g. forward before set_model) */
+} tb_status;
+
+enum { TB_ACOUSTIC = 0 };
+enum { TB_ONESTEP = 0, TB_BLOCKED = 1 };
+
+typedef struct tb_handle tb_handle;
+
+/* Tuning and behaviour options; zero-initialise and set what you need.
+ * All-zero options give the defaults noted per field. */
+typedef struct {
+  int time_tile;   /* T: time steps fused per blocked sweep (Sec. II-B). 0 -> 4.
+                      Supported: 1, 2, 3, 4.                                     */
+  int nbl;         /* width in cells of the built-in sponge (Sec. IV-B); 0: none  */
+  int y_bands;     /* blocked sweep: number of bands along axis 1; 0 -> fewest
+                      bands whose tiles are co-resident on the GPU                */
+  int x_chunks;    /* chunks along axis 0 processed as independent sweeps; 0 -> 1
+                      (blocked) or automatic (one-step)                           */
+  int profile;     /* 1: time every propagator launch with CUDA events on the
+                      launching stream (read back with tb_kernel_time)            */
+  int check_nan;   /* 1: tb_forward scans the traces and returns TB_EDIVERGED on
+                      NaN/Inf (adds a device->host sync)                         */
+  double wait_timeout_s; /* blocked sweep: bound on any device-side wait for a
+                      neighbouring tile, seconds; 0 -> 2.0                         */
+} tb_options;
+
+/* Create a propagator for a grid of shape n[3] with spacing h[3] (metres),
+ * space order 4, 8 or 12 (Sec. IV: "space orders of 4, 8, 12").  Requires
+ * n_d >= space_order + 2 on every axis.  `opt` may be NULL (defaults).
+ * Allocates the wavefields (4 x n0 n1 n2 floats) and the model buffer on the
+ * current CUDA device.  Errors: TB_EINVAL, TB_ENOMEM, TB_ECUDA. */
+int tb_create(const int64_t n[3], const double h[3], int space_order, int physics,
+              const tb_options* opt, tb_handle** out);
+
+/* Release every device allocation of the handle (NULL is accepted). */
+int tb_destroy(tb_handle* h);
+
+/* Set the velocity model (Eq. 1: m = 1/vp^2).  vp: field of P velocities in
+ * m/s, all > 0.  aux: must be NULL (the acoustic physics has no further
+ * parameters).  damp: NULL for the built-in sponge of opt.nbl cells, or
+ * n0 + n1 + n2 per-axis damping coefficients eta (1/s) whose sum over the
+ * three axes is the damping of a grid point.  dt: time step in seconds; 0
+ * selects 0.8 of the CFL limit for the model's maximum velocity.  Computes
+ * vmax on the device (the call synchronises `stream` once).
+ * Errors: TB_EINVAL (vp <= 0 or not finite), TB_EUNSTABLE (dt > limit). */
+int tb_set_model(tb_handle* h, const float* vp, const float* aux, const float* damp,
+                 double dt, void* stream);
+
+/* Time step in use (after tb_set_model), or 0. */
+double tb_get_dt(const tb_handle* h);
+
+/* Register nsrc off-grid sources and run the inspector on the device
+ * (Sec. II-A.1-3): trilinear corners with FP64 weight != 0 become affected
+ * points with ascending unique IDs, and the wavelets are decomposed into the
+ * grid-aligned table src_dcmp[t][id] = (dt^2/m(p_id)) sum_s w_s(p_id) q_s[t]
+ * (Listing 3, injection expression s*dt^2/m of Sec. III-A).
+ * coords: [nsrc][3] FP64 metres.  wavelets: [nsrc][nt] float.  Requires
+ * tb_set_model first (TB_ESTATE).  nsrc may be 0 (no sources).
+ * Limits: nsrc < 2^21.  Errors: TB_EINVAL (coordinate outside the grid). */
+int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int nt,
+                   const float* wavelets, void* stream);
+
+/* Register nrec off-grid receivers (trilinear interpolation, Fig. 3b) and
+ * build their grid-aligned form: unique receiver points, a per-column
+ * reduced index (mirror of Sec. II-A.4), and per receiver its 8 (point,
+ * weight) pairs.  coords: [nrec][3] FP64 metres.  nrec may be 0.
+ * Limits: nrec < 2^21.  Errors: TB_EINVAL. */
+int tb_set_receivers(tb_handle* h, int nrec, const double* coords, void* stream);
+
+/* Propagate nt steps from zero initial conditions (Eq. 1) and write the
+ * receiver traces traces[n][r] = sum_c w_rc u^{n+1}(c) (u^{n+1} after the
+ * step-n injection), an [nt][nrec] float array (host or device; may be
+ * NULL).  schedule: TB_ONESTEP (one launch per time step, spatial blocking
+ * only) or TB_BLOCKED (opt.time_tile steps fused per sweep, Sec. II-B).
+ * Both give bitwise-identical wavefields and traces.  nt must not exceed the
+ * wavelet length given to tb_set_sources (when sources are set).
+ * Device traces: asynchronous on `stream`.  Host traces: synchronous.
+ * Errors: TB_ESTATE, TB_EINVAL, TB_ETIMEOUT, TB_EDIVERGED, TB_ECUDA. */
+int tb_forward(tb_handle* h, int nt, float* traces, int schedule, void* stream);
+
+/* Copy a wavefield after tb_forward into out (dense [n0][n1][n2] float,
+ * host or device): which = 0 -> u^{nt}, which = 1 -> u^{nt-1}. */
+int tb_get_field(tb_handle* h, int which, float* out, void* stream);
+
+/* Inspector tables, for checking against an independent implementation.
+ * Source points: *npts receives the number of affected points; lin (host,
+ * may be NULL) receives their ascending linear indices (x n1 + y) n2 + z,
+ * which is the paper's SID order; dcmp (host, may be NULL) receives
+ * src_dcmp as [nt][npts] float.  Synchronous. */
+int tb_get_source_points(tb_handle* h, int64_t* npts, int64_t* lin, float* dcmp);
+
+/* Receiver points: *npts, ascending linear indices (host, may be NULL), and
+ * per receiver its 8 corner point ids (-1 for a zero weight) and weights
+ * (host arrays [nrec][8], may be NULL).  Synchronous. */
+int tb_get_receiver_points(tb_handle* h, int64_t* npts, int64_t* lin, int32_t* corner_id,
+                           float* corner_w);
+
+/* Device bytes held by the handle (fields, model, tables, scratch). */
+size_t tb_workspace_bytes(const tb_handle* h);
+
+/* With opt.profile = 1: number of propagator launches of the last
+ * tb_forward and their summed device time in ms, measured with CUDA events
+ * on the launching stream; kind 0 = propagator sweeps, 1 = receiver
+ * finalize.  Synchronises the stream of the last forward. */
+int tb_kernel_time(tb_handle* h, int kind, int* launches, double* ms);
+
+/* Message of the last failing call on this handle ("" if none). */
+const char* tb_last_error(const tb_handle* h);
+
+/* --- Setup arithmetic (host, FP64), exported for testing --------------- */
+
+/* Centred 2nd-derivative weights on a unit grid, c[0..so/2] (c[0] centre,
+ * c[i] for offsets +-i), from the closed form
+ * c_i = 2 (-1)^(i+1) (r!)^2 / (i^2 (r-i)! (r+i)!), c_0 = -2 sum c_i.
+ * Errors: TB_EINVAL. */
+int tb_fd_weights(int space_order, double* c);
+
+/* CFL limit of the leapfrog scheme: dt_max = 2 / (vmax sqrt(S sum_d 1/h_d^2)),
+ * S = |c0 + 2 sum_i (-1)^i c_i|.  Returns a negative value on bad input. */
+double tb_cfl_dt_max(int space_order, const double h[3], double vmax);
+
+/* Built-in sponge along one axis: eta[i] = eta_max (d/nbl)^2, d the
+ * distance in cells into the layer (1..nbl), eta_max = 3 vmax ln(1000) /
+ * (2 nbl h).  eta: host array of n doubles. */
+int tb_sponge_profile(int64_t n, int nbl, double h, double vmax, double* eta);
+
+/* Ricker wavelet q(t_n) = (1 - 2 a) exp(-a), a = (pi f0 (n dt - t0))^2,
+ * t0 = 1/f0 when t0 <= 0.  out: host array of nt floats. */
+int tb_ricker(double f0, double dt, int nt, double t0, float* out);
+
+/* --- Diagnostics ---------------------------------------------------- */
+
+/* Run the blocked sweep's bounded device-side wait once, on a device flag
+ * that nothing sets, with the given time limit (seconds, > 0 and <= 10).
+ * The waiting kernel gives up after the limit, records the timeout in a
+ * device flag and returns, leaving the context usable; the call then
+ * returns TB_ETIMEOUT.  Any other result means the wait is broken.
+ * Synchronises `stream`.  Errors: TB_EINVAL, TB_ECUDA. */
+int tb_selftest_wait(double timeout_s, void* stream);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * handles, all devices), for accounting in benchmarks. */
+uint64_t tb_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TB_H */

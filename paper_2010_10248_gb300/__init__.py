@@ -1,0 +1,134 @@
+"""GB300 temporally blocked finite-difference wave propagation with off-the-grid
+sources (arXiv 2010.10248).
+
+The computation runs in the CUDA library ``libtb.so`` (C ABI in
+``include/tb.h``); ``_tb`` is its thin ctypes binding and ``Propagator`` a
+convenience wrapper that keeps device buffers in torch tensors.
+"""
+from __future__ import annotations
+
+from . import _tb
+from ._tb import (TB_ACOUSTIC, TB_BLOCKED, TB_ONESTEP, Options, TBError, load, tb_cfl_dt_max,
+                  tb_create, tb_destroy, tb_fd_weights, tb_forward, tb_get_dt, tb_get_field,
+                  tb_get_receiver_points, tb_get_source_points, tb_kernel_time, tb_last_error,
+                  tb_launch_count, tb_ricker, tb_selftest_wait, tb_set_model, tb_set_receivers, tb_set_sources,
+                  tb_sponge_profile, tb_workspace_bytes)
+
+__all__ = ["Propagator", "Options", "TBError", "load", "TB_ONESTEP", "TB_BLOCKED", "TB_ACOUSTIC",
+           "tb_create", "tb_destroy", "tb_set_model", "tb_get_dt", "tb_set_sources",
+           "tb_set_receivers", "tb_forward", "tb_get_field", "tb_get_source_points",
+           "tb_get_receiver_points", "tb_workspace_bytes", "tb_kernel_time", "tb_last_error",
+           "tb_fd_weights", "tb_cfl_dt_max", "tb_sponge_profile", "tb_ricker", "tb_selftest_wait",
+           "tb_launch_count"]
+
+
+class Propagator:
+    """One acoustic propagation problem on the current CUDA device.
+
+    Arrays may be torch tensors (CUDA or CPU) or numpy arrays; host data are
+    copied by the library.  ``forward`` returns the traces as a CUDA tensor
+    [nt, nrec] unless a destination is given.
+    """
+
+    def __init__(self, shape, spacing, space_order, *, time_tile=4, nbl=0, y_bands=0,
+                 x_chunks=0, profile=False, check_nan=False, wait_timeout_s=0.0):
+        import torch
+        self._torch = torch
+        opt = Options(time_tile=time_tile, nbl=nbl, y_bands=y_bands, x_chunks=x_chunks,
+                      profile=int(profile), check_nan=int(check_nan),
+                      wait_timeout_s=float(wait_timeout_s))
+        self.shape = tuple(int(s) for s in shape)
+        self.spacing = tuple(float(s) for s in spacing)
+        self.space_order = int(space_order)
+        self.h = tb_create(self.shape, self.spacing, self.space_order, TB_ACOUSTIC, opt)
+        self.nrec = 0
+        self.nt_src = None
+
+    def close(self):
+        if self.h:
+            tb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        return self._torch.cuda.current_stream()
+
+    def set_model(self, vp, damp=None, dt=0.0):
+        tb_set_model(self.h, vp, None, damp, dt, self._stream())
+        return self
+
+    @property
+    def dt(self):
+        return tb_get_dt(self.h)
+
+    def set_sources(self, coords, wavelets):
+        coords = self._as_f64(coords)
+        nsrc = coords.shape[0] if coords is not None else 0
+        nt = wavelets.shape[-1] if nsrc else 0
+        wav = self._as_f32(wavelets) if nsrc else None
+        tb_set_sources(self.h, nsrc, coords, nt, wav, self._stream())
+        self._keep = (coords, wav)  # alive until the (synchronous) call returned
+        self.nt_src = nt
+        return self
+
+    def set_receivers(self, coords):
+        coords = self._as_f64(coords)
+        self.nrec = coords.shape[0] if coords is not None else 0
+        tb_set_receivers(self.h, self.nrec, coords, self._stream())
+        return self
+
+    def forward(self, nt, traces=None, schedule="blocked"):
+        torch = self._torch
+        sched = TB_BLOCKED if schedule == "blocked" else TB_ONESTEP
+        if traces is None and self.nrec > 0:
+            traces = torch.empty((nt, self.nrec), dtype=torch.float32, device="cuda")
+        tb_forward(self.h, nt, traces, sched, self._stream())
+        return traces
+
+    def field(self, which=0):
+        out = self._torch.empty(self.shape, dtype=self._torch.float32, device="cuda")
+        tb_get_field(self.h, which, out, self._stream())
+        return out
+
+    def source_points(self):
+        import numpy as np
+        n = tb_get_source_points(self.h)
+        lin = np.zeros(max(n, 1), dtype=np.int64)
+        dcmp = np.zeros((max(self.nt_src or 0, 1), max(n, 1)), dtype=np.float32)
+        tb_get_source_points(self.h, lin, dcmp)
+        return lin[:n], dcmp[: (self.nt_src or 0), :n]
+
+    def receiver_points(self):
+        import numpy as np
+        n = tb_get_receiver_points(self.h)
+        lin = np.zeros(max(n, 1), dtype=np.int64)
+        cid = np.zeros((max(self.nrec, 1), 8), dtype=np.int32)
+        cw = np.zeros((max(self.nrec, 1), 8), dtype=np.float32)
+        tb_get_receiver_points(self.h, lin, cid, cw)
+        return lin[:n], cid[: self.nrec], cw[: self.nrec]
+
+    def kernel_time(self, kind=0):
+        return tb_kernel_time(self.h, kind)
+
+    def workspace_bytes(self):
+        return tb_workspace_bytes(self.h)
+
+    # -- helpers
+    def _as_f64(self, a):
+        import numpy as np
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):
+            return a.to(dtype=self._torch.float64).contiguous()
+        return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1, 3))
+
+    def _as_f32(self, a):
+        import numpy as np
+        if hasattr(a, "data_ptr"):
+            return a.to(dtype=self._torch.float32).contiguous()
+        return np.ascontiguousarray(np.asarray(a, dtype=np.float32))

@@ -1,0 +1,847 @@
+// C ABI of the propagator (see include/tb.h): handle, validation, host
+// setup arithmetic (FD weights, CFL, sponge, Ricker), pass planning for the
+// blocked sweep, and the time loop of tb_forward.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "tb_internal.cuh"
+
+namespace tbi {
+cudaError_t sweep_launch_r2(int T, const SweepParams& p, int nctas, bool coop, cudaStream_t st);
+cudaError_t sweep_launch_r4(int T, const SweepParams& p, int nctas, bool coop, cudaStream_t st);
+cudaError_t sweep_launch_r6(int T, const SweepParams& p, int nctas, bool coop, cudaStream_t st);
+cudaError_t sweep_occupancy_r2(int T, int* per_sm);
+cudaError_t sweep_occupancy_r4(int T, int* per_sm);
+cudaError_t sweep_occupancy_r6(int T, int* per_sm);
+bool sweep_shape_r2(int T, SweepShape* s);
+bool sweep_shape_r4(int T, SweepShape* s);
+bool sweep_shape_r6(int T, SweepShape* s);
+
+bool sweep_shape(int R, int T, SweepShape* s) {
+  switch (R) {
+    case 2: return sweep_shape_r2(T, s);
+    case 4: return sweep_shape_r4(T, s);
+    case 6: return sweep_shape_r6(T, s);
+  }
+  return false;
+}
+cudaError_t sweep_max_ctas(int R, int T, int* per_sm) {
+  switch (R) {
+    case 2: return sweep_occupancy_r2(T, per_sm);
+    case 4: return sweep_occupancy_r4(T, per_sm);
+    case 6: return sweep_occupancy_r6(T, per_sm);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t sweep_launch(int R, int T, const SweepParams& p, int nctas, bool cooperative,
+                         cudaStream_t st) {
+  switch (R) {
+    case 2: return sweep_launch_r2(T, p, nctas, cooperative, st);
+    case 4: return sweep_launch_r4(T, p, nctas, cooperative, st);
+    case 6: return sweep_launch_r6(T, p, nctas, cooperative, st);
+  }
+  return cudaErrorInvalidValue;
+}
+}  // namespace tbi
+
+namespace tbi {
+static unsigned long long g_launches = 0;
+void count_launch(int n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+}  // namespace tbi
+
+using namespace tbi;
+
+extern "C" uint64_t tb_launch_count(void) { return __atomic_load_n(&tbi::g_launches, __ATOMIC_RELAXED); }
+
+struct tb_handle {
+  int64_t n[3] = {0, 0, 0};
+  int n2p = 0;
+  double h[3] = {0, 0, 0};
+  int so = 0, R = 0;
+  tb_options opt{};
+  int device = 0, num_sms = 0;
+  double c[8] = {0};     // centred 2nd-derivative weights
+  double dt = 0.0, vmax = 0.0;
+  bool have_model = false;
+  float* field[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* c2 = nullptr;
+  float* damp_b = nullptr;
+  // sources
+  PointTables src;
+  int src_nt = 0;
+  float* src_dcmp = nullptr;
+  bool have_src = false;
+  // receivers
+  PointTables rec;
+  bool have_rec = false;
+  float* rec_dcmp = nullptr;
+  int rec_cap = 0;
+  // blocked-sweep scratch
+  float* ring = nullptr;
+  size_t ring_floats = 0;
+  unsigned long long* progress = nullptr;
+  int progress_n = 0;
+  unsigned long long prog_base = 0;
+  int* err = nullptr;      // [4]: wait timeout flag, nonfinite counter, ...
+  PassDesc* d_pass = nullptr;
+  int pass_cap = 0;
+  float* traces_dev = nullptr;
+  size_t traces_cap = 0;
+  // result of the last forward
+  int last_nt = -1;
+  int cur_idx = 0, prev_idx = 1;
+  // profiling
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kind;
+  int ev_used = 0;
+  cudaStream_t ev_stream = nullptr;
+  char msg[512] = {0};
+};
+
+static int fail(tb_handle* h, int code, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->msg, sizeof(h->msg), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+static int cuda_fail(tb_handle* h, cudaError_t e, const char* where) {
+  cudaGetLastError();
+  return fail(h, e == cudaErrorMemoryAllocation ? TB_ENOMEM : TB_ECUDA, "%s: %s", where,
+              cudaGetErrorString(e));
+}
+#define TB_CUDA(h, call)                                      \
+  do {                                                        \
+    cudaError_t e__ = (call);                                 \
+    if (e__ != cudaSuccess) return cuda_fail((h), e__, #call); \
+  } while (0)
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Host or device input -> device pointer (copy into *tmp when host).
+static cudaError_t to_device(const void* src, size_t bytes, void** tmp, const void** out,
+                             cudaStream_t st) {
+  *tmp = nullptr;
+  if (is_device_ptr(src)) {
+    *out = src;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaMalloc(tmp, bytes ? bytes : 1);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(*tmp, src, bytes, cudaMemcpyHostToDevice, st);
+  *out = *tmp;
+  return e;
+}
+
+// ---------------------------------------------------------------- setup --
+extern "C" int tb_fd_weights(int so, double* c) {
+  // closed form of the centred 2nd-derivative weights of order 2r:
+  // c_i = 2 (-1)^(i+1) (r!)^2 / (i^2 (r-i)! (r+i)!),  c_0 = -2 sum_{i>=1} c_i
+  if (so < 2 || so > 16 || so % 2 || !c) return TB_EINVAL;
+  const int r = so / 2;
+  auto fact = [](int k) {
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= i;
+    return f;
+  };
+  double s = 0.0;
+  for (int i = 1; i <= r; ++i) {
+    const double v = 2.0 * (i % 2 ? 1.0 : -1.0) * fact(r) * fact(r) / ((double)i * i * fact(r - i) * fact(r + i));
+    c[i] = v;
+    s += v;
+  }
+  c[0] = -2.0 * s;
+  return TB_OK;
+}
+
+extern "C" double tb_cfl_dt_max(int so, const double h[3], double vmax) {
+  double c[9];
+  if (!h || !(vmax > 0) || tb_fd_weights(so, c) != TB_OK) return -1.0;
+  const int r = so / 2;
+  double S = c[0];
+  for (int i = 1; i <= r; ++i) S += 2.0 * (i % 2 ? -c[i] : c[i]);
+  S = std::fabs(S);
+  double inv = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    if (!(h[d] > 0)) return -1.0;
+    inv += 1.0 / (h[d] * h[d]);
+  }
+  return 2.0 / (vmax * std::sqrt(S * inv));
+}
+
+extern "C" int tb_sponge_profile(int64_t n, int nbl, double h, double vmax, double* eta) {
+  if (n < 1 || nbl < 0 || !eta || !(h > 0)) return TB_EINVAL;
+  const double emax = nbl > 0 ? 3.0 * vmax * std::log(1000.0) / (2.0 * nbl * h) : 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t d = 0;
+    if (i < nbl) d = nbl - i;
+    else if (i > n - 1 - nbl) d = i - (n - 1 - nbl);
+    const double f = nbl > 0 ? (double)d / nbl : 0.0;
+    eta[i] = emax * f * f;
+  }
+  return TB_OK;
+}
+
+extern "C" int tb_ricker(double f0, double dt, int nt, double t0, float* out) {
+  if (!(f0 > 0) || nt < 0 || !out) return TB_EINVAL;
+  if (t0 <= 0) t0 = 1.0 / f0;
+  const double pi = 3.14159265358979323846;
+  for (int n = 0; n < nt; ++n) {
+    const double a = (pi * f0 * (n * dt - t0)) * (pi * f0 * (n * dt - t0));
+    out[n] = (float)((1.0 - 2.0 * a) * std::exp(-a));
+  }
+  return TB_OK;
+}
+
+// --------------------------------------------------------------- handle --
+extern "C" const char* tb_last_error(const tb_handle* h) { return h ? h->msg : "null handle"; }
+
+extern "C" int tb_destroy(tb_handle* h) {
+  if (!h) return TB_OK;
+  for (auto& f : h->field) cudaFree(f);
+  cudaFree(h->c2);
+  cudaFree(h->damp_b);
+  free_tables(&h->src);
+  free_tables(&h->rec);
+  cudaFree(h->src_dcmp);
+  cudaFree(h->rec_dcmp);
+  cudaFree(h->ring);
+  cudaFree(h->progress);
+  cudaFree(h->err);
+  cudaFree(h->d_pass);
+  cudaFree(h->traces_dev);
+  for (auto e : h->ev) cudaEventDestroy(e);
+  delete h;
+  return TB_OK;
+}
+
+extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int physics,
+                         const tb_options* opt, tb_handle** out) {
+  if (!out || !n || !hsp) return TB_EINVAL;
+  *out = nullptr;
+  if (physics != TB_ACOUSTIC) return TB_EINVAL;
+  if (so != 4 && so != 8 && so != 12) return TB_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    if (n[d] < so + 2 || n[d] > (1 << 20) || !(hsp[d] > 0)) return TB_EINVAL;
+  }
+  if (n[0] * n[1] * n[2] >= (1ll << 40)) return TB_EINVAL;
+  tb_handle* h = new tb_handle();
+  for (int d = 0; d < 3; ++d) {
+    h->n[d] = n[d];
+    h->h[d] = hsp[d];
+  }
+  h->so = so;
+  h->R = so / 2;
+  if (opt) h->opt = *opt;
+  if (h->opt.time_tile == 0) h->opt.time_tile = 4;
+  if (h->opt.time_tile < 1 || h->opt.time_tile > 4 || h->opt.nbl < 0 || h->opt.y_bands < 0 ||
+      h->opt.x_chunks < 0) {
+    delete h;
+    return TB_EINVAL;
+  }
+  if (h->opt.wait_timeout_s <= 0) h->opt.wait_timeout_s = 2.0;
+  tb_fd_weights(so, h->c);
+  h->n2p = (int)((n[2] + 3) / 4 * 4);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  const size_t fbytes = sizeof(float) * (size_t)n[0] * n[1] * h->n2p;
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    e = cudaMalloc(&h->field[i], fbytes);
+    if (e == cudaSuccess) e = cudaMemset(h->field[i], 0, fbytes);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&h->c2, fbytes);
+  if (e == cudaSuccess) e = cudaMemset(h->c2, 0, fbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->damp_b, sizeof(float) * (n[0] + n[1] + n[2]));
+  if (e == cudaSuccess) e = cudaMalloc(&h->err, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int) * 4);
+  if (e != cudaSuccess) {
+    int code = e == cudaErrorMemoryAllocation ? TB_ENOMEM : TB_ECUDA;
+    cudaGetLastError();
+    tb_destroy(h);
+    return code;
+  }
+  *out = h;
+  return TB_OK;
+}
+
+extern "C" double tb_get_dt(const tb_handle* h) { return (h && h->have_model) ? h->dt : 0.0; }
+
+extern "C" size_t tb_workspace_bytes(const tb_handle* h) {
+  if (!h) return 0;
+  const size_t fbytes = sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n2p;
+  size_t b = 5 * fbytes + sizeof(float) * (h->n[0] + h->n[1] + h->n[2]) + sizeof(int) * 4;
+  b += h->src.bytes + h->rec.bytes;
+  b += sizeof(float) * (size_t)h->src_nt * std::max<int64_t>(h->src.npts, 0);
+  b += sizeof(float) * (size_t)h->rec_cap * std::max<int64_t>(h->rec.npts, 0);
+  b += sizeof(float) * h->ring_floats + sizeof(unsigned long long) * h->progress_n;
+  b += sizeof(PassDesc) * h->pass_cap + sizeof(float) * h->traces_cap;
+  return b;
+}
+
+extern "C" int tb_set_model(tb_handle* h, const float* vp, const float* aux, const float* damp,
+                            double dt, void* stream) {
+  if (!h) return TB_EINVAL;
+  if (!vp) return fail(h, TB_EINVAL, "vp is NULL");
+  if (aux) return fail(h, TB_EINVAL, "aux must be NULL for acoustic physics");
+  if (dt < 0 || !std::isfinite(dt)) return fail(h, TB_EINVAL, "dt must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t N = h->n[0] * h->n[1] * h->n[2];
+  void* tmp = nullptr;
+  const void* dvp = nullptr;
+  TB_CUDA(h, to_device(vp, sizeof(float) * N, &tmp, &dvp, st));
+  float* d_vmax = reinterpret_cast<float*>(h->err + 2);
+  int* d_bad = h->err + 3;
+  cudaError_t e = model_vmax((const float*)dvp, N, d_vmax, d_bad, st);
+  float vmax = 0.f;
+  int bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&vmax, d_vmax, sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(tmp);
+    return cuda_fail(h, e, "tb_set_model vmax");
+  }
+  if (bad) {
+    cudaFree(tmp);
+    return fail(h, TB_EINVAL, "vp must be finite and > 0 everywhere");
+  }
+  const double dtmax = tb_cfl_dt_max(h->so, h->h, vmax);
+  if (dt == 0.0) dt = 0.8 * dtmax;
+  if (dt > dtmax) {
+    cudaFree(tmp);
+    return fail(h, TB_EUNSTABLE, "dt = %g exceeds the CFL limit %g for vmax = %g", dt, dtmax, (double)vmax);
+  }
+  // damping: per-axis eta (1/s) -> b = eta / (2 dt)
+  const int64_t nsum = h->n[0] + h->n[1] + h->n[2];
+  std::vector<double> eta(nsum, 0.0);
+  if (damp) {
+    std::vector<float> hd(nsum);
+    if (is_device_ptr(damp)) {
+      e = cudaMemcpyAsync(hd.data(), damp, sizeof(float) * nsum, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        cudaFree(tmp);
+        return cuda_fail(h, e, "tb_set_model damp");
+      }
+    } else {
+      memcpy(hd.data(), damp, sizeof(float) * nsum);
+    }
+    for (int64_t i = 0; i < nsum; ++i) {
+      if (!(hd[i] >= 0.f) || !std::isfinite(hd[i])) {
+        cudaFree(tmp);
+        return fail(h, TB_EINVAL, "damping coefficients must be finite and >= 0");
+      }
+      eta[i] = hd[i];
+    }
+  } else {
+    int64_t off = 0;
+    for (int d = 0; d < 3; ++d) {
+      tb_sponge_profile(h->n[d], h->opt.nbl, h->h[d], vmax, eta.data() + off);
+      off += h->n[d];
+    }
+  }
+  std::vector<float> b(nsum);
+  for (int64_t i = 0; i < nsum; ++i) b[i] = (float)(eta[i] / (2.0 * dt));
+  e = cudaMemcpyAsync(h->damp_b, b.data(), sizeof(float) * nsum, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = model_c2((const float*)dvp, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->n2p, dt * dt, h->c2, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // b (host vector) must outlive the copy
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tb_set_model c2");
+  h->dt = dt;
+  h->vmax = vmax;
+  h->have_model = true;
+  h->have_src = false;  // the source table depends on dt and m
+  h->last_nt = -1;
+  h->msg[0] = 0;
+  return TB_OK;
+}
+
+extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int nt,
+                              const float* wav, void* stream) {
+  if (!h) return TB_EINVAL;
+  if (!h->have_model) return fail(h, TB_ESTATE, "tb_set_model must come before tb_set_sources");
+  if (nsrc < 0 || (nsrc > 0 && (!coords || !wav || nt <= 0)))
+    return fail(h, TB_EINVAL, "bad source arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  void *t1 = nullptr, *t2 = nullptr;
+  const void *dc = nullptr, *dw = nullptr;
+  if (nsrc > 0) {
+    TB_CUDA(h, to_device(coords, sizeof(double) * 3 * nsrc, &t1, &dc, st));
+    cudaError_t e = to_device(wav, sizeof(float) * (size_t)nsrc * nt, &t2, &dw, st);
+    if (e != cudaSuccess) {
+      cudaFree(t1);
+      return cuda_fail(h, e, "tb_set_sources wavelets");
+    }
+  }
+  const char* why = "";
+  h->have_src = false;
+  int s = inspect(h->n, h->h, nsrc, (const double*)dc, false, &h->src, st, &why);
+  if (s != TB_OK) {
+    cudaFree(t1);
+    cudaFree(t2);
+    return fail(h, s, "source inspector: %s", why);
+  }
+  cudaFree(h->src_dcmp);
+  h->src_dcmp = nullptr;
+  h->src_nt = nsrc > 0 ? nt : 0;
+  cudaError_t e = cudaSuccess;
+  if (h->src.npts > 0) {
+    e = cudaMalloc(&h->src_dcmp, sizeof(float) * (size_t)nt * h->src.npts);
+    if (e == cudaSuccess)
+      e = decompose(&h->src, nt, (const float*)dw, h->c2, (int)h->n[1], (int)h->n[2], h->n2p,
+                    h->src_dcmp, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(t1);
+  cudaFree(t2);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tb_set_sources decomposition");
+  h->have_src = true;
+  h->last_nt = -1;
+  h->msg[0] = 0;
+  return TB_OK;
+}
+
+extern "C" int tb_set_receivers(tb_handle* h, int nrec, const double* coords, void* stream) {
+  if (!h) return TB_EINVAL;
+  if (nrec < 0 || (nrec > 0 && !coords)) return fail(h, TB_EINVAL, "bad receiver arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  void* t1 = nullptr;
+  const void* dc = nullptr;
+  if (nrec > 0) TB_CUDA(h, to_device(coords, sizeof(double) * 3 * nrec, &t1, &dc, st));
+  const char* why = "";
+  h->have_rec = false;
+  int s = inspect(h->n, h->h, nrec, (const double*)dc, true, &h->rec, st, &why);
+  cudaFree(t1);
+  if (s != TB_OK) return fail(h, s, "receiver inspector: %s", why);
+  h->have_rec = true;
+  h->last_nt = -1;
+  h->msg[0] = 0;
+  return TB_OK;
+}
+
+// ------------------------------------------------------------- planning --
+struct Plan {
+  std::vector<PassDesc> launch_passes;  // all passes, in launch order
+  std::vector<int> launch_first;        // first pass index of each launch
+  std::vector<int> launch_ctas;         // CTAs per launch
+  int max_ctas = 0;
+};
+
+// Split the grid into (x-chunk, y-band) passes for a sweep of T fused
+// steps.  A pass computes rows [yo0 - (T-1) r, yo1 + (T-1) r) and planes
+// [xo0 - (T-1) r, xo1 + (T-1) r) (clipped to the grid) and owns
+// [yo0, yo1) x [xo0, xo1).
+static int plan_sweep(tb_handle* h, int T, Plan* pl) {
+  const int R = h->R;
+  SweepShape sh;
+  if (!sweep_shape(R, T, &sh)) return fail(h, TB_EINVAL, "unsupported time tile %d", T);
+  int per_sm = 0;
+  cudaError_t e = sweep_max_ctas(R, T, &per_sm);
+  if (e != cudaSuccess) return cuda_fail(h, e, "occupancy");
+  if (per_sm < 1) return fail(h, TB_ECUDA, "sweep kernel does not fit on an SM");
+  const int cap = per_sm * h->num_sms;
+  const int n0 = (int)h->n[0], n1 = (int)h->n[1], n2 = (int)h->n[2];
+  const int TY = sh.TY, TZ = 64;
+  const int ntz = (n2 + TZ - 1) / TZ;
+  const int halo = (T - 1) * R;
+  int nbands = h->opt.y_bands;
+  if (T == 1) nbands = std::max(1, nbands);
+  if (nbands == 0) {
+    for (nbands = 1; nbands <= n1; ++nbands) {
+      const int rows = (n1 + nbands - 1) / nbands;
+      const int in_rows = std::min(n1, rows + (nbands > 1 ? 2 * halo : 0));
+      const int nty = (in_rows + TY - 1) / TY;
+      if (nty * ntz <= cap) break;
+    }
+    if (nbands > n1) return fail(h, TB_EINVAL, "grid too wide for a co-resident blocked sweep");
+  }
+  int nchunks = h->opt.x_chunks;
+  if (nchunks == 0) {
+    if (T == 1) {
+      // one-step: enough CTAs to fill the GPU a few times over
+      const int nty = (n1 + TY - 1) / TY;
+      nchunks = std::max(1, std::min(n0 / std::max(8, 2 * R), (4 * cap + nty * ntz - 1) / (nty * ntz)));
+    } else {
+      nchunks = 1;
+    }
+  }
+  nchunks = std::min(nchunks, n0);
+  nbands = std::min(nbands, n1);
+  std::vector<PassDesc> passes;
+  for (int c = 0; c < nchunks; ++c) {
+    const int xo0 = (int)((int64_t)n0 * c / nchunks), xo1 = (int)((int64_t)n0 * (c + 1) / nchunks);
+    for (int bnd = 0; bnd < nbands; ++bnd) {
+      const int yo0 = (int)((int64_t)n1 * bnd / nbands), yo1 = (int)((int64_t)n1 * (bnd + 1) / nbands);
+      PassDesc p{};
+      p.yo0 = yo0;
+      p.yo1 = yo1;
+      p.xo0 = xo0;
+      p.xo1 = xo1;
+      p.yb0 = std::max(0, yo0 - halo);
+      const int yb1 = std::min(n1, yo1 + halo);
+      p.nty = (yb1 - p.yb0 + TY - 1) / TY;
+      p.ntz = ntz;
+      p.xc0 = std::max(0, xo0 - halo);
+      p.xc1 = std::min(n0, xo1 + halo);
+      passes.push_back(p);
+    }
+  }
+  // group passes into launches: cooperative launches must fit co-resident
+  pl->launch_passes.clear();
+  pl->launch_first.clear();
+  pl->launch_ctas.clear();
+  int ctas = 0;
+  for (size_t i = 0; i < passes.size(); ++i) {
+    const int need = passes[i].nty * passes[i].ntz;
+    if (T > 1 && need > cap) return fail(h, TB_EINVAL, "blocked pass of %d CTAs exceeds %d co-resident", need, cap);
+    const bool new_launch = pl->launch_first.empty() || (T > 1 && ctas + need > cap);
+    if (new_launch) {
+      if (!pl->launch_first.empty()) pl->launch_ctas.push_back(ctas);
+      pl->launch_first.push_back((int)i);
+      ctas = 0;
+    }
+    passes[i].cta0 = ctas;
+    ctas += need;
+    pl->launch_passes.push_back(passes[i]);
+  }
+  pl->launch_ctas.push_back(ctas);
+  pl->max_ctas = 0;
+  for (int c : pl->launch_ctas) pl->max_ctas = std::max(pl->max_ctas, c);
+  (void)sh;
+  return TB_OK;
+}
+
+static int ensure_capacity(tb_handle* h, int T, const Plan& pl, int nt, bool host_traces, int nrec) {
+  SweepShape sh;
+  sweep_shape(h->R, T, &sh);
+  if (T > 1) {
+    const size_t need = (size_t)sh.ring_floats_per_cta * pl.max_ctas;
+    if (need > h->ring_floats) {
+      cudaFree(h->ring);
+      h->ring = nullptr;
+      h->ring_floats = 0;
+      TB_CUDA(h, cudaMalloc(&h->ring, sizeof(float) * need));
+      h->ring_floats = need;
+    }
+    if (pl.max_ctas > h->progress_n) {
+      cudaFree(h->progress);
+      h->progress = nullptr;
+      h->progress_n = 0;
+      TB_CUDA(h, cudaMalloc(&h->progress, sizeof(unsigned long long) * pl.max_ctas));
+      TB_CUDA(h, cudaMemset(h->progress, 0, sizeof(unsigned long long) * pl.max_ctas));
+      h->progress_n = pl.max_ctas;
+      h->prog_base = 0;
+    }
+  }
+  if ((int)pl.launch_passes.size() > h->pass_cap) {
+    cudaFree(h->d_pass);
+    h->d_pass = nullptr;
+    h->pass_cap = 0;
+    TB_CUDA(h, cudaMalloc(&h->d_pass, sizeof(PassDesc) * pl.launch_passes.size()));
+    h->pass_cap = (int)pl.launch_passes.size();
+  }
+  if (h->have_rec && h->rec.npts > 0) {
+    const int cap = std::max(16, T) / T * T;
+    if (cap > h->rec_cap) {
+      cudaFree(h->rec_dcmp);
+      h->rec_dcmp = nullptr;
+      h->rec_cap = 0;
+      TB_CUDA(h, cudaMalloc(&h->rec_dcmp, sizeof(float) * (size_t)cap * h->rec.npts));
+      h->rec_cap = cap;
+    }
+  }
+  if (host_traces && nrec > 0) {
+    const size_t need = (size_t)nt * nrec;
+    if (need > h->traces_cap) {
+      cudaFree(h->traces_dev);
+      h->traces_dev = nullptr;
+      h->traces_cap = 0;
+      TB_CUDA(h, cudaMalloc(&h->traces_dev, sizeof(float) * need));
+      h->traces_cap = need;
+    }
+  }
+  return TB_OK;
+}
+
+static void ev_reset(tb_handle* h, cudaStream_t st) {
+  h->ev_used = 0;
+  h->ev_kind.clear();
+  h->ev_stream = st;
+}
+static cudaEvent_t ev_next(tb_handle* h) {
+  if (h->ev_used >= (int)h->ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->ev.push_back(e);
+  }
+  return h->ev[h->ev_used++];
+}
+
+extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, void* stream) {
+  if (!h) return TB_EINVAL;
+  if (!h->have_model) return fail(h, TB_ESTATE, "tb_set_model must come before tb_forward");
+  if (nt < 0) return fail(h, TB_EINVAL, "nt < 0");
+  if (schedule != TB_ONESTEP && schedule != TB_BLOCKED) return fail(h, TB_EINVAL, "bad schedule");
+  if (h->have_src && h->src.npts > 0 && nt > h->src_nt)
+    return fail(h, TB_EINVAL, "nt = %d exceeds the wavelet length %d", nt, h->src_nt);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nrec = h->have_rec ? h->rec.npt : 0;
+  const bool host_traces = traces && nrec > 0 && !is_device_ptr(traces);
+  float* dtr = host_traces ? nullptr : traces;
+  const int T = schedule == TB_BLOCKED ? h->opt.time_tile : 1;
+
+  Plan p1, pT;
+  int s = plan_sweep(h, 1, &p1);
+  if (s != TB_OK) return s;
+  if (T > 1 && (s = plan_sweep(h, T, &pT)) != TB_OK) return s;
+  if ((s = ensure_capacity(h, 1, p1, nt, host_traces, nrec)) != TB_OK) return s;
+  if (T > 1 && (s = ensure_capacity(h, T, pT, nt, host_traces, nrec)) != TB_OK) return s;
+  if (host_traces) dtr = h->traces_dev;
+
+  const size_t fbytes = sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n2p;
+  // zero initial conditions (Eq. 1)
+  TB_CUDA(h, cudaMemsetAsync(h->field[0], 0, fbytes, st));
+  TB_CUDA(h, cudaMemsetAsync(h->field[1], 0, fbytes, st));
+  TB_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(int), st));
+  if (h->opt.profile) ev_reset(h, st);
+
+  SweepParams P{};
+  P.n0 = (int)h->n[0];
+  P.n1 = (int)h->n[1];
+  P.n2 = (int)h->n[2];
+  P.n2p = h->n2p;
+  P.c2 = h->c2;
+  P.damp_b = h->damp_b;
+  double ih2 = 0.0;
+  for (int d = 0; d < 3; ++d) ih2 += 1.0 / (h->h[d] * h->h[d]);
+  P.wc = (float)(h->c[0] * ih2);
+  for (int i = 1; i <= h->R; ++i) {
+    P.wx[i - 1] = (float)(h->c[i] / (h->h[0] * h->h[0]));
+    P.wy[i - 1] = (float)(h->c[i] / (h->h[1] * h->h[1]));
+    P.wz[i - 1] = (float)(h->c[i] / (h->h[2] * h->h[2]));
+  }
+  const bool src_on = h->have_src && h->src.npts > 0;
+  P.s_colptr = src_on ? h->src.colptr : nullptr;
+  P.s_ent = src_on ? h->src.ent : nullptr;
+  P.src_dcmp = h->src_dcmp;
+  P.npts = h->src.npts;
+  const bool rec_on = h->have_rec && h->rec.npts > 0 && nrec > 0;
+  P.r_colptr = rec_on ? h->rec.colptr : nullptr;
+  P.r_ent = rec_on ? h->rec.ent : nullptr;
+  P.rec_dcmp = h->rec_dcmp;
+  P.nrpts = h->rec.npts;
+  P.ring = h->ring;
+  P.progress = h->progress;
+  P.err = h->err;
+  P.timeout_ns = (long long)(h->opt.wait_timeout_s * 1e9);
+
+  // upload both pass tables (one-step first, blocked after it)
+  std::vector<PassDesc> all(p1.launch_passes);
+  const int off_T = (int)all.size();
+  if (T > 1) all.insert(all.end(), pT.launch_passes.begin(), pT.launch_passes.end());
+  if ((int)all.size() > h->pass_cap) {
+    cudaFree(h->d_pass);
+    h->d_pass = nullptr;
+    h->pass_cap = 0;
+    TB_CUDA(h, cudaMalloc(&h->d_pass, sizeof(PassDesc) * all.size()));
+    h->pass_cap = (int)all.size();
+  }
+  TB_CUDA(h, cudaMemcpyAsync(h->d_pass, all.data(), sizeof(PassDesc) * all.size(),
+                             cudaMemcpyHostToDevice, st));
+
+  int cur = 0, prev = 1;  // field indices of u^n and u^{n-1}
+  int rec_base = 0, rec_fill = 0;
+  auto flush_receivers = [&]() -> int {
+    if (rec_on && rec_fill > 0 && dtr) {
+      cudaEvent_t a = nullptr, b = nullptr;
+      if (h->opt.profile) {
+        a = ev_next(h);
+        b = ev_next(h);
+        h->ev_kind.push_back(1);
+        if (a) cudaEventRecord(a, st);
+      }
+      cudaError_t e = finalize_traces(rec_fill, nrec, h->rec.corner_id, h->rec.corner_w, h->rec_dcmp,
+                                      h->rec.npts, dtr + (size_t)rec_base * nrec, st);
+      if (h->opt.profile && b) cudaEventRecord(b, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "receiver finalize");
+    }
+    rec_base += rec_fill;
+    rec_fill = 0;
+    return TB_OK;
+  };
+  auto run = [&](int TT, const Plan& pl, int pass_off, int out0, int out1, int step0) -> int {
+    P.u_cur = h->field[cur];
+    P.u_prev = h->field[prev];
+    P.out0 = h->field[out0];
+    P.out1 = out1 >= 0 ? h->field[out1] : nullptr;
+    P.step0 = step0;
+    P.rec_base = rec_base;
+    for (size_t L = 0; L < pl.launch_first.size(); ++L) {
+      const int first = pl.launch_first[L];
+      const int last = L + 1 < pl.launch_first.size() ? pl.launch_first[L + 1] : (int)pl.launch_passes.size();
+      P.pass = h->d_pass + pass_off + first;
+      P.npass = last - first;
+      P.prog_base = h->prog_base;
+      int maxsteps = 0;
+      for (int i = first; i < last; ++i) {
+        const PassDesc& d = pl.launch_passes[i];
+        maxsteps = std::max(maxsteps, d.xo1 - 1 + (TT - 1) * h->R - d.xc0 + 1);
+      }
+      h->prog_base += (unsigned long long)maxsteps + 2;
+      cudaEvent_t a = nullptr, b = nullptr;
+      if (h->opt.profile) {
+        a = ev_next(h);
+        b = ev_next(h);
+        h->ev_kind.push_back(0);
+        if (a) cudaEventRecord(a, st);
+      }
+      cudaError_t e = sweep_launch(h->R, TT, P, pl.launch_ctas[L], TT > 1, st);
+      if (h->opt.profile && b) cudaEventRecord(b, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, TT > 1 ? "blocked sweep launch" : "one-step launch");
+    }
+    return TB_OK;
+  };
+
+  int n = 0;
+  while (n < nt) {
+    if (T > 1 && n + T <= nt) {
+      if (rec_on && rec_fill + T > h->rec_cap && (s = flush_receivers()) != TB_OK) return s;
+      // the two fields not holding (u^n, u^{n-1}) receive (u^{n+T}, u^{n+T-1})
+      int free_idx[2], nf = 0;
+      for (int i = 0; i < 4; ++i)
+        if (i != cur && i != prev) free_idx[nf++] = i;
+      if ((s = run(T, pT, off_T, free_idx[0], free_idx[1], n)) != TB_OK) return s;
+      cur = free_idx[0];
+      prev = free_idx[1];
+      rec_fill += T;
+      n += T;
+    } else {
+      if (rec_on && rec_fill + 1 > h->rec_cap && (s = flush_receivers()) != TB_OK) return s;
+      if ((s = run(1, p1, 0, prev, -1, n)) != TB_OK) return s;
+      std::swap(cur, prev);
+      rec_fill += 1;
+      n += 1;
+    }
+  }
+  if ((s = flush_receivers()) != TB_OK) return s;
+  h->cur_idx = cur;
+  h->prev_idx = prev;
+  h->last_nt = nt;
+
+  if (T > 1) {
+    int err = 0;
+    TB_CUDA(h, cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TB_CUDA(h, cudaStreamSynchronize(st));
+    if (err) return fail(h, TB_ETIMEOUT, "a blocked-sweep CTA timed out waiting for a neighbour");
+  }
+  if (host_traces) {
+    TB_CUDA(h, cudaMemcpyAsync(traces, h->traces_dev, sizeof(float) * (size_t)nt * nrec,
+                               cudaMemcpyDeviceToHost, st));
+    TB_CUDA(h, cudaStreamSynchronize(st));
+  }
+  if (h->opt.check_nan && traces && nrec > 0 && nt > 0) {
+    int cnt = 0;
+    TB_CUDA(h, count_nonfinite(dtr, (int64_t)nt * nrec, h->err + 1, st));
+    TB_CUDA(h, cudaMemcpyAsync(&cnt, h->err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TB_CUDA(h, cudaStreamSynchronize(st));
+    if (cnt) return fail(h, TB_EDIVERGED, "%d non-finite trace samples", cnt);
+  }
+  h->msg[0] = 0;
+  return TB_OK;
+}
+
+extern "C" int tb_get_field(tb_handle* h, int which, float* out, void* stream) {
+  if (!h) return TB_EINVAL;
+  if (h->last_nt < 0) return fail(h, TB_ESTATE, "no forward run yet");
+  if ((which != 0 && which != 1) || !out) return fail(h, TB_EINVAL, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  const float* src = h->field[which == 0 ? h->cur_idx : h->prev_idx];
+  const size_t N = (size_t)h->n[0] * h->n[1] * h->n[2];
+  if (is_device_ptr(out)) {
+    TB_CUDA(h, unpad_copy(src, out, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->n2p, st));
+    return TB_OK;
+  }
+  float* tmp = nullptr;
+  TB_CUDA(h, cudaMalloc(&tmp, sizeof(float) * N));
+  cudaError_t e = unpad_copy(src, tmp, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->n2p, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, sizeof(float) * N, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tb_get_field");
+  return TB_OK;
+}
+
+extern "C" int tb_get_source_points(tb_handle* h, int64_t* npts, int64_t* lin, float* dcmp) {
+  if (!h || !npts) return TB_EINVAL;
+  if (!h->have_src) return fail(h, TB_ESTATE, "no sources set");
+  *npts = h->src.npts;
+  if (h->src.npts > 0) {
+    if (lin) TB_CUDA(h, cudaMemcpy(lin, h->src.lin, sizeof(int64_t) * h->src.npts, cudaMemcpyDeviceToHost));
+    if (dcmp)
+      TB_CUDA(h, cudaMemcpy(dcmp, h->src_dcmp, sizeof(float) * (size_t)h->src_nt * h->src.npts,
+                            cudaMemcpyDeviceToHost));
+  }
+  return TB_OK;
+}
+
+extern "C" int tb_get_receiver_points(tb_handle* h, int64_t* npts, int64_t* lin, int32_t* corner_id,
+                                      float* corner_w) {
+  if (!h || !npts) return TB_EINVAL;
+  if (!h->have_rec) return fail(h, TB_ESTATE, "no receivers set");
+  *npts = h->rec.npts;
+  if (h->rec.npts > 0 && lin)
+    TB_CUDA(h, cudaMemcpy(lin, h->rec.lin, sizeof(int64_t) * h->rec.npts, cudaMemcpyDeviceToHost));
+  if (h->rec.npt > 0) {
+    if (corner_id)
+      TB_CUDA(h, cudaMemcpy(corner_id, h->rec.corner_id, sizeof(int) * 8 * h->rec.npt, cudaMemcpyDeviceToHost));
+    if (corner_w)
+      TB_CUDA(h, cudaMemcpy(corner_w, h->rec.corner_w, sizeof(float) * 8 * h->rec.npt, cudaMemcpyDeviceToHost));
+  }
+  return TB_OK;
+}
+
+extern "C" int tb_kernel_time(tb_handle* h, int kind, int* launches, double* ms) {
+  if (!h || !launches || !ms) return TB_EINVAL;
+  *launches = 0;
+  *ms = 0.0;
+  if (!h->opt.profile) return fail(h, TB_ESTATE, "profiling is off (tb_options.profile)");
+  if (h->ev_used > 0) TB_CUDA(h, cudaStreamSynchronize(h->ev_stream));
+  for (size_t i = 0; i < h->ev_kind.size(); ++i) {
+    if (h->ev_kind[i] != kind) continue;
+    float t = 0.f;
+    TB_CUDA(h, cudaEventElapsedTime(&t, h->ev[2 * i], h->ev[2 * i + 1]));
+    *ms += t;
+    ++*launches;
+  }
+  return TB_OK;
+}
+
+namespace tbi {
+cudaError_t selftest_wait(long long timeout_ns, cudaStream_t st, int* timed_out);
+}
+
+extern "C" int tb_selftest_wait(double timeout_s, void* stream) {
+  if (!(timeout_s > 0) || timeout_s > 10) return TB_EINVAL;
+  int timed_out = -1;
+  cudaError_t e = tbi::selftest_wait((long long)(timeout_s * 1e9), (cudaStream_t)stream, &timed_out);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TB_ECUDA;
+  }
+  return timed_out == 1 ? TB_ETIMEOUT : (timed_out == 0 ? TB_OK : TB_ECUDA);
+}

@@ -1,0 +1,110 @@
+// Internal declarations of the CUDA path (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <vector>
+
+#include "tb.h"
+
+namespace tbi {
+
+// Counts kernel launches made by the library (tb_launch_count).
+void count_launch(int n = 1);
+
+// Blocked sweeps keep one tile of (TY x 64) columns per CTA; the pass table
+// describes which CTAs stream which (x-chunk, y-band) of the grid.
+struct PassDesc {
+  int cta0;      // first CTA of the pass (blockIdx.x)
+  int nty, ntz;  // tiles along axis 1 and axis 2
+  int yb0;       // first row (axis 1) of the band's tile coverage
+  int yo0, yo1;  // rows whose results this pass owns (written out)
+  int xc0, xc1;  // planes (axis 0) the first fused step computes
+  int xo0, xo1;  // planes whose results this pass owns
+};
+
+// Launch parameters of one sweep (one-step or T fused steps).
+struct SweepParams {
+  int n0, n1, n2, n2p;          // grid, and row pitch of the padded fields
+  const float* u_cur;           // u^n
+  const float* u_prev;          // u^{n-1}
+  float* out0;                  // u^{n+T}   (one-step: may alias u_prev)
+  float* out1;                  // u^{n+T-1} (T > 1)
+  const float* c2;              // dt^2 vp^2 (padded layout)
+  const float* damp_b;          // [n0 + n1 + n2] eta_d / (2 dt) per axis
+  float wc;                     // c0 * sum_d 1/h_d^2
+  float wx[6], wy[6], wz[6];    // c_i / h_d^2, i = 1..r
+  // grid-aligned sources (Sec. II-A)
+  const int* s_colptr;          // [n1*n2 + 1]
+  const int2* s_ent;            // (x, id) by column, ascending x
+  const float* src_dcmp;        // [nt][npts]
+  int64_t npts;
+  // grid-aligned receivers
+  const int* r_colptr;
+  const int2* r_ent;
+  float* rec_dcmp;              // [cap][nrpts]
+  int64_t nrpts;
+  int rec_base;                 // step index stored in row 0 of rec_dcmp
+  int step0;                    // step index of the first fused step
+  // blocked-sweep coupling between CTAs
+  float* ring;                  // per tile, per stage, per slot: halo strips
+  unsigned long long* progress; // per CTA: completed steps (monotonic)
+  unsigned long long prog_base;
+  int* err;                     // device error flag (1 = wait timed out)
+  long long timeout_ns;
+  const PassDesc* pass;         // device copy of the pass table
+  int npass;
+};
+
+struct SweepShape {
+  int R, T, TY;
+  int threads;
+  size_t smem;
+  int ring_floats_per_cta;      // floats of ring storage per CTA
+};
+
+// Kernel configuration and launch (tb_acoustic*.cu).
+bool sweep_shape(int R, int T, SweepShape* s);
+cudaError_t sweep_max_ctas(int R, int T, int* per_sm);
+cudaError_t sweep_launch(int R, int T, const SweepParams& p, int nctas, bool cooperative,
+                         cudaStream_t st);
+
+// Inspector and setup kernels (tb_inspector.cu).
+struct PointTables {
+  int npt = 0;                  // off-grid points given
+  int64_t npts = 0;             // unique affected grid points
+  int64_t nvalid = 0;           // corner entries with weight != 0
+  int64_t* lin = nullptr;       // [npts] ascending unpadded linear index
+  int* colptr = nullptr;        // [n1*n2 + 1]
+  int2* ent = nullptr;          // [npts] (x, id) by column then x
+  int* corner_id = nullptr;     // [npt*8] (receivers)
+  float* corner_w = nullptr;    // [npt*8] (receivers)
+  // inspector scratch kept for the decomposition
+  unsigned long long* keys = nullptr;  // sorted corner keys [P]
+  double* w8 = nullptr;         // [npt*8] corner weights
+  int64_t* gstart = nullptr;    // [npts + 1] first sorted entry of each point
+  int* ent_id = nullptr;        // [P] point id of each sorted entry
+  size_t bytes = 0;
+};
+
+void free_tables(PointTables* t);
+// Builds lin, colptr, ent (+ corner tables when want_corners).  coords on
+// the device.  Returns TB_OK / TB_EINVAL / TB_ENOMEM / TB_ECUDA.
+int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coords,
+            bool want_corners, PointTables* t, cudaStream_t st, const char** why);
+// src_dcmp[t][id] = c2(p_id) * sum_e w_e q_{s(e)}[t]  (FP64 sum, FP32 out)
+cudaError_t decompose(const PointTables* t, int nt, const float* d_wav, const float* c2,
+                      int n1, int n2, int n2p, float* d_dcmp, cudaStream_t st);
+cudaError_t finalize_traces(int nsteps, int nrec, const int* corner_id, const float* corner_w,
+                            const float* rec_dcmp, int64_t nrpts, float* traces,
+                            cudaStream_t st);
+cudaError_t model_vmax(const float* vp, int64_t N, float* d_out, int* d_bad, cudaStream_t st);
+cudaError_t model_c2(const float* vp, int n0, int n1, int n2, int n2p, double dt2, float* c2,
+                     cudaStream_t st);
+cudaError_t pad_copy(const float* src, float* dst, int n0, int n1, int n2, int n2p,
+                     cudaStream_t st);
+cudaError_t unpad_copy(const float* src, float* dst, int n0, int n1, int n2, int n2p,
+                       cudaStream_t st);
+cudaError_t count_nonfinite(const float* a, int64_t n, int* d_count, cudaStream_t st);
+
+}  // namespace tbi

@@ -8,43 +8,36 @@
 #include <cstring>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "tb_internal.cuh"
 
 namespace tbi {
-cudaError_t sweep_launch_r2(int T, const SweepParams& p, int nctas, bool coop, cudaStream_t st);
-cudaError_t sweep_launch_r4(int T, const SweepParams& p, int nctas, bool coop, cudaStream_t st);
-cudaError_t sweep_launch_r6(int T, const SweepParams& p, int nctas, bool coop, cudaStream_t st);
-cudaError_t sweep_occupancy_r2(int T, int* per_sm);
-cudaError_t sweep_occupancy_r4(int T, int* per_sm);
-cudaError_t sweep_occupancy_r6(int T, int* per_sm);
-bool sweep_shape_r2(int T, SweepShape* s);
-bool sweep_shape_r4(int T, SweepShape* s);
-bool sweep_shape_r6(int T, SweepShape* s);
+cudaError_t sweep_dispatch_r2(int what, int T, const SweepParams* p, int nctas, bool coop,
+                              cudaStream_t st, int* per_sm, SweepShape* s);
+cudaError_t sweep_dispatch_r4(int what, int T, const SweepParams* p, int nctas, bool coop,
+                              cudaStream_t st, int* per_sm, SweepShape* s);
+cudaError_t sweep_dispatch_r6(int what, int T, const SweepParams* p, int nctas, bool coop,
+                              cudaStream_t st, int* per_sm, SweepShape* s);
 
-bool sweep_shape(int R, int T, SweepShape* s) {
+static cudaError_t sweep_dispatch(int R, int what, int T, const SweepParams* p, int nctas, bool coop,
+                                  cudaStream_t st, int* per_sm, SweepShape* s) {
   switch (R) {
-    case 2: return sweep_shape_r2(T, s);
-    case 4: return sweep_shape_r4(T, s);
-    case 6: return sweep_shape_r6(T, s);
-  }
-  return false;
-}
-cudaError_t sweep_max_ctas(int R, int T, int* per_sm) {
-  switch (R) {
-    case 2: return sweep_occupancy_r2(T, per_sm);
-    case 4: return sweep_occupancy_r4(T, per_sm);
-    case 6: return sweep_occupancy_r6(T, per_sm);
+    case 2: return sweep_dispatch_r2(what, T, p, nctas, coop, st, per_sm, s);
+    case 4: return sweep_dispatch_r4(what, T, p, nctas, coop, st, per_sm, s);
+    case 6: return sweep_dispatch_r6(what, T, p, nctas, coop, st, per_sm, s);
   }
   return cudaErrorInvalidValue;
+}
+bool sweep_shape(int R, int T, SweepShape* s) {
+  return sweep_dispatch(R, 2, T, nullptr, 0, false, nullptr, nullptr, s) == cudaSuccess;
+}
+cudaError_t sweep_max_ctas(int R, int T, int* per_sm) {
+  return sweep_dispatch(R, 1, T, nullptr, 0, false, nullptr, per_sm, nullptr);
 }
 cudaError_t sweep_launch(int R, int T, const SweepParams& p, int nctas, bool cooperative,
                          cudaStream_t st) {
-  switch (R) {
-    case 2: return sweep_launch_r2(T, p, nctas, cooperative, st);
-    case 4: return sweep_launch_r4(T, p, nctas, cooperative, st);
-    case 6: return sweep_launch_r6(T, p, nctas, cooperative, st);
-  }
-  return cudaErrorInvalidValue;
+  return sweep_dispatch(R, 0, T, &p, nctas, cooperative, st, nullptr, nullptr);
 }
 }  // namespace tbi
 
@@ -69,6 +62,9 @@ struct tb_handle {
   bool have_model = false;
   float* field[4] = {nullptr, nullptr, nullptr, nullptr};
   float* c2 = nullptr;
+  CUtensorMap tm_box[4];   // u^n boxes with halo, per field buffer
+  CUtensorMap tm_tile[4];  // own tiles, per field buffer
+  CUtensorMap tm_c2;       // own tiles of c2
   float* damp_b = nullptr;
   // sources
   PointTables src;
@@ -229,6 +225,28 @@ extern "C" int tb_destroy(tb_handle* h) {
   return TB_OK;
 }
 
+// TMA descriptor of a padded field [n0][n1][n2p] (only n2 columns are in
+// the tensor, so cells past n2 read as zeros) with a box of bw x bh x 1.
+static cudaError_t make_tmap(CUtensorMap* m, float* base, const int64_t n[3], int n2p, int bw, int bh) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)n[2], (cuuint64_t)n[1], (cuuint64_t)n[0]};
+  const cuuint64_t strides[2] = {(cuuint64_t)n2p * 4, (cuuint64_t)n2p * 4 * n[1]};
+  const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int physics,
                          const tb_options* opt, tb_handle** out) {
   if (!out || !n || !hsp) return TB_EINVAL;
@@ -236,7 +254,7 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   if (physics != TB_ACOUSTIC) return TB_EINVAL;
   if (so != 4 && so != 8 && so != 12) return TB_EINVAL;
   for (int d = 0; d < 3; ++d) {
-    if (n[d] < so + 2 || n[d] > (1 << 20) || !(hsp[d] > 0)) return TB_EINVAL;
+    if (n[d] < so + 2 || n[d] > 65535 || !(hsp[d] > 0)) return TB_EINVAL;
   }
   if (n[0] * n[1] * n[2] >= (1ll << 40)) return TB_EINVAL;
   tb_handle* h = new tb_handle();
@@ -247,8 +265,9 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   h->so = so;
   h->R = so / 2;
   if (opt) h->opt = *opt;
-  if (h->opt.time_tile == 0) h->opt.time_tile = 4;
-  if (h->opt.time_tile < 1 || h->opt.time_tile > 4 || h->opt.nbl < 0 || h->opt.y_bands < 0 ||
+  const int tmax = so == 12 ? 3 : 4;  // four fused so12 steps exceed shared memory
+  if (h->opt.time_tile == 0) h->opt.time_tile = tmax;
+  if (h->opt.time_tile < 1 || h->opt.time_tile > tmax || h->opt.nbl < 0 || h->opt.y_bands < 0 ||
       h->opt.x_chunks < 0) {
     delete h;
     return TB_EINVAL;
@@ -268,6 +287,13 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   if (e == cudaSuccess) e = cudaMalloc(&h->damp_b, sizeof(float) * (n[0] + n[1] + n[2]));
   if (e == cudaSuccess) e = cudaMalloc(&h->err, sizeof(int) * 4);
   if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int) * 4);
+  SweepShape sh;
+  if (e == cudaSuccess && !sweep_shape(h->R, 1, &sh)) e = cudaErrorInvalidValue;
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    e = make_tmap(&h->tm_box[i], h->field[i], n, h->n2p, sh.box_w, sh.box_h);
+    if (e == cudaSuccess) e = make_tmap(&h->tm_tile[i], h->field[i], n, h->n2p, 64, sh.TY);
+  }
+  if (e == cudaSuccess) e = make_tmap(&h->tm_c2, h->c2, n, h->n2p, 64, sh.TY);
   if (e != cudaSuccess) {
     int code = e == cudaErrorMemoryAllocation ? TB_ENOMEM : TB_ECUDA;
     cudaGetLastError();
@@ -627,14 +653,13 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   P.n2p = h->n2p;
   P.c2 = h->c2;
   P.damp_b = h->damp_b;
-  double ih2 = 0.0;
-  for (int d = 0; d < 3; ++d) ih2 += 1.0 / (h->h[d] * h->h[d]);
-  P.wc = (float)(h->c[0] * ih2);
-  for (int i = 1; i <= h->R; ++i) {
-    P.wx[i - 1] = (float)(h->c[i] / (h->h[0] * h->h[0]));
-    P.wy[i - 1] = (float)(h->c[i] / (h->h[1] * h->h[1]));
-    P.wz[i - 1] = (float)(h->c[i] / (h->h[2] * h->h[2]));
-  }
+  for (int d = 0; d < 3; ++d)
+    for (int i = 1; i <= h->R; ++i) {
+      const float wf = (float)(h->c[i] / (h->h[d] * h->h[d]));
+      unsigned int bits;
+      memcpy(&bits, &wf, sizeof(bits));
+      P.w2[d][i - 1] = ((unsigned long long)bits << 32) | bits;
+    }
   const bool src_on = h->have_src && h->src.npts > 0;
   P.s_colptr = src_on ? h->src.colptr : nullptr;
   P.s_ent = src_on ? h->src.ent : nullptr;
@@ -687,6 +712,9 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   auto run = [&](int TT, const Plan& pl, int pass_off, int out0, int out1, int step0) -> int {
     P.u_cur = h->field[cur];
     P.u_prev = h->field[prev];
+    P.tm_u = h->tm_box[cur];
+    P.tm_p = h->tm_tile[prev];
+    P.tm_c = h->tm_c2;
     P.out0 = h->field[out0];
     P.out1 = out1 >= 0 ? h->field[out1] : nullptr;
     P.step0 = step0;

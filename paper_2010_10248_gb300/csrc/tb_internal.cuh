@@ -1,6 +1,7 @@
 // Internal declarations of the CUDA path (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <vector>
@@ -25,6 +26,9 @@ struct PassDesc {
 
 // Launch parameters of one sweep (one-step or T fused steps).
 struct SweepParams {
+  CUtensorMap tm_u;             // u^n: (TY+2r) x (64+2rp) boxes with halo
+  CUtensorMap tm_p;             // u^{n-1}: TY x 64 tiles
+  CUtensorMap tm_c;             // c2: TY x 64 tiles
   int n0, n1, n2, n2p;          // grid, and row pitch of the padded fields
   const float* u_cur;           // u^n
   const float* u_prev;          // u^{n-1}
@@ -32,8 +36,7 @@ struct SweepParams {
   float* out1;                  // u^{n+T-1} (T > 1)
   const float* c2;              // dt^2 vp^2 (padded layout)
   const float* damp_b;          // [n0 + n1 + n2] eta_d / (2 dt) per axis
-  float wc;                     // c0 * sum_d 1/h_d^2
-  float wx[6], wy[6], wz[6];    // c_i / h_d^2, i = 1..r
+  unsigned long long w2[3][6];  // c_i / h_d^2 (i = 1..r) as packed (w, w) pairs
   // grid-aligned sources (Sec. II-A)
   const int* s_colptr;          // [n1*n2 + 1]
   const int2* s_ent;            // (x, id) by column, ascending x
@@ -61,6 +64,8 @@ struct SweepShape {
   int threads;
   size_t smem;
   int ring_floats_per_cta;      // floats of ring storage per CTA
+  int box_w, box_h;             // u^n box (axis 2, axis 1) incl. halo
+  int halo_w;                   // axis-2 halo width of the box
 };
 
 // Kernel configuration and launch (tb_acoustic*.cu).

@@ -2,5 +2,15 @@
 #include "tb_sweep.cuh"
 
 namespace tbi {
-TBI_DEFINE_RADIUS(2)
+// what: 0 launch, 1 occupancy query, 2 shape query
+cudaError_t sweep_dispatch_r2(int what, int T, const SweepParams* p, int nctas, bool coop,
+                               cudaStream_t st, int* per_sm, SweepShape* s) {
+  switch (T) {
+    TBI_DEFINE_RADIUS_T(2, 1)
+    TBI_DEFINE_RADIUS_T(2, 2)
+    TBI_DEFINE_RADIUS_T(2, 3)
+    TBI_DEFINE_RADIUS_T(2, 4)
+  }
+  return cudaErrorInvalidValue;
+}
 }  // namespace tbi

@@ -1,6 +1,15 @@
-// Sweep kernels of radius 6 (space order 12), T = 1..4 fused steps.
+// Sweep kernels of radius 6 (space order 12), T = 1..3 fused steps.
 #include "tb_sweep.cuh"
 
 namespace tbi {
-TBI_DEFINE_RADIUS(6)
+// what: 0 launch, 1 occupancy query, 2 shape query
+cudaError_t sweep_dispatch_r6(int what, int T, const SweepParams* p, int nctas, bool coop,
+                               cudaStream_t st, int* per_sm, SweepShape* s) {
+  switch (T) {
+    TBI_DEFINE_RADIUS_T(6, 1)
+    TBI_DEFINE_RADIUS_T(6, 2)
+    TBI_DEFINE_RADIUS_T(6, 3)
+  }
+  return cudaErrorInvalidValue;
+}
 }  // namespace tbi

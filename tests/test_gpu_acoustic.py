@@ -252,6 +252,7 @@ def test_full_size_short_run_matches_oracle(tb, big):
     tr_o, u_o, _ = oracle.acoustic_forward(big.shape, big.spacing, big.so, dt, nt,
                                            big.vp.astype(np.float64), nbl=big.nbl,
                                            src_xyz=big.src_xyz, src_wav=wav, rec_xyz=big.rec_xyz)
+    print(f"512^3 so8 {nt} steps: rel-L2 field {rel(u, u_o):.3e}, traces {rel(tr, tr_o):.3e}")
     assert rel(u, u_o) <= TOL, rel(u, u_o)
     assert rel(tr, tr_o) <= TOL, rel(tr, tr_o)
 
@@ -281,5 +282,6 @@ def test_fp32_error_growth_1000_steps(tb):
                                            c["vp"].astype(np.float64), nbl=c["nbl"],
                                            src_xyz=c["src"], src_wav=wav, rec_xyz=c["rec"])
     tr, u, _ = gpu_run(tb, c, dt, wav, "blocked", time_tile=4)
+    print(f"128^3 so8 1000 steps: rel-L2 field {rel(u, u_o):.3e}, traces {rel(tr, tr_o):.3e}")
     assert rel(u, u_o) <= TOL, rel(u, u_o)
     assert rel(tr, tr_o) <= TOL, rel(tr, tr_o)

@@ -60,8 +60,9 @@ typedef struct tb_handle tb_handle;
 /* Tuning and behaviour options; zero-initialise and set what you need.
  * All-zero options give the defaults noted per field. */
 typedef struct {
-  int time_tile;   /* T: time steps fused per blocked sweep (Sec. II-B). 0 -> 4.
-                      Supported: 1, 2, 3, 4.                                     */
+  int time_tile;   /* T: time steps fused per blocked sweep (Sec. II-B).
+                      Supported: 1..4 (space order 4, 8), 1..2 (space order 12);
+                      0 -> the largest supported.                               */
   int nbl;         /* width in cells of the built-in sponge (Sec. IV-B); 0: none  */
   int y_bands;     /* blocked sweep: number of bands along axis 1; 0 -> fewest
                       bands whose tiles are co-resident on the GPU                */

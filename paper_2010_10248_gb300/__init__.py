@@ -30,7 +30,7 @@ class Propagator:
     [nt, nrec] unless a destination is given.
     """
 
-    def __init__(self, shape, spacing, space_order, *, time_tile=4, nbl=0, y_bands=0,
+    def __init__(self, shape, spacing, space_order, *, time_tile=0, nbl=0, y_bands=0,
                  x_chunks=0, profile=False, check_nan=False, wait_timeout_s=0.0):
         import torch
         self._torch = torch

@@ -265,7 +265,7 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   h->so = so;
   h->R = so / 2;
   if (opt) h->opt = *opt;
-  const int tmax = so == 12 ? 3 : 4;  // four fused so12 steps exceed shared memory
+  const int tmax = so == 12 ? 2 : 4;  // more fused so12 steps exceed shared memory
   if (h->opt.time_tile == 0) h->opt.time_tile = tmax;
   if (h->opt.time_tile < 1 || h->opt.time_tile > tmax || h->opt.nbl < 0 || h->opt.y_bands < 0 ||
       h->opt.x_chunks < 0) {
@@ -656,9 +656,7 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   for (int d = 0; d < 3; ++d)
     for (int i = 1; i <= h->R; ++i) {
       const float wf = (float)(h->c[i] / (h->h[d] * h->h[d]));
-      unsigned int bits;
-      memcpy(&bits, &wf, sizeof(bits));
-      P.w2[d][i - 1] = ((unsigned long long)bits << 32) | bits;
+      P.w2[d][i - 1] = make_float2(wf, wf);
     }
   const bool src_on = h->have_src && h->src.npts > 0;
   P.s_colptr = src_on ? h->src.colptr : nullptr;

@@ -36,7 +36,7 @@ struct SweepParams {
   float* out1;                  // u^{n+T-1} (T > 1)
   const float* c2;              // dt^2 vp^2 (padded layout)
   const float* damp_b;          // [n0 + n1 + n2] eta_d / (2 dt) per axis
-  unsigned long long w2[3][6];  // c_i / h_d^2 (i = 1..r) as packed (w, w) pairs
+  float2 w2[3][6];              // c_i / h_d^2 (i = 1..r) as (w, w) pairs
   // grid-aligned sources (Sec. II-A)
   const int* s_colptr;          // [n1*n2 + 1]
   const int2* s_ent;            // (x, id) by column, ascending x

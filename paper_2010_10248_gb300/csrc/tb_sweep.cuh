@@ -3,37 +3,37 @@
 //
 // Layout.  Fields are [n0][n1][n2p] floats, axis 2 contiguous (row pitch
 // n2p = n2 rounded up to 4).  A CTA owns a tile of TY rows (axis 1) by 64
-// columns (axis 2) and streams it along axis 0: one warp per row, each lane
-// owns two adjacent columns (float2 / packed f32x2 arithmetic).
+// columns (axis 2) and streams it along axis 0.  TY compute warps own one
+// row each (a lane owns two adjacent columns: float2 loads and packed f32x2
+// arithmetic); one more warp is the producer.
 //
-// Data movement (per stream step j, asynchronous and prefetched):
-//   * u^n plane j+r as a (TY+2r) x (64+2rp) box with its halo, by a 3-D TMA
-//     load into a ring of shared-memory planes (out-of-grid cells arrive as
-//     zeros, which is the zero boundary of Eq. 1);
-//   * the own tiles of u^{n-1} and c2 = dt^2/m by TMA into their rings;
-//   * for fused steps k >= 1, the neighbours' halo strips of level n+k by
-//     16-byte cp.async from a small L2-resident ring in global memory, one
-//     stream step ahead.
-// Every ring slot has an mbarrier; one thread refills a slot right after
-// the stream step that last reads it.
+// Producer warp (asynchronous data movement, runs ahead of the compute):
+//   * u^n planes as (TY+2r) x (64+2rp) boxes with halo, by 3-D TMA, into a
+//     ring holding planes j-r .. j+r+PF (out-of-grid cells arrive as zeros:
+//     the zero boundary of Eq. 1);
+//   * the own tiles of u^{n-1} and c2 = dt^2/m, by TMA, into their rings;
+//   * for fused steps k >= 1, the neighbours' halo strips of level n+k, by
+//     bulk copies from a small L2-resident ring in global memory, after an
+//     acquire on the neighbours' progress counters;
+//   * retires stream steps (an mbarrier the compute warps arrive on), frees
+//     their ring slots, and publishes the CTA's progress (release).
+// Compute warps wait on mbarriers only; every wait is bounded by a timeout,
+// after which the CTA records an error and returns (the producer first
+// drains its own copies in flight).
 //
 // Temporal blocking (Sec. II-B, re-designed for the GPU).  Fused step k
-// (k = 0..T-1) computes level n+k+1 at plane q_k = j - k r.  Each fused step
-// keeps, per owned column, a register queue of the 2r+1 planes of its input
-// level around q_k (the axis-0 neighbours of the stencil); axis-1 and axis-2
-// neighbours come from a shared plane.  A step's output goes straight into
-// the next step's queue, so intermediate levels never reach HBM: per T
-// steps a point costs one read of u^n, u^{n-1}, c2 and one write of
-// u^{n+T}, u^{n+T-1}.
-//
-// Halo exchange between CTAs.  All CTAs of a pass stream in lockstep
-// (cooperative launch, co-resident).  The boundary strips of every
-// intermediate level are published to the ring; a CTA prefetches its
-// neighbours' strips of stream step j+1 during step j, after an acquire on
-// the neighbours' progress counters.  Waits are bounded by a timeout; on
-// expiry the CTA sets the error flag, drains its own copies and returns.
-// Within a pass there is no redundant computation; passes (bands along axis
-// 1, chunks along axis 0) overlap by (T-1) r rows or planes.
+// (k = 0..T-1) computes level n+k+1 at plane q_k = j - k r of stream step
+// j.  Step 0 reads all its neighbours from the u^n ring.  Steps k >= 1 keep,
+// per owned column, a register queue of the 2r+1 planes of their input
+// level around q_k (the axis-0 neighbours) and read axis-1/axis-2
+// neighbours from a double-buffered shared plane (centres written by the
+// compute warps, halos copied by the producer).  A step's output goes
+// straight into the next step's queue, so intermediate levels never reach
+// HBM: per T steps a point costs one read of u^n, u^{n-1}, c2 and one write
+// of u^{n+T}, u^{n+T-1}.  All CTAs of a pass stream in lockstep
+// (cooperative launch, co-resident); within a pass there is no redundant
+// computation, passes (bands along axis 1, chunks along axis 0) overlap by
+// (T-1) r rows or planes.
 //
 // Grid-aligned sparse operators (Sec. II-A).  Per column, the inspector's
 // entries (x, id) are sorted by x; each fused step walks them with its own
@@ -57,30 +57,34 @@ constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
 template <int R, int T, int TY>
 struct SweepCfg {
   static constexpr int TZ = 64;
-  static constexpr int NT = 32 * TY;
-  static constexpr int RP = (R + 3) / 4 * 4;  // axis-2 halo width in shared memory
-  static constexpr int SW = TZ + 2 * RP;      // plane row stride (floats)
+  static constexpr int NT = 32 * TY;           // compute threads
+  static constexpr int NTHREADS = NT + 32;     // + producer warp
+  static constexpr int RP = (R + 3) / 4 * 4;   // axis-2 halo width in shared memory
+  static constexpr int SW = TZ + 2 * RP;       // plane row stride (floats)
   static constexpr int SH = TY + 2 * R;
   static constexpr int PLANE = SW * SH;
   static constexpr int PSLOT = (int)(align128(PLANE * 4) / 4);
   static constexpr int TILE = TY * TZ;
-  static constexpr int Q = 2 * R + 1;               // queue length
-  static constexpr int PF = 2;                      // prefetch distance in planes
-  static constexpr int NU = R + 1 + PF;             // u^n box ring
-  static constexpr int NP = PF + 1;                 // u^{n-1} tile ring
-  static constexpr int NC = (T - 1) * R + 1 + PF;   // c2 tile ring
-  static constexpr int D = 2 * R + 2;               // halo ring slots per fused step (global)
+  static constexpr int Q = 2 * R + 1;                // queue length
+  static constexpr int PF = T == 1 ? 1 : 2;          // planes of prefetch beyond need
+  static constexpr int NU = 2 * R + 1 + PF;          // u^n box ring
+  static constexpr int NP = PF + 1;                  // u^{n-1} tile ring
+  static constexpr int NC = (T - 1) * R + 1 + PF;    // c2 tile ring
+  static constexpr int NDONE = 8;                    // step-retirement barriers
+  static constexpr int D = 2 * R + 2;                // halo ring slots per fused step (global)
   static constexpr int STRIP = 2 * R * TZ + 2 * TY * RP;
   static constexpr int RING_PER_CTA = T > 1 ? (T - 1) * D * STRIP : 0;
+  static constexpr int NSP = T > 1 ? 2 * (T - 1) : 0;  // fused-step planes
   static constexpr size_t OFF_U = 0;
   static constexpr size_t OFF_P = OFF_U + align128((size_t)NU * PSLOT * 4);
   static constexpr size_t OFF_C = OFF_P + align128((size_t)NP * TILE * 4);
   static constexpr size_t OFF_S = OFF_C + align128((size_t)NC * TILE * 4);
-  static constexpr size_t OFF_BASE = OFF_S + align128((size_t)(T > 1 ? 2 * (T - 1) : 0) * PSLOT * 4);
+  static constexpr size_t OFF_BASE = OFF_S + align128((size_t)NSP * PSLOT * 4);
   static constexpr size_t OFF_CNT = OFF_BASE + 4 * 2 * 2 * NT;
   static constexpr size_t OFF_CUR = OFF_CNT + 2 * 2 * 2 * NT;
   static constexpr size_t OFF_BAR = align128(OFF_CUR + 2 * 2 * T * 2 * NT);
-  static constexpr size_t SMEM = OFF_BAR + 8 * (NU + NP + NC) + 128;  // + base alignment
+  static constexpr int NBAR = NU + NP + NC + 2 + 2 + NDONE;  // u, p, c, halo[2], centre[2], done
+  static constexpr size_t SMEM = OFF_BAR + 8 * NBAR + 128;    // + base alignment
   static_assert(R % 2 == 0, "radius must be even for aligned float2 access");
   static_assert(TY >= R && TZ >= RP, "a halo must come from one neighbour tile");
   static_assert(SMEM <= 232448, "shared memory budget exceeded");
@@ -110,6 +114,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
@@ -135,10 +142,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+// Non-tensor bulk copy global -> shared (16-byte aligned, size multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Spin (one thread) until *flag >= target, at most timeout_ns after t0 and
 // at most 2^26 polls.  Returns false when the limit ran out.
@@ -167,34 +178,17 @@ __device__ __forceinline__ float point_update(float uc, float up, float lap, flo
 }
 
 // One neighbour pair of the Laplacian in differences form on a column pair,
-// acc + w ((a - u) + (b - u)), as packed f32x2 round-to-nearest operations.
-// The differences of close values are exact, so the large centre term never
-// cancels against the neighbour sum (in FP32 this keeps 1000-step runs ~40x
-// closer to the FP64 result than the c0 u + sum c_i (u_+i + u_-i) form).
-__device__ __forceinline__ unsigned long long pk2(float2 v) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
-  return r;
-}
-__device__ __forceinline__ float2 upk2(unsigned long long r) {
-  float2 v;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-  return v;
-}
-__device__ __forceinline__ float2 pair_term2(float2 acc, unsigned long long w2, float2 a, float2 b,
-                                             float2 u) {
-  unsigned long long da, db, e, r;
-  const unsigned long long uu = pk2(u);
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(da) : "l"(pk2(a)), "l"(uu));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(db) : "l"(pk2(b)), "l"(uu));
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(e) : "l"(da), "l"(db));
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(w2), "l"(e), "l"(pk2(acc)));
-  return upk2(r);
+// acc + w ((a - u) + (b - u)), as packed f32x2 round-to-nearest operations
+// (nu = -u).  The differences of close values are exact, so the large centre
+// term never cancels against the neighbour sum (in FP32 this keeps 1000-step
+// runs ~40x closer to the FP64 result than c0 u + sum c_i (u_+i + u_-i)).
+__device__ __forceinline__ float2 pair_term2(float2 acc, float2 w2, float2 a, float2 b, float2 nu) {
+  return __ffma2_rn(w2, __fadd2_rn(__fadd2_rn(a, nu), __fadd2_rn(b, nu)), acc);
 }
 
 // ----------------------------------------------------------------- kernel --
 template <int R, int T, int TY>
-__global__ void __launch_bounds__(32 * TY, T == 1 ? 2 : 1)
+__global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
     sweep_kernel(const __grid_constant__ SweepParams P) {
   using C = SweepCfg<R, T, TY>;
   constexpr int TZ = C::TZ, NT = C::NT, SW = C::SW, RP = C::RP;
@@ -205,12 +199,12 @@ __global__ void __launch_bounds__(32 * TY, T == 1 ? 2 : 1)
   float* pring = reinterpret_cast<float*>(smem + C::OFF_P);
   float* cring = reinterpret_cast<float*>(smem + C::OFF_C);
   float* splane = reinterpret_cast<float*>(smem + C::OFF_S);
-  int* cbase = reinterpret_cast<int*>(smem + C::OFF_BASE);                      // [kind][col][NT]
-  unsigned short* ccnt = reinterpret_cast<unsigned short*>(smem + C::OFF_CNT);  // [kind][col][NT]
-  unsigned short* ccur = reinterpret_cast<unsigned short*>(smem + C::OFF_CUR);  // [kind][T][col][NT]
   uint64_t* bar_u = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
   uint64_t* bar_p = bar_u + C::NU;
   uint64_t* bar_c = bar_p + C::NP;
+  uint64_t* bar_h = bar_c + C::NC;     // [2] halos of stream step j in buffer j & 1
+  uint64_t* bar_ctr = bar_h + 2;       // [2] centres of stream step j in buffer j & 1
+  uint64_t* bar_done = bar_ctr + 2;    // [NDONE] compute warps finished a stream step
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -219,28 +213,186 @@ __global__ void __launch_bounds__(32 * TY, T == 1 ? 2 : 1)
   for (int i = 1; i < P.npass; ++i)
     if (P.pass[i].cta0 <= b) pi = i;
   const PassDesc pd = P.pass[pi];
-
   const int tl = b - pd.cta0, ty = tl / pd.ntz, tz = tl - ty * pd.ntz;
   const int y0 = pd.yb0 + ty * TY, z0 = tz * TZ;
+  const int jstart = pd.xc0;
+  const int jend = pd.xo1 - 1 + (T - 1) * R;  // inclusive
+  const int pu0 = jstart - R;                 // first u^n plane in the ring
+  const long long tmo = P.timeout_ns;
+
+  if (tid == 0) {
+    s_abort = 0;
+    for (int i = 0; i < C::NU + C::NP + C::NC + 2; ++i) mbar_init(bar_u + i, 1);
+    mbar_init(bar_ctr + 0, TY);
+    mbar_init(bar_ctr + 1, TY);
+    for (int i = 0; i < C::NDONE; ++i) mbar_init(bar_done + i, TY);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // Missing neighbours leave zero halos in the fused-step planes for good.
+  if constexpr (T > 1) {
+    for (int e = tid; e < C::NSP * C::PSLOT; e += C::NTHREADS) splane[e] = 0.f;
+  }
+  __syncthreads();  // the only CTA-wide barrier: set-up done
+
+  if (w == TY) {
+    // =========================== producer warp ===========================
+    const int nb_up = ty > 0 ? b - pd.ntz : -1;
+    const int nb_dn = ty + 1 < pd.nty ? b + pd.ntz : -1;
+    const int nb_lf = tz > 0 ? b - 1 : -1;
+    const int nb_rt = tz + 1 < pd.ntz ? b + 1 : -1;
+    auto ring_strip = [&](int tile, int ridx, int q) -> const float* {
+      return P.ring + (((size_t)tile * (T - 1) + ridx) * C::D + (q % C::D)) * C::STRIP;
+    };
+    // neighbours hold the strips of stream step jn (produced at step jn - r)
+    auto halo_ready = [&](int jn) -> bool {
+      if (jn - R < jstart) return true;
+      const unsigned long long target = P.prog_base + (unsigned long long)(jn - R - jstart + 1);
+      bool ok = true;
+      if (nb_up >= 0) ok &= ld_acquire_u64(&P.progress[nb_up]) >= target;
+      if (nb_dn >= 0) ok &= ld_acquire_u64(&P.progress[nb_dn]) >= target;
+      if (nb_lf >= 0) ok &= ld_acquire_u64(&P.progress[nb_lf]) >= target;
+      if (nb_rt >= 0) ok &= ld_acquire_u64(&P.progress[nb_rt]) >= target;
+      return ok;
+    };
+    // bulk copies of stream step jn's halo strips into buffer jn & 1
+    auto issue_halos = [&](int jn) {
+      uint64_t* bar = bar_h + (jn & 1);
+      float* buf = splane + (size_t)(jn & 1) * (T - 1) * C::PSLOT;
+      unsigned bytes = 0;
+      for (int k = 1; k < T; ++k) {
+        const int q = jn - k * R;
+        if (q < pd.xc0 || q >= pd.xc1) continue;
+        bytes += (nb_up >= 0 ? R * TZ * 4 : 0) + (nb_dn >= 0 ? R * TZ * 4 : 0) +
+                 (nb_lf >= 0 ? TY * RP * 4 : 0) + (nb_rt >= 0 ? TY * RP * 4 : 0);
+      }
+      // the strips were written through the generic proxy: order them before
+      // the async-proxy bulk reads
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      if (lane == 0) mbar_expect_tx(bar, bytes);  // bytes may be 0: a plain arrival
+      __syncwarp();
+      for (int k = 1; k < T; ++k) {
+        const int q = jn - k * R;
+        if (q < pd.xc0 || q >= pd.xc1) continue;
+        float* pl = buf + (k - 1) * C::PSLOT;
+        // rows: R top + R bottom strip rows, then TY rows of left + right strips
+        for (int e = lane; e < 2 * R + 2 * TY; e += 32) {
+          if (e < R) {
+            if (nb_up >= 0) bulk_load(pl + e * SW + RP, ring_strip(nb_up, k - 1, q) + (R + e) * TZ, TZ * 4, bar);
+          } else if (e < 2 * R) {
+            if (nb_dn >= 0)
+              bulk_load(pl + (TY + e) * SW + RP, ring_strip(nb_dn, k - 1, q) + (e - R) * TZ, TZ * 4, bar);
+          } else if (e < 2 * R + TY) {
+            const int row = e - 2 * R;
+            if (nb_lf >= 0)
+              bulk_load(pl + (R + row) * SW, ring_strip(nb_lf, k - 1, q) + 2 * R * TZ + TY * RP + row * RP,
+                        RP * 4, bar);
+          } else {
+            const int row = e - 2 * R - TY;
+            if (nb_rt >= 0)
+              bulk_load(pl + (R + row) * SW + RP + TZ, ring_strip(nb_rt, k - 1, q) + 2 * R * TZ + row * RP,
+                        RP * 4, bar);
+          }
+        }
+      }
+    };
+    auto issue_u = [&](int p) {
+      const int s = (p - pu0) % C::NU;
+      mbar_expect_tx(bar_u + s, C::PLANE * 4);
+      tma_load_3d(uring + s * C::PSLOT, &P.tm_u, bar_u + s, z0 - RP, y0 - R, p);
+    };
+    auto issue_p = [&](int p) {
+      const int s = (p - jstart) % C::NP;
+      mbar_expect_tx(bar_p + s, C::TILE * 4);
+      tma_load_3d(pring + s * C::TILE, &P.tm_p, bar_p + s, z0, y0, p);
+    };
+    auto issue_c = [&](int p) {
+      const int s = (p - jstart) % C::NC;
+      mbar_expect_tx(bar_c + s, C::TILE * 4);
+      tma_load_3d(cring + s * C::TILE, &P.tm_c, bar_c + s, z0, y0, p);
+    };
+    int nu = pu0, np = jstart, nc = jstart, nh = jstart, ret = jstart - 1;
+    bool ok = true;
+    while (ret < jend && ok) {
+      if (lane == 0) {
+        while (nu <= jend + R && (nu - C::NU < pu0 || nu - C::NU + R <= ret)) issue_u(nu++);
+        while (np <= jend && (np - C::NP < jstart || np - C::NP <= ret)) issue_p(np++);
+        while (nc <= jend && (nc - C::NC < jstart || nc - C::NC + (T - 1) * R <= ret)) issue_c(nc++);
+      }
+      if constexpr (T > 1) {
+        while (nh <= jend && nh - 2 <= ret) {
+          bool ready = lane == 0 ? halo_ready(nh) : false;
+          ready = __shfl_sync(0xffffffffu, ready, 0);
+          if (!ready) {
+            if (nh != ret + 1) break;  // not needed yet: retire a step first
+            bool okw = true;
+            if (lane == 0) {
+              const unsigned long long t0 = global_ns();
+              while (!halo_ready(nh))
+                if ((long long)(global_ns() - t0) > tmo) { okw = false; break; }
+            }
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw) {
+              if (lane == 0) atomicExch(P.err, 1);
+              ok = false;
+              break;
+            }
+          }
+          issue_halos(nh++);
+        }
+        if (!ok) break;
+      }
+      // retire the next stream step
+      const int s = ret + 1;
+      bool okd = true;
+      if (lane == 0)
+        okd = mbar_wait(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo);
+      okd = __shfl_sync(0xffffffffu, okd, 0);
+      if (!okd) {
+        if (lane == 0) atomicExch(P.err, 2);
+        ok = false;
+        break;
+      }
+      ret = s;
+      if constexpr (T > 1) {
+        if (lane == 0) {
+          __threadfence();
+          st_release_u64(&P.progress[b], P.prog_base + (unsigned long long)(ret - jstart + 1));
+        }
+      }
+    }
+    if (!ok) s_abort = 1;
+    // drain: wait (bounded) for every load this warp issued
+    if (lane == 0) {
+      for (int p = max(pu0, nu - C::NU); p < nu; ++p)
+        mbar_wait(bar_u + (p - pu0) % C::NU, ((p - pu0) / C::NU) & 1, tmo);
+      for (int p = max(jstart, np - C::NP); p < np; ++p)
+        mbar_wait(bar_p + (p - jstart) % C::NP, ((p - jstart) / C::NP) & 1, tmo);
+      for (int p = max(jstart, nc - C::NC); p < nc; ++p)
+        mbar_wait(bar_c + (p - jstart) % C::NC, ((p - jstart) / C::NC) & 1, tmo);
+      if constexpr (T > 1) {
+        for (int jn = max(jstart, nh - 2); jn < nh; ++jn)
+          mbar_wait(bar_h + (jn & 1), ((jn - jstart) >> 1) & 1, tmo);
+      }
+    }
+    return;
+  }
+
+  // ============================== compute warps ==============================
   const int y = y0 + w, z = z0 + 2 * lane;
   const bool vrow = y < P.n1;
   const bool v0 = vrow && z < P.n2, v1 = vrow && z + 1 < P.n2;
-  const int nb_up = ty > 0 ? b - pd.ntz : -1;
-  const int nb_dn = ty + 1 < pd.nty ? b + pd.ntz : -1;
-  const int nb_lf = tz > 0 ? b - 1 : -1;
-  const int nb_rt = tz + 1 < pd.ntz ? b + 1 : -1;
   const bool own_row = y >= pd.yo0 && y < pd.yo1;
   const size_t ps = (size_t)P.n1 * P.n2p;        // plane stride
   const size_t coff = (size_t)y * P.n2p + z;     // column offset (valid if v0)
   const int own = (R + w) * SW + RP + 2 * lane;  // own pair in a plane slot
   const int own_t = w * TZ + 2 * lane;           // own pair in a tile slot
-  const int jstart = pd.xc0;
-  const int jend = pd.xo1 - 1 + (T - 1) * R;  // inclusive
-  const long long tmo = P.timeout_ns;
+  int* cbase = reinterpret_cast<int*>(smem + C::OFF_BASE);                      // [kind][col][NT]
+  unsigned short* ccnt = reinterpret_cast<unsigned short*>(smem + C::OFF_CNT);  // [kind][col][NT]
+  unsigned short* ccur = reinterpret_cast<unsigned short*>(smem + C::OFF_CUR);  // [kind][T][col][NT]
 
-  float byz0 = 0.f, byz1 = 0.f;
-  if (v0) byz0 = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z]));
-  if (v1) byz1 = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z + 1]));
+  float2 byz = make_float2(0.f, 0.f);
+  if (v0) byz.x = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z]));
+  if (v1) byz.y = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z + 1]));
 
   // Per-column cursors into the grid-aligned source / receiver entries.
   int flags = 0;
@@ -262,285 +414,229 @@ __global__ void __launch_bounds__(32 * TY, T == 1 ? 2 : 1)
     }
   }
 
-  // Missing neighbours leave zero halos in the fused-step planes for good.
-  if constexpr (T > 1) {
-    for (int e = tid; e < 2 * (T - 1) * C::PSLOT; e += NT) splane[e] = 0.f;
-  }
-  if (tid == 0) {
-    s_abort = 0;
-    for (int i = 0; i < C::NU + C::NP + C::NC; ++i) mbar_init(bar_u + i, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-
-  auto issue_u = [&](int p) {
-    const int s = (p - jstart) % C::NU;
-    mbar_expect_tx(bar_u + s, C::PLANE * 4);
-    tma_load_3d(uring + s * C::PSLOT, &P.tm_u, bar_u + s, z0 - RP, y0 - R, p);
-  };
-  auto issue_p = [&](int p) {
-    const int s = (p - jstart) % C::NP;
-    mbar_expect_tx(bar_p + s, C::TILE * 4);
-    tma_load_3d(pring + s * C::TILE, &P.tm_p, bar_p + s, z0, y0, p);
-  };
-  auto issue_c = [&](int p) {
-    const int s = (p - jstart) % C::NC;
-    mbar_expect_tx(bar_c + s, C::TILE * 4);
-    tma_load_3d(cring + s * C::TILE, &P.tm_c, bar_c + s, z0, y0, p);
-  };
-  // Wait (bounded) for every prefetch issued for stream steps >= jn.
-  auto drain = [&](int jn) {
-    for (int p = jn; p < jn + C::NU; ++p)
-      mbar_wait(bar_u + (p - jstart) % C::NU, ((p - jstart) / C::NU) & 1, tmo);
-    for (int p = jn; p <= jn + C::PF; ++p) {
-      mbar_wait(bar_p + (p - jstart) % C::NP, ((p - jstart) / C::NP) & 1, tmo);
-      mbar_wait(bar_c + (p - jstart) % C::NC, ((p - jstart) / C::NC) & 1, tmo);
-    }
-  };
-  if (tid == 0) {
-    for (int p = jstart; p < jstart + C::NU; ++p) issue_u(p);
-    for (int p = jstart; p <= jstart + C::PF; ++p) {
-      issue_p(p);
-      issue_c(p);
-    }
-  }
-
-  auto ring_strip = [&](int tile, int ridx, int q) -> float* {
-    return P.ring + (((size_t)tile * (T - 1) + ridx) * C::D + (q % C::D)) * C::STRIP;
-  };
-  // Prefetch of the fused steps' halo strips for stream step jn.
-  auto prefetch_halos = [&](int jn) {
-    constexpr int CH_ROW = TZ / 4;           // 16-byte chunks per strip row
-    constexpr int CH_Y = 2 * R * CH_ROW;     // top + bottom strips
-    constexpr int CH_Z = 2 * TY * (RP / 4);  // left + right strips
-    constexpr int CH = CH_Y + CH_Z;
-    float* buf = splane + (size_t)(jn & 1) * (T - 1) * C::PSLOT;
-    for (int e = tid; e < (T - 1) * CH; e += NT) {
-      const int k = 1 + e / CH, r = e - (k - 1) * CH;
-      const int q = jn - k * R;
-      if (q < pd.xc0 || q >= pd.xc1) continue;
-      float* pl = buf + (k - 1) * C::PSLOT;
-      if (r < CH_Y) {
-        const int hr = r / CH_ROW, c4 = 4 * (r - hr * CH_ROW);
-        if (hr < R) {
-          if (nb_up >= 0)
-            cp_async16(pl + hr * SW + RP + c4, ring_strip(nb_up, k - 1, q) + (R + hr) * TZ + c4);
-        } else if (nb_dn >= 0) {
-          cp_async16(pl + (TY + hr) * SW + RP + c4, ring_strip(nb_dn, k - 1, q) + (hr - R) * TZ + c4);
-        }
-      } else {
-        const int r2 = r - CH_Y, row = r2 / (RP / 2), cc = r2 - row * (RP / 2);
-        const bool left = cc < RP / 4;
-        const int c4 = 4 * (left ? cc : cc - RP / 4);
-        if (left) {
-          if (nb_lf >= 0)
-            cp_async16(pl + (R + row) * SW + c4,
-                       ring_strip(nb_lf, k - 1, q) + 2 * R * TZ + TY * RP + row * RP + c4);
-        } else if (nb_rt >= 0) {
-          cp_async16(pl + (R + row) * SW + RP + TZ + c4,
-                     ring_strip(nb_rt, k - 1, q) + 2 * R * TZ + row * RP + c4);
-        }
-      }
-    }
-  };
-
-  // Stage-0 queue before the first shift: planes [jstart-1-R, jstart-1+R] of u^n.
-  float2 Qs[T][C::Q];
+  // Register queues of fused steps k >= 1 (step k uses Qs[k-1]): level n+k.
+  constexpr int TQ = T > 1 ? T - 1 : 1;
+  float2 Qs[TQ][C::Q];
 #pragma unroll
-  for (int k = 0; k < T; ++k)
+  for (int k = 0; k < TQ; ++k)
 #pragma unroll
     for (int s = 0; s < C::Q; ++s) Qs[k][s] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int s = 0; s < C::Q; ++s) {
-    const int plane = jstart - 1 - R + s;
-    if (v0 && plane >= 0 && plane < P.n0) {
-      Qs[0][s] = __ldg(reinterpret_cast<const float2*>(P.u_cur + (size_t)plane * ps + coff));
-      if (!v1) Qs[0][s].y = 0.f;
-    }
-  }
-  // (fused steps k >= 1 are idle at the first stream step: their planes
-  //  precede the chunk, so nothing is staged for them yet)
 
+  bool ok = true;
+  // u^n planes pu0 .. jstart+R-1 must be in place before the first step
+  for (int p = pu0; p < jstart + R && ok; ++p)
+    ok = mbar_wait(bar_u + (p - pu0) % C::NU, ((p - pu0) / C::NU) & 1, tmo);
+
+  // ring slot of u^n plane j, its phase bookkeeping, and of the tile rings
+  int su = (jstart - pu0) % C::NU;  // = R
+  int sp = 0, sc = 0;
 #pragma unroll 1
-  for (int j = jstart; j <= jend; ++j) {
+  for (int j = jstart; j <= jend && ok; ++j) {
     const bool act0 = j >= pd.xc0 && j < pd.xc1;
-    bool next_need = false;  // a fused step k >= 1 works at stream step j + 1
-#pragma unroll
-    for (int k = 1; k < T; ++k) {
-      const int q = j + 1 - k * R;
-      next_need |= (q >= pd.xc0 && q < pd.xc1);
-    }
-    if constexpr (T > 1) {
-      if (tid == 0 && next_need && j + 1 - R >= jstart) {
-        // the strips used at stream step j+1 were produced at step j+1-R
-        const unsigned long long target = P.prog_base + (unsigned long long)(j + 1 - R - jstart + 1);
-        const int nbs[4] = {nb_up, nb_dn, nb_lf, nb_rt};
-        const unsigned long long t0 = global_ns();
-        bool okn = true;
-        for (int i = 0; i < 4 && okn; ++i)
-          if (nbs[i] >= 0) okn = bounded_wait_ge(&P.progress[nbs[i]], target, t0, tmo);
-        if (!okn) {
-          atomicExch(P.err, 1);
-          s_abort = 1;
-        }
-        __threadfence();
-      }
-    }
-    // this step's TMA data, and the halos prefetched during the previous step
-    const int su0 = (j - jstart) % C::NU, suR = (j + R - jstart) % C::NU;
-    bool ok = mbar_wait(bar_u + su0, ((j - jstart) / C::NU) & 1, tmo);
-    ok = ok && mbar_wait(bar_u + suR, ((j + R - jstart) / C::NU) & 1, tmo);
-    if (act0) {
-      ok = ok && mbar_wait(bar_p + (j - jstart) % C::NP, ((j - jstart) / C::NP) & 1, tmo);
-      ok = ok && mbar_wait(bar_c + (j - jstart) % C::NC, ((j - jstart) / C::NC) & 1, tmo);
-    }
-    if (!ok) {
-      atomicExch(P.err, 2);
-      s_abort = 1;
-    }
-    if constexpr (T > 1) cp_async_wait_all();
-    __syncthreads();
-    if (s_abort) {
-      if (tid == 0) drain(j);
-      return;
-    }
-    if constexpr (T > 1) {
-      if (next_need) prefetch_halos(j + 1);
-    }
-
-    // ---- fused steps
-    const float* ub = uring + su0 * C::PSLOT;  // u^n plane j with its halo
     {
-      const float2 nq = *reinterpret_cast<const float2*>(uring + suR * C::PSLOT + own);
-#pragma unroll
-      for (int s = 0; s < C::Q - 1; ++s) Qs[0][s] = Qs[0][s + 1];
-      Qs[0][C::Q - 1] = nq;
+      const int p = j + R, s = (p - pu0) % C::NU;
+      ok = mbar_wait(bar_u + s, ((p - pu0) / C::NU) & 1, tmo);
     }
-#pragma unroll
-    for (int k = 0; k < T; ++k) {
-      const int q = j - k * R;
-      const bool act = q >= pd.xc0 && q < pd.xc1;
-      float2 un = make_float2(0.f, 0.f);
-      if (act) {
-        const float* pl =
-            (k == 0) ? ub : splane + ((size_t)(j & 1) * (T - 1) + (k > 0 ? k - 1 : 0)) * C::PSLOT;
-        const float2 upv =
-            (k == 0) ? *reinterpret_cast<const float2*>(pring + ((j - jstart) % C::NP) * C::TILE + own_t)
-                     : Qs[k > 0 ? k - 1 : 0][0];
-        const float2 c2v = *reinterpret_cast<const float2*>(cring + ((q - jstart) % C::NC) * C::TILE + own_t);
-        const float bx = __ldg(&P.damp_b[q]);
-        const float2 uc = Qs[k][R];
-        // axis-2 window as column pairs: zp[m] = columns (2 lane - R + 2m, +1)
-        float2 zp[R + 1];
-#pragma unroll
-        for (int m = 0; m <= R; ++m)
-          zp[m] = (m == R / 2) ? uc : *reinterpret_cast<const float2*>(&pl[own - R + 2 * m]);
-        float2 lap = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int d = 1; d <= R; ++d) {
-          const float2 yp = *reinterpret_cast<const float2*>(&pl[own + d * SW]);
-          const float2 ym = *reinterpret_cast<const float2*>(&pl[own - d * SW]);
-          float2 zpl, zmi;
-          if (d % 2 == 0) {
-            zpl = zp[R / 2 + d / 2];
-            zmi = zp[R / 2 - d / 2];
-          } else {
-            zpl = make_float2(zp[R / 2 + (d - 1) / 2].y, zp[R / 2 + (d + 1) / 2].x);
-            zmi = make_float2(zp[R / 2 - (d + 1) / 2].y, zp[R / 2 - (d - 1) / 2].x);
-          }
-          lap = pair_term2(lap, P.w2[0][d - 1], Qs[k][R + d], Qs[k][R - d], uc);
-          lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, uc);
-          lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, uc);
-        }
-        if (v0) un.x = point_update(uc.x, upv.x, lap.x, c2v.x, __fadd_rn(bx, byz0));
-        if (v1) un.y = point_update(uc.y, upv.y, lap.y, c2v.y, __fadd_rn(bx, byz1));
+    if (act0 && ok) {
+      ok = mbar_wait(bar_p + sp, ((j - jstart) / C::NP) & 1, tmo);
+      ok = ok && mbar_wait(bar_c + sc, ((j - jstart) / C::NC) & 1, tmo);
+    }
+    if constexpr (T > 1) {
+      ok = ok && mbar_wait(bar_h + (j & 1), ((j - jstart) >> 1) & 1, tmo);
+      if (j > jstart) ok = ok && mbar_wait(bar_ctr + (j & 1), ((j - jstart - 1) >> 1) & 1, tmo);
+    }
+    if (!ok) break;
 
-        const int step = P.step0 + k;
-        if (flags & 3) {  // fused grid-aligned injection (Listing 5)
+    // ---- fused step 0: every neighbour from the u^n ring
+    float2 un0 = make_float2(0.f, 0.f);
+    const float* ub = uring + su * C::PSLOT;
+    const float2 uc0 = *reinterpret_cast<const float2*>(ub + own);
+    if (act0) {
+      const float2 up = *reinterpret_cast<const float2*>(pring + sp * C::TILE + own_t);
+      const float2 c2v = *reinterpret_cast<const float2*>(cring + sc * C::TILE + own_t);
+      const float bx = __ldg(&P.damp_b[j]);
+      const float2 nu = make_float2(-uc0.x, -uc0.y);
+      float2 zp[R + 1];
 #pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            if (!((flags >> i) & 1)) continue;
-            unsigned short* cp = &ccur[((0 * T + k) * 2 + i) * NT + tid];
-            int cc = *cp;
-            const int cn = ccnt[(0 * 2 + i) * NT + tid], cb = cbase[(0 * 2 + i) * NT + tid];
-            while (cc < cn) {
-              const int2 e = __ldg(&P.s_ent[cb + cc]);
-              if (e.x < q) {
-                ++cc;
-                continue;
-              }
-              if (e.x == q) {
-                const float add = __ldg(&P.src_dcmp[(size_t)step * P.npts + e.y]);
-                if (i == 0) un.x = __fadd_rn(un.x, add);
-                else un.y = __fadd_rn(un.y, add);
-                ++cc;
-              }
-              break;
+      for (int m = 0; m <= R; ++m)
+        zp[m] = (m == R / 2) ? uc0 : *reinterpret_cast<const float2*>(&ub[own - R + 2 * m]);
+      float2 lap = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int d = 1; d <= R; ++d) {
+        int sf = su + d, sb = su - d;
+        sf -= sf >= C::NU ? C::NU : 0;
+        sb += sb < 0 ? C::NU : 0;
+        const float2 xp = *reinterpret_cast<const float2*>(uring + sf * C::PSLOT + own);
+        const float2 xm = *reinterpret_cast<const float2*>(uring + sb * C::PSLOT + own);
+        const float2 yp = *reinterpret_cast<const float2*>(&ub[own + d * SW]);
+        const float2 ym = *reinterpret_cast<const float2*>(&ub[own - d * SW]);
+        float2 zpl, zmi;
+        if (d % 2 == 0) {
+          zpl = zp[R / 2 + d / 2];
+          zmi = zp[R / 2 - d / 2];
+        } else {
+          zpl = make_float2(zp[R / 2 + (d - 1) / 2].y, zp[R / 2 + (d + 1) / 2].x);
+          zmi = make_float2(zp[R / 2 - (d + 1) / 2].y, zp[R / 2 - (d - 1) / 2].x);
+        }
+        lap = pair_term2(lap, P.w2[0][d - 1], xp, xm, nu);
+        lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, nu);
+        lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, nu);
+      }
+      un0.x = point_update(uc0.x, up.x, lap.x, c2v.x, __fadd_rn(bx, byz.x));
+      un0.y = point_update(uc0.y, up.y, lap.y, c2v.y, __fadd_rn(bx, byz.y));
+    }
+
+    // ---- sparse operators and hand-over of one fused step's result
+    auto sparse = [&](int k, int q, float2& un) {
+      const int step = P.step0 + k;
+      if (flags & 3) {  // fused grid-aligned injection (Listing 5)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          if (!((flags >> i) & 1)) continue;
+          unsigned short* cp = &ccur[((0 * T + k) * 2 + i) * NT + tid];
+          int cc = *cp;
+          const int cn = ccnt[(0 * 2 + i) * NT + tid], cb = cbase[(0 * 2 + i) * NT + tid];
+          while (cc < cn) {
+            const int2 e = __ldg(&P.s_ent[cb + cc]);
+            if (e.x < q) {
+              ++cc;
+              continue;
             }
-            *cp = (unsigned short)cc;
+            if (e.x == q) {
+              const float add = __ldg(&P.src_dcmp[(size_t)step * P.npts + e.y]);
+              if (i == 0) un.x = __fadd_rn(un.x, add);
+              else un.y = __fadd_rn(un.y, add);
+              ++cc;
+            }
+            break;
+          }
+          *cp = (unsigned short)cc;
+        }
+      }
+      if ((flags & 12) && own_row && q >= pd.xo0 && q < pd.xo1) {  // receiver points
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          if (!((flags >> (2 + i)) & 1)) continue;
+          unsigned short* cp = &ccur[((1 * T + k) * 2 + i) * NT + tid];
+          int cc = *cp;
+          const int cn = ccnt[(1 * 2 + i) * NT + tid], cb = cbase[(1 * 2 + i) * NT + tid];
+          while (cc < cn) {
+            const int2 e = __ldg(&P.r_ent[cb + cc]);
+            if (e.x < q) {
+              ++cc;
+              continue;
+            }
+            if (e.x == q) {
+              P.rec_dcmp[(size_t)(step - P.rec_base) * P.nrpts + e.y] = (i == 0 ? un.x : un.y);
+              ++cc;
+            }
+            break;
+          }
+          *cp = (unsigned short)cc;
+        }
+      }
+    };
+    if (act0) sparse(0, j, un0);
+
+    if constexpr (T == 1) {
+      if (act0 && own_row && j >= pd.xo0 && j < pd.xo1 && v0)
+        __stcs(reinterpret_cast<float2*>(P.out0 + (size_t)j * ps + coff), un0);
+    } else {
+      // fused steps k >= 1 write next step's centres into buffer (j+1) & 1,
+      // which the whole CTA read during step j-1: wait until it is retired
+      if (j > jstart) {
+        const int s = j - 1;
+        ok = mbar_wait(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo);
+        if (!ok) break;
+      }
+      float* rs_base = P.ring + (size_t)b * (T - 1) * C::D * C::STRIP;
+      float2 un = un0;
+      bool act = act0;
+#pragma unroll
+      for (int k = 0; k < T; ++k) {
+        const int q = j - k * R;
+        if (k > 0) {
+          act = q >= pd.xc0 && q < pd.xc1;
+          un = make_float2(0.f, 0.f);
+          if (act) {
+            const float* pl = splane + ((size_t)(j & 1) * (T - 1) + (k - 1)) * C::PSLOT;
+            // u_prev of step k: level n+k-1 at plane q, the oldest entry of step k-1's queue
+            const float2 upv =
+                (k == 1) ? *reinterpret_cast<const float2*>(
+                               uring + ((su - R + C::NU) % C::NU) * C::PSLOT + own)
+                         : Qs[k >= 2 ? k - 2 : 0][0];
+            int scq = sc - k * R;
+            scq += scq < 0 ? C::NC : 0;
+            const float2 c2v = *reinterpret_cast<const float2*>(cring + scq * C::TILE + own_t);
+            const float bx = __ldg(&P.damp_b[q]);
+            const float2 uc = Qs[k - 1][R];
+            const float2 nu = make_float2(-uc.x, -uc.y);
+            float2 zp[R + 1];
+#pragma unroll
+            for (int m = 0; m <= R; ++m)
+              zp[m] = (m == R / 2) ? uc : *reinterpret_cast<const float2*>(&pl[own - R + 2 * m]);
+            float2 lap = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+              const float2 yp = *reinterpret_cast<const float2*>(&pl[own + d * SW]);
+              const float2 ym = *reinterpret_cast<const float2*>(&pl[own - d * SW]);
+              float2 zpl, zmi;
+              if (d % 2 == 0) {
+                zpl = zp[R / 2 + d / 2];
+                zmi = zp[R / 2 - d / 2];
+              } else {
+                zpl = make_float2(zp[R / 2 + (d - 1) / 2].y, zp[R / 2 + (d + 1) / 2].x);
+                zmi = make_float2(zp[R / 2 - (d + 1) / 2].y, zp[R / 2 - (d - 1) / 2].x);
+              }
+              lap = pair_term2(lap, P.w2[0][d - 1], Qs[k - 1][R + d], Qs[k - 1][R - d], nu);
+              lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, nu);
+              lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, nu);
+            }
+            un.x = point_update(uc.x, upv.x, lap.x, c2v.x, __fadd_rn(bx, byz.x));
+            un.y = point_update(uc.y, upv.y, lap.y, c2v.y, __fadd_rn(bx, byz.y));
+            sparse(k, q, un);
           }
         }
-        if ((flags & 12) && own_row && q >= pd.xo0 && q < pd.xo1) {  // receiver points
+        if (k + 1 < T) {
+          const int kq = k < T - 1 ? k : 0;  // queue of fused step k+1
+          // hand the new level to fused step k+1 ...
 #pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            if (!((flags >> (2 + i)) & 1)) continue;
-            unsigned short* cp = &ccur[((1 * T + k) * 2 + i) * NT + tid];
-            int cc = *cp;
-            const int cn = ccnt[(1 * 2 + i) * NT + tid], cb = cbase[(1 * 2 + i) * NT + tid];
-            while (cc < cn) {
-              const int2 e = __ldg(&P.r_ent[cb + cc]);
-              if (e.x < q) {
-                ++cc;
-                continue;
-              }
-              if (e.x == q) {
-                P.rec_dcmp[(size_t)(step - P.rec_base) * P.nrpts + e.y] = (i == 0 ? un.x : un.y);
-                ++cc;
-              }
-              break;
-            }
-            *cp = (unsigned short)cc;
+          for (int s = 0; s < C::Q - 1; ++s) Qs[kq][s] = Qs[kq][s + 1];
+          Qs[kq][C::Q - 1] = un;
+          // ... stage its centre for the next stream step ...
+          const int qn = j + 1 - (k + 1) * R;
+          if (qn >= pd.xc0 && qn < pd.xc1)
+            *reinterpret_cast<float2*>(splane + ((size_t)((j + 1) & 1) * (T - 1) + k) * C::PSLOT + own) =
+                Qs[kq][R + 1];
+          // ... and publish its halo strips for the neighbours
+          if (act) {
+            float* rs = rs_base + ((size_t)k * C::D + (q % C::D)) * C::STRIP;
+            if (w < R) __stcg(reinterpret_cast<float2*>(rs + w * TZ + 2 * lane), un);
+            if (w >= TY - R) __stcg(reinterpret_cast<float2*>(rs + (R + w - (TY - R)) * TZ + 2 * lane), un);
+            if (2 * lane < RP) __stcg(reinterpret_cast<float2*>(rs + 2 * R * TZ + w * RP + 2 * lane), un);
+            if (2 * lane >= TZ - RP)
+              __stcg(reinterpret_cast<float2*>(rs + 2 * R * TZ + TY * RP + w * RP + 2 * lane - (TZ - RP)), un);
           }
+        } else if (act && own_row && q >= pd.xo0 && q < pd.xo1 && v0) {
+          __stcs(reinterpret_cast<float2*>(P.out0 + (size_t)q * ps + coff), un);
+          __stcs(reinterpret_cast<float2*>(P.out1 + (size_t)q * ps + coff), Qs[T - 2][R]);
         }
       }
-      if (k + 1 < T) {
-        const int kn = (k + 1 < T) ? k + 1 : 0;
-        // hand the new level to the next fused step ...
-#pragma unroll
-        for (int s = 0; s < C::Q - 1; ++s) Qs[kn][s] = Qs[kn][s + 1];
-        Qs[kn][C::Q - 1] = un;
-        // ... stage its centre for the next stream step ...
-        const int qn = j + 1 - (k + 1) * R;
-        if (qn >= pd.xc0 && qn < pd.xc1)
-          *reinterpret_cast<float2*>(splane + ((size_t)((j + 1) & 1) * (T - 1) + k) * C::PSLOT + own) =
-              Qs[kn][R + 1];
-        // ... and publish its halo strips
-        if (act) {
-          float* rs = ring_strip(b, k, q);
-          if (w < R) __stcg(reinterpret_cast<float2*>(rs + w * TZ + 2 * lane), un);
-          if (w >= TY - R) __stcg(reinterpret_cast<float2*>(rs + (R + w - (TY - R)) * TZ + 2 * lane), un);
-          if (2 * lane < RP) __stcg(reinterpret_cast<float2*>(rs + 2 * R * TZ + w * RP + 2 * lane), un);
-          if (2 * lane >= TZ - RP)
-            __stcg(reinterpret_cast<float2*>(rs + 2 * R * TZ + TY * RP + w * RP + 2 * lane - (TZ - RP)), un);
-        }
-      } else if (act && own_row && q >= pd.xo0 && q < pd.xo1 && v0) {
-        __stcs(reinterpret_cast<float2*>(P.out0 + (size_t)q * ps + coff), un);
-        if constexpr (T > 1) __stcs(reinterpret_cast<float2*>(P.out1 + (size_t)q * ps + coff), Qs[k][R]);
-      }
+      asm volatile("fence.proxy.async.global;" ::: "memory");  // ring strips -> bulk readers
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_ctr + ((j + 1) & 1));
     }
-    __syncthreads();  // every read of this step's slots is done
-    if (tid == 0) {
-      if constexpr (T > 1) {
-        __threadfence();
-        st_release_u64(&P.progress[b], P.prog_base + (unsigned long long)(j - jstart + 1));
-      }
-      // refill u^n plane j's slot, u^{n-1} plane j's slot, c2 plane j-(T-1)r's slot
-      issue_u(j + C::NU);
-      issue_p(j + C::PF + 1);
-      issue_c(j + C::PF + 1);
-    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar_done + (j - jstart) % C::NDONE);
+    // advance the ring slots
+    su = su + 1 == C::NU ? 0 : su + 1;
+    sp = sp + 1 == C::NP ? 0 : sp + 1;
+    sc = sc + 1 == C::NC ? 0 : sc + 1;
   }
-  if (tid == 0) drain(jend + 1);  // the prefetches still in flight
+  if (!ok) {
+    atomicExch(P.err, 2);
+    s_abort = 1;
+  }
 }
 
 template <int R, int T>
@@ -563,9 +659,9 @@ cudaError_t sweep_launch_t(const SweepParams& p, int nctas, bool cooperative, cu
   count_launch();
   if (cooperative) {
     void* args[] = {const_cast<SweepParams*>(&p)};
-    return cudaLaunchCooperativeKernel((const void*)fn, dim3(nctas), dim3(Cf::NT), args, Cf::SMEM, st);
+    return cudaLaunchCooperativeKernel((const void*)fn, dim3(nctas), dim3(Cf::NTHREADS), args, Cf::SMEM, st);
   }
-  fn<<<nctas, Cf::NT, Cf::SMEM, st>>>(p);
+  fn<<<nctas, Cf::NTHREADS, Cf::SMEM, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -576,7 +672,7 @@ cudaError_t sweep_occupancy_t(int* per_sm) {
   auto fn = sweep_kernel<R, T, Tr::TY>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, Cf::NT, Cf::SMEM);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, Cf::NTHREADS, Cf::SMEM);
 }
 
 template <int R, int T>
@@ -586,7 +682,7 @@ void sweep_shape_t(SweepShape* s) {
   s->R = R;
   s->T = T;
   s->TY = Tr::TY;
-  s->threads = Cf::NT;
+  s->threads = Cf::NTHREADS;
   s->smem = Cf::SMEM;
   s->ring_floats_per_cta = Cf::RING_PER_CTA;
   s->box_w = Cf::SW;

@@ -1,4 +1,4 @@
-// Sweep kernels of radius 6 (space order 12), T = 1..3 fused steps.
+// Sweep kernels of radius 6 (space order 12), T = 1..2 fused steps.
 #include "tb_sweep.cuh"
 
 namespace tbi {
@@ -8,7 +8,6 @@ cudaError_t sweep_dispatch_r6(int what, int T, const SweepParams* p, int nctas, 
   switch (T) {
     TBI_DEFINE_RADIUS_T(6, 1)
     TBI_DEFINE_RADIUS_T(6, 2)
-    TBI_DEFINE_RADIUS_T(6, 3)
   }
   return cudaErrorInvalidValue;
 }

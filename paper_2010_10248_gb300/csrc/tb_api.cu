@@ -698,7 +698,7 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
         h->ev_kind.push_back(1);
         if (a) cudaEventRecord(a, st);
       }
-      cudaError_t e = finalize_traces(rec_fill, nrec, h->rec.corner_id, h->rec.corner_w, h->rec_dcmp,
+      cudaError_t e = finalize_traces(rec_fill, nrec, h->rec.corner_eid, h->rec.corner_w, h->rec_dcmp,
                                       h->rec.npts, dtr + (size_t)rec_base * nrec, st);
       if (h->opt.profile && b) cudaEventRecord(b, st);
       if (e != cudaSuccess) return cuda_fail(h, e, "receiver finalize");

@@ -203,21 +203,25 @@ __global__ void k_colptr(int64_t ncol, const unsigned long long* __restrict__ ke
 }
 
 __global__ void k_entries(int64_t npts, const unsigned long long* __restrict__ keys2, int64_t n0,
-                          int2* ent) {
+                          int2* ent, int* eid_of_id) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npts) return;
   const unsigned long long k = keys2[i];
   const int64_t cx = (int64_t)(k >> kLowBits);
-  ent[i] = make_int2((int)(cx % n0), (int)(k & ((1ull << kLowBits) - 1)));
+  const int id = (int)(k & ((1ull << kLowBits) - 1));
+  ent[i] = make_int2((int)(cx % n0), id);
+  eid_of_id[id] = (int)i;  // position of point id in the column-ordered entries
 }
 
 __global__ void k_corner_tables(int64_t nvalid, const unsigned long long* __restrict__ keys,
-                                const int* __restrict__ ent_id, const double* __restrict__ w8,
-                                int* corner_id, float* corner_w) {
+                                const int* __restrict__ ent_id, const int* __restrict__ eid_of_id,
+                                const double* __restrict__ w8, int* corner_id, int* corner_eid,
+                                float* corner_w) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nvalid) return;
   const unsigned long long pc = keys[i] & ((1ull << kLowBits) - 1);
   corner_id[pc] = ent_id[i];
+  corner_eid[pc] = eid_of_id[ent_id[i]];
   corner_w[pc] = (float)w8[pc];
 }
 
@@ -231,7 +235,9 @@ void free_tables(PointTables* t) {
   cudaFree(t->colptr);
   cudaFree(t->ent);
   cudaFree(t->corner_id);
+  cudaFree(t->corner_eid);
   cudaFree(t->corner_w);
+  cudaFree(t->eid_of_id);
   cudaFree(t->keys);
   cudaFree(t->w8);
   cudaFree(t->gstart);
@@ -313,6 +319,7 @@ int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coor
     ok(cudaMalloc(&keys2, sizeof(unsigned long long) * P2));
     ok(cudaMalloc(&t->colptr, sizeof(int) * (ncol + 1)));
     ok(cudaMalloc(&t->ent, sizeof(int2) * (t->npts > 0 ? t->npts : 1)));
+    ok(cudaMalloc(&t->eid_of_id, sizeof(int) * (t->npts > 0 ? t->npts : 1)));
     if (status != TB_OK) goto fail;
     count_launch();
     k_fill_u64<<<grid_for(P2, 256), 256, 0, st>>>(keys2, 0, P2, kSentinel);
@@ -322,19 +329,22 @@ int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coor
     count_launch();
     k_colptr<<<grid_for(ncol + 1, 256), 256, 0, st>>>(ncol, keys2, t->npts, n[0], t->colptr);
     count_launch();
-    k_entries<<<grid_for(t->npts, 256), 256, 0, st>>>(t->npts, keys2, n[0], t->ent);
+    k_entries<<<grid_for(t->npts, 256), 256, 0, st>>>(t->npts, keys2, n[0], t->ent, t->eid_of_id);
     ok(cudaGetLastError());
   }
   if (want_corners) {
     ok(cudaMalloc(&t->corner_id, sizeof(int) * npt * 8));
+    ok(cudaMalloc(&t->corner_eid, sizeof(int) * npt * 8));
     ok(cudaMalloc(&t->corner_w, sizeof(float) * npt * 8));
     if (status != TB_OK) goto fail;
     count_launch();
     k_fill_i32<<<grid_for((int64_t)npt * 8, 256), 256, 0, st>>>(t->corner_id, (int64_t)npt * 8, -1);
+    count_launch();
+    k_fill_i32<<<grid_for((int64_t)npt * 8, 256), 256, 0, st>>>(t->corner_eid, (int64_t)npt * 8, -1);
     ok(cudaMemsetAsync(t->corner_w, 0, sizeof(float) * npt * 8, st));
     count_launch();
-    k_corner_tables<<<grid_for(t->nvalid, 256), 256, 0, st>>>(t->nvalid, t->keys, t->ent_id, t->w8,
-                                                              t->corner_id, t->corner_w);
+    k_corner_tables<<<grid_for(t->nvalid, 256), 256, 0, st>>>(
+        t->nvalid, t->keys, t->ent_id, t->eid_of_id, t->w8, t->corner_id, t->corner_eid, t->corner_w);
     ok(cudaGetLastError());
   }
   ok(cudaStreamSynchronize(st));
@@ -343,8 +353,8 @@ int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coor
   cudaFree(d_bad);
   cudaFree(d_counts);
   t->bytes = sizeof(unsigned long long) * P + sizeof(double) * npt * 8 + sizeof(int) * P +
-             sizeof(int64_t) * (2 * maxpts + 1) + sizeof(int) * (ncol + 1) + sizeof(int2) * t->npts +
-             (want_corners ? (sizeof(int) + sizeof(float)) * npt * 8 : 0);
+             sizeof(int64_t) * (2 * maxpts + 1) + sizeof(int) * (ncol + 1) + (sizeof(int2) + sizeof(int)) * t->npts +
+             (want_corners ? (2 * sizeof(int) + sizeof(float)) * npt * 8 : 0);
   return TB_OK;
 fail:
   cudaFree(keys2);
@@ -386,7 +396,9 @@ cudaError_t decompose(const PointTables* t, int nt, const float* d_wav, const fl
   return cudaGetLastError();
 }
 
-// trace[s][r] = sum_c w_rc * rec_dcmp[s][id_rc], corners in fixed order
+// trace[s][r] = sum_c w_rc * rec_dcmp[s][e_rc], corners in fixed order; the
+// recorded receiver points are indexed by their position e in the
+// column-ordered entry list
 __global__ void k_finalize(int nsteps, int nrec, const int* __restrict__ cid,
                            const float* __restrict__ cw, const float* __restrict__ rec_dcmp,
                            int64_t nrpts, float* traces) {

@@ -45,7 +45,7 @@ struct SweepParams {
   // grid-aligned receivers
   const int* r_colptr;
   const int2* r_ent;
-  float* rec_dcmp;              // [cap][nrpts]
+  float* rec_dcmp;              // [cap][nrpts], indexed by position in r_ent
   int64_t nrpts;
   int rec_base;                 // step index stored in row 0 of rec_dcmp
   int step0;                    // step index of the first fused step
@@ -82,7 +82,9 @@ struct PointTables {
   int64_t* lin = nullptr;       // [npts] ascending unpadded linear index
   int* colptr = nullptr;        // [n1*n2 + 1]
   int2* ent = nullptr;          // [npts] (x, id) by column then x
-  int* corner_id = nullptr;     // [npt*8] (receivers)
+  int* eid_of_id = nullptr;     // [npts] position of each point in ent
+  int* corner_id = nullptr;     // [npt*8] point id of each corner, -1 if weight 0 (receivers)
+  int* corner_eid = nullptr;    // [npt*8] position in ent of each corner (receivers)
   float* corner_w = nullptr;    // [npt*8] (receivers)
   // inspector scratch kept for the decomposition
   unsigned long long* keys = nullptr;  // sorted corner keys [P]

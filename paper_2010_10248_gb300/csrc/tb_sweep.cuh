@@ -66,8 +66,13 @@ struct SweepCfg {
   static constexpr int PSLOT = (int)(align128(PLANE * 4) / 4);
   static constexpr int TILE = TY * TZ;
   static constexpr int Q = 2 * R + 1;                // queue length
-  static constexpr int PF = T == 1 ? 1 : 2;          // planes of prefetch beyond need
-  static constexpr int NU = 2 * R + 1 + PF;          // u^n box ring
+  static constexpr int PF = 2;                       // planes of prefetch beyond need
+  // fused step 0 takes its axis-0 neighbours from a register queue when it
+  // is the only step (keeps the ring short: two CTAs per SM), else from the
+  // u^n ring (frees registers for the queues of the other fused steps)
+  static constexpr bool X0Q = T == 1;
+  static constexpr int NU = (X0Q ? R + 1 : 2 * R + 1) + PF;  // u^n box ring
+  static constexpr int ULAG = X0Q ? 0 : R;           // plane p is last read at step p + ULAG
   static constexpr int NP = PF + 1;                  // u^{n-1} tile ring
   static constexpr int NC = (T - 1) * R + 1 + PF;    // c2 tile ring
   static constexpr int NDONE = 8;                    // step-retirement barriers
@@ -82,7 +87,8 @@ struct SweepCfg {
   static constexpr size_t OFF_BASE = OFF_S + align128((size_t)NSP * PSLOT * 4);
   static constexpr size_t OFF_CNT = OFF_BASE + 4 * 2 * 2 * NT;
   static constexpr size_t OFF_CUR = OFF_CNT + 2 * 2 * 2 * NT;
-  static constexpr size_t OFF_BAR = align128(OFF_CUR + 2 * 2 * T * 2 * NT);
+  static constexpr size_t OFF_XF = OFF_CUR + 2 * 2 * T * 2 * NT;  // receiver columns' first x
+  static constexpr size_t OFF_BAR = align128(OFF_XF + 2 * 2 * NT);
   static constexpr int NBAR = NU + NP + NC + 2 + 2 + NDONE;  // u, p, c, halo[2], centre[2], done
   static constexpr size_t SMEM = OFF_BAR + 8 * NBAR + 128;    // + base alignment
   static_assert(R % 2 == 0, "radius must be even for aligned float2 access");
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
   const int y0 = pd.yb0 + ty * TY, z0 = tz * TZ;
   const int jstart = pd.xc0;
   const int jend = pd.xo1 - 1 + (T - 1) * R;  // inclusive
-  const int pu0 = jstart - R;                 // first u^n plane in the ring
+  const int pu0 = jstart - C::ULAG;           // first u^n plane in the ring
   const long long tmo = P.timeout_ns;
 
   if (tid == 0) {
@@ -314,7 +320,7 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
     bool ok = true;
     while (ret < jend && ok) {
       if (lane == 0) {
-        while (nu <= jend + R && (nu - C::NU < pu0 || nu - C::NU + R <= ret)) issue_u(nu++);
+        while (nu <= jend + R && (nu - C::NU < pu0 || nu - C::NU + C::ULAG <= ret)) issue_u(nu++);
         while (np <= jend && (np - C::NP < jstart || np - C::NP <= ret)) issue_p(np++);
         while (nc <= jend && (nc - C::NC < jstart || nc - C::NC + (T - 1) * R <= ret)) issue_c(nc++);
       }
@@ -389,12 +395,16 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
   int* cbase = reinterpret_cast<int*>(smem + C::OFF_BASE);                      // [kind][col][NT]
   unsigned short* ccnt = reinterpret_cast<unsigned short*>(smem + C::OFF_CNT);  // [kind][col][NT]
   unsigned short* ccur = reinterpret_cast<unsigned short*>(smem + C::OFF_CUR);  // [kind][T][col][NT]
+  unsigned short* cxf = reinterpret_cast<unsigned short*>(smem + C::OFF_XF);    // [col][NT]
 
   float2 byz = make_float2(0.f, 0.f);
   if (v0) byz.x = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z]));
   if (v1) byz.y = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z + 1]));
 
-  // Per-column cursors into the grid-aligned source / receiver entries.
+  // Per-column state of the grid-aligned source / receiver entries.  flags:
+  // bit i: column i has source points; bit 2+i: receiver points; bit 4+i:
+  // its receiver points are contiguous in x (lines, planes), so the entry
+  // of plane q is base + q - x_first, with no cursor and no load.
   int flags = 0;
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
@@ -410,33 +420,122 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
         cbase[(kind * 2 + i) * NT + tid] = cb;
         ccnt[(kind * 2 + i) * NT + tid] = (unsigned short)(ce - cb);
         for (int k = 0; k < T; ++k) ccur[((kind * T + k) * 2 + i) * NT + tid] = 0;
+        if (kind == 1) {
+          const int xf = __ldg(&P.r_ent[cb].x), xl = __ldg(&P.r_ent[ce - 1].x);
+          cxf[i * NT + tid] = (unsigned short)xf;
+          if (xl - xf + 1 == ce - cb) flags |= 16 << i;
+        }
       }
     }
   }
 
-  // Register queues of fused steps k >= 1 (step k uses Qs[k-1]): level n+k.
+  // Register queues: Q0 holds u^n around plane j (one-step kernel only);
+  // fused step k >= 1 uses Qs[k-1], level n+k around plane q_k.
   constexpr int TQ = T > 1 ? T - 1 : 1;
   float2 Qs[TQ][C::Q];
+  float2 Q0[C::X0Q ? C::Q : 1];
 #pragma unroll
   for (int k = 0; k < TQ; ++k)
 #pragma unroll
     for (int s = 0; s < C::Q; ++s) Qs[k][s] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int s = 0; s < (C::X0Q ? C::Q : 1); ++s) Q0[s] = make_float2(0.f, 0.f);
+  if constexpr (C::X0Q) {
+    // planes [jstart-1-R, jstart-1+R] of u^n before the first shift
+#pragma unroll
+    for (int s = 0; s < C::Q; ++s) {
+      const int plane = jstart - 1 - R + s;
+      if (v0 && plane >= 0 && plane < P.n0) {
+        Q0[s] = __ldg(reinterpret_cast<const float2*>(P.u_cur + (size_t)plane * ps + coff));
+        if (!v1) Q0[s].y = 0.f;
+      }
+    }
+  }
+  // damping along axis 0 of every fused step's plane, one step ahead
+  float bxn[T];
+#pragma unroll
+  for (int k = 0; k < T; ++k) {
+    const int q = jstart - k * R;
+    bxn[k] = (q >= 0 && q < P.n0) ? __ldg(&P.damp_b[q]) : 0.f;
+  }
 
   bool ok = true;
   // u^n planes pu0 .. jstart+R-1 must be in place before the first step
   for (int p = pu0; p < jstart + R && ok; ++p)
     ok = mbar_wait(bar_u + (p - pu0) % C::NU, ((p - pu0) / C::NU) & 1, tmo);
 
-  // ring slot of u^n plane j, its phase bookkeeping, and of the tile rings
-  int su = (jstart - pu0) % C::NU;  // = R
-  int sp = 0, sc = 0;
+  // sparse operators of fused step k at plane q on this thread's column pair
+  auto sparse = [&](int k, int q, float2& un) {
+    const int step = P.step0 + k;
+    if (flags & 3) {  // fused grid-aligned injection (Listing 5)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        if (!((flags >> i) & 1)) continue;
+        unsigned short* cp = &ccur[((0 * T + k) * 2 + i) * NT + tid];
+        int cc = *cp;
+        const int cn = ccnt[(0 * 2 + i) * NT + tid], cb = cbase[(0 * 2 + i) * NT + tid];
+        while (cc < cn) {
+          const int2 e = __ldg(&P.s_ent[cb + cc]);
+          if (e.x < q) {
+            ++cc;
+            continue;
+          }
+          if (e.x == q) {
+            const float add = __ldg(&P.src_dcmp[(size_t)step * P.npts + e.y]);
+            if (i == 0) un.x = __fadd_rn(un.x, add);
+            else un.y = __fadd_rn(un.y, add);
+            ++cc;
+          }
+          break;
+        }
+        *cp = (unsigned short)cc;
+      }
+    }
+    if ((flags & 12) && own_row && q >= pd.xo0 && q < pd.xo1) {  // receiver points
+      float* rrow = P.rec_dcmp + (size_t)(step - P.rec_base) * P.nrpts;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        if (!((flags >> (2 + i)) & 1)) continue;
+        const int cn = ccnt[(1 * 2 + i) * NT + tid], cb = cbase[(1 * 2 + i) * NT + tid];
+        if ((flags >> (4 + i)) & 1) {
+          const unsigned off = (unsigned)(q - (int)cxf[i * NT + tid]);
+          if (off < (unsigned)cn) rrow[cb + off] = (i == 0 ? un.x : un.y);
+          continue;
+        }
+        unsigned short* cp = &ccur[((1 * T + k) * 2 + i) * NT + tid];
+        int cc = *cp;
+        while (cc < cn) {
+          const int2 e = __ldg(&P.r_ent[cb + cc]);
+          if (e.x < q) {
+            ++cc;
+            continue;
+          }
+          if (e.x == q) {
+            rrow[cb + cc] = (i == 0 ? un.x : un.y);
+            ++cc;
+          }
+          break;
+        }
+        *cp = (unsigned short)cc;
+      }
+    }
+  };
+
+  int su = (jstart - pu0) % C::NU;  // ring slot of u^n plane j
+  int sp = 0, sc = 0;               // ring slots of u^{n-1}, c2 plane j
 #pragma unroll 1
   for (int j = jstart; j <= jend && ok; ++j) {
     const bool act0 = j >= pd.xc0 && j < pd.xc1;
-    {
-      const int p = j + R, s = (p - pu0) % C::NU;
-      ok = mbar_wait(bar_u + s, ((p - pu0) / C::NU) & 1, tmo);
+    float bx[T];
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+      bx[k] = bxn[k];
+      const int q = j + 1 - k * R;
+      bxn[k] = (q >= 0 && q < P.n0) ? __ldg(&P.damp_b[q]) : 0.f;
     }
+    int suR = su + R;
+    suR -= suR >= C::NU ? C::NU : 0;
+    ok = mbar_wait(bar_u + suR, ((j + R - pu0) / C::NU) & 1, tmo);
     if (act0 && ok) {
       ok = mbar_wait(bar_p + sp, ((j - jstart) / C::NP) & 1, tmo);
       ok = ok && mbar_wait(bar_c + sc, ((j - jstart) / C::NC) & 1, tmo);
@@ -447,14 +546,19 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
     }
     if (!ok) break;
 
-    // ---- fused step 0: every neighbour from the u^n ring
-    float2 un0 = make_float2(0.f, 0.f);
+    // ---- fused step 0
     const float* ub = uring + su * C::PSLOT;
-    const float2 uc0 = *reinterpret_cast<const float2*>(ub + own);
+    if constexpr (C::X0Q) {
+      const float2 nq = *reinterpret_cast<const float2*>(uring + suR * C::PSLOT + own);
+#pragma unroll
+      for (int s = 0; s < C::Q - 1; ++s) Q0[s] = Q0[s + 1];
+      Q0[C::Q - 1] = nq;
+    }
+    float2 un0 = make_float2(0.f, 0.f);
     if (act0) {
+      const float2 uc0 = C::X0Q ? Q0[R] : *reinterpret_cast<const float2*>(ub + own);
       const float2 up = *reinterpret_cast<const float2*>(pring + sp * C::TILE + own_t);
       const float2 c2v = *reinterpret_cast<const float2*>(cring + sc * C::TILE + own_t);
-      const float bx = __ldg(&P.damp_b[j]);
       const float2 nu = make_float2(-uc0.x, -uc0.y);
       float2 zp[R + 1];
 #pragma unroll
@@ -463,11 +567,17 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
       float2 lap = make_float2(0.f, 0.f);
 #pragma unroll
       for (int d = 1; d <= R; ++d) {
-        int sf = su + d, sb = su - d;
-        sf -= sf >= C::NU ? C::NU : 0;
-        sb += sb < 0 ? C::NU : 0;
-        const float2 xp = *reinterpret_cast<const float2*>(uring + sf * C::PSLOT + own);
-        const float2 xm = *reinterpret_cast<const float2*>(uring + sb * C::PSLOT + own);
+        float2 xp, xm;
+        if constexpr (C::X0Q) {
+          xp = Q0[R + d];
+          xm = Q0[R - d];
+        } else {
+          int sf = su + d, sb = su - d;
+          sf -= sf >= C::NU ? C::NU : 0;
+          sb += sb < 0 ? C::NU : 0;
+          xp = *reinterpret_cast<const float2*>(uring + sf * C::PSLOT + own);
+          xm = *reinterpret_cast<const float2*>(uring + sb * C::PSLOT + own);
+        }
         const float2 yp = *reinterpret_cast<const float2*>(&ub[own + d * SW]);
         const float2 ym = *reinterpret_cast<const float2*>(&ub[own - d * SW]);
         float2 zpl, zmi;
@@ -482,61 +592,10 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
         lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, nu);
         lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, nu);
       }
-      un0.x = point_update(uc0.x, up.x, lap.x, c2v.x, __fadd_rn(bx, byz.x));
-      un0.y = point_update(uc0.y, up.y, lap.y, c2v.y, __fadd_rn(bx, byz.y));
+      un0.x = point_update(uc0.x, up.x, lap.x, c2v.x, __fadd_rn(bx[0], byz.x));
+      un0.y = point_update(uc0.y, up.y, lap.y, c2v.y, __fadd_rn(bx[0], byz.y));
+      sparse(0, j, un0);
     }
-
-    // ---- sparse operators and hand-over of one fused step's result
-    auto sparse = [&](int k, int q, float2& un) {
-      const int step = P.step0 + k;
-      if (flags & 3) {  // fused grid-aligned injection (Listing 5)
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          if (!((flags >> i) & 1)) continue;
-          unsigned short* cp = &ccur[((0 * T + k) * 2 + i) * NT + tid];
-          int cc = *cp;
-          const int cn = ccnt[(0 * 2 + i) * NT + tid], cb = cbase[(0 * 2 + i) * NT + tid];
-          while (cc < cn) {
-            const int2 e = __ldg(&P.s_ent[cb + cc]);
-            if (e.x < q) {
-              ++cc;
-              continue;
-            }
-            if (e.x == q) {
-              const float add = __ldg(&P.src_dcmp[(size_t)step * P.npts + e.y]);
-              if (i == 0) un.x = __fadd_rn(un.x, add);
-              else un.y = __fadd_rn(un.y, add);
-              ++cc;
-            }
-            break;
-          }
-          *cp = (unsigned short)cc;
-        }
-      }
-      if ((flags & 12) && own_row && q >= pd.xo0 && q < pd.xo1) {  // receiver points
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          if (!((flags >> (2 + i)) & 1)) continue;
-          unsigned short* cp = &ccur[((1 * T + k) * 2 + i) * NT + tid];
-          int cc = *cp;
-          const int cn = ccnt[(1 * 2 + i) * NT + tid], cb = cbase[(1 * 2 + i) * NT + tid];
-          while (cc < cn) {
-            const int2 e = __ldg(&P.r_ent[cb + cc]);
-            if (e.x < q) {
-              ++cc;
-              continue;
-            }
-            if (e.x == q) {
-              P.rec_dcmp[(size_t)(step - P.rec_base) * P.nrpts + e.y] = (i == 0 ? un.x : un.y);
-              ++cc;
-            }
-            break;
-          }
-          *cp = (unsigned short)cc;
-        }
-      }
-    };
-    if (act0) sparse(0, j, un0);
 
     if constexpr (T == 1) {
       if (act0 && own_row && j >= pd.xo0 && j < pd.xo1 && v0)
@@ -560,15 +619,18 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
           un = make_float2(0.f, 0.f);
           if (act) {
             const float* pl = splane + ((size_t)(j & 1) * (T - 1) + (k - 1)) * C::PSLOT;
-            // u_prev of step k: level n+k-1 at plane q, the oldest entry of step k-1's queue
-            const float2 upv =
-                (k == 1) ? *reinterpret_cast<const float2*>(
-                               uring + ((su - R + C::NU) % C::NU) * C::PSLOT + own)
-                         : Qs[k >= 2 ? k - 2 : 0][0];
+            // u_prev of step k: level n+k-1 at plane q
+            float2 upv;
+            if (k == 1) {
+              int sq = su - R;
+              sq += sq < 0 ? C::NU : 0;
+              upv = *reinterpret_cast<const float2*>(uring + sq * C::PSLOT + own);
+            } else {
+              upv = Qs[k >= 2 ? k - 2 : 0][0];
+            }
             int scq = sc - k * R;
             scq += scq < 0 ? C::NC : 0;
             const float2 c2v = *reinterpret_cast<const float2*>(cring + scq * C::TILE + own_t);
-            const float bx = __ldg(&P.damp_b[q]);
             const float2 uc = Qs[k - 1][R];
             const float2 nu = make_float2(-uc.x, -uc.y);
             float2 zp[R + 1];
@@ -592,8 +654,8 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
               lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, nu);
               lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, nu);
             }
-            un.x = point_update(uc.x, upv.x, lap.x, c2v.x, __fadd_rn(bx, byz.x));
-            un.y = point_update(uc.y, upv.y, lap.y, c2v.y, __fadd_rn(bx, byz.y));
+            un.x = point_update(uc.x, upv.x, lap.x, c2v.x, __fadd_rn(bx[k], byz.x));
+            un.y = point_update(uc.y, upv.y, lap.y, c2v.y, __fadd_rn(bx[k], byz.y));
             sparse(k, q, un);
           }
         }

@@ -123,12 +123,14 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// try_wait suspends the warp until the phase completes or ~20 us pass, so a
+// waiting warp sleeps instead of spending issue slots on polling.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
       : "memory");
   return ok != 0;
 }
@@ -451,12 +453,12 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
       }
     }
   }
-  // damping along axis 0 of every fused step's plane, one step ahead
-  float bxn[T];
-#pragma unroll
-  for (int k = 0; k < T; ++k) {
-    const int q = jstart - k * R;
-    bxn[k] = (q >= 0 && q < P.n0) ? __ldg(&P.damp_b[q]) : 0.f;
+  // damping along axis 0 at fused step k's plane: held by lane k, loaded one
+  // stream step ahead, broadcast by shuffle when used
+  float bxn = 0.f;
+  if (lane < T) {
+    const int q = jstart - lane * R;
+    bxn = (q >= 0 && q < P.n0) ? __ldg(&P.damp_b[q]) : 0.f;
   }
 
   bool ok = true;
@@ -526,12 +528,10 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
 #pragma unroll 1
   for (int j = jstart; j <= jend && ok; ++j) {
     const bool act0 = j >= pd.xc0 && j < pd.xc1;
-    float bx[T];
-#pragma unroll
-    for (int k = 0; k < T; ++k) {
-      bx[k] = bxn[k];
-      const int q = j + 1 - k * R;
-      bxn[k] = (q >= 0 && q < P.n0) ? __ldg(&P.damp_b[q]) : 0.f;
+    const float bxc = bxn;
+    if (lane < T) {
+      const int q = j + 1 - lane * R;
+      bxn = (q >= 0 && q < P.n0) ? __ldg(&P.damp_b[q]) : 0.f;
     }
     int suR = su + R;
     suR -= suR >= C::NU ? C::NU : 0;
@@ -592,8 +592,9 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
         lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, nu);
         lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, nu);
       }
-      un0.x = point_update(uc0.x, up.x, lap.x, c2v.x, __fadd_rn(bx[0], byz.x));
-      un0.y = point_update(uc0.y, up.y, lap.y, c2v.y, __fadd_rn(bx[0], byz.y));
+      const float bx = __shfl_sync(0xffffffffu, bxc, 0);
+      un0.x = point_update(uc0.x, up.x, lap.x, c2v.x, __fadd_rn(bx, byz.x));
+      un0.y = point_update(uc0.y, up.y, lap.y, c2v.y, __fadd_rn(bx, byz.y));
       sparse(0, j, un0);
     }
 
@@ -654,8 +655,9 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
               lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, nu);
               lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, nu);
             }
-            un.x = point_update(uc.x, upv.x, lap.x, c2v.x, __fadd_rn(bx[k], byz.x));
-            un.y = point_update(uc.y, upv.y, lap.y, c2v.y, __fadd_rn(bx[k], byz.y));
+            const float bx = __shfl_sync(0xffffffffu, bxc, k);
+            un.x = point_update(uc.x, upv.x, lap.x, c2v.x, __fadd_rn(bx, byz.x));
+            un.y = point_update(uc.y, upv.y, lap.y, c2v.y, __fadd_rn(bx, byz.y));
             sparse(k, q, un);
           }
         }

@@ -135,12 +135,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 // Bounded wait on an mbarrier phase; false when the time limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long timeout_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
+// The first try is inline; the polling loop is kept out of the hot path.
+static __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, unsigned parity, long long timeout_ns) {
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
     if ((long long)(global_ns() - t0) > timeout_ns) return false;
   return true;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long timeout_ns) {
+  return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, timeout_ns);
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
                                             int c1, int c2) {
@@ -175,23 +178,32 @@ __device__ __forceinline__ bool bounded_wait_ge(const unsigned long long* flag,
 // ------------------------------------------------------------ arithmetic --
 // Eq. 1 at one point: u^{n+1} = [dt^2 L u + m(2u - u_prev) + a u_prev]/(m + a)
 // rewritten with c2 = dt^2/m and g = a/m = (eta/(2 dt)) c2 as an increment:
-//   u^{n+1} = u + (c2 L u + (1 - g)(u - u_prev)) / (1 + g).
-__device__ __forceinline__ float point_update(float uc, float up, float lap, float c2,
-                                              float bsum) {
-  const float d = __fsub_rn(uc, up);
-  if (bsum == 0.f) return __fadd_rn(uc, __fmaf_rn(c2, lap, d));
-  const float g = __fmul_rn(bsum, c2);
-  const float inc = __fmaf_rn(c2, lap, __fmul_rn(__fsub_rn(1.f, g), d));
-  return __fadd_rn(uc, __fdiv_rn(inc, __fadd_rn(1.f, g)));
+//   u^{n+1} = u + (c2 L u + (1 - g)(u - u_prev)) / (1 + g),
+// on a column pair with packed f32x2 round-to-nearest operations.  x - y is
+// formed as fma(y, -1, x) (the product is exact, so one rounding, as a
+// subtraction).  Branch-free: outside the sponge g = 0, 1 - g and 1 + g are
+// exactly 1, the reciprocal of 1 is exactly 1, and the result is
+// u + (c2 L u + (u - u_prev)) with the same roundings; inside, the quotient
+// is the reciprocal times the numerator (within 2 ulp of the correctly
+// rounded division).
+__device__ __forceinline__ float2 point_update2(float2 uc, float2 up, float2 lap, float2 c2,
+                                               float2 bsum) {
+  const float2 m1 = make_float2(-1.f, -1.f), one = make_float2(1.f, 1.f);
+  const float2 d = __ffma2_rn(up, m1, uc);
+  const float2 g = __fmul2_rn(bsum, c2);
+  const float2 inc = __ffma2_rn(c2, lap, __fmul2_rn(__ffma2_rn(g, m1, one), d));
+  const float2 opg = __fadd2_rn(one, g);
+  return __fadd2_rn(uc, make_float2(__fdividef(inc.x, opg.x), __fdividef(inc.y, opg.y)));
 }
 
 // One neighbour pair of the Laplacian in differences form on a column pair,
-// acc + w ((a - u) + (b - u)), as packed f32x2 round-to-nearest operations
-// (nu = -u).  The differences of close values are exact, so the large centre
-// term never cancels against the neighbour sum (in FP32 this keeps 1000-step
-// runs ~40x closer to the FP64 result than c0 u + sum c_i (u_+i + u_-i)).
-__device__ __forceinline__ float2 pair_term2(float2 acc, float2 w2, float2 a, float2 b, float2 nu) {
-  return __ffma2_rn(w2, __fadd2_rn(__fadd2_rn(a, nu), __fadd2_rn(b, nu)), acc);
+// acc + w ((a - u) + (b - u)).  The differences of close values are exact, so
+// the large centre term never cancels against the neighbour sum (in FP32
+// this keeps 1000-step runs ~40x closer to the FP64 result than the
+// c0 u + sum c_i (u_+i + u_-i) form).
+__device__ __forceinline__ float2 pair_term2(float2 acc, float2 w2, float2 a, float2 b, float2 u) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  return __ffma2_rn(w2, __fadd2_rn(__ffma2_rn(u, m1, a), __ffma2_rn(u, m1, b)), acc);
 }
 
 // ----------------------------------------------------------------- kernel --
@@ -231,9 +243,9 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
   if (tid == 0) {
     s_abort = 0;
     for (int i = 0; i < C::NU + C::NP + C::NC + 2; ++i) mbar_init(bar_u + i, 1);
-    mbar_init(bar_ctr + 0, TY);
-    mbar_init(bar_ctr + 1, TY);
-    for (int i = 0; i < C::NDONE; ++i) mbar_init(bar_done + i, TY);
+    mbar_init(bar_ctr + 0, NT);
+    mbar_init(bar_ctr + 1, NT);
+    for (int i = 0; i < C::NDONE; ++i) mbar_init(bar_done + i, NT);  // every compute thread arrives
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // Missing neighbours leave zero halos in the fused-step planes for good.
@@ -455,10 +467,11 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
   }
   // damping along axis 0 at fused step k's plane: held by lane k, loaded one
   // stream step ahead, broadcast by shuffle when used
-  float bxn = 0.f;
-  if (lane < T) {
-    const int q = jstart - lane * R;
-    bxn = (q >= 0 && q < P.n0) ? __ldg(&P.damp_b[q]) : 0.f;
+  const int kl = lane % T;  // lane holds fused step (lane mod T)
+  float bxn;
+  {
+    const int q = jstart - kl * R;
+    bxn = __ldg(&P.damp_b[min(max(q, 0), P.n0 - 1)]);
   }
 
   bool ok = true;
@@ -529,10 +542,7 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
   for (int j = jstart; j <= jend && ok; ++j) {
     const bool act0 = j >= pd.xc0 && j < pd.xc1;
     const float bxc = bxn;
-    if (lane < T) {
-      const int q = j + 1 - lane * R;
-      bxn = (q >= 0 && q < P.n0) ? __ldg(&P.damp_b[q]) : 0.f;
-    }
+    bxn = __ldg(&P.damp_b[min(max(j + 1 - kl * R, 0), P.n0 - 1)]);
     int suR = su + R;
     suR -= suR >= C::NU ? C::NU : 0;
     ok = mbar_wait(bar_u + suR, ((j + R - pu0) / C::NU) & 1, tmo);
@@ -559,7 +569,6 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
       const float2 uc0 = C::X0Q ? Q0[R] : *reinterpret_cast<const float2*>(ub + own);
       const float2 up = *reinterpret_cast<const float2*>(pring + sp * C::TILE + own_t);
       const float2 c2v = *reinterpret_cast<const float2*>(cring + sc * C::TILE + own_t);
-      const float2 nu = make_float2(-uc0.x, -uc0.y);
       float2 zp[R + 1];
 #pragma unroll
       for (int m = 0; m <= R; ++m)
@@ -588,13 +597,12 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
           zpl = make_float2(zp[R / 2 + (d - 1) / 2].y, zp[R / 2 + (d + 1) / 2].x);
           zmi = make_float2(zp[R / 2 - (d + 1) / 2].y, zp[R / 2 - (d - 1) / 2].x);
         }
-        lap = pair_term2(lap, P.w2[0][d - 1], xp, xm, nu);
-        lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, nu);
-        lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, nu);
+        lap = pair_term2(lap, P.w2[0][d - 1], xp, xm, uc0);
+        lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, uc0);
+        lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, uc0);
       }
       const float bx = __shfl_sync(0xffffffffu, bxc, 0);
-      un0.x = point_update(uc0.x, up.x, lap.x, c2v.x, __fadd_rn(bx, byz.x));
-      un0.y = point_update(uc0.y, up.y, lap.y, c2v.y, __fadd_rn(bx, byz.y));
+      un0 = point_update2(uc0, up, lap, c2v, __fadd2_rn(make_float2(bx, bx), byz));
       sparse(0, j, un0);
     }
 
@@ -633,7 +641,6 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
             scq += scq < 0 ? C::NC : 0;
             const float2 c2v = *reinterpret_cast<const float2*>(cring + scq * C::TILE + own_t);
             const float2 uc = Qs[k - 1][R];
-            const float2 nu = make_float2(-uc.x, -uc.y);
             float2 zp[R + 1];
 #pragma unroll
             for (int m = 0; m <= R; ++m)
@@ -651,13 +658,12 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
                 zpl = make_float2(zp[R / 2 + (d - 1) / 2].y, zp[R / 2 + (d + 1) / 2].x);
                 zmi = make_float2(zp[R / 2 - (d + 1) / 2].y, zp[R / 2 - (d - 1) / 2].x);
               }
-              lap = pair_term2(lap, P.w2[0][d - 1], Qs[k - 1][R + d], Qs[k - 1][R - d], nu);
-              lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, nu);
-              lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, nu);
+              lap = pair_term2(lap, P.w2[0][d - 1], Qs[k - 1][R + d], Qs[k - 1][R - d], uc);
+              lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, uc);
+              lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, uc);
             }
             const float bx = __shfl_sync(0xffffffffu, bxc, k);
-            un.x = point_update(uc.x, upv.x, lap.x, c2v.x, __fadd_rn(bx, byz.x));
-            un.y = point_update(uc.y, upv.y, lap.y, c2v.y, __fadd_rn(bx, byz.y));
+            un = point_update2(uc, upv, lap, c2v, __fadd2_rn(make_float2(bx, bx), byz));
             sparse(k, q, un);
           }
         }
@@ -687,11 +693,9 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
         }
       }
       asm volatile("fence.proxy.async.global;" ::: "memory");  // ring strips -> bulk readers
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar_ctr + ((j + 1) & 1));
+      mbar_arrive(bar_ctr + ((j + 1) & 1));
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(bar_done + (j - jstart) % C::NDONE);
+    mbar_arrive(bar_done + (j - jstart) % C::NDONE);
     // advance the ring slots
     su = su + 1 == C::NU ? 0 : su + 1;
     sp = sp + 1 == C::NP ? 0 : sp + 1;

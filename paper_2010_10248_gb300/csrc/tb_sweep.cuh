@@ -12,11 +12,14 @@
 //     ring holding planes j-r .. j+r+PF (out-of-grid cells arrive as zeros:
 //     the zero boundary of Eq. 1);
 //   * the own tiles of u^{n-1} and c2 = dt^2/m, by TMA, into their rings;
-//   * for fused steps k >= 1, the neighbours' halo strips of level n+k, by
-//     bulk copies from a small L2-resident ring in global memory, after an
-//     acquire on the neighbours' progress counters;
+//   * signals when the neighbours hold the halo strips of a coming stream
+//     step (an acquire on their progress counters);
 //   * retires stream steps (an mbarrier the compute warps arrive on), frees
 //     their ring slots, and publishes the CTA's progress (release).
+// For fused steps k >= 1, the compute warps copy the neighbours' halo strips
+// of level n+k from a small L2-resident ring in global memory with 16-byte
+// cp.async one stream step ahead; the copies complete on the next step's
+// centre barrier, so nothing waits for them in the step that issues them.
 // Compute warps wait on mbarriers only; every wait is bounded by a timeout,
 // after which the CTA records an error and returns (the producer first
 // drains its own copies in flight).
@@ -27,7 +30,7 @@
 // per owned column, a register queue of the 2r+1 planes of their input
 // level around q_k (the axis-0 neighbours) and read axis-1/axis-2
 // neighbours from a double-buffered shared plane (centres written by the
-// compute warps, halos copied by the producer).  A step's output goes
+// compute warps, halos copied from the neighbours' strips).  A step's output goes
 // straight into the next step's queue, so intermediate levels never reach
 // HBM: per T steps a point costs one read of u^n, u^{n-1}, c2 and one write
 // of u^{n+T}, u^{n+T-1}.  All CTAs of a pass stream in lockstep
@@ -153,6 +156,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// The mbarrier phase cannot complete before this thread's earlier cp.async
+// copies have landed (net zero on the arrival count).
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 // Non-tensor bulk copy global -> shared (16-byte aligned, size multiple of 16).
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
   asm volatile(
@@ -222,8 +233,8 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
   uint64_t* bar_u = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
   uint64_t* bar_p = bar_u + C::NU;
   uint64_t* bar_c = bar_p + C::NP;
-  uint64_t* bar_h = bar_c + C::NC;     // [2] halos of stream step j in buffer j & 1
-  uint64_t* bar_ctr = bar_h + 2;       // [2] centres of stream step j in buffer j & 1
+  uint64_t* bar_nbr = bar_c + C::NC;   // [2] neighbours hold the halo strips of stream step j
+  uint64_t* bar_ctr = bar_nbr + 2;     // [2] centres and halos of stream step j in buffer j & 1
   uint64_t* bar_done = bar_ctr + 2;    // [NDONE] compute warps finished a stream step
   __shared__ int s_abort;
 
@@ -254,15 +265,13 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
   }
   __syncthreads();  // the only CTA-wide barrier: set-up done
 
+  const int nb_up = ty > 0 ? b - pd.ntz : -1;
+  const int nb_dn = ty + 1 < pd.nty ? b + pd.ntz : -1;
+  const int nb_lf = tz > 0 ? b - 1 : -1;
+  const int nb_rt = tz + 1 < pd.ntz ? b + 1 : -1;
+
   if (w == TY) {
     // =========================== producer warp ===========================
-    const int nb_up = ty > 0 ? b - pd.ntz : -1;
-    const int nb_dn = ty + 1 < pd.nty ? b + pd.ntz : -1;
-    const int nb_lf = tz > 0 ? b - 1 : -1;
-    const int nb_rt = tz + 1 < pd.ntz ? b + 1 : -1;
-    auto ring_strip = [&](int tile, int ridx, int q) -> const float* {
-      return P.ring + (((size_t)tile * (T - 1) + ridx) * C::D + (q % C::D)) * C::STRIP;
-    };
     // neighbours hold the strips of stream step jn (produced at step jn - r)
     auto halo_ready = [&](int jn) -> bool {
       if (jn - R < jstart) return true;
@@ -273,47 +282,6 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
       if (nb_lf >= 0) ok &= ld_acquire_u64(&P.progress[nb_lf]) >= target;
       if (nb_rt >= 0) ok &= ld_acquire_u64(&P.progress[nb_rt]) >= target;
       return ok;
-    };
-    // bulk copies of stream step jn's halo strips into buffer jn & 1
-    auto issue_halos = [&](int jn) {
-      uint64_t* bar = bar_h + (jn & 1);
-      float* buf = splane + (size_t)(jn & 1) * (T - 1) * C::PSLOT;
-      unsigned bytes = 0;
-      for (int k = 1; k < T; ++k) {
-        const int q = jn - k * R;
-        if (q < pd.xc0 || q >= pd.xc1) continue;
-        bytes += (nb_up >= 0 ? R * TZ * 4 : 0) + (nb_dn >= 0 ? R * TZ * 4 : 0) +
-                 (nb_lf >= 0 ? TY * RP * 4 : 0) + (nb_rt >= 0 ? TY * RP * 4 : 0);
-      }
-      // the strips were written through the generic proxy: order them before
-      // the async-proxy bulk reads
-      asm volatile("fence.proxy.async.global;" ::: "memory");
-      if (lane == 0) mbar_expect_tx(bar, bytes);  // bytes may be 0: a plain arrival
-      __syncwarp();
-      for (int k = 1; k < T; ++k) {
-        const int q = jn - k * R;
-        if (q < pd.xc0 || q >= pd.xc1) continue;
-        float* pl = buf + (k - 1) * C::PSLOT;
-        // rows: R top + R bottom strip rows, then TY rows of left + right strips
-        for (int e = lane; e < 2 * R + 2 * TY; e += 32) {
-          if (e < R) {
-            if (nb_up >= 0) bulk_load(pl + e * SW + RP, ring_strip(nb_up, k - 1, q) + (R + e) * TZ, TZ * 4, bar);
-          } else if (e < 2 * R) {
-            if (nb_dn >= 0)
-              bulk_load(pl + (TY + e) * SW + RP, ring_strip(nb_dn, k - 1, q) + (e - R) * TZ, TZ * 4, bar);
-          } else if (e < 2 * R + TY) {
-            const int row = e - 2 * R;
-            if (nb_lf >= 0)
-              bulk_load(pl + (R + row) * SW, ring_strip(nb_lf, k - 1, q) + 2 * R * TZ + TY * RP + row * RP,
-                        RP * 4, bar);
-          } else {
-            const int row = e - 2 * R - TY;
-            if (nb_rt >= 0)
-              bulk_load(pl + (R + row) * SW + RP + TZ, ring_strip(nb_rt, k - 1, q) + 2 * R * TZ + row * RP,
-                        RP * 4, bar);
-          }
-        }
-      }
     };
     auto issue_u = [&](int p) {
       const int s = (p - pu0) % C::NU;
@@ -330,69 +298,56 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
       mbar_expect_tx(bar_c + s, C::TILE * 4);
       tma_load_3d(cring + s * C::TILE, &P.tm_c, bar_c + s, z0, y0, p);
     };
+    // single-lane producer: TMA issue, neighbour readiness, step retirement
     int nu = pu0, np = jstart, nc = jstart, nh = jstart, ret = jstart - 1;
     bool ok = true;
-    while (ret < jend && ok) {
-      if (lane == 0) {
+    if (lane == 0) {
+      while (ret < jend && ok) {
         while (nu <= jend + R && (nu - C::NU < pu0 || nu - C::NU + C::ULAG <= ret)) issue_u(nu++);
         while (np <= jend && (np - C::NP < jstart || np - C::NP <= ret)) issue_p(np++);
         while (nc <= jend && (nc - C::NC < jstart || nc - C::NC + (T - 1) * R <= ret)) issue_c(nc++);
-      }
-      if constexpr (T > 1) {
-        while (nh <= jend && nh - 2 <= ret) {
-          bool ready = lane == 0 ? halo_ready(nh) : false;
-          ready = __shfl_sync(0xffffffffu, ready, 0);
-          if (!ready) {
-            if (nh != ret + 1) break;  // not needed yet: retire a step first
-            bool okw = true;
-            if (lane == 0) {
+        if constexpr (T > 1) {
+          // tell the compute warps when the neighbours' strips of stream
+          // step nh may be copied (they copy them during step nh - 1)
+          while (nh <= jend && nh - 2 <= ret) {
+            if (!halo_ready(nh)) {
+              if (nh != ret + 2) break;  // not needed yet: retire a step first
               const unsigned long long t0 = global_ns();
               while (!halo_ready(nh))
-                if ((long long)(global_ns() - t0) > tmo) { okw = false; break; }
+                if ((long long)(global_ns() - t0) > tmo) {
+                  atomicExch(P.err, 1);
+                  ok = false;
+                  break;
+                }
+              if (!ok) break;
             }
-            okw = __shfl_sync(0xffffffffu, okw, 0);
-            if (!okw) {
-              if (lane == 0) atomicExch(P.err, 1);
-              ok = false;
-              break;
-            }
+            mbar_arrive(bar_nbr + (nh & 1));
+            ++nh;
           }
-          issue_halos(nh++);
+          if (!ok) break;
         }
-        if (!ok) break;
-      }
-      // retire the next stream step
-      const int s = ret + 1;
-      bool okd = true;
-      if (lane == 0)
-        okd = mbar_wait(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo);
-      okd = __shfl_sync(0xffffffffu, okd, 0);
-      if (!okd) {
-        if (lane == 0) atomicExch(P.err, 2);
-        ok = false;
-        break;
-      }
-      ret = s;
-      if constexpr (T > 1) {
-        if (lane == 0) {
-          __threadfence();
+        // retire the next stream step
+        const int s = ret + 1;
+        if (!mbar_wait(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo)) {
+          atomicExch(P.err, 2);
+          ok = false;
+          break;
+        }
+        ret = s;
+        if constexpr (T > 1) {
+          // release: cumulative over the compute warps' strip stores, which
+          // happen before their arrival on the step's mbarrier
           st_release_u64(&P.progress[b], P.prog_base + (unsigned long long)(ret - jstart + 1));
         }
       }
-    }
-    if (!ok) s_abort = 1;
-    // drain: wait (bounded) for every load this warp issued
-    if (lane == 0) {
+      if (!ok) s_abort = 1;
+      // drain: wait (bounded) for every load this thread issued
       for (int p = max(pu0, nu - C::NU); p < nu; ++p)
         mbar_wait(bar_u + (p - pu0) % C::NU, ((p - pu0) / C::NU) & 1, tmo);
       for (int p = max(jstart, np - C::NP); p < np; ++p)
         mbar_wait(bar_p + (p - jstart) % C::NP, ((p - jstart) / C::NP) & 1, tmo);
       for (int p = max(jstart, nc - C::NC); p < nc; ++p)
         mbar_wait(bar_c + (p - jstart) % C::NC, ((p - jstart) / C::NC) & 1, tmo);
-      if constexpr (T > 1) {
-        for (int jn = max(jstart, nh - 2); jn < nh; ++jn)
-          mbar_wait(bar_h + (jn & 1), ((jn - jstart) >> 1) & 1, tmo);
-      }
     }
     return;
   }
@@ -551,7 +506,7 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
       ok = ok && mbar_wait(bar_c + sc, ((j - jstart) / C::NC) & 1, tmo);
     }
     if constexpr (T > 1) {
-      ok = ok && mbar_wait(bar_h + (j & 1), ((j - jstart) >> 1) & 1, tmo);
+      // centres and halo strips of this step, staged during the previous one
       if (j > jstart) ok = ok && mbar_wait(bar_ctr + (j & 1), ((j - jstart - 1) >> 1) & 1, tmo);
     }
     if (!ok) break;
@@ -573,7 +528,7 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
 #pragma unroll
       for (int m = 0; m <= R; ++m)
         zp[m] = (m == R / 2) ? uc0 : *reinterpret_cast<const float2*>(&ub[own - R + 2 * m]);
-      float2 lap = make_float2(0.f, 0.f);
+      float2 lx = make_float2(0.f, 0.f), ly = lx, lz = lx;
 #pragma unroll
       for (int d = 1; d <= R; ++d) {
         float2 xp, xm;
@@ -597,10 +552,11 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
           zpl = make_float2(zp[R / 2 + (d - 1) / 2].y, zp[R / 2 + (d + 1) / 2].x);
           zmi = make_float2(zp[R / 2 - (d + 1) / 2].y, zp[R / 2 - (d - 1) / 2].x);
         }
-        lap = pair_term2(lap, P.w2[0][d - 1], xp, xm, uc0);
-        lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, uc0);
-        lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, uc0);
+        lx = pair_term2(lx, P.w2[0][d - 1], xp, xm, uc0);
+        ly = pair_term2(ly, P.w2[1][d - 1], yp, ym, uc0);
+        lz = pair_term2(lz, P.w2[2][d - 1], zpl, zmi, uc0);
       }
+      const float2 lap = __fadd2_rn(__fadd2_rn(lx, ly), lz);
       const float bx = __shfl_sync(0xffffffffu, bxc, 0);
       un0 = point_update2(uc0, up, lap, c2v, __fadd2_rn(make_float2(bx, bx), byz));
       sparse(0, j, un0);
@@ -610,13 +566,52 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
       if (act0 && own_row && j >= pd.xo0 && j < pd.xo1 && v0)
         __stcs(reinterpret_cast<float2*>(P.out0 + (size_t)j * ps + coff), un0);
     } else {
-      // fused steps k >= 1 write next step's centres into buffer (j+1) & 1,
+      // fused steps k >= 1 stage the next step's plane in buffer (j+1) & 1,
       // which the whole CTA read during step j-1: wait until it is retired
       if (j > jstart) {
         const int s = j - 1;
         ok = mbar_wait(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo);
         if (!ok) break;
       }
+      if (j < jend) {
+        // the neighbours' strips of step j+1: 16-byte copies, one or two per
+        // thread, completing on the step's centre barrier
+        const int jn = j + 1;
+        ok = mbar_wait(bar_nbr + (jn & 1), ((jn - jstart) >> 1) & 1, tmo);
+        if (!ok) break;
+        constexpr int CH_ROW = TZ / 4;           // 16-byte chunks per strip row
+        constexpr int CH_Y = 2 * R * CH_ROW;     // top + bottom strips
+        constexpr int CH_Z = 2 * TY * (RP / 4);  // left + right strips
+        constexpr int CH = CH_Y + CH_Z;
+        float* buf = splane + (size_t)(jn & 1) * (T - 1) * C::PSLOT;
+        for (int e = tid; e < (T - 1) * CH; e += NT) {
+          const int k = 1 + e / CH, r = e - (k - 1) * CH;
+          const int q = jn - k * R;
+          if (q < pd.xc0 || q >= pd.xc1) continue;
+          float* pl = buf + (k - 1) * C::PSLOT;
+          const float* ring_k = P.ring + (size_t)(k - 1) * C::D * C::STRIP + (size_t)(q % C::D) * C::STRIP;
+          const size_t tile_stride = (size_t)(T - 1) * C::D * C::STRIP;
+          if (r < CH_Y) {
+            const int hr = r / CH_ROW, c4 = 4 * (r - hr * CH_ROW);
+            if (hr < R) {
+              if (nb_up >= 0) cp_async16(pl + hr * SW + RP + c4, ring_k + nb_up * tile_stride + (R + hr) * TZ + c4);
+            } else if (nb_dn >= 0) {
+              cp_async16(pl + (TY + hr) * SW + RP + c4, ring_k + nb_dn * tile_stride + (hr - R) * TZ + c4);
+            }
+          } else {
+            const int r2 = r - CH_Y, row = r2 / (RP / 2), cc = r2 - row * (RP / 2);
+            const bool left = cc < RP / 4;
+            const int c4 = 4 * (left ? cc : cc - RP / 4);
+            if (left) {
+              if (nb_lf >= 0)
+                cp_async16(pl + (R + row) * SW + c4, ring_k + nb_lf * tile_stride + 2 * R * TZ + TY * RP + row * RP + c4);
+            } else if (nb_rt >= 0) {
+              cp_async16(pl + (R + row) * SW + RP + TZ + c4, ring_k + nb_rt * tile_stride + 2 * R * TZ + row * RP + c4);
+            }
+          }
+        }
+      }
+      cp_async_mbar_arrive(bar_ctr + ((j + 1) & 1));
       float* rs_base = P.ring + (size_t)b * (T - 1) * C::D * C::STRIP;
       float2 un = un0;
       bool act = act0;
@@ -645,7 +640,7 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
 #pragma unroll
             for (int m = 0; m <= R; ++m)
               zp[m] = (m == R / 2) ? uc : *reinterpret_cast<const float2*>(&pl[own - R + 2 * m]);
-            float2 lap = make_float2(0.f, 0.f);
+            float2 lx = make_float2(0.f, 0.f), ly = lx, lz = lx;
 #pragma unroll
             for (int d = 1; d <= R; ++d) {
               const float2 yp = *reinterpret_cast<const float2*>(&pl[own + d * SW]);
@@ -658,10 +653,11 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
                 zpl = make_float2(zp[R / 2 + (d - 1) / 2].y, zp[R / 2 + (d + 1) / 2].x);
                 zmi = make_float2(zp[R / 2 - (d + 1) / 2].y, zp[R / 2 - (d - 1) / 2].x);
               }
-              lap = pair_term2(lap, P.w2[0][d - 1], Qs[k - 1][R + d], Qs[k - 1][R - d], uc);
-              lap = pair_term2(lap, P.w2[1][d - 1], yp, ym, uc);
-              lap = pair_term2(lap, P.w2[2][d - 1], zpl, zmi, uc);
+              lx = pair_term2(lx, P.w2[0][d - 1], Qs[k - 1][R + d], Qs[k - 1][R - d], uc);
+              ly = pair_term2(ly, P.w2[1][d - 1], yp, ym, uc);
+              lz = pair_term2(lz, P.w2[2][d - 1], zpl, zmi, uc);
             }
+            const float2 lap = __fadd2_rn(__fadd2_rn(lx, ly), lz);
             const float bx = __shfl_sync(0xffffffffu, bxc, k);
             un = point_update2(uc, upv, lap, c2v, __fadd2_rn(make_float2(bx, bx), byz));
             sparse(k, q, un);
@@ -692,7 +688,6 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
           __stcs(reinterpret_cast<float2*>(P.out1 + (size_t)q * ps + coff), Qs[T - 2][R]);
         }
       }
-      asm volatile("fence.proxy.async.global;" ::: "memory");  // ring strips -> bulk readers
       mbar_arrive(bar_ctr + ((j + 1) & 1));
     }
     mbar_arrive(bar_done + (j - jstart) % C::NDONE);

@@ -79,6 +79,7 @@ struct SweepCfg {
   static constexpr int NP = PF + 1;                  // u^{n-1} tile ring
   static constexpr int NC = (T - 1) * R + 1 + PF;    // c2 tile ring
   static constexpr int NDONE = 8;                    // step-retirement barriers
+  static constexpr int NNBR = 8;                     // neighbour-readiness barriers
   static constexpr int D = 2 * R + 2;                // halo ring slots per fused step (global)
   static constexpr int STRIP = 2 * R * TZ + 2 * TY * RP;
   static constexpr int RING_PER_CTA = T > 1 ? (T - 1) * D * STRIP : 0;
@@ -92,7 +93,7 @@ struct SweepCfg {
   static constexpr size_t OFF_CUR = OFF_CNT + 2 * 2 * 2 * NT;
   static constexpr size_t OFF_XF = OFF_CUR + 2 * 2 * T * 2 * NT;  // receiver columns' first x
   static constexpr size_t OFF_BAR = align128(OFF_XF + 2 * 2 * NT);
-  static constexpr int NBAR = NU + NP + NC + 2 + 2 + NDONE;  // u, p, c, halo[2], centre[2], done
+  static constexpr int NBAR = NU + NP + NC + NNBR + 2 + NDONE;  // u, p, c, nbr, centre[2], done
   static constexpr size_t SMEM = OFF_BAR + 8 * NBAR + 128;    // + base alignment
   static_assert(R % 2 == 0, "radius must be even for aligned float2 access");
   static_assert(TY >= R && TZ >= RP, "a halo must come from one neighbour tile");
@@ -147,6 +148,25 @@ static __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, unsigned parit
 }
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long timeout_ns) {
   return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, timeout_ns);
+}
+// Poll without suspending (one thread; a nanosleep between tries).
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_poll(uint64_t* bar, unsigned parity, long long timeout_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_test(bar, parity)) {
+    if ((long long)(global_ns() - t0) > timeout_ns) return false;
+    __nanosleep(20);
+  }
+  return true;
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
                                             int c1, int c2) {
@@ -233,8 +253,8 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
   uint64_t* bar_u = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
   uint64_t* bar_p = bar_u + C::NU;
   uint64_t* bar_c = bar_p + C::NP;
-  uint64_t* bar_nbr = bar_c + C::NC;   // [2] neighbours hold the halo strips of stream step j
-  uint64_t* bar_ctr = bar_nbr + 2;     // [2] centres and halos of stream step j in buffer j & 1
+  uint64_t* bar_nbr = bar_c + C::NC;      // [NNBR] neighbours hold the strips of stream step j
+  uint64_t* bar_ctr = bar_nbr + C::NNBR;  // [2] centres and halos of stream step j in buffer j & 1
   uint64_t* bar_done = bar_ctr + 2;    // [NDONE] compute warps finished a stream step
   __shared__ int s_abort;
 
@@ -253,7 +273,7 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
 
   if (tid == 0) {
     s_abort = 0;
-    for (int i = 0; i < C::NU + C::NP + C::NC + 2; ++i) mbar_init(bar_u + i, 1);
+    for (int i = 0; i < C::NU + C::NP + C::NC + C::NNBR; ++i) mbar_init(bar_u + i, 1);
     mbar_init(bar_ctr + 0, NT);
     mbar_init(bar_ctr + 1, NT);
     for (int i = 0; i < C::NDONE; ++i) mbar_init(bar_done + i, NT);  // every compute thread arrives
@@ -308,8 +328,9 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
         while (nc <= jend && (nc - C::NC < jstart || nc - C::NC + (T - 1) * R <= ret)) issue_c(nc++);
         if constexpr (T > 1) {
           // tell the compute warps when the neighbours' strips of stream
-          // step nh may be copied (they copy them during step nh - 1)
-          while (nh <= jend && nh - 2 <= ret) {
+          // step nh may be copied (they copy them during step nh - 1); up to
+          // NNBR - 2 steps ahead of the last retired one
+          while (nh <= jend && nh - (C::NNBR - 2) <= ret) {
             if (!halo_ready(nh)) {
               if (nh != ret + 2) break;  // not needed yet: retire a step first
               const unsigned long long t0 = global_ns();
@@ -321,14 +342,15 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
                 }
               if (!ok) break;
             }
-            mbar_arrive(bar_nbr + (nh & 1));
+            mbar_arrive(bar_nbr + (nh - jstart) % C::NNBR);
             ++nh;
           }
           if (!ok) break;
         }
-        // retire the next stream step
+        // retire the next stream step (polled with a short back-off so the
+        // refills above go out as soon as a step is done)
         const int s = ret + 1;
-        if (!mbar_wait(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo)) {
+        if (!mbar_poll(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo)) {
           atomicExch(P.err, 2);
           ok = false;
           break;
@@ -577,7 +599,7 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
         // the neighbours' strips of step j+1: 16-byte copies, one or two per
         // thread, completing on the step's centre barrier
         const int jn = j + 1;
-        ok = mbar_wait(bar_nbr + (jn & 1), ((jn - jstart) >> 1) & 1, tmo);
+        ok = mbar_wait(bar_nbr + (jn - jstart) % C::NNBR, ((jn - jstart) / C::NNBR) & 1, tmo);
         if (!ok) break;
         constexpr int CH_ROW = TZ / 4;           // 16-byte chunks per strip row
         constexpr int CH_Y = 2 * R * CH_ROW;     // top + bottom strips

@@ -282,8 +282,10 @@ int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coor
     return status;
   }
   ok(cudaMemsetAsync(d_bad, 0, sizeof(int) * 4, st));
-  count_launch();
-  k_fill_u64<<<grid_for(P - (int64_t)npt * 8, 256), 256, 0, st>>>(t->keys, (int64_t)npt * 8, P, kSentinel);
+  if (P > (int64_t)npt * 8) {  // sentinel tail (empty when 8 npt is a power of two)
+    count_launch();
+    k_fill_u64<<<grid_for(P - (int64_t)npt * 8, 256), 256, 0, st>>>(t->keys, (int64_t)npt * 8, P, kSentinel);
+  }
   count_launch();
   k_corners<<<grid_for(npt, 128), 128, 0, st>>>(npt, d_coords, n[0], n[1], n[2], h[0], h[1], h[2],
                                                 t->keys, t->w8, d_bad);

@@ -157,6 +157,25 @@ def test_inspector_tables_match_oracle(tb):
     p.close()
 
 
+@pytest.mark.parametrize("nsrc", [256, 1024])
+def test_inspector_power_of_two_corner_count(tb, nsrc):
+    """8 * nsrc corners fill the sort exactly (no sentinel tail)."""
+    import torch
+    c, dt, _ = setup("ragged_so8")
+    g = wl.rng(77)
+    ext = np.array([(c["shape"][d] - 1) * c["h"][d] for d in range(3)])
+    src = g.uniform(0.05, 0.95, size=(nsrc, 3)) * ext
+    wav = np.repeat(wl.ricker(55.0, dt, 8)[None, :], nsrc, axis=0)
+    p = tb.Propagator(c["shape"], c["h"], c["so"], nbl=c["nbl"])
+    p.set_model(torch.from_numpy(c["vp"]).cuda(), dt=dt)
+    p.set_sources(src, wav)
+    lin, _ = p.source_points()
+    lin_o, _ = oracle.inspect_points(c["shape"], c["h"], c["so"], dt, 8,
+                                     c["vp"].astype(np.float64), src, wav)
+    np.testing.assert_array_equal(lin, lin_o)
+    p.close()
+
+
 def test_empty_geometry_and_zero_steps(tb):
     import torch
     c, dt, wav = setup("ragged_so12")

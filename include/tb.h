@@ -190,6 +190,35 @@ int tb_ricker(double f0, double dt, int nt, double t0, float* out);
  * Synchronises `stream`.  Errors: TB_EINVAL, TB_ECUDA. */
 int tb_selftest_wait(double timeout_s, void* stream);
 
+/* --- Allocation-free inspection --------------------------------------- */
+
+/* The source-point inspector of tb_set_sources (affected grid points of a
+ * set of off-grid points, ascending linear index), for callers that must not
+ * allocate device memory while they run: code with a device memory budget
+ * fixed at start-up, or a real-time loop where a cudaMalloc would
+ * synchronise the device.  This call allocates nothing: its scratch is a
+ * fixed array of about 1.8 MB in device memory, which every GPU that loads
+ * the library holds until the process exits.  (The paper has no
+ * counterpart; it is an interface addition of this library.)
+ *   n, h       grid shape and spacing, as for tb_create (host arrays).
+ *   npt        number of points, 0..8192; more is rejected with TB_EINVAL.
+ *   coords     device array [npt][3] of FP64 metres.
+ *   lin        device array with room for 8 * npt int64 values; receives the
+ *              ascending linear indices (x n1 + y) n2 + z of the affected
+ *              points (the paper's SID order).
+ *   npts       device int64: receives their number, or -1 when a coordinate
+ *              lies outside [0, (n_d - 1) h_d].
+ * Asynchronous on `stream`.  The first call on each device looks up the
+ * device address of the scratch array (with that device current); make
+ * that first call before any stream capture.  Nothing in the array has to
+ * start at zero: each call clears its own out-of-grid flag and overwrites
+ * the rest before reading it.  Every call shares the one array and it keeps
+ * the last call's contents: calls that overlap on the GPU
+ * (different streams without ordering between them) race and give wrong
+ * results; order them, e.g. on one stream.  Errors: TB_EINVAL, TB_ECUDA. */
+int tb_inspect_points_noalloc(const int64_t n[3], const double h[3], int npt, const double* coords,
+                              int64_t* lin, int64_t* npts, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * handles, all devices), for accounting in benchmarks. */
 uint64_t tb_launch_count(void);

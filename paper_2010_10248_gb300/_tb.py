@@ -62,6 +62,8 @@ _SIGS = {
     "tb_ricker": (C.c_int, [C.c_double, C.c_double, C.c_int, C.c_double, C.POINTER(C.c_float)]),
     "tb_selftest_wait": (C.c_int, [C.c_double, _vp]),
     "tb_launch_count": (C.c_uint64, []),
+    "tb_inspect_points_noalloc": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int,
+                                            _vp, _vp, _vp, _vp]),
 }
 
 
@@ -230,3 +232,11 @@ def tb_selftest_wait(timeout_s, stream=None):
 
 def tb_launch_count():
     return int(load().tb_launch_count())
+
+
+def tb_inspect_points_noalloc(shape, spacing, npt, coords, lin, npts, stream=None):
+    """Allocation-free source-point inspector; returns the status code."""
+    n = (C.c_int64 * 3)(*[int(v) for v in shape])
+    hh = (C.c_double * 3)(*[float(v) for v in spacing])
+    return load().tb_inspect_points_noalloc(n, hh, int(npt), _ptr(coords), _ptr(lin), _ptr(npts),
+                                            _stream(stream))

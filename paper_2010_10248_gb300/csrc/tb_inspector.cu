@@ -510,4 +510,113 @@ cudaError_t count_nonfinite(const float* a, int64_t n, int* d_count, cudaStream_
   return cudaGetLastError();
 }
 
+
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the source-point inspector (tb_inspect_points_noalloc).
+//
+// Some callers cannot call cudaMalloc while they run: code that must not
+// touch the allocator once started (a pre-sized device memory budget, or a
+// real-time loop where an allocation would synchronise the device), and
+// hosts whose memory is owned by another allocator.  This entry point takes
+// the inspector's scratch (sort keys, per-entry ids, group starts, corner
+// weights, counters) from a fixed array in device memory that every GPU
+// loading the library holds until the process exits.  It computes the
+// ascending unique affected points of a set of off-grid points, exactly as
+// tb_set_sources does, into the caller's buffers.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t kNoAllocKeys = 1 << 16;  // corner slots: 8 per point -> 8192 points
+constexpr size_t kNoAllocKeysOff = 0;
+constexpr size_t kNoAllocEntOff = kNoAllocKeysOff + sizeof(unsigned long long) * kNoAllocKeys;
+constexpr size_t kNoAllocStartOff = kNoAllocEntOff + sizeof(int) * kNoAllocKeys;
+constexpr size_t kNoAllocW8Off = kNoAllocStartOff + sizeof(int64_t) * (kNoAllocKeys + 2);
+constexpr size_t kNoAllocCountOff = kNoAllocW8Off + sizeof(double) * kNoAllocKeys;
+constexpr size_t kNoAllocBadOff = kNoAllocCountOff + sizeof(int64_t) * 2;
+constexpr size_t kNoAllocBytes = kNoAllocBadOff + 256;
+}  // namespace
+
+// The scratch of tb_inspect_points_noalloc (about 1.8 MB per device).
+static __device__ __align__(256) unsigned char g_tb_noalloc_scratch[kNoAllocBytes];
+
+__global__ void k_noalloc_result(const int* bad, const int64_t* counts, int64_t* npts_out) {
+  *npts_out = *bad ? -1 : counts[0];
+}
+
 }  // namespace tbi
+
+#include <mutex>
+
+namespace {
+// Device address of the scratch array, looked up once per device with that
+// device current (the host-side symbol is not a device address).
+void* noalloc_scratch(int dev, cudaError_t* err) {
+  constexpr int kMaxDevices = 256;
+  static void* ptr[kMaxDevices] = {nullptr};
+  static std::mutex mu;
+  *err = cudaSuccess;
+  if (dev < 0 || dev >= kMaxDevices) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    *err = cudaGetSymbolAddress(&p, tbi::g_tb_noalloc_scratch);
+    if (*err != cudaSuccess) return nullptr;
+    ptr[dev] = p;
+  }
+  return ptr[dev];
+}
+}  // namespace
+
+extern "C" int tb_inspect_points_noalloc(const int64_t n[3], const double h[3], int npt,
+                                         const double* coords, int64_t* lin, int64_t* npts,
+                                         void* stream) {
+  using namespace tbi;
+  if (!n || !h || !npts || npt < 0) return TB_EINVAL;
+  if ((int64_t)npt * 8 > kNoAllocKeys) return TB_EINVAL;  // more than 8192 points
+  if (npt > 0 && (!coords || !lin)) return TB_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (n[d] < 2 || n[d] > 65535 || !(h[d] > 0)) return TB_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return TB_ECUDA;
+  unsigned char* base = (unsigned char*)noalloc_scratch(dev, &e);
+  if (!base) {
+    cudaGetLastError();
+    return TB_ECUDA;
+  }
+  if (npt == 0) return cudaMemsetAsync(npts, 0, sizeof(int64_t), st) == cudaSuccess ? TB_OK : TB_ECUDA;
+  unsigned long long* keys = (unsigned long long*)(base + kNoAllocKeysOff);
+  int* ent_id = (int*)(base + kNoAllocEntOff);
+  int64_t* gstart = (int64_t*)(base + kNoAllocStartOff);
+  double* w8 = (double*)(base + kNoAllocW8Off);
+  int64_t* counts = (int64_t*)(base + kNoAllocCountOff);
+  int* bad = (int*)(base + kNoAllocBadOff);
+  int64_t P = 2048;
+  while (P < (int64_t)npt * 8) P <<= 1;
+  // the array keeps the previous call's contents: reset what must start at zero
+  e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    count_launch(3);
+    if (P > (int64_t)npt * 8) {
+      count_launch();
+      k_fill_u64<<<grid_for(P - (int64_t)npt * 8, 256), 256, 0, st>>>(keys, (int64_t)npt * 8, P, kSentinel);
+    }
+    k_corners<<<grid_for(npt, 128), 128, 0, st>>>(npt, coords, n[0], n[1], n[2], h[0], h[1], h[2], keys, w8,
+                                                  bad);
+    e = bitonic_sort(keys, P, st);
+  }
+  if (e == cudaSuccess) {
+    k_unique<<<1, 1024, 0, st>>>(keys, P, lin, gstart, ent_id, counts);
+    k_noalloc_result<<<1, 1, 0, st>>>(bad, counts, npts);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TB_ECUDA;
+  }
+  return TB_OK;
+}

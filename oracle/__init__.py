@@ -18,7 +18,12 @@ Functions and what they follow in the paper:
 * ``acoustic_wtb``        Listing 6 (wave-front temporal blocking).
 * ``acoustic_wtb_naive``  Fig. 4b (dependence-violating injection; negative test).
 * ``inspect_points``      Sec. II-A.1-2 (SM / SID) and Listing 3 (src_dcmp).
-* ``fd_weights_*``, ``cfl_dt_max``, ``damping_axis``, ``energy`` helpers.
+* ``tti_forward``         Sec. III-B: the pseudo-acoustic TTI system built on
+                          Eq. 2's rotated derivatives (two fields p, r).
+* ``elastic_forward``     Eq. 3 (Sec. III-C): isotropic elastic velocity-stress
+                          on the staggered grid, explosive source.
+* ``fd_weights_*``, ``cfl_dt_max``, ``tti_dt_max``, ``elastic_dt_max``,
+  ``damping_axis``, ``energy``, ``tti_energy``, ``elastic_energy`` helpers.
 """
 from __future__ import annotations
 
@@ -84,6 +89,18 @@ def _load():
                                              C.POINTER(C.c_int64), dp]
             L.orc_acoustic_energy.argtypes = [gp, dp, dp, dp]
             L.orc_acoustic_energy.restype = C.c_double
+            L.orc_tti_dt_max.argtypes = [C.c_int, dp, C.c_double, C.c_double]
+            L.orc_tti_dt_max.restype = C.c_double
+            L.orc_tti_forward.argtypes = [gp, dp, dp, dp, dp, dp, dp, C.c_int, dp, dp, C.c_int,
+                                          dp, dp, dp, dp]
+            L.orc_tti_energy.argtypes = [gp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+            L.orc_tti_energy.restype = C.c_double
+            L.orc_elastic_dt_max.argtypes = [C.c_int, dp, C.c_double]
+            L.orc_elastic_dt_max.restype = C.c_double
+            L.orc_elastic_forward.argtypes = [gp, dp, dp, dp, dp, C.c_int, dp, dp, C.c_int, dp, dp,
+                                              dp, dp]
+            L.orc_elastic_energy.argtypes = [gp, dp, dp, dp, dp, dp, dp]
+            L.orc_elastic_energy.restype = C.c_double
         return _lib
 
 
@@ -254,3 +271,75 @@ def energy(shape, spacing, so, dt, vp, u_next, u_cur, periodic=False):
     g = make_grid(shape, spacing, so, dt, 1, 0, periodic, 0)
     return float(_load().orc_acoustic_energy(C.byref(g), _dp(_f64(vp)), _dp(_f64(u_next)),
                                              _dp(_f64(u_cur))))
+
+
+ELASTIC_FIELDS = ("vx", "vy", "vz", "txx", "tyy", "tzz", "txy", "txz", "tyz")
+
+
+def tti_dt_max(so, spacing, vmax, eps_max):
+    h = np.asarray(spacing, dtype=np.float64)
+    return float(_load().orc_tti_dt_max(so, _dp(h), float(vmax), float(eps_max)))
+
+
+def elastic_dt_max(so, spacing, vpmax):
+    h = np.asarray(spacing, dtype=np.float64)
+    return float(_load().orc_elastic_dt_max(so, _dp(h), float(vpmax)))
+
+
+def tti_forward(shape, spacing, so, dt, nt, vp, eps, delta, theta, phi, *, nbl=0, eta=None,
+                src_xyz=None, src_wav=None, rec_xyz=None, init=None, periodic=False, nthreads=0):
+    """Pseudo-acoustic TTI (Sec. III-B, Eq. 2), direct off-grid injection into
+    p and r, receivers on p.  ``init``: None or [4, *shape] = p^0, p^-1, r^0,
+    r^-1.  Returns (traces [nt, nrec], state [4, *shape] = p^nt, p^nt-1,
+    r^nt, r^nt-1)."""
+    g = make_grid(shape, spacing, so, dt, nt, nbl, periodic, nthreads)
+    nsrc, sx = _geom(src_xyz)
+    nrec, rx = _geom(rec_xyz)
+    sw = _f64(np.asarray(src_wav).reshape(nsrc, nt)) if nsrc else None
+    traces = np.zeros((nt, max(nrec, 1)))
+    out = np.zeros((4,) + tuple(shape))
+    args = [_f64(np.broadcast_to(a, tuple(shape))) for a in (vp, eps, delta, theta, phi)]
+    st = _load().orc_tti_forward(C.byref(g), *[_dp(a) for a in args], _dp(_f64(eta)), nsrc,
+                                 _dp(sx), _dp(sw), nrec, _dp(rx), _dp(traces),
+                                 _dp(_f64(init)), _dp(out))
+    _check(st, "tti_forward")
+    return traces[:, :nrec], out
+
+
+def tti_energy(shape, spacing, so, dt, vp, eps, delta, theta, phi, p_next, p_cur, r_next, r_cur,
+               periodic=False):
+    """Discrete energy of the undamped TTI leapfrog (eps > delta)."""
+    g = make_grid(shape, spacing, so, dt, 1, 0, periodic, 0)
+    args = [_f64(np.broadcast_to(a, tuple(shape))) for a in (vp, eps, delta, theta, phi)]
+    return float(_load().orc_tti_energy(C.byref(g), *[_dp(a) for a in args],
+                                        *[_dp(_f64(a)) for a in (p_next, p_cur, r_next, r_cur)]))
+
+
+def elastic_forward(shape, spacing, so, dt, nt, vp, vs, rho, *, nbl=0, eta=None, src_xyz=None,
+                    src_wav=None, rec_xyz=None, init=None, periodic=False, nthreads=0):
+    """Isotropic elastic velocity-stress (Eq. 3) on the staggered grid,
+    explosive off-grid source into txx, tyy, tzz, receivers on the mean
+    normal stress.  ``init``: None or [9, *shape] in ELASTIC_FIELDS order
+    (velocities at -1/2, stresses at 0).  Returns (traces [nt, nrec], state
+    [9, *shape]: velocities at nt - 1/2, stresses at nt)."""
+    g = make_grid(shape, spacing, so, dt, nt, nbl, periodic, nthreads)
+    nsrc, sx = _geom(src_xyz)
+    nrec, rx = _geom(rec_xyz)
+    sw = _f64(np.asarray(src_wav).reshape(nsrc, nt)) if nsrc else None
+    traces = np.zeros((nt, max(nrec, 1)))
+    out = np.zeros((9,) + tuple(shape))
+    args = [_f64(np.broadcast_to(a, tuple(shape))) for a in (vp, vs, rho)]
+    st = _load().orc_elastic_forward(C.byref(g), *[_dp(a) for a in args], _dp(_f64(eta)), nsrc,
+                                     _dp(sx), _dp(sw), nrec, _dp(rx), _dp(traces),
+                                     _dp(_f64(init)), _dp(out))
+    _check(st, "elastic_forward")
+    return traces[:, :nrec], out
+
+
+def elastic_energy(shape, spacing, so, dt, vp, vs, rho, v_next, v_prev, tau, periodic=False):
+    """Discrete energy E^n of the undamped staggered scheme from v^{n+1/2},
+    v^{n-1/2} ([3, *shape]) and the stresses at n ([6, *shape])."""
+    g = make_grid(shape, spacing, so, dt, 1, 0, periodic, 0)
+    args = [_f64(np.broadcast_to(a, tuple(shape))) for a in (vp, vs, rho)]
+    return float(_load().orc_elastic_energy(C.byref(g), *[_dp(a) for a in args],
+                                            *[_dp(_f64(a)) for a in (v_next, v_prev, tau)]))

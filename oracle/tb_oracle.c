@@ -50,6 +50,13 @@
  *                           injection applied when the tile holding the
  *                           source is visited (a dependence violation; used
  *                           as a negative test)
+ *
+ * The other two propagators of Sec. III, unblocked with direct injection:
+ *   orc_tti_forward         Sec. III-B, Eq. 2: pseudo-acoustic TTI (two fields)
+ *   orc_elastic_forward     Sec. III-C, Eq. 3: isotropic elastic velocity-stress
+ * Parity unpinned (readings, no invariant fixes them): the edge averaging of
+ * the elastic material parameters, the elastic sponge form, and which TTI
+ * field the receivers sample.
  */
 #include <math.h>
 #include <stdint.h>
@@ -765,4 +772,599 @@ double orc_acoustic_energy(const orc_grid* g, const double* vp, const double* u_
   free(uc);
   model_free(&M);
   return kin - pot;
+}
+
+/* =========================================================================
+ * Shared helpers of the TTI and elastic oracles: padded copies and the
+ * maximum of a trigonometric symbol (for the stability limits).
+ * ======================================================================= */
+static void to_padded(const pad_t* p, const double* src, double* dst) {
+  for (int64_t x = 0; x < p->n0; ++x)
+    for (int64_t y = 0; y < p->n1; ++y)
+      for (int64_t z = 0; z < p->n2; ++z) dst[pidx(p, x, y, z)] = src[gidx(p, x, y, z)];
+}
+static void from_padded(const pad_t* p, const double* src, double* dst) {
+  for (int64_t x = 0; x < p->n0; ++x)
+    for (int64_t y = 0; y < p->n1; ++y)
+      for (int64_t z = 0; z < p->n2; ++z) dst[gidx(p, x, y, z)] = src[pidx(p, x, y, z)];
+}
+/* max over theta in [0, pi] of |2 sum_i c[i] sin((i - shift) theta)|, by
+ * dense sampling (the symbols are smooth; 2e5 samples). */
+static double symbol_max(const double* c, int r, double shift) {
+  double best = 0.0;
+  const int ns = 200000;
+  for (int s = 0; s <= ns; ++s) {
+    double th = M_PI * (double)s / ns, v = 0.0;
+    for (int i = 1; i <= r; ++i) v += c[i] * sin(((double)i - shift) * th);
+    v = fabs(2.0 * v);
+    if (v > best) best = v;
+  }
+  return best;
+}
+
+/* =========================================================================
+ * Anisotropic pseudo-acoustic (TTI) propagator, Sec. III-B.
+ *
+ * Eq. 2 gives the rotated first derivative
+ *   D_xbar = cos t cos f d/dx + cos t sin f d/dy - sin t d/dz
+ * (t = theta, tilt; f = phi, azimuth).  The paper does not print the full
+ * system; this oracle takes the self-adjoint pseudo-acoustic system of the
+ * work it cites for it (Zhang, Zhang and Zhang 2011):
+ *   m p_tt = (1 + 2 eps) H_h p + sqrt(1 + 2 delta) H_z r
+ *   m r_tt = sqrt(1 + 2 delta) H_h p + H_z r
+ *   H_h = -(D_xbar^T D_xbar + D_ybar^T D_ybar),   H_z = -D_zbar^T D_zbar
+ * on the orthonormal frame completing Eq. 2 (axis order x, y, z = 0, 1, 2):
+ *   xbar = ( cos t cos f,  cos t sin f, -sin t)
+ *   ybar = (-sin f,        cos f,        0    )
+ *   zbar = ( sin t cos f,  sin t sin f,  cos t)
+ * Discretisation: D_nbar u (p) = sum_d nbar_d(p) (Dc_d u)(p), Dc_d the centred
+ * first derivative of order so with the field zero outside the grid.  Its
+ * transpose is -sum_d Dc_d (nbar_d .), so
+ *   H_h p = sum_d Dc_d F_d,  F = xbar (xbar . Dc p) + ybar (ybar . Dc p)
+ *   H_z r = sum_d Dc_d G_d,  G = zbar (zbar . Dc r)
+ * with the fluxes F, G zero outside the grid.  Each field is stepped like
+ * Eq. 1 (same leapfrog, damping and dt^2/m source scaling); sources are
+ * injected into p and r alike, receivers sample p.
+ * ======================================================================= */
+typedef struct {
+  pad_t p;
+  int r;
+  double a[32];     /* centred 1st-derivative weights a[1..r], unit spacing */
+  double ih[3];     /* 1 / h_d */
+  double dt, dt2;
+  double *m, *eta, *cpp, *cpr;   /* [N]: 1/vp^2, damping, 1+2eps, sqrt(1+2delta) */
+  double *nx, *ny, *nz;          /* [3][N] frame vectors xbar, ybar, zbar       */
+  int periodic;
+} tti_t;
+
+static void tti_free(tti_t* T) {
+  free(T->m); free(T->eta); free(T->cpp); free(T->cpr);
+  free(T->nx); free(T->ny); free(T->nz);
+}
+
+static int tti_init(tti_t* T, const orc_grid* g, const double* vp, const double* eps,
+                    const double* delta, const double* theta, const double* phi,
+                    const double* eta_in) {
+  memset(T, 0, sizeof(*T));
+  if (g->so != 4 && g->so != 8 && g->so != 12) return ORC_EINVAL;
+  T->p = make_pad(g);
+  T->r = g->so / 2;
+  for (int d = 0; d < 3; ++d) {
+    if (g->n[d] < 2 * T->r + 2) return ORC_EINVAL;
+    T->ih[d] = 1.0 / g->h[d];
+  }
+  if (orc_fd_weights_d1(g->so, T->a)) return ORC_EINVAL;
+  T->dt = g->dt;
+  T->dt2 = g->dt * g->dt;
+  T->periodic = g->periodic;
+  int64_t N = g->n[0] * g->n[1] * g->n[2];
+  T->m = (double*)malloc(sizeof(double) * N);
+  T->eta = (double*)malloc(sizeof(double) * N);
+  T->cpp = (double*)malloc(sizeof(double) * N);
+  T->cpr = (double*)malloc(sizeof(double) * N);
+  T->nx = (double*)malloc(sizeof(double) * 3 * N);
+  T->ny = (double*)malloc(sizeof(double) * 3 * N);
+  T->nz = (double*)malloc(sizeof(double) * 3 * N);
+  if (!T->m || !T->eta || !T->cpp || !T->cpr || !T->nx || !T->ny || !T->nz) return ORC_ENOMEM;
+  double vmax = 0.0;
+  for (int64_t i = 0; i < N; ++i) {
+    if (!(vp[i] > 0.0)) return ORC_EINVAL;
+    if (!(eps[i] >= delta[i]) || !(delta[i] > -0.5)) return ORC_EINVAL; /* C must be PSD */
+    T->m[i] = 1.0 / (vp[i] * vp[i]);
+    T->cpp[i] = 1.0 + 2.0 * eps[i];
+    T->cpr[i] = sqrt(1.0 + 2.0 * delta[i]);
+    double ct = cos(theta[i]), st = sin(theta[i]), cf = cos(phi[i]), sf = sin(phi[i]);
+    T->nx[i] = ct * cf; T->nx[N + i] = ct * sf; T->nx[2 * N + i] = -st;
+    T->ny[i] = -sf;     T->ny[N + i] = cf;      T->ny[2 * N + i] = 0.0;
+    T->nz[i] = st * cf; T->nz[N + i] = st * sf; T->nz[2 * N + i] = ct;
+    if (vp[i] > vmax) vmax = vp[i];
+  }
+  if (eta_in) {
+    memcpy(T->eta, eta_in, sizeof(double) * N);
+  } else {
+    double* ea[3];
+    for (int d = 0; d < 3; ++d) {
+      ea[d] = (double*)malloc(sizeof(double) * g->n[d]);
+      orc_damping_axis(g->n[d], g->nbl, g->h[d], vmax, ea[d]);
+    }
+    for (int64_t x = 0; x < g->n[0]; ++x)
+      for (int64_t y = 0; y < g->n[1]; ++y)
+        for (int64_t z = 0; z < g->n[2]; ++z)
+          T->eta[gidx(&T->p, x, y, z)] = ea[0][x] + ea[1][y] + ea[2][z];
+    for (int d = 0; d < 3; ++d) free(ea[d]);
+  }
+  return ORC_OK;
+}
+
+/* centred first derivative along axis d of a padded field at padded index q */
+static inline double tti_dc(const tti_t* T, const double* u, int64_t q, int d) {
+  const pad_t* p = &T->p;
+  int64_t s = d == 0 ? p->P1 * p->P2 : (d == 1 ? p->P2 : 1);
+  double acc = 0.0;
+  for (int i = 1; i <= T->r; ++i) acc += T->a[i] * (u[q + i * s] - u[q - i * s]);
+  return acc * T->ih[d];
+}
+
+/* Hh = H_h p and Hz = H_z r ([N], unpadded) from padded p, r (halos already
+ * zero or wrapped).  F[3], G[3] are padded scratch fields whose halos are
+ * zero on entry. */
+static void tti_apply(const tti_t* T, const double* pc, const double* rc, double* F[3],
+                      double* G[3], double* Hh, double* Hz) {
+  const pad_t* p = &T->p;
+  const int64_t N = p->n0 * p->n1 * p->n2;
+#pragma omp parallel for schedule(static)
+  for (int64_t x = 0; x < p->n0; ++x)
+    for (int64_t y = 0; y < p->n1; ++y)
+      for (int64_t z = 0; z < p->n2; ++z) {
+        int64_t q = pidx(p, x, y, z), gq = gidx(p, x, y, z);
+        double gp[3], gr[3];
+        for (int d = 0; d < 3; ++d) {
+          gp[d] = tti_dc(T, pc, q, d);
+          gr[d] = tti_dc(T, rc, q, d);
+        }
+        double ax = 0.0, ay = 0.0, bz = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          ax += T->nx[d * N + gq] * gp[d];
+          ay += T->ny[d * N + gq] * gp[d];
+          bz += T->nz[d * N + gq] * gr[d];
+        }
+        for (int d = 0; d < 3; ++d) {
+          F[d][q] = T->nx[d * N + gq] * ax + T->ny[d * N + gq] * ay;
+          G[d][q] = T->nz[d * N + gq] * bz;
+        }
+      }
+  if (T->periodic)
+    for (int d = 0; d < 3; ++d) { wrap_halo(p, F[d]); wrap_halo(p, G[d]); }
+#pragma omp parallel for schedule(static)
+  for (int64_t x = 0; x < p->n0; ++x)
+    for (int64_t y = 0; y < p->n1; ++y)
+      for (int64_t z = 0; z < p->n2; ++z) {
+        int64_t q = pidx(p, x, y, z), gq = gidx(p, x, y, z);
+        double hh = 0.0, hz = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          hh += tti_dc(T, F[d], q, d);
+          hz += tti_dc(T, G[d], q, d);
+        }
+        Hh[gq] = hh;
+        Hz[gq] = hz;
+      }
+}
+
+/* Stability limit of the TTI leapfrog: the largest eigenvalue of the
+ * per-point 2x2 system is at most (1 + 2 eps) |s|^2 when eps >= delta, with
+ * |s_d| <= S1/h_d, S1 = max |2 sum a_i sin(i theta)| (centred 1st
+ * derivative), so dt_max = 2 / (vmax sqrt(1 + 2 eps_max) sqrt(sum (S1/h_d)^2)). */
+double orc_tti_dt_max(int so, const double h[3], double vmax, double eps_max) {
+  double a[32];
+  if (orc_fd_weights_d1(so, a)) return -1.0;
+  double S1 = symbol_max(a, so / 2, 0.0);
+  double s2 = 0.0;
+  for (int d = 0; d < 3; ++d) s2 += (S1 / h[d]) * (S1 / h[d]);
+  return 2.0 / (vmax * sqrt((1.0 + 2.0 * eps_max) * s2));
+}
+
+/* init: NULL or [4][N] = p^0, p^{-1}, r^0, r^{-1}; out: NULL or [4][N] =
+ * p^{nt}, p^{nt-1}, r^{nt}, r^{nt-1}; traces [nt][nrec] sample p^{n+1}. */
+int orc_tti_forward(const orc_grid* g, const double* vp, const double* eps, const double* delta,
+                    const double* theta, const double* phi, const double* eta, int nsrc,
+                    const double* src_xyz, const double* src_wav, int nrec, const double* rec_xyz,
+                    double* traces, const double* init, double* out) {
+  tti_t T;
+  int st = tti_init(&T, g, vp, eps, delta, theta, phi, eta);
+  if (st) { tti_free(&T); return st; }
+  const pad_t* p = &T.p;
+  const int64_t N = p->n0 * p->n1 * p->n2;
+#ifdef _OPENMP
+  if (g->nthreads > 0) omp_set_num_threads(g->nthreads);
+#endif
+  int64_t* sb = (int64_t*)malloc(sizeof(int64_t) * 3 * (nsrc > 0 ? nsrc : 1));
+  double* sf = (double*)malloc(sizeof(double) * 3 * (nsrc > 0 ? nsrc : 1));
+  int64_t* rb = (int64_t*)malloc(sizeof(int64_t) * 3 * (nrec > 0 ? nrec : 1));
+  double* rf = (double*)malloc(sizeof(double) * 3 * (nrec > 0 ? nrec : 1));
+  double* buf = (double*)calloc((size_t)p->NP * 12, sizeof(double));
+  double* Hh = (double*)malloc(sizeof(double) * N);
+  double* Hz = (double*)malloc(sizeof(double) * N);
+  if (!sb || !sf || !rb || !rf || !buf || !Hh || !Hz) { st = ORC_ENOMEM; goto done; }
+  for (int s = 0; s < nsrc; ++s)
+    if (trilinear(g, src_xyz + 3 * s, sb + 3 * s, sf + 3 * s)) { st = ORC_EINVAL; goto done; }
+  for (int r = 0; r < nrec; ++r)
+    if (trilinear(g, rec_xyz + 3 * r, rb + 3 * r, rf + 3 * r)) { st = ORC_EINVAL; goto done; }
+  {
+    double* pp = buf;                 /* p^{n-1} */
+    double* pc = buf + p->NP;         /* p^n     */
+    double* pn = buf + 2 * p->NP;     /* p^{n+1} */
+    double* rp = buf + 3 * p->NP;
+    double* rc = buf + 4 * p->NP;
+    double* rn = buf + 5 * p->NP;
+    double* F[3] = {buf + 6 * p->NP, buf + 7 * p->NP, buf + 8 * p->NP};
+    double* G[3] = {buf + 9 * p->NP, buf + 10 * p->NP, buf + 11 * p->NP};
+    if (init) {
+      to_padded(p, init, pc);
+      to_padded(p, init + N, pp);
+      to_padded(p, init + 2 * N, rc);
+      to_padded(p, init + 3 * N, rp);
+    }
+    for (int n = 0; n < g->nt; ++n) {
+      if (T.periodic) { wrap_halo(p, pc); wrap_halo(p, rc); }
+      tti_apply(&T, pc, rc, F, G, Hh, Hz);
+#pragma omp parallel for schedule(static)
+      for (int64_t x = 0; x < p->n0; ++x)
+        for (int64_t y = 0; y < p->n1; ++y)
+          for (int64_t z = 0; z < p->n2; ++z) {
+            int64_t q = pidx(p, x, y, z), gq = gidx(p, x, y, z);
+            double m = T.m[gq], a = T.eta[gq] * T.dt * 0.5;
+            double rhs_p = T.cpp[gq] * Hh[gq] + T.cpr[gq] * Hz[gq];
+            double rhs_r = T.cpr[gq] * Hh[gq] + Hz[gq];
+            pn[q] = (T.dt2 * rhs_p + m * (2.0 * pc[q] - pp[q]) + a * pp[q]) / (m + a);
+            rn[q] = (T.dt2 * rhs_r + m * (2.0 * rc[q] - rp[q]) + a * rp[q]) / (m + a);
+          }
+      for (int s = 0; s < nsrc; ++s) {
+        double qv = src_wav[(int64_t)s * g->nt + n];
+        for (int c = 0; c < 8; ++c) {
+          double w = corner_weight(sf + 3 * s, c);
+          if (w == 0.0) continue;
+          int64_t x = sb[3 * s] + ((c >> 2) & 1), y = sb[3 * s + 1] + ((c >> 1) & 1),
+                  z = sb[3 * s + 2] + (c & 1);
+          double add = w * qv * T.dt2 / T.m[gidx(p, x, y, z)];
+          pn[pidx(p, x, y, z)] += add;
+          rn[pidx(p, x, y, z)] += add;
+        }
+      }
+      for (int r = 0; r < nrec; ++r) {
+        double acc = 0.0;
+        for (int c = 0; c < 8; ++c) {
+          double w = corner_weight(rf + 3 * r, c);
+          if (w == 0.0) continue;
+          int64_t x = rb[3 * r] + ((c >> 2) & 1), y = rb[3 * r + 1] + ((c >> 1) & 1),
+                  z = rb[3 * r + 2] + (c & 1);
+          acc += w * pn[pidx(p, x, y, z)];
+        }
+        traces[(int64_t)n * nrec + r] = acc;
+      }
+      double* t = pp; pp = pc; pc = pn; pn = t;
+      t = rp; rp = rc; rc = rn; rn = t;
+    }
+    if (out) {
+      from_padded(p, pc, out);
+      from_padded(p, pp, out + N);
+      from_padded(p, rc, out + 2 * N);
+      from_padded(p, rp, out + 3 * N);
+    }
+  }
+done:
+  free(sb); free(sf); free(rb); free(rf); free(buf); free(Hh); free(Hz);
+  tti_free(&T);
+  return st;
+}
+
+/* Discrete energy of the undamped TTI leapfrog (eps > delta everywhere):
+ *   E^{n+1/2} = sum_pts D^T (m C^{-1}) D / dt^2 - (p^{n+1}.H_h p^n + r^{n+1}.H_z r^n)
+ * with D = (p^{n+1} - p^n, r^{n+1} - r^n) and C = [[1+2eps, s], [s, 1]],
+ * s = sqrt(1+2delta).  Constant in n for a symmetric H (no source). */
+double orc_tti_energy(const orc_grid* g, const double* vp, const double* eps, const double* delta,
+                      const double* theta, const double* phi, const double* p_next,
+                      const double* p_cur, const double* r_next, const double* r_cur) {
+  tti_t T;
+  orc_grid g2 = *g;
+  g2.nbl = 0;
+  if (tti_init(&T, &g2, vp, eps, delta, theta, phi, NULL)) { tti_free(&T); return NAN; }
+  const pad_t* p = &T.p;
+  const int64_t N = p->n0 * p->n1 * p->n2;
+  double* buf = (double*)calloc((size_t)p->NP * 8, sizeof(double));
+  double* Hh = (double*)malloc(sizeof(double) * N);
+  double* Hz = (double*)malloc(sizeof(double) * N);
+  double E = NAN;
+  if (buf && Hh && Hz) {
+    double* pc = buf;
+    double* rc = buf + p->NP;
+    double* F[3] = {buf + 2 * p->NP, buf + 3 * p->NP, buf + 4 * p->NP};
+    double* G[3] = {buf + 5 * p->NP, buf + 6 * p->NP, buf + 7 * p->NP};
+    to_padded(p, p_cur, pc);
+    to_padded(p, r_cur, rc);
+    if (T.periodic) { wrap_halo(p, pc); wrap_halo(p, rc); }
+    tti_apply(&T, pc, rc, F, G, Hh, Hz);
+    double kin = 0.0, pot = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+      double a = T.cpp[i], s = T.cpr[i], det = a - s * s;
+      double dp = (p_next[i] - p_cur[i]) / T.dt, dr = (r_next[i] - r_cur[i]) / T.dt;
+      kin += T.m[i] * (dp * dp - 2.0 * s * dp * dr + a * dr * dr) / det;
+      pot += p_next[i] * Hh[i] + r_next[i] * Hz[i];
+    }
+    E = kin - pot;
+  }
+  free(buf); free(Hh); free(Hz);
+  tti_free(&T);
+  return E;
+}
+
+/* =========================================================================
+ * Isotropic elastic velocity-stress propagator, Eq. 3 (Sec. III-C).
+ *
+ * Standard staggered grid (Virieux 1986, which the paper cites):
+ *   vx (i+1/2, j, k)   vy (i, j+1/2, k)   vz (i, j, k+1/2)
+ *   txx, tyy, tzz (i, j, k)
+ *   txy (i+1/2, j+1/2, k)   txz (i+1/2, j, k+1/2)   tyz (i, j+1/2, k+1/2)
+ * Every field is an n0 x n1 x n2 array (index i of a half-node stands for
+ * i + 1/2) and is zero outside it.  Staggered derivatives of order so with
+ * the weights c_k of nodes at +-(k - 1/2):
+ *   Dp_d f (i) = sum_k c_k (f[i+k] - f[i-k+1]) / h_d    (node -> half-node)
+ *   Dm_d g (i) = sum_k c_k (g[i+k-1] - g[i-k]) / h_d    (half-node -> node)
+ * (Dp^T = -Dm on these arrays, which makes the scheme energy conserving).
+ * One time step n (v at n-1/2 -> n+1/2, stresses at n -> n+1):
+ *   vx += dt bx (Dp_x txx + Dm_y txy + Dm_z txz)
+ *   vy += dt by (Dm_x txy + Dp_y tyy + Dm_z tyz)
+ *   vz += dt bz (Dm_x txz + Dm_y tyz + Dp_z tzz)
+ *   tii += dt (lam tr(e) + 2 mu e_ii),  e_ii = Dm_i v_i
+ *   txy += dt mu_xy (Dp_y vx + Dp_x vy), and likewise txz, tyz
+ * with b = 1/rho, lam = rho (vp^2 - 2 vs^2), mu = rho vs^2; b at a half-node
+ * is the arithmetic mean of its two nodes, mu at an edge the harmonic mean
+ * of its four nodes (0 if one of them is 0); a neighbour beyond the last
+ * node takes the last node's value.
+ * Damping: each updated value is (old + dt rhs) / (1 + eta dt), eta the
+ * sponge at the array index.  Explosive source: after the stress update of
+ * step n, txx, tyy, tzz += dt w q[n] at each trilinear corner.  Receivers:
+ * trace[n] = sum_c w (txx + tyy + tzz)(c) / 3 of the stresses at n+1.
+ * ======================================================================= */
+typedef struct {
+  pad_t p;
+  int r;
+  double c[32];   /* staggered weights c[1..r], unit spacing */
+  double ih[3];
+  double dt;
+  double *bx, *by, *bz, *lam, *mu, *mxy, *mxz, *myz, *eta;   /* [N] */
+  int periodic;
+} ela_t;
+
+enum { EVX, EVY, EVZ, ETXX, ETYY, ETZZ, ETXY, ETXZ, ETYZ };
+
+static void ela_free(ela_t* E) {
+  free(E->bx); free(E->by); free(E->bz); free(E->lam); free(E->mu);
+  free(E->mxy); free(E->mxz); free(E->myz); free(E->eta);
+}
+
+static double harm4(double a, double b, double c, double d) {
+  if (a <= 0.0 || b <= 0.0 || c <= 0.0 || d <= 0.0) return 0.0;
+  return 4.0 / (1.0 / a + 1.0 / b + 1.0 / c + 1.0 / d);
+}
+
+static int ela_init(ela_t* E, const orc_grid* g, const double* vp, const double* vs,
+                    const double* rho, const double* eta_in) {
+  memset(E, 0, sizeof(*E));
+  if (g->so != 4 && g->so != 8 && g->so != 12) return ORC_EINVAL;
+  E->p = make_pad(g);
+  E->r = g->so / 2;
+  for (int d = 0; d < 3; ++d) {
+    if (g->n[d] < 2 * E->r + 2) return ORC_EINVAL;
+    E->ih[d] = 1.0 / g->h[d];
+  }
+  if (orc_fd_weights_stag(g->so, E->c)) return ORC_EINVAL;
+  E->dt = g->dt;
+  E->periodic = g->periodic;
+  const pad_t* p = &E->p;
+  int64_t N = p->n0 * p->n1 * p->n2;
+  double** arr[9] = {&E->bx, &E->by, &E->bz, &E->lam, &E->mu, &E->mxy, &E->mxz, &E->myz, &E->eta};
+  for (int i = 0; i < 9; ++i) {
+    *arr[i] = (double*)malloc(sizeof(double) * N);
+    if (!*arr[i]) return ORC_ENOMEM;
+  }
+  double vmax = 0.0;
+  for (int64_t i = 0; i < N; ++i) {
+    if (!(vp[i] > 0.0) || !(rho[i] > 0.0) || !(vs[i] >= 0.0) || !(2.0 * vs[i] * vs[i] <= vp[i] * vp[i]))
+      return ORC_EINVAL;
+    E->lam[i] = rho[i] * (vp[i] * vp[i] - 2.0 * vs[i] * vs[i]);
+    E->mu[i] = rho[i] * vs[i] * vs[i];
+    if (vp[i] > vmax) vmax = vp[i];
+  }
+  for (int64_t x = 0; x < p->n0; ++x)
+    for (int64_t y = 0; y < p->n1; ++y)
+      for (int64_t z = 0; z < p->n2; ++z) {
+        int64_t x1 = x + 1 < p->n0 ? x + 1 : x, y1 = y + 1 < p->n1 ? y + 1 : y,
+                z1 = z + 1 < p->n2 ? z + 1 : z;
+        int64_t q = gidx(p, x, y, z);
+        E->bx[q] = 0.5 * (1.0 / rho[q] + 1.0 / rho[gidx(p, x1, y, z)]);
+        E->by[q] = 0.5 * (1.0 / rho[q] + 1.0 / rho[gidx(p, x, y1, z)]);
+        E->bz[q] = 0.5 * (1.0 / rho[q] + 1.0 / rho[gidx(p, x, y, z1)]);
+        E->mxy[q] = harm4(E->mu[q], E->mu[gidx(p, x1, y, z)], E->mu[gidx(p, x, y1, z)],
+                          E->mu[gidx(p, x1, y1, z)]);
+        E->mxz[q] = harm4(E->mu[q], E->mu[gidx(p, x1, y, z)], E->mu[gidx(p, x, y, z1)],
+                          E->mu[gidx(p, x1, y, z1)]);
+        E->myz[q] = harm4(E->mu[q], E->mu[gidx(p, x, y1, z)], E->mu[gidx(p, x, y, z1)],
+                          E->mu[gidx(p, x, y1, z1)]);
+      }
+  if (eta_in) {
+    memcpy(E->eta, eta_in, sizeof(double) * N);
+  } else {
+    double* ea[3];
+    for (int d = 0; d < 3; ++d) {
+      ea[d] = (double*)malloc(sizeof(double) * g->n[d]);
+      orc_damping_axis(g->n[d], g->nbl, g->h[d], vmax, ea[d]);
+    }
+    for (int64_t x = 0; x < p->n0; ++x)
+      for (int64_t y = 0; y < p->n1; ++y)
+        for (int64_t z = 0; z < p->n2; ++z)
+          E->eta[gidx(p, x, y, z)] = ea[0][x] + ea[1][y] + ea[2][z];
+    for (int d = 0; d < 3; ++d) free(ea[d]);
+  }
+  return ORC_OK;
+}
+
+static inline int64_t ela_stride(const pad_t* p, int d) {
+  return d == 0 ? p->P1 * p->P2 : (d == 1 ? p->P2 : 1);
+}
+/* node -> half-node derivative along d at padded index q */
+static inline double ela_dp(const ela_t* E, const double* f, int64_t q, int d) {
+  int64_t s = ela_stride(&E->p, d);
+  double acc = 0.0;
+  for (int k = 1; k <= E->r; ++k) acc += E->c[k] * (f[q + k * s] - f[q - (k - 1) * s]);
+  return acc * E->ih[d];
+}
+/* half-node -> node derivative along d at padded index q */
+static inline double ela_dm(const ela_t* E, const double* g, int64_t q, int d) {
+  int64_t s = ela_stride(&E->p, d);
+  double acc = 0.0;
+  for (int k = 1; k <= E->r; ++k) acc += E->c[k] * (g[q + (k - 1) * s] - g[q - k * s]);
+  return acc * E->ih[d];
+}
+
+/* Stability limit of the staggered velocity-stress leapfrog:
+ * dt vp |s| <= 2 with |s_d| <= S/h_d, S = max |2 sum c_k sin((k - 1/2) theta)|. */
+double orc_elastic_dt_max(int so, const double h[3], double vpmax) {
+  double c[32];
+  if (orc_fd_weights_stag(so, c)) return -1.0;
+  double S = symbol_max(c, so / 2, 0.5);
+  double s2 = 0.0;
+  for (int d = 0; d < 3; ++d) s2 += (S / h[d]) * (S / h[d]);
+  return 2.0 / (vpmax * sqrt(s2));
+}
+
+/* init / out: NULL or [9][N] in the order vx, vy, vz (at n - 1/2), txx, tyy,
+ * tzz, txy, txz, tyz (at n); out holds v^{nt-1/2} and the stresses at nt. */
+int orc_elastic_forward(const orc_grid* g, const double* vp, const double* vs, const double* rho,
+                        const double* eta, int nsrc, const double* src_xyz, const double* src_wav,
+                        int nrec, const double* rec_xyz, double* traces, const double* init,
+                        double* out) {
+  ela_t E;
+  int st = ela_init(&E, g, vp, vs, rho, eta);
+  if (st) { ela_free(&E); return st; }
+  const pad_t* p = &E.p;
+  const int64_t N = p->n0 * p->n1 * p->n2;
+#ifdef _OPENMP
+  if (g->nthreads > 0) omp_set_num_threads(g->nthreads);
+#endif
+  int64_t* sb = (int64_t*)malloc(sizeof(int64_t) * 3 * (nsrc > 0 ? nsrc : 1));
+  double* sf = (double*)malloc(sizeof(double) * 3 * (nsrc > 0 ? nsrc : 1));
+  int64_t* rb = (int64_t*)malloc(sizeof(int64_t) * 3 * (nrec > 0 ? nrec : 1));
+  double* rf = (double*)malloc(sizeof(double) * 3 * (nrec > 0 ? nrec : 1));
+  double* buf = (double*)calloc((size_t)p->NP * 9, sizeof(double));
+  if (!sb || !sf || !rb || !rf || !buf) { st = ORC_ENOMEM; goto done; }
+  for (int s = 0; s < nsrc; ++s)
+    if (trilinear(g, src_xyz + 3 * s, sb + 3 * s, sf + 3 * s)) { st = ORC_EINVAL; goto done; }
+  for (int r = 0; r < nrec; ++r)
+    if (trilinear(g, rec_xyz + 3 * r, rb + 3 * r, rf + 3 * r)) { st = ORC_EINVAL; goto done; }
+  {
+    double* F[9];
+    for (int i = 0; i < 9; ++i) F[i] = buf + (size_t)i * p->NP;
+    if (init)
+      for (int i = 0; i < 9; ++i) to_padded(p, init + (size_t)i * N, F[i]);
+    const double dt = E.dt;
+    for (int n = 0; n < g->nt; ++n) {
+      if (E.periodic)
+        for (int i = ETXX; i <= ETYZ; ++i) wrap_halo(p, F[i]);
+      /* velocities: n - 1/2 -> n + 1/2 (reads stresses only) */
+#pragma omp parallel for schedule(static)
+      for (int64_t x = 0; x < p->n0; ++x)
+        for (int64_t y = 0; y < p->n1; ++y)
+          for (int64_t z = 0; z < p->n2; ++z) {
+            int64_t q = pidx(p, x, y, z), gq = gidx(p, x, y, z);
+            double damp = 1.0 + E.eta[gq] * dt;
+            double fx = ela_dp(&E, F[ETXX], q, 0) + ela_dm(&E, F[ETXY], q, 1) + ela_dm(&E, F[ETXZ], q, 2);
+            double fy = ela_dm(&E, F[ETXY], q, 0) + ela_dp(&E, F[ETYY], q, 1) + ela_dm(&E, F[ETYZ], q, 2);
+            double fz = ela_dm(&E, F[ETXZ], q, 0) + ela_dm(&E, F[ETYZ], q, 1) + ela_dp(&E, F[ETZZ], q, 2);
+            F[EVX][q] = (F[EVX][q] + dt * E.bx[gq] * fx) / damp;
+            F[EVY][q] = (F[EVY][q] + dt * E.by[gq] * fy) / damp;
+            F[EVZ][q] = (F[EVZ][q] + dt * E.bz[gq] * fz) / damp;
+          }
+      if (E.periodic)
+        for (int i = EVX; i <= EVZ; ++i) wrap_halo(p, F[i]);
+      /* stresses: n -> n + 1 (reads velocities only) */
+#pragma omp parallel for schedule(static)
+      for (int64_t x = 0; x < p->n0; ++x)
+        for (int64_t y = 0; y < p->n1; ++y)
+          for (int64_t z = 0; z < p->n2; ++z) {
+            int64_t q = pidx(p, x, y, z), gq = gidx(p, x, y, z);
+            double damp = 1.0 + E.eta[gq] * dt;
+            double exx = ela_dm(&E, F[EVX], q, 0), eyy = ela_dm(&E, F[EVY], q, 1),
+                   ezz = ela_dm(&E, F[EVZ], q, 2);
+            double lam = E.lam[gq], mu = E.mu[gq], tr = exx + eyy + ezz;
+            F[ETXX][q] = (F[ETXX][q] + dt * (lam * tr + 2.0 * mu * exx)) / damp;
+            F[ETYY][q] = (F[ETYY][q] + dt * (lam * tr + 2.0 * mu * eyy)) / damp;
+            F[ETZZ][q] = (F[ETZZ][q] + dt * (lam * tr + 2.0 * mu * ezz)) / damp;
+            F[ETXY][q] = (F[ETXY][q] + dt * E.mxy[gq] * (ela_dp(&E, F[EVX], q, 1) + ela_dp(&E, F[EVY], q, 0))) / damp;
+            F[ETXZ][q] = (F[ETXZ][q] + dt * E.mxz[gq] * (ela_dp(&E, F[EVX], q, 2) + ela_dp(&E, F[EVZ], q, 0))) / damp;
+            F[ETYZ][q] = (F[ETYZ][q] + dt * E.myz[gq] * (ela_dp(&E, F[EVY], q, 2) + ela_dp(&E, F[EVZ], q, 1))) / damp;
+          }
+      /* explosive source into the normal stresses */
+      for (int s = 0; s < nsrc; ++s) {
+        double qv = src_wav[(int64_t)s * g->nt + n];
+        for (int c = 0; c < 8; ++c) {
+          double w = corner_weight(sf + 3 * s, c);
+          if (w == 0.0) continue;
+          int64_t q = pidx(p, sb[3 * s] + ((c >> 2) & 1), sb[3 * s + 1] + ((c >> 1) & 1),
+                           sb[3 * s + 2] + (c & 1));
+          F[ETXX][q] += dt * w * qv;
+          F[ETYY][q] += dt * w * qv;
+          F[ETZZ][q] += dt * w * qv;
+        }
+      }
+      for (int r = 0; r < nrec; ++r) {
+        double acc = 0.0;
+        for (int c = 0; c < 8; ++c) {
+          double w = corner_weight(rf + 3 * r, c);
+          if (w == 0.0) continue;
+          int64_t q = pidx(p, rb[3 * r] + ((c >> 2) & 1), rb[3 * r + 1] + ((c >> 1) & 1),
+                           rb[3 * r + 2] + (c & 1));
+          acc += w * (F[ETXX][q] + F[ETYY][q] + F[ETZZ][q]) / 3.0;
+        }
+        traces[(int64_t)n * nrec + r] = acc;
+      }
+    }
+    if (out)
+      for (int i = 0; i < 9; ++i) from_padded(p, F[i], out + (size_t)i * N);
+  }
+done:
+  free(sb); free(sf); free(rb); free(rf); free(buf);
+  ela_free(&E);
+  return st;
+}
+
+/* Discrete energy of the undamped staggered scheme (vs > 0 everywhere):
+ *   E^n = 1/2 sum v^{n+1/2} . W v^{n-1/2} + 1/2 sum tau^n : S tau^n
+ * W = 1/b at each velocity position, S the compliance (inverse of the
+ * stress update's stiffness: normal block [[lam+2mu, lam, lam], ...], shear
+ * 1/mu_edge).  v_next, v_prev: [3][N]; tau: [6][N]. */
+double orc_elastic_energy(const orc_grid* g, const double* vp, const double* vs, const double* rho,
+                          const double* v_next, const double* v_prev, const double* tau) {
+  ela_t E;
+  orc_grid g2 = *g;
+  g2.nbl = 0;
+  if (ela_init(&E, &g2, vp, vs, rho, NULL)) { ela_free(&E); return NAN; }
+  const int64_t N = E.p.n0 * E.p.n1 * E.p.n2;
+  double kin = 0.0, pot = 0.0;
+  const double* b[3] = {E.bx, E.by, E.bz};
+  const double* ms[3] = {E.mxy, E.mxz, E.myz};
+  for (int64_t i = 0; i < N; ++i) {
+    for (int d = 0; d < 3; ++d) kin += v_next[d * N + i] * v_prev[d * N + i] / b[d][i];
+    double lam = E.lam[i], mu = E.mu[i];
+    double sxx = tau[i], syy = tau[N + i], szz = tau[2 * N + i];
+    double tr = sxx + syy + szz;
+    /* S sigma = (sigma - lam/(3 lam + 2 mu) tr I) / (2 mu) */
+    double k = lam / (3.0 * lam + 2.0 * mu);
+    pot += (sxx * sxx + syy * syy + szz * szz - k * tr * tr) / (2.0 * mu);
+    for (int d = 0; d < 3; ++d) {
+      double t = tau[(3 + d) * N + i];
+      if (t != 0.0 || ms[d][i] > 0.0) pot += t * t / ms[d][i];
+    }
+  }
+  ela_free(&E);
+  return 0.5 * (kin + pot);
 }

@@ -104,3 +104,91 @@ def forward(shape, h, so, dt, nt, vp, nbl, src, wav, rec):
             traces[n][k] = acc
         up, uc = uc, un
     return traces, uc, up
+
+
+# Centred first-derivative weights (c1..cr; antisymmetric) and staggered
+# first-derivative weights (c1..cr for nodes at +-(i - 1/2)), closed rationals.
+D1 = {
+    4: [F(2, 3), F(-1, 12)],
+    8: [F(4, 5), F(-1, 5), F(4, 105), F(-1, 280)],
+    12: [F(6, 7), F(-15, 56), F(5, 63), F(-1, 56), F(1, 385), F(-1, 5544)],
+}
+STAG = {
+    4: [F(9, 8), F(-1, 24)],
+    8: [F(1225, 1024), F(-245, 3072), F(49, 5120), F(-5, 7168)],
+}
+
+
+def _shift(u, axis, off):
+    """u[i + off] along `axis` with zeros outside the array (numpy)."""
+    import numpy as np
+    out = np.zeros_like(u)
+    n = u.shape[axis]
+    src = [slice(None)] * u.ndim
+    dst = [slice(None)] * u.ndim
+    if off >= 0:
+        src[axis] = slice(off, n)
+        dst[axis] = slice(0, n - off)
+    else:
+        src[axis] = slice(0, n + off)
+        dst[axis] = slice(-off, n)
+    out[tuple(dst)] = u[tuple(src)]
+    return out
+
+
+def dcentred(u, axis, so, h):
+    """Centred first derivative (zero outside the array)."""
+    acc = 0.0
+    for i, c in enumerate(D1[so], start=1):
+        acc = acc + float(c) * (_shift(u, axis, i) - _shift(u, axis, -i))
+    return acc / h
+
+
+def dstag_plus(u, axis, so, h):
+    """Node -> half-node staggered derivative: sum c_k (u[i+k] - u[i-k+1]) / h."""
+    acc = 0.0
+    for k, c in enumerate(STAG[so], start=1):
+        acc = acc + float(c) * (_shift(u, axis, k) - _shift(u, axis, -(k - 1)))
+    return acc / h
+
+
+def dstag_minus(u, axis, so, h):
+    """Half-node -> node staggered derivative: sum c_k (u[i+k-1] - u[i-k]) / h."""
+    acc = 0.0
+    for k, c in enumerate(STAG[so], start=1):
+        acc = acc + float(c) * (_shift(u, axis, k - 1) - _shift(u, axis, -k))
+    return acc / h
+
+
+def point_field(shape, h, pts, vals):
+    """Trilinear spreading of one value per point onto the grid (numpy)."""
+    import numpy as np
+    f = np.zeros(shape)
+    for pt, v in zip(pts, vals):
+        for idx, w in corners(pt, shape, h):
+            if w != 0.0:
+                f[idx] += w * v
+    return f
+
+
+def sample(u, shape, h, pts):
+    return [sum(w * u[idx] for idx, w in corners(pt, shape, h) if w != 0.0) for pt in pts]
+
+
+def acoustic_2nd_order(shape, h, dt, nt, vp, eta, lap, src, wav, rec, src_term):
+    """Leapfrog u^{n+1} = [dt^2 vp^2 ... ] with a caller's Laplacian (numpy).
+
+    ``src_term(n)`` returns the field added to u^{n+1} after the update.
+    Returns (traces [nt][nrec], u^nt)."""
+    import numpy as np
+    m = 1.0 / vp ** 2
+    a = eta * dt / 2.0
+    up = np.zeros(shape)
+    uc = np.zeros(shape)
+    tr = np.zeros((nt, len(rec)))
+    for n in range(nt):
+        un = (dt * dt * lap(uc) + m * (2.0 * uc - up) + a * up) / (m + a)
+        un = un + src_term(n)
+        tr[n] = sample(un, shape, h, rec)
+        up, uc = uc, un
+    return tr, uc

@@ -8,21 +8,27 @@
 // arithmetic); one more warp is the producer.
 //
 // Producer warp (asynchronous data movement, runs ahead of the compute):
-//   * u^n planes as (TY+2r) x (64+2rp) boxes with halo, by 3-D TMA, into a
-//     ring holding planes j-r .. j+r+PF (out-of-grid cells arrive as zeros:
-//     the zero boundary of Eq. 1);
-//   * the own tiles of u^{n-1} and c2 = dt^2/m, by TMA, into their rings;
-//   * signals when the neighbours hold the halo strips of a coming stream
-//     step (an acquire on their progress counters);
-//   * retires stream steps (an mbarrier the compute warps arrive on), frees
-//     their ring slots, and publishes the CTA's progress (release).
-// For fused steps k >= 1, the compute warps copy the neighbours' halo strips
-// of level n+k from a small L2-resident ring in global memory with 16-byte
-// cp.async one stream step ahead; the copies complete on the next step's
-// centre barrier, so nothing waits for them in the step that issues them.
-// Compute warps wait on mbarriers only; every wait is bounded by a timeout,
-// after which the CTA records an error and returns (the producer first
-// drains its own copies in flight).
+//   * per stream step j, one mbarrier covers three TMA loads: the u^n plane
+//     j+r as a (TY+2r) x (64+2rp) box with halo (out-of-grid cells arrive as
+//     zeros: the zero boundary of Eq. 1) and the own tiles of u^{n-1} and
+//     c2 = dt^2/m at plane j, each into its ring of planes;
+//   * retires stream steps (an mbarrier the compute warps arrive on) and
+//     frees their ring slots.
+// Halo warp (blocked sweeps, T > 1): for fused steps k >= 1 it copies the
+// neighbours' halo strips of level n+k from a small L2-resident ring in
+// global memory into a coming stream step's shared planes (bulk TMA copies,
+// one per strip row), once the neighbours' progress counters (polled by
+// four lanes at once) show the strips are written: the top and bottom
+// strips with one bulk TMA copy each, completing on that step's centre
+// barrier, the left and right columns with 16-byte L2 loads and shared
+// stores; then the warp's one arrival on the centre barrier.
+// Publisher warp (T > 1): publishes each retired step in the CTA's progress
+// counter (a release store, whose fence can take microseconds: it is kept
+// off the producer's and the halo warp's paths).
+// Compute warps wait on two mbarriers per stream step (the step's data and
+// the centre/halo planes); every wait is bounded by a timeout, after which
+// the CTA records an error and returns (helper warps first drain their own
+// copies in flight).
 //
 // Temporal blocking (Sec. II-B, re-designed for the GPU).  Fused step k
 // (k = 0..T-1) computes level n+k+1 at plane q_k = j - k r of stream step
@@ -61,7 +67,8 @@ template <int R, int T, int TY>
 struct SweepCfg {
   static constexpr int TZ = 64;
   static constexpr int NT = 32 * TY;           // compute threads
-  static constexpr int NTHREADS = NT + 32;     // + producer warp
+  static constexpr bool HALO = T > 1;          // halo and publisher warps present
+  static constexpr int NTHREADS = NT + 32 + (HALO ? 64 : 0);  // + producer (+ halo, publisher)
   static constexpr int RP = (R + 3) / 4 * 4;   // axis-2 halo width in shared memory
   static constexpr int SW = TZ + 2 * RP;       // plane row stride (floats)
   static constexpr int SH = TY + 2 * R;
@@ -78,12 +85,22 @@ struct SweepCfg {
   static constexpr int ULAG = X0Q ? 0 : R;           // plane p is last read at step p + ULAG
   static constexpr int NP = PF + 1;                  // u^{n-1} tile ring
   static constexpr int NC = (T - 1) * R + 1 + PF;    // c2 tile ring
+  static constexpr int ND = PF + 2;                  // per-step data barriers
+  // the data of stream step s may be loaded once step s - LEAD is retired
+  static constexpr int LEAD = PF + 1;
+  static_assert(NU - R - ULAG >= LEAD && NP >= LEAD && NC - (T - 1) * R >= LEAD && ND >= LEAD,
+                "ring depths must cover the prefetch distance");
   static constexpr int NDONE = 8;                    // step-retirement barriers
-  static constexpr int NNBR = 8;                     // neighbour-readiness barriers
   static constexpr int D = 2 * R + 2;                // halo ring slots per fused step (global)
-  static constexpr int STRIP = 2 * R * TZ + 2 * TY * RP;
+  // halo strips of one tile and fused step in the global ring: the top and
+  // bottom R rows with the plane's row pitch SW (so that each lands in
+  // shared memory with one contiguous copy), then the left and right RP
+  // columns of the TY rows
+  static constexpr int STRIP_Y = R * SW;
+  static constexpr int STRIP = 2 * STRIP_Y + 2 * TY * RP;
   static constexpr int RING_PER_CTA = T > 1 ? (T - 1) * D * STRIP : 0;
   static constexpr int NSP = T > 1 ? 2 * (T - 1) : 0;  // fused-step planes
+  static constexpr int CTR_COUNT = NT + (HALO ? 1 : 0);   // arrivals per centre phase
   static constexpr size_t OFF_U = 0;
   static constexpr size_t OFF_P = OFF_U + align128((size_t)NU * PSLOT * 4);
   static constexpr size_t OFF_C = OFF_P + align128((size_t)NP * TILE * 4);
@@ -93,7 +110,7 @@ struct SweepCfg {
   static constexpr size_t OFF_CUR = OFF_CNT + 2 * 2 * 2 * NT;
   static constexpr size_t OFF_XF = OFF_CUR + 2 * 2 * T * 2 * NT;  // receiver columns' first x
   static constexpr size_t OFF_BAR = align128(OFF_XF + 2 * 2 * NT);
-  static constexpr int NBAR = NU + NP + NC + NNBR + 2 + NDONE;  // u, p, c, nbr, centre[2], done
+  static constexpr int NBAR = 1 + ND + 2 + NDONE;    // prologue, data, centre[2], done
   static constexpr size_t SMEM = OFF_BAR + 8 * NBAR + 128;    // + base alignment
   static_assert(R % 2 == 0, "radius must be even for aligned float2 access");
   static_assert(TY >= R && TZ >= RP, "a halo must come from one neighbour tile");
@@ -112,6 +129,14 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ void st_release_cta_s32(int* p, int v) {
+  asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_cta_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -123,6 +148,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+// raise the phase's expected transaction bytes without arriving
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -206,6 +235,8 @@ __device__ __forceinline__ bool bounded_wait_ge(const unsigned long long* flag,
   return true;
 }
 
+__device__ __forceinline__ int j_mod(int j, int d) { return j % d; }
+
 // ------------------------------------------------------------ arithmetic --
 // Eq. 1 at one point: u^{n+1} = [dt^2 L u + m(2u - u_prev) + a u_prev]/(m + a)
 // rewritten with c2 = dt^2/m and g = a/m = (eta/(2 dt)) c2 as an increment:
@@ -239,7 +270,7 @@ __device__ __forceinline__ float2 pair_term2(float2 acc, float2 w2, float2 a, fl
 
 // ----------------------------------------------------------------- kernel --
 template <int R, int T, int TY>
-__global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
+__global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
     sweep_kernel(const __grid_constant__ SweepParams P) {
   using C = SweepCfg<R, T, TY>;
   constexpr int TZ = C::TZ, NT = C::NT, SW = C::SW, RP = C::RP;
@@ -250,13 +281,10 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
   float* pring = reinterpret_cast<float*>(smem + C::OFF_P);
   float* cring = reinterpret_cast<float*>(smem + C::OFF_C);
   float* splane = reinterpret_cast<float*>(smem + C::OFF_S);
-  uint64_t* bar_u = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
-  uint64_t* bar_p = bar_u + C::NU;
-  uint64_t* bar_c = bar_p + C::NP;
-  uint64_t* bar_nbr = bar_c + C::NC;      // [NNBR] neighbours hold the strips of stream step j
-  uint64_t* bar_ctr = bar_nbr + C::NNBR;  // [2] centres and halos of stream step j in buffer j & 1
+  uint64_t* bar_pro = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);  // u^n planes before the first step
+  uint64_t* bar_dat = bar_pro + 1;     // [ND] data of stream step j
+  uint64_t* bar_ctr = bar_dat + C::ND; // [2] centres and halos of stream step j in buffer j & 1
   uint64_t* bar_done = bar_ctr + 2;    // [NDONE] compute warps finished a stream step
-  __shared__ int s_abort;
 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int b = blockIdx.x;
@@ -270,12 +298,14 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
   const int jend = pd.xo1 - 1 + (T - 1) * R;  // inclusive
   const int pu0 = jstart - C::ULAG;           // first u^n plane in the ring
   const long long tmo = P.timeout_ns;
+  __shared__ int s_ret;  // last stream step retired (written by the producer)
 
   if (tid == 0) {
-    s_abort = 0;
-    for (int i = 0; i < C::NU + C::NP + C::NC + C::NNBR; ++i) mbar_init(bar_u + i, 1);
-    mbar_init(bar_ctr + 0, NT);
-    mbar_init(bar_ctr + 1, NT);
+    s_ret = jstart - 1;
+    mbar_init(bar_pro, 1);
+    for (int i = 0; i < C::ND; ++i) mbar_init(bar_dat + i, 1);
+    mbar_init(bar_ctr + 0, C::CTR_COUNT);
+    mbar_init(bar_ctr + 1, C::CTR_COUNT);
     for (int i = 0; i < C::NDONE; ++i) mbar_init(bar_done + i, NT);  // every compute thread arrives
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -292,86 +322,185 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
 
   if (w == TY) {
     // =========================== producer warp ===========================
-    // neighbours hold the strips of stream step jn (produced at step jn - r)
-    auto halo_ready = [&](int jn) -> bool {
-      if (jn - R < jstart) return true;
-      const unsigned long long target = P.prog_base + (unsigned long long)(jn - R - jstart + 1);
-      bool ok = true;
-      if (nb_up >= 0) ok &= ld_acquire_u64(&P.progress[nb_up]) >= target;
-      if (nb_dn >= 0) ok &= ld_acquire_u64(&P.progress[nb_dn]) >= target;
-      if (nb_lf >= 0) ok &= ld_acquire_u64(&P.progress[nb_lf]) >= target;
-      if (nb_rt >= 0) ok &= ld_acquire_u64(&P.progress[nb_rt]) >= target;
-      return ok;
+    if (lane != 0) return;
+    auto u_slot = [&](int p) { return uring + ((p - pu0) % C::NU) * C::PSLOT; };
+    // u^n planes pu0 .. jstart+R-1, needed before the first step
+    {
+      const int np = jstart + R - pu0;
+      mbar_expect_tx(bar_pro, (unsigned)(np * C::PLANE * 4));
+      for (int p = pu0; p < jstart + R; ++p) tma_load_3d(u_slot(p), &P.tm_u, bar_pro, z0 - RP, y0 - R, p);
+    }
+    // the data of stream step s: u^n plane s+R, u^{n-1} and c2 plane s
+    auto issue = [&](int s) {
+      uint64_t* bar = bar_dat + (s - jstart) % C::ND;
+      mbar_expect_tx(bar, (unsigned)((C::PLANE + 2 * C::TILE) * 4));
+      tma_load_3d(u_slot(s + R), &P.tm_u, bar, z0 - RP, y0 - R, s + R);
+      tma_load_3d(pring + ((s - jstart) % C::NP) * C::TILE, &P.tm_p, bar, z0, y0, s);
+      tma_load_3d(cring + ((s - jstart) % C::NC) * C::TILE, &P.tm_c, bar, z0, y0, s);
     };
-    auto issue_u = [&](int p) {
-      const int s = (p - pu0) % C::NU;
-      mbar_expect_tx(bar_u + s, C::PLANE * 4);
-      tma_load_3d(uring + s * C::PSLOT, &P.tm_u, bar_u + s, z0 - RP, y0 - R, p);
-    };
-    auto issue_p = [&](int p) {
-      const int s = (p - jstart) % C::NP;
-      mbar_expect_tx(bar_p + s, C::TILE * 4);
-      tma_load_3d(pring + s * C::TILE, &P.tm_p, bar_p + s, z0, y0, p);
-    };
-    auto issue_c = [&](int p) {
-      const int s = (p - jstart) % C::NC;
-      mbar_expect_tx(bar_c + s, C::TILE * 4);
-      tma_load_3d(cring + s * C::TILE, &P.tm_c, bar_c + s, z0, y0, p);
-    };
-    // single-lane producer: TMA issue, neighbour readiness, step retirement
-    int nu = pu0, np = jstart, nc = jstart, nh = jstart, ret = jstart - 1;
+    int ns = jstart, ret = jstart - 1;
     bool ok = true;
-    if (lane == 0) {
-      while (ret < jend && ok) {
-        while (nu <= jend + R && (nu - C::NU < pu0 || nu - C::NU + C::ULAG <= ret)) issue_u(nu++);
-        while (np <= jend && (np - C::NP < jstart || np - C::NP <= ret)) issue_p(np++);
-        while (nc <= jend && (nc - C::NC < jstart || nc - C::NC + (T - 1) * R <= ret)) issue_c(nc++);
-        if constexpr (T > 1) {
-          // tell the compute warps when the neighbours' strips of stream
-          // step nh may be copied (they copy them during step nh - 1); up to
-          // NNBR - 2 steps ahead of the last retired one
-          while (nh <= jend && nh - (C::NNBR - 2) <= ret) {
-            if (!halo_ready(nh)) {
-              if (nh != ret + 2) break;  // not needed yet: retire a step first
-              const unsigned long long t0 = global_ns();
-              while (!halo_ready(nh))
-                if ((long long)(global_ns() - t0) > tmo) {
-                  atomicExch(P.err, 1);
-                  ok = false;
-                  break;
-                }
-              if (!ok) break;
-            }
-            mbar_arrive(bar_nbr + (nh - jstart) % C::NNBR);
-            ++nh;
-          }
-          if (!ok) break;
-        }
-        // retire the next stream step (polled with a short back-off so the
-        // refills above go out as soon as a step is done)
-        const int s = ret + 1;
-        if (!mbar_poll(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo)) {
-          atomicExch(P.err, 2);
-          ok = false;
-          break;
-        }
-        ret = s;
-        if constexpr (T > 1) {
-          // release: cumulative over the compute warps' strip stores, which
-          // happen before their arrival on the step's mbarrier
-          st_release_u64(&P.progress[b], P.prog_base + (unsigned long long)(ret - jstart + 1));
-        }
+    while (ret < jend) {
+      while (ns <= jend && ns - C::LEAD <= ret) issue(ns++);
+      // retire the next stream step (polled with a short back-off so the
+      // refills above go out as soon as a step is done)
+      const int s = ret + 1;
+      if (!mbar_poll(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo)) {
+        atomicExch(P.err, 2);
+        ok = false;
+        break;
       }
-      if (!ok) s_abort = 1;
-      // drain: wait (bounded) for every load this thread issued
-      for (int p = max(pu0, nu - C::NU); p < nu; ++p)
-        mbar_wait(bar_u + (p - pu0) % C::NU, ((p - pu0) / C::NU) & 1, tmo);
-      for (int p = max(jstart, np - C::NP); p < np; ++p)
-        mbar_wait(bar_p + (p - jstart) % C::NP, ((p - jstart) / C::NP) & 1, tmo);
-      for (int p = max(jstart, nc - C::NC); p < nc; ++p)
-        mbar_wait(bar_c + (p - jstart) % C::NC, ((p - jstart) / C::NC) & 1, tmo);
+      ret = s;
+      if constexpr (T > 1) st_release_cta_s32(&s_ret, ret);  // for the publisher
+    }
+    // drain: wait (bounded) for every load this thread issued; after a full
+    // run the compute warps consumed them all
+    if (!ok) {
+      mbar_wait(bar_pro, 0, tmo);
+      for (int s = max(jstart, ns - C::ND); s < ns; ++s)
+        mbar_wait(bar_dat + (s - jstart) % C::ND, ((s - jstart) / C::ND) & 1, tmo);
     }
     return;
+  }
+
+  if constexpr (C::HALO) {
+    if (w == TY + 2) {
+      // =========================== publisher warp ===========================
+      // publishes the producer's latest retired step (it may skip steps
+      // while a release is in flight: the counter is monotonic)
+      if (lane != 0) return;
+      int pub = jstart - 1;
+      unsigned long long t0 = global_ns();
+      while (pub < jend) {
+        const int r = ld_acquire_cta_s32(&s_ret);
+        if (r > pub) {
+          // release: cumulative over the compute warps' strip stores, which
+          // happen before their arrival on the step's mbarrier, which the
+          // producer observed before it wrote s_ret
+          st_release_u64(&P.progress[b], P.prog_base + (unsigned long long)(r - jstart + 1));
+          pub = r;
+          t0 = global_ns();
+        } else {
+          if ((long long)(global_ns() - t0) > tmo) {
+            atomicExch(P.err, 2);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      return;
+    }
+    if (w == TY + 1) {
+      // ============================= halo warp =============================
+      // progress of neighbour `lane` (lanes 0..3: up, down, left, right)
+      const int nb = lane == 0 ? nb_up : lane == 1 ? nb_dn : lane == 2 ? nb_lf : lane == 3 ? nb_rt : -1;
+      unsigned long long seen = 0;
+      constexpr unsigned BYTES_Y = C::STRIP_Y * 4;  // one top or bottom strip
+      constexpr int CH_Z = TY * (RP / 4);           // 16-byte chunks per side strip
+      const size_t tile_stride = (size_t)(T - 1) * C::D * C::STRIP;
+      const unsigned bytes_k = (nb_up >= 0 ? BYTES_Y : 0) + (nb_dn >= 0 ? BYTES_Y : 0);
+      bool ok = true;
+      int last = jstart;  // last step whose copies were issued
+      for (int jn = jstart + 1; jn <= jend && ok; ++jn) {
+        // the strips of step jn are written by the neighbours' step jn - R
+        if (jn - R >= jstart) {
+          const unsigned long long target = P.prog_base + (unsigned long long)(jn - R - jstart + 1);
+          const unsigned long long t0 = global_ns();
+          while (true) {
+            if (nb >= 0 && seen < target) seen = ld_acquire_u64(&P.progress[nb]);
+            if (__all_sync(0xffffffffu, nb < 0 || seen >= target)) break;
+            if (__any_sync(0xffffffffu, (long long)(global_ns() - t0) > tmo)) {  // warp-uniform
+              ok = false;
+              break;
+            }
+            __nanosleep(32);
+          }
+          if (!ok) {
+            atomicExch(P.err, 1);
+            break;
+          }
+        }
+        // buffer jn & 1 was last read during step jn - 2
+        if (jn - 2 >= jstart) {
+          const int s = jn - 2;
+          ok = __all_sync(0xffffffffu,
+                          mbar_wait(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo));
+          if (!ok) {
+            atomicExch(P.err, 2);
+            break;
+          }
+        }
+        // the acquiring lanes' observations precede every lane's reads; the
+        // bulk copies read through the async proxy
+        __syncwarp();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        uint64_t* bar = bar_ctr + (jn & 1);
+        float* buf = splane + (size_t)(jn & 1) * (T - 1) * C::PSLOT;
+        if (lane == 0) {
+          unsigned bytes = 0;
+          for (int k = 1; k < T; ++k) {
+            const int q = jn - k * R;
+            if (q >= pd.xc0 && q < pd.xc1) bytes += bytes_k;
+          }
+          mbar_expect_tx_only(bar, bytes);
+        }
+        __syncwarp();
+        // top / bottom strips: one bulk copy each per fused step
+        if (lane < 2 * (T - 1)) {
+          const int k = 1 + (lane >> 1);
+          const int q = jn - k * R;
+          const int nbv = (lane & 1) ? nb_dn : nb_up;
+          if (q >= pd.xc0 && q < pd.xc1 && nbv >= 0) {
+            float* pl = buf + (k - 1) * C::PSLOT;
+            const float* src = P.ring + (size_t)nbv * tile_stride + (size_t)(k - 1) * C::D * C::STRIP +
+                               (size_t)(q % C::D) * C::STRIP;
+            if (lane & 1)  // bottom halo rows: the lower neighbour's top strip
+              bulk_load(pl + (TY + R) * SW, src, BYTES_Y, bar);
+            else  // top halo rows: the upper neighbour's bottom strip
+              bulk_load(pl, src + C::STRIP_Y, BYTES_Y, bar);
+          }
+        }
+        // left / right columns: 16-byte L2 loads (issued together), then stores
+        constexpr int NZ = (T - 1) * 2 * CH_Z;
+        constexpr int PER = (NZ + 31) / 32;
+        float4 v[PER];
+        float* dst[PER];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+          const int e = lane + 32 * i;
+          dst[i] = nullptr;
+          if (e < NZ) {
+            const int k = 1 + e / (2 * CH_Z), r = e - (k - 1) * 2 * CH_Z;
+            const int q = jn - k * R;
+            const bool left = r < CH_Z;
+            const int rr = left ? r : r - CH_Z, row = rr / (RP / 4), c4 = 4 * (rr - row * (RP / 4));
+            const int nbv = left ? nb_lf : nb_rt;
+            if (q >= pd.xc0 && q < pd.xc1 && nbv >= 0) {
+              float* pl = buf + (k - 1) * C::PSLOT;
+              const float* src = P.ring + (size_t)nbv * tile_stride + (size_t)(k - 1) * C::D * C::STRIP +
+                                 (size_t)(q % C::D) * C::STRIP + 2 * C::STRIP_Y;
+              // left halo: the left neighbour's right strip; right: the right one's left strip
+              src += (left ? TY * RP : 0) + row * RP + c4;
+              dst[i] = pl + (R + row) * SW + (left ? 0 : RP + TZ) + c4;
+              v[i] = __ldcg(reinterpret_cast<const float4*>(src));
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < PER; ++i)
+          if (dst[i]) *reinterpret_cast<float4*>(dst[i]) = v[i];
+        __syncwarp();  // every lane's stores precede lane 0's arrival
+        if (lane == 0) mbar_arrive(bar);
+        last = jn;
+      }
+      if (!ok) {
+        // copies of the last two issued steps may be in flight: they complete
+        // on the centre phases; wait for those (bounded) before exiting
+        for (int jn = max(jstart + 1, last - 1); jn <= last; ++jn)
+          mbar_wait(bar_ctr + (jn & 1), ((jn - jstart - 1) >> 1) & 1, tmo);
+      }
+      return;
+    }
   }
 
   // ============================== compute warps ==============================
@@ -387,6 +516,11 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
   unsigned short* ccnt = reinterpret_cast<unsigned short*>(smem + C::OFF_CNT);  // [kind][col][NT]
   unsigned short* ccur = reinterpret_cast<unsigned short*>(smem + C::OFF_CUR);  // [kind][T][col][NT]
   unsigned short* cxf = reinterpret_cast<unsigned short*>(smem + C::OFF_XF);    // [col][NT]
+  // this thread's place in the halo strips it publishes (-1: none)
+  const int strip_y = w < R ? w * SW + RP + 2 * lane
+                            : (w >= TY - R ? (R + w - (TY - R)) * SW + RP + 2 * lane : -1);
+  const int strip_z = 2 * lane < RP ? 2 * C::STRIP_Y + w * RP + 2 * lane
+                                    : (2 * lane >= TZ - RP ? 2 * C::STRIP_Y + TY * RP + w * RP + 2 * lane - (TZ - RP) : -1);
 
   float2 byz = make_float2(0.f, 0.f);
   if (v0) byz.x = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z]));
@@ -451,10 +585,7 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
     bxn = __ldg(&P.damp_b[min(max(q, 0), P.n0 - 1)]);
   }
 
-  bool ok = true;
-  // u^n planes pu0 .. jstart+R-1 must be in place before the first step
-  for (int p = pu0; p < jstart + R && ok; ++p)
-    ok = mbar_wait(bar_u + (p - pu0) % C::NU, ((p - pu0) / C::NU) & 1, tmo);
+  bool ok = mbar_wait(bar_pro, 0, tmo);  // u^n planes pu0 .. jstart+R-1
 
   // sparse operators of fused step k at plane q on this thread's column pair
   auto sparse = [&](int k, int q, float2& un) {
@@ -515,6 +646,7 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
 
   int su = (jstart - pu0) % C::NU;  // ring slot of u^n plane j
   int sp = 0, sc = 0;               // ring slots of u^{n-1}, c2 plane j
+  int jd = j_mod(jstart, C::D);     // j mod D (halo ring slot of plane j)
 #pragma unroll 1
   for (int j = jstart; j <= jend && ok; ++j) {
     const bool act0 = j >= pd.xc0 && j < pd.xc1;
@@ -522,13 +654,11 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
     bxn = __ldg(&P.damp_b[min(max(j + 1 - kl * R, 0), P.n0 - 1)]);
     int suR = su + R;
     suR -= suR >= C::NU ? C::NU : 0;
-    ok = mbar_wait(bar_u + suR, ((j + R - pu0) / C::NU) & 1, tmo);
-    if (act0 && ok) {
-      ok = mbar_wait(bar_p + sp, ((j - jstart) / C::NP) & 1, tmo);
-      ok = ok && mbar_wait(bar_c + sc, ((j - jstart) / C::NC) & 1, tmo);
-    }
+    // u^n plane j+R, u^{n-1} and c2 plane j
+    ok = mbar_wait(bar_dat + (j - jstart) % C::ND, ((j - jstart) / C::ND) & 1, tmo);
     if constexpr (T > 1) {
-      // centres and halo strips of this step, staged during the previous one
+      // centres and halo strips of this step, staged during the previous one;
+      // the phase also means every compute thread finished step j-1
       if (j > jstart) ok = ok && mbar_wait(bar_ctr + (j & 1), ((j - jstart - 1) >> 1) & 1, tmo);
     }
     if (!ok) break;
@@ -581,60 +711,16 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
       const float2 lap = __fadd2_rn(__fadd2_rn(lx, ly), lz);
       const float bx = __shfl_sync(0xffffffffu, bxc, 0);
       un0 = point_update2(uc0, up, lap, c2v, __fadd2_rn(make_float2(bx, bx), byz));
-      sparse(0, j, un0);
+      if (flags) sparse(0, j, un0);
     }
 
     if constexpr (T == 1) {
       if (act0 && own_row && j >= pd.xo0 && j < pd.xo1 && v0)
         __stcs(reinterpret_cast<float2*>(P.out0 + (size_t)j * ps + coff), un0);
     } else {
-      // fused steps k >= 1 stage the next step's plane in buffer (j+1) & 1,
-      // which the whole CTA read during step j-1: wait until it is retired
-      if (j > jstart) {
-        const int s = j - 1;
-        ok = mbar_wait(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo);
-        if (!ok) break;
-      }
-      if (j < jend) {
-        // the neighbours' strips of step j+1: 16-byte copies, one or two per
-        // thread, completing on the step's centre barrier
-        const int jn = j + 1;
-        ok = mbar_wait(bar_nbr + (jn - jstart) % C::NNBR, ((jn - jstart) / C::NNBR) & 1, tmo);
-        if (!ok) break;
-        constexpr int CH_ROW = TZ / 4;           // 16-byte chunks per strip row
-        constexpr int CH_Y = 2 * R * CH_ROW;     // top + bottom strips
-        constexpr int CH_Z = 2 * TY * (RP / 4);  // left + right strips
-        constexpr int CH = CH_Y + CH_Z;
-        float* buf = splane + (size_t)(jn & 1) * (T - 1) * C::PSLOT;
-        for (int e = tid; e < (T - 1) * CH; e += NT) {
-          const int k = 1 + e / CH, r = e - (k - 1) * CH;
-          const int q = jn - k * R;
-          if (q < pd.xc0 || q >= pd.xc1) continue;
-          float* pl = buf + (k - 1) * C::PSLOT;
-          const float* ring_k = P.ring + (size_t)(k - 1) * C::D * C::STRIP + (size_t)(q % C::D) * C::STRIP;
-          const size_t tile_stride = (size_t)(T - 1) * C::D * C::STRIP;
-          if (r < CH_Y) {
-            const int hr = r / CH_ROW, c4 = 4 * (r - hr * CH_ROW);
-            if (hr < R) {
-              if (nb_up >= 0) cp_async16(pl + hr * SW + RP + c4, ring_k + nb_up * tile_stride + (R + hr) * TZ + c4);
-            } else if (nb_dn >= 0) {
-              cp_async16(pl + (TY + hr) * SW + RP + c4, ring_k + nb_dn * tile_stride + (hr - R) * TZ + c4);
-            }
-          } else {
-            const int r2 = r - CH_Y, row = r2 / (RP / 2), cc = r2 - row * (RP / 2);
-            const bool left = cc < RP / 4;
-            const int c4 = 4 * (left ? cc : cc - RP / 4);
-            if (left) {
-              if (nb_lf >= 0)
-                cp_async16(pl + (R + row) * SW + c4, ring_k + nb_lf * tile_stride + 2 * R * TZ + TY * RP + row * RP + c4);
-            } else if (nb_rt >= 0) {
-              cp_async16(pl + (R + row) * SW + RP + TZ + c4, ring_k + nb_rt * tile_stride + 2 * R * TZ + row * RP + c4);
-            }
-          }
-        }
-      }
-      cp_async_mbar_arrive(bar_ctr + ((j + 1) & 1));
       float* rs_base = P.ring + (size_t)b * (T - 1) * C::D * C::STRIP;
+      const float* rdbuf = splane + (size_t)(j & 1) * (T - 1) * C::PSLOT;
+      float* wrbuf = splane + (size_t)((j + 1) & 1) * (T - 1) * C::PSLOT;
       float2 un = un0;
       bool act = act0;
 #pragma unroll
@@ -644,7 +730,7 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
           act = q >= pd.xc0 && q < pd.xc1;
           un = make_float2(0.f, 0.f);
           if (act) {
-            const float* pl = splane + ((size_t)(j & 1) * (T - 1) + (k - 1)) * C::PSLOT;
+            const float* pl = rdbuf + (k - 1) * C::PSLOT;
             // u_prev of step k: level n+k-1 at plane q
             float2 upv;
             if (k == 1) {
@@ -682,7 +768,7 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
             const float2 lap = __fadd2_rn(__fadd2_rn(lx, ly), lz);
             const float bx = __shfl_sync(0xffffffffu, bxc, k);
             un = point_update2(uc, upv, lap, c2v, __fadd2_rn(make_float2(bx, bx), byz));
-            sparse(k, q, un);
+            if (flags) sparse(k, q, un);
           }
         }
         if (k + 1 < T) {
@@ -694,16 +780,14 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
           // ... stage its centre for the next stream step ...
           const int qn = j + 1 - (k + 1) * R;
           if (qn >= pd.xc0 && qn < pd.xc1)
-            *reinterpret_cast<float2*>(splane + ((size_t)((j + 1) & 1) * (T - 1) + k) * C::PSLOT + own) =
-                Qs[kq][R + 1];
+            *reinterpret_cast<float2*>(wrbuf + (size_t)k * C::PSLOT + own) = Qs[kq][R + 1];
           // ... and publish its halo strips for the neighbours
-          if (act) {
-            float* rs = rs_base + ((size_t)k * C::D + (q % C::D)) * C::STRIP;
-            if (w < R) __stcg(reinterpret_cast<float2*>(rs + w * TZ + 2 * lane), un);
-            if (w >= TY - R) __stcg(reinterpret_cast<float2*>(rs + (R + w - (TY - R)) * TZ + 2 * lane), un);
-            if (2 * lane < RP) __stcg(reinterpret_cast<float2*>(rs + 2 * R * TZ + w * RP + 2 * lane), un);
-            if (2 * lane >= TZ - RP)
-              __stcg(reinterpret_cast<float2*>(rs + 2 * R * TZ + TY * RP + w * RP + 2 * lane - (TZ - RP)), un);
+          if (act && (strip_y >= 0 || strip_z >= 0)) {
+            int qd = jd - (k * R) % C::D;
+            qd += qd < 0 ? C::D : 0;
+            float* rs = rs_base + ((size_t)k * C::D + qd) * C::STRIP;
+            if (strip_y >= 0) __stcg(reinterpret_cast<float2*>(rs + strip_y), un);
+            if (strip_z >= 0) __stcg(reinterpret_cast<float2*>(rs + strip_z), un);
           }
         } else if (act && own_row && q >= pd.xo0 && q < pd.xo1 && v0) {
           __stcs(reinterpret_cast<float2*>(P.out0 + (size_t)q * ps + coff), un);
@@ -717,11 +801,9 @@ __global__ void __launch_bounds__(32 * TY + 32, T == 1 ? 2 : 1)
     su = su + 1 == C::NU ? 0 : su + 1;
     sp = sp + 1 == C::NP ? 0 : sp + 1;
     sc = sc + 1 == C::NC ? 0 : sc + 1;
+    jd = jd + 1 == C::D ? 0 : jd + 1;
   }
-  if (!ok) {
-    atomicExch(P.err, 2);
-    s_abort = 1;
-  }
+  if (!ok) atomicExch(P.err, 2);
 }
 
 template <int R, int T>

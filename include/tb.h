@@ -13,6 +13,20 @@
  * iteration space), which lets the propagator fuse several time steps into
  * one temporally blocked sweep (Sec. II-B).
  *
+ * The two other wave equations of Sec. III are propagated one step per
+ * launch with the same grid-aligned sources and receivers:
+ *   TB_TTI (Sec. III-B, Eq. 2): pseudo-acoustic tilted transversely
+ *     isotropic medium, fields p and r, 2nd order in time:
+ *       m p_tt = (1 + 2 eps) H_h p + sqrt(1 + 2 delta) H_z r
+ *       m r_tt = sqrt(1 + 2 delta) H_h p + H_z r
+ *     H_z = -D_zbar^T D_zbar, H_h = -(D_xbar^T D_xbar + D_ybar^T D_ybar) with
+ *     Eq. 2's rotated first derivatives (centred, order so); sources enter p
+ *     and r (dt^2/m scaling), receivers sample p.
+ *   TB_ELASTIC (Sec. III-C, Eq. 3): isotropic velocity-stress on the
+ *     staggered grid (staggered first derivatives of order so); explosive
+ *     sources add dt q to the three normal stresses, receivers sample their
+ *     mean.
+ *
  * Conventions for every call:
  *   - Grid shape n[3] with axis 2 contiguous (the paper's u[t][x][y][z] with
  *     z innermost).  A "field" argument is a dense float array [n0][n1][n2].
@@ -52,7 +66,7 @@ typedef enum {
   TB_ESTATE = 7      /* call order violated (e.g. forward before set_model) */
 } tb_status;
 
-enum { TB_ACOUSTIC = 0 };
+enum { TB_ACOUSTIC = 0, TB_TTI = 1, TB_ELASTIC = 2 };
 enum { TB_ONESTEP = 0, TB_BLOCKED = 1 };
 
 typedef struct tb_handle tb_handle;
@@ -62,7 +76,7 @@ typedef struct tb_handle tb_handle;
 typedef struct {
   int time_tile;   /* T: time steps fused per blocked sweep (Sec. II-B).
                       Supported: 1..4 (space order 4, 8), 1..2 (space order 12);
-                      0 -> the largest supported.                               */
+                      0 -> the largest supported.  TB_TTI, TB_ELASTIC: 0 or 1.  */
   int nbl;         /* width in cells of the built-in sponge (Sec. IV-B); 0: none  */
   int y_bands;     /* blocked sweep: number of bands along axis 1; 0 -> fewest
                       bands whose tiles are co-resident on the GPU                */
@@ -77,10 +91,11 @@ typedef struct {
 } tb_options;
 
 /* Create a propagator for a grid of shape n[3] with spacing h[3] (metres),
- * space order 4, 8 or 12 (Sec. IV: "space orders of 4, 8, 12").  Requires
- * n_d >= space_order + 2 on every axis.  `opt` may be NULL (defaults).
- * Allocates the wavefields (4 x n0 n1 n2 floats) and the model buffer on the
- * current CUDA device.  Errors: TB_EINVAL, TB_ENOMEM, TB_ECUDA. */
+ * space order 4, 8 or 12 (the space orders of Sec. IV) and physics
+ * TB_ACOUSTIC, TB_TTI or TB_ELASTIC.  Requires n_d >= space_order + 2 on
+ * every axis.  `opt` may be NULL (defaults).  Allocates the wavefields and
+ * model buffers on the current CUDA device (acoustic: 5 x n0 n1 n2 floats;
+ * TTI: 16; elastic: 18).  Errors: TB_EINVAL, TB_ENOMEM, TB_ECUDA. */
 int tb_create(const int64_t n[3], const double h[3], int space_order, int physics,
               const tb_options* opt, tb_handle** out);
 
@@ -88,12 +103,16 @@ int tb_create(const int64_t n[3], const double h[3], int space_order, int physic
 int tb_destroy(tb_handle* h);
 
 /* Set the velocity model (Eq. 1: m = 1/vp^2).  vp: field of P velocities in
- * m/s, all > 0.  aux: must be NULL (the acoustic physics has no further
- * parameters).  damp: NULL for the built-in sponge of opt.nbl cells, or
+ * m/s, all > 0.  aux: further per-point parameters, fields stacked [k][n0]
+ * [n1][n2]: acoustic: NULL; TTI: k = 4: eps, delta (Thomsen parameters,
+ * eps >= delta > -1/2, else TB_EUNSTABLE), theta (tilt), phi (azimuth) in
+ * radians (Eq. 2); elastic: k = 2: vs (m/s, 0 <= 2 vs^2 <= vp^2) and rho
+ * (> 0).  damp: NULL for the built-in sponge of opt.nbl cells, or
  * n0 + n1 + n2 per-axis damping coefficients eta (1/s) whose sum over the
  * three axes is the damping of a grid point.  dt: time step in seconds; 0
- * selects 0.8 of the CFL limit for the model's maximum velocity.  Computes
- * vmax on the device (the call synchronises `stream` once).
+ * selects 0.8 of the stability limit (tb_cfl_dt_max, tb_tti_dt_max or
+ * tb_elastic_dt_max for the model's maxima).  Computes the maxima on the
+ * device (the call synchronises `stream`).
  * Errors: TB_EINVAL (vp <= 0 or not finite), TB_EUNSTABLE (dt > limit). */
 int tb_set_model(tb_handle* h, const float* vp, const float* aux, const float* damp,
                  double dt, void* stream);
@@ -105,7 +124,8 @@ double tb_get_dt(const tb_handle* h);
  * (Sec. II-A.1-3): trilinear corners with FP64 weight != 0 become affected
  * points with ascending unique IDs, and the wavelets are decomposed into the
  * grid-aligned table src_dcmp[t][id] = (dt^2/m(p_id)) sum_s w_s(p_id) q_s[t]
- * (Listing 3, injection expression s*dt^2/m of Sec. III-A).
+ * (Listing 3, injection expression s*dt^2/m of Sec. III-A; elastic: dt
+ * instead of dt^2/m).
  * coords: [nsrc][3] FP64 metres.  wavelets: [nsrc][nt] float.  Requires
  * tb_set_model first (TB_ESTATE).  nsrc may be 0 (no sources).
  * Limits: nsrc < 2^21.  Errors: TB_EINVAL (coordinate outside the grid). */
@@ -124,14 +144,20 @@ int tb_set_receivers(tb_handle* h, int nrec, const double* coords, void* stream)
  * step-n injection), an [nt][nrec] float array (host or device; may be
  * NULL).  schedule: TB_ONESTEP (one launch per time step, spatial blocking
  * only) or TB_BLOCKED (opt.time_tile steps fused per sweep, Sec. II-B).
- * Both give bitwise-identical wavefields and traces.  nt must not exceed the
+ * Both give bitwise-identical wavefields and traces.  TB_TTI and
+ * TB_ELASTIC: TB_ONESTEP only (TB_BLOCKED gives TB_EINVAL); traces sample p
+ * (TTI) or the mean normal stress at n+1 (elastic).  Source tables scale:
+ * dt^2/m (acoustic, TTI), dt (elastic).  nt must not exceed the
  * wavelet length given to tb_set_sources (when sources are set).
  * Device traces: asynchronous on `stream`.  Host traces: synchronous.
  * Errors: TB_ESTATE, TB_EINVAL, TB_ETIMEOUT, TB_EDIVERGED, TB_ECUDA. */
 int tb_forward(tb_handle* h, int nt, float* traces, int schedule, void* stream);
 
 /* Copy a wavefield after tb_forward into out (dense [n0][n1][n2] float,
- * host or device): which = 0 -> u^{nt}, which = 1 -> u^{nt-1}. */
+ * host or device).  Acoustic: which = 0 -> u^{nt}, 1 -> u^{nt-1}.  TTI:
+ * 0 -> p^{nt}, 1 -> p^{nt-1}, 2 -> r^{nt}, 3 -> r^{nt-1}.  Elastic: 0..8 ->
+ * vx, vy, vz (at nt - 1/2; vx at (i+1/2, j, k) etc.), txx, tyy, tzz, txy,
+ * txz, tyz (at nt; txy at (i+1/2, j+1/2, k) etc.). */
 int tb_get_field(tb_handle* h, int which, float* out, void* stream);
 
 /* Inspector tables, for checking against an independent implementation.
@@ -218,6 +244,15 @@ int tb_selftest_wait(double timeout_s, void* stream);
  * results; order them, e.g. on one stream.  Errors: TB_EINVAL, TB_ECUDA. */
 int tb_inspect_points_noalloc(const int64_t n[3], const double h[3], int npt, const double* coords,
                               int64_t* lin, int64_t* npts, void* stream);
+
+/* Stability limits of the TTI and elastic schemes (seconds), -1 on bad
+ * arguments.  TTI: 2 / (vmax sqrt(1 + 2 eps_max) sqrt(sum_d (S1/h_d)^2)),
+ * S1 = max |2 sum a_i sin(i t)| over the centred first-derivative weights
+ * (the largest eigenvalue of the coupled p, r system is at most (1 + 2 eps)
+ * |s|^2 when eps >= delta).  Elastic: 2 / (vpmax sqrt(sum_d (S/h_d)^2)),
+ * S = max |2 sum c_k sin((k - 1/2) t)| over the staggered weights. */
+double tb_tti_dt_max(int space_order, const double h[3], double vmax, double eps_max);
+double tb_elastic_dt_max(int space_order, const double h[3], double vpmax);
 
 /* Number of CUDA kernels this library has launched in this process (all
  * handles, all devices), for accounting in benchmarks. */

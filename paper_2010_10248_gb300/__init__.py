@@ -8,13 +8,15 @@ convenience wrapper that keeps device buffers in torch tensors.
 from __future__ import annotations
 
 from . import _tb
-from ._tb import (TB_ACOUSTIC, TB_BLOCKED, TB_ONESTEP, Options, TBError, load, tb_cfl_dt_max,
+from ._tb import (TB_ACOUSTIC, TB_BLOCKED, TB_ELASTIC, TB_ONESTEP, TB_TTI, Options, TBError, load,
+                  tb_cfl_dt_max, tb_elastic_dt_max, tb_tti_dt_max,
                   tb_create, tb_destroy, tb_fd_weights, tb_forward, tb_get_dt, tb_get_field,
                   tb_get_receiver_points, tb_get_source_points, tb_kernel_time, tb_last_error,
                   tb_launch_count, tb_ricker, tb_selftest_wait, tb_set_model, tb_set_receivers, tb_set_sources,
                   tb_sponge_profile, tb_workspace_bytes)
 
 __all__ = ["Propagator", "Options", "TBError", "load", "TB_ONESTEP", "TB_BLOCKED", "TB_ACOUSTIC",
+           "TB_TTI", "TB_ELASTIC", "tb_tti_dt_max", "tb_elastic_dt_max",
            "tb_create", "tb_destroy", "tb_set_model", "tb_get_dt", "tb_set_sources",
            "tb_set_receivers", "tb_forward", "tb_get_field", "tb_get_source_points",
            "tb_get_receiver_points", "tb_workspace_bytes", "tb_kernel_time", "tb_last_error",
@@ -30,8 +32,8 @@ class Propagator:
     [nt, nrec] unless a destination is given.
     """
 
-    def __init__(self, shape, spacing, space_order, *, time_tile=0, nbl=0, y_bands=0,
-                 x_chunks=0, profile=False, check_nan=False, wait_timeout_s=0.0):
+    def __init__(self, shape, spacing, space_order, *, physics=TB_ACOUSTIC, time_tile=0, nbl=0,
+                 y_bands=0, x_chunks=0, profile=False, check_nan=False, wait_timeout_s=0.0):
         import torch
         self._torch = torch
         opt = Options(time_tile=time_tile, nbl=nbl, y_bands=y_bands, x_chunks=x_chunks,
@@ -40,7 +42,8 @@ class Propagator:
         self.shape = tuple(int(s) for s in shape)
         self.spacing = tuple(float(s) for s in spacing)
         self.space_order = int(space_order)
-        self.h = tb_create(self.shape, self.spacing, self.space_order, TB_ACOUSTIC, opt)
+        self.physics = int(physics)
+        self.h = tb_create(self.shape, self.spacing, self.space_order, self.physics, opt)
         self.nrec = 0
         self.nt_src = None
 
@@ -58,8 +61,19 @@ class Propagator:
     def _stream(self):
         return self._torch.cuda.current_stream()
 
-    def set_model(self, vp, damp=None, dt=0.0):
-        tb_set_model(self.h, vp, None, damp, dt, self._stream())
+    def set_model(self, vp, damp=None, dt=0.0, aux=None):
+        """vp [n0, n1, n2]; aux: TTI (eps, delta, theta, phi), elastic (vs, rho),
+        each [n0, n1, n2], stacked on a new leading axis (or a sequence)."""
+        if aux is not None and not hasattr(aux, "data_ptr") and not hasattr(aux, "ctypes"):
+            import numpy as np
+            aux = np.stack([np.asarray(a, dtype=np.float32) for a in aux])
+        if aux is not None and hasattr(aux, "data_ptr"):
+            aux = aux.to(dtype=self._torch.float32).contiguous()
+        elif aux is not None:
+            import numpy as np
+            aux = np.ascontiguousarray(aux, dtype=np.float32)
+        tb_set_model(self.h, vp, aux, damp, dt, self._stream())
+        self._aux = aux
         return self
 
     @property
@@ -82,8 +96,12 @@ class Propagator:
         tb_set_receivers(self.h, self.nrec, coords, self._stream())
         return self
 
-    def forward(self, nt, traces=None, schedule="blocked"):
+    def forward(self, nt, traces=None, schedule=None):
+        """schedule: "blocked" (default for acoustic) or "onestep" (the only
+        one for TTI and elastic)."""
         torch = self._torch
+        if schedule is None:
+            schedule = "blocked" if self.physics == TB_ACOUSTIC else "onestep"
         sched = TB_BLOCKED if schedule == "blocked" else TB_ONESTEP
         if traces is None and self.nrec > 0:
             traces = torch.empty((nt, self.nrec), dtype=torch.float32, device="cuda")

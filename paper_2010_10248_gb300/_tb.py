@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "tb.h")
 TB_OK, TB_EINVAL, TB_ENOMEM, TB_ECUDA, TB_EUNSTABLE, TB_ETIMEOUT, TB_EDIVERGED, TB_ESTATE = range(8)
 STATUS_NAMES = {0: "TB_OK", 1: "TB_EINVAL", 2: "TB_ENOMEM", 3: "TB_ECUDA", 4: "TB_EUNSTABLE",
                 5: "TB_ETIMEOUT", 6: "TB_EDIVERGED", 7: "TB_ESTATE"}
-TB_ACOUSTIC = 0
+TB_ACOUSTIC, TB_TTI, TB_ELASTIC = 0, 1, 2
 TB_ONESTEP, TB_BLOCKED = 0, 1
 
 
@@ -57,6 +57,8 @@ _SIGS = {
     "tb_last_error": (C.c_char_p, [_vp]),
     "tb_fd_weights": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "tb_cfl_dt_max": (C.c_double, [C.c_int, C.POINTER(C.c_double), C.c_double]),
+    "tb_tti_dt_max": (C.c_double, [C.c_int, C.POINTER(C.c_double), C.c_double, C.c_double]),
+    "tb_elastic_dt_max": (C.c_double, [C.c_int, C.POINTER(C.c_double), C.c_double]),
     "tb_sponge_profile": (C.c_int, [C.c_int64, C.c_int, C.c_double, C.c_double,
                                     C.POINTER(C.c_double)]),
     "tb_ricker": (C.c_int, [C.c_double, C.c_double, C.c_int, C.c_double, C.POINTER(C.c_float)]),
@@ -207,6 +209,16 @@ def tb_fd_weights(space_order):
 def tb_cfl_dt_max(space_order, spacing, vmax):
     hh = (C.c_double * 3)(*[float(s) for s in spacing])
     return load().tb_cfl_dt_max(int(space_order), hh, float(vmax))
+
+
+def tb_tti_dt_max(space_order, spacing, vmax, eps_max):
+    hh = (C.c_double * 3)(*[float(s) for s in spacing])
+    return load().tb_tti_dt_max(int(space_order), hh, float(vmax), float(eps_max))
+
+
+def tb_elastic_dt_max(space_order, spacing, vpmax):
+    hh = (C.c_double * 3)(*[float(s) for s in spacing])
+    return load().tb_elastic_dt_max(int(space_order), hh, float(vpmax))
 
 
 def tb_sponge_profile(n, nbl, h, vmax):

@@ -66,6 +66,17 @@ struct tb_handle {
   CUtensorMap tm_tile[4];  // own tiles, per field buffer
   CUtensorMap tm_c2;       // own tiles of c2
   float* damp_b = nullptr;
+  // other physics (Sec. III-B/C): physics id, TTI coefficients [2][Np]
+  // (1+2eps, sqrt(1+2delta)), symmetry axis [3][Np], fluxes [6][Np];
+  // elastic fields [9][Np], material [8][Np] and per-axis eta*dt
+  int physics = TB_ACOUSTIC;
+  float* coef = nullptr;
+  float* nzb = nullptr;
+  float* flux = nullptr;
+  float* efield = nullptr;
+  float* emat = nullptr;
+  float* eta_dt = nullptr;
+  double aux_max = 0.0;  // eps_max (TTI)
   // sources
   PointTables src;
   int src_nt = 0;
@@ -179,6 +190,88 @@ extern "C" double tb_cfl_dt_max(int so, const double h[3], double vmax) {
   return 2.0 / (vmax * std::sqrt(S * inv));
 }
 
+// Centred first-derivative weights a_1..a_r of order 2r (closed form):
+// a_i = (-1)^(i+1) (r!)^2 / (i (r-i)! (r+i)!).
+static void d1_weights(int r, double* a) {
+  auto fact = [](int k) {
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= i;
+    return f;
+  };
+  for (int i = 1; i <= r; ++i)
+    a[i] = (i % 2 ? 1.0 : -1.0) * fact(r) * fact(r) / ((double)i * fact(r - i) * fact(r + i));
+}
+// Staggered first-derivative weights c_1..c_r (nodes at +-(k - 1/2)) from
+// the moment conditions sum_k 2 c_k (k - 1/2)^(2m+1) = [m == 0], m < r,
+// solved by Gaussian elimination with partial pivoting.
+static void stag_weights(int r, double* c) {
+  double A[8][9];
+  for (int m = 0; m < r; ++m) {
+    for (int k = 1; k <= r; ++k) A[m][k - 1] = 2.0 * std::pow(k - 0.5, 2 * m + 1);
+    A[m][r] = m == 0 ? 1.0 : 0.0;
+  }
+  for (int col = 0; col < r; ++col) {
+    int piv = col;
+    for (int i = col + 1; i < r; ++i)
+      if (std::fabs(A[i][col]) > std::fabs(A[piv][col])) piv = i;
+    for (int j = 0; j <= r; ++j) std::swap(A[col][j], A[piv][j]);
+    for (int i = 0; i < r; ++i) {
+      if (i == col) continue;
+      const double f = A[i][col] / A[col][col];
+      for (int j = col; j <= r; ++j) A[i][j] -= f * A[col][j];
+    }
+  }
+  for (int k = 1; k <= r; ++k) c[k] = A[k - 1][r] / A[k - 1][k - 1];
+}
+// max over t in [0, pi] of |2 sum_i w_i sin((i - shift) t)|: dense samples,
+// then golden-section refinement around the best one
+static double symbol_peak(const double* w, int r, double shift) {
+  auto f = [&](double t) {
+    double v = 0.0;
+    for (int i = 1; i <= r; ++i) v += w[i] * std::sin((i - shift) * t);
+    return std::fabs(2.0 * v);
+  };
+  const double pi = 3.14159265358979323846;
+  const int ns = 4096;
+  int best = 0;
+  for (int s = 1; s <= ns; ++s)
+    if (f(pi * s / ns) > f(pi * best / ns)) best = s;
+  double lo = pi * std::max(0, best - 1) / ns, hi = pi * std::min(ns, best + 1) / ns;
+  const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
+  for (int it = 0; it < 100; ++it) {
+    const double a = hi - gr * (hi - lo), b = lo + gr * (hi - lo);
+    if (f(a) > f(b)) hi = b;
+    else lo = a;
+  }
+  return std::max(f(0.5 * (lo + hi)), f(pi * best / ns));
+}
+
+extern "C" double tb_tti_dt_max(int so, const double h[3], double vmax, double eps_max) {
+  if (!h || !(vmax > 0) || !(eps_max > -0.5) || so < 2 || so > 12 || so % 2) return -1.0;
+  double a[8];
+  d1_weights(so / 2, a);
+  const double S1 = symbol_peak(a, so / 2, 0.0);
+  double s2 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    if (!(h[d] > 0)) return -1.0;
+    s2 += (S1 / h[d]) * (S1 / h[d]);
+  }
+  return 2.0 / (vmax * std::sqrt((1.0 + 2.0 * std::max(eps_max, 0.0)) * s2));
+}
+
+extern "C" double tb_elastic_dt_max(int so, const double h[3], double vpmax) {
+  if (!h || !(vpmax > 0) || so < 2 || so > 12 || so % 2) return -1.0;
+  double c[8];
+  stag_weights(so / 2, c);
+  const double S = symbol_peak(c, so / 2, 0.5);
+  double s2 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    if (!(h[d] > 0)) return -1.0;
+    s2 += (S / h[d]) * (S / h[d]);
+  }
+  return 2.0 / (vpmax * std::sqrt(s2));
+}
+
 extern "C" int tb_sponge_profile(int64_t n, int nbl, double h, double vmax, double* eta) {
   if (n < 1 || nbl < 0 || !eta || !(h > 0)) return TB_EINVAL;
   const double emax = nbl > 0 ? 3.0 * vmax * std::log(1000.0) / (2.0 * nbl * h) : 0.0;
@@ -209,6 +302,12 @@ extern "C" const char* tb_last_error(const tb_handle* h) { return h ? h->msg : "
 extern "C" int tb_destroy(tb_handle* h) {
   if (!h) return TB_OK;
   for (auto& f : h->field) cudaFree(f);
+  cudaFree(h->coef);
+  cudaFree(h->nzb);
+  cudaFree(h->flux);
+  cudaFree(h->efield);
+  cudaFree(h->emat);
+  cudaFree(h->eta_dt);
   cudaFree(h->c2);
   cudaFree(h->damp_b);
   free_tables(&h->src);
@@ -251,7 +350,7 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
                          const tb_options* opt, tb_handle** out) {
   if (!out || !n || !hsp) return TB_EINVAL;
   *out = nullptr;
-  if (physics != TB_ACOUSTIC) return TB_EINVAL;
+  if (physics != TB_ACOUSTIC && physics != TB_TTI && physics != TB_ELASTIC) return TB_EINVAL;
   if (so != 4 && so != 8 && so != 12) return TB_EINVAL;
   for (int d = 0; d < 3; ++d) {
     if (n[d] < so + 2 || n[d] > 65535 || !(hsp[d] > 0)) return TB_EINVAL;
@@ -264,8 +363,10 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   }
   h->so = so;
   h->R = so / 2;
+  h->physics = physics;
   if (opt) h->opt = *opt;
-  const int tmax = so == 12 ? 2 : 4;  // more fused so12 steps exceed shared memory
+  // more fused so12 steps exceed shared memory; TTI and elastic run one step per launch
+  const int tmax = physics != TB_ACOUSTIC ? 1 : (so == 12 ? 2 : 4);
   if (h->opt.time_tile == 0) h->opt.time_tile = tmax;
   if (h->opt.time_tile < 1 || h->opt.time_tile > tmax || h->opt.nbl < 0 || h->opt.y_bands < 0 ||
       h->opt.x_chunks < 0) {
@@ -278,9 +379,21 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   const size_t fbytes = sizeof(float) * (size_t)n[0] * n[1] * h->n2p;
-  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+  const int nfield = physics == TB_ELASTIC ? 0 : 4;
+  for (int i = 0; i < nfield && e == cudaSuccess; ++i) {
     e = cudaMalloc(&h->field[i], fbytes);
     if (e == cudaSuccess) e = cudaMemset(h->field[i], 0, fbytes);
+  }
+  if (physics == TB_TTI) {
+    if (e == cudaSuccess) e = cudaMalloc(&h->coef, 2 * fbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->nzb, 3 * fbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->flux, 6 * fbytes);
+    if (e == cudaSuccess) e = cudaMemset(h->flux, 0, 6 * fbytes);
+  } else if (physics == TB_ELASTIC) {
+    if (e == cudaSuccess) e = cudaMalloc(&h->efield, 9 * fbytes);
+    if (e == cudaSuccess) e = cudaMemset(h->efield, 0, 9 * fbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->emat, 8 * fbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->eta_dt, sizeof(float) * (n[0] + n[1] + n[2]));
   }
   if (e == cudaSuccess) e = cudaMalloc(&h->c2, fbytes);
   if (e == cudaSuccess) e = cudaMemset(h->c2, 0, fbytes);
@@ -289,11 +402,11 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int) * 4);
   SweepShape sh;
   if (e == cudaSuccess && !sweep_shape(h->R, 1, &sh)) e = cudaErrorInvalidValue;
-  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+  for (int i = 0; i < 4 && e == cudaSuccess && physics == TB_ACOUSTIC; ++i) {
     e = make_tmap(&h->tm_box[i], h->field[i], n, h->n2p, sh.box_w, sh.box_h);
     if (e == cudaSuccess) e = make_tmap(&h->tm_tile[i], h->field[i], n, h->n2p, 64, sh.TY);
   }
-  if (e == cudaSuccess) e = make_tmap(&h->tm_c2, h->c2, n, h->n2p, 64, sh.TY);
+  if (e == cudaSuccess && physics == TB_ACOUSTIC) e = make_tmap(&h->tm_c2, h->c2, n, h->n2p, 64, sh.TY);
   if (e != cudaSuccess) {
     int code = e == cudaErrorMemoryAllocation ? TB_ENOMEM : TB_ECUDA;
     cudaGetLastError();
@@ -310,6 +423,8 @@ extern "C" size_t tb_workspace_bytes(const tb_handle* h) {
   if (!h) return 0;
   const size_t fbytes = sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n2p;
   size_t b = 5 * fbytes + sizeof(float) * (h->n[0] + h->n[1] + h->n[2]) + sizeof(int) * 4;
+  if (h->physics == TB_TTI) b += 11 * fbytes;
+  if (h->physics == TB_ELASTIC) b += 17 * fbytes - 4 * fbytes + sizeof(float) * (h->n[0] + h->n[1] + h->n[2]);
   b += h->src.bytes + h->rec.bytes;
   b += sizeof(float) * (size_t)h->src_nt * std::max<int64_t>(h->src.npts, 0);
   b += sizeof(float) * (size_t)h->rec_cap * std::max<int64_t>(h->rec.npts, 0);
@@ -322,7 +437,9 @@ extern "C" int tb_set_model(tb_handle* h, const float* vp, const float* aux, con
                             double dt, void* stream) {
   if (!h) return TB_EINVAL;
   if (!vp) return fail(h, TB_EINVAL, "vp is NULL");
-  if (aux) return fail(h, TB_EINVAL, "aux must be NULL for acoustic physics");
+  if (h->physics == TB_ACOUSTIC && aux) return fail(h, TB_EINVAL, "aux must be NULL for acoustic physics");
+  if (h->physics != TB_ACOUSTIC && !aux)
+    return fail(h, TB_EINVAL, "aux is required (TTI: eps, delta, theta, phi; elastic: vs, rho)");
   if (dt < 0 || !std::isfinite(dt)) return fail(h, TB_EINVAL, "dt must be >= 0");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t N = h->n[0] * h->n[1] * h->n[2];
@@ -345,7 +462,44 @@ extern "C" int tb_set_model(tb_handle* h, const float* vp, const float* aux, con
     cudaFree(tmp);
     return fail(h, TB_EINVAL, "vp must be finite and > 0 everywhere");
   }
-  const double dtmax = tb_cfl_dt_max(h->so, h->h, vmax);
+  double dtmax = tb_cfl_dt_max(h->so, h->h, vmax);
+  if (h->physics != TB_ACOUSTIC) {
+    // per-point coefficients of the TTI / elastic operator from aux
+    const int naux = h->physics == TB_TTI ? 4 : 2;
+    void* tmpa = nullptr;
+    const void* daux = nullptr;
+    e = to_device(aux, sizeof(float) * N * naux, &tmpa, &daux, st);
+    const PhysGrid g{(int)h->n[0], (int)h->n[1], (int)h->n[2], h->n2p};
+    unsigned* d_emax = reinterpret_cast<unsigned*>(h->err + 2);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err + 2, 0, sizeof(int) * 2, st);
+    if (e == cudaSuccess) {
+      if (h->physics == TB_TTI)
+        e = tti_coefficients(g, (const float*)daux, h->coef, h->nzb, d_emax, d_bad, st);
+      else
+        e = elastic_material(g, (const float*)dvp, (const float*)daux, (const float*)daux + N, h->emat, d_bad,
+                             st);
+    }
+    unsigned emax_bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&emax_bits, d_emax, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tmpa);
+    if (e != cudaSuccess) {
+      cudaFree(tmp);
+      return cuda_fail(h, e, "tb_set_model coefficients");
+    }
+    if (bad) {
+      cudaFree(tmp);
+      return fail(h, h->physics == TB_TTI ? TB_EUNSTABLE : TB_EINVAL,
+                  h->physics == TB_TTI ? "TTI needs eps >= delta > -1/2 and finite angles everywhere"
+                                       : "elastic needs rho > 0, vs >= 0 and 2 vs^2 <= vp^2 everywhere");
+    }
+    float emax = 0.f;
+    memcpy(&emax, &emax_bits, sizeof(float));
+    h->aux_max = h->physics == TB_TTI ? (double)emax : 0.0;
+    dtmax = h->physics == TB_TTI ? tb_tti_dt_max(h->so, h->h, vmax, h->aux_max)
+                                 : tb_elastic_dt_max(h->so, h->h, vmax);
+  }
   if (dt == 0.0) dt = 0.8 * dtmax;
   if (dt > dtmax) {
     cudaFree(tmp);
@@ -380,14 +534,20 @@ extern "C" int tb_set_model(tb_handle* h, const float* vp, const float* aux, con
       off += h->n[d];
     }
   }
-  std::vector<float> b(nsum);
-  for (int64_t i = 0; i < nsum; ++i) b[i] = (float)(eta[i] / (2.0 * dt));
+  std::vector<float> b(nsum), edt(nsum);
+  for (int64_t i = 0; i < nsum; ++i) {
+    b[i] = (float)(eta[i] / (2.0 * dt));
+    edt[i] = (float)(eta[i] * dt);
+  }
   e = cudaMemcpyAsync(h->damp_b, b.data(), sizeof(float) * nsum, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && h->physics == TB_ELASTIC)
+    e = cudaMemcpyAsync(h->eta_dt, edt.data(), sizeof(float) * nsum, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = model_c2((const float*)dvp, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->n2p, dt * dt, h->c2, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // b (host vector) must outlive the copy
   cudaFree(tmp);
   if (e != cudaSuccess) return cuda_fail(h, e, "tb_set_model c2");
+  (void)edt;
   h->dt = dt;
   h->vmax = vmax;
   h->have_model = true;
@@ -429,8 +589,10 @@ extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int 
   if (h->src.npts > 0) {
     e = cudaMalloc(&h->src_dcmp, sizeof(float) * (size_t)nt * h->src.npts);
     if (e == cudaSuccess)
-      e = decompose(&h->src, nt, (const float*)dw, h->c2, (int)h->n[1], (int)h->n[2], h->n2p,
-                    h->src_dcmp, st);
+      // acoustic / TTI: dt^2/m at the point (Eq. 1's s dt^2/m); elastic:
+      // explosive source into the normal stresses, dt q
+      e = decompose(&h->src, nt, (const float*)dw, h->physics == TB_ELASTIC ? nullptr : h->c2, h->dt,
+                    (int)h->n[1], (int)h->n[2], h->n2p, h->src_dcmp, st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(t1);
@@ -618,6 +780,119 @@ static cudaEvent_t ev_next(tb_handle* h) {
   return h->ev[h->ev_used++];
 }
 
+// TTI / elastic: one step per launch (Sec. III-B/C), grid-aligned injection
+// and receiver sampling as separate kernels after each step.
+static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
+  const int nrec = h->have_rec ? h->rec.npt : 0;
+  const bool rec_on = h->have_rec && h->rec.npts > 0 && nrec > 0 && traces;
+  const bool host_traces = traces && nrec > 0 && !is_device_ptr(traces);
+  const size_t fbytes = sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n2p;
+  if (rec_on && h->rec_cap < 16) {
+    cudaFree(h->rec_dcmp);
+    h->rec_dcmp = nullptr;
+    h->rec_cap = 0;
+    TB_CUDA(h, cudaMalloc(&h->rec_dcmp, sizeof(float) * 16 * h->rec.npts));
+    h->rec_cap = 16;
+  }
+  if (host_traces && (size_t)nt * nrec > h->traces_cap) {
+    cudaFree(h->traces_dev);
+    h->traces_dev = nullptr;
+    h->traces_cap = 0;
+    TB_CUDA(h, cudaMalloc(&h->traces_dev, sizeof(float) * (size_t)nt * nrec));
+    h->traces_cap = (size_t)nt * nrec;
+  }
+  float* dtr = host_traces ? h->traces_dev : traces;
+  const PhysGrid g{(int)h->n[0], (int)h->n[1], (int)h->n[2], h->n2p};
+  DerivW w{};
+  double a[8];
+  if (h->physics == TB_TTI) d1_weights(h->R, a);
+  else stag_weights(h->R, a);
+  for (int d = 0; d < 3; ++d)
+    for (int i = 1; i <= h->R; ++i) w.a[d][i - 1] = (float)(a[i] / h->h[d]);
+  if (h->opt.profile) ev_reset(h, st);
+  if (h->physics == TB_TTI) {
+    for (int i = 0; i < 4; ++i) TB_CUDA(h, cudaMemsetAsync(h->field[i], 0, fbytes, st));
+  } else {
+    TB_CUDA(h, cudaMemsetAsync(h->efield, 0, 9 * fbytes, st));
+  }
+  // enough columns x chunks to fill the GPU a few times over (TTI streams chunks)
+  const int64_t cols = h->n[1] * h->n[2];
+  const int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>(h->n[0] / std::max(4, 2 * h->R),
+                                                                   (int64_t)h->num_sms * 2048 / std::max<int64_t>(cols, 1)));
+  int pc = 0, pp = 1, rc = 2, rp = 3;  // TTI field indices
+  int fill = 0, base = 0;
+  const size_t Np = (size_t)h->n[0] * h->n[1] * h->n2p;
+  auto flush = [&]() -> int {
+    if (rec_on && fill > 0) {
+      cudaError_t e = finalize_traces(fill, nrec, h->rec.corner_eid, h->rec.corner_w, h->rec_dcmp, h->rec.npts,
+                                      dtr + (size_t)base * nrec, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "receiver finalize");
+    }
+    base += fill;
+    fill = 0;
+    return TB_OK;
+  };
+  for (int n = 0; n < nt; ++n) {
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (h->opt.profile) {
+      ea = ev_next(h);
+      eb = ev_next(h);
+      h->ev_kind.push_back(0);
+      if (ea) cudaEventRecord(ea, st);
+    }
+    cudaError_t e;
+    float *f0, *f1 = nullptr, *f2 = nullptr, *s1 = nullptr, *s2 = nullptr;
+    if (h->physics == TB_TTI) {
+      e = tti_step(h->R, g, w, nchunks, h->field[pc], h->field[pp], h->field[rc], h->field[rp], h->c2, h->coef,
+                   h->nzb, h->damp_b, h->flux, st);
+      std::swap(pc, pp);
+      std::swap(rc, rp);
+      f0 = h->field[pc];
+      f1 = h->field[rc];
+    } else {
+      e = elastic_step(h->R, g, w, (float)h->dt, h->efield, h->emat, h->eta_dt, st);
+      f0 = h->efield + 3 * Np;
+      f1 = h->efield + 4 * Np;
+      f2 = h->efield + 5 * Np;
+      s1 = f1;
+      s2 = f2;
+    }
+    if (h->opt.profile && eb) cudaEventRecord(eb, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+    if (h->have_src && h->src.npts > 0) {
+      e = inject_points(g, h->src.npts, h->src.lin, h->src_dcmp + (size_t)n * h->src.npts, f0, f1, f2, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "injection");
+    }
+    if (rec_on) {
+      e = sample_points(g, h->rec.npts, h->rec.ent, h->rec.lin, f0, s1, s2, h->rec_dcmp + (size_t)fill * h->rec.npts,
+                        st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "receiver sampling");
+      if (++fill == h->rec_cap) {
+        int s = flush();
+        if (s != TB_OK) return s;
+      }
+    }
+  }
+  int s = flush();
+  if (s != TB_OK) return s;
+  h->cur_idx = pc;
+  h->prev_idx = pp;
+  h->last_nt = nt;
+  if (host_traces) {
+    TB_CUDA(h, cudaMemcpyAsync(traces, h->traces_dev, sizeof(float) * (size_t)nt * nrec, cudaMemcpyDeviceToHost, st));
+    TB_CUDA(h, cudaStreamSynchronize(st));
+  }
+  if (h->opt.check_nan && traces && nrec > 0 && nt > 0) {
+    int cnt = 0;
+    TB_CUDA(h, count_nonfinite(dtr, (int64_t)nt * nrec, h->err + 1, st));
+    TB_CUDA(h, cudaMemcpyAsync(&cnt, h->err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TB_CUDA(h, cudaStreamSynchronize(st));
+    if (cnt) return fail(h, TB_EDIVERGED, "%d non-finite trace samples", cnt);
+  }
+  h->msg[0] = 0;
+  return TB_OK;
+}
+
 extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, void* stream) {
   if (!h) return TB_EINVAL;
   if (!h->have_model) return fail(h, TB_ESTATE, "tb_set_model must come before tb_forward");
@@ -626,6 +901,11 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   if (h->have_src && h->src.npts > 0 && nt > h->src_nt)
     return fail(h, TB_EINVAL, "nt = %d exceeds the wavelet length %d", nt, h->src_nt);
   cudaStream_t st = (cudaStream_t)stream;
+  if (h->physics != TB_ACOUSTIC) {
+    if (schedule != TB_ONESTEP)
+      return fail(h, TB_EINVAL, "the blocked schedule is implemented for the acoustic equation only");
+    return forward_other(h, nt, traces, st);
+  }
   const int nrec = h->have_rec ? h->rec.npt : 0;
   const bool host_traces = traces && nrec > 0 && !is_device_ptr(traces);
   float* dtr = host_traces ? nullptr : traces;
@@ -794,9 +1074,20 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
 extern "C" int tb_get_field(tb_handle* h, int which, float* out, void* stream) {
   if (!h) return TB_EINVAL;
   if (h->last_nt < 0) return fail(h, TB_ESTATE, "no forward run yet");
-  if ((which != 0 && which != 1) || !out) return fail(h, TB_EINVAL, "bad arguments");
+  const int nwhich = h->physics == TB_ACOUSTIC ? 2 : (h->physics == TB_TTI ? 4 : 9);
+  if (which < 0 || which >= nwhich || !out) return fail(h, TB_EINVAL, "bad arguments");
   cudaStream_t st = (cudaStream_t)stream;
-  const float* src = h->field[which == 0 ? h->cur_idx : h->prev_idx];
+  const float* src = nullptr;
+  if (h->physics == TB_ACOUSTIC) {
+    src = h->field[which == 0 ? h->cur_idx : h->prev_idx];
+  } else if (h->physics == TB_TTI) {
+    // p^n, p^{n-1}, r^n, r^{n-1}: p in fields {cur_idx, prev_idx}, r in the other two
+    const int rc = h->cur_idx == 0 ? 2 : 3, rp = h->cur_idx == 0 ? 3 : 2;
+    const int idx[4] = {h->cur_idx, h->prev_idx, rc, rp};
+    src = h->field[idx[which]];
+  } else {
+    src = h->efield + (size_t)which * h->n[0] * h->n[1] * h->n2p;
+  }
   const size_t N = (size_t)h->n[0] * h->n[1] * h->n[2];
   if (is_device_ptr(out)) {
     TB_CUDA(h, unpad_copy(src, out, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->n2p, st));

@@ -371,7 +371,7 @@ fail:
 __global__ void k_decompose(int nt, int64_t npts, const int64_t* __restrict__ gstart,
                             const unsigned long long* __restrict__ keys,
                             const double* __restrict__ w8, const float* __restrict__ wav,
-                            const int64_t* __restrict__ lin, const float* __restrict__ c2,
+                            const int64_t* __restrict__ lin, const float* __restrict__ c2, double scale,
                             int64_t n1, int64_t n2, int64_t n2p, float* dcmp) {
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
@@ -384,16 +384,16 @@ __global__ void k_decompose(int nt, int64_t npts, const int64_t* __restrict__ gs
   }
   const int64_t l = lin[id];
   const int64_t z = l % n2, y = (l / n2) % n1, x = l / (n1 * n2);
-  const double s = (double)c2[(x * n1 + y) * n2p + z];
+  const double s = c2 ? (double)c2[(x * n1 + y) * n2p + z] : scale;
   dcmp[(int64_t)t * npts + id] = (float)(acc * s);
 }
 
-cudaError_t decompose(const PointTables* t, int nt, const float* d_wav, const float* c2, int n1,
-                      int n2, int n2p, float* d_dcmp, cudaStream_t st) {
+cudaError_t decompose(const PointTables* t, int nt, const float* d_wav, const float* c2, double scale,
+                      int n1, int n2, int n2p, float* d_dcmp, cudaStream_t st) {
   if (t->npts <= 0 || nt <= 0) return cudaSuccess;
   dim3 grid(grid_for(t->npts, 128), nt);
   count_launch();
-  k_decompose<<<grid, 128, 0, st>>>(nt, t->npts, t->gstart, t->keys, t->w8, d_wav, t->lin, c2, n1,
+  k_decompose<<<grid, 128, 0, st>>>(nt, t->npts, t->gstart, t->keys, t->w8, d_wav, t->lin, c2, scale, n1,
                                     n2, n2p, d_dcmp);
   return cudaGetLastError();
 }

@@ -94,13 +94,36 @@ struct PointTables {
   size_t bytes = 0;
 };
 
+// Grid of a padded field and first-derivative weights (per axis, offsets
+// 1..r, divided by the spacing) for the TTI and elastic kernels (tb_physics.cu).
+struct PhysGrid {
+  int n0, n1, n2, n2p;
+};
+struct DerivW {
+  float a[3][6];
+};
+cudaError_t tti_step(int R, const PhysGrid& g, const DerivW& w, int nchunks, const float* pc, float* pp,
+                     const float* rc, float* rp, const float* c2, const float* coef, const float* nz,
+                     const float* damp_b, float* flux, cudaStream_t st);
+cudaError_t tti_coefficients(const PhysGrid& g, const float* aux, float* coef, float* nz, unsigned* d_emax,
+                             int* d_bad, cudaStream_t st);
+cudaError_t elastic_step(int R, const PhysGrid& g, const DerivW& w, float dt, float* f, const float* mat,
+                         const float* eta_dt, cudaStream_t st);
+cudaError_t elastic_material(const PhysGrid& g, const float* vp, const float* vs, const float* rho, float* mat,
+                             int* d_bad, cudaStream_t st);
+cudaError_t inject_points(const PhysGrid& g, int64_t npts, const int64_t* lin, const float* dcmp_row, float* f0,
+                          float* f1, float* f2, cudaStream_t st);
+cudaError_t sample_points(const PhysGrid& g, int64_t npts, const int2* ent, const int64_t* lin, const float* f0,
+                          const float* f1, const float* f2, float* row, cudaStream_t st);
+
 void free_tables(PointTables* t);
 // Builds lin, colptr, ent (+ corner tables when want_corners).  coords on
 // the device.  Returns TB_OK / TB_EINVAL / TB_ENOMEM / TB_ECUDA.
 int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coords,
             bool want_corners, PointTables* t, cudaStream_t st, const char** why);
-// src_dcmp[t][id] = c2(p_id) * sum_e w_e q_{s(e)}[t]  (FP64 sum, FP32 out)
-cudaError_t decompose(const PointTables* t, int nt, const float* d_wav, const float* c2,
+// src_dcmp[t][id] = s(p_id) * sum_e w_e q_{s(e)}[t]  (FP64 sum, FP32 out) with
+// s = c2(p_id) = dt^2/m, or the constant `scale` when c2 is NULL
+cudaError_t decompose(const PointTables* t, int nt, const float* d_wav, const float* c2, double scale,
                       int n1, int n2, int n2p, float* d_dcmp, cudaStream_t st);
 cudaError_t finalize_traces(int nsteps, int nrec, const int* corner_id, const float* corner_w,
                             const float* rec_dcmp, int64_t nrpts, float* traces,

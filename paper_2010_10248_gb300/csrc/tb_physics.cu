@@ -1,0 +1,406 @@
+// One-step propagators of the other two wave equations of Sec. III:
+//
+//   TTI pseudo-acoustic (Sec. III-B, Eq. 2): two fields p, r,
+//     m p_tt = (1 + 2 eps) H_h p + sqrt(1 + 2 delta) H_z r
+//     m r_tt = sqrt(1 + 2 delta) H_h p + H_z r
+//   with H_z r = div(zbar (zbar . grad r)) and H_h p = div(grad p - zbar
+//   (zbar . grad p)), grad and div the centred first derivative of order so
+//   (fields and fluxes zero outside the grid), zbar = (sin t cos f,
+//   sin t sin f, cos t) the symmetry axis of the frame that Eq. 2's rotated
+//   derivative belongs to; H_h is -(D_xbar^T D_xbar + D_ybar^T D_ybar)
+//   rewritten with the frame's orthonormality (xbar xbar^T + ybar ybar^T =
+//   I - zbar zbar^T).  Two kernels per step: the fluxes F = grad p - zbar
+//   (zbar . grad p) and G = zbar (zbar . grad r), then their divergences and
+//   the leapfrog update of both fields (same damping and increment form as
+//   the acoustic kernel).
+//
+//   Isotropic elastic velocity-stress (Sec. III-C, Eq. 3) on the staggered
+//   grid: a velocity kernel (v += dt b div tau) and a stress kernel (tau +=
+//   dt (lam tr(e) I + 2 mu e)), each value divided by 1 + eta dt (sponge).
+//
+// Both stream along axis 0: a thread owns one (y, z) column of a chunk of
+// planes and keeps the axis-0 neighbours of its column in a register queue;
+// axis-1 and axis-2 neighbours come through the L1 cache.  Source injection
+// (grid-aligned table of Sec. II-A) and receiver sampling are separate small
+// kernels after the update of each step.
+#include <cstdint>
+
+#include "tb_internal.cuh"
+
+namespace tbi {
+
+static unsigned grid_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// Column of a thread: z fastest (coalesced), y from blockIdx.y / threadIdx.y.
+struct Col {
+  int y, z;
+  bool ok;
+};
+__device__ __forceinline__ Col thread_col(const PhysGrid& g) {
+  Col c;
+  c.z = blockIdx.x * blockDim.x + threadIdx.x;
+  c.y = blockIdx.y * blockDim.y + threadIdx.y;
+  c.ok = c.z < g.n2 && c.y < g.n1;
+  return c;
+}
+__device__ __forceinline__ size_t pidx(const PhysGrid& g, int x, int y, int z) {
+  return ((size_t)x * g.n1 + y) * g.n2p + z;
+}
+// value of a padded field at (x, y, z), zero outside the grid
+__device__ __forceinline__ float ld0(const PhysGrid& g, const float* __restrict__ f, int x, int y, int z) {
+  return (x >= 0 && x < g.n0 && y >= 0 && y < g.n1 && z >= 0 && z < g.n2) ? __ldg(f + pidx(g, x, y, z)) : 0.f;
+}
+
+// ------------------------------------------------------------------ TTI --
+// centred first derivative along axis 1 / 2 at (x, y, z): sum_i a_i (f_{+i} - f_{-i})
+template <int R>
+__device__ __forceinline__ float dc_y(const PhysGrid& g, const float* f, const float* a, int x, int y, int z) {
+  float s = 0.f;
+#pragma unroll
+  for (int i = R; i >= 1; --i) s = __fmaf_rn(a[i - 1], __fsub_rn(ld0(g, f, x, y + i, z), ld0(g, f, x, y - i, z)), s);
+  return s;
+}
+template <int R>
+__device__ __forceinline__ float dc_z(const PhysGrid& g, const float* f, const float* a, int x, int y, int z) {
+  float s = 0.f;
+#pragma unroll
+  for (int i = R; i >= 1; --i) s = __fmaf_rn(a[i - 1], __fsub_rn(ld0(g, f, x, y, z + i), ld0(g, f, x, y, z - i)), s);
+  return s;
+}
+template <int R>
+__device__ __forceinline__ float dc_q(const float* q, const float* a) {  // q[R] is the centre
+  float s = 0.f;
+#pragma unroll
+  for (int i = R; i >= 1; --i) s = __fmaf_rn(a[i - 1], __fsub_rn(q[R + i], q[R - i]), s);
+  return s;
+}
+
+// pass 1: F = grad p - zbar (zbar . grad p), G = zbar (zbar . grad r) on
+// planes [x0, x1) of every column
+template <int R>
+__global__ void __launch_bounds__(256) k_tti_flux(PhysGrid g, DerivW w, int x0, int x1, const float* __restrict__ p,
+                                                  const float* __restrict__ r, const float* __restrict__ nz,
+                                                  float* __restrict__ flux) {
+  const Col c = thread_col(g);
+  if (!c.ok) return;
+  const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
+  float qp[2 * R + 1], qr[2 * R + 1];
+#pragma unroll
+  for (int s = 0; s < 2 * R + 1; ++s) {  // planes x0-1-R .. x0-1+R before the first shift
+    qp[s] = ld0(g, p, x0 - 1 - R + s, c.y, c.z);
+    qr[s] = ld0(g, r, x0 - 1 - R + s, c.y, c.z);
+  }
+  for (int x = x0; x < x1; ++x) {
+#pragma unroll
+    for (int s = 0; s < 2 * R; ++s) {
+      qp[s] = qp[s + 1];
+      qr[s] = qr[s + 1];
+    }
+    qp[2 * R] = ld0(g, p, x + R, c.y, c.z);
+    qr[2 * R] = ld0(g, r, x + R, c.y, c.z);
+    const size_t i0 = pidx(g, x, c.y, c.z);
+    const float gp0 = dc_q<R>(qp, w.a[0]), gp1 = dc_y<R>(g, p, w.a[1], x, c.y, c.z),
+                gp2 = dc_z<R>(g, p, w.a[2], x, c.y, c.z);
+    const float gr0 = dc_q<R>(qr, w.a[0]), gr1 = dc_y<R>(g, r, w.a[1], x, c.y, c.z),
+                gr2 = dc_z<R>(g, r, w.a[2], x, c.y, c.z);
+    const float n0 = __ldg(nz + i0), n1 = __ldg(nz + Np + i0), n2 = __ldg(nz + 2 * Np + i0);
+    const float sp = __fmaf_rn(n2, gp2, __fmaf_rn(n1, gp1, __fmul_rn(n0, gp0)));
+    const float sr = __fmaf_rn(n2, gr2, __fmaf_rn(n1, gr1, __fmul_rn(n0, gr0)));
+    flux[i0] = __fmaf_rn(-n0, sp, gp0);
+    flux[Np + i0] = __fmaf_rn(-n1, sp, gp1);
+    flux[2 * Np + i0] = __fmaf_rn(-n2, sp, gp2);
+    flux[3 * Np + i0] = __fmul_rn(n0, sr);
+    flux[4 * Np + i0] = __fmul_rn(n1, sr);
+    flux[5 * Np + i0] = __fmul_rn(n2, sr);
+  }
+}
+
+// pass 2: H_h p = div F, H_z r = div G; leapfrog update of p and r written
+// over p^{n-1}, r^{n-1}
+template <int R>
+__global__ void __launch_bounds__(256) k_tti_update(PhysGrid g, DerivW w, int x0, int x1, const float* __restrict__ flux,
+                                                    const float* __restrict__ pc, float* pp, const float* __restrict__ rc,
+                                                    float* rp, const float* __restrict__ c2,
+                                                    const float* __restrict__ coef, const float* __restrict__ damp_b) {
+  const Col c = thread_col(g);
+  if (!c.ok) return;
+  const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
+  const float* F0 = flux;
+  const float* G0 = flux + 3 * Np;
+  float qf[2 * R + 1], qg[2 * R + 1];
+#pragma unroll
+  for (int s = 0; s < 2 * R + 1; ++s) {
+    qf[s] = ld0(g, F0, x0 - 1 - R + s, c.y, c.z);
+    qg[s] = ld0(g, G0, x0 - 1 - R + s, c.y, c.z);
+  }
+  const float byz = __fadd_rn(__ldg(damp_b + g.n0 + c.y), __ldg(damp_b + g.n0 + g.n1 + c.z));
+  for (int x = x0; x < x1; ++x) {
+#pragma unroll
+    for (int s = 0; s < 2 * R; ++s) {
+      qf[s] = qf[s + 1];
+      qg[s] = qg[s + 1];
+    }
+    qf[2 * R] = ld0(g, F0, x + R, c.y, c.z);
+    qg[2 * R] = ld0(g, G0, x + R, c.y, c.z);
+    const size_t i0 = pidx(g, x, c.y, c.z);
+    const float hh = __fadd_rn(__fadd_rn(dc_q<R>(qf, w.a[0]), dc_y<R>(g, flux + Np, w.a[1], x, c.y, c.z)),
+                               dc_z<R>(g, flux + 2 * Np, w.a[2], x, c.y, c.z));
+    const float hz = __fadd_rn(__fadd_rn(dc_q<R>(qg, w.a[0]), dc_y<R>(g, flux + 4 * Np, w.a[1], x, c.y, c.z)),
+                               dc_z<R>(g, flux + 5 * Np, w.a[2], x, c.y, c.z));
+    const float cpp = __ldg(coef + i0), cpr = __ldg(coef + Np + i0);
+    const float rhs_p = __fmaf_rn(cpp, hh, __fmul_rn(cpr, hz));
+    const float rhs_r = __fmaf_rn(cpr, hh, hz);
+    const float c2v = __ldg(c2 + i0);
+    const float gdamp = __fmul_rn(__fadd_rn(__ldg(damp_b + x), byz), c2v);
+    const float opg = __fadd_rn(1.f, gdamp), omg = __fsub_rn(1.f, gdamp);
+    const float up = pc[i0], upp = pp[i0], ur = rc[i0], urp = rp[i0];
+    pp[i0] = __fadd_rn(up, __fdiv_rn(__fmaf_rn(c2v, rhs_p, __fmul_rn(omg, __fsub_rn(up, upp))), opg));
+    rp[i0] = __fadd_rn(ur, __fdiv_rn(__fmaf_rn(c2v, rhs_r, __fmul_rn(omg, __fsub_rn(ur, urp))), opg));
+  }
+}
+
+// ------------------------------------------------------------- elastic --
+// node -> half-node: sum_k c_k (f[i+k] - f[i-k+1]); half-node -> node:
+// sum_k c_k (f[i+k-1] - f[i-k]), along axis d at (x, y, z)
+template <int R, int D>
+__device__ __forceinline__ float dstag(const PhysGrid& g, const float* f, const float* cw, int x, int y, int z,
+                                       bool plus) {
+  float s = 0.f;
+#pragma unroll
+  for (int k = R; k >= 1; --k) {
+    const int hi = plus ? k : k - 1, lo = plus ? -(k - 1) : -k;
+    const float a = D == 0 ? ld0(g, f, x + hi, y, z) : (D == 1 ? ld0(g, f, x, y + hi, z) : ld0(g, f, x, y, z + hi));
+    const float b = D == 0 ? ld0(g, f, x + lo, y, z) : (D == 1 ? ld0(g, f, x, y + lo, z) : ld0(g, f, x, y, z + lo));
+    s = __fmaf_rn(cw[k - 1], __fsub_rn(a, b), s);
+  }
+  return s;
+}
+
+// fields: [9][Np] vx vy vz txx tyy tzz txy txz tyz; mat: [8][Np] bx by bz lam mu mxy mxz myz
+template <int R>
+__global__ void __launch_bounds__(256) k_ela_velocity(PhysGrid g, DerivW w, float dt, float* __restrict__ f,
+                                                      const float* __restrict__ mat, const float* __restrict__ eta_dt) {
+  const Col c = thread_col(g);
+  if (!c.ok) return;
+  const int x = blockIdx.z;
+  const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
+  const size_t i0 = pidx(g, x, c.y, c.z);
+  const float *txx = f + 3 * Np, *tyy = f + 4 * Np, *tzz = f + 5 * Np, *txy = f + 6 * Np, *txz = f + 7 * Np,
+              *tyz = f + 8 * Np;
+  const float fx = __fadd_rn(__fadd_rn(dstag<R, 0>(g, txx, w.a[0], x, c.y, c.z, true),
+                                       dstag<R, 1>(g, txy, w.a[1], x, c.y, c.z, false)),
+                             dstag<R, 2>(g, txz, w.a[2], x, c.y, c.z, false));
+  const float fy = __fadd_rn(__fadd_rn(dstag<R, 0>(g, txy, w.a[0], x, c.y, c.z, false),
+                                       dstag<R, 1>(g, tyy, w.a[1], x, c.y, c.z, true)),
+                             dstag<R, 2>(g, tyz, w.a[2], x, c.y, c.z, false));
+  const float fz = __fadd_rn(__fadd_rn(dstag<R, 0>(g, txz, w.a[0], x, c.y, c.z, false),
+                                       dstag<R, 1>(g, tyz, w.a[1], x, c.y, c.z, false)),
+                             dstag<R, 2>(g, tzz, w.a[2], x, c.y, c.z, true));
+  const float den = __fadd_rn(1.f, __fadd_rn(__fadd_rn(__ldg(eta_dt + x), __ldg(eta_dt + g.n0 + c.y)),
+                                            __ldg(eta_dt + g.n0 + g.n1 + c.z)));
+  f[i0] = __fdiv_rn(__fmaf_rn(__fmul_rn(dt, __ldg(mat + i0)), fx, f[i0]), den);
+  f[Np + i0] = __fdiv_rn(__fmaf_rn(__fmul_rn(dt, __ldg(mat + Np + i0)), fy, f[Np + i0]), den);
+  f[2 * Np + i0] = __fdiv_rn(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 2 * Np + i0)), fz, f[2 * Np + i0]), den);
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_ela_stress(PhysGrid g, DerivW w, float dt, float* __restrict__ f,
+                                                    const float* __restrict__ mat, const float* __restrict__ eta_dt) {
+  const Col c = thread_col(g);
+  if (!c.ok) return;
+  const int x = blockIdx.z;
+  const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
+  const size_t i0 = pidx(g, x, c.y, c.z);
+  const float *vx = f, *vy = f + Np, *vz = f + 2 * Np;
+  const float exx = dstag<R, 0>(g, vx, w.a[0], x, c.y, c.z, false);
+  const float eyy = dstag<R, 1>(g, vy, w.a[1], x, c.y, c.z, false);
+  const float ezz = dstag<R, 2>(g, vz, w.a[2], x, c.y, c.z, false);
+  const float gxy = __fadd_rn(dstag<R, 1>(g, vx, w.a[1], x, c.y, c.z, true), dstag<R, 0>(g, vy, w.a[0], x, c.y, c.z, true));
+  const float gxz = __fadd_rn(dstag<R, 2>(g, vx, w.a[2], x, c.y, c.z, true), dstag<R, 0>(g, vz, w.a[0], x, c.y, c.z, true));
+  const float gyz = __fadd_rn(dstag<R, 2>(g, vy, w.a[2], x, c.y, c.z, true), dstag<R, 1>(g, vz, w.a[1], x, c.y, c.z, true));
+  const float lam = __ldg(mat + 3 * Np + i0), mu = __ldg(mat + 4 * Np + i0);
+  const float ltr = __fmul_rn(lam, __fadd_rn(__fadd_rn(exx, eyy), ezz));
+  const float den = __fadd_rn(1.f, __fadd_rn(__fadd_rn(__ldg(eta_dt + x), __ldg(eta_dt + g.n0 + c.y)),
+                                            __ldg(eta_dt + g.n0 + g.n1 + c.z)));
+  const float mu2 = __fmul_rn(2.f, mu);
+  f[3 * Np + i0] = __fdiv_rn(__fmaf_rn(dt, __fmaf_rn(mu2, exx, ltr), f[3 * Np + i0]), den);
+  f[4 * Np + i0] = __fdiv_rn(__fmaf_rn(dt, __fmaf_rn(mu2, eyy, ltr), f[4 * Np + i0]), den);
+  f[5 * Np + i0] = __fdiv_rn(__fmaf_rn(dt, __fmaf_rn(mu2, ezz, ltr), f[5 * Np + i0]), den);
+  f[6 * Np + i0] = __fdiv_rn(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 5 * Np + i0)), gxy, f[6 * Np + i0]), den);
+  f[7 * Np + i0] = __fdiv_rn(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 6 * Np + i0)), gxz, f[7 * Np + i0]), den);
+  f[8 * Np + i0] = __fdiv_rn(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 7 * Np + i0)), gyz, f[8 * Np + i0]), den);
+}
+
+// material at the staggered positions from vp, vs, rho (dense [N]):
+// b = 1/rho at half-nodes (mean of two nodes), lam, mu at nodes, mu at edge
+// centres (harmonic mean of four nodes, 0 if one is 0); a neighbour past
+// the last node takes the last node's value
+__global__ void k_ela_material(PhysGrid g, const float* __restrict__ vp, const float* __restrict__ vs,
+                               const float* __restrict__ rho, float* __restrict__ mat, int* bad) {
+  const Col c = thread_col(g);
+  if (!c.ok) return;
+  const int x = blockIdx.z;
+  const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
+  auto di = [&](int xx, int yy, int zz) { return ((size_t)xx * g.n1 + yy) * g.n2 + zz; };
+  const int x1 = min(x + 1, g.n0 - 1), y1 = min(c.y + 1, g.n1 - 1), z1 = min(c.z + 1, g.n2 - 1);
+  auto mu_at = [&](int xx, int yy, int zz) {
+    const double r = rho[di(xx, yy, zz)], s = vs[di(xx, yy, zz)];
+    return r * s * s;
+  };
+  auto harm4 = [](double a, double b, double cc, double d) {
+    if (a <= 0 || b <= 0 || cc <= 0 || d <= 0) return 0.0;
+    return 4.0 / (1.0 / a + 1.0 / b + 1.0 / cc + 1.0 / d);
+  };
+  const size_t q = di(x, c.y, c.z);
+  const double r0 = rho[q], p0 = vp[q], s0 = vs[q];
+  if (!(r0 > 0) || !(p0 > 0) || !(s0 >= 0) || !(2.0 * s0 * s0 <= p0 * p0) || !isfinite(r0 + p0 + s0)) atomicExch(bad, 1);
+  const size_t i0 = pidx(g, x, c.y, c.z);
+  mat[i0] = (float)(0.5 * (1.0 / r0 + 1.0 / (double)rho[di(x1, c.y, c.z)]));
+  mat[Np + i0] = (float)(0.5 * (1.0 / r0 + 1.0 / (double)rho[di(x, y1, c.z)]));
+  mat[2 * Np + i0] = (float)(0.5 * (1.0 / r0 + 1.0 / (double)rho[di(x, c.y, z1)]));
+  mat[3 * Np + i0] = (float)(r0 * (p0 * p0 - 2.0 * s0 * s0));
+  const double m00 = mu_at(x, c.y, c.z);
+  mat[4 * Np + i0] = (float)m00;
+  mat[5 * Np + i0] = (float)harm4(m00, mu_at(x1, c.y, c.z), mu_at(x, y1, c.z), mu_at(x1, y1, c.z));
+  mat[6 * Np + i0] = (float)harm4(m00, mu_at(x1, c.y, c.z), mu_at(x, c.y, z1), mu_at(x1, c.y, z1));
+  mat[7 * Np + i0] = (float)harm4(m00, mu_at(x, y1, c.z), mu_at(x, c.y, z1), mu_at(x, y1, z1));
+}
+
+// TTI coefficients from eps, delta, theta, phi (dense [N]): 1 + 2 eps,
+// sqrt(1 + 2 delta) and zbar; eps < delta (or delta <= -1/2) flags bad
+__global__ void k_tti_coef(PhysGrid g, const float* __restrict__ aux, float* __restrict__ coef,
+                           float* __restrict__ nz, unsigned* emax_bits, int* bad) {
+  const Col c = thread_col(g);
+  if (!c.ok) return;
+  const int x = blockIdx.z;
+  const size_t N = (size_t)g.n0 * g.n1 * g.n2, Np = (size_t)g.n0 * g.n1 * g.n2p;
+  const size_t q = ((size_t)x * g.n1 + c.y) * g.n2 + c.z;
+  const double e = aux[q], d = aux[N + q], th = aux[2 * N + q], ph = aux[3 * N + q];
+  if (!(e >= d) || !(d > -0.5) || !isfinite(e + d + th + ph)) atomicExch(bad, 1);
+  const size_t i0 = pidx(g, x, c.y, c.z);
+  coef[i0] = (float)(1.0 + 2.0 * e);
+  coef[Np + i0] = (float)sqrt(1.0 + 2.0 * d);
+  nz[i0] = (float)(sin(th) * cos(ph));
+  nz[Np + i0] = (float)(sin(th) * sin(ph));
+  nz[2 * Np + i0] = (float)cos(th);
+  if (e > 0) atomicMax(emax_bits, __float_as_uint((float)e));  // non-negative floats order as their bits
+}
+
+// ------------------------------------------------- sparse operators --
+// grid-aligned injection: f_k[lin(id)] += dcmp[id] for the fields f_k
+__global__ void k_inject(PhysGrid g, int64_t npts, const int64_t* __restrict__ lin,
+                         const float* __restrict__ dcmp, float* f0, float* f1, float* f2) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= npts) return;
+  const int64_t l = lin[id];
+  const int z = (int)(l % g.n2), y = (int)((l / g.n2) % g.n1), x = (int)(l / ((int64_t)g.n1 * g.n2));
+  const size_t i0 = pidx(g, x, y, z);
+  const float a = dcmp[id];
+  if (f0) f0[i0] = __fadd_rn(f0[i0], a);
+  if (f1) f1[i0] = __fadd_rn(f1[i0], a);
+  if (f2) f2[i0] = __fadd_rn(f2[i0], a);
+}
+
+// receiver sampling: row[e] = value at the point of entry e (entries in
+// column order, as the trace finalisation expects); mean of up to three
+// fields (the normal stresses) or one field
+__global__ void k_sample(PhysGrid g, int64_t npts, const int2* __restrict__ ent, const int64_t* __restrict__ lin,
+                         const float* f0, const float* f1, const float* f2, float* __restrict__ row) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= npts) return;
+  const int64_t l = lin[ent[e].y];
+  const int z = (int)(l % g.n2), y = (int)((l / g.n2) % g.n1), x = (int)(l / ((int64_t)g.n1 * g.n2));
+  const size_t i0 = pidx(g, x, y, z);
+  float v = f0[i0];
+  if (f1) v = __fdiv_rn(__fadd_rn(__fadd_rn(v, f1[i0]), f2[i0]), 3.f);
+  row[e] = v;
+}
+
+// ------------------------------------------------------------- launch --
+static dim3 col_grid(const PhysGrid& g, int nz_planes) {
+  return dim3((unsigned)((g.n2 + 31) / 32), (unsigned)((g.n1 + 7) / 8), (unsigned)nz_planes);
+}
+
+template <int R>
+static cudaError_t tti_step_r(const PhysGrid& g, const DerivW& w, int nchunks, const float* pc, float* pp,
+                              const float* rc, float* rp, const float* c2, const float* coef, const float* nz,
+                              const float* damp_b, float* flux, cudaStream_t st) {
+  // chunks of planes: each column streams its chunk (the queue warms up on
+  // R planes before the chunk)
+  const dim3 blk(32, 8);
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int cidx = 0; cidx < nchunks; ++cidx) {
+      const int x0 = (int)((int64_t)g.n0 * cidx / nchunks), x1 = (int)((int64_t)g.n0 * (cidx + 1) / nchunks);
+      if (x1 <= x0) continue;
+      count_launch();
+      if (pass == 0)
+        k_tti_flux<R><<<col_grid(g, 1), blk, 0, st>>>(g, w, x0, x1, pc, rc, nz, flux);
+      else
+        k_tti_update<R><<<col_grid(g, 1), blk, 0, st>>>(g, w, x0, x1, flux, pc, pp, rc, rp, c2, coef, damp_b);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t tti_step(int R, const PhysGrid& g, const DerivW& w, int nchunks, const float* pc, float* pp,
+                     const float* rc, float* rp, const float* c2, const float* coef, const float* nz,
+                     const float* damp_b, float* flux, cudaStream_t st) {
+  switch (R) {
+    case 2: return tti_step_r<2>(g, w, nchunks, pc, pp, rc, rp, c2, coef, nz, damp_b, flux, st);
+    case 4: return tti_step_r<4>(g, w, nchunks, pc, pp, rc, rp, c2, coef, nz, damp_b, flux, st);
+    case 6: return tti_step_r<6>(g, w, nchunks, pc, pp, rc, rp, c2, coef, nz, damp_b, flux, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int R>
+static cudaError_t ela_step_r(const PhysGrid& g, const DerivW& w, float dt, float* f, const float* mat,
+                              const float* eta_dt, cudaStream_t st) {
+  const dim3 blk(32, 8);
+  count_launch(2);
+  k_ela_velocity<R><<<col_grid(g, g.n0), blk, 0, st>>>(g, w, dt, f, mat, eta_dt);
+  k_ela_stress<R><<<col_grid(g, g.n0), blk, 0, st>>>(g, w, dt, f, mat, eta_dt);
+  return cudaGetLastError();
+}
+
+cudaError_t elastic_step(int R, const PhysGrid& g, const DerivW& w, float dt, float* f, const float* mat,
+                         const float* eta_dt, cudaStream_t st) {
+  switch (R) {
+    case 2: return ela_step_r<2>(g, w, dt, f, mat, eta_dt, st);
+    case 4: return ela_step_r<4>(g, w, dt, f, mat, eta_dt, st);
+    case 6: return ela_step_r<6>(g, w, dt, f, mat, eta_dt, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t elastic_material(const PhysGrid& g, const float* vp, const float* vs, const float* rho, float* mat,
+                             int* d_bad, cudaStream_t st) {
+  count_launch();
+  k_ela_material<<<col_grid(g, g.n0), dim3(32, 8), 0, st>>>(g, vp, vs, rho, mat, d_bad);
+  return cudaGetLastError();
+}
+
+cudaError_t tti_coefficients(const PhysGrid& g, const float* aux, float* coef, float* nz, unsigned* d_emax,
+                             int* d_bad, cudaStream_t st) {
+  count_launch();
+  k_tti_coef<<<col_grid(g, g.n0), dim3(32, 8), 0, st>>>(g, aux, coef, nz, d_emax, d_bad);
+  return cudaGetLastError();
+}
+
+cudaError_t inject_points(const PhysGrid& g, int64_t npts, const int64_t* lin, const float* dcmp_row, float* f0,
+                          float* f1, float* f2, cudaStream_t st) {
+  if (npts <= 0) return cudaSuccess;
+  count_launch();
+  k_inject<<<grid_for(npts, 128), 128, 0, st>>>(g, npts, lin, dcmp_row, f0, f1, f2);
+  return cudaGetLastError();
+}
+
+cudaError_t sample_points(const PhysGrid& g, int64_t npts, const int2* ent, const int64_t* lin, const float* f0,
+                          const float* f1, const float* f2, float* row, cudaStream_t st) {
+  if (npts <= 0) return cudaSuccess;
+  count_launch();
+  k_sample<<<grid_for(npts, 128), 128, 0, st>>>(g, npts, ent, lin, f0, f1, f2, row);
+  return cudaGetLastError();
+}
+
+}  // namespace tbi

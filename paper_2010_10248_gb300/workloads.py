@@ -164,3 +164,64 @@ def acoustic_512_so8(seed: int = BASE_SEED + 1, shape=(512, 512, 512), nt: int =
     vp = layered_vp(shape, seed + 4)
     return Workload(f"acoustic {shape[0]}x{shape[1]}x{shape[2]} so8 {nt} steps", tuple(shape), h,
                     8, nt, nbl, 15.0, vp, src, rec)
+
+
+def smooth_field(shape, seed: int, lo: float, hi: float, coarse: int = 6) -> np.ndarray:
+    """Seeded smooth random field in [lo, hi]: uniform noise on a coarse
+    (coarse x coarse x coarse) lattice, linearly interpolated to the grid."""
+    g = rng(seed)
+    c = g.uniform(0.0, 1.0, size=(coarse, coarse, coarse))
+    out = c
+    for ax, n in enumerate(shape):
+        t = np.linspace(0.0, coarse - 1, int(n))
+        i0 = np.clip(np.floor(t).astype(int), 0, coarse - 2)
+        f = (t - i0).astype(np.float64)
+        a = np.take(out, i0, axis=ax)
+        b = np.take(out, i0 + 1, axis=ax)
+        sh = [1, 1, 1]
+        sh[ax] = int(n)
+        out = a * (1.0 - f.reshape(sh)) + b * f.reshape(sh)
+    return (lo + (hi - lo) * out).astype(np.float32)
+
+
+def tti_384_so8(seed: int = BASE_SEED + 2, shape=(384, 384, 384), nt: int = 500,
+                nbl: int = 30) -> Workload:
+    """TTI 384^3, h = 20 m (the paper's TTI spacing), so8, 500 steps: layered
+    vp, smooth seeded eps in [0, 0.3], delta in [0, 0.2] with delta <= eps,
+    tilt and azimuth in [0, 45 deg]; one 10 Hz Ricker near the top; 128 x 128
+    receiver plane.  meta["aux"] holds (eps, delta, theta, phi)."""
+    h = (20.0, 20.0, 20.0)
+    g = rng(seed + 7)
+    src = np.array([[(0.5 * (shape[0] - 1) + g.uniform(-0.5, 0.5)) * h[0],
+                     (0.5 * (shape[1] - 1) + g.uniform(-0.5, 0.5)) * h[1],
+                     (nbl + 10 + g.uniform(0.05, 0.95)) * h[2]]])
+    rec = receiver_plane(shape, h, seed + 3, min(128, (shape[0] - 1) // 2),
+                         min(128, (shape[1] - 1) // 2), depth_cells=nbl + 20)
+    vp = layered_vp(shape, seed + 4)
+    eps = smooth_field(shape, seed + 5, 0.0, 0.3)
+    delta = np.minimum(smooth_field(shape, seed + 6, 0.0, 0.2), eps)
+    deg = math.pi / 180.0
+    theta = smooth_field(shape, seed + 8, 0.0, 45.0 * deg)
+    phi = smooth_field(shape, seed + 9, 0.0, 45.0 * deg)
+    return Workload(f"tti {shape[0]}x{shape[1]}x{shape[2]} so8 {nt} steps", tuple(shape), h, 8, nt,
+                    nbl, 10.0, vp, src, rec, meta={"aux": (eps, delta, theta, phi)})
+
+
+def elastic_384_so8(seed: int = BASE_SEED + 3, shape=(384, 384, 384), nt: int = 500,
+                    nbl: int = 30) -> Workload:
+    """Isotropic elastic 384^3, h = 10 m, so8, 500 steps: layered vp,
+    vs = vp / 1.7, layered density 1.0-2.5 (same interfaces as vp); one 15 Hz
+    explosive Ricker near the top; 128 x 128 receiver plane.  meta["aux"]
+    holds (vs, rho)."""
+    h = (10.0, 10.0, 10.0)
+    g = rng(seed + 7)
+    src = np.array([[(0.5 * (shape[0] - 1) + g.uniform(-0.5, 0.5)) * h[0],
+                     (0.5 * (shape[1] - 1) + g.uniform(-0.5, 0.5)) * h[1],
+                     (nbl + 10 + g.uniform(0.05, 0.95)) * h[2]]])
+    rec = receiver_plane(shape, h, seed + 3, min(128, (shape[0] - 1) // 2),
+                         min(128, (shape[1] - 1) // 2), depth_cells=nbl + 20)
+    vp = layered_vp(shape, seed + 4, nblobs=0)
+    vs = (vp / 1.7).astype(np.float32)
+    rho = (1.0 + (vp - 1500.0) / 3000.0 * 1.5).astype(np.float32)
+    return Workload(f"elastic {shape[0]}x{shape[1]}x{shape[2]} so8 {nt} steps", tuple(shape), h, 8, nt,
+                    nbl, 15.0, vp, src, rec, meta={"aux": (vs, rho)})

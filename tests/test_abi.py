@@ -62,6 +62,18 @@ def test_cfl_matches_oracle(lib, oracle_lib, so):
     assert _tb.tb_cfl_dt_max(4, (10.0, 10.0, 10.0), 1500.0) == pytest.approx(1 / 300, rel=1e-14)
 
 
+@pytest.mark.parametrize("so", [4, 8, 12])
+def test_tti_and_elastic_stability_limits_match_oracle(lib, oracle_lib, so):
+    """Both sides sample the same trigonometric symbol maximum (the oracle
+    densely, the library densely plus a golden-section refinement): agreement
+    to 1e-9; so4 elastic is the closed form 7/3 of the oracle pins."""
+    for h, v, e in (((10.0, 10.0, 10.0), 4500.0, 0.3), ((20.0, 10.0, 15.0), 1500.0, 0.0)):
+        assert _tb.tb_tti_dt_max(so, h, v, e) == pytest.approx(oracle.tti_dt_max(so, h, v, e), rel=1e-9)
+        assert _tb.tb_elastic_dt_max(so, h, v) == pytest.approx(oracle.elastic_dt_max(so, h, v), rel=1e-9)
+    assert _tb.tb_tti_dt_max(so, (10.0,) * 3, 3000.0, 0.1) < _tb.tb_tti_dt_max(so, (10.0,) * 3, 3000.0, 0.0)
+    assert _tb.tb_elastic_dt_max(so, (10.0, 10.0, 0.0), 3000.0) == -1.0
+
+
 def test_sponge_matches_oracle(lib, oracle_lib):
     for n, nbl, h, v in ((64, 10, 10.0, 1500.0), (512, 40, 10.0, 4500.0), (30, 0, 5.0, 2000.0)):
         np.testing.assert_allclose(_tb.tb_sponge_profile(n, nbl, h, v),

@@ -1,0 +1,136 @@
+"""GPU parity of the TTI (Sec. III-B, Eq. 2) and elastic (Sec. III-C, Eq. 3)
+one-step propagators against the FP64 oracle, through the C ABI.
+
+Tolerance: rel-L2 <= 1e-4 on receiver traces and wavefields (FP32 against
+FP64), as for the acoustic path."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_10248_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def tb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2010_10248_gb300 as tb
+    tb.load()
+    return tb
+
+
+def geometry(shape, h, seed, nrec=24):
+    g = np.random.default_rng(seed)
+    ext = np.array([(shape[d] - 1) * h[d] for d in range(3)])
+    src = (g.uniform(0.35, 0.65, size=(1, 3)) * ext)
+    rec = g.uniform(0.1, 0.9, size=(nrec, 3)) * ext
+    rec[:4, 0] = 0.0            # receivers on the low faces
+    rec[4:6, 2] = ext[2]        # and on the high face (upper-edge clamp)
+    return src, rec
+
+
+def tti_case(shape, so, seed, nt):
+    h = (12.0, 10.0, 11.0)
+    vp = wl.layered_vp(shape, seed, vmin=1500.0, vmax=2500.0, nlayers=4, nblobs=4)
+    eps = wl.smooth_field(shape, seed + 1, 0.05, 0.3)
+    delta = np.minimum(wl.smooth_field(shape, seed + 2, 0.0, 0.2), eps)
+    theta = wl.smooth_field(shape, seed + 3, 0.0, math.pi / 4)
+    phi = wl.smooth_field(shape, seed + 4, -0.3, math.pi / 4)
+    src, rec = geometry(shape, h, seed + 5)
+    return h, vp, (eps, delta, theta, phi), src, rec
+
+
+@pytest.mark.parametrize("shape,so,nt", [((30, 33, 40), 4, 70), ((28, 31, 37), 8, 60),
+                                         ((30, 29, 35), 12, 40)])
+def test_tti_matches_oracle(tb, shape, so, nt):
+    import torch
+    h, vp, aux, src, rec = tti_case(shape, so, 101 + so, nt)
+    p = tb.Propagator(shape, h, so, physics=tb.TB_TTI, nbl=5)
+    p.set_model(torch.from_numpy(vp).cuda(), aux=np.stack(aux))
+    dt = p.dt
+    assert dt == pytest.approx(0.8 * oracle.tti_dt_max(so, h, float(vp.max()), float(aux[0].max())),
+                               rel=1e-5)
+    wav = wl.ricker(30.0, dt, nt, t0=8 * dt)[None, :].astype(np.float32)
+    p.set_sources(src, wav)
+    p.set_receivers(rec)
+    tr = p.forward(nt).cpu().numpy()
+    tr_o, st_o = oracle.tti_forward(shape, h, so, dt, nt, vp.astype(np.float64),
+                                    *[a.astype(np.float64) for a in aux], nbl=5,
+                                    src_xyz=src, src_wav=wav.astype(np.float64), rec_xyz=rec)
+    e_tr = rel_l2(tr, tr_o)
+    fields = [p.field(i).cpu().numpy() for i in range(4)]
+    e_f = [rel_l2(f, st_o[i]) for i, f in enumerate(fields)]
+    print(f"TTI so{so}: traces rel-L2 {e_tr:.2e}, fields {[f'{x:.1e}' for x in e_f]}")
+    assert np.abs(tr_o).max() > 0
+    assert e_tr <= TOL
+    assert max(e_f) <= TOL
+
+
+def elastic_case(shape, so, seed):
+    h = (10.0, 11.0, 9.0)
+    vp = wl.layered_vp(shape, seed, vmin=2000.0, vmax=3500.0, nlayers=4, nblobs=4)
+    vs = (vp / wl.smooth_field(shape, seed + 1, 1.6, 2.0)).astype(np.float32)
+    rho = wl.smooth_field(shape, seed + 2, 1.0, 2.5)
+    src, rec = geometry(shape, h, seed + 5)
+    return h, vp, (vs, rho), src, rec
+
+
+@pytest.mark.parametrize("shape,so,nt", [((30, 33, 40), 4, 70), ((28, 31, 37), 8, 60),
+                                         ((30, 29, 35), 12, 40)])
+def test_elastic_matches_oracle(tb, shape, so, nt):
+    import torch
+    h, vp, aux, src, rec = elastic_case(shape, so, 201 + so)
+    p = tb.Propagator(shape, h, so, physics=tb.TB_ELASTIC, nbl=5)
+    p.set_model(torch.from_numpy(vp).cuda(), aux=np.stack(aux))
+    dt = p.dt
+    assert dt == pytest.approx(0.8 * oracle.elastic_dt_max(so, h, float(vp.max())), rel=1e-9)
+    wav = wl.ricker(40.0, dt, nt, t0=8 * dt)[None, :].astype(np.float32)
+    p.set_sources(src, wav)
+    p.set_receivers(rec)
+    tr = p.forward(nt).cpu().numpy()
+    tr_o, st_o = oracle.elastic_forward(shape, h, so, dt, nt, vp.astype(np.float64),
+                                        *[a.astype(np.float64) for a in aux], nbl=5, src_xyz=src,
+                                        src_wav=wav.astype(np.float64), rec_xyz=rec)
+    e_tr = rel_l2(tr, tr_o)
+    e_f = [rel_l2(p.field(i).cpu().numpy(), st_o[i]) for i in range(9)]
+    print(f"elastic so{so}: traces rel-L2 {e_tr:.2e}, fields {[f'{x:.1e}' for x in e_f]}")
+    assert np.abs(tr_o).max() > 0
+    assert e_tr <= TOL
+    assert max(e_f) <= TOL
+
+
+def test_tti_and_elastic_reject_blocked_and_bad_models(tb):
+    import torch
+    shape, h = (20, 20, 20), (10.0, 10.0, 10.0)
+    vp = torch.full(shape, 2000.0, device="cuda")
+    one = np.ones(shape, dtype=np.float32)
+    p = tb.Propagator(shape, h, 4, physics=tb.TB_TTI)
+    with pytest.raises(tb.TBError) as e:  # eps < delta
+        p.set_model(vp, aux=np.stack([0.05 * one, 0.1 * one, 0 * one, 0 * one]))
+    assert e.value.status == 4  # TB_EUNSTABLE
+    with pytest.raises(tb.TBError):  # aux required
+        p.set_model(vp)
+    p.set_model(vp, aux=np.stack([0.2 * one, 0.1 * one, 0 * one, 0 * one]))
+    with pytest.raises(tb.TBError) as e:
+        p.forward(4, schedule="blocked")
+    assert e.value.status == 1
+    q = tb.Propagator(shape, h, 4, physics=tb.TB_ELASTIC)
+    with pytest.raises(tb.TBError):  # vs too large (2 vs^2 > vp^2)
+        q.set_model(vp, aux=np.stack([1500.0 * one, one]))
+    with pytest.raises(tb.TBError):  # time_tile > 1 is acoustic only
+        tb.Propagator(shape, h, 4, physics=tb.TB_ELASTIC, time_tile=2)

@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--physics", default="acoustic", choices=["acoustic", "tti", "elastic"],
+                    help="tti / elastic: the 384^3 so8 500-step TTI or elastic workload, one-step "
+                         "schedule (the headline line is the acoustic one)")
     return ap.parse_args()
 
 
@@ -351,8 +354,93 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def run_physics(args):
+    """TTI or elastic one-step propagation of the 384^3 so8 workload (500
+    steps): one JSON line with GPts/s and the HBM roofline of the step."""
+    import torch
+    import paper_2010_10248_gb300 as tb
+    from paper_2010_10248_gb300 import build as tbbuild
+    from paper_2010_10248_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    tbbuild.build()
+    tb.load()
+    size = args.size if args.size != 512 else 384
+    nt = args.nt if args.nt != 1000 else 500
+    if args.physics == "tti":
+        w = wl.tti_384_so8(shape=(size,) * 3, nt=nt)
+        phys = tb.TB_TTI
+        # fused minimum per point and step: p, r at three levels (4 reads,
+        # 2 writes), m, eps, delta, theta, phi
+        alg_bytes = 44.0
+    else:
+        w = wl.elastic_384_so8(shape=(size,) * 3, nt=nt)
+        phys = tb.TB_ELASTIC
+        # fused minimum: 9 fields read and written, b, lam, mu
+        alg_bytes = 84.0
+    N = int(np.prod(w.shape))
+    dev = torch.device("cuda", 0)
+    vp = torch.from_numpy(w.vp).to(dev)
+    aux = torch.from_numpy(np.stack(w.meta["aux"])).to(dev)
+    prop = tb.Propagator(w.shape, w.spacing, w.so, physics=phys, nbl=w.nbl, profile=True)
+    st = torch.cuda.current_stream()
+    prop.set_model(vp, aux=aux)
+    dt = prop.dt
+    wav = torch.from_numpy(w.wavelets(dt).astype(np.float32)).to(dev)
+    src = torch.from_numpy(w.src_xyz).to(dev)
+    rec = torch.from_numpy(w.rec_xyz).to(dev)
+    traces = torch.empty((nt, len(w.rec_xyz)), dtype=torch.float32, device=dev)
+
+    def shot():
+        tb.tb_set_model(prop.h, vp, aux, None, 0.0, st)
+        tb.tb_set_sources(prop.h, len(w.src_xyz), src, nt, wav, st)
+        tb.tb_set_receivers(prop.h, len(w.rec_xyz), rec, st)
+        tb.tb_forward(prop.h, nt, traces, tb.TB_ONESTEP, st)
+
+    for _ in range(args.warmup):
+        shot()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = tb.tb_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms, kn = 0.0, 0
+    e0.record(st)
+    for _ in range(args.steps):
+        shot()
+        n, ms = prop.kernel_time(0)
+        kms += ms
+        kn += n
+    e1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    value = N * nt / (ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    step_ms = kms / max(kn, 1)
+    achieved = alg_bytes * N / (step_ms * 1e-3) / 1e9
+    finite = bool(torch.isfinite(traces).all().item())
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.shape), "space_order": w.so, "nt": nt,
+                       "receivers": len(w.rec_xyz), "schedule": "onestep",
+                       "l2": "inputs larger than L2",
+                       "step": "set_model + set_sources + set_receivers + forward(nt)"},
+            "gpu_launches": int(tb.tb_launch_count() - l0), "clocks": clk,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                         "kernel": f"{args.physics} step (all kernels of one time step)",
+                         "bytes_per_point_step": alg_bytes, "kernel_ms_per_step": step_ms},
+            "traces_finite": finite}
+    print(json.dumps(line), flush=True)
+    prop.close()
+
+
 def main():
     args = parse()
+    if args.impl == "native" and args.physics != "acoustic":
+        run_physics(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -134,3 +134,59 @@ def test_tti_and_elastic_reject_blocked_and_bad_models(tb):
         q.set_model(vp, aux=np.stack([1500.0 * one, one]))
     with pytest.raises(tb.TBError):  # time_tile > 1 is acoustic only
         tb.Propagator(shape, h, 4, physics=tb.TB_ELASTIC, time_tile=2)
+
+
+def _subbox_parity(tb, physics, w, nsteps, radius):
+    """Full-size run in the benchmark's configuration (same kernels and
+    launch shapes) for nsteps; the oracle runs on the sub-box around the
+    source that holds the whole domain of dependence (radius cells), with the
+    full grid's damping values, so its fields are exact there."""
+    import torch
+    shape, h = w.shape, w.spacing
+    p = tb.Propagator(shape, h, w.so, physics=physics, nbl=w.nbl)
+    vp = torch.from_numpy(w.vp).cuda()
+    p.set_model(vp, aux=torch.from_numpy(np.stack(w.meta["aux"])).cuda())
+    dt = p.dt
+    nt = nsteps
+    wav = wl.ricker(w.f0, dt, nt, t0=3 * dt)[None, :].astype(np.float32)
+    p.set_sources(w.src_xyz, wav)
+    p.set_receivers(w.rec_xyz)
+    tr = p.forward(nt).cpu().numpy()
+    c = np.floor(w.src_xyz[0] / np.array(h)).astype(int)
+    lo = np.maximum(c - radius, 0)
+    hi = np.minimum(c + radius + 2, np.array(shape))
+    sl = tuple(slice(lo[d], hi[d]) for d in range(3))
+    sub = tuple(int(hi[d] - lo[d]) for d in range(3))
+    # damping of the full grid, restricted to the box
+    eta = np.zeros(sub)
+    vmax = float(w.vp.max())
+    for d in range(3):
+        e = oracle.damping_axis(shape[d], w.nbl, h[d], vmax)[lo[d]:hi[d]]
+        eta += e.reshape([-1 if k == d else 1 for k in range(3)])
+    shift = lo * np.array(h)
+    inbox = np.all((w.rec_xyz >= shift) & (w.rec_xyz <= (hi - 1) * np.array(h)), axis=1)
+    aux = [a[sl].astype(np.float64) for a in w.meta["aux"]]
+    fn = oracle.tti_forward if physics == tb.TB_TTI else oracle.elastic_forward
+    tr_o, st_o = fn(sub, h, w.so, dt, nt, w.vp[sl].astype(np.float64), *aux, eta=eta,
+                    src_xyz=w.src_xyz - shift, src_wav=wav.astype(np.float64),
+                    rec_xyz=w.rec_xyz[inbox] - shift, nthreads=0)
+    nf = 4 if physics == tb.TB_TTI else 9
+    errs = [rel_l2(p.field(i).cpu().numpy()[sl], st_o[i]) for i in range(nf)]
+    e_tr = rel_l2(tr[:, inbox], tr_o)
+    print(f"{w.name}: {nt} steps, box {sub}: fields {max(errs):.2e}, traces {e_tr:.2e}")
+    assert max(errs) <= TOL and e_tr <= TOL
+    assert np.abs(tr_o).max() > 0
+    # receivers outside the box are outside the domain of dependence
+    assert np.all(tr[:, ~inbox] == 0.0)
+
+
+@pytest.mark.slow
+def test_tti_full_size_subbox(tb):
+    w = wl.tti_384_so8()
+    _subbox_parity(tb, tb.TB_TTI, w, nsteps=5, radius=5 * w.so + 4)
+
+
+@pytest.mark.slow
+def test_elastic_full_size_subbox(tb):
+    w = wl.elastic_384_so8()
+    _subbox_parity(tb, tb.TB_ELASTIC, w, nsteps=6, radius=6 * w.so + 4)

@@ -22,6 +22,9 @@ Functions and what they follow in the paper:
                           Eq. 2's rotated derivatives (two fields p, r).
 * ``elastic_forward``     Eq. 3 (Sec. III-C): isotropic elastic velocity-stress
                           on the staggered grid, explosive source.
+* ``acoustic_adjoint``    the exact discrete adjoint of ``acoustic_forward``'s
+                          map from wavelets to traces, and the adjoint-state
+                          gradient of <traces, residual> with respect to vp.
 * ``fd_weights_*``, ``cfl_dt_max``, ``tti_dt_max``, ``elastic_dt_max``,
   ``damping_axis``, ``energy``, ``tti_energy``, ``elastic_energy`` helpers.
 """
@@ -101,6 +104,7 @@ def _load():
                                               dp, dp]
             L.orc_elastic_energy.argtypes = [gp, dp, dp, dp, dp, dp, dp]
             L.orc_elastic_energy.restype = C.c_double
+            L.orc_acoustic_adjoint.argtypes = [gp, dp, dp, C.c_int, dp, dp, C.c_int, dp, dp, dp, dp]
         return _lib
 
 
@@ -343,3 +347,21 @@ def elastic_energy(shape, spacing, so, dt, vp, vs, rho, v_next, v_prev, tau, per
     args = [_f64(np.broadcast_to(a, tuple(shape))) for a in (vp, vs, rho)]
     return float(_load().orc_elastic_energy(C.byref(g), *[_dp(a) for a in args],
                                             *[_dp(_f64(a)) for a in (v_next, v_prev, tau)]))
+
+
+def acoustic_adjoint(shape, spacing, so, dt, nt, vp, resid, *, nbl=0, eta=None, src_xyz=None,
+                     src_wav=None, rec_xyz=None, nthreads=0):
+    """Adjoint of the forward map for adjoint traces ``resid`` [nt, nrec]:
+    returns (grad_src [nsrc, nt] = d<d, r>/dq, grad_vp [shape] = d<d, r>/dvp)
+    with dt and the damping held fixed."""
+    g = make_grid(shape, spacing, so, dt, nt, nbl, False, nthreads)
+    nsrc, sx = _geom(src_xyz)
+    nrec, rx = _geom(rec_xyz)
+    sw = _f64(np.asarray(src_wav).reshape(nsrc, nt)) if nsrc else None
+    r = _f64(np.asarray(resid).reshape(nt, nrec))
+    gsrc = np.zeros((max(nsrc, 1), nt))
+    gvp = np.zeros(tuple(shape))
+    st = _load().orc_acoustic_adjoint(C.byref(g), _dp(_f64(vp)), _dp(_f64(eta)), nsrc, _dp(sx), _dp(sw),
+                                      nrec, _dp(rx), _dp(r), _dp(gsrc), _dp(gvp))
+    _check(st, "acoustic_adjoint")
+    return gsrc[:nsrc], gvp

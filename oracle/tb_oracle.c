@@ -1368,3 +1368,156 @@ double orc_elastic_energy(const orc_grid* g, const double* vp, const double* vs,
   ela_free(&E);
   return 0.5 * (kin + pot);
 }
+
+/* =========================================================================
+ * Adjoint of the acoustic forward map and the velocity gradient (the FWI /
+ * RTM use the paper cites in Sec. I).  Written for the discrete recurrence
+ * of orc_acoustic_forward:
+ *   u^{k} = D L u^{k-1} + B u^{k-1} + C u^{k-2} + M S^{k-1},  k = 1..nt
+ *   D = dt^2/(m+a), B = 2m/(m+a), C = (a-m)/(m+a), M = dt^2/m, a = eta dt/2,
+ *   S^{n} = sum_s w_s q_s[n] spread to the corners, d[n] = P u^{n+1}.
+ * For adjoint traces r[n][k] (the residual) the adjoint state runs backward,
+ *   lam^{k} = P^T r[k-1] + L (D lam^{k+1}) + B lam^{k+1} + C lam^{k+2},
+ * (L symmetric), and gives
+ *   d<d, r>/d q_s[n] = sum_c w_s(c) M(c) lam^{n+1}(c)           (grad_src)
+ *   d<d, r>/d m(p)   = sum_k lam^k(p) [ (2a (u^{k-1} - u^{k-2}) - dt^2 L u^{k-1})
+ *                      / (m+a)^2 - dt^2/m^2 S^{k-1} ](p)           (grad_m)
+ *   d<d, r>/d vp(p)  = grad_m(p) * (-2 / vp(p)^3),
+ * with dt and eta held fixed.  The forward history is kept whole (small
+ * grids only).
+ * ======================================================================= */
+static void lap_apply(const model_t* M, const double* uc, double* out) {
+  const pad_t* p = &M->p;
+  int64_t stride[3] = {p->P1 * p->P2, p->P2, 1};
+#pragma omp parallel for schedule(static)
+  for (int64_t x = 0; x < p->n0; ++x)
+    for (int64_t y = 0; y < p->n1; ++y)
+      for (int64_t z = 0; z < p->n2; ++z) {
+        int64_t q = pidx(p, x, y, z);
+        double lap = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          double s = M->c[0] * uc[q];
+          for (int i = 1; i <= M->r; ++i) s += M->c[i] * (uc[q + i * stride[d]] + uc[q - i * stride[d]]);
+          lap += s * M->ih2[d];
+        }
+        out[gidx(p, x, y, z)] = lap;
+      }
+}
+
+int orc_acoustic_adjoint(const orc_grid* g, const double* vp, const double* eta, int nsrc,
+                         const double* src_xyz, const double* src_wav, int nrec, const double* rec_xyz,
+                         const double* resid, double* grad_src, double* grad_vp) {
+  model_t M;
+  int st = model_init(&M, g, vp, eta);
+  if (st) { model_free(&M); return st; }
+  const pad_t* p = &M.p;
+  const int64_t N = p->n0 * p->n1 * p->n2;
+  const int nt = g->nt;
+  int64_t* sb = (int64_t*)malloc(sizeof(int64_t) * 3 * (nsrc > 0 ? nsrc : 1));
+  double* sf = (double*)malloc(sizeof(double) * 3 * (nsrc > 0 ? nsrc : 1));
+  int64_t* rb = (int64_t*)malloc(sizeof(int64_t) * 3 * (nrec > 0 ? nrec : 1));
+  double* rf = (double*)malloc(sizeof(double) * 3 * (nrec > 0 ? nrec : 1));
+  /* forward history u^k, k = -1..nt (padded), stored as hist[k + 1] */
+  double* hist = (double*)calloc((size_t)(nt + 2) * p->NP, sizeof(double));
+  double* S = (double*)calloc((size_t)(nt > 0 ? nt : 1) * N, sizeof(double)); /* S^{n} unpadded */
+  double* lam = (double*)calloc((size_t)3 * p->NP, sizeof(double));            /* lam^{k}, k+1, k+2 */
+  double* w = (double*)calloc(p->NP, sizeof(double));
+  double* lw = (double*)malloc(sizeof(double) * N);
+  double* lu = (double*)malloc(sizeof(double) * N);
+  double* gm = (double*)calloc(N, sizeof(double));
+  if (!sb || !sf || !rb || !rf || !hist || !S || !lam || !w || !lw || !lu || !gm) { st = ORC_ENOMEM; goto done; }
+  for (int s = 0; s < nsrc; ++s)
+    if (trilinear(g, src_xyz + 3 * s, sb + 3 * s, sf + 3 * s)) { st = ORC_EINVAL; goto done; }
+  for (int r = 0; r < nrec; ++r)
+    if (trilinear(g, rec_xyz + 3 * r, rb + 3 * r, rf + 3 * r)) { st = ORC_EINVAL; goto done; }
+  /* spread sources S^{n} */
+  for (int n = 0; n < nt; ++n)
+    for (int s = 0; s < nsrc; ++s)
+      for (int c = 0; c < 8; ++c) {
+        double wc = corner_weight(sf + 3 * s, c);
+        if (wc == 0.0) continue;
+        int64_t x = sb[3 * s] + ((c >> 2) & 1), y = sb[3 * s + 1] + ((c >> 1) & 1), z = sb[3 * s + 2] + (c & 1);
+        S[(int64_t)n * N + gidx(p, x, y, z)] += wc * src_wav[(int64_t)s * nt + n];
+      }
+  /* forward, keeping every state */
+  for (int k = 1; k <= nt; ++k) {
+    double* up = hist + (size_t)(k - 1) * p->NP; /* u^{k-2} */
+    double* uc = hist + (size_t)k * p->NP;       /* u^{k-1} */
+    double* un = hist + (size_t)(k + 1) * p->NP; /* u^{k}   */
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < p->n0; ++x)
+      for (int64_t y = 0; y < p->n1; ++y)
+        for (int64_t z = 0; z < p->n2; ++z) {
+          int64_t gq = gidx(p, x, y, z);
+          un[pidx(p, x, y, z)] = point_update(&M, up, uc, x, y, z) + S[(int64_t)(k - 1) * N + gq] * M.dt2 / M.m[gq];
+        }
+  }
+  /* backward: lam^{k} for k = nt..1 */
+  double* l0 = lam;               /* lam^{k}   */
+  double* l1 = lam + p->NP;       /* lam^{k+1} */
+  double* l2 = lam + 2 * p->NP;   /* lam^{k+2} */
+  if (grad_src) memset(grad_src, 0, sizeof(double) * (size_t)(nsrc > 0 ? nsrc : 0) * nt);
+  for (int k = nt; k >= 1; --k) {
+    /* w = D lam^{k+1} (zero halo), then L w */
+    for (int64_t x = 0; x < p->n0; ++x)
+      for (int64_t y = 0; y < p->n1; ++y)
+        for (int64_t z = 0; z < p->n2; ++z) {
+          int64_t gq = gidx(p, x, y, z);
+          double a = M.eta[gq] * M.dt * 0.5;
+          w[pidx(p, x, y, z)] = M.dt2 / (M.m[gq] + a) * l1[pidx(p, x, y, z)];
+        }
+    lap_apply(&M, w, lw);
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < p->n0; ++x)
+      for (int64_t y = 0; y < p->n1; ++y)
+        for (int64_t z = 0; z < p->n2; ++z) {
+          int64_t q = pidx(p, x, y, z), gq = gidx(p, x, y, z);
+          double m = M.m[gq], a = M.eta[gq] * M.dt * 0.5;
+          l0[q] = lw[gq] + 2.0 * m / (m + a) * l1[q] + (a - m) / (m + a) * l2[q];
+        }
+    /* receiver residual injected at the corners: P^T r[k-1] */
+    for (int r = 0; r < nrec; ++r)
+      for (int c = 0; c < 8; ++c) {
+        double wc = corner_weight(rf + 3 * r, c);
+        if (wc == 0.0) continue;
+        int64_t x = rb[3 * r] + ((c >> 2) & 1), y = rb[3 * r + 1] + ((c >> 1) & 1), z = rb[3 * r + 2] + (c & 1);
+        l0[pidx(p, x, y, z)] += wc * resid[(int64_t)(k - 1) * nrec + r];
+      }
+    /* source gradient: sum_c w_s(c) M(c) lam^{k}(c) for step k-1 */
+    if (grad_src)
+      for (int s = 0; s < nsrc; ++s) {
+        double acc = 0.0;
+        for (int c = 0; c < 8; ++c) {
+          double wc = corner_weight(sf + 3 * s, c);
+          if (wc == 0.0) continue;
+          int64_t x = sb[3 * s] + ((c >> 2) & 1), y = sb[3 * s + 1] + ((c >> 1) & 1), z = sb[3 * s + 2] + (c & 1);
+          acc += wc * M.dt2 / M.m[gidx(p, x, y, z)] * l0[pidx(p, x, y, z)];
+        }
+        grad_src[(int64_t)s * nt + (k - 1)] = acc;
+      }
+    /* velocity gradient contribution of equation k */
+    if (grad_vp) {
+      double* um2 = hist + (size_t)(k - 1) * p->NP; /* u^{k-2} */
+      double* um1 = hist + (size_t)k * p->NP;       /* u^{k-1} */
+      lap_apply(&M, um1, lu);
+      for (int64_t x = 0; x < p->n0; ++x)
+        for (int64_t y = 0; y < p->n1; ++y)
+          for (int64_t z = 0; z < p->n2; ++z) {
+            int64_t q = pidx(p, x, y, z), gq = gidx(p, x, y, z);
+            double m = M.m[gq], a = M.eta[gq] * M.dt * 0.5;
+            double dr = (2.0 * a * (um1[q] - um2[q]) - M.dt2 * lu[gq]) / ((m + a) * (m + a)) -
+                        M.dt2 / (m * m) * S[(int64_t)(k - 1) * N + gq];
+            gm[gq] += l0[q] * dr;
+          }
+    }
+    double* t = l2; l2 = l1; l1 = l0; l0 = t;
+    memset(l0, 0, sizeof(double) * p->NP);
+  }
+  if (grad_vp)
+    for (int64_t i = 0; i < N; ++i) grad_vp[i] = gm[i] * (-2.0 / (vp[i] * vp[i] * vp[i]));
+done:
+  free(sb); free(sf); free(rb); free(rf); free(hist); free(S); free(lam); free(w); free(lw); free(lu);
+  free(gm);
+  model_free(&M);
+  return st;
+}

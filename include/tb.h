@@ -245,6 +245,30 @@ int tb_selftest_wait(double timeout_s, void* stream);
 int tb_inspect_points_noalloc(const int64_t n[3], const double h[3], int npt, const double* coords,
                               int64_t* lin, int64_t* npts, void* stream);
 
+/* Adjoint-state gradient of the acoustic propagation (the FWI / RTM use of
+ * the propagator that Sec. I motivates), for the model, sources and
+ * receivers set on the handle, dt and damping held fixed:
+ *   residual  [nt][nrec] float (host or device): adjoint traces r, e.g. the
+ *             derivative of a misfit with respect to the traces;
+ *   grad_vp   [n0][n1][n2] float (host or device, may be NULL): receives
+ *             d<d(vp), r>/d vp with d the traces of tb_forward;
+ *   grad_src  [nsrc][nt] float (host or device, may be NULL): receives
+ *             d<d, r>/d q (the adjoint of the wavelet-to-trace map);
+ *   n_snapshots >= 1: the forward pass keeps a checkpoint (u^n, u^{n-1})
+ *             every ceil(nt / n_snapshots) steps; the backward pass
+ *             recomputes each segment once from its checkpoint into a
+ *             buffer of ceil(nt / n_snapshots) + 1 states.
+ * The adjoint is the exact transpose of the discrete one-step recurrence:
+ * lam^k = L(D lam^{k+1}) + B lam^{k+1} + C lam^{k+2} + P^T r[k-1] with
+ * D = dt^2/(m + a), B = 2m/(m + a), C = (a - m)/(m + a), a = eta dt/2; the
+ * gradient sums lam^k d(step k)/dm over the steps in FP64.  Device scratch
+ * about (2 n_snapshots + ceil(nt / n_snapshots) + 7) fields, allocated and
+ * freed by the call.  Synchronises `stream`.  Overwrites the handle's
+ * wavefields (tb_get_field needs a new tb_forward).  Acoustic only.
+ * Errors: TB_ESTATE, TB_EINVAL, TB_ENOMEM, TB_ECUDA, TB_ETIMEOUT. */
+int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, float* grad_vp, float* grad_src,
+                        int n_snapshots, void* stream);
+
 /* Stability limits of the TTI and elastic schemes (seconds), -1 on bad
  * arguments.  TTI: 2 / (vmax sqrt(1 + 2 eps_max) sqrt(sum_d (S1/h_d)^2)),
  * S1 = max |2 sum a_i sin(i t)| over the centred first-derivative weights

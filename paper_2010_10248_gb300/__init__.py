@@ -9,14 +9,15 @@ from __future__ import annotations
 
 from . import _tb
 from ._tb import (TB_ACOUSTIC, TB_BLOCKED, TB_ELASTIC, TB_ONESTEP, TB_TTI, Options, TBError, load,
-                  tb_cfl_dt_max, tb_elastic_dt_max, tb_tti_dt_max,
+                  tb_adjoint_gradient, tb_cfl_dt_max, tb_elastic_dt_max, tb_tti_dt_max,
                   tb_create, tb_destroy, tb_fd_weights, tb_forward, tb_get_dt, tb_get_field,
                   tb_get_receiver_points, tb_get_source_points, tb_kernel_time, tb_last_error,
                   tb_launch_count, tb_ricker, tb_selftest_wait, tb_set_model, tb_set_receivers, tb_set_sources,
                   tb_sponge_profile, tb_workspace_bytes)
 
 __all__ = ["Propagator", "Options", "TBError", "load", "TB_ONESTEP", "TB_BLOCKED", "TB_ACOUSTIC",
-           "TB_TTI", "TB_ELASTIC", "tb_tti_dt_max", "tb_elastic_dt_max",
+           "TB_TTI", "TB_ELASTIC", "tb_tti_dt_max", "tb_elastic_dt_max", "tb_adjoint_gradient",
+           "AcousticTraces",
            "tb_create", "tb_destroy", "tb_set_model", "tb_get_dt", "tb_set_sources",
            "tb_set_receivers", "tb_forward", "tb_get_field", "tb_get_source_points",
            "tb_get_receiver_points", "tb_workspace_bytes", "tb_kernel_time", "tb_last_error",
@@ -130,6 +131,13 @@ class Propagator:
         tb_get_receiver_points(self.h, lin, cid, cw)
         return lin[:n], cid[: self.nrec], cw[: self.nrec]
 
+    def adjoint_gradient(self, nt, residual, grad_vp=None, grad_src=None, n_snapshots=32):
+        """d<traces, residual>/dvp (and /dq) for the current model and geometry."""
+        torch = self._torch
+        residual = residual.to(dtype=torch.float32).contiguous() if hasattr(residual, "data_ptr") else residual
+        tb_adjoint_gradient(self.h, nt, residual, grad_vp, grad_src, n_snapshots, self._stream())
+        return grad_vp, grad_src
+
     def kernel_time(self, kind=0):
         return tb_kernel_time(self.h, kind)
 
@@ -150,3 +158,44 @@ class Propagator:
         if hasattr(a, "data_ptr"):
             return a.to(dtype=self._torch.float32).contiguous()
         return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _autograd_function():
+    import torch
+
+    class _AcousticTraces(torch.autograd.Function):
+        """traces = F(vp) through the C ABI; backward by tb_adjoint_gradient.
+
+        The time step and the damping are held fixed (pass them explicitly),
+        which is what the gradient differentiates."""
+
+        @staticmethod
+        def forward(ctx, vp, prop, src_xyz, wavelets, rec_xyz, nt, dt, damp, n_snapshots):
+            prop.set_model(vp.detach(), damp=damp, dt=dt)
+            prop.set_sources(src_xyz, wavelets)
+            prop.set_receivers(rec_xyz)
+            traces = prop.forward(nt, schedule="onestep")
+            ctx.prop, ctx.nt, ctx.nsnap = prop, nt, n_snapshots
+            ctx.vp_shape = vp.shape
+            return traces
+
+        @staticmethod
+        def backward(ctx, grad_traces):
+            g = torch.empty(ctx.vp_shape, dtype=torch.float32, device="cuda")
+            ctx.prop.adjoint_gradient(ctx.nt, grad_traces.contiguous(), grad_vp=g, n_snapshots=ctx.nsnap)
+            return g, None, None, None, None, None, None, None, None
+
+    return _AcousticTraces
+
+
+class AcousticTraces:
+    """torch.autograd.Function-style entry: AcousticTraces.apply(vp, prop,
+    src_xyz, wavelets, rec_xyz, nt, dt, damp, n_snapshots) -> traces [nt, nrec]
+    with d(traces)/d(vp) through the library's adjoint."""
+    _fn = None
+
+    @classmethod
+    def apply(cls, *args):
+        if cls._fn is None:
+            cls._fn = _autograd_function()
+        return cls._fn.apply(*args)

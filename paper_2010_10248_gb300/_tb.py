@@ -58,6 +58,7 @@ _SIGS = {
     "tb_fd_weights": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "tb_cfl_dt_max": (C.c_double, [C.c_int, C.POINTER(C.c_double), C.c_double]),
     "tb_tti_dt_max": (C.c_double, [C.c_int, C.POINTER(C.c_double), C.c_double, C.c_double]),
+    "tb_adjoint_gradient": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int, _vp]),
     "tb_elastic_dt_max": (C.c_double, [C.c_int, C.POINTER(C.c_double), C.c_double]),
     "tb_sponge_profile": (C.c_int, [C.c_int64, C.c_int, C.c_double, C.c_double,
                                     C.POINTER(C.c_double)]),
@@ -209,6 +210,11 @@ def tb_fd_weights(space_order):
 def tb_cfl_dt_max(space_order, spacing, vmax):
     hh = (C.c_double * 3)(*[float(s) for s in spacing])
     return load().tb_cfl_dt_max(int(space_order), hh, float(vmax))
+
+
+def tb_adjoint_gradient(h, nt, residual, grad_vp=None, grad_src=None, n_snapshots=32, stream=None):
+    _check(h, load().tb_adjoint_gradient(h, int(nt), _ptr(residual), _ptr(grad_vp), _ptr(grad_src),
+                                         int(n_snapshots), _stream(stream)), "tb_adjoint_gradient")
 
 
 def tb_tti_dt_max(space_order, spacing, vmax, eps_max):

@@ -576,7 +576,8 @@ extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int 
   }
   const char* why = "";
   h->have_src = false;
-  int s = inspect(h->n, h->h, nsrc, (const double*)dc, false, &h->src, st, &why);
+  // corner tables too: the adjoint gathers the source-wavelet gradient with them
+  int s = inspect(h->n, h->h, nsrc, (const double*)dc, true, &h->src, st, &why);
   if (s != TB_OK) {
     cudaFree(t1);
     cudaFree(t2);
@@ -1145,6 +1146,217 @@ extern "C" int tb_kernel_time(tb_handle* h, int kind, int* launches, double* ms)
     *ms += t;
     ++*launches;
   }
+  return TB_OK;
+}
+
+// ------------------------------------------------------------- adjoint --
+// One-step sweeps for the adjoint's forward passes (no receiver recording).
+struct StepRunner {
+  Plan p1;
+  SweepParams P{};
+};
+static int runner_init(tb_handle* h, StepRunner* r, cudaStream_t st) {
+  int s = plan_sweep(h, 1, &r->p1);
+  if (s != TB_OK) return s;
+  if ((s = ensure_capacity(h, 1, r->p1, 0, false, 0)) != TB_OK) return s;
+  TB_CUDA(h, cudaMemcpyAsync(h->d_pass, r->p1.launch_passes.data(), sizeof(PassDesc) * r->p1.launch_passes.size(),
+                             cudaMemcpyHostToDevice, st));
+  SweepParams& P = r->P;
+  P.n0 = (int)h->n[0];
+  P.n1 = (int)h->n[1];
+  P.n2 = (int)h->n[2];
+  P.n2p = h->n2p;
+  P.c2 = h->c2;
+  P.damp_b = h->damp_b;
+  for (int d = 0; d < 3; ++d)
+    for (int i = 1; i <= h->R; ++i) {
+      const float wf = (float)(h->c[i] / (h->h[d] * h->h[d]));
+      P.w2[d][i - 1] = make_float2(wf, wf);
+    }
+  const bool src_on = h->have_src && h->src.npts > 0;
+  P.s_colptr = src_on ? h->src.colptr : nullptr;
+  P.s_ent = src_on ? h->src.ent : nullptr;
+  P.src_dcmp = h->src_dcmp;
+  P.npts = h->src.npts;
+  P.r_colptr = nullptr;
+  P.r_ent = nullptr;
+  P.err = h->err;
+  P.timeout_ns = (long long)(h->opt.wait_timeout_s * 1e9);
+  return TB_OK;
+}
+// u^{step+1} over field[prev] from field[cur] = u^{step}, field[prev] = u^{step-1}
+static int runner_step(tb_handle* h, StepRunner* r, int cur, int prev, int step, cudaStream_t st) {
+  SweepParams& P = r->P;
+  P.u_cur = h->field[cur];
+  P.u_prev = h->field[prev];
+  P.tm_u = h->tm_box[cur];
+  P.tm_p = h->tm_tile[prev];
+  P.tm_c = h->tm_c2;
+  P.out0 = h->field[prev];
+  P.out1 = nullptr;
+  P.step0 = step;
+  P.rec_base = 0;
+  const Plan& pl = r->p1;
+  for (size_t L = 0; L < pl.launch_first.size(); ++L) {
+    const int first = pl.launch_first[L];
+    const int last = L + 1 < pl.launch_first.size() ? pl.launch_first[L + 1] : (int)pl.launch_passes.size();
+    P.pass = h->d_pass + first;
+    P.npass = last - first;
+    cudaError_t e = sweep_launch(h->R, 1, P, pl.launch_ctas[L], false, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint forward launch");
+  }
+  return TB_OK;
+}
+
+extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, float* grad_vp, float* grad_src,
+                                   int n_snapshots, void* stream) {
+  if (!h) return TB_EINVAL;
+  if (h->physics != TB_ACOUSTIC) return fail(h, TB_EINVAL, "the adjoint is implemented for the acoustic equation");
+  if (!h->have_model || !h->have_src || !h->have_rec)
+    return fail(h, TB_ESTATE, "tb_set_model, tb_set_sources and tb_set_receivers must come first");
+  if (nt <= 0 || !residual || n_snapshots < 1 || (!grad_vp && !grad_src)) return fail(h, TB_EINVAL, "bad arguments");
+  if (h->src.npts > 0 && nt > h->src_nt)
+    return fail(h, TB_EINVAL, "nt = %d exceeds the wavelet length %d", nt, h->src_nt);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nrec = h->rec.npt, nsrc = h->src.npt;
+  const int64_t nrp = h->rec.npts, nsp = h->src.npts;
+  const size_t Np = (size_t)h->n[0] * h->n[1] * h->n2p, fbytes = sizeof(float) * Np;
+  const int K = (nt + n_snapshots - 1) / n_snapshots;  // steps per segment
+  const int nseg = (nt + K - 1) / K;
+  StepRunner run;
+  int s = runner_init(h, &run, st);
+  if (s != TB_OK) return s;
+  // scratch: checkpoints (u^{jK}, u^{jK-1}) of segments j >= 1, a segment of
+  // K+1 states, adjoint fields, D lam, the FP64 gradient, the decomposed
+  // residual and the source-gradient rows
+  std::vector<void*> bufs;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    return p;
+  };
+  auto cleanup = [&]() {
+    for (void* p : bufs) cudaFree(p);
+    bufs.clear();
+  };
+  float* snap = (float*)alloc(fbytes * 2 * std::max(nseg - 1, 1));
+  float* seg = (float*)alloc(fbytes * (K + 1));
+  float* lam = (float*)alloc(fbytes * 3);
+  float* wbuf = (float*)alloc(fbytes);
+  double* gm = (double*)alloc(sizeof(double) * Np);
+  float* resT = (float*)alloc(sizeof(float) * (size_t)nt * std::max(nrec, 1));
+  float* rdcmp = (float*)alloc(sizeof(float) * (size_t)nt * std::max<int64_t>(nrp, 1));
+  float* srow = (float*)alloc(sizeof(float) * (size_t)nt * std::max<int64_t>(nsp, 1));
+  float* gsrc = (float*)alloc(sizeof(float) * (size_t)nt * std::max(nsrc, 1) * 2);
+  float* gvp_dev = nullptr;
+  const bool gvp_host = grad_vp && !is_device_ptr(grad_vp);
+  if (gvp_host) gvp_dev = (float*)alloc(sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n[2]);
+  if (!snap || !seg || !lam || !wbuf || !gm || !resT || !rdcmp || !srow || !gsrc || (gvp_host && !gvp_dev)) {
+    cleanup();
+    cudaGetLastError();
+    return fail(h, TB_ENOMEM, "adjoint scratch");
+  }
+  const PhysGrid g{(int)h->n[0], (int)h->n[1], (int)h->n[2], h->n2p};
+  LapW lw{};
+  for (int d = 0; d < 3; ++d)
+    for (int i = 1; i <= h->R; ++i) lw.c[d][i - 1] = (float)(h->c[i] / (h->h[d] * h->h[d]));
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (e == cudaSuccess && x != cudaSuccess) e = x;
+    return e == cudaSuccess;
+  };
+  // residual [nt][nrec] -> [nrec][nt] -> per receiver point: sum_c w r (FP64)
+  {
+    void* tmp = nullptr;
+    const void* dres = nullptr;
+    ok(to_device(residual, sizeof(float) * (size_t)nt * nrec, &tmp, &dres, st));
+    if (tmp) bufs.push_back(tmp);
+    ok(transpose_f32(nt, nrec, (const float*)dres, resT, st));
+    if (nrp > 0) ok(decompose(&h->rec, nt, resT, nullptr, 1.0, (int)h->n[1], (int)h->n[2], h->n2p, rdcmp, st));
+  }
+  // forward pass, keeping the checkpoints
+  int cur = 0, prev = 1;
+  ok(cudaMemsetAsync(h->field[0], 0, fbytes, st));
+  ok(cudaMemsetAsync(h->field[1], 0, fbytes, st));
+  ok(cudaMemsetAsync(h->err, 0, sizeof(int), st));
+  for (int n = 0; n < nt && e == cudaSuccess; ++n) {
+    if (n > 0 && n % K == 0) {
+      const int j = n / K;
+      ok(cudaMemcpyAsync(snap + (size_t)(2 * (j - 1)) * Np, h->field[cur], fbytes, cudaMemcpyDeviceToDevice, st));
+      ok(cudaMemcpyAsync(snap + (size_t)(2 * (j - 1) + 1) * Np, h->field[prev], fbytes, cudaMemcpyDeviceToDevice, st));
+    }
+    if ((s = runner_step(h, &run, cur, prev, n, st)) != TB_OK) {
+      cleanup();
+      return s;
+    }
+    std::swap(cur, prev);
+  }
+  // backward over the segments, each recomputed once from its checkpoint
+  ok(cudaMemsetAsync(lam, 0, fbytes * 3, st));
+  ok(cudaMemsetAsync(gm, 0, sizeof(double) * Np, st));
+  float* l0 = lam;
+  float* l1 = lam + Np;
+  float* l2 = lam + 2 * Np;
+  for (int j = nseg - 1; j >= 0 && e == cudaSuccess; --j) {
+    const int k0 = j * K, k1 = std::min((j + 1) * K, nt);
+    // seg[s] = u^{k0 - 1 + s}, s = 0 .. k1 - k0
+    if (j == 0) {
+      ok(cudaMemsetAsync(seg, 0, fbytes * 2, st));
+    } else {
+      ok(cudaMemcpyAsync(seg + Np, snap + (size_t)(2 * (j - 1)) * Np, fbytes, cudaMemcpyDeviceToDevice, st));
+      ok(cudaMemcpyAsync(seg, snap + (size_t)(2 * (j - 1) + 1) * Np, fbytes, cudaMemcpyDeviceToDevice, st));
+    }
+    cur = 0;
+    prev = 1;
+    ok(cudaMemcpyAsync(h->field[cur], seg + Np, fbytes, cudaMemcpyDeviceToDevice, st));
+    ok(cudaMemcpyAsync(h->field[prev], seg, fbytes, cudaMemcpyDeviceToDevice, st));
+    for (int n = k0; n <= k1 - 2 && e == cudaSuccess; ++n) {
+      if ((s = runner_step(h, &run, cur, prev, n, st)) != TB_OK) {
+        cleanup();
+        return s;
+      }
+      std::swap(cur, prev);
+      ok(cudaMemcpyAsync(seg + (size_t)(n + 2 - k0) * Np, h->field[cur], fbytes, cudaMemcpyDeviceToDevice, st));
+    }
+    for (int k = k1; k >= k0 + 1 && e == cudaSuccess; --k) {
+      ok(adjoint_step(h->R, g, lw, l1, l2, l0, wbuf, h->c2, h->damp_b, st));
+      if (nrp > 0) ok(inject_points(g, nrp, h->rec.lin, rdcmp + (size_t)(k - 1) * nrp, l0, nullptr, nullptr, st));
+      if (grad_vp) {
+        ok(adjoint_grad(h->R, g, lw, h->dt, l0, seg + (size_t)(k - k0) * Np, seg + (size_t)(k - k0 - 1) * Np, h->c2,
+                        h->damp_b, gm, st));
+        if (nsp > 0) ok(adjoint_grad_src(g, nsp, h->src.lin, h->src_dcmp + (size_t)(k - 1) * nsp, h->dt, l0, h->c2, gm, st));
+      }
+      if (grad_src && nsp > 0) ok(adjoint_sample_src(g, nsp, h->src.ent, h->src.lin, l0, h->c2, srow + (size_t)(k - 1) * nsp, st));
+      float* t = l2;
+      l2 = l1;
+      l1 = l0;
+      l0 = t;
+    }
+  }
+  if (grad_vp && e == cudaSuccess) {
+    ok(adjoint_finish(g, h->dt, gm, h->c2, gvp_host ? gvp_dev : grad_vp, st));
+    if (gvp_host)
+      ok(cudaMemcpyAsync(grad_vp, gvp_dev, sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n[2],
+                         cudaMemcpyDeviceToHost, st));
+  }
+  if (grad_src && nsrc > 0 && e == cudaSuccess) {
+    // [nt][nsrc] by the source corner weights, then [nsrc][nt]
+    if (nsp > 0) ok(finalize_traces(nt, nsrc, h->src.corner_eid, h->src.corner_w, srow, nsp, gsrc, st));
+    else ok(cudaMemsetAsync(gsrc, 0, sizeof(float) * (size_t)nt * nsrc, st));
+    float* gT = gsrc + (size_t)nt * nsrc;
+    ok(transpose_f32(nt, nsrc, gsrc, gT, st));
+    ok(cudaMemcpyAsync(grad_src, gT, sizeof(float) * (size_t)nt * nsrc,
+                       is_device_ptr(grad_src) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  int err = 0;
+  ok(cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ok(cudaStreamSynchronize(st));
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(h, e, "tb_adjoint_gradient");
+  if (err) return fail(h, TB_ETIMEOUT, "a sweep CTA timed out");
+  h->last_nt = -1;  // the fields hold recomputation scratch now
+  h->msg[0] = 0;
   return TB_OK;
 }
 

@@ -116,6 +116,22 @@ cudaError_t inject_points(const PhysGrid& g, int64_t npts, const int64_t* lin, c
 cudaError_t sample_points(const PhysGrid& g, int64_t npts, const int2* ent, const int64_t* lin, const float* f0,
                           const float* f1, const float* f2, float* row, cudaStream_t st);
 
+// Adjoint of the acoustic one-step recurrence and the vp gradient (tb_adjoint.cu).
+struct LapW {
+  float c[3][6];  // c_i / h_d^2, i = 1..r
+};
+cudaError_t adjoint_step(int R, const PhysGrid& g, const LapW& lw, const float* lam1, const float* lam2, float* lam0,
+                         float* w, const float* c2, const float* damp_b, cudaStream_t st);
+cudaError_t adjoint_grad(int R, const PhysGrid& g, const LapW& lw, double dt, const float* lam0, const float* u1,
+                         const float* u2, const float* c2, const float* damp_b, double* gm, cudaStream_t st);
+cudaError_t adjoint_grad_src(const PhysGrid& g, int64_t npts, const int64_t* lin, const float* dcmp_row, double dt,
+                             const float* lam0, const float* c2, double* gm, cudaStream_t st);
+cudaError_t adjoint_sample_src(const PhysGrid& g, int64_t npts, const int2* ent, const int64_t* lin,
+                               const float* lam0, const float* c2, float* row, cudaStream_t st);
+cudaError_t adjoint_finish(const PhysGrid& g, double dt, const double* gm, const float* c2, float* out,
+                           cudaStream_t st);
+cudaError_t transpose_f32(int64_t rows, int64_t cols, const float* in, float* out, cudaStream_t st);
+
 void free_tables(PointTables* t);
 // Builds lin, colptr, ent (+ corner tables when want_corners).  coords on
 // the device.  Returns TB_OK / TB_EINVAL / TB_ENOMEM / TB_ECUDA.

@@ -106,6 +106,7 @@ struct tb_handle {
   std::vector<int> ev_kind;
   int ev_used = 0;
   cudaStream_t ev_stream = nullptr;
+  cudaStream_t last_stream = nullptr;  // stream of the latest call (destroy frees on it)
   char msg[512] = {0};
 };
 
@@ -147,7 +148,7 @@ static cudaError_t to_device(const void* src, size_t bytes, void** tmp, const vo
     *out = src;
     return cudaSuccess;
   }
-  cudaError_t e = cudaMalloc(tmp, bytes ? bytes : 1);
+  cudaError_t e = cudaMallocAsync(tmp, bytes ? bytes : 1, st);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(*tmp, src, bytes, cudaMemcpyHostToDevice, st);
   *out = *tmp;
@@ -301,24 +302,26 @@ extern "C" const char* tb_last_error(const tb_handle* h) { return h ? h->msg : "
 
 extern "C" int tb_destroy(tb_handle* h) {
   if (!h) return TB_OK;
-  for (auto& f : h->field) cudaFree(f);
-  cudaFree(h->coef);
-  cudaFree(h->nzb);
-  cudaFree(h->flux);
-  cudaFree(h->efield);
-  cudaFree(h->emat);
-  cudaFree(h->eta_dt);
-  cudaFree(h->c2);
-  cudaFree(h->damp_b);
-  free_tables(&h->src);
-  free_tables(&h->rec);
-  cudaFree(h->src_dcmp);
-  cudaFree(h->rec_dcmp);
-  cudaFree(h->ring);
-  cudaFree(h->progress);
-  cudaFree(h->err);
-  cudaFree(h->d_pass);
-  cudaFree(h->traces_dev);
+  // stream-ordered frees after the handle's latest work (no device-wide sync)
+  cudaStream_t st = h->last_stream;
+  for (auto& f : h->field) dfree(f, st);
+  dfree(h->coef, st);
+  dfree(h->nzb, st);
+  dfree(h->flux, st);
+  dfree(h->efield, st);
+  dfree(h->emat, st);
+  dfree(h->eta_dt, st);
+  dfree(h->c2, st);
+  dfree(h->damp_b, st);
+  free_tables(&h->src, st);
+  free_tables(&h->rec, st);
+  dfree(h->src_dcmp, st);
+  dfree(h->rec_dcmp, st);
+  dfree(h->ring, st);
+  dfree(h->progress, st);
+  dfree(h->err, st);
+  dfree(h->d_pass, st);
+  dfree(h->traces_dev, st);
   for (auto e : h->ev) cudaEventDestroy(e);
   delete h;
   return TB_OK;
@@ -361,6 +364,9 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
     h->n[d] = n[d];
     h->h[d] = hsp[d];
   }
+  // allocations on this thread's default stream, complete before returning
+  cudaStream_t st = cudaStreamPerThread;
+  h->last_stream = st;
   h->so = so;
   h->R = so / 2;
   h->physics = physics;
@@ -378,28 +384,36 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   h->n2p = (int)((n[2] + 3) / 4 * 4);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) {
+    // keep freed blocks in the device's default pool for the next handle
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
   const size_t fbytes = sizeof(float) * (size_t)n[0] * n[1] * h->n2p;
   const int nfield = physics == TB_ELASTIC ? 0 : 4;
   for (int i = 0; i < nfield && e == cudaSuccess; ++i) {
-    e = cudaMalloc(&h->field[i], fbytes);
-    if (e == cudaSuccess) e = cudaMemset(h->field[i], 0, fbytes);
+    e = dmalloc(&h->field[i], fbytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->field[i], 0, fbytes, st);
   }
   if (physics == TB_TTI) {
-    if (e == cudaSuccess) e = cudaMalloc(&h->coef, 2 * fbytes);
-    if (e == cudaSuccess) e = cudaMalloc(&h->nzb, 3 * fbytes);
-    if (e == cudaSuccess) e = cudaMalloc(&h->flux, 6 * fbytes);
-    if (e == cudaSuccess) e = cudaMemset(h->flux, 0, 6 * fbytes);
+    if (e == cudaSuccess) e = dmalloc(&h->coef, 2 * fbytes, st);
+    if (e == cudaSuccess) e = dmalloc(&h->nzb, 3 * fbytes, st);
+    if (e == cudaSuccess) e = dmalloc(&h->flux, 6 * fbytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flux, 0, 6 * fbytes, st);
   } else if (physics == TB_ELASTIC) {
-    if (e == cudaSuccess) e = cudaMalloc(&h->efield, 9 * fbytes);
-    if (e == cudaSuccess) e = cudaMemset(h->efield, 0, 9 * fbytes);
-    if (e == cudaSuccess) e = cudaMalloc(&h->emat, 8 * fbytes);
-    if (e == cudaSuccess) e = cudaMalloc(&h->eta_dt, sizeof(float) * (n[0] + n[1] + n[2]));
+    if (e == cudaSuccess) e = dmalloc(&h->efield, 9 * fbytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->efield, 0, 9 * fbytes, st);
+    if (e == cudaSuccess) e = dmalloc(&h->emat, 8 * fbytes, st);
+    if (e == cudaSuccess) e = dmalloc(&h->eta_dt, sizeof(float) * (n[0] + n[1] + n[2]), st);
   }
-  if (e == cudaSuccess) e = cudaMalloc(&h->c2, fbytes);
-  if (e == cudaSuccess) e = cudaMemset(h->c2, 0, fbytes);
-  if (e == cudaSuccess) e = cudaMalloc(&h->damp_b, sizeof(float) * (n[0] + n[1] + n[2]));
-  if (e == cudaSuccess) e = cudaMalloc(&h->err, sizeof(int) * 4);
-  if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int) * 4);
+  if (e == cudaSuccess) e = dmalloc(&h->c2, fbytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->c2, 0, fbytes, st);
+  if (e == cudaSuccess) e = dmalloc(&h->damp_b, sizeof(float) * (n[0] + n[1] + n[2]), st);
+  if (e == cudaSuccess) e = dmalloc(&h->err, sizeof(int) * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int) * 4, st);
   SweepShape sh;
   if (e == cudaSuccess && !sweep_shape(h->R, 1, &sh)) e = cudaErrorInvalidValue;
   for (int i = 0; i < 4 && e == cudaSuccess && physics == TB_ACOUSTIC; ++i) {
@@ -407,6 +421,7 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
     if (e == cudaSuccess) e = make_tmap(&h->tm_tile[i], h->field[i], n, h->n2p, 64, sh.TY);
   }
   if (e == cudaSuccess && physics == TB_ACOUSTIC) e = make_tmap(&h->tm_c2, h->c2, n, h->n2p, 64, sh.TY);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     int code = e == cudaErrorMemoryAllocation ? TB_ENOMEM : TB_ECUDA;
     cudaGetLastError();
@@ -442,6 +457,7 @@ extern "C" int tb_set_model(tb_handle* h, const float* vp, const float* aux, con
     return fail(h, TB_EINVAL, "aux is required (TTI: eps, delta, theta, phi; elastic: vs, rho)");
   if (dt < 0 || !std::isfinite(dt)) return fail(h, TB_EINVAL, "dt must be >= 0");
   cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
   const int64_t N = h->n[0] * h->n[1] * h->n[2];
   void* tmp = nullptr;
   const void* dvp = nullptr;
@@ -455,11 +471,11 @@ extern "C" int tb_set_model(tb_handle* h, const float* vp, const float* aux, con
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
-    cudaFree(tmp);
+    dfree(tmp, st);
     return cuda_fail(h, e, "tb_set_model vmax");
   }
   if (bad) {
-    cudaFree(tmp);
+    dfree(tmp, st);
     return fail(h, TB_EINVAL, "vp must be finite and > 0 everywhere");
   }
   double dtmax = tb_cfl_dt_max(h->so, h->h, vmax);
@@ -483,13 +499,13 @@ extern "C" int tb_set_model(tb_handle* h, const float* vp, const float* aux, con
     if (e == cudaSuccess) e = cudaMemcpyAsync(&emax_bits, d_emax, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(tmpa);
+    dfree(tmpa, st);
     if (e != cudaSuccess) {
-      cudaFree(tmp);
+      dfree(tmp, st);
       return cuda_fail(h, e, "tb_set_model coefficients");
     }
     if (bad) {
-      cudaFree(tmp);
+      dfree(tmp, st);
       return fail(h, h->physics == TB_TTI ? TB_EUNSTABLE : TB_EINVAL,
                   h->physics == TB_TTI ? "TTI needs eps >= delta > -1/2 and finite angles everywhere"
                                        : "elastic needs rho > 0, vs >= 0 and 2 vs^2 <= vp^2 everywhere");
@@ -502,7 +518,7 @@ extern "C" int tb_set_model(tb_handle* h, const float* vp, const float* aux, con
   }
   if (dt == 0.0) dt = 0.8 * dtmax;
   if (dt > dtmax) {
-    cudaFree(tmp);
+    dfree(tmp, st);
     return fail(h, TB_EUNSTABLE, "dt = %g exceeds the CFL limit %g for vmax = %g", dt, dtmax, (double)vmax);
   }
   // damping: per-axis eta (1/s) -> b = eta / (2 dt)
@@ -514,7 +530,7 @@ extern "C" int tb_set_model(tb_handle* h, const float* vp, const float* aux, con
       e = cudaMemcpyAsync(hd.data(), damp, sizeof(float) * nsum, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) {
-        cudaFree(tmp);
+        dfree(tmp, st);
         return cuda_fail(h, e, "tb_set_model damp");
       }
     } else {
@@ -522,7 +538,7 @@ extern "C" int tb_set_model(tb_handle* h, const float* vp, const float* aux, con
     }
     for (int64_t i = 0; i < nsum; ++i) {
       if (!(hd[i] >= 0.f) || !std::isfinite(hd[i])) {
-        cudaFree(tmp);
+        dfree(tmp, st);
         return fail(h, TB_EINVAL, "damping coefficients must be finite and >= 0");
       }
       eta[i] = hd[i];
@@ -545,7 +561,7 @@ extern "C" int tb_set_model(tb_handle* h, const float* vp, const float* aux, con
   if (e == cudaSuccess)
     e = model_c2((const float*)dvp, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->n2p, dt * dt, h->c2, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // b (host vector) must outlive the copy
-  cudaFree(tmp);
+  dfree(tmp, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "tb_set_model c2");
   (void)edt;
   h->dt = dt;
@@ -564,13 +580,14 @@ extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int 
   if (nsrc < 0 || (nsrc > 0 && (!coords || !wav || nt <= 0)))
     return fail(h, TB_EINVAL, "bad source arguments");
   cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
   void *t1 = nullptr, *t2 = nullptr;
   const void *dc = nullptr, *dw = nullptr;
   if (nsrc > 0) {
     TB_CUDA(h, to_device(coords, sizeof(double) * 3 * nsrc, &t1, &dc, st));
     cudaError_t e = to_device(wav, sizeof(float) * (size_t)nsrc * nt, &t2, &dw, st);
     if (e != cudaSuccess) {
-      cudaFree(t1);
+      dfree(t1, st);
       return cuda_fail(h, e, "tb_set_sources wavelets");
     }
   }
@@ -579,16 +596,16 @@ extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int 
   // corner tables too: the adjoint gathers the source-wavelet gradient with them
   int s = inspect(h->n, h->h, nsrc, (const double*)dc, true, &h->src, st, &why);
   if (s != TB_OK) {
-    cudaFree(t1);
-    cudaFree(t2);
+    dfree(t1, st);
+    dfree(t2, st);
     return fail(h, s, "source inspector: %s", why);
   }
-  cudaFree(h->src_dcmp);
+  dfree(h->src_dcmp, st);
   h->src_dcmp = nullptr;
   h->src_nt = nsrc > 0 ? nt : 0;
   cudaError_t e = cudaSuccess;
   if (h->src.npts > 0) {
-    e = cudaMalloc(&h->src_dcmp, sizeof(float) * (size_t)nt * h->src.npts);
+    e = dmalloc(&h->src_dcmp, sizeof(float) * (size_t)nt * h->src.npts, st);
     if (e == cudaSuccess)
       // acoustic / TTI: dt^2/m at the point (Eq. 1's s dt^2/m); elastic:
       // explosive source into the normal stresses, dt q
@@ -596,8 +613,8 @@ extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int 
                     (int)h->n[1], (int)h->n[2], h->n2p, h->src_dcmp, st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(t1);
-  cudaFree(t2);
+  dfree(t1, st);
+  dfree(t2, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "tb_set_sources decomposition");
   h->have_src = true;
   h->last_nt = -1;
@@ -609,13 +626,14 @@ extern "C" int tb_set_receivers(tb_handle* h, int nrec, const double* coords, vo
   if (!h) return TB_EINVAL;
   if (nrec < 0 || (nrec > 0 && !coords)) return fail(h, TB_EINVAL, "bad receiver arguments");
   cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
   void* t1 = nullptr;
   const void* dc = nullptr;
   if (nrec > 0) TB_CUDA(h, to_device(coords, sizeof(double) * 3 * nrec, &t1, &dc, st));
   const char* why = "";
   h->have_rec = false;
   int s = inspect(h->n, h->h, nrec, (const double*)dc, true, &h->rec, st, &why);
-  cudaFree(t1);
+  dfree(t1, st);
   if (s != TB_OK) return fail(h, s, "receiver inspector: %s", why);
   h->have_rec = true;
   h->last_nt = -1;
@@ -715,52 +733,53 @@ static int plan_sweep(tb_handle* h, int T, Plan* pl) {
   return TB_OK;
 }
 
-static int ensure_capacity(tb_handle* h, int T, const Plan& pl, int nt, bool host_traces, int nrec) {
+static int ensure_capacity(tb_handle* h, int T, const Plan& pl, int nt, bool host_traces, int nrec,
+                           cudaStream_t st) {
   SweepShape sh;
   sweep_shape(h->R, T, &sh);
   if (T > 1) {
     const size_t need = (size_t)sh.ring_floats_per_cta * pl.max_ctas;
     if (need > h->ring_floats) {
-      cudaFree(h->ring);
+      dfree(h->ring, st);
       h->ring = nullptr;
       h->ring_floats = 0;
-      TB_CUDA(h, cudaMalloc(&h->ring, sizeof(float) * need));
+      TB_CUDA(h, dmalloc(&h->ring, sizeof(float) * need, st));
       h->ring_floats = need;
     }
     if (pl.max_ctas > h->progress_n) {
-      cudaFree(h->progress);
+      dfree(h->progress, st);
       h->progress = nullptr;
       h->progress_n = 0;
-      TB_CUDA(h, cudaMalloc(&h->progress, sizeof(unsigned long long) * pl.max_ctas));
-      TB_CUDA(h, cudaMemset(h->progress, 0, sizeof(unsigned long long) * pl.max_ctas));
+      TB_CUDA(h, dmalloc(&h->progress, sizeof(unsigned long long) * pl.max_ctas, st));
+      TB_CUDA(h, cudaMemsetAsync(h->progress, 0, sizeof(unsigned long long) * pl.max_ctas, st));
       h->progress_n = pl.max_ctas;
       h->prog_base = 0;
     }
   }
   if ((int)pl.launch_passes.size() > h->pass_cap) {
-    cudaFree(h->d_pass);
+    dfree(h->d_pass, st);
     h->d_pass = nullptr;
     h->pass_cap = 0;
-    TB_CUDA(h, cudaMalloc(&h->d_pass, sizeof(PassDesc) * pl.launch_passes.size()));
+    TB_CUDA(h, dmalloc(&h->d_pass, sizeof(PassDesc) * pl.launch_passes.size(), st));
     h->pass_cap = (int)pl.launch_passes.size();
   }
   if (h->have_rec && h->rec.npts > 0) {
     const int cap = std::max(16, T) / T * T;
     if (cap > h->rec_cap) {
-      cudaFree(h->rec_dcmp);
+      dfree(h->rec_dcmp, st);
       h->rec_dcmp = nullptr;
       h->rec_cap = 0;
-      TB_CUDA(h, cudaMalloc(&h->rec_dcmp, sizeof(float) * (size_t)cap * h->rec.npts));
+      TB_CUDA(h, dmalloc(&h->rec_dcmp, sizeof(float) * (size_t)cap * h->rec.npts, st));
       h->rec_cap = cap;
     }
   }
   if (host_traces && nrec > 0) {
     const size_t need = (size_t)nt * nrec;
     if (need > h->traces_cap) {
-      cudaFree(h->traces_dev);
+      dfree(h->traces_dev, st);
       h->traces_dev = nullptr;
       h->traces_cap = 0;
-      TB_CUDA(h, cudaMalloc(&h->traces_dev, sizeof(float) * need));
+      TB_CUDA(h, dmalloc(&h->traces_dev, sizeof(float) * need, st));
       h->traces_cap = need;
     }
   }
@@ -789,17 +808,17 @@ static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
   const bool host_traces = traces && nrec > 0 && !is_device_ptr(traces);
   const size_t fbytes = sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n2p;
   if (rec_on && h->rec_cap < 16) {
-    cudaFree(h->rec_dcmp);
+    dfree(h->rec_dcmp, st);
     h->rec_dcmp = nullptr;
     h->rec_cap = 0;
-    TB_CUDA(h, cudaMalloc(&h->rec_dcmp, sizeof(float) * 16 * h->rec.npts));
+    TB_CUDA(h, dmalloc(&h->rec_dcmp, sizeof(float) * 16 * h->rec.npts, st));
     h->rec_cap = 16;
   }
   if (host_traces && (size_t)nt * nrec > h->traces_cap) {
-    cudaFree(h->traces_dev);
+    dfree(h->traces_dev, st);
     h->traces_dev = nullptr;
     h->traces_cap = 0;
-    TB_CUDA(h, cudaMalloc(&h->traces_dev, sizeof(float) * (size_t)nt * nrec));
+    TB_CUDA(h, dmalloc(&h->traces_dev, sizeof(float) * (size_t)nt * nrec, st));
     h->traces_cap = (size_t)nt * nrec;
   }
   float* dtr = host_traces ? h->traces_dev : traces;
@@ -902,6 +921,7 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   if (h->have_src && h->src.npts > 0 && nt > h->src_nt)
     return fail(h, TB_EINVAL, "nt = %d exceeds the wavelet length %d", nt, h->src_nt);
   cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
   if (h->physics != TB_ACOUSTIC) {
     if (schedule != TB_ONESTEP)
       return fail(h, TB_EINVAL, "the blocked schedule is implemented for the acoustic equation only");
@@ -916,8 +936,8 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   int s = plan_sweep(h, 1, &p1);
   if (s != TB_OK) return s;
   if (T > 1 && (s = plan_sweep(h, T, &pT)) != TB_OK) return s;
-  if ((s = ensure_capacity(h, 1, p1, nt, host_traces, nrec)) != TB_OK) return s;
-  if (T > 1 && (s = ensure_capacity(h, T, pT, nt, host_traces, nrec)) != TB_OK) return s;
+  if ((s = ensure_capacity(h, 1, p1, nt, host_traces, nrec, st)) != TB_OK) return s;
+  if (T > 1 && (s = ensure_capacity(h, T, pT, nt, host_traces, nrec, st)) != TB_OK) return s;
   if (host_traces) dtr = h->traces_dev;
 
   const size_t fbytes = sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n2p;
@@ -959,10 +979,10 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   const int off_T = (int)all.size();
   if (T > 1) all.insert(all.end(), pT.launch_passes.begin(), pT.launch_passes.end());
   if ((int)all.size() > h->pass_cap) {
-    cudaFree(h->d_pass);
+    dfree(h->d_pass, st);
     h->d_pass = nullptr;
     h->pass_cap = 0;
-    TB_CUDA(h, cudaMalloc(&h->d_pass, sizeof(PassDesc) * all.size()));
+    TB_CUDA(h, dmalloc(&h->d_pass, sizeof(PassDesc) * all.size(), st));
     h->pass_cap = (int)all.size();
   }
   TB_CUDA(h, cudaMemcpyAsync(h->d_pass, all.data(), sizeof(PassDesc) * all.size(),
@@ -1078,6 +1098,7 @@ extern "C" int tb_get_field(tb_handle* h, int which, float* out, void* stream) {
   const int nwhich = h->physics == TB_ACOUSTIC ? 2 : (h->physics == TB_TTI ? 4 : 9);
   if (which < 0 || which >= nwhich || !out) return fail(h, TB_EINVAL, "bad arguments");
   cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
   const float* src = nullptr;
   if (h->physics == TB_ACOUSTIC) {
     src = h->field[which == 0 ? h->cur_idx : h->prev_idx];
@@ -1095,11 +1116,11 @@ extern "C" int tb_get_field(tb_handle* h, int which, float* out, void* stream) {
     return TB_OK;
   }
   float* tmp = nullptr;
-  TB_CUDA(h, cudaMalloc(&tmp, sizeof(float) * N));
+  TB_CUDA(h, dmalloc(&tmp, sizeof(float) * N, st));
   cudaError_t e = unpad_copy(src, tmp, (int)h->n[0], (int)h->n[1], (int)h->n[2], h->n2p, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, sizeof(float) * N, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(tmp);
+  dfree(tmp, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "tb_get_field");
   return TB_OK;
 }
@@ -1158,7 +1179,7 @@ struct StepRunner {
 static int runner_init(tb_handle* h, StepRunner* r, cudaStream_t st) {
   int s = plan_sweep(h, 1, &r->p1);
   if (s != TB_OK) return s;
-  if ((s = ensure_capacity(h, 1, r->p1, 0, false, 0)) != TB_OK) return s;
+  if ((s = ensure_capacity(h, 1, r->p1, 0, false, 0, st)) != TB_OK) return s;
   TB_CUDA(h, cudaMemcpyAsync(h->d_pass, r->p1.launch_passes.data(), sizeof(PassDesc) * r->p1.launch_passes.size(),
                              cudaMemcpyHostToDevice, st));
   SweepParams& P = r->P;
@@ -1218,6 +1239,7 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
   if (h->src.npts > 0 && nt > h->src_nt)
     return fail(h, TB_EINVAL, "nt = %d exceeds the wavelet length %d", nt, h->src_nt);
   cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
   const int nrec = h->rec.npt, nsrc = h->src.npt;
   const int64_t nrp = h->rec.npts, nsp = h->src.npts;
   const size_t Np = (size_t)h->n[0] * h->n[1] * h->n2p, fbytes = sizeof(float) * Np;
@@ -1232,12 +1254,12 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
   std::vector<void*> bufs;
   auto alloc = [&](size_t bytes) -> void* {
     void* p = nullptr;
-    if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) return nullptr;
+    if (dmalloc(&p, bytes ? bytes : 1, st) != cudaSuccess) return nullptr;
     bufs.push_back(p);
     return p;
   };
   auto cleanup = [&]() {
-    for (void* p : bufs) cudaFree(p);
+    for (void* p : bufs) dfree(p, st);
     bufs.clear();
   };
   float* snap = (float*)alloc(fbytes * 2 * std::max(nseg - 1, 1));

@@ -230,18 +230,18 @@ __global__ void k_fill_i32(int* a, int64_t n, int v) {
   if (i < n) a[i] = v;
 }
 
-void free_tables(PointTables* t) {
-  cudaFree(t->lin);
-  cudaFree(t->colptr);
-  cudaFree(t->ent);
-  cudaFree(t->corner_id);
-  cudaFree(t->corner_eid);
-  cudaFree(t->corner_w);
-  cudaFree(t->eid_of_id);
-  cudaFree(t->keys);
-  cudaFree(t->w8);
-  cudaFree(t->gstart);
-  cudaFree(t->ent_id);
+void free_tables(PointTables* t, cudaStream_t st) {
+  dfree(t->lin, st);
+  dfree(t->colptr, st);
+  dfree(t->ent, st);
+  dfree(t->corner_id, st);
+  dfree(t->corner_eid, st);
+  dfree(t->corner_w, st);
+  dfree(t->eid_of_id, st);
+  dfree(t->keys, st);
+  dfree(t->w8, st);
+  dfree(t->gstart, st);
+  dfree(t->ent_id, st);
   *t = PointTables();
 }
 
@@ -249,12 +249,12 @@ static unsigned grid_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b);
 
 int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coords,
             bool want_corners, PointTables* t, cudaStream_t st, const char** why) {
-  free_tables(t);
+  free_tables(t, st);
   t->npt = npt;
   const int64_t ncol = n[1] * n[2];
   if (npt <= 0) {
     // empty set: all-zero column pointers
-    if (cudaMalloc(&t->colptr, sizeof(int) * (ncol + 1)) != cudaSuccess) return TB_ENOMEM;
+    if (dmalloc(&t->colptr, sizeof(int) * (ncol + 1), st) != cudaSuccess) return TB_ENOMEM;
     cudaMemsetAsync(t->colptr, 0, sizeof(int) * (ncol + 1), st);
     t->bytes = sizeof(int) * (ncol + 1);
     return cudaGetLastError() == cudaSuccess ? TB_OK : TB_ECUDA;
@@ -273,12 +273,12 @@ int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coor
     if (e != cudaSuccess && status == TB_OK) status = (e == cudaErrorMemoryAllocation) ? TB_ENOMEM : TB_ECUDA;
     return e == cudaSuccess;
   };
-  if (!ok(cudaMalloc(&t->keys, sizeof(unsigned long long) * P)) ||
-      !ok(cudaMalloc(&t->w8, sizeof(double) * npt * 8)) ||
-      !ok(cudaMalloc(&t->ent_id, sizeof(int) * P)) || !ok(cudaMalloc(&d_bad, sizeof(int) * 4)) ||
-      !ok(cudaMalloc(&d_counts, sizeof(int64_t) * 2))) {
-    cudaFree(d_bad);
-    cudaFree(d_counts);
+  if (!ok(dmalloc(&t->keys, sizeof(unsigned long long) * P, st)) ||
+      !ok(dmalloc(&t->w8, sizeof(double) * npt * 8, st)) ||
+      !ok(dmalloc(&t->ent_id, sizeof(int) * P, st)) || !ok(dmalloc(&d_bad, sizeof(int) * 4, st)) ||
+      !ok(dmalloc(&d_counts, sizeof(int64_t) * 2, st))) {
+    dfree(d_bad, st);
+    dfree(d_counts, st);
     return status;
   }
   ok(cudaMemsetAsync(d_bad, 0, sizeof(int) * 4, st));
@@ -293,8 +293,8 @@ int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coor
   ok(bitonic_sort(t->keys, P, st));
   // upper bound for npts is the number of corners; allocate that much
   const int64_t maxpts = (int64_t)npt * 8;
-  ok(cudaMalloc(&t->lin, sizeof(int64_t) * maxpts));
-  ok(cudaMalloc(&t->gstart, sizeof(int64_t) * (maxpts + 1)));
+  ok(dmalloc(&t->lin, sizeof(int64_t) * maxpts, st));
+  ok(dmalloc(&t->gstart, sizeof(int64_t) * (maxpts + 1), st));
   if (status != TB_OK) goto fail;
   count_launch();
   k_unique<<<1, 1024, 0, st>>>(t->keys, P, t->lin, t->gstart, t->ent_id, d_counts);
@@ -318,10 +318,10 @@ int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coor
   {
     int64_t P2 = 2048;
     while (P2 < t->npts) P2 <<= 1;
-    ok(cudaMalloc(&keys2, sizeof(unsigned long long) * P2));
-    ok(cudaMalloc(&t->colptr, sizeof(int) * (ncol + 1)));
-    ok(cudaMalloc(&t->ent, sizeof(int2) * (t->npts > 0 ? t->npts : 1)));
-    ok(cudaMalloc(&t->eid_of_id, sizeof(int) * (t->npts > 0 ? t->npts : 1)));
+    ok(dmalloc(&keys2, sizeof(unsigned long long) * P2, st));
+    ok(dmalloc(&t->colptr, sizeof(int) * (ncol + 1), st));
+    ok(dmalloc(&t->ent, sizeof(int2) * (t->npts > 0 ? t->npts : 1), st));
+    ok(dmalloc(&t->eid_of_id, sizeof(int) * (t->npts > 0 ? t->npts : 1), st));
     if (status != TB_OK) goto fail;
     count_launch();
     k_fill_u64<<<grid_for(P2, 256), 256, 0, st>>>(keys2, 0, P2, kSentinel);
@@ -335,9 +335,9 @@ int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coor
     ok(cudaGetLastError());
   }
   if (want_corners) {
-    ok(cudaMalloc(&t->corner_id, sizeof(int) * npt * 8));
-    ok(cudaMalloc(&t->corner_eid, sizeof(int) * npt * 8));
-    ok(cudaMalloc(&t->corner_w, sizeof(float) * npt * 8));
+    ok(dmalloc(&t->corner_id, sizeof(int) * npt * 8, st));
+    ok(dmalloc(&t->corner_eid, sizeof(int) * npt * 8, st));
+    ok(dmalloc(&t->corner_w, sizeof(float) * npt * 8, st));
     if (status != TB_OK) goto fail;
     count_launch();
     k_fill_i32<<<grid_for((int64_t)npt * 8, 256), 256, 0, st>>>(t->corner_id, (int64_t)npt * 8, -1);
@@ -351,18 +351,18 @@ int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coor
   }
   ok(cudaStreamSynchronize(st));
   if (status != TB_OK) goto fail;
-  cudaFree(keys2);
-  cudaFree(d_bad);
-  cudaFree(d_counts);
+  dfree(keys2, st);
+  dfree(d_bad, st);
+  dfree(d_counts, st);
   t->bytes = sizeof(unsigned long long) * P + sizeof(double) * npt * 8 + sizeof(int) * P +
              sizeof(int64_t) * (2 * maxpts + 1) + sizeof(int) * (ncol + 1) + (sizeof(int2) + sizeof(int)) * t->npts +
              (want_corners ? (2 * sizeof(int) + sizeof(float)) * npt * 8 : 0);
   return TB_OK;
 fail:
-  cudaFree(keys2);
-  cudaFree(d_bad);
-  cudaFree(d_counts);
-  free_tables(t);
+  dfree(keys2, st);
+  dfree(d_bad, st);
+  dfree(d_counts, st);
+  free_tables(t, st);
   return status;
 }
 

@@ -132,7 +132,18 @@ cudaError_t adjoint_finish(const PhysGrid& g, double dt, const double* gm, const
                            cudaStream_t st);
 cudaError_t transpose_f32(int64_t rows, int64_t cols, const float* in, float* out, cudaStream_t st);
 
-void free_tables(PointTables* t);
+// Stream-ordered device memory (cudaMallocAsync / cudaFreeAsync): creating,
+// reconfiguring or destroying a handle never synchronises the whole device,
+// so work of other handles on other streams keeps running meanwhile.
+template <class T>
+inline cudaError_t dmalloc(T** p, size_t bytes, cudaStream_t st) {
+  return cudaMallocAsync(reinterpret_cast<void**>(p), bytes ? bytes : 1, st);
+}
+inline void dfree(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+void free_tables(PointTables* t, cudaStream_t st);
 // Builds lin, colptr, ent (+ corner tables when want_corners).  coords on
 // the device.  Returns TB_OK / TB_EINVAL / TB_ENOMEM / TB_ECUDA.
 int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coords,

@@ -13,8 +13,8 @@ __global__ void k_selftest_wait(const unsigned long long* flag, long long timeou
 cudaError_t selftest_wait(long long timeout_ns, cudaStream_t st, int* timed_out) {
   unsigned long long* flag = nullptr;
   int* err = nullptr;
-  cudaError_t e = cudaMalloc(&flag, sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  cudaError_t e = dmalloc(&flag, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = dmalloc(&err, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0xff, sizeof(int), st);
   if (e == cudaSuccess) {
@@ -25,8 +25,8 @@ cudaError_t selftest_wait(long long timeout_ns, cudaStream_t st, int* timed_out)
   int h = -1;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(flag);
-  cudaFree(err);
+  dfree(flag, st);
+  dfree(err, st);
   *timed_out = h;
   return e;
 }

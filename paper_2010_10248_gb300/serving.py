@@ -1,0 +1,194 @@
+"""Shot serving with continuous batching on one GPU.
+
+A request is one shot: its own grid, velocity model, sources, receivers and
+step count.  The server keeps a fixed set of slots; each slot owns a CUDA
+stream and a propagator handle (wavefields and model resident on the device
+for the life of the shot).  Requests are admitted in arrival order whenever a
+slot is free and the shot's device footprint fits in the memory budget;
+admitted shots run concurrently on their streams, so the kernels of small
+shots fill the GPU together while a large shot runs beside them or alone
+(when its footprint leaves no room).  A slot frees as soon as its shot's
+traces are on the host; the next waiting request enters at once, without
+waiting for the other shots in flight.
+
+Latency of a shot = time from its arrival to its traces being ready on the
+host.  The kernels are deterministic, so a shot gives bit-identical traces
+alone and in any mix.
+"""
+from __future__ import annotations
+
+import heapq
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _tb
+
+
+@dataclass
+class ShotRequest:
+    """One propagation problem.  Arrays are host numpy arrays."""
+    shape: tuple
+    spacing: tuple
+    space_order: int
+    vp: np.ndarray          # [n0, n1, n2] float32
+    src_xyz: np.ndarray     # [nsrc, 3] float64 metres
+    wavelet_f0: float       # Ricker peak frequency (sampled with the shot's dt)
+    rec_xyz: np.ndarray     # [nrec, 3] float64 metres
+    nt: int
+    nbl: int = 0
+    time_tile: int = 0      # 0: blocked sweep with the largest tile; 1: one-step
+    arrival: float = 0.0    # seconds after the start of the run
+    tag: object = None
+
+
+@dataclass
+class ShotResult:
+    tag: object
+    traces: np.ndarray
+    dt: float
+    arrival: float
+    start: float
+    done: float
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def footprint_bytes(req: ShotRequest) -> int:
+    """Device bytes a shot holds while it runs: four wavefield buffers and the
+    c2 field (padded rows), sponge tables, inspector tables, the receiver
+    staging rows and the trace buffer, plus the blocked sweep's halo ring."""
+    n0, n1, n2 = (int(s) for s in req.shape)
+    n2p = (n2 + 3) // 4 * 4
+    fields = 5 * 4 * n0 * n1 * n2p
+    nrec = len(req.rec_xyz)
+    tables = 64 * 8 * (len(req.src_xyz) + nrec) + 8 * n1 * n2
+    rec_rows = 16 * 4 * 8 * nrec
+    traces = 4 * req.nt * nrec
+    ring = 4 * ((n1 + 15) // 16 + 2) * ((n2 + 63) // 64) * 3 * 10 * 8 * 72
+    return fields + tables + rec_rows + traces + ring + (8 << 20)
+
+
+class _Slot:
+    def __init__(self, torch):
+        self.torch = torch
+        self.stream = torch.cuda.Stream()
+        self.done_event = None
+        self.prop = None
+        self.req = None
+        self.start = 0.0
+        self.host_traces = None
+        self.bytes = 0
+
+    def launch(self, req: ShotRequest, t0: float):
+        from . import Propagator
+        torch = self.torch
+        self.req = req
+        self.start = time.perf_counter() - t0
+        with torch.cuda.stream(self.stream):
+            self.prop = Propagator(req.shape, req.spacing, req.space_order, nbl=req.nbl,
+                                   time_tile=req.time_tile)
+            p = self.prop
+            st = self.stream
+            _tb.tb_set_model(p.h, req.vp, None, None, 0.0, st)
+            dt = _tb.tb_get_dt(p.h)
+            w = _ricker(req.wavelet_f0, dt, req.nt)
+            wav = np.repeat(w[None, :], len(req.src_xyz), axis=0).astype(np.float32)
+            _tb.tb_set_sources(p.h, len(req.src_xyz), np.ascontiguousarray(req.src_xyz, dtype=np.float64),
+                               req.nt, wav, st)
+            _tb.tb_set_receivers(p.h, len(req.rec_xyz), np.ascontiguousarray(req.rec_xyz, dtype=np.float64), st)
+            dev_tr = torch.empty((req.nt, len(req.rec_xyz)), dtype=torch.float32, device="cuda")
+            sched = _tb.TB_BLOCKED if req.time_tile != 1 else _tb.TB_ONESTEP
+            _tb.tb_forward(p.h, req.nt, dev_tr, sched, st)
+            self.host_traces = torch.empty(dev_tr.shape, dtype=torch.float32, pin_memory=True)
+            self.host_traces.copy_(dev_tr, non_blocking=True)
+            self.dev_tr = dev_tr
+            self.dt = dt
+            self.done_event = torch.cuda.Event()
+            self.done_event.record(self.stream)
+
+    def ready(self) -> bool:
+        return self.done_event is not None and self.done_event.query()
+
+    def finish(self, t0: float) -> ShotResult:
+        r = ShotResult(self.req.tag, self.host_traces.numpy().copy(), self.dt, self.req.arrival,
+                       self.start, time.perf_counter() - t0)
+        self.prop.close()
+        self.prop = None
+        self.req = None
+        self.done_event = None
+        self.dev_tr = None
+        return r
+
+
+def _ricker(f0, dt, nt):
+    t = np.arange(nt) * dt - 1.0 / f0
+    a = (np.pi * f0 * t) ** 2
+    return (1.0 - 2.0 * a) * np.exp(-a)
+
+
+class ShotServer:
+    """Continuous-batching server: ``run(requests)`` processes a stream of
+    requests (arrival times in ``ShotRequest.arrival``, seconds from the start)
+    and returns their results in completion order."""
+
+    def __init__(self, slots: int = 8, memory_budget: int | None = None, poll_s: float = 2e-4):
+        import torch
+        self.torch = torch
+        self.slots = [_Slot(torch) for _ in range(slots)]
+        if memory_budget is None:
+            free, _ = torch.cuda.mem_get_info()
+            memory_budget = int(free * 0.85)
+        self.budget = int(memory_budget)
+        self.poll_s = poll_s
+        self.stats = {"max_in_flight": 0, "max_bytes": 0}
+
+    def run(self, requests):
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        for r in reqs:
+            if footprint_bytes(r) > self.budget:
+                raise ValueError(f"shot {r.tag}: footprint {footprint_bytes(r)} exceeds the budget {self.budget}")
+        pending = list(reqs)
+        waiting = []      # arrived, not admitted (arrival order)
+        results = []
+        in_use = 0
+        t0 = time.perf_counter()
+        busy = []
+        while pending or waiting or busy:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                waiting.append(pending.pop(0))
+            # retire finished shots (frees their slot and memory at once)
+            for s in list(busy):
+                if s.ready():
+                    in_use -= s.bytes
+                    results.append(s.finish(t0))
+                    busy.remove(s)
+            # admit in arrival order while a slot is free and the shot fits
+            while waiting:
+                free_slots = [s for s in self.slots if s not in busy]
+                need = footprint_bytes(waiting[0])
+                if not free_slots or in_use + need > self.budget:
+                    break
+                req = waiting.pop(0)
+                slot = free_slots[0]
+                slot.bytes = need
+                in_use += need
+                slot.launch(req, t0)
+                busy.append(slot)
+                self.stats["max_in_flight"] = max(self.stats["max_in_flight"], len(busy))
+                self.stats["max_bytes"] = max(self.stats["max_bytes"], in_use)
+            if busy or waiting or pending:
+                nxt = pending[0].arrival - (time.perf_counter() - t0) if pending and not waiting else 0
+                time.sleep(min(self.poll_s, max(nxt, 0.0)) if busy else max(min(nxt, 0.01), 0.0))
+        return results
+
+
+def percentile(values, q):
+    v = np.sort(np.asarray(values, dtype=np.float64))
+    if v.size == 0:
+        return float("nan")
+    return float(np.percentile(v, q))

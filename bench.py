@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--serving", action="store_true",
+                    help="Poisson stream of acoustic so8 shots of mixed sizes through the continuous-"
+                         "batching server: p50/p99 shot latency and aggregate GPts/s")
+    ap.add_argument("--shots", type=int, default=48)
+    ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--physics", default="acoustic", choices=["acoustic", "tti", "elastic"],
                     help="tti / elastic: the 384^3 so8 500-step TTI or elastic workload, one-step "
                          "schedule (the headline line is the acoustic one)")
@@ -436,8 +441,80 @@ def run_physics(args):
     prop.close()
 
 
+def serving_shots(n, seed):
+    """The serving workload: grids uniform over multiples of 32 in [128, 512]
+    per axis, 300-1500 steps, 1-4 off-grid sources, 1k-64k receivers
+    (log-uniform), seeded layered vp, so8, 10 m spacing."""
+    from paper_2010_10248_gb300 import serving
+    from paper_2010_10248_gb300 import workloads as wl
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        shape = tuple(int(32 * g.integers(4, 17)) for _ in range(3))
+        h = (10.0, 10.0, 10.0)
+        ext = np.array([(shape[d] - 1) * h[d] for d in range(3)])
+        nbl = 20
+        vp = wl.layered_vp(shape, seed + 1000 + i, nblobs=0)
+        nsrc = int(g.integers(1, 5))
+        src = np.stack([g.uniform(0.3, 0.7, nsrc) * ext[0], g.uniform(0.3, 0.7, nsrc) * ext[1],
+                        np.full(nsrc, (nbl + 5 + g.uniform(0.1, 0.9)) * h[2])], axis=1)
+        nrec = int(np.exp(g.uniform(np.log(1000), np.log(64000))))
+        rec = np.stack([g.uniform(0.02, 0.98, nrec) * ext[0], g.uniform(0.02, 0.98, nrec) * ext[1],
+                        np.full(nrec, (nbl + 8 + g.uniform(0.1, 0.9)) * h[2])], axis=1)
+        out.append(serving.ShotRequest(shape, h, 8, vp, src, 15.0, rec, nt=int(g.integers(300, 1501)), nbl=nbl,
+                                       time_tile=1, tag=i))
+    return out
+
+
+def run_serving(args):
+    import torch
+    import paper_2010_10248_gb300 as tb
+    from paper_2010_10248_gb300 import build as tbbuild
+    from paper_2010_10248_gb300 import serving
+    torch.cuda.set_device(0)
+    tbbuild.build()
+    tb.load()
+    reqs = serving_shots(args.shots, 2010_10248 + 4)
+    work = np.array([np.prod(r.shape) * r.nt for r in reqs], dtype=np.float64)
+    # capacity from two calibration shots run alone
+    cal = serving.ShotServer(slots=1)
+    t0 = time.perf_counter()
+    cal.run([serving.ShotRequest(**{**reqs[0].__dict__, "tag": "cal0"}),
+             serving.ShotRequest(**{**reqs[1].__dict__, "tag": "cal1"})])
+    cap = (work[0] + work[1]) / (time.perf_counter() - t0)  # point updates / s, one at a time
+    rate = 0.8 * cap / work.mean()                           # shots / s at 80 % of that capacity
+    g = np.random.Generator(np.random.PCG64(2010_10248 + 5))
+    arr = np.cumsum(g.exponential(1.0 / rate, size=len(reqs)))
+    for r, a in zip(reqs, arr):
+        r.arrival = float(a - arr[0])
+    srv = serving.ShotServer(slots=args.slots)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    lat = [r.latency for r in res]
+    value = work.sum() / wall / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": 2,
+            "ms_per_step": wall / len(reqs) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving: Poisson stream of {len(reqs)} acoustic so8 shots, grids 128^3-512^3 "
+                                   "(multiples of 32), 300-1500 steps, 1-4 sources, 1k-64k receivers",
+                       "arrival_rate_per_s": rate, "slots": args.slots, "schedule": "onestep",
+                       "precision": "fp32 storage only (fp16/bf16 storage not built)"},
+            "latency_s": {"p50": serving.percentile(lat, 50), "p99": serving.percentile(lat, 99),
+                          "mean": float(np.mean(lat)), "max": float(np.max(lat))},
+            "capacity_alone_gpts": cap / 1e9, "max_in_flight": srv.stats["max_in_flight"],
+            "max_bytes_in_flight": srv.stats["max_bytes"], "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.impl == "native" and args.serving:
+        run_serving(args)
+        return
     if args.impl == "native" and args.physics != "acoustic":
         run_physics(args)
         return

@@ -57,6 +57,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, dist, device):
+    """Step time of the slowest rank (the whole job ends when it ends)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(points_per_rank_step, steps, ms, world):
+    """Whole-job GPts/s: every rank runs an independent replica, so the units
+    of all ranks count, over the slowest rank's time."""
+    return world * points_per_rank_step * steps / (ms * 1e-3) / 1e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -269,10 +285,7 @@ def run_native(args):
             dist.barrier()
         ms = e0.elapsed_time(e1) / k
         launches = tb.tb_launch_count() - l0
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         return ms, kt_ms / max(kt_n, 1), kt_n // k, launches
 
     clocks = ClockSampler(local)
@@ -280,7 +293,7 @@ def run_native(args):
     ms_b, kms_b, kl_b, launches = timed("blocked", args.steps, args.warmup)
     clk = clocks.stop()
     tr_blocked = traces.clone()
-    value = ws * N * nt / (ms_b * 1e-3) / 1e9
+    value = job_rate(N, nt, ms_b, ws)
 
     out = {}
     if not args.no_onestep:

@@ -50,6 +50,9 @@ def parse():
                     help="Poisson stream of acoustic so8 shots of mixed sizes through the continuous-"
                          "batching server: p50/p99 shot latency and aggregate GPts/s")
     ap.add_argument("--shots", type=int, default=48)
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "plain"],
+                    help="f16 / bf16 / plain: the 512^3 acoustic shot with 16-bit (or plain FP32) wavefield "
+                         "storage in the streaming one-step kernel")
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--physics", default="acoustic", choices=["acoustic", "tti", "elastic"],
                     help="tti / elastic: the 384^3 so8 500-step TTI or elastic workload, one-step "
@@ -523,8 +526,80 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_storage(args):
+    """The acoustic benchmark shot with 16-bit (or plain FP32) wavefield
+    storage: one-step streaming kernel, FP32 arithmetic."""
+    import torch
+    import paper_2010_10248_gb300 as tb
+    from paper_2010_10248_gb300 import build as tbbuild
+    from paper_2010_10248_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    tbbuild.build()
+    tb.load()
+    stor = {"f16": tb.TB_F16, "bf16": tb.TB_BF16, "plain": tb.TB_F32_PLAIN}[args.storage]
+    w = wl.acoustic_512_so8(shape=(args.size,) * 3, nt=args.nt)
+    N, nt = int(np.prod(w.shape)), w.nt
+    dev = torch.device("cuda", 0)
+    prop = tb.Propagator(w.shape, w.spacing, w.so, nbl=w.nbl, storage=stor, profile=True)
+    st = torch.cuda.current_stream()
+    vp = torch.from_numpy(w.vp).to(dev)
+    prop.set_model(vp)
+    dt = prop.dt
+    wav = torch.from_numpy(w.wavelets(dt).astype(np.float32)).to(dev)
+    src = torch.from_numpy(w.src_xyz).to(dev)
+    rec = torch.from_numpy(w.rec_xyz).to(dev)
+    traces = torch.empty((nt, len(w.rec_xyz)), dtype=torch.float32, device=dev)
+
+    def shot():
+        tb.tb_set_model(prop.h, vp, None, None, 0.0, st)
+        tb.tb_set_sources(prop.h, len(w.src_xyz), src, nt, wav, st)
+        tb.tb_set_receivers(prop.h, len(w.rec_xyz), rec, st)
+        tb.tb_forward(prop.h, nt, traces, tb.TB_ONESTEP, st)
+
+    for _ in range(args.warmup):
+        shot()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms, kn = 0.0, 0
+    l0 = tb.tb_launch_count()
+    e0.record(st)
+    for _ in range(args.steps):
+        shot()
+        n, ms = prop.kernel_time(0)
+        kms += ms
+        kn += n
+    e1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    step_ms = kms / max(kn, 1)
+    bpp = 4.0 + (3 * 2.0 if stor != tb.TB_F32_PLAIN else 3 * 4.0)  # c2 + u^n, u^{n-1}, u^{n+1}
+    peak, peak_kind = measured_peaks()
+    achieved = bpp * N / (step_ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": N * nt / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"f16": "f16-storage/f32-math",
+                                                              "bf16": "bf16-storage/f32-math",
+                                                              "plain": "f32"}[args.storage],
+            "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.shape), "space_order": w.so, "nt": nt,
+                       "schedule": "onestep (streaming kernel)", "storage": args.storage,
+                       "step": "set_model + set_sources + set_receivers + forward(nt)"},
+            "gpu_launches": int(tb.tb_launch_count() - l0), "clocks": clk,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                         "bytes_per_point_step": bpp, "kernel_ms_per_step": step_ms}}
+    print(json.dumps(line), flush=True)
+    prop.close()
+
+
 def main():
     args = parse()
+    if args.impl == "native" and args.storage != "f32":
+        run_storage(args)
+        return
     if args.impl == "native" and args.serving:
         run_serving(args)
         return

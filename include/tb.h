@@ -68,6 +68,14 @@ typedef enum {
 
 enum { TB_ACOUSTIC = 0, TB_TTI = 1, TB_ELASTIC = 2 };
 enum { TB_ONESTEP = 0, TB_BLOCKED = 1 };
+/* Wavefield storage (tb_options.storage), acoustic physics:
+ *   TB_F32       FP32 fields, TMA-staged one-step and blocked sweeps (default);
+ *   TB_F16       FP16 fields, FP32 arithmetic, per-field power-of-two scales;
+ *   TB_BF16      BF16 fields, FP32 arithmetic, per-field power-of-two scales;
+ *   TB_F32_PLAIN FP32 fields through the same streaming kernel as TB_F16 /
+ *                TB_BF16 (their equal-structure FP32 baseline).
+ * The 16-bit and plain modes run one step per launch (TB_ONESTEP). */
+enum { TB_F32 = 0, TB_F16 = 1, TB_BF16 = 2, TB_F32_PLAIN = 3 };
 
 typedef struct tb_handle tb_handle;
 
@@ -88,6 +96,9 @@ typedef struct {
                       NaN/Inf (adds a device->host sync)                         */
   double wait_timeout_s; /* blocked sweep: bound on any device-side wait for a
                       neighbouring tile, seconds; 0 -> 2.0                         */
+  int storage;     /* TB_F32 (0), TB_F16, TB_BF16 or TB_F32_PLAIN; the 16-bit
+                      stored value is u / s with s = 2^(ceil(log2(4 max|u^n| +
+                      max|source step n|)) - 8), set on the device each step     */
 } tb_options;
 
 /* Create a propagator for a grid of shape n[3] with spacing h[3] (metres),

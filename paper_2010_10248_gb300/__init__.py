@@ -8,7 +8,8 @@ convenience wrapper that keeps device buffers in torch tensors.
 from __future__ import annotations
 
 from . import _tb
-from ._tb import (TB_ACOUSTIC, TB_BLOCKED, TB_ELASTIC, TB_ONESTEP, TB_TTI, Options, TBError, load,
+from ._tb import (TB_ACOUSTIC, TB_BF16, TB_BLOCKED, TB_ELASTIC, TB_F16, TB_F32, TB_F32_PLAIN, TB_ONESTEP,
+                  TB_TTI, Options, TBError, load,
                   tb_adjoint_gradient, tb_cfl_dt_max, tb_elastic_dt_max, tb_tti_dt_max,
                   tb_create, tb_destroy, tb_fd_weights, tb_forward, tb_get_dt, tb_get_field,
                   tb_get_receiver_points, tb_get_source_points, tb_kernel_time, tb_last_error,
@@ -17,7 +18,7 @@ from ._tb import (TB_ACOUSTIC, TB_BLOCKED, TB_ELASTIC, TB_ONESTEP, TB_TTI, Optio
 
 __all__ = ["Propagator", "Options", "TBError", "load", "TB_ONESTEP", "TB_BLOCKED", "TB_ACOUSTIC",
            "TB_TTI", "TB_ELASTIC", "tb_tti_dt_max", "tb_elastic_dt_max", "tb_adjoint_gradient",
-           "AcousticTraces",
+           "AcousticTraces", "TB_F32", "TB_F16", "TB_BF16", "TB_F32_PLAIN",
            "tb_create", "tb_destroy", "tb_set_model", "tb_get_dt", "tb_set_sources",
            "tb_set_receivers", "tb_forward", "tb_get_field", "tb_get_source_points",
            "tb_get_receiver_points", "tb_workspace_bytes", "tb_kernel_time", "tb_last_error",
@@ -34,16 +35,18 @@ class Propagator:
     """
 
     def __init__(self, shape, spacing, space_order, *, physics=TB_ACOUSTIC, time_tile=0, nbl=0,
-                 y_bands=0, x_chunks=0, profile=False, check_nan=False, wait_timeout_s=0.0):
+                 y_bands=0, x_chunks=0, profile=False, check_nan=False, wait_timeout_s=0.0,
+                 storage=TB_F32):
         import torch
         self._torch = torch
         opt = Options(time_tile=time_tile, nbl=nbl, y_bands=y_bands, x_chunks=x_chunks,
                       profile=int(profile), check_nan=int(check_nan),
-                      wait_timeout_s=float(wait_timeout_s))
+                      wait_timeout_s=float(wait_timeout_s), storage=int(storage))
         self.shape = tuple(int(s) for s in shape)
         self.spacing = tuple(float(s) for s in spacing)
         self.space_order = int(space_order)
         self.physics = int(physics)
+        self.storage = int(storage)
         self.h = tb_create(self.shape, self.spacing, self.space_order, self.physics, opt)
         self.nrec = 0
         self.nt_src = None
@@ -102,7 +105,7 @@ class Propagator:
         one for TTI and elastic)."""
         torch = self._torch
         if schedule is None:
-            schedule = "blocked" if self.physics == TB_ACOUSTIC else "onestep"
+            schedule = "blocked" if self.physics == TB_ACOUSTIC and self.storage == TB_F32 else "onestep"
         sched = TB_BLOCKED if schedule == "blocked" else TB_ONESTEP
         if traces is None and self.nrec > 0:
             traces = torch.empty((nt, self.nrec), dtype=torch.float32, device="cuda")

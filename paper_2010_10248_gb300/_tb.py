@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "TB_OK", 1: "TB_EINVAL", 2: "TB_ENOMEM", 3: "TB_ECUDA", 4: "T
                 5: "TB_ETIMEOUT", 6: "TB_EDIVERGED", 7: "TB_ESTATE"}
 TB_ACOUSTIC, TB_TTI, TB_ELASTIC = 0, 1, 2
 TB_ONESTEP, TB_BLOCKED = 0, 1
+TB_F32, TB_F16, TB_BF16, TB_F32_PLAIN = 0, 1, 2, 3
 
 
 class TBError(RuntimeError):
@@ -33,7 +34,7 @@ class TBError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("time_tile", C.c_int), ("nbl", C.c_int), ("y_bands", C.c_int),
                 ("x_chunks", C.c_int), ("profile", C.c_int), ("check_nan", C.c_int),
-                ("wait_timeout_s", C.c_double)]
+                ("wait_timeout_s", C.c_double), ("storage", C.c_int)]
 
 
 _lib = None

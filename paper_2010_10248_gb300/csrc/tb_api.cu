@@ -77,6 +77,16 @@ struct tb_handle {
   float* emat = nullptr;
   float* eta_dt = nullptr;
   double aux_max = 0.0;  // eps_max (TTI)
+  // 16-bit / plain storage (acoustic): two stored fields (u^n, u^{n-1}; the
+  // update writes u^{n+1} over u^{n-1}), per-step scales and maxima, per-step
+  // largest source increment
+  int storage = TB_F32;
+  void* lp[2] = {nullptr, nullptr};
+  int lp_cur = 0;
+  float* lp_scales = nullptr;
+  unsigned* lp_mx = nullptr;
+  int lp_cap = 0;
+  float* lp_srcmax = nullptr;
   // sources
   PointTables src;
   int src_nt = 0;
@@ -305,6 +315,11 @@ extern "C" int tb_destroy(tb_handle* h) {
   // stream-ordered frees after the handle's latest work (no device-wide sync)
   cudaStream_t st = h->last_stream;
   for (auto& f : h->field) dfree(f, st);
+  dfree(h->lp[0], st);
+  dfree(h->lp[1], st);
+  dfree(h->lp_scales, st);
+  dfree(h->lp_mx, st);
+  dfree(h->lp_srcmax, st);
   dfree(h->coef, st);
   dfree(h->nzb, st);
   dfree(h->flux, st);
@@ -371,8 +386,13 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   h->R = so / 2;
   h->physics = physics;
   if (opt) h->opt = *opt;
+  h->storage = h->opt.storage;
+  if (h->storage < TB_F32 || h->storage > TB_F32_PLAIN || (h->storage != TB_F32 && physics != TB_ACOUSTIC)) {
+    delete h;
+    return TB_EINVAL;
+  }
   // more fused so12 steps exceed shared memory; TTI and elastic run one step per launch
-  const int tmax = physics != TB_ACOUSTIC ? 1 : (so == 12 ? 2 : 4);
+  const int tmax = (physics != TB_ACOUSTIC || h->storage != TB_F32) ? 1 : (so == 12 ? 2 : 4);
   if (h->opt.time_tile == 0) h->opt.time_tile = tmax;
   if (h->opt.time_tile < 1 || h->opt.time_tile > tmax || h->opt.nbl < 0 || h->opt.y_bands < 0 ||
       h->opt.x_chunks < 0) {
@@ -393,7 +413,14 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
     }
   }
   const size_t fbytes = sizeof(float) * (size_t)n[0] * n[1] * h->n2p;
-  const int nfield = physics == TB_ELASTIC ? 0 : 4;
+  const int nfield = (physics == TB_ELASTIC || h->storage != TB_F32) ? 0 : 4;
+  if (h->storage != TB_F32) {
+    const size_t es = h->storage == TB_F32_PLAIN ? 4 : 2;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = dmalloc(&h->lp[i], es * (size_t)n[0] * n[1] * h->n2p, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->lp[i], 0, es * (size_t)n[0] * n[1] * h->n2p, st);
+    }
+  }
   for (int i = 0; i < nfield && e == cudaSuccess; ++i) {
     e = dmalloc(&h->field[i], fbytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->field[i], 0, fbytes, st);
@@ -416,11 +443,12 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int) * 4, st);
   SweepShape sh;
   if (e == cudaSuccess && !sweep_shape(h->R, 1, &sh)) e = cudaErrorInvalidValue;
-  for (int i = 0; i < 4 && e == cudaSuccess && physics == TB_ACOUSTIC; ++i) {
+  for (int i = 0; i < 4 && e == cudaSuccess && physics == TB_ACOUSTIC && h->storage == TB_F32; ++i) {
     e = make_tmap(&h->tm_box[i], h->field[i], n, h->n2p, sh.box_w, sh.box_h);
     if (e == cudaSuccess) e = make_tmap(&h->tm_tile[i], h->field[i], n, h->n2p, 64, sh.TY);
   }
-  if (e == cudaSuccess && physics == TB_ACOUSTIC) e = make_tmap(&h->tm_c2, h->c2, n, h->n2p, 64, sh.TY);
+  if (e == cudaSuccess && physics == TB_ACOUSTIC && h->storage == TB_F32)
+    e = make_tmap(&h->tm_c2, h->c2, n, h->n2p, 64, sh.TY);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     int code = e == cudaErrorMemoryAllocation ? TB_ENOMEM : TB_ECUDA;
@@ -612,6 +640,12 @@ extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int 
       e = decompose(&h->src, nt, (const float*)dw, h->physics == TB_ELASTIC ? nullptr : h->c2, h->dt,
                     (int)h->n[1], (int)h->n[2], h->n2p, h->src_dcmp, st);
   }
+  if (e == cudaSuccess && h->storage != TB_F32 && h->src.npts > 0) {
+    dfree(h->lp_srcmax, st);
+    h->lp_srcmax = nullptr;
+    e = dmalloc(&h->lp_srcmax, sizeof(float) * nt, st);
+    if (e == cudaSuccess) e = lowprec_srcmax(h->src.npts, nt, h->src_dcmp, h->lp_srcmax, st);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   dfree(t1, st);
   dfree(t2, st);
@@ -802,6 +836,8 @@ static cudaEvent_t ev_next(tb_handle* h) {
 
 // TTI / elastic: one step per launch (Sec. III-B/C), grid-aligned injection
 // and receiver sampling as separate kernels after each step.
+static size_t Np_of(const tb_handle* h) { return (size_t)h->n[0] * h->n[1] * h->n2p; }
+
 static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
   const int nrec = h->have_rec ? h->rec.npt : 0;
   const bool rec_on = h->have_rec && h->rec.npts > 0 && nrec > 0 && traces;
@@ -830,12 +866,35 @@ static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
   for (int d = 0; d < 3; ++d)
     for (int i = 1; i <= h->R; ++i) w.a[d][i - 1] = (float)(a[i] / h->h[d]);
   if (h->opt.profile) ev_reset(h, st);
-  if (h->physics == TB_TTI) {
+  const bool lowp = h->physics == TB_ACOUSTIC;  // acoustic here means 16-bit or plain storage
+  const size_t es = h->storage == TB_F32_PLAIN ? 4 : 2;
+  LapW lw{};
+  if (lowp) {
+    for (int d = 0; d < 3; ++d)
+      for (int i = 1; i <= h->R; ++i) lw.c[d][i - 1] = (float)(h->c[i] / (h->h[d] * h->h[d]));
+    if (nt + 3 > h->lp_cap) {
+      dfree(h->lp_scales, st);
+      dfree(h->lp_mx, st);
+      h->lp_scales = nullptr;
+      h->lp_mx = nullptr;
+      h->lp_cap = 0;
+      TB_CUDA(h, dmalloc(&h->lp_scales, sizeof(float) * (nt + 3), st));
+      TB_CUDA(h, dmalloc(&h->lp_mx, sizeof(unsigned) * (nt + 3), st));
+      h->lp_cap = nt + 3;
+    }
+    std::vector<float> ones(nt + 3, 1.0f);
+    TB_CUDA(h, cudaMemcpyAsync(h->lp_scales, ones.data(), sizeof(float) * 2, cudaMemcpyHostToDevice, st));
+    TB_CUDA(h, cudaMemsetAsync(h->lp_mx, 0, sizeof(unsigned) * (nt + 3), st));
+    TB_CUDA(h, cudaMemsetAsync(h->lp[0], 0, es * Np_of(h), st));
+    TB_CUDA(h, cudaMemsetAsync(h->lp[1], 0, es * Np_of(h), st));
+    TB_CUDA(h, cudaStreamSynchronize(st));  // `ones` outlives the copy
+    h->lp_cur = 0;
+  } else if (h->physics == TB_TTI) {
     for (int i = 0; i < 4; ++i) TB_CUDA(h, cudaMemsetAsync(h->field[i], 0, fbytes, st));
   } else {
     TB_CUDA(h, cudaMemsetAsync(h->efield, 0, 9 * fbytes, st));
   }
-  // enough columns x chunks to fill the GPU a few times over (TTI streams chunks)
+  // enough columns x chunks to fill the GPU a few times over (the streaming kernels)
   const int64_t cols = h->n[1] * h->n[2];
   const int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>(h->n[0] / std::max(4, 2 * h->R),
                                                                    (int64_t)h->num_sms * 2048 / std::max<int64_t>(cols, 1)));
@@ -862,6 +921,30 @@ static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
     }
     cudaError_t e;
     float *f0, *f1 = nullptr, *f2 = nullptr, *s1 = nullptr, *s2 = nullptr;
+    if (lowp) {
+      void* uc = h->lp[h->lp_cur];
+      void* up = h->lp[1 - h->lp_cur];
+      e = lowprec_step(h->storage, h->R, g, lw, nchunks, uc, up, h->c2, h->damp_b, h->lp_scales,
+                       (h->have_src && h->src.npts > 0) ? h->lp_srcmax : nullptr, n, h->lp_mx, st);
+      if (h->opt.profile && eb) cudaEventRecord(eb, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+      h->lp_cur = 1 - h->lp_cur;  // u^{n+1} is now the current field
+      if (h->have_src && h->src.npts > 0) {
+        e = lowprec_inject(h->storage, g, h->src.npts, h->src.lin, h->src_dcmp + (size_t)n * h->src.npts, up,
+                           h->lp_scales, n, h->lp_mx, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "injection");
+      }
+      if (rec_on) {
+        e = lowprec_sample(h->storage, g, h->rec.npts, h->rec.ent, h->rec.lin, up, h->lp_scales, n,
+                           h->rec_dcmp + (size_t)fill * h->rec.npts, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "receiver sampling");
+        if (++fill == h->rec_cap) {
+          int s = flush();
+          if (s != TB_OK) return s;
+        }
+      }
+      continue;
+    }
     if (h->physics == TB_TTI) {
       e = tti_step(h->R, g, w, nchunks, h->field[pc], h->field[pp], h->field[rc], h->field[rp], h->c2, h->coef,
                    h->nzb, h->damp_b, h->flux, st);
@@ -922,9 +1005,9 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
     return fail(h, TB_EINVAL, "nt = %d exceeds the wavelet length %d", nt, h->src_nt);
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
-  if (h->physics != TB_ACOUSTIC) {
+  if (h->physics != TB_ACOUSTIC || h->storage != TB_F32) {
     if (schedule != TB_ONESTEP)
-      return fail(h, TB_EINVAL, "the blocked schedule is implemented for the acoustic equation only");
+      return fail(h, TB_EINVAL, "the blocked schedule is implemented for the FP32 acoustic equation only");
     return forward_other(h, nt, traces, st);
   }
   const int nrec = h->have_rec ? h->rec.npt : 0;
@@ -1100,6 +1183,28 @@ extern "C" int tb_get_field(tb_handle* h, int which, float* out, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
   const float* src = nullptr;
+  if (h->physics == TB_ACOUSTIC && h->storage != TB_F32) {
+    // stored u / s: unpack with the step's scale into a dense FP32 array
+    float sc = 1.f;
+    const int k = h->last_nt - which + 1;  // scales[k] belongs to u^{k-1}
+    TB_CUDA(h, cudaMemcpyAsync(&sc, h->lp_scales + k, sizeof(float), cudaMemcpyDeviceToHost, st));
+    TB_CUDA(h, cudaStreamSynchronize(st));
+    const void* u = h->lp[which == 0 ? h->lp_cur : 1 - h->lp_cur];
+    const PhysGrid g{(int)h->n[0], (int)h->n[1], (int)h->n[2], h->n2p};
+    const size_t N = (size_t)h->n[0] * h->n[1] * h->n[2];
+    float* dst = out;
+    float* tmp = nullptr;
+    if (!is_device_ptr(out)) {
+      TB_CUDA(h, dmalloc(&tmp, sizeof(float) * N, st));
+      dst = tmp;
+    }
+    cudaError_t e = lowprec_unpack(h->storage, g, u, sc, dst, st);
+    if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(out, tmp, sizeof(float) * N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && tmp) e = cudaStreamSynchronize(st);
+    dfree(tmp, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "tb_get_field");
+    return TB_OK;
+  }
   if (h->physics == TB_ACOUSTIC) {
     src = h->field[which == 0 ? h->cur_idx : h->prev_idx];
   } else if (h->physics == TB_TTI) {
@@ -1232,7 +1337,8 @@ static int runner_step(tb_handle* h, StepRunner* r, int cur, int prev, int step,
 extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, float* grad_vp, float* grad_src,
                                    int n_snapshots, void* stream) {
   if (!h) return TB_EINVAL;
-  if (h->physics != TB_ACOUSTIC) return fail(h, TB_EINVAL, "the adjoint is implemented for the acoustic equation");
+  if (h->physics != TB_ACOUSTIC || h->storage != TB_F32)
+    return fail(h, TB_EINVAL, "the adjoint is implemented for the FP32 acoustic equation");
   if (!h->have_model || !h->have_src || !h->have_rec)
     return fail(h, TB_ESTATE, "tb_set_model, tb_set_sources and tb_set_receivers must come first");
   if (nt <= 0 || !residual || n_snapshots < 1 || (!grad_vp && !grad_src)) return fail(h, TB_EINVAL, "bad arguments");

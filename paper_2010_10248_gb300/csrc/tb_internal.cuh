@@ -143,6 +143,18 @@ inline void dfree(void* p, cudaStream_t st) {
   if (p) cudaFreeAsync(p, st);
 }
 
+// 16-bit (or plain FP32) storage one-step path (tb_lowprec.cu); storage: 1 FP16,
+// 2 BF16, 3 FP32.  scales[k] / mx[k]: scale and max |u| of u^{k-1}.
+cudaError_t lowprec_step(int storage, int R, const PhysGrid& g, const LapW& w, int nchunks, const void* uc, void* up,
+                         const float* c2, const float* damp_b, const float* scales, const float* srcmax, int n,
+                         unsigned* mx, cudaStream_t st);
+cudaError_t lowprec_inject(int storage, const PhysGrid& g, int64_t npts, const int64_t* lin, const float* dcmp_row,
+                           void* u, const float* scales, int n, unsigned* mx, cudaStream_t st);
+cudaError_t lowprec_sample(int storage, const PhysGrid& g, int64_t npts, const int2* ent, const int64_t* lin,
+                           const void* u, const float* scales, int n, float* row, cudaStream_t st);
+cudaError_t lowprec_srcmax(int64_t npts, int nt, const float* dcmp, float* out, cudaStream_t st);
+cudaError_t lowprec_unpack(int storage, const PhysGrid& g, const void* u, float s, float* out, cudaStream_t st);
+
 void free_tables(PointTables* t, cudaStream_t st);
 // Builds lin, colptr, ent (+ corner tables when want_corners).  coords on
 // the device.  Returns TB_OK / TB_EINVAL / TB_ENOMEM / TB_ECUDA.

@@ -1,0 +1,61 @@
+"""16-bit wavefield storage (FP16 / BF16, FP32 arithmetic, per-field
+power-of-two scales) against the FP64 oracle: the error of each storage is
+measured and stated; the plain-FP32 instantiation of the same kernel meets
+the FP32 bar (1e-4)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_10248_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2010_10248_gb300 as tb
+    tb.load()
+    return tb
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def case():
+    w = wl.acoustic_512_so8(shape=(72, 70, 96), nt=300, nbl=12)
+    dt = 0.8 * oracle.cfl_dt_max(w.so, w.spacing, float(w.vp.max()))
+    wav = w.wavelets(dt)
+    tr, u, _ = oracle.acoustic_forward(w.shape, w.spacing, w.so, dt, w.nt, w.vp.astype(np.float64), nbl=w.nbl,
+                                       src_xyz=w.src_xyz, src_wav=wav, rec_xyz=w.rec_xyz)
+    return w, dt, wav, tr, u
+
+
+# (storage, bound on rel-L2 vs FP64) -- the 16-bit bounds are loose ceilings;
+# the measured values are printed and recorded in the design notes
+LIMITS = {"TB_F32_PLAIN": 1e-4, "TB_F16": 2e-2, "TB_BF16": 2e-1}
+
+
+@pytest.mark.parametrize("storage", list(LIMITS))
+def test_storage_error_against_oracle(tb, case, storage):
+    import torch
+    w, dt, wav, tr_o, u_o = case
+    p = tb.Propagator(w.shape, w.spacing, w.so, nbl=w.nbl, storage=getattr(tb, storage))
+    p.set_model(torch.from_numpy(w.vp).cuda(), dt=dt)
+    p.set_sources(w.src_xyz, wav.astype(np.float32))
+    p.set_receivers(w.rec_xyz)
+    tr = p.forward(w.nt).cpu().numpy()
+    u = p.field(0).cpu().numpy()
+    e_tr, e_u = rel_l2(tr, tr_o), rel_l2(u, u_o)
+    print(f"{storage}: traces rel-L2 {e_tr:.2e}, field rel-L2 {e_u:.2e} ({w.nt} steps)")
+    assert e_tr <= LIMITS[storage] and e_u <= LIMITS[storage]
+    with pytest.raises(tb.TBError):
+        p.forward(4, schedule="blocked")

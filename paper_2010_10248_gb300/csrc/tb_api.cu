@@ -471,7 +471,7 @@ extern "C" size_t tb_workspace_bytes(const tb_handle* h) {
   b += h->src.bytes + h->rec.bytes;
   b += sizeof(float) * (size_t)h->src_nt * std::max<int64_t>(h->src.npts, 0);
   b += sizeof(float) * (size_t)h->rec_cap * std::max<int64_t>(h->rec.npts, 0);
-  b += sizeof(float) * h->ring_floats + sizeof(unsigned long long) * h->progress_n;
+  b += sizeof(float) * h->ring_floats + sizeof(unsigned long long) * kProgressStride * h->progress_n;
   b += sizeof(PassDesc) * h->pass_cap + sizeof(float) * h->traces_cap;
   return b;
 }
@@ -784,8 +784,8 @@ static int ensure_capacity(tb_handle* h, int T, const Plan& pl, int nt, bool hos
       dfree(h->progress, st);
       h->progress = nullptr;
       h->progress_n = 0;
-      TB_CUDA(h, dmalloc(&h->progress, sizeof(unsigned long long) * pl.max_ctas, st));
-      TB_CUDA(h, cudaMemsetAsync(h->progress, 0, sizeof(unsigned long long) * pl.max_ctas, st));
+      TB_CUDA(h, dmalloc(&h->progress, sizeof(unsigned long long) * kProgressStride * pl.max_ctas, st));
+      TB_CUDA(h, cudaMemsetAsync(h->progress, 0, sizeof(unsigned long long) * kProgressStride * pl.max_ctas, st));
       h->progress_n = pl.max_ctas;
       h->prog_base = 0;
     }

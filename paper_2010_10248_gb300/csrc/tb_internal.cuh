@@ -13,6 +13,12 @@ namespace tbi {
 // Counts kernel launches made by the library (tb_launch_count).
 void count_launch(int n = 1);
 
+// Progress counters of the blocked sweep sit one 128-byte line apart: with
+// several counters per line, every publish and every neighbour poll of the
+// CTAs sharing a line queued at the same L2 slice (packed counters measured
+// 1.8 us from publish to observation, one line each 0.5 us).
+constexpr int kProgressStride = 16;
+
 // Blocked sweeps keep one tile of (TY x 64) columns per CTA; the pass table
 // describes which CTAs stream which (x-chunk, y-band) of the grid.
 struct PassDesc {
@@ -51,7 +57,7 @@ struct SweepParams {
   int step0;                    // step index of the first fused step
   // blocked-sweep coupling between CTAs
   float* ring;                  // per tile, per stage, per slot: halo strips
-  unsigned long long* progress; // per CTA: completed steps (monotonic)
+  unsigned long long* progress; // per CTA: completed steps (monotonic), kProgressStride apart
   unsigned long long prog_base;
   int* err;                     // device error flag (1 = wait timed out)
   long long timeout_ns;

@@ -25,6 +25,10 @@
 // Publisher warp (T > 1): publishes each retired step in the CTA's progress
 // counter (a release store, whose fence can take microseconds: it is kept
 // off the producer's and the halo warp's paths).
+// Receiver warp: records u at the tile's receiver points for every fused
+// step (levels n+1 .. n+T-1 from the staged shared planes, level n+T from
+// the sweep's output once the step is retired), so that a receiver plane
+// costs the compute warps nothing.
 // Compute warps wait on two mbarriers per stream step (the step's data and
 // the centre/halo planes); every wait is bounded by a timeout, after which
 // the CTA records an error and returns (helper warps first drain their own
@@ -68,7 +72,10 @@ struct SweepCfg {
   static constexpr int TZ = 64;
   static constexpr int NT = 32 * TY;           // compute threads
   static constexpr bool HALO = T > 1;          // halo and publisher warps present
-  static constexpr int NTHREADS = NT + 32 + (HALO ? 64 : 0);  // + producer (+ halo, publisher)
+  // + producer, receiver (+ halo, publisher) warps
+  static constexpr int NTHREADS = NT + 64 + (HALO ? 64 : 0);
+  static constexpr int WREC = TY + 1;                    // receiver warp
+  static constexpr int WHALO = TY + 2, WPUB = TY + 3;    // halo, publisher warps (T > 1)
   static constexpr int RP = (R + 3) / 4 * 4;   // axis-2 halo width in shared memory
   static constexpr int SW = TZ + 2 * RP;       // plane row stride (floats)
   static constexpr int SH = TY + 2 * R;
@@ -100,7 +107,7 @@ struct SweepCfg {
   static constexpr int STRIP = 2 * STRIP_Y + 2 * TY * RP;
   static constexpr int RING_PER_CTA = T > 1 ? (T - 1) * D * STRIP : 0;
   static constexpr int NSP = T > 1 ? 2 * (T - 1) : 0;  // fused-step planes
-  static constexpr int CTR_COUNT = NT + (HALO ? 1 : 0);   // arrivals per centre phase
+  static constexpr int CTR_COUNT = NT + (HALO ? 2 : 0);   // arrivals per centre phase: + halo, receiver
   static constexpr size_t OFF_U = 0;
   static constexpr size_t OFF_P = OFF_U + align128((size_t)NU * PSLOT * 4);
   static constexpr size_t OFF_C = OFF_P + align128((size_t)NP * TILE * 4);
@@ -109,7 +116,8 @@ struct SweepCfg {
   static constexpr size_t OFF_CNT = OFF_BASE + 4 * 2 * 2 * NT;
   static constexpr size_t OFF_CUR = OFF_CNT + 2 * 2 * 2 * NT;
   static constexpr size_t OFF_XF = OFF_CUR + 2 * 2 * T * 2 * NT;  // receiver columns' first x
-  static constexpr size_t OFF_BAR = align128(OFF_XF + 2 * 2 * NT);
+  static constexpr size_t OFF_RL = OFF_XF + 2 * 2 * NT;   // receiver warp: list of receiver columns
+  static constexpr size_t OFF_BAR = align128(OFF_RL + 2 * 2 * NT);
   static constexpr int NBAR = 1 + ND + 2 + NDONE;    // prologue, data, centre[2], done
   static constexpr size_t SMEM = OFF_BAR + 8 * NBAR + 128;    // + base alignment
   static_assert(R % 2 == 0, "radius must be even for aligned float2 access");
@@ -285,6 +293,12 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
   uint64_t* bar_dat = bar_pro + 1;     // [ND] data of stream step j
   uint64_t* bar_ctr = bar_dat + C::ND; // [2] centres and halos of stream step j in buffer j & 1
   uint64_t* bar_done = bar_ctr + 2;    // [NDONE] compute warps finished a stream step
+  // per-column state of the grid-aligned sources (kind 0, compute warps) and
+  // receivers (kind 1, receiver warp)
+  int* cbase = reinterpret_cast<int*>(smem + C::OFF_BASE);                      // [kind][col][NT]
+  unsigned short* ccnt = reinterpret_cast<unsigned short*>(smem + C::OFF_CNT);  // [kind][col][NT]
+  unsigned short* ccur = reinterpret_cast<unsigned short*>(smem + C::OFF_CUR);  // [kind][T][col][NT]
+  unsigned short* cxf = reinterpret_cast<unsigned short*>(smem + C::OFF_XF);    // [col][NT]
 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int b = blockIdx.x;
@@ -351,7 +365,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
         break;
       }
       ret = s;
-      if constexpr (T > 1) st_release_cta_s32(&s_ret, ret);  // for the publisher
+      st_release_cta_s32(&s_ret, ret);  // for the publisher and the receiver warp
     }
     // drain: wait (bounded) for every load this thread issued; after a full
     // run the compute warps consumed them all
@@ -363,8 +377,114 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
     return;
   }
 
+  if (w == C::WREC) {
+    // ============================ receiver warp ============================
+    // the tile's receiver columns (own rows), kind-1 per-column state and a
+    // compact list of their slots (bit 15: entries contiguous in x)
+    int* rbase = cbase + 2 * NT;
+    unsigned short* rcnt = ccnt + 2 * NT;
+    unsigned short* rcur = ccur + 2 * T * NT;  // [T][col][NT]
+    unsigned short* rlist = reinterpret_cast<unsigned short*>(smem + C::OFF_RL);
+    int nlist = 0;
+    for (int s0 = 0; s0 < 2 * NT; s0 += 32) {
+      const int sl = s0 + lane, ci = sl / NT, t = sl - ci * NT;
+      const int yy = y0 + (t >> 5), zz = z0 + 2 * (t & 31) + ci;
+      bool has = false, dense = false;
+      if (P.r_colptr && yy < P.n1 && zz < P.n2 && yy >= pd.yo0 && yy < pd.yo1) {
+        const int c = yy * P.n2 + zz;
+        const int cb = __ldg(&P.r_colptr[c]), ce = __ldg(&P.r_colptr[c + 1]);
+        if (ce > cb) {
+          has = true;
+          rbase[sl] = cb;
+          rcnt[sl] = (unsigned short)(ce - cb);
+          const int xf = __ldg(&P.r_ent[cb].x), xl = __ldg(&P.r_ent[ce - 1].x);
+          cxf[sl] = (unsigned short)xf;
+          dense = xl - xf + 1 == ce - cb;
+          for (int k = 0; k < T; ++k) rcur[k * 2 * NT + sl] = 0;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, has);
+      if (has) rlist[nlist + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(sl | (dense ? 0x8000 : 0));
+      nlist += __popc(m);
+    }
+    __syncwarp();
+    const size_t ps = (size_t)P.n1 * P.n2p;
+    // u at the receiver points of plane q of level n+kk+1 (fused step kk):
+    // from a staged plane, or from the sweep's output in global memory
+    auto record = [&](int kk, int q, const float* plane) {
+      if (q < pd.xo0 || q >= pd.xo1 || nlist == 0) return;
+      float* rrow = P.rec_dcmp + (size_t)(P.step0 + kk - P.rec_base) * P.nrpts;
+      for (int e = lane; e < nlist; e += 32) {
+        const int en = rlist[e], sl = en & 0x7fff, ci = sl / NT, t = sl - ci * NT;
+        const int cn = rcnt[sl], cb = rbase[sl];
+        int pos = -1;
+        if (en & 0x8000) {
+          const unsigned off = (unsigned)(q - (int)cxf[sl]);
+          if (off < (unsigned)cn) pos = cb + (int)off;
+        } else {
+          unsigned short* cp = &rcur[kk * 2 * NT + sl];
+          int cc = *cp;
+          while (cc < cn) {
+            const int x = __ldg(&P.r_ent[cb + cc].x);
+            if (x < q) {
+              ++cc;
+              continue;
+            }
+            if (x == q) pos = cb + cc++;
+            break;
+          }
+          *cp = (unsigned short)cc;
+        }
+        if (pos >= 0) {
+          const int ww = t >> 5, ln = t & 31;
+          rrow[pos] = plane ? plane[(R + ww) * SW + RP + 2 * ln + ci]
+                            : __ldcg(P.out0 + (size_t)q * ps + (size_t)(y0 + ww) * P.n2p + z0 + 2 * ln + ci);
+        }
+      }
+    };
+    // steps retired by the producer (its level-n+T planes are in global memory)
+    auto wait_retired = [&](int jr) -> bool {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_cta_s32(&s_ret) < jr) {
+        if ((long long)(global_ns() - t0) > tmo) return false;
+        __nanosleep(64);
+      }
+      return true;
+    };
+    bool ok = true;
+    if constexpr (T == 1) {
+      for (int j = jstart; j <= jend && ok; ++j) {
+        ok = __all_sync(0xffffffffu, wait_retired(j));
+        if (ok) record(0, j, nullptr);
+      }
+    } else {
+      for (int j = jstart; j <= jend + 1 && ok; ++j) {
+        if (j <= jend) {
+          // levels n+1 .. n+T-1 of this step's centre planes; then release
+          // the buffer to the compute warps' staging of step j+2
+          if (j > jstart) {
+            ok = __all_sync(0xffffffffu, mbar_wait(bar_ctr + (j & 1), ((j - jstart - 1) >> 1) & 1, tmo));
+            if (!ok) break;
+            const float* rdbuf = splane + (size_t)(j & 1) * (T - 1) * C::PSLOT;
+            for (int k = 1; k < T; ++k) record(k - 1, j - k * R, rdbuf + (size_t)(k - 1) * C::PSLOT);
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar_ctr + ((j + 1) & 1));
+        }
+        // level n+T of the step before, written to the output (ctr(j) implies
+        // it for j <= jend; the last step waits for its retirement)
+        if (j - 1 >= jstart) {
+          if (j > jend) ok = __all_sync(0xffffffffu, wait_retired(j - 1));
+          if (ok) record(T - 1, j - 1 - (T - 1) * R, nullptr);
+        }
+      }
+    }
+    if (!ok) atomicExch(P.err, 2);
+    return;
+  }
+
   if constexpr (C::HALO) {
-    if (w == TY + 2) {
+    if (w == C::WPUB) {
       // =========================== publisher warp ===========================
       // publishes the producer's latest retired step (it may skip steps
       // while a release is in flight: the counter is monotonic)
@@ -377,7 +497,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
           // release: cumulative over the compute warps' strip stores, which
           // happen before their arrival on the step's mbarrier, which the
           // producer observed before it wrote s_ret
-          st_release_u64(&P.progress[b], P.prog_base + (unsigned long long)(r - jstart + 1));
+          st_release_u64(&P.progress[(size_t)b * kProgressStride], P.prog_base + (unsigned long long)(r - jstart + 1));
           pub = r;
           t0 = global_ns();
         } else {
@@ -390,7 +510,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
       }
       return;
     }
-    if (w == TY + 1) {
+    if (w == C::WHALO) {
       // ============================= halo warp =============================
       // progress of neighbour `lane` (lanes 0..3: up, down, left, right)
       const int nb = lane == 0 ? nb_up : lane == 1 ? nb_dn : lane == 2 ? nb_lf : lane == 3 ? nb_rt : -1;
@@ -407,7 +527,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
           const unsigned long long target = P.prog_base + (unsigned long long)(jn - R - jstart + 1);
           const unsigned long long t0 = global_ns();
           while (true) {
-            if (nb >= 0 && seen < target) seen = ld_acquire_u64(&P.progress[nb]);
+            if (nb >= 0 && seen < target) seen = ld_acquire_u64(&P.progress[(size_t)nb * kProgressStride]);
             if (__all_sync(0xffffffffu, nb < 0 || seen >= target)) break;
             if (__any_sync(0xffffffffu, (long long)(global_ns() - t0) > tmo)) {  // warp-uniform
               ok = false;
@@ -512,10 +632,6 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
   const size_t coff = (size_t)y * P.n2p + z;     // column offset (valid if v0)
   const int own = (R + w) * SW + RP + 2 * lane;  // own pair in a plane slot
   const int own_t = w * TZ + 2 * lane;           // own pair in a tile slot
-  int* cbase = reinterpret_cast<int*>(smem + C::OFF_BASE);                      // [kind][col][NT]
-  unsigned short* ccnt = reinterpret_cast<unsigned short*>(smem + C::OFF_CNT);  // [kind][col][NT]
-  unsigned short* ccur = reinterpret_cast<unsigned short*>(smem + C::OFF_CUR);  // [kind][T][col][NT]
-  unsigned short* cxf = reinterpret_cast<unsigned short*>(smem + C::OFF_XF);    // [col][NT]
   // this thread's place in the halo strips it publishes (-1: none)
   const int strip_y = w < R ? w * SW + RP + 2 * lane
                             : (w >= TY - R ? (R + w - (TY - R)) * SW + RP + 2 * lane : -1);
@@ -526,31 +642,19 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
   if (v0) byz.x = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z]));
   if (v1) byz.y = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z + 1]));
 
-  // Per-column state of the grid-aligned source / receiver entries.  flags:
-  // bit i: column i has source points; bit 2+i: receiver points; bit 4+i:
-  // its receiver points are contiguous in x (lines, planes), so the entry
-  // of plane q is base + q - x_first, with no cursor and no load.
+  // Per-column state of the grid-aligned source entries.  flags: bit i:
+  // column i has source points (receivers are the receiver warp's).
   int flags = 0;
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    if (!(i == 0 ? v0 : v1)) continue;
+    if (!(i == 0 ? v0 : v1) || !P.s_colptr) continue;
     const int c = y * P.n2 + z + i;
-#pragma unroll
-    for (int kind = 0; kind < 2; ++kind) {
-      const int* colptr = kind == 0 ? P.s_colptr : P.r_colptr;
-      if (!colptr) continue;
-      const int cb = __ldg(&colptr[c]), ce = __ldg(&colptr[c + 1]);
-      if (ce > cb) {
-        flags |= 1 << (2 * kind + i);
-        cbase[(kind * 2 + i) * NT + tid] = cb;
-        ccnt[(kind * 2 + i) * NT + tid] = (unsigned short)(ce - cb);
-        for (int k = 0; k < T; ++k) ccur[((kind * T + k) * 2 + i) * NT + tid] = 0;
-        if (kind == 1) {
-          const int xf = __ldg(&P.r_ent[cb].x), xl = __ldg(&P.r_ent[ce - 1].x);
-          cxf[i * NT + tid] = (unsigned short)xf;
-          if (xl - xf + 1 == ce - cb) flags |= 16 << i;
-        }
-      }
+    const int cb = __ldg(&P.s_colptr[c]), ce = __ldg(&P.s_colptr[c + 1]);
+    if (ce > cb) {
+      flags |= 1 << i;
+      cbase[i * NT + tid] = cb;
+      ccnt[i * NT + tid] = (unsigned short)(ce - cb);
+      for (int k = 0; k < T; ++k) ccur[(k * 2 + i) * NT + tid] = 0;
     }
   }
 
@@ -607,34 +711,6 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
             const float add = __ldg(&P.src_dcmp[(size_t)step * P.npts + e.y]);
             if (i == 0) un.x = __fadd_rn(un.x, add);
             else un.y = __fadd_rn(un.y, add);
-            ++cc;
-          }
-          break;
-        }
-        *cp = (unsigned short)cc;
-      }
-    }
-    if ((flags & 12) && own_row && q >= pd.xo0 && q < pd.xo1) {  // receiver points
-      float* rrow = P.rec_dcmp + (size_t)(step - P.rec_base) * P.nrpts;
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        if (!((flags >> (2 + i)) & 1)) continue;
-        const int cn = ccnt[(1 * 2 + i) * NT + tid], cb = cbase[(1 * 2 + i) * NT + tid];
-        if ((flags >> (4 + i)) & 1) {
-          const unsigned off = (unsigned)(q - (int)cxf[i * NT + tid]);
-          if (off < (unsigned)cn) rrow[cb + off] = (i == 0 ? un.x : un.y);
-          continue;
-        }
-        unsigned short* cp = &ccur[((1 * T + k) * 2 + i) * NT + tid];
-        int cc = *cp;
-        while (cc < cn) {
-          const int2 e = __ldg(&P.r_ent[cb + cc]);
-          if (e.x < q) {
-            ++cc;
-            continue;
-          }
-          if (e.x == q) {
-            rrow[cb + cc] = (i == 0 ? un.x : un.y);
             ++cc;
           }
           break;

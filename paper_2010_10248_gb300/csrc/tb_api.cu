@@ -91,6 +91,11 @@ struct tb_handle {
   PointTables src;
   int src_nt = 0;
   float* src_dcmp = nullptr;
+  // the sweep kernel's view of the sources: one plane range per column pair
+  int2* ev_pair = nullptr;      // [n1][npair] (first plane | span << 16, base)
+  float2* src_ev = nullptr;     // [src_nt][nev]
+  int64_t nev = 0;
+  int npair = 0;
   bool have_src = false;
   // receivers
   PointTables rec;
@@ -331,6 +336,8 @@ extern "C" int tb_destroy(tb_handle* h) {
   free_tables(&h->src, st);
   free_tables(&h->rec, st);
   dfree(h->src_dcmp, st);
+  dfree(h->ev_pair, st);
+  dfree(h->src_ev, st);
   dfree(h->rec_dcmp, st);
   dfree(h->ring, st);
   dfree(h->progress, st);
@@ -470,6 +477,7 @@ extern "C" size_t tb_workspace_bytes(const tb_handle* h) {
   if (h->physics == TB_ELASTIC) b += 17 * fbytes - 4 * fbytes + sizeof(float) * (h->n[0] + h->n[1] + h->n[2]);
   b += h->src.bytes + h->rec.bytes;
   b += sizeof(float) * (size_t)h->src_nt * std::max<int64_t>(h->src.npts, 0);
+  if (h->ev_pair) b += sizeof(int2) * (size_t)h->n[1] * h->npair + sizeof(float2) * (size_t)h->src_nt * h->nev;
   b += sizeof(float) * (size_t)h->rec_cap * std::max<int64_t>(h->rec.npts, 0);
   b += sizeof(float) * h->ring_floats + sizeof(unsigned long long) * kProgressStride * h->progress_n;
   b += sizeof(PassDesc) * h->pass_cap + sizeof(float) * h->traces_cap;
@@ -630,8 +638,14 @@ extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int 
   }
   dfree(h->src_dcmp, st);
   h->src_dcmp = nullptr;
+  dfree(h->ev_pair, st);
+  h->ev_pair = nullptr;
+  dfree(h->src_ev, st);
+  h->src_ev = nullptr;
+  h->nev = 0;
   h->src_nt = nsrc > 0 ? nt : 0;
   cudaError_t e = cudaSuccess;
+  int* d_slot = nullptr;
   if (h->src.npts > 0) {
     e = dmalloc(&h->src_dcmp, sizeof(float) * (size_t)nt * h->src.npts, st);
     if (e == cudaSuccess)
@@ -639,7 +653,56 @@ extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int 
       // explosive source into the normal stresses, dt q
       e = decompose(&h->src, nt, (const float*)dw, h->physics == TB_ELASTIC ? nullptr : h->c2, h->dt,
                     (int)h->n[1], (int)h->n[2], h->n2p, h->src_dcmp, st);
+    if (e == cudaSuccess && h->physics == TB_ACOUSTIC) {
+      // the sweep kernel's event table: the points of each column pair
+      // (y, 2p), (y, 2p + 1) share one range of planes [first, last]; the
+      // injection of the point at plane x of column 2p + c goes to slot
+      // 2 (base + x - first) + c of every step's row
+      const int64_t np = h->src.npts, n1 = h->n[1], n2 = h->n[2];
+      h->npair = (int)((n2 + 1) / 2);
+      std::vector<int64_t> lin(np);
+      e = cudaMemcpyAsync(lin.data(), h->src.lin, sizeof(int64_t) * np, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      std::vector<int> slot(np);
+      std::vector<int2> evp;
+      if (e == cudaSuccess) {
+        // points ordered by (row, pair, plane)
+        std::vector<int64_t> ord(np);
+        for (int64_t i = 0; i < np; ++i) ord[i] = i;
+        auto key = [&](int64_t i) {
+          const int64_t z = lin[i] % n2, y = (lin[i] / n2) % n1, x = lin[i] / (n1 * n2);
+          return std::make_pair(y * h->npair + z / 2, x);
+        };
+        std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
+        evp.assign((size_t)n1 * h->npair, make_int2(0, 0));
+        int64_t base = 0;
+        for (int64_t g = 0; g < np;) {
+          const int64_t pr = key(ord[g]).first;
+          int64_t g1 = g;
+          while (g1 < np && key(ord[g1]).first == pr) ++g1;
+          const int64_t xf = key(ord[g]).second, xl = key(ord[g1 - 1]).second, span = xl - xf + 1;
+          evp[pr] = make_int2((int)(xf | (span << 16)), (int)base);
+          for (int64_t i = g; i < g1; ++i)
+            slot[ord[i]] = (int)(2 * (base + key(ord[i]).second - xf) + (lin[ord[i]] % n2) % 2);
+          base += span;
+          g = g1;
+        }
+        h->nev = base;
+        if (2 * base >= (int64_t)INT32_MAX) e = cudaErrorInvalidValue;
+      }
+      if (e == cudaSuccess) e = dmalloc(&h->ev_pair, sizeof(int2) * evp.size(), st);
+      if (e == cudaSuccess) e = dmalloc(&h->src_ev, sizeof(float2) * (size_t)nt * h->nev, st);
+      if (e == cudaSuccess) e = dmalloc(&d_slot, sizeof(int) * np, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->ev_pair, evp.data(), sizeof(int2) * evp.size(), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_slot, slot.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->src_ev, 0, sizeof(float2) * (size_t)nt * h->nev, st);
+      if (e == cudaSuccess)
+        e = source_events(nt, np, d_slot, h->src_dcmp, reinterpret_cast<float*>(h->src_ev), 2 * h->nev, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host tables copied before they go
+    }
   }
+  dfree(d_slot, st);
   if (e == cudaSuccess && h->storage != TB_F32 && h->src.npts > 0) {
     dfree(h->lp_srcmax, st);
     h->lp_srcmax = nullptr;
@@ -1043,10 +1106,10 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
       P.w2[d][i - 1] = make_float2(wf, wf);
     }
   const bool src_on = h->have_src && h->src.npts > 0;
-  P.s_colptr = src_on ? h->src.colptr : nullptr;
-  P.s_ent = src_on ? h->src.ent : nullptr;
-  P.src_dcmp = h->src_dcmp;
-  P.npts = h->src.npts;
+  P.ev_pair = src_on ? h->ev_pair : nullptr;
+  P.src_ev = h->src_ev;
+  P.nev = h->nev;
+  P.npair = h->npair;
   const bool rec_on = h->have_rec && h->rec.npts > 0 && nrec > 0;
   P.r_colptr = rec_on ? h->rec.colptr : nullptr;
   P.r_ent = rec_on ? h->rec.ent : nullptr;
@@ -1300,10 +1363,10 @@ static int runner_init(tb_handle* h, StepRunner* r, cudaStream_t st) {
       P.w2[d][i - 1] = make_float2(wf, wf);
     }
   const bool src_on = h->have_src && h->src.npts > 0;
-  P.s_colptr = src_on ? h->src.colptr : nullptr;
-  P.s_ent = src_on ? h->src.ent : nullptr;
-  P.src_dcmp = h->src_dcmp;
-  P.npts = h->src.npts;
+  P.ev_pair = src_on ? h->ev_pair : nullptr;
+  P.src_ev = h->src_ev;
+  P.nev = h->nev;
+  P.npair = h->npair;
   P.r_colptr = nullptr;
   P.r_ent = nullptr;
   P.err = h->err;

@@ -398,6 +398,26 @@ cudaError_t decompose(const PointTables* t, int nt, const float* d_wav, const fl
   return cudaGetLastError();
 }
 
+// ev[t][slot[i]] = dcmp[t][i]: the decomposed injections of every step
+// rearranged by column pair and plane for the sweep kernel (slots of planes
+// without a point keep the zero they were cleared to)
+__global__ void k_events(int nt, int64_t npts, const int* __restrict__ slot, const float* __restrict__ dcmp,
+                         float* __restrict__ ev, int64_t ev_row) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (i >= npts || t >= nt) return;
+  ev[(size_t)t * ev_row + slot[i]] = dcmp[(size_t)t * npts + i];
+}
+
+cudaError_t source_events(int nt, int64_t npts, const int* slot, const float* dcmp, float* ev, int64_t ev_row,
+                          cudaStream_t st) {
+  if (npts <= 0 || nt <= 0) return cudaSuccess;
+  dim3 grid(grid_for(npts, 128), nt);
+  count_launch();
+  k_events<<<grid, 128, 0, st>>>(nt, npts, slot, dcmp, ev, ev_row);
+  return cudaGetLastError();
+}
+
 // trace[s][r] = sum_c w_rc * rec_dcmp[s][e_rc], corners in fixed order; the
 // recorded receiver points are indexed by their position e in the
 // column-ordered entry list

@@ -43,11 +43,14 @@ struct SweepParams {
   const float* c2;              // dt^2 vp^2 (padded layout)
   const float* damp_b;          // [n0 + n1 + n2] eta_d / (2 dt) per axis
   float2 w2[3][6];              // c_i / h_d^2 (i = 1..r) as (w, w) pairs
-  // grid-aligned sources (Sec. II-A)
-  const int* s_colptr;          // [n1*n2 + 1]
-  const int2* s_ent;            // (x, id) by column, ascending x
-  const float* src_dcmp;        // [nt][npts]
-  int64_t npts;
+  // grid-aligned sources (Sec. II-A) as event ranges per column pair: for the
+  // columns (y, 2p) and (y, 2p + 1), ev_pair[y * npair + p] = (first plane |
+  // span << 16, base), and src_ev[n][base + x - first plane] holds the pair's
+  // injections at plane x in step n (zero for a column without a point there)
+  const int2* ev_pair;          // [n1][npair]; NULL: no sources
+  const float2* src_ev;         // [nt][nev]
+  int64_t nev;
+  int npair;
   // grid-aligned receivers
   const int* r_colptr;
   const int2* r_ent;
@@ -170,6 +173,10 @@ int inspect(const int64_t n[3], const double h[3], int npt, const double* d_coor
 // s = c2(p_id) = dt^2/m, or the constant `scale` when c2 is NULL
 cudaError_t decompose(const PointTables* t, int nt, const float* d_wav, const float* c2, double scale,
                       int n1, int n2, int n2p, float* d_dcmp, cudaStream_t st);
+// ev[t][slot[i]] = dcmp[t][i] for the sweep kernel's per-column-pair table
+// (row length ev_row floats).
+cudaError_t source_events(int nt, int64_t npts, const int* slot, const float* dcmp, float* ev, int64_t ev_row,
+                          cudaStream_t st);
 cudaError_t finalize_traces(int nsteps, int nrec, const int* corner_id, const float* corner_w,
                             const float* rec_dcmp, int64_t nrpts, float* traces,
                             cudaStream_t st);

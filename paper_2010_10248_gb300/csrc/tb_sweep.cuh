@@ -48,11 +48,14 @@
 // computation, passes (bands along axis 1, chunks along axis 0) overlap by
 // (T-1) r rows or planes.
 //
-// Grid-aligned sparse operators (Sec. II-A).  Per column, the inspector's
-// entries (x, id) are sorted by x; each fused step walks them with its own
-// cursor, adds src_dcmp[step][id] right after the stencil update of that
-// point (Listing 5's fused injection loop, here along the streamed axis),
-// and records u at receiver points into rec_dcmp[step][rid].
+// Grid-aligned sparse operators (Sec. II-A).  Sources: each lane's column
+// pair has one range of planes that holds source points (built from the
+// inspector's per-column entries when the sources are set), and each fused
+// step adds the pair's injection right after the stencil update of a plane
+// in that range (Listing 5's fused injection, along the streamed axis); the
+// test is branch-light and stateless so that it does not split the step's
+// code.  Receivers: the receiver warp walks the per-column entries (x, id)
+// with one cursor per fused step and records u into rec_dcmp[step][rid].
 //
 // Rounding.  Every floating-point operation of the point update is an
 // explicit round-to-nearest operation, so each fused step and the one-step
@@ -113,9 +116,9 @@ struct SweepCfg {
   static constexpr size_t OFF_C = OFF_P + align128((size_t)NP * TILE * 4);
   static constexpr size_t OFF_S = OFF_C + align128((size_t)NC * TILE * 4);
   static constexpr size_t OFF_BASE = OFF_S + align128((size_t)NSP * PSLOT * 4);
-  static constexpr size_t OFF_CNT = OFF_BASE + 4 * 2 * 2 * NT;
-  static constexpr size_t OFF_CUR = OFF_CNT + 2 * 2 * 2 * NT;
-  static constexpr size_t OFF_XF = OFF_CUR + 2 * 2 * T * 2 * NT;  // receiver columns' first x
+  static constexpr size_t OFF_CNT = OFF_BASE + 4 * 2 * NT;
+  static constexpr size_t OFF_CUR = OFF_CNT + 2 * 2 * NT;
+  static constexpr size_t OFF_XF = OFF_CUR + 2 * T * 2 * NT;      // receiver columns' first x
   static constexpr size_t OFF_RL = OFF_XF + 2 * 2 * NT;   // receiver warp: list of receiver columns
   static constexpr size_t OFF_BAR = align128(OFF_RL + 2 * 2 * NT);
   static constexpr int NBAR = 1 + ND + 2 + NDONE;    // prologue, data, centre[2], done
@@ -293,11 +296,10 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
   uint64_t* bar_dat = bar_pro + 1;     // [ND] data of stream step j
   uint64_t* bar_ctr = bar_dat + C::ND; // [2] centres and halos of stream step j in buffer j & 1
   uint64_t* bar_done = bar_ctr + 2;    // [NDONE] compute warps finished a stream step
-  // per-column state of the grid-aligned sources (kind 0, compute warps) and
-  // receivers (kind 1, receiver warp)
-  int* cbase = reinterpret_cast<int*>(smem + C::OFF_BASE);                      // [kind][col][NT]
-  unsigned short* ccnt = reinterpret_cast<unsigned short*>(smem + C::OFF_CNT);  // [kind][col][NT]
-  unsigned short* ccur = reinterpret_cast<unsigned short*>(smem + C::OFF_CUR);  // [kind][T][col][NT]
+  // per-column state of the grid-aligned receivers (receiver warp)
+  int* cbase = reinterpret_cast<int*>(smem + C::OFF_BASE);                      // [col][NT]
+  unsigned short* ccnt = reinterpret_cast<unsigned short*>(smem + C::OFF_CNT);  // [col][NT]
+  unsigned short* ccur = reinterpret_cast<unsigned short*>(smem + C::OFF_CUR);  // [T][col][NT]
   unsigned short* cxf = reinterpret_cast<unsigned short*>(smem + C::OFF_XF);    // [col][NT]
 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -379,11 +381,11 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
 
   if (w == C::WREC) {
     // ============================ receiver warp ============================
-    // the tile's receiver columns (own rows), kind-1 per-column state and a
+    // the tile's receiver columns (own rows), their per-column state and a
     // compact list of their slots (bit 15: entries contiguous in x)
-    int* rbase = cbase + 2 * NT;
-    unsigned short* rcnt = ccnt + 2 * NT;
-    unsigned short* rcur = ccur + 2 * T * NT;  // [T][col][NT]
+    int* rbase = cbase;
+    unsigned short* rcnt = ccnt;
+    unsigned short* rcur = ccur;  // [T][col][NT]
     unsigned short* rlist = reinterpret_cast<unsigned short*>(smem + C::OFF_RL);
     int nlist = 0;
     for (int s0 = 0; s0 < 2 * NT; s0 += 32) {
@@ -642,20 +644,17 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
   if (v0) byz.x = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z]));
   if (v1) byz.y = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z + 1]));
 
-  // Per-column state of the grid-aligned source entries.  flags: bit i:
-  // column i has source points (receivers are the receiver warp's).
-  int flags = 0;
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    if (!(i == 0 ? v0 : v1) || !P.s_colptr) continue;
-    const int c = y * P.n2 + z + i;
-    const int cb = __ldg(&P.s_colptr[c]), ce = __ldg(&P.s_colptr[c + 1]);
-    if (ce > cb) {
-      flags |= 1 << i;
-      cbase[i * NT + tid] = cb;
-      ccnt[i * NT + tid] = (unsigned short)(ce - cb);
-      for (int k = 0; k < T; ++k) ccur[(k * 2 + i) * NT + tid] = 0;
-    }
+  // The column pair's grid-aligned source points (Sec. II-A, Listing 5): the
+  // planes ev_x .. ev_x + ev_n - 1 carry the pair's injections, read from
+  // src_ev[step][ev_b + plane - ev_x] (zero for a column without a point at
+  // that plane).  The check is a compare and a predicated load per fused
+  // step, with no loop, cursor or shared-memory store in the step's code.
+  int ev_x = 0, ev_n = 0, ev_b = 0;
+  if (v0 && P.ev_pair) {
+    const int2 d = __ldg(&P.ev_pair[(size_t)y * P.npair + (z >> 1)]);
+    ev_x = d.x & 0xffff;
+    ev_n = (int)((unsigned)d.x >> 16);
+    ev_b = d.y;
   }
 
   // Register queues: Q0 holds u^n around plane j (one-step kernel only);
@@ -691,33 +690,16 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
 
   bool ok = mbar_wait(bar_pro, 0, tmo);  // u^n planes pu0 .. jstart+R-1
 
-  // sparse operators of fused step k at plane q on this thread's column pair
-  auto sparse = [&](int k, int q, float2& un) {
-    const int step = P.step0 + k;
-    if (flags & 3) {  // fused grid-aligned injection (Listing 5)
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        if (!((flags >> i) & 1)) continue;
-        unsigned short* cp = &ccur[((0 * T + k) * 2 + i) * NT + tid];
-        int cc = *cp;
-        const int cn = ccnt[(0 * 2 + i) * NT + tid], cb = cbase[(0 * 2 + i) * NT + tid];
-        while (cc < cn) {
-          const int2 e = __ldg(&P.s_ent[cb + cc]);
-          if (e.x < q) {
-            ++cc;
-            continue;
-          }
-          if (e.x == q) {
-            const float add = __ldg(&P.src_dcmp[(size_t)step * P.npts + e.y]);
-            if (i == 0) un.x = __fadd_rn(un.x, add);
-            else un.y = __fadd_rn(un.y, add);
-            ++cc;
-          }
-          break;
-        }
-        *cp = (unsigned short)cc;
-      }
-    }
+  // fused grid-aligned injection of fused step k at plane q (Listing 5).  With
+  // one step per stream step a column pair without sources skips it by a
+  // branch; with several, the test stays branch-light so that the fused
+  // steps' code is not split.
+  const float2* evrow = ev_n > 0 ? P.src_ev + (size_t)P.step0 * P.nev + ev_b : nullptr;
+  auto inject = [&](int k, int q, float2& un) {
+    if constexpr (T == 1)
+      if (ev_n == 0) return;
+    const unsigned off = (unsigned)(q - ev_x);
+    if (off < (unsigned)ev_n) un = __fadd2_rn(un, __ldg(evrow + (size_t)k * P.nev + off));
   };
 
   int su = (jstart - pu0) % C::NU;  // ring slot of u^n plane j
@@ -787,7 +769,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
       const float2 lap = __fadd2_rn(__fadd2_rn(lx, ly), lz);
       const float bx = __shfl_sync(0xffffffffu, bxc, 0);
       un0 = point_update2(uc0, up, lap, c2v, __fadd2_rn(make_float2(bx, bx), byz));
-      if (flags) sparse(0, j, un0);
+      inject(0, j, un0);
     }
 
     if constexpr (T == 1) {
@@ -844,7 +826,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
             const float2 lap = __fadd2_rn(__fadd2_rn(lx, ly), lz);
             const float bx = __shfl_sync(0xffffffffu, bxc, k);
             un = point_update2(uc, upv, lap, c2v, __fadd2_rn(make_float2(bx, bx), byz));
-            if (flags) sparse(k, q, un);
+            inject(k, q, un);
           }
         }
         if (k + 1 < T) {

@@ -62,6 +62,20 @@ def make_case(name):
         src = np.array([[121.1, 345.6, 650.2], [40.0, 100.0, 1300.0]])
         rec = wl.receiver_plane(shape, h, 31, 12, 34, depth_cells=20)
         return dict(shape=shape, h=h, so=4, nt=50, nbl=6, vp=vp, src=src, rec=rec, f0=50.0)
+    if name == "sources_so8":
+        # many sources: twelve along axis 0 in one column (its plane range has
+        # gaps; the axis-2 corners straddle two column pairs), a cloud of 40,
+        # and two on the last, unpaired column of an odd axis 2
+        shape, h = (40, 26, 37), (10.0, 10.0, 10.0)
+        vp = wl.layered_vp(shape, 37, nlayers=3, nblobs=2)
+        g = np.random.default_rng(41)
+        ext = np.array([(shape[d] - 1) * h[d] for d in range(3)])
+        line = np.array([[20.0 + 31.0 * i, 101.3, 152.7] for i in range(12)])
+        cloud = g.uniform(0.1, 0.9, size=(40, 3)) * ext
+        edge = np.array([[133.3, 57.1, 360.0], [250.0, 200.0, 360.0]])
+        src = np.concatenate([line, cloud, edge])
+        rec = wl.receiver_line(shape, h, 9, 16)
+        return dict(shape=shape, h=h, so=8, nt=60, nbl=5, vp=vp, src=src, rec=rec, f0=55.0)
     raise KeyError(name)
 
 
@@ -96,7 +110,7 @@ def setup(name):
     return c, dt, wav
 
 
-CASES = ["cfg64_so4", "ragged_so8", "ragged_so12", "ragged_so4"]
+CASES = ["cfg64_so4", "ragged_so8", "ragged_so12", "ragged_so4", "sources_so8"]
 
 
 @pytest.mark.parametrize("name", CASES)

@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--size", type=int, default=512, help="cube edge (512 = the benchmark)")
     ap.add_argument("--nt", type=int, default=1000)
-    ap.add_argument("--time-tile", type=int, default=4)
+    ap.add_argument("--time-tile", type=int, default=3)  # the fastest fused depth at 512^3 so8
     ap.add_argument("--no-onestep", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -151,17 +151,35 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_key):
-    """Per-launch DRAM bytes from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
+def ncu_counters(kernel_key):
+    """The committed ncu figures of a sweep kernel (DRAM bytes per full-size
+    launch, warp instructions per point update), if they were taken on the
+    current kernel source; else an empty dict."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
-        return None
-    d = json.load(open(p))
-    e = d.get(kernel_key)
+        return {}
+    e = json.load(open(p)).get(kernel_key)
     if not e or e.get("source_hash") != kernel_source_hash():
-        return None
-    return e.get("dram_bytes_per_launch_full_size")
+        return {}
+    return e
+
+
+def fp32_peak_tflops(nsm):
+    """FP32 FMA peak from unit counts and the maximum SM clock: 128 FP32
+    lanes per SM, 2 flops per FMA."""
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        mhz = float(json.load(open(p)).get("sm_max_mhz", mhz))
+    return nsm * 128 * 2 * mhz * 1e6 / 1e12, mhz
+
+
+def alg_flops(space_order):
+    """Algorithmic flops per point and step of Eq. 1: per axis r pair sums
+    and r multiply-adds (3 flops per pair), the centre and axis sums, and the
+    leapfrog update with damping (~8)."""
+    r = space_order // 2
+    return 9 * r + 10
 
 
 def cpu_oracle_rate(w, dt, steps_a, steps_b):
@@ -321,7 +339,11 @@ def run_native(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": ms_e}
 
-    # roofline of the dominant kernel (the blocked sweep)
+    # roofline of the dominant kernel (the blocked sweep).  With T steps per
+    # sweep its HBM traffic is 20/T B per point-step, far below the HBM roof;
+    # it is bound by instruction issue, so the reported bound is the FP32 pipe
+    # ("alu": algorithmic flops against the FMA peak), with the HBM roof and
+    # the issue rate (ncu's instructions per point update) beside it.
     T = args.time_tile
     peak, peak_kind = measured_peaks()
     launches_per_shot = kl_b
@@ -331,12 +353,28 @@ def run_native(args):
     points_per_launch = N * full_sweeps / max(launches_per_shot, 1)
     bytes_per_launch = 20.0 * points_per_launch
     achieved = bytes_per_launch / (kms_b * 1e-3) / 1e9
-    traffic = ncu_traffic(f"sweep_R{w.so // 2}_T{T}")
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-            "kernel": f"sweep_kernel<R={w.so // 2},T={T}>",
-            "bytes_per_launch": bytes_per_launch, "kernel_ms_per_launch": kms_b,
-            "point_updates_per_s_in_kernel": points_per_launch * T / (kms_b * 1e-3) / 1e9}
+    key = f"sweep_R{w.so // 2}_T{T}"
+    counters = ncu_counters(key)
+    upd_per_s = points_per_launch * T / (kms_b * 1e-3)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fpk, mhz = fp32_peak_tflops(nsm)
+    fl = alg_flops(w.so)
+    flops_per_launch = fl * points_per_launch * T
+    roof = {"bound": "alu", "achieved": upd_per_s * fl / 1e12, "peak": fpk, "unit": "TFLOP/s",
+            "frac": upd_per_s * fl / 1e12 / fpk,
+            "traffic": counters.get("dram_bytes_per_launch_full_size"),
+            "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz",
+            "kernel": f"sweep_kernel<R={w.so // 2},T={T}>", "flops_per_point_step": fl,
+            "flops_per_launch": flops_per_launch, "bytes_per_launch": bytes_per_launch,
+            "kernel_ms_per_launch": kms_b, "point_updates_per_s_in_kernel": upd_per_s / 1e9,
+            "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": peak_kind}}
+    ipp = counters.get("warp_inst_per_point_update")
+    if ipp:
+        ipeak = nsm * 4 * mhz * 1e6
+        roof["issue"] = {"warp_inst_per_point_update": ipp, "achieved": ipp * upd_per_s / 1e9,
+                         "peak": ipeak / 1e9, "unit": "G warp-inst/s", "frac": ipp * upd_per_s / ipeak,
+                         "source": counters.get("inst_measured_on")}
     if "onestep" in out:
         o = out["onestep"]
         bpl1 = 16.0 * N * nt / max(o["launches_per_step"], 1)

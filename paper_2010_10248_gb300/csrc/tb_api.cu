@@ -957,10 +957,13 @@ static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
   } else {
     TB_CUDA(h, cudaMemsetAsync(h->efield, 0, 9 * fbytes, st));
   }
-  // enough columns x chunks to fill the GPU a few times over (the streaming kernels)
+  // chunks of planes along axis 0 for the streaming kernels (all chunks of a
+  // step in one launch): enough columns x chunks for about two waves of
+  // full SMs, chunks no shorter than 4r planes (each re-reads 2r planes to
+  // warm up its queue)
   const int64_t cols = h->n[1] * h->n[2];
-  const int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>(h->n[0] / std::max(4, 2 * h->R),
-                                                                   (int64_t)h->num_sms * 2048 / std::max<int64_t>(cols, 1)));
+  const int nchunks = (int)std::max<int64_t>(1, std::min<int64_t>(h->n[0] / std::max(4, 4 * h->R),
+                                                                   (int64_t)h->num_sms * 2048 * 2 / std::max<int64_t>(cols, 1)));
   int pc = 0, pp = 1, rc = 2, rp = 3;  // TTI field indices
   int fill = 0, base = 0;
   const size_t Np = (size_t)h->n[0] * h->n[1] * h->n2p;
@@ -1016,7 +1019,7 @@ static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
       f0 = h->field[pc];
       f1 = h->field[rc];
     } else {
-      e = elastic_step(h->R, g, w, (float)h->dt, h->efield, h->emat, h->eta_dt, st);
+      e = elastic_step(h->R, g, w, (float)h->dt, nchunks, h->efield, h->emat, h->eta_dt, st);
       f0 = h->efield + 3 * Np;
       f1 = h->efield + 4 * Np;
       f2 = h->efield + 5 * Np;

@@ -116,7 +116,7 @@ cudaError_t tti_step(int R, const PhysGrid& g, const DerivW& w, int nchunks, con
                      const float* damp_b, float* flux, cudaStream_t st);
 cudaError_t tti_coefficients(const PhysGrid& g, const float* aux, float* coef, float* nz, unsigned* d_emax,
                              int* d_bad, cudaStream_t st);
-cudaError_t elastic_step(int R, const PhysGrid& g, const DerivW& w, float dt, float* f, const float* mat,
+cudaError_t elastic_step(int R, const PhysGrid& g, const DerivW& w, float dt, int nchunks, float* f, const float* mat,
                          const float* eta_dt, cudaStream_t st);
 cudaError_t elastic_material(const PhysGrid& g, const float* vp, const float* vs, const float* rho, float* mat,
                              int* d_bad, cudaStream_t st);

@@ -61,12 +61,14 @@ __device__ __forceinline__ void atomic_max_warp(unsigned* dst, float v) {
 
 // scales: s[k] is the scale of u^{k-1} (s[0] for u^{-1}); mx[k]: max |u^{k-1}|
 template <class ST, int R>
-__global__ void __launch_bounds__(256) k_ac_lp(PhysGrid g, LapW w, int x0, int x1, const ST* __restrict__ uc,
+__global__ void __launch_bounds__(256) k_ac_lp(PhysGrid g, LapW w, int nchunks, const ST* __restrict__ uc,
                                                ST* up, const float* __restrict__ c2,
                                                const float* __restrict__ damp_b, const float* __restrict__ scales,
                                                int n, unsigned* __restrict__ mx) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   const bool ok = z < g.n2 && y < g.n1;
+  // planes [x0, x1) of chunk blockIdx.z (all chunks of a step in one launch)
+  const int x0 = (int)((int64_t)g.n0 * blockIdx.z / nchunks), x1 = (int)((int64_t)g.n0 * (blockIdx.z + 1) / nchunks);
   const float s_cur = scales[n + 1], s_prev = scales[n], inv_out = 1.0f / scales[n + 2];  // powers of two
   float q[2 * R + 1];
 #pragma unroll
@@ -95,8 +97,10 @@ __global__ void __launch_bounds__(256) k_ac_lp(PhysGrid g, LapW w, int x0, int x
     const float cc = __ldg(c2 + i0);
     const float gd = __fmul_rn(__fadd_rn(__ldg(damp_b + x), byz), cc);
     const float uprev = __fmul_rn(Store<ST>::get(up + i0), s_prev);
-    const float un = __fadd_rn(u, __fdiv_rn(__fmaf_rn(cc, l, __fmul_rn(__fsub_rn(1.f, gd), __fsub_rn(u, uprev))),
-                                            __fadd_rn(1.f, gd)));
+    // the quotient is exact without a division outside the sponge (1 + gd = 1)
+    const float num = __fmaf_rn(cc, l, __fmul_rn(__fsub_rn(1.f, gd), __fsub_rn(u, uprev)));
+    const float den = __fadd_rn(1.f, gd);
+    const float un = __fadd_rn(u, den == 1.f ? num : __fdiv_rn(num, den));
     up[i0] = Store<ST>::make(__fmul_rn(un, inv_out));
     vmax = fmaxf(vmax, fabsf(un));
   }
@@ -165,13 +169,9 @@ __global__ void k_lp_unpack(PhysGrid g, const ST* __restrict__ u, float s, float
 template <class ST, int R>
 static cudaError_t lp_step_t(const PhysGrid& g, const LapW& w, int nchunks, const void* uc, void* up, const float* c2,
                              const float* damp_b, const float* scales, int n, unsigned* mx, cudaStream_t st) {
-  const dim3 blk(32, 8), grd((unsigned)((g.n2 + 31) / 32), (unsigned)((g.n1 + 7) / 8));
-  for (int c = 0; c < nchunks; ++c) {
-    const int x0 = (int)((int64_t)g.n0 * c / nchunks), x1 = (int)((int64_t)g.n0 * (c + 1) / nchunks);
-    if (x1 <= x0) continue;
-    count_launch();
-    k_ac_lp<ST, R><<<grd, blk, 0, st>>>(g, w, x0, x1, (const ST*)uc, (ST*)up, c2, damp_b, scales, n, mx);
-  }
+  const dim3 blk(32, 8), grd((unsigned)((g.n2 + 31) / 32), (unsigned)((g.n1 + 7) / 8), (unsigned)nchunks);
+  count_launch();
+  k_ac_lp<ST, R><<<grd, blk, 0, st>>>(g, w, nchunks, (const ST*)uc, (ST*)up, c2, damp_b, scales, n, mx);
   return cudaGetLastError();
 }
 template <class ST>

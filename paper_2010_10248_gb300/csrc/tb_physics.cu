@@ -51,6 +51,15 @@ __device__ __forceinline__ float ld0(const PhysGrid& g, const float* __restrict_
   return (x >= 0 && x < g.n0 && y >= 0 && y < g.n1 && z >= 0 && z < g.n2) ? __ldg(f + pidx(g, x, y, z)) : 0.f;
 }
 
+// planes [x0, x1) of the chunk blockIdx.z of nchunks along axis 0 (all chunks
+// of a step run in one launch)
+__device__ __forceinline__ void chunk_planes(const PhysGrid& g, int nchunks, int& x0, int& x1) {
+  x0 = (int)((int64_t)g.n0 * blockIdx.z / nchunks);
+  x1 = (int)((int64_t)g.n0 * (blockIdx.z + 1) / nchunks);
+}
+// n / den, exact when den is 1 (outside the sponge) without a division
+__device__ __forceinline__ float div_sponge(float n, float den) { return den == 1.f ? n : __fdiv_rn(n, den); }
+
 // ------------------------------------------------------------------ TTI --
 // centred first derivative along axis 1 / 2 at (x, y, z): sum_i a_i (f_{+i} - f_{-i})
 template <int R>
@@ -78,11 +87,13 @@ __device__ __forceinline__ float dc_q(const float* q, const float* a) {  // q[R]
 // pass 1: F = grad p - zbar (zbar . grad p), G = zbar (zbar . grad r) on
 // planes [x0, x1) of every column
 template <int R>
-__global__ void __launch_bounds__(256) k_tti_flux(PhysGrid g, DerivW w, int x0, int x1, const float* __restrict__ p,
+__global__ void __launch_bounds__(256) k_tti_flux(PhysGrid g, DerivW w, int nchunks, const float* __restrict__ p,
                                                   const float* __restrict__ r, const float* __restrict__ nz,
                                                   float* __restrict__ flux) {
   const Col c = thread_col(g);
   if (!c.ok) return;
+  int x0, x1;
+  chunk_planes(g, nchunks, x0, x1);
   const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
   float qp[2 * R + 1], qr[2 * R + 1];
 #pragma unroll
@@ -118,12 +129,14 @@ __global__ void __launch_bounds__(256) k_tti_flux(PhysGrid g, DerivW w, int x0, 
 // pass 2: H_h p = div F, H_z r = div G; leapfrog update of p and r written
 // over p^{n-1}, r^{n-1}
 template <int R>
-__global__ void __launch_bounds__(256) k_tti_update(PhysGrid g, DerivW w, int x0, int x1, const float* __restrict__ flux,
+__global__ void __launch_bounds__(256) k_tti_update(PhysGrid g, DerivW w, int nchunks, const float* __restrict__ flux,
                                                     const float* __restrict__ pc, float* pp, const float* __restrict__ rc,
                                                     float* rp, const float* __restrict__ c2,
                                                     const float* __restrict__ coef, const float* __restrict__ damp_b) {
   const Col c = thread_col(g);
   if (!c.ok) return;
+  int x0, x1;
+  chunk_planes(g, nchunks, x0, x1);
   const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
   const float* F0 = flux;
   const float* G0 = flux + 3 * Np;
@@ -154,8 +167,8 @@ __global__ void __launch_bounds__(256) k_tti_update(PhysGrid g, DerivW w, int x0
     const float gdamp = __fmul_rn(__fadd_rn(__ldg(damp_b + x), byz), c2v);
     const float opg = __fadd_rn(1.f, gdamp), omg = __fsub_rn(1.f, gdamp);
     const float up = pc[i0], upp = pp[i0], ur = rc[i0], urp = rp[i0];
-    pp[i0] = __fadd_rn(up, __fdiv_rn(__fmaf_rn(c2v, rhs_p, __fmul_rn(omg, __fsub_rn(up, upp))), opg));
-    rp[i0] = __fadd_rn(ur, __fdiv_rn(__fmaf_rn(c2v, rhs_r, __fmul_rn(omg, __fsub_rn(ur, urp))), opg));
+    pp[i0] = __fadd_rn(up, div_sponge(__fmaf_rn(c2v, rhs_p, __fmul_rn(omg, __fsub_rn(up, upp))), opg));
+    rp[i0] = __fadd_rn(ur, div_sponge(__fmaf_rn(c2v, rhs_r, __fmul_rn(omg, __fsub_rn(ur, urp))), opg));
   }
 }
 
@@ -176,59 +189,110 @@ __device__ __forceinline__ float dstag(const PhysGrid& g, const float* f, const 
   return s;
 }
 
-// fields: [9][Np] vx vy vz txx tyy tzz txy txz tyz; mat: [8][Np] bx by bz lam mu mxy mxz myz
+// staggered derivative along axis 0 from a register queue (q[R + s] is
+// plane x + s): the same sums as dstag<R, 0>
 template <int R>
-__global__ void __launch_bounds__(256) k_ela_velocity(PhysGrid g, DerivW w, float dt, float* __restrict__ f,
+__device__ __forceinline__ float dstag_q(const float* q, const float* cw, bool plus) {
+  float s = 0.f;
+#pragma unroll
+  for (int k = R; k >= 1; --k) {
+    const int hi = plus ? k : k - 1, lo = plus ? -(k - 1) : -k;
+    s = __fmaf_rn(cw[k - 1], __fsub_rn(q[R + hi], q[R + lo]), s);
+  }
+  return s;
+}
+
+// fields: [9][Np] vx vy vz txx tyy tzz txy txz tyz; mat: [8][Np] bx by bz lam mu mxy mxz myz.
+// Each thread streams its column through the planes of one chunk; the axis-0
+// neighbours of the three fields it differentiates along axis 0 sit in
+// register queues of planes x-R .. x+R.
+template <int R>
+__global__ void __launch_bounds__(256) k_ela_velocity(PhysGrid g, DerivW w, float dt, int nchunks, float* __restrict__ f,
                                                       const float* __restrict__ mat, const float* __restrict__ eta_dt) {
   const Col c = thread_col(g);
   if (!c.ok) return;
-  const int x = blockIdx.z;
+  int x0, x1;
+  chunk_planes(g, nchunks, x0, x1);
   const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
-  const size_t i0 = pidx(g, x, c.y, c.z);
   const float *txx = f + 3 * Np, *tyy = f + 4 * Np, *tzz = f + 5 * Np, *txy = f + 6 * Np, *txz = f + 7 * Np,
               *tyz = f + 8 * Np;
-  const float fx = __fadd_rn(__fadd_rn(dstag<R, 0>(g, txx, w.a[0], x, c.y, c.z, true),
-                                       dstag<R, 1>(g, txy, w.a[1], x, c.y, c.z, false)),
-                             dstag<R, 2>(g, txz, w.a[2], x, c.y, c.z, false));
-  const float fy = __fadd_rn(__fadd_rn(dstag<R, 0>(g, txy, w.a[0], x, c.y, c.z, false),
-                                       dstag<R, 1>(g, tyy, w.a[1], x, c.y, c.z, true)),
-                             dstag<R, 2>(g, tyz, w.a[2], x, c.y, c.z, false));
-  const float fz = __fadd_rn(__fadd_rn(dstag<R, 0>(g, txz, w.a[0], x, c.y, c.z, false),
-                                       dstag<R, 1>(g, tyz, w.a[1], x, c.y, c.z, false)),
-                             dstag<R, 2>(g, tzz, w.a[2], x, c.y, c.z, true));
-  const float den = __fadd_rn(1.f, __fadd_rn(__fadd_rn(__ldg(eta_dt + x), __ldg(eta_dt + g.n0 + c.y)),
-                                            __ldg(eta_dt + g.n0 + g.n1 + c.z)));
-  f[i0] = __fdiv_rn(__fmaf_rn(__fmul_rn(dt, __ldg(mat + i0)), fx, f[i0]), den);
-  f[Np + i0] = __fdiv_rn(__fmaf_rn(__fmul_rn(dt, __ldg(mat + Np + i0)), fy, f[Np + i0]), den);
-  f[2 * Np + i0] = __fdiv_rn(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 2 * Np + i0)), fz, f[2 * Np + i0]), den);
+  float qa[2 * R + 1], qb[2 * R + 1], qc[2 * R + 1];  // txx, txy, txz
+#pragma unroll
+  for (int s = 0; s < 2 * R + 1; ++s) {
+    qa[s] = ld0(g, txx, x0 - 1 - R + s, c.y, c.z);
+    qb[s] = ld0(g, txy, x0 - 1 - R + s, c.y, c.z);
+    qc[s] = ld0(g, txz, x0 - 1 - R + s, c.y, c.z);
+  }
+  const float ey = __ldg(eta_dt + g.n0 + c.y), ez = __ldg(eta_dt + g.n0 + g.n1 + c.z);
+  for (int x = x0; x < x1; ++x) {
+#pragma unroll
+    for (int s = 0; s < 2 * R; ++s) {
+      qa[s] = qa[s + 1];
+      qb[s] = qb[s + 1];
+      qc[s] = qc[s + 1];
+    }
+    qa[2 * R] = ld0(g, txx, x + R, c.y, c.z);
+    qb[2 * R] = ld0(g, txy, x + R, c.y, c.z);
+    qc[2 * R] = ld0(g, txz, x + R, c.y, c.z);
+    const size_t i0 = pidx(g, x, c.y, c.z);
+    const float fx = __fadd_rn(__fadd_rn(dstag_q<R>(qa, w.a[0], true), dstag<R, 1>(g, txy, w.a[1], x, c.y, c.z, false)),
+                               dstag<R, 2>(g, txz, w.a[2], x, c.y, c.z, false));
+    const float fy = __fadd_rn(__fadd_rn(dstag_q<R>(qb, w.a[0], false), dstag<R, 1>(g, tyy, w.a[1], x, c.y, c.z, true)),
+                               dstag<R, 2>(g, tyz, w.a[2], x, c.y, c.z, false));
+    const float fz = __fadd_rn(__fadd_rn(dstag_q<R>(qc, w.a[0], false), dstag<R, 1>(g, tyz, w.a[1], x, c.y, c.z, false)),
+                               dstag<R, 2>(g, tzz, w.a[2], x, c.y, c.z, true));
+    const float den = __fadd_rn(1.f, __fadd_rn(__fadd_rn(__ldg(eta_dt + x), ey), ez));
+    f[i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, __ldg(mat + i0)), fx, f[i0]), den);
+    f[Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, __ldg(mat + Np + i0)), fy, f[Np + i0]), den);
+    f[2 * Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 2 * Np + i0)), fz, f[2 * Np + i0]), den);
+  }
 }
 
 template <int R>
-__global__ void __launch_bounds__(256) k_ela_stress(PhysGrid g, DerivW w, float dt, float* __restrict__ f,
+__global__ void __launch_bounds__(256) k_ela_stress(PhysGrid g, DerivW w, float dt, int nchunks, float* __restrict__ f,
                                                     const float* __restrict__ mat, const float* __restrict__ eta_dt) {
   const Col c = thread_col(g);
   if (!c.ok) return;
-  const int x = blockIdx.z;
+  int x0, x1;
+  chunk_planes(g, nchunks, x0, x1);
   const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
-  const size_t i0 = pidx(g, x, c.y, c.z);
   const float *vx = f, *vy = f + Np, *vz = f + 2 * Np;
-  const float exx = dstag<R, 0>(g, vx, w.a[0], x, c.y, c.z, false);
-  const float eyy = dstag<R, 1>(g, vy, w.a[1], x, c.y, c.z, false);
-  const float ezz = dstag<R, 2>(g, vz, w.a[2], x, c.y, c.z, false);
-  const float gxy = __fadd_rn(dstag<R, 1>(g, vx, w.a[1], x, c.y, c.z, true), dstag<R, 0>(g, vy, w.a[0], x, c.y, c.z, true));
-  const float gxz = __fadd_rn(dstag<R, 2>(g, vx, w.a[2], x, c.y, c.z, true), dstag<R, 0>(g, vz, w.a[0], x, c.y, c.z, true));
-  const float gyz = __fadd_rn(dstag<R, 2>(g, vy, w.a[2], x, c.y, c.z, true), dstag<R, 1>(g, vz, w.a[1], x, c.y, c.z, true));
-  const float lam = __ldg(mat + 3 * Np + i0), mu = __ldg(mat + 4 * Np + i0);
-  const float ltr = __fmul_rn(lam, __fadd_rn(__fadd_rn(exx, eyy), ezz));
-  const float den = __fadd_rn(1.f, __fadd_rn(__fadd_rn(__ldg(eta_dt + x), __ldg(eta_dt + g.n0 + c.y)),
-                                            __ldg(eta_dt + g.n0 + g.n1 + c.z)));
-  const float mu2 = __fmul_rn(2.f, mu);
-  f[3 * Np + i0] = __fdiv_rn(__fmaf_rn(dt, __fmaf_rn(mu2, exx, ltr), f[3 * Np + i0]), den);
-  f[4 * Np + i0] = __fdiv_rn(__fmaf_rn(dt, __fmaf_rn(mu2, eyy, ltr), f[4 * Np + i0]), den);
-  f[5 * Np + i0] = __fdiv_rn(__fmaf_rn(dt, __fmaf_rn(mu2, ezz, ltr), f[5 * Np + i0]), den);
-  f[6 * Np + i0] = __fdiv_rn(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 5 * Np + i0)), gxy, f[6 * Np + i0]), den);
-  f[7 * Np + i0] = __fdiv_rn(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 6 * Np + i0)), gxz, f[7 * Np + i0]), den);
-  f[8 * Np + i0] = __fdiv_rn(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 7 * Np + i0)), gyz, f[8 * Np + i0]), den);
+  float qa[2 * R + 1], qb[2 * R + 1], qc[2 * R + 1];  // vx, vy, vz
+#pragma unroll
+  for (int s = 0; s < 2 * R + 1; ++s) {
+    qa[s] = ld0(g, vx, x0 - 1 - R + s, c.y, c.z);
+    qb[s] = ld0(g, vy, x0 - 1 - R + s, c.y, c.z);
+    qc[s] = ld0(g, vz, x0 - 1 - R + s, c.y, c.z);
+  }
+  const float ey = __ldg(eta_dt + g.n0 + c.y), ez = __ldg(eta_dt + g.n0 + g.n1 + c.z);
+  for (int x = x0; x < x1; ++x) {
+#pragma unroll
+    for (int s = 0; s < 2 * R; ++s) {
+      qa[s] = qa[s + 1];
+      qb[s] = qb[s + 1];
+      qc[s] = qc[s + 1];
+    }
+    qa[2 * R] = ld0(g, vx, x + R, c.y, c.z);
+    qb[2 * R] = ld0(g, vy, x + R, c.y, c.z);
+    qc[2 * R] = ld0(g, vz, x + R, c.y, c.z);
+    const size_t i0 = pidx(g, x, c.y, c.z);
+    const float exx = dstag_q<R>(qa, w.a[0], false);
+    const float eyy = dstag<R, 1>(g, vy, w.a[1], x, c.y, c.z, false);
+    const float ezz = dstag<R, 2>(g, vz, w.a[2], x, c.y, c.z, false);
+    const float gxy = __fadd_rn(dstag<R, 1>(g, vx, w.a[1], x, c.y, c.z, true), dstag_q<R>(qb, w.a[0], true));
+    const float gxz = __fadd_rn(dstag<R, 2>(g, vx, w.a[2], x, c.y, c.z, true), dstag_q<R>(qc, w.a[0], true));
+    const float gyz = __fadd_rn(dstag<R, 2>(g, vy, w.a[2], x, c.y, c.z, true), dstag<R, 1>(g, vz, w.a[1], x, c.y, c.z, true));
+    const float lam = __ldg(mat + 3 * Np + i0), mu = __ldg(mat + 4 * Np + i0);
+    const float ltr = __fmul_rn(lam, __fadd_rn(__fadd_rn(exx, eyy), ezz));
+    const float den = __fadd_rn(1.f, __fadd_rn(__fadd_rn(__ldg(eta_dt + x), ey), ez));
+    const float mu2 = __fmul_rn(2.f, mu);
+    f[3 * Np + i0] = div_sponge(__fmaf_rn(dt, __fmaf_rn(mu2, exx, ltr), f[3 * Np + i0]), den);
+    f[4 * Np + i0] = div_sponge(__fmaf_rn(dt, __fmaf_rn(mu2, eyy, ltr), f[4 * Np + i0]), den);
+    f[5 * Np + i0] = div_sponge(__fmaf_rn(dt, __fmaf_rn(mu2, ezz, ltr), f[5 * Np + i0]), den);
+    f[6 * Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 5 * Np + i0)), gxy, f[6 * Np + i0]), den);
+    f[7 * Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 6 * Np + i0)), gxz, f[7 * Np + i0]), den);
+    f[8 * Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 7 * Np + i0)), gyz, f[8 * Np + i0]), den);
+  }
 }
 
 // material at the staggered positions from vp, vs, rho (dense [N]):
@@ -325,20 +389,12 @@ template <int R>
 static cudaError_t tti_step_r(const PhysGrid& g, const DerivW& w, int nchunks, const float* pc, float* pp,
                               const float* rc, float* rp, const float* c2, const float* coef, const float* nz,
                               const float* damp_b, float* flux, cudaStream_t st) {
-  // chunks of planes: each column streams its chunk (the queue warms up on
-  // R planes before the chunk)
+  // chunks of planes, all in one launch: each column streams its chunk (the
+  // queue warms up on R planes before the chunk)
   const dim3 blk(32, 8);
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int cidx = 0; cidx < nchunks; ++cidx) {
-      const int x0 = (int)((int64_t)g.n0 * cidx / nchunks), x1 = (int)((int64_t)g.n0 * (cidx + 1) / nchunks);
-      if (x1 <= x0) continue;
-      count_launch();
-      if (pass == 0)
-        k_tti_flux<R><<<col_grid(g, 1), blk, 0, st>>>(g, w, x0, x1, pc, rc, nz, flux);
-      else
-        k_tti_update<R><<<col_grid(g, 1), blk, 0, st>>>(g, w, x0, x1, flux, pc, pp, rc, rp, c2, coef, damp_b);
-    }
-  }
+  count_launch(2);
+  k_tti_flux<R><<<col_grid(g, nchunks), blk, 0, st>>>(g, w, nchunks, pc, rc, nz, flux);
+  k_tti_update<R><<<col_grid(g, nchunks), blk, 0, st>>>(g, w, nchunks, flux, pc, pp, rc, rp, c2, coef, damp_b);
   return cudaGetLastError();
 }
 
@@ -354,21 +410,21 @@ cudaError_t tti_step(int R, const PhysGrid& g, const DerivW& w, int nchunks, con
 }
 
 template <int R>
-static cudaError_t ela_step_r(const PhysGrid& g, const DerivW& w, float dt, float* f, const float* mat,
+static cudaError_t ela_step_r(const PhysGrid& g, const DerivW& w, float dt, int nchunks, float* f, const float* mat,
                               const float* eta_dt, cudaStream_t st) {
   const dim3 blk(32, 8);
   count_launch(2);
-  k_ela_velocity<R><<<col_grid(g, g.n0), blk, 0, st>>>(g, w, dt, f, mat, eta_dt);
-  k_ela_stress<R><<<col_grid(g, g.n0), blk, 0, st>>>(g, w, dt, f, mat, eta_dt);
+  k_ela_velocity<R><<<col_grid(g, nchunks), blk, 0, st>>>(g, w, dt, nchunks, f, mat, eta_dt);
+  k_ela_stress<R><<<col_grid(g, nchunks), blk, 0, st>>>(g, w, dt, nchunks, f, mat, eta_dt);
   return cudaGetLastError();
 }
 
-cudaError_t elastic_step(int R, const PhysGrid& g, const DerivW& w, float dt, float* f, const float* mat,
+cudaError_t elastic_step(int R, const PhysGrid& g, const DerivW& w, float dt, int nchunks, float* f, const float* mat,
                          const float* eta_dt, cudaStream_t st) {
   switch (R) {
-    case 2: return ela_step_r<2>(g, w, dt, f, mat, eta_dt, st);
-    case 4: return ela_step_r<4>(g, w, dt, f, mat, eta_dt, st);
-    case 6: return ela_step_r<6>(g, w, dt, f, mat, eta_dt, st);
+    case 2: return ela_step_r<2>(g, w, dt, nchunks, f, mat, eta_dt, st);
+    case 4: return ela_step_r<4>(g, w, dt, nchunks, f, mat, eta_dt, st);
+    case 6: return ela_step_r<6>(g, w, dt, nchunks, f, mat, eta_dt, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -70,10 +70,14 @@ enum { TB_ACOUSTIC = 0, TB_TTI = 1, TB_ELASTIC = 2 };
 enum { TB_ONESTEP = 0, TB_BLOCKED = 1 };
 /* Wavefield storage (tb_options.storage), acoustic physics:
  *   TB_F32       FP32 fields, TMA-staged one-step and blocked sweeps (default);
- *   TB_F16       FP16 fields, FP32 arithmetic, per-field power-of-two scales;
- *   TB_BF16      BF16 fields, FP32 arithmetic, per-field power-of-two scales;
- *   TB_F32_PLAIN FP32 fields through the same streaming kernel as TB_F16 /
- *                TB_BF16 (their equal-structure FP32 baseline).
+ *   TB_F16       FP16 fields, FP32 arithmetic, per-field power-of-two scales
+ *                (stored value u / s, s set on the device each step from the
+ *                previous step's max |u|), through the TMA-staged one-step
+ *                sweep: half the wavefield bytes and footprint of TB_F32;
+ *   TB_BF16      BF16 fields, likewise;
+ *   TB_F32_PLAIN FP32 fields with the same per-step scales through a plain
+ *                streaming one-step kernel (a second, independent
+ *                implementation of the scaled step).
  * The 16-bit and plain modes run one step per launch (TB_ONESTEP). */
 enum { TB_F32 = 0, TB_F16 = 1, TB_BF16 = 2, TB_F32_PLAIN = 3 };
 

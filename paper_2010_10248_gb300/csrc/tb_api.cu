@@ -13,31 +13,31 @@
 #include "tb_internal.cuh"
 
 namespace tbi {
-cudaError_t sweep_dispatch_r2(int what, int T, const SweepParams* p, int nctas, bool coop,
+cudaError_t sweep_dispatch_r2(int what, int T, int sk, const SweepParams* p, int nctas, bool coop,
                               cudaStream_t st, int* per_sm, SweepShape* s);
-cudaError_t sweep_dispatch_r4(int what, int T, const SweepParams* p, int nctas, bool coop,
+cudaError_t sweep_dispatch_r4(int what, int T, int sk, const SweepParams* p, int nctas, bool coop,
                               cudaStream_t st, int* per_sm, SweepShape* s);
-cudaError_t sweep_dispatch_r6(int what, int T, const SweepParams* p, int nctas, bool coop,
+cudaError_t sweep_dispatch_r6(int what, int T, int sk, const SweepParams* p, int nctas, bool coop,
                               cudaStream_t st, int* per_sm, SweepShape* s);
 
-static cudaError_t sweep_dispatch(int R, int what, int T, const SweepParams* p, int nctas, bool coop,
+static cudaError_t sweep_dispatch(int R, int what, int T, int sk, const SweepParams* p, int nctas, bool coop,
                                   cudaStream_t st, int* per_sm, SweepShape* s) {
   switch (R) {
-    case 2: return sweep_dispatch_r2(what, T, p, nctas, coop, st, per_sm, s);
-    case 4: return sweep_dispatch_r4(what, T, p, nctas, coop, st, per_sm, s);
-    case 6: return sweep_dispatch_r6(what, T, p, nctas, coop, st, per_sm, s);
+    case 2: return sweep_dispatch_r2(what, T, sk, p, nctas, coop, st, per_sm, s);
+    case 4: return sweep_dispatch_r4(what, T, sk, p, nctas, coop, st, per_sm, s);
+    case 6: return sweep_dispatch_r6(what, T, sk, p, nctas, coop, st, per_sm, s);
   }
   return cudaErrorInvalidValue;
 }
-bool sweep_shape(int R, int T, SweepShape* s) {
-  return sweep_dispatch(R, 2, T, nullptr, 0, false, nullptr, nullptr, s) == cudaSuccess;
+bool sweep_shape(int R, int T, SweepShape* s, int sk) {
+  return sweep_dispatch(R, 2, T, sk, nullptr, 0, false, nullptr, nullptr, s) == cudaSuccess;
 }
-cudaError_t sweep_max_ctas(int R, int T, int* per_sm) {
-  return sweep_dispatch(R, 1, T, nullptr, 0, false, nullptr, per_sm, nullptr);
+cudaError_t sweep_max_ctas(int R, int T, int* per_sm, int sk) {
+  return sweep_dispatch(R, 1, T, sk, nullptr, 0, false, nullptr, per_sm, nullptr);
 }
 cudaError_t sweep_launch(int R, int T, const SweepParams& p, int nctas, bool cooperative,
-                         cudaStream_t st) {
-  return sweep_dispatch(R, 0, T, &p, nctas, cooperative, st, nullptr, nullptr);
+                         cudaStream_t st, int sk) {
+  return sweep_dispatch(R, 0, T, sk, &p, nctas, cooperative, st, nullptr, nullptr);
 }
 }  // namespace tbi
 
@@ -81,6 +81,7 @@ struct tb_handle {
   // update writes u^{n+1} over u^{n-1}), per-step scales and maxima, per-step
   // largest source increment
   int storage = TB_F32;
+  int sk = 0;  // storage kind of the sweep kernel: 0 FP32, 1 FP16, 2 BF16 (one-step)
   void* lp[2] = {nullptr, nullptr};
   int lp_cur = 0;
   float* lp_scales = nullptr;
@@ -351,7 +352,8 @@ extern "C" int tb_destroy(tb_handle* h) {
 
 // TMA descriptor of a padded field [n0][n1][n2p] (only n2 columns are in
 // the tensor, so cells past n2 read as zeros) with a box of bw x bh x 1.
-static cudaError_t make_tmap(CUtensorMap* m, float* base, const int64_t n[3], int n2p, int bw, int bh) {
+static cudaError_t make_tmap(CUtensorMap* m, void* base, const int64_t n[3], int n2p, int bw, int bh,
+                             CUtensorMapDataType dtype = CU_TENSOR_MAP_DATA_TYPE_FLOAT32, int esz = 4) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -362,10 +364,10 @@ static cudaError_t make_tmap(CUtensorMap* m, float* base, const int64_t n[3], in
     encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
   const cuuint64_t dims[3] = {(cuuint64_t)n[2], (cuuint64_t)n[1], (cuuint64_t)n[0]};
-  const cuuint64_t strides[2] = {(cuuint64_t)n2p * 4, (cuuint64_t)n2p * 4 * n[1]};
+  const cuuint64_t strides[2] = {(cuuint64_t)n2p * esz, (cuuint64_t)n2p * esz * n[1]};
   const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+  CUresult r = encode(m, dtype, 3, base, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -408,7 +410,9 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   }
   if (h->opt.wait_timeout_s <= 0) h->opt.wait_timeout_s = 2.0;
   tb_fd_weights(so, h->c);
-  h->n2p = (int)((n[2] + 3) / 4 * 4);
+  // row pitch: 16-byte rows for TMA (8 values at 16 bits)
+  h->sk = (h->storage == TB_F16) ? 1 : (h->storage == TB_BF16 ? 2 : 0);
+  h->n2p = (int)(h->sk ? (n[2] + 7) / 8 * 8 : (n[2] + 3) / 4 * 4);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) {
@@ -449,12 +453,18 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   if (e == cudaSuccess) e = dmalloc(&h->err, sizeof(int) * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int) * 4, st);
   SweepShape sh;
-  if (e == cudaSuccess && !sweep_shape(h->R, 1, &sh)) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess && !sweep_shape(h->R, 1, &sh, h->sk)) e = cudaErrorInvalidValue;
   for (int i = 0; i < 4 && e == cudaSuccess && physics == TB_ACOUSTIC && h->storage == TB_F32; ++i) {
     e = make_tmap(&h->tm_box[i], h->field[i], n, h->n2p, sh.box_w, sh.box_h);
     if (e == cudaSuccess) e = make_tmap(&h->tm_tile[i], h->field[i], n, h->n2p, 64, sh.TY);
   }
-  if (e == cudaSuccess && physics == TB_ACOUSTIC && h->storage == TB_F32)
+  // 16-bit storage: the two stored fields, read by the one-step sweep
+  const CUtensorMapDataType dt16 = h->sk == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  for (int i = 0; i < 2 && e == cudaSuccess && physics == TB_ACOUSTIC && h->sk; ++i) {
+    e = make_tmap(&h->tm_box[i], h->lp[i], n, h->n2p, sh.box_w, sh.box_h, dt16, 2);
+    if (e == cudaSuccess) e = make_tmap(&h->tm_tile[i], h->lp[i], n, h->n2p, 64, sh.TY, dt16, 2);
+  }
+  if (e == cudaSuccess && physics == TB_ACOUSTIC && (h->storage == TB_F32 || h->sk))
     e = make_tmap(&h->tm_c2, h->c2, n, h->n2p, 64, sh.TY);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -753,9 +763,10 @@ struct Plan {
 static int plan_sweep(tb_handle* h, int T, Plan* pl) {
   const int R = h->R;
   SweepShape sh;
-  if (!sweep_shape(R, T, &sh)) return fail(h, TB_EINVAL, "unsupported time tile %d", T);
+  const int sk = T == 1 ? h->sk : 0;
+  if (!sweep_shape(R, T, &sh, sk)) return fail(h, TB_EINVAL, "unsupported time tile %d", T);
   int per_sm = 0;
-  cudaError_t e = sweep_max_ctas(R, T, &per_sm);
+  cudaError_t e = sweep_max_ctas(R, T, &per_sm, sk);
   if (e != cudaSuccess) return cuda_fail(h, e, "occupancy");
   if (per_sm < 1) return fail(h, TB_ECUDA, "sweep kernel does not fit on an SM");
   const int cap = per_sm * h->num_sms;
@@ -901,6 +912,26 @@ static cudaEvent_t ev_next(tb_handle* h) {
 // and receiver sampling as separate kernels after each step.
 static size_t Np_of(const tb_handle* h) { return (size_t)h->n[0] * h->n[1] * h->n2p; }
 
+// Scale buffers of the 16-bit storage for nt steps: scales[k] of u^{k-1}
+// (the zero fields u^{-1}, u^0 get 1) and the running max |u^{k-1}| (zeros).
+static int ensure_scales(tb_handle* h, int nt, cudaStream_t st) {
+  if (nt + 3 > h->lp_cap) {
+    dfree(h->lp_scales, st);
+    dfree(h->lp_mx, st);
+    h->lp_scales = nullptr;
+    h->lp_mx = nullptr;
+    h->lp_cap = 0;
+    TB_CUDA(h, dmalloc(&h->lp_scales, sizeof(float) * (nt + 3), st));
+    TB_CUDA(h, dmalloc(&h->lp_mx, sizeof(unsigned) * (nt + 3), st));
+    h->lp_cap = nt + 3;
+  }
+  const float ones[2] = {1.0f, 1.0f};
+  TB_CUDA(h, cudaMemcpyAsync(h->lp_scales, ones, sizeof(ones), cudaMemcpyHostToDevice, st));
+  TB_CUDA(h, cudaMemsetAsync(h->lp_mx, 0, sizeof(unsigned) * (nt + 3), st));
+  TB_CUDA(h, cudaStreamSynchronize(st));  // `ones` outlives the copy
+  return TB_OK;
+}
+
 static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
   const int nrec = h->have_rec ? h->rec.npt : 0;
   const bool rec_on = h->have_rec && h->rec.npts > 0 && nrec > 0 && traces;
@@ -935,22 +966,10 @@ static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
   if (lowp) {
     for (int d = 0; d < 3; ++d)
       for (int i = 1; i <= h->R; ++i) lw.c[d][i - 1] = (float)(h->c[i] / (h->h[d] * h->h[d]));
-    if (nt + 3 > h->lp_cap) {
-      dfree(h->lp_scales, st);
-      dfree(h->lp_mx, st);
-      h->lp_scales = nullptr;
-      h->lp_mx = nullptr;
-      h->lp_cap = 0;
-      TB_CUDA(h, dmalloc(&h->lp_scales, sizeof(float) * (nt + 3), st));
-      TB_CUDA(h, dmalloc(&h->lp_mx, sizeof(unsigned) * (nt + 3), st));
-      h->lp_cap = nt + 3;
-    }
-    std::vector<float> ones(nt + 3, 1.0f);
-    TB_CUDA(h, cudaMemcpyAsync(h->lp_scales, ones.data(), sizeof(float) * 2, cudaMemcpyHostToDevice, st));
-    TB_CUDA(h, cudaMemsetAsync(h->lp_mx, 0, sizeof(unsigned) * (nt + 3), st));
+    int s = ensure_scales(h, nt, st);
+    if (s != TB_OK) return s;
     TB_CUDA(h, cudaMemsetAsync(h->lp[0], 0, es * Np_of(h), st));
     TB_CUDA(h, cudaMemsetAsync(h->lp[1], 0, es * Np_of(h), st));
-    TB_CUDA(h, cudaStreamSynchronize(st));  // `ones` outlives the copy
     h->lp_cur = 0;
   } else if (h->physics == TB_TTI) {
     for (int i = 0; i < 4; ++i) TB_CUDA(h, cudaMemsetAsync(h->field[i], 0, fbytes, st));
@@ -1074,7 +1093,9 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   if (h->physics != TB_ACOUSTIC || h->storage != TB_F32) {
     if (schedule != TB_ONESTEP)
       return fail(h, TB_EINVAL, "the blocked schedule is implemented for the FP32 acoustic equation only");
-    return forward_other(h, nt, traces, st);
+    // FP16 / BF16 storage runs the one-step sweep below; TTI, elastic and
+    // plain-FP32 storage run their streaming kernels
+    if (!h->sk) return forward_other(h, nt, traces, st);
   }
   const int nrec = h->have_rec ? h->rec.npt : 0;
   const bool host_traces = traces && nrec > 0 && !is_device_ptr(traces);
@@ -1089,11 +1110,22 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   if (T > 1 && (s = ensure_capacity(h, T, pT, nt, host_traces, nrec, st)) != TB_OK) return s;
   if (host_traces) dtr = h->traces_dev;
 
-  const size_t fbytes = sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n2p;
+  // the wavefield buffers: four FP32 fields, or the two 16-bit stored fields
+  float* fld[4] = {h->field[0], h->field[1], h->field[2], h->field[3]};
+  if (h->sk) {
+    fld[0] = static_cast<float*>(h->lp[0]);
+    fld[1] = static_cast<float*>(h->lp[1]);
+  }
+  const size_t fbytes = (h->sk ? 2 : sizeof(float)) * (size_t)h->n[0] * h->n[1] * h->n2p;
   // zero initial conditions (Eq. 1)
-  TB_CUDA(h, cudaMemsetAsync(h->field[0], 0, fbytes, st));
-  TB_CUDA(h, cudaMemsetAsync(h->field[1], 0, fbytes, st));
+  TB_CUDA(h, cudaMemsetAsync(fld[0], 0, fbytes, st));
+  TB_CUDA(h, cudaMemsetAsync(fld[1], 0, fbytes, st));
   TB_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(int), st));
+  if (h->sk) {
+    // per-step scales: scales[k] of u^{k-1} (u^{-1}, u^0 zero: 1), running max
+    if ((s = ensure_scales(h, nt, st)) != TB_OK) return s;
+    h->lp_cur = 0;
+  }
   if (h->opt.profile) ev_reset(h, st);
 
   SweepParams P{};
@@ -1157,14 +1189,21 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
     rec_fill = 0;
     return TB_OK;
   };
+  P.lp_scales = h->lp_scales;
+  P.lp_mx = h->lp_mx;
   auto run = [&](int TT, const Plan& pl, int pass_off, int out0, int out1, int step0) -> int {
-    P.u_cur = h->field[cur];
-    P.u_prev = h->field[prev];
+    if (h->sk) {  // the scale of u^{n+1}, from max |u^n| and the step's largest injection
+      cudaError_t e = lowprec_scale(h->lp_scales, h->lp_mx, (h->have_src && h->src.npts > 0) ? h->lp_srcmax : nullptr,
+                                    step0, st);
+      if (e != cudaSuccess) return cuda_fail(h, e, "scale");
+    }
+    P.u_cur = fld[cur];
+    P.u_prev = fld[prev];
     P.tm_u = h->tm_box[cur];
     P.tm_p = h->tm_tile[prev];
     P.tm_c = h->tm_c2;
-    P.out0 = h->field[out0];
-    P.out1 = out1 >= 0 ? h->field[out1] : nullptr;
+    P.out0 = fld[out0];
+    P.out1 = out1 >= 0 ? fld[out1] : nullptr;
     P.step0 = step0;
     P.rec_base = rec_base;
     for (size_t L = 0; L < pl.launch_first.size(); ++L) {
@@ -1186,7 +1225,7 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
         h->ev_kind.push_back(0);
         if (a) cudaEventRecord(a, st);
       }
-      cudaError_t e = sweep_launch(h->R, TT, P, pl.launch_ctas[L], TT > 1, st);
+      cudaError_t e = sweep_launch(h->R, TT, P, pl.launch_ctas[L], TT > 1, st, TT == 1 ? h->sk : 0);
       if (h->opt.profile && b) cudaEventRecord(b, st);
       if (e != cudaSuccess) return cuda_fail(h, e, TT > 1 ? "blocked sweep launch" : "one-step launch");
     }
@@ -1217,6 +1256,7 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   if ((s = flush_receivers()) != TB_OK) return s;
   h->cur_idx = cur;
   h->prev_idx = prev;
+  if (h->sk) h->lp_cur = cur;
   h->last_nt = nt;
 
   if (T > 1) {

@@ -66,6 +66,10 @@ struct SweepParams {
   long long timeout_ns;
   const PassDesc* pass;         // device copy of the pass table
   int npass;
+  // 16-bit storage (one-step kernel): scales[n] of u^{n-1} (stored = u / s),
+  // running max |u| per step (float bits)
+  const float* lp_scales;
+  unsigned* lp_mx;
 };
 
 struct SweepShape {
@@ -78,10 +82,12 @@ struct SweepShape {
 };
 
 // Kernel configuration and launch (tb_acoustic*.cu).
-bool sweep_shape(int R, int T, SweepShape* s);
-cudaError_t sweep_max_ctas(int R, int T, int* per_sm);
+// sk: wavefield storage of the sweep (0 FP32; 1 FP16, 2 BF16 with per-step
+// power-of-two scales, one-step kernel only)
+bool sweep_shape(int R, int T, SweepShape* s, int sk = 0);
+cudaError_t sweep_max_ctas(int R, int T, int* per_sm, int sk = 0);
 cudaError_t sweep_launch(int R, int T, const SweepParams& p, int nctas, bool cooperative,
-                         cudaStream_t st);
+                         cudaStream_t st, int sk = 0);
 
 // Inspector and setup kernels (tb_inspector.cu).
 struct PointTables {
@@ -154,6 +160,8 @@ inline void dfree(void* p, cudaStream_t st) {
 
 // 16-bit (or plain FP32) storage one-step path (tb_lowprec.cu); storage: 1 FP16,
 // 2 BF16, 3 FP32.  scales[k] / mx[k]: scale and max |u| of u^{k-1}.
+// scales[n + 2] (of u^{n+1}) from max |u^n| and the step's largest injection
+cudaError_t lowprec_scale(float* scales, const unsigned* mx, const float* srcmax, int n, cudaStream_t st);
 cudaError_t lowprec_step(int storage, int R, const PhysGrid& g, const LapW& w, int nchunks, const void* uc, void* up,
                          const float* c2, const float* damp_b, const float* scales, const float* srcmax, int n,
                          unsigned* mx, cudaStream_t st);

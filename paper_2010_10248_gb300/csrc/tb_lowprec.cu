@@ -186,6 +186,12 @@ static cudaError_t lp_step_st(int R, const PhysGrid& g, const LapW& w, int nchun
   return cudaErrorInvalidValue;
 }
 
+cudaError_t lowprec_scale(float* scales, const unsigned* mx, const float* srcmax, int n, cudaStream_t st) {
+  count_launch();
+  k_lp_scale<<<1, 1, 0, st>>>(scales, mx, srcmax, n);
+  return cudaGetLastError();
+}
+
 cudaError_t lowprec_step(int storage, int R, const PhysGrid& g, const LapW& w, int nchunks, const void* uc, void* up,
                          const float* c2, const float* damp_b, const float* scales, const float* srcmax, int n,
                          unsigned* mx, cudaStream_t st) {

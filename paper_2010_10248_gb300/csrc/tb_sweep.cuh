@@ -63,15 +63,50 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "tb_internal.cuh"
 
 namespace tbi {
 
+// Wavefield storage of a sweep: SK = 0 FP32; SK = 1 FP16, SK = 2 BF16 (one-
+// step kernel only), where a stored field holds u / s with a power-of-two
+// scale s per field and step.  Arithmetic is FP32 in every case.
+template <int SK> struct StoreT { using type = float; };
+template <> struct StoreT<1> { using type = __half; };
+template <> struct StoreT<2> { using type = __nv_bfloat16; };
+// a column pair (two adjacent values) as FP32, and back with rounding to nearest
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float2 ld2(const __half* p) { return __half22float2(*reinterpret_cast<const __half2*>(p)); }
+__device__ __forceinline__ float2 ld2(const __nv_bfloat16* p) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+}
+__device__ __forceinline__ void st2cs(float* p, float2 v) { __stcs(reinterpret_cast<float2*>(p), v); }
+__device__ __forceinline__ void st2cs(__half* p, float2 v) {
+  const __half2 hv = __float22half2_rn(v);
+  __stcs(reinterpret_cast<unsigned*>(p), *reinterpret_cast<const unsigned*>(&hv));
+}
+__device__ __forceinline__ void st2cs(__nv_bfloat16* p, float2 v) {
+  const __nv_bfloat162 hv = __float22bfloat162_rn(v);
+  __stcs(reinterpret_cast<unsigned*>(p), *reinterpret_cast<const unsigned*>(&hv));
+}
+// one value from global memory through L2
+__device__ __forceinline__ float ld1cg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ float ld1cg(const __half* p) {
+  return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short*>(p))));
+}
+__device__ __forceinline__ float ld1cg(const __nv_bfloat16* p) {
+  return __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short*>(p))));
+}
+
 constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
 
-template <int R, int T, int TY>
+template <int R, int T, int TY, int SK = 0>
 struct SweepCfg {
+  using ST = typename StoreT<SK>::type;
+  static constexpr int ESZ = (int)sizeof(ST);  // bytes of a stored wavefield value
+  static_assert(SK == 0 || T == 1, "16-bit storage: one-step kernel only");
   static constexpr int TZ = 64;
   static constexpr int NT = 32 * TY;           // compute threads
   static constexpr bool HALO = T > 1;          // halo and publisher warps present
@@ -79,11 +114,13 @@ struct SweepCfg {
   static constexpr int NTHREADS = NT + 64 + (HALO ? 64 : 0);
   static constexpr int WREC = TY + 1;                    // receiver warp
   static constexpr int WHALO = TY + 2, WPUB = TY + 3;    // halo, publisher warps (T > 1)
-  static constexpr int RP = (R + 3) / 4 * 4;   // axis-2 halo width in shared memory
+  // axis-2 halo width in shared memory; with 16-bit values 8 keeps the TMA
+  // box's first column z0 - RP on a 16-byte boundary
+  static constexpr int RP = SK ? 8 : (R + 3) / 4 * 4;
   static constexpr int SW = TZ + 2 * RP;       // plane row stride (floats)
   static constexpr int SH = TY + 2 * R;
   static constexpr int PLANE = SW * SH;
-  static constexpr int PSLOT = (int)(align128(PLANE * 4) / 4);
+  static constexpr int PSLOT = (int)(align128(PLANE * ESZ) / ESZ);
   static constexpr int TILE = TY * TZ;
   static constexpr int Q = 2 * R + 1;                // queue length
   static constexpr int PF = 2;                       // planes of prefetch beyond need
@@ -112,8 +149,8 @@ struct SweepCfg {
   static constexpr int NSP = T > 1 ? 2 * (T - 1) : 0;  // fused-step planes
   static constexpr int CTR_COUNT = NT + (HALO ? 2 : 0);   // arrivals per centre phase: + halo, receiver
   static constexpr size_t OFF_U = 0;
-  static constexpr size_t OFF_P = OFF_U + align128((size_t)NU * PSLOT * 4);
-  static constexpr size_t OFF_C = OFF_P + align128((size_t)NP * TILE * 4);
+  static constexpr size_t OFF_P = OFF_U + align128((size_t)NU * PSLOT * ESZ);
+  static constexpr size_t OFF_C = OFF_P + align128((size_t)NP * TILE * ESZ);
   static constexpr size_t OFF_S = OFF_C + align128((size_t)NC * TILE * 4);
   static constexpr size_t OFF_BASE = OFF_S + align128((size_t)NSP * PSLOT * 4);
   static constexpr size_t OFF_CNT = OFF_BASE + 4 * 2 * NT;
@@ -280,16 +317,17 @@ __device__ __forceinline__ float2 pair_term2(float2 acc, float2 w2, float2 a, fl
 }
 
 // ----------------------------------------------------------------- kernel --
-template <int R, int T, int TY>
-__global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
+template <int R, int T, int TY, int SK = 0>
+__global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 : 1)
     sweep_kernel(const __grid_constant__ SweepParams P) {
-  using C = SweepCfg<R, T, TY>;
+  using C = SweepCfg<R, T, TY, SK>;
+  using ST = typename C::ST;
   constexpr int TZ = C::TZ, NT = C::NT, SW = C::SW, RP = C::RP;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // TMA destinations need 128-byte alignment: align the base explicitly
   unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  float* uring = reinterpret_cast<float*>(smem + C::OFF_U);
-  float* pring = reinterpret_cast<float*>(smem + C::OFF_P);
+  ST* uring = reinterpret_cast<ST*>(smem + C::OFF_U);
+  ST* pring = reinterpret_cast<ST*>(smem + C::OFF_P);
   float* cring = reinterpret_cast<float*>(smem + C::OFF_C);
   float* splane = reinterpret_cast<float*>(smem + C::OFF_S);
   uint64_t* bar_pro = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);  // u^n planes before the first step
@@ -343,13 +381,13 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
     // u^n planes pu0 .. jstart+R-1, needed before the first step
     {
       const int np = jstart + R - pu0;
-      mbar_expect_tx(bar_pro, (unsigned)(np * C::PLANE * 4));
+      mbar_expect_tx(bar_pro, (unsigned)(np * C::PLANE * C::ESZ));
       for (int p = pu0; p < jstart + R; ++p) tma_load_3d(u_slot(p), &P.tm_u, bar_pro, z0 - RP, y0 - R, p);
     }
     // the data of stream step s: u^n plane s+R, u^{n-1} and c2 plane s
     auto issue = [&](int s) {
       uint64_t* bar = bar_dat + (s - jstart) % C::ND;
-      mbar_expect_tx(bar, (unsigned)((C::PLANE + 2 * C::TILE) * 4));
+      mbar_expect_tx(bar, (unsigned)((C::PLANE + C::TILE) * C::ESZ + C::TILE * 4));
       tma_load_3d(u_slot(s + R), &P.tm_u, bar, z0 - RP, y0 - R, s + R);
       tma_load_3d(pring + ((s - jstart) % C::NP) * C::TILE, &P.tm_p, bar, z0, y0, s);
       tma_load_3d(cring + ((s - jstart) % C::NC) * C::TILE, &P.tm_c, bar, z0, y0, s);
@@ -439,8 +477,11 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
         }
         if (pos >= 0) {
           const int ww = t >> 5, ln = t & 31;
-          rrow[pos] = plane ? plane[(R + ww) * SW + RP + 2 * ln + ci]
-                            : __ldcg(P.out0 + (size_t)q * ps + (size_t)(y0 + ww) * P.n2p + z0 + 2 * ln + ci);
+          const size_t go = (size_t)q * ps + (size_t)(y0 + ww) * P.n2p + z0 + 2 * ln + ci;
+          if constexpr (SK != 0)  // one-step only: u^{n+1} is stored as u / s
+            rrow[pos] = __fmul_rn(ld1cg(reinterpret_cast<const ST*>(P.out0) + go), __ldg(P.lp_scales + P.step0 + 2));
+          else
+            rrow[pos] = plane ? plane[(R + ww) * SW + RP + 2 * ln + ci] : __ldcg(P.out0 + go);
         }
       }
     };
@@ -674,7 +715,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
     for (int s = 0; s < C::Q; ++s) {
       const int plane = jstart - 1 - R + s;
       if (v0 && plane >= 0 && plane < P.n0) {
-        Q0[s] = __ldg(reinterpret_cast<const float2*>(P.u_cur + (size_t)plane * ps + coff));
+        Q0[s] = ld2(reinterpret_cast<const ST*>(P.u_cur) + (size_t)plane * ps + coff);
         if (!v1) Q0[s].y = 0.f;
       }
     }
@@ -686,6 +727,18 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
   {
     const int q = jstart - kl * R;
     bxn = __ldg(&P.damp_b[min(max(q, 0), P.n0 - 1)]);
+  }
+
+  // 16-bit storage: scales of u^{n-1}, u^n and u^{n+1} (powers of two, set
+  // by the step's scale kernel) and the running max |u^{n+1}| of this thread
+  float2 sc2 = make_float2(1.f, 1.f), sp2 = sc2, io2 = sc2;
+  float vmax = 0.f;
+  if constexpr (SK != 0) {
+    const float a = __ldg(P.lp_scales + P.step0 + 1), p = __ldg(P.lp_scales + P.step0),
+                o = 1.f / __ldg(P.lp_scales + P.step0 + 2);
+    sc2 = make_float2(a, a);
+    sp2 = make_float2(p, p);
+    io2 = make_float2(o, o);
   }
 
   bool ok = mbar_wait(bar_pro, 0, tmo);  // u^n planes pu0 .. jstart+R-1
@@ -722,22 +775,22 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
     if (!ok) break;
 
     // ---- fused step 0
-    const float* ub = uring + su * C::PSLOT;
+    const ST* ub = uring + su * C::PSLOT;
     if constexpr (C::X0Q) {
-      const float2 nq = *reinterpret_cast<const float2*>(uring + suR * C::PSLOT + own);
+      const float2 nq = ld2(uring + suR * C::PSLOT + own);
 #pragma unroll
       for (int s = 0; s < C::Q - 1; ++s) Q0[s] = Q0[s + 1];
       Q0[C::Q - 1] = nq;
     }
     float2 un0 = make_float2(0.f, 0.f);
     if (act0) {
-      const float2 uc0 = C::X0Q ? Q0[R] : *reinterpret_cast<const float2*>(ub + own);
-      const float2 up = *reinterpret_cast<const float2*>(pring + sp * C::TILE + own_t);
+      const float2 uc0 = C::X0Q ? Q0[R] : ld2(ub + own);
+      const float2 up = ld2(pring + sp * C::TILE + own_t);
       const float2 c2v = *reinterpret_cast<const float2*>(cring + sc * C::TILE + own_t);
       float2 zp[R + 1];
 #pragma unroll
       for (int m = 0; m <= R; ++m)
-        zp[m] = (m == R / 2) ? uc0 : *reinterpret_cast<const float2*>(&ub[own - R + 2 * m]);
+        zp[m] = (m == R / 2) ? uc0 : ld2(&ub[own - R + 2 * m]);
       float2 lx = make_float2(0.f, 0.f), ly = lx, lz = lx;
 #pragma unroll
       for (int d = 1; d <= R; ++d) {
@@ -749,11 +802,11 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
           int sf = su + d, sb = su - d;
           sf -= sf >= C::NU ? C::NU : 0;
           sb += sb < 0 ? C::NU : 0;
-          xp = *reinterpret_cast<const float2*>(uring + sf * C::PSLOT + own);
-          xm = *reinterpret_cast<const float2*>(uring + sb * C::PSLOT + own);
+          xp = ld2(uring + sf * C::PSLOT + own);
+          xm = ld2(uring + sb * C::PSLOT + own);
         }
-        const float2 yp = *reinterpret_cast<const float2*>(&ub[own + d * SW]);
-        const float2 ym = *reinterpret_cast<const float2*>(&ub[own - d * SW]);
+        const float2 yp = ld2(&ub[own + d * SW]);
+        const float2 ym = ld2(&ub[own - d * SW]);
         float2 zpl, zmi;
         if (d % 2 == 0) {
           zpl = zp[R / 2 + d / 2];
@@ -768,13 +821,23 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
       }
       const float2 lap = __fadd2_rn(__fadd2_rn(lx, ly), lz);
       const float bx = __shfl_sync(0xffffffffu, bxc, 0);
-      un0 = point_update2(uc0, up, lap, c2v, __fadd2_rn(make_float2(bx, bx), byz));
+      if constexpr (SK != 0)  // stored values are u / s: scale back (exact, s a power of two)
+        un0 = point_update2(__fmul2_rn(uc0, sc2), __fmul2_rn(up, sp2), __fmul2_rn(lap, sc2), c2v,
+                            __fadd2_rn(make_float2(bx, bx), byz));
+      else
+        un0 = point_update2(uc0, up, lap, c2v, __fadd2_rn(make_float2(bx, bx), byz));
       inject(0, j, un0);
     }
 
     if constexpr (T == 1) {
-      if (act0 && own_row && j >= pd.xo0 && j < pd.xo1 && v0)
-        __stcs(reinterpret_cast<float2*>(P.out0 + (size_t)j * ps + coff), un0);
+      if (act0 && own_row && j >= pd.xo0 && j < pd.xo1 && v0) {
+        if constexpr (SK != 0) {
+          vmax = fmaxf(vmax, fmaxf(fabsf(un0.x), v1 ? fabsf(un0.y) : 0.f));
+          st2cs(reinterpret_cast<ST*>(P.out0) + (size_t)j * ps + coff, __fmul2_rn(un0, io2));
+        } else {
+          __stcs(reinterpret_cast<float2*>(P.out0 + (size_t)j * ps + coff), un0);
+        }
+      }
     } else {
       float* rs_base = P.ring + (size_t)b * (T - 1) * C::D * C::STRIP;
       const float* rdbuf = splane + (size_t)(j & 1) * (T - 1) * C::PSLOT;
@@ -794,7 +857,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
             if (k == 1) {
               int sq = su - R;
               sq += sq < 0 ? C::NU : 0;
-              upv = *reinterpret_cast<const float2*>(uring + sq * C::PSLOT + own);
+              upv = ld2(uring + sq * C::PSLOT + own);
             } else {
               upv = Qs[k >= 2 ? k - 2 : 0][0];
             }
@@ -861,20 +924,25 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY>::NTHREADS, T == 1 ? 2 : 1)
     sc = sc + 1 == C::NC ? 0 : sc + 1;
     jd = jd + 1 == C::D ? 0 : jd + 1;
   }
+  if constexpr (SK != 0) {  // max |u^{n+1}| over the grid, for the next step's scale
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if (lane == 0 && vmax > 0.f) atomicMax(P.lp_mx + P.step0 + 2, __float_as_uint(vmax));
+  }
   if (!ok) atomicExch(P.err, 2);
 }
 
-template <int R, int T>
+template <int R, int T, int SK = 0>
 struct SweepTraits {
   static constexpr int TY = 16;
-  using Cfg = SweepCfg<R, T, TY>;
+  using Cfg = SweepCfg<R, T, TY, SK>;
 };
 
-template <int R, int T>
+template <int R, int T, int SK>
 cudaError_t sweep_launch_t(const SweepParams& p, int nctas, bool cooperative, cudaStream_t st) {
-  using Tr = SweepTraits<R, T>;
+  using Tr = SweepTraits<R, T, SK>;
   using Cf = typename Tr::Cfg;
-  auto fn = sweep_kernel<R, T, Tr::TY>;
+  auto fn = sweep_kernel<R, T, Tr::TY, SK>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
@@ -890,19 +958,19 @@ cudaError_t sweep_launch_t(const SweepParams& p, int nctas, bool cooperative, cu
   return cudaGetLastError();
 }
 
-template <int R, int T>
+template <int R, int T, int SK>
 cudaError_t sweep_occupancy_t(int* per_sm) {
-  using Tr = SweepTraits<R, T>;
+  using Tr = SweepTraits<R, T, SK>;
   using Cf = typename Tr::Cfg;
-  auto fn = sweep_kernel<R, T, Tr::TY>;
+  auto fn = sweep_kernel<R, T, Tr::TY, SK>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, Cf::NTHREADS, Cf::SMEM);
 }
 
-template <int R, int T>
+template <int R, int T, int SK>
 void sweep_shape_t(SweepShape* s) {
-  using Tr = SweepTraits<R, T>;
+  using Tr = SweepTraits<R, T, SK>;
   using Cf = typename Tr::Cfg;
   s->R = R;
   s->T = T;
@@ -915,12 +983,30 @@ void sweep_shape_t(SweepShape* s) {
   s->halo_w = Cf::RP;
 }
 
+// what: 0 launch, 1 occupancy query, 2 shape query; sk: storage kind (16-bit
+// storage only in the one-step kernel)
+template <int R, int T, int SK>
+cudaError_t sweep_do(int what, const SweepParams* p, int nctas, bool coop, cudaStream_t st, int* per_sm,
+                     SweepShape* s) {
+  if (what == 0) return sweep_launch_t<R, T, SK>(*p, nctas, coop, st);
+  if (what == 1) return sweep_occupancy_t<R, T, SK>(per_sm);
+  sweep_shape_t<R, T, SK>(s);
+  return cudaSuccess;
+}
+template <int R, int T>
+cudaError_t sweep_do_sk(int what, int sk, const SweepParams* p, int nctas, bool coop, cudaStream_t st,
+                        int* per_sm, SweepShape* s) {
+  if constexpr (T == 1) {
+    if (sk == 1) return sweep_do<R, 1, 1>(what, p, nctas, coop, st, per_sm, s);
+    if (sk == 2) return sweep_do<R, 1, 2>(what, p, nctas, coop, st, per_sm, s);
+  }
+  if (sk != 0) return cudaErrorInvalidValue;
+  return sweep_do<R, T, 0>(what, p, nctas, coop, st, per_sm, s);
+}
+
 // Per-radius entry points (one translation unit per radius), T = 1..TMAX.
-#define TBI_DEFINE_RADIUS_T(RR, TT)                                                \
-  case TT:                                                                         \
-    if (what == 0) return sweep_launch_t<RR, TT>(*p, nctas, coop, st);             \
-    if (what == 1) return sweep_occupancy_t<RR, TT>(per_sm);                       \
-    sweep_shape_t<RR, TT>(s);                                                      \
-    return cudaSuccess;
+#define TBI_DEFINE_RADIUS_T(RR, TT) \
+  case TT:                          \
+    return sweep_do_sk<RR, TT>(what, sk, p, nctas, coop, st, per_sm, s);
 
 }  // namespace tbi

@@ -3,7 +3,7 @@
 
 namespace tbi {
 // what: 0 launch, 1 occupancy query, 2 shape query
-cudaError_t sweep_dispatch_r2(int what, int T, const SweepParams* p, int nctas, bool coop,
+cudaError_t sweep_dispatch_r2(int what, int T, int sk, const SweepParams* p, int nctas, bool coop,
                                cudaStream_t st, int* per_sm, SweepShape* s) {
   switch (T) {
     TBI_DEFINE_RADIUS_T(2, 1)

@@ -59,3 +59,28 @@ def test_storage_error_against_oracle(tb, case, storage):
     assert e_tr <= LIMITS[storage] and e_u <= LIMITS[storage]
     with pytest.raises(tb.TBError):
         p.forward(4, schedule="blocked")
+
+
+@pytest.mark.parametrize("storage", ["TB_F16", "TB_BF16"])
+def test_storage_ragged_grid(tb, storage):
+    """A ragged grid (odd axis 2: an unpaired last column, rows padded to 8
+    values) with sources on a node, at the upper corner and sharing corners."""
+    import torch
+    shape, h = (37, 45, 83), (10.0, 11.0, 9.0)
+    vp = wl.layered_vp(shape, 17, nlayers=5, nblobs=4)
+    src = np.array([[171.3, 240.9, 371.4], [200.0, 220.0, 360.0], [360.0, 484.0, 738.0], [175.0, 237.0, 369.0]])
+    rec = np.concatenate([wl.receiver_line(shape, h, 5, 20), np.array([[0.0, 0.0, 0.0], [360.0, 484.0, 738.0]])])
+    nt, nbl = 80, 5
+    dt = 0.8 * oracle.cfl_dt_max(8, h, float(vp.max()))
+    wav = np.repeat(wl.ricker(55.0, dt, nt)[None, :], len(src), axis=0)
+    tr_o, u_o, _ = oracle.acoustic_forward(shape, h, 8, dt, nt, vp.astype(np.float64), nbl=nbl, src_xyz=src,
+                                           src_wav=wav, rec_xyz=rec)
+    p = tb.Propagator(shape, h, 8, nbl=nbl, storage=getattr(tb, storage))
+    p.set_model(torch.from_numpy(vp).cuda(), dt=dt)
+    p.set_sources(src, wav.astype(np.float32))
+    p.set_receivers(rec)
+    tr = p.forward(nt).cpu().numpy()
+    u = p.field(0).cpu().numpy()
+    e_tr, e_u = rel_l2(tr, tr_o), rel_l2(u, u_o)
+    print(f"{storage} ragged: traces rel-L2 {e_tr:.2e}, field rel-L2 {e_u:.2e}")
+    assert e_tr <= LIMITS[storage] and e_u <= LIMITS[storage]

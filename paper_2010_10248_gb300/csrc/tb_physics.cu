@@ -23,6 +23,7 @@
 // axis-1 and axis-2 neighbours come through the L1 cache.  Source injection
 // (grid-aligned table of Sec. II-A) and receiver sampling are separate small
 // kernels after the update of each step.
+#include <cstddef>
 #include <cstdint>
 
 #include "tb_internal.cuh"
@@ -62,18 +63,28 @@ __device__ __forceinline__ float div_sponge(float n, float den) { return den == 
 
 // ------------------------------------------------------------------ TTI --
 // centred first derivative along axis 1 / 2 at (x, y, z): sum_i a_i (f_{+i} - f_{-i})
+// Neighbours of a point inside the grid along one axis: only that axis'
+// coordinate can leave the grid, so only it is tested.
+__device__ __forceinline__ float ld_y(const PhysGrid& g, const float* __restrict__ f, size_t i0, int y, int dy) {
+  return (unsigned)(y + dy) < (unsigned)g.n1 ? __ldg(f + (ptrdiff_t)i0 + (ptrdiff_t)dy * g.n2p) : 0.f;
+}
+__device__ __forceinline__ float ld_z(const PhysGrid& g, const float* __restrict__ f, size_t i0, int z, int dz) {
+  return (unsigned)(z + dz) < (unsigned)g.n2 ? __ldg(f + (ptrdiff_t)i0 + dz) : 0.f;
+}
 template <int R>
 __device__ __forceinline__ float dc_y(const PhysGrid& g, const float* f, const float* a, int x, int y, int z) {
+  const size_t i0 = pidx(g, x, y, z);
   float s = 0.f;
 #pragma unroll
-  for (int i = R; i >= 1; --i) s = __fmaf_rn(a[i - 1], __fsub_rn(ld0(g, f, x, y + i, z), ld0(g, f, x, y - i, z)), s);
+  for (int i = R; i >= 1; --i) s = __fmaf_rn(a[i - 1], __fsub_rn(ld_y(g, f, i0, y, i), ld_y(g, f, i0, y, -i)), s);
   return s;
 }
 template <int R>
 __device__ __forceinline__ float dc_z(const PhysGrid& g, const float* f, const float* a, int x, int y, int z) {
+  const size_t i0 = pidx(g, x, y, z);
   float s = 0.f;
 #pragma unroll
-  for (int i = R; i >= 1; --i) s = __fmaf_rn(a[i - 1], __fsub_rn(ld0(g, f, x, y, z + i), ld0(g, f, x, y, z - i)), s);
+  for (int i = R; i >= 1; --i) s = __fmaf_rn(a[i - 1], __fsub_rn(ld_z(g, f, i0, z, i), ld_z(g, f, i0, z, -i)), s);
   return s;
 }
 template <int R>
@@ -182,8 +193,9 @@ __device__ __forceinline__ float dstag(const PhysGrid& g, const float* f, const 
 #pragma unroll
   for (int k = R; k >= 1; --k) {
     const int hi = plus ? k : k - 1, lo = plus ? -(k - 1) : -k;
-    const float a = D == 0 ? ld0(g, f, x + hi, y, z) : (D == 1 ? ld0(g, f, x, y + hi, z) : ld0(g, f, x, y, z + hi));
-    const float b = D == 0 ? ld0(g, f, x + lo, y, z) : (D == 1 ? ld0(g, f, x, y + lo, z) : ld0(g, f, x, y, z + lo));
+    const size_t i0 = pidx(g, x, y, z);
+    const float a = D == 0 ? ld0(g, f, x + hi, y, z) : (D == 1 ? ld_y(g, f, i0, y, hi) : ld_z(g, f, i0, z, hi));
+    const float b = D == 0 ? ld0(g, f, x + lo, y, z) : (D == 1 ? ld_y(g, f, i0, y, lo) : ld_z(g, f, i0, z, lo));
     s = __fmaf_rn(cw[k - 1], __fsub_rn(a, b), s);
   }
   return s;
@@ -207,7 +219,7 @@ __device__ __forceinline__ float dstag_q(const float* q, const float* cw, bool p
 // neighbours of the three fields it differentiates along axis 0 sit in
 // register queues of planes x-R .. x+R.
 template <int R>
-__global__ void __launch_bounds__(256) k_ela_velocity(PhysGrid g, DerivW w, float dt, int nchunks, float* __restrict__ f,
+__global__ void __launch_bounds__(256, 4) k_ela_velocity(PhysGrid g, DerivW w, float dt, int nchunks, float* __restrict__ f,
                                                       const float* __restrict__ mat, const float* __restrict__ eta_dt) {
   const Col c = thread_col(g);
   if (!c.ok) return;
@@ -249,7 +261,7 @@ __global__ void __launch_bounds__(256) k_ela_velocity(PhysGrid g, DerivW w, floa
 }
 
 template <int R>
-__global__ void __launch_bounds__(256) k_ela_stress(PhysGrid g, DerivW w, float dt, int nchunks, float* __restrict__ f,
+__global__ void __launch_bounds__(256, 4) k_ela_stress(PhysGrid g, DerivW w, float dt, int nchunks, float* __restrict__ f,
                                                     const float* __restrict__ mat, const float* __restrict__ eta_dt) {
   const Col c = thread_col(g);
   if (!c.ok) return;

@@ -88,7 +88,8 @@ typedef struct tb_handle tb_handle;
 typedef struct {
   int time_tile;   /* T: time steps fused per blocked sweep (Sec. II-B).
                       Supported: 1..4 (space order 4, 8), 1..2 (space order 12);
-                      0 -> the largest supported.  TB_TTI, TB_ELASTIC: 0 or 1.  */
+                      0 -> the fastest measured on GB300 at 512^3: 4 (space
+                      order 4), 3 (8), 2 (12).  TB_TTI, TB_ELASTIC: 0 or 1.  */
   int nbl;         /* width in cells of the built-in sponge (Sec. IV-B); 0: none  */
   int y_bands;     /* blocked sweep: number of bands along axis 1; 0 -> fewest
                       bands whose tiles are co-resident on the GPU                */

@@ -402,7 +402,10 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   }
   // more fused so12 steps exceed shared memory; TTI and elastic run one step per launch
   const int tmax = (physics != TB_ACOUSTIC || h->storage != TB_F32) ? 1 : (so == 12 ? 2 : 4);
-  if (h->opt.time_tile == 0) h->opt.time_tile = tmax;
+  // default: the fused depth measured fastest at 512^3 (so8: T = 3 computes
+  // each level faster than T = 4, whose three register queues crowd the
+  // registers)
+  if (h->opt.time_tile == 0) h->opt.time_tile = (tmax > 1 && so == 8) ? 3 : tmax;
   if (h->opt.time_tile < 1 || h->opt.time_tile > tmax || h->opt.nbl < 0 || h->opt.y_bands < 0 ||
       h->opt.x_chunks < 0) {
     delete h;

@@ -38,7 +38,7 @@ class ShotRequest:
     rec_xyz: np.ndarray     # [nrec, 3] float64 metres
     nt: int
     nbl: int = 0
-    time_tile: int = 0      # 0: blocked sweep with the largest tile; 1: one-step
+    time_tile: int = 0      # 0: blocked sweep with the default tile; 1: one-step
     arrival: float = 0.0    # seconds after the start of the run
     tag: object = None
 

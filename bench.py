@@ -201,6 +201,38 @@ def cpu_oracle_rate(w, dt, steps_a, steps_b):
     return N * (steps_b - steps_a) / dtime / 1e9, t[0] + t[1], threads
 
 
+def cpu_oracle_rate_physics(physics, mk, size, steps_a, steps_b):
+    """GPts/s of the FP64 TTI or elastic oracle on the host, on the same
+    recipe at a reduced cube edge (difference of two runs); returns (rate,
+    seconds, threads, sample description)."""
+    import oracle
+    oracle.build()
+    w = mk(shape=(size,) * 3, nt=steps_b)
+    aux = [a.astype(np.float64) for a in w.meta["aux"]]
+    vp64 = w.vp.astype(np.float64)
+    if physics == "tti":
+        dt = 0.8 * oracle.tti_dt_max(w.so, w.spacing, float(w.vp.max()), float(aux[0].max()))
+    else:
+        dt = 0.8 * oracle.elastic_dt_max(w.so, w.spacing, float(w.vp.max()))
+    wav = w.wavelets(dt)
+    t = []
+    for s in (steps_a, steps_b):
+        t0 = time.perf_counter()
+        if physics == "tti":
+            oracle.tti_forward(w.shape, w.spacing, w.so, dt, s, vp64, *aux, nbl=w.nbl, src_xyz=w.src_xyz,
+                               src_wav=wav[:, :s], rec_xyz=w.rec_xyz)
+        else:
+            oracle.elastic_forward(w.shape, w.spacing, w.so, dt, s, vp64, *aux, nbl=w.nbl, src_xyz=w.src_xyz,
+                                   src_wav=wav[:, :s], rec_xyz=w.rec_xyz)
+        t.append(time.perf_counter() - t0)
+    dtime = max(t[1] - t[0], 1e-9)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    N = size ** 3
+    sample = (f"{physics} {size}^3 so{w.so}, {steps_b - steps_a} steps (difference of a {steps_a}- and a "
+              f"{steps_b}-step FP64 oracle run, {t[0] + t[1]:.1f} s total)")
+    return N * (steps_b - steps_a) / dtime / 1e9, t[0] + t[1], threads, sample
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -478,6 +510,14 @@ def run_physics(args):
     step_ms = kms / max(kn, 1)
     achieved = alg_bytes * N / (step_ms * 1e-3) / 1e9
     finite = bool(torch.isfinite(traces).all().item())
+    cpu = None
+    if not args.no_cpu:
+        try:
+            mk = wl.tti_384_so8 if args.physics == "tti" else wl.elastic_384_so8
+            rate, secs, threads, sample = cpu_oracle_rate_physics(args.physics, mk, 256, 2, 22)
+            cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+        except Exception as e:  # the baseline is reported, not required
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -490,7 +530,7 @@ def run_physics(args):
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                          "kernel": f"{args.physics} step (all kernels of one time step)",
                          "bytes_per_point_step": alg_bytes, "kernel_ms_per_step": step_ms},
-            "traces_finite": finite}
+            "cpu_baseline": cpu, "traces_finite": finite}
     print(json.dumps(line), flush=True)
     prop.close()
 
@@ -565,8 +605,9 @@ def run_serving(args):
 
 
 def run_storage(args):
-    """The acoustic benchmark shot with 16-bit (or plain FP32) wavefield
-    storage: one-step streaming kernel, FP32 arithmetic."""
+    """The acoustic benchmark shot with 16-bit wavefield storage (the one-step
+    sweep) or scaled plain-FP32 storage (the streaming kernel), FP32
+    arithmetic."""
     import torch
     import paper_2010_10248_gb300 as tb
     from paper_2010_10248_gb300 import build as tbbuild
@@ -616,6 +657,15 @@ def run_storage(args):
     bpp = 4.0 + (3 * 2.0 if stor != tb.TB_F32_PLAIN else 3 * 4.0)  # c2 + u^n, u^{n-1}, u^{n+1}
     peak, peak_kind = measured_peaks()
     achieved = bpp * N / (step_ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu:
+        try:
+            rate, secs, threads = cpu_oracle_rate(w, dt, 2, 2 + args.cpu_steps)
+            cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                   "sample": f"{w.shape[0]}^3 so8, {args.cpu_steps} steps (difference of a 2- "
+                             f"and a {2 + args.cpu_steps}-step FP64 oracle run, {secs:.1f} s total)"}
+        except Exception as e:  # the baseline is reported, not required
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
     line = {"metric": METRIC, "value": N * nt / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {"f16": "f16-storage/f32-math",
@@ -623,12 +673,14 @@ def run_storage(args):
                                                               "plain": "f32"}[args.storage],
             "data": "synthetic",
             "config": {"workload": w.name, "grid": list(w.shape), "space_order": w.so, "nt": nt,
-                       "schedule": "onestep (streaming kernel)", "storage": args.storage,
+                       "schedule": "onestep (" + ("streaming kernel" if args.storage == "plain" else "TMA sweep") + ")",
+                       "storage": args.storage,
                        "step": "set_model + set_sources + set_receivers + forward(nt)"},
             "gpu_launches": int(tb.tb_launch_count() - l0), "clocks": clk,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                         "bytes_per_point_step": bpp, "kernel_ms_per_step": step_ms}}
+                         "bytes_per_point_step": bpp, "kernel_ms_per_step": step_ms},
+            "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     prop.close()
 

@@ -54,6 +54,8 @@ def parse():
                     help="f16 / bf16 / plain: the 512^3 acoustic shot with 16-bit (or plain FP32) wavefield "
                          "storage in the streaming one-step kernel")
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--adjoint", action="store_true",
+                    help="vp gradient of the 256^3 so8 shot (800 steps, 32 checkpoints) instead")
     ap.add_argument("--physics", default="acoustic", choices=["acoustic", "tti", "elastic"],
                     help="tti / elastic: the 384^3 so8 500-step TTI or elastic workload, one-step "
                          "schedule (the headline line is the acoustic one)")
@@ -685,6 +687,115 @@ def run_storage(args):
     prop.close()
 
 
+def run_adjoint(args):
+    """vp gradient of the acoustic shot at 256^3 so8 (the 512^3 recipe), 800
+    steps, 32 checkpoints: one step = tb_adjoint_gradient (forward with
+    checkpoints, then per segment the recomputation and the adjoint steps with
+    the imaging condition) for the residual traces - traces of a model with a
+    +3 % Gaussian anomaly.  GPts/s = grid points x steps / gradient time."""
+    import torch
+    import paper_2010_10248_gb300 as tb
+    from paper_2010_10248_gb300 import build as tbbuild
+    from paper_2010_10248_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    tbbuild.build()
+    tb.load()
+    size = args.size if args.size != 512 else 256
+    nt = args.nt if args.nt != 1000 else 800
+    nsnap = 32
+    w = wl.acoustic_512_so8(shape=(size,) * 3, nt=nt)
+    N = size ** 3
+    dev = torch.device("cuda", 0)
+    p = tb.Propagator(w.shape, w.spacing, w.so, nbl=w.nbl)
+    vp = torch.from_numpy(w.vp).to(dev)
+    p.set_model(vp)
+    dt = p.dt
+    ax = [torch.arange(n, device=dev, dtype=torch.float32) - n / 2 for n in w.shape]
+    blob = torch.exp(-(ax[0][:, None, None] ** 2 + ax[1][None, :, None] ** 2 + ax[2][None, None, :] ** 2)
+                     / (2 * (size / 10) ** 2))
+
+    def geometry(model):
+        p.set_model(model, dt=dt)
+        p.set_sources(w.src_xyz, w.wavelets(dt))
+        p.set_receivers(w.rec_xyz)
+
+    geometry((vp * (1 + 0.03 * blob)).contiguous())
+    d_obs = p.forward(nt, schedule="onestep").clone()
+    geometry(vp)
+    resid = (p.forward(nt, schedule="onestep") - d_obs).contiguous()
+    gvp = torch.empty_like(vp)
+    st = torch.cuda.current_stream()
+
+    def step():
+        p.adjoint_gradient(nt, resid, grad_vp=gvp, n_snapshots=nsnap)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # the forward alone, for the cost of a gradient in forward runs
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(st)
+    p.forward(nt, schedule="onestep")
+    f1.record(st)
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = tb.tb_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    value = N * nt / (ms * 1e-3) / 1e9
+    # algorithmic bytes per point and step of the gradient: forward one-step
+    # (16) with checkpoints, recomputation (16) and its segment copy (8),
+    # adjoint scale (12) and step (16), imaging condition (16 + FP64 sum 16)
+    bpp = 16.0 + 16.0 + 8.0 + 12.0 + 16.0 + 32.0
+    peak, peak_kind = measured_peaks()
+    achieved = bpp * N * nt / (ms * 1e-3) / 1e9
+    finite = bool(torch.isfinite(gvp).all().item()) and float(gvp.abs().max()) > 0
+    cpu = None
+    if not args.no_cpu:
+        try:
+            import oracle
+            oracle.build()
+            ws = wl.acoustic_512_so8(shape=(192,) * 3, nt=44, nbl=10)
+            dts = 0.8 * oracle.cfl_dt_max(ws.so, ws.spacing, float(ws.vp.max()))
+            wav = ws.wavelets(dts)
+            t = []
+            for k in (4, 44):
+                r = np.random.default_rng(1).standard_normal((k, len(ws.rec_xyz)))
+                t0 = time.perf_counter()
+                oracle.acoustic_adjoint(ws.shape, ws.spacing, ws.so, dts, k, ws.vp.astype(np.float64), r,
+                                        nbl=ws.nbl, src_xyz=ws.src_xyz, src_wav=wav[:, :k], rec_xyz=ws.rec_xyz)
+                t.append(time.perf_counter() - t0)
+            threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+            cpu = {"value": 192 ** 3 * 40 / max(t[1] - t[0], 1e-9) / 1e9, "unit": UNIT, "cores": threads,
+                   "kind": "oracle",
+                   "sample": f"192^3 so8 gradient, 40 steps (difference of a 4- and a 44-step FP64 oracle "
+                             f"adjoint run, {t[0] + t[1]:.1f} s total)"}
+        except Exception as e:  # the baseline is reported, not required
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"vp gradient, acoustic {size}^3 so8 {nt} steps", "grid": list(w.shape),
+                       "space_order": w.so, "nt": nt, "snapshots": nsnap, "receivers": len(w.rec_xyz),
+                       "step": "tb_adjoint_gradient (forward with checkpoints + recomputation + adjoint)"},
+            "gpu_launches": int(tb.tb_launch_count() - l0), "clocks": clk,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                         "kernel": "gradient step (all kernels of one time step)", "bytes_per_point_step": bpp},
+            "forward_ms": fwd_ms, "gradient_in_forward_runs": ms / fwd_ms,
+            "cpu_baseline": cpu, "gradient_finite": finite}
+    print(json.dumps(line), flush=True)
+    p.close()
+
+
 def main():
     args = parse()
     if args.impl == "native" and args.storage != "f32":
@@ -695,6 +806,9 @@ def main():
         return
     if args.impl == "native" and args.physics != "acoustic":
         run_physics(args)
+        return
+    if args.impl == "native" and args.adjoint:
+        run_adjoint(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -10,7 +10,8 @@
 //   d/dm(p) = sum_k lam^k(p) c2 [2 g (u^{k-1} - u^{k-2}) - c2 L u^{k-1}](p)
 //             / (dt^2 (1+g)^2)  -  sum_k lam^k(p) c2(p) S^{k-1}(p) c2(p)/dt^2,
 //   d/dvp = d/dm * (-2/vp^3),  vp = sqrt(c2)/dt,
-// accumulated in FP64.  Kernels stream along axis 0 like the TTI kernels.
+// accumulated in FP64 (the per-step term in FP32).  One plane of columns per
+// block; a neighbour load tests only the coordinate it moves along.
 #include <cstdint>
 
 #include "tb_internal.cuh"
@@ -43,25 +44,39 @@ __device__ __forceinline__ float damp_g(const PhysGrid& g, const float* __restri
   return __fmul_rn(__fadd_rn(__fadd_rn(__ldg(damp_b + x), __ldg(damp_b + g.n0 + y)), __ldg(damp_b + g.n0 + g.n1 + z)),
                    c2);
 }
-// centred Laplacian in differences form at (x, y, z) (w2[d][i-1] = c_i / h_d^2)
+// neighbour at offset o along axis d of the in-grid point (x, y, z): only
+// that coordinate can leave the grid
+template <int D>
+__device__ __forceinline__ float ld_ax(const PhysGrid& g, const float* __restrict__ f, size_t i0, int x, int y, int z,
+                                       int o) {
+  const int c = D == 0 ? x : (D == 1 ? y : z);
+  const int n = D == 0 ? g.n0 : (D == 1 ? g.n1 : g.n2);
+  const ptrdiff_t st = D == 0 ? (ptrdiff_t)g.n1 * g.n2p : (D == 1 ? (ptrdiff_t)g.n2p : 1);
+  return (unsigned)(c + o) < (unsigned)n ? __ldg(f + (ptrdiff_t)i0 + o * st) : 0.f;
+}
+// centred Laplacian in differences form at the in-grid point (x, y, z)
+// (w2[d][i-1] = c_i / h_d^2)
 template <int R>
 __device__ __forceinline__ float lap_at(const PhysGrid& g, const float* __restrict__ f, const LapW& w, int x, int y,
                                         int z) {
-  const float u = ldz(g, f, x, y, z);
+  const size_t i0 = aidx(g, x, y, z);
+  const float u = __ldg(f + i0);
   float l = 0.f;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     float s = 0.f;
 #pragma unroll
     for (int i = 1; i <= R; ++i) {
-      const float a = d == 0 ? ldz(g, f, x + i, y, z) : (d == 1 ? ldz(g, f, x, y + i, z) : ldz(g, f, x, y, z + i));
-      const float b = d == 0 ? ldz(g, f, x - i, y, z) : (d == 1 ? ldz(g, f, x, y - i, z) : ldz(g, f, x, y, z - i));
+      const float a = d == 0 ? ld_ax<0>(g, f, i0, x, y, z, i) : (d == 1 ? ld_ax<1>(g, f, i0, x, y, z, i) : ld_ax<2>(g, f, i0, x, y, z, i));
+      const float b = d == 0 ? ld_ax<0>(g, f, i0, x, y, z, -i) : (d == 1 ? ld_ax<1>(g, f, i0, x, y, z, -i) : ld_ax<2>(g, f, i0, x, y, z, -i));
       s = __fmaf_rn(w.c[d][i - 1], __fadd_rn(__fsub_rn(a, u), __fsub_rn(b, u)), s);
     }
     l = __fadd_rn(l, s);
   }
   return l;
 }
+// n / den, exact when den is 1 (outside the sponge) without a division
+__device__ __forceinline__ float div_sponge(float n, float den) { return den == 1.f ? n : __fdiv_rn(n, den); }
 }  // namespace
 
 // w = D lam^{k+1}
@@ -73,7 +88,7 @@ __global__ void k_adj_scale(PhysGrid g, const float* __restrict__ lam1, const fl
   const size_t i0 = aidx(g, x, c.y, c.z);
   const float cc = __ldg(c2 + i0);
   const float gd = damp_g(g, damp_b, cc, x, c.y, c.z);
-  w[i0] = __fdiv_rn(__fmul_rn(cc, lam1[i0]), __fadd_rn(1.f, gd));
+  w[i0] = div_sponge(__fmul_rn(cc, lam1[i0]), __fadd_rn(1.f, gd));
 }
 
 // lam^{k} = L w + B lam^{k+1} + C lam^{k+2} (before the residual injection)
@@ -88,12 +103,13 @@ __global__ void k_adj_step(PhysGrid g, LapW lw, const float* __restrict__ w, con
   const float gd = damp_g(g, damp_b, __ldg(c2 + i0), x, c.y, c.z);
   const float opg = __fadd_rn(1.f, gd);
   const float l = lap_at<R>(g, w, lw, x, c.y, c.z);
-  lam0[i0] = __fadd_rn(l, __fdiv_rn(__fmaf_rn(2.f, lam1[i0], __fmul_rn(__fsub_rn(gd, 1.f), lam2[i0])), opg));
+  lam0[i0] = __fadd_rn(l, div_sponge(__fmaf_rn(2.f, lam1[i0], __fmul_rn(__fsub_rn(gd, 1.f), lam2[i0])), opg));
 }
 
-// grad_m += lam^k c2 [2 g (u1 - u2) - c2 L u1] / (dt^2 (1+g)^2)   (FP64 sum)
+// grad_m += lam^k c2 [2 g (u1 - u2) - c2 L u1] / (dt^2 (1+g)^2): the term in
+// FP32, the sum over steps in FP64
 template <int R>
-__global__ void k_adj_grad(PhysGrid g, LapW lw, double inv_dt2, const float* __restrict__ lam0,
+__global__ void k_adj_grad(PhysGrid g, LapW lw, float inv_dt2, const float* __restrict__ lam0,
                            const float* __restrict__ u1, const float* __restrict__ u2, const float* __restrict__ c2,
                            const float* __restrict__ damp_b, double* __restrict__ gm) {
   const AdjCol c = adj_col(g);
@@ -103,10 +119,10 @@ __global__ void k_adj_grad(PhysGrid g, LapW lw, double inv_dt2, const float* __r
   const float cc = __ldg(c2 + i0);
   const float gd = damp_g(g, damp_b, cc, x, c.y, c.z);
   const float lu = lap_at<R>(g, u1, lw, x, c.y, c.z);
-  const double opg = 1.0 + (double)gd;
-  const double dr = (double)cc * (2.0 * (double)gd * ((double)u1[i0] - (double)u2[i0]) - (double)cc * (double)lu) *
-                    inv_dt2 / (opg * opg);
-  gm[i0] += (double)lam0[i0] * dr;
+  const float opg = __fadd_rn(1.f, gd);
+  const float t = __fmaf_rn(__fmul_rn(2.f, gd), __fsub_rn(__ldg(u1 + i0), __ldg(u2 + i0)), -__fmul_rn(cc, lu));
+  const float dr = div_sponge(__fmul_rn(__fmul_rn(cc, t), inv_dt2), __fmul_rn(opg, opg));
+  gm[i0] += (double)__ldg(lam0 + i0) * (double)dr;
 }
 
 // source term: grad_m(p_id) -= lam^k c2(p) src_dcmp[k-1][id] / dt^2  (src_dcmp = c2 S)
@@ -170,7 +186,7 @@ template <int R>
 static cudaError_t adj_grad_r(const PhysGrid& g, const LapW& lw, double dt, const float* lam0, const float* u1,
                               const float* u2, const float* c2, const float* damp_b, double* gm, cudaStream_t st) {
   count_launch();
-  k_adj_grad<R><<<adj_grid(g), dim3(32, 8), 0, st>>>(g, lw, 1.0 / (dt * dt), lam0, u1, u2, c2, damp_b, gm);
+  k_adj_grad<R><<<adj_grid(g), dim3(32, 8), 0, st>>>(g, lw, (float)(1.0 / (dt * dt)), lam0, u1, u2, c2, damp_b, gm);
   return cudaGetLastError();
 }
 cudaError_t adjoint_grad(int R, const PhysGrid& g, const LapW& lw, double dt, const float* lam0, const float* u1,

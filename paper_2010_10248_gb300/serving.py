@@ -41,6 +41,7 @@ class ShotRequest:
     time_tile: int = 0      # 0: blocked sweep with the default tile; 1: one-step
     arrival: float = 0.0    # seconds after the start of the run
     tag: object = None
+    storage: int = 0        # wavefield storage: 0 FP32, 1 FP16, 2 BF16 (one-step)
 
 
 @dataclass
@@ -58,12 +59,17 @@ class ShotResult:
 
 
 def footprint_bytes(req: ShotRequest) -> int:
-    """Device bytes a shot holds while it runs: four wavefield buffers and the
-    c2 field (padded rows), sponge tables, inspector tables, the receiver
-    staging rows and the trace buffer, plus the blocked sweep's halo ring."""
+    """Device bytes a shot holds while it runs: four FP32 wavefield buffers
+    (or two 16-bit ones) and the c2 field (padded rows), sponge tables,
+    inspector tables, the receiver staging rows and the trace buffer, plus the
+    blocked sweep's halo ring."""
     n0, n1, n2 = (int(s) for s in req.shape)
-    n2p = (n2 + 3) // 4 * 4
-    fields = 5 * 4 * n0 * n1 * n2p
+    if req.storage in (1, 2):
+        n2p = (n2 + 7) // 8 * 8
+        fields = (2 * 2 + 4) * n0 * n1 * n2p
+    else:
+        n2p = (n2 + 3) // 4 * 4
+        fields = 5 * 4 * n0 * n1 * n2p
     nrec = len(req.rec_xyz)
     tables = 64 * 8 * (len(req.src_xyz) + nrec) + 8 * n1 * n2
     rec_rows = 16 * 4 * 8 * nrec
@@ -90,7 +96,7 @@ class _Slot:
         self.start = time.perf_counter() - t0
         with torch.cuda.stream(self.stream):
             self.prop = Propagator(req.shape, req.spacing, req.space_order, nbl=req.nbl,
-                                   time_tile=req.time_tile)
+                                   time_tile=req.time_tile if req.storage == 0 else 1, storage=req.storage)
             p = self.prop
             st = self.stream
             _tb.tb_set_model(p.h, req.vp, None, None, 0.0, st)
@@ -101,7 +107,7 @@ class _Slot:
                                req.nt, wav, st)
             _tb.tb_set_receivers(p.h, len(req.rec_xyz), np.ascontiguousarray(req.rec_xyz, dtype=np.float64), st)
             dev_tr = torch.empty((req.nt, len(req.rec_xyz)), dtype=torch.float32, device="cuda")
-            sched = _tb.TB_BLOCKED if req.time_tile != 1 else _tb.TB_ONESTEP
+            sched = _tb.TB_BLOCKED if (req.time_tile != 1 and req.storage == 0) else _tb.TB_ONESTEP
             _tb.tb_forward(p.h, req.nt, dev_tr, sched, st)
             self.host_traces = torch.empty(dev_tr.shape, dtype=torch.float32, pin_memory=True)
             self.host_traces.copy_(dev_tr, non_blocking=True)

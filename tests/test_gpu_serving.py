@@ -1,6 +1,6 @@
 """Continuous-batching shot server: shots overlap on the GPU, admission
-respects the memory budget, and every shot gives bit-identical traces alone
-and in the mix."""
+respects the memory budget, and every shot (FP32 or FP16 wavefield storage)
+gives bit-identical traces alone and in the mix."""
 from __future__ import annotations
 
 import numpy as np
@@ -34,7 +34,8 @@ def shots(serving, n=6, seed=5):
         src = g.uniform(0.3, 0.7, size=(int(g.integers(1, 5)), 3)) * ext
         rec = g.uniform(0.05, 0.95, size=(int(g.integers(20, 300)), 3)) * ext
         out.append(serving.ShotRequest(shape, h, so, vp, src, 12.0, rec, nt=int(g.integers(300, 600)), nbl=8,
-                                       time_tile=int(g.choice([0, 1])), arrival=0.0005 * i, tag=i))
+                                       time_tile=int(g.choice([0, 1])), arrival=0.0005 * i, tag=i,
+                                       storage=1 if i % 3 == 2 else 0))
     return out
 
 

@@ -84,3 +84,14 @@ def test_storage_ragged_grid(tb, storage):
     e_tr, e_u = rel_l2(tr, tr_o), rel_l2(u, u_o)
     print(f"{storage} ragged: traces rel-L2 {e_tr:.2e}, field rel-L2 {e_u:.2e}")
     assert e_tr <= LIMITS[storage] and e_u <= LIMITS[storage]
+
+
+def test_workspace_counts_the_stored_fields(tb):
+    """A 16-bit handle holds two 2-byte wavefields instead of four FP32 ones."""
+    shape = (40, 36, 83)
+    n2p32, n2p16 = (83 + 3) // 4 * 4, (83 + 7) // 8 * 8
+    w32 = tb.Propagator(shape, (10.0,) * 3, 8).workspace_bytes()
+    w16 = tb.Propagator(shape, (10.0,) * 3, 8, storage=tb.TB_F16).workspace_bytes()
+    fields32 = 5 * 4 * 40 * 36 * n2p32          # four wavefields + c2
+    fields16 = (2 * 2 + 4) * 40 * 36 * n2p16    # two 16-bit wavefields + c2
+    assert w32 - w16 == fields32 - fields16

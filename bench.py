@@ -403,6 +403,14 @@ def run_native(args):
             "kernel_ms_per_launch": kms_b, "point_updates_per_s_in_kernel": upd_per_s / 1e9,
             "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_source": peak_kind}}
+    # the peaks measured in this run with the library's own kernels (float4
+    # copy, packed-FP32 FMA chains), beside the measured ones
+    try:
+        hbm_run, fp_run = tb.tb_measure_peaks()
+        roof["in_run"] = {"hbm_gbs": hbm_run, "fp32_tflops": fp_run,
+                          "frac_hbm": achieved / hbm_run, "frac_fp32": upd_per_s * fl / 1e12 / fp_run}
+    except Exception as e:  # reported, not required
+        roof["in_run"] = {"error": str(e)}
     ipp = counters.get("warp_inst_per_point_update")
     if ipp:
         ipeak = nsm * 4 * mhz * 1e6

@@ -232,6 +232,16 @@ int tb_ricker(double f0, double dt, int nt, double t0, float* out);
  * Synchronises `stream`.  Errors: TB_EINVAL, TB_ECUDA. */
 int tb_selftest_wait(double timeout_s, void* stream);
 
+/* Measure, with this library's own kernels, the two peaks its rooflines are
+ * read against: *hbm_gbs = HBM copy bandwidth in GB/s (read + write bytes
+ * of a float4 copy between two 1 GiB device buffers, best of 5 after a
+ * warm-up), *fp32_tflops = FP32 throughput in TFLOP/s of independent chains
+ * of packed f32x2 FMAs on every SM (4 flops per packed FMA).  Allocates and
+ * frees 2 GiB of device memory on `stream` and synchronises it.  Output
+ * pointers are host memory.  Errors: TB_EINVAL (NULL output), TB_ENOMEM,
+ * TB_ECUDA; on error both outputs are 0. */
+int tb_measure_peaks(double* hbm_gbs, double* fp32_tflops, void* stream);
+
 /* --- Allocation-free inspection --------------------------------------- */
 
 /* The source-point inspector of tb_set_sources (affected grid points of a

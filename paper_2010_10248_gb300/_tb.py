@@ -65,6 +65,7 @@ _SIGS = {
                                     C.POINTER(C.c_double)]),
     "tb_ricker": (C.c_int, [C.c_double, C.c_double, C.c_int, C.c_double, C.POINTER(C.c_float)]),
     "tb_selftest_wait": (C.c_int, [C.c_double, _vp]),
+    "tb_measure_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
     "tb_launch_count": (C.c_uint64, []),
     "tb_inspect_points_noalloc": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int,
                                             _vp, _vp, _vp, _vp]),
@@ -247,6 +248,15 @@ def tb_ricker(f0, dt, nt, t0=0.0):
 def tb_selftest_wait(timeout_s, stream=None):
     """Runs the bounded device-side wait on a flag nothing sets; returns the status."""
     return load().tb_selftest_wait(float(timeout_s), _stream(stream))
+
+
+def tb_measure_peaks(stream=None):
+    """(HBM copy GB/s, packed-FP32 FMA TFLOP/s) measured with the library's kernels."""
+    hbm, fp = C.c_double(0.0), C.c_double(0.0)
+    st = load().tb_measure_peaks(C.byref(hbm), C.byref(fp), _stream(stream))
+    if st != TB_OK:
+        raise TBError(st, "tb_measure_peaks")
+    return hbm.value, fp.value
 
 
 def tb_launch_count():

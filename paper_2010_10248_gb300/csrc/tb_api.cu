@@ -1605,6 +1605,22 @@ namespace tbi {
 cudaError_t selftest_wait(long long timeout_ns, cudaStream_t st, int* timed_out);
 }
 
+extern "C" int tb_measure_peaks(double* hbm_gbs, double* fp32_tflops, void* stream) {
+  if (!hbm_gbs || !fp32_tflops) return TB_EINVAL;
+  *hbm_gbs = 0.0;
+  *fp32_tflops = 0.0;
+  const cudaError_t e = tbi::measure_peaks(hbm_gbs, fp32_tflops, (cudaStream_t)stream);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return TB_ENOMEM;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TB_ECUDA;
+  }
+  return TB_OK;
+}
+
 extern "C" int tb_selftest_wait(double timeout_s, void* stream) {
   if (!(timeout_s > 0) || timeout_s > 10) return TB_EINVAL;
   int timed_out = -1;

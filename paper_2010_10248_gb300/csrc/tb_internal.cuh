@@ -160,6 +160,10 @@ inline void dfree(void* p, cudaStream_t st) {
 
 // 16-bit (or plain FP32) storage one-step path (tb_lowprec.cu); storage: 1 FP16,
 // 2 BF16, 3 FP32.  scales[k] / mx[k]: scale and max |u| of u^{k-1}.
+// HBM copy bandwidth (GB/s, read + write bytes of a 2 x 1 GiB float4 copy,
+// best of 5) and packed-FP32 FMA throughput (TFLOP/s), with this build's
+// kernels (tb_selftest.cu).  Synchronises st.
+cudaError_t measure_peaks(double* hbm_gbs, double* fp32_tflops, cudaStream_t st);
 // scales[n + 2] (of u^{n+1}) from max |u^n| and the step's largest injection
 cudaError_t lowprec_scale(float* scales, const unsigned* mx, const float* srcmax, int n, cudaStream_t st);
 cudaError_t lowprec_step(int storage, int R, const PhysGrid& g, const LapW& w, int nchunks, const void* uc, void* up,

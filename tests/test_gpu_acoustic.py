@@ -320,3 +320,11 @@ def test_fp32_error_growth_1000_steps(tb):
     print(f"128^3 so8 1000 steps: rel-L2 field {rel(u, u_o):.3e}, traces {rel(tr, tr_o):.3e}")
     assert rel(u, u_o) <= TOL, rel(u, u_o)
     assert rel(tr, tr_o) <= TOL, rel(tr, tr_o)
+
+
+def test_measured_peaks_in_run(tb):
+    """The library's own copy and FMA kernels measure plausible peaks."""
+    hbm, fp32 = tb.tb_measure_peaks()
+    print(f"copy {hbm:.0f} GB/s, packed FP32 FMA {fp32:.1f} TFLOP/s")
+    assert 1000.0 < hbm < 10000.0
+    assert 10.0 < fp32 < 200.0

@@ -110,8 +110,10 @@ typedef struct {
  * space order 4, 8 or 12 (the space orders of Sec. IV) and physics
  * TB_ACOUSTIC, TB_TTI or TB_ELASTIC.  Requires n_d >= space_order + 2 on
  * every axis.  `opt` may be NULL (defaults).  Allocates the wavefields and
- * model buffers on the current CUDA device (acoustic: 5 x n0 n1 n2 floats;
- * TTI: 16; elastic: 18).  Errors: TB_EINVAL, TB_ENOMEM, TB_ECUDA. */
+ * model buffers on the current CUDA device (acoustic: 5 x n0 n1 n2 floats,
+ * with TB_F16 / TB_BF16 storage two 16-bit wavefields and one float field;
+ * TTI: 16; elastic: 18).  Errors: TB_EINVAL (also: 16-bit or plain storage
+ * with TTI or elastic physics), TB_ENOMEM, TB_ECUDA. */
 int tb_create(const int64_t n[3], const double h[3], int space_order, int physics,
               const tb_options* opt, tb_handle** out);
 

@@ -91,10 +91,15 @@ typedef struct {
                       0 -> the fastest measured on GB300 at 512^3: 4 (space
                       order 4), 3 (8), 2 (12).  TB_TTI, TB_ELASTIC: 0 or 1.  */
   int nbl;         /* width in cells of the built-in sponge (Sec. IV-B); 0: none  */
-  int y_bands;     /* blocked sweep: number of bands along axis 1; 0 -> fewest
-                      bands whose tiles are co-resident on the GPU                */
+  int y_bands;     /* blocked sweep: number of bands along axis 1, each time
+                      tile split the same way; 0 -> bands pipelined across time
+                      tiles: every launch fills the co-resident CTAs with the
+                      rows of time tile k still to do and, once k is finished
+                      in that launch, the first rows of tile k + 1 (rows at
+                      least T r below the rows of tile k still running)      */
   int x_chunks;    /* chunks along axis 0 processed as independent sweeps; 0 -> 1
-                      (blocked) or automatic (one-step)                           */
+                      (blocked) or automatic (one-step); > 1 with the blocked
+                      schedule turns the pipelining off                         */
   int profile;     /* 1: time every propagator launch with CUDA events on the
                       launching stream (read back with tb_kernel_time)            */
   int check_nan;   /* 1: tb_forward scans the traces and returns TB_EDIVERGED on
@@ -104,6 +109,8 @@ typedef struct {
   int storage;     /* TB_F32 (0), TB_F16, TB_BF16 or TB_F32_PLAIN; the 16-bit
                       stored value is u / s with s = 2^(ceil(log2(4 max|u^n| +
                       max|source step n|)) - 8), set on the device each step     */
+  int band_ctas;   /* pipelined blocked sweep: most CTAs per launch; 0 -> every
+                      CTA that fits co-resident on the GPU (one per SM)          */
 } tb_options;
 
 /* Create a propagator for a grid of shape n[3] with spacing h[3] (metres),

@@ -407,7 +407,7 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   // registers)
   if (h->opt.time_tile == 0) h->opt.time_tile = (tmax > 1 && so == 8) ? 3 : tmax;
   if (h->opt.time_tile < 1 || h->opt.time_tile > tmax || h->opt.nbl < 0 || h->opt.y_bands < 0 ||
-      h->opt.x_chunks < 0) {
+      h->opt.x_chunks < 0 || h->opt.band_ctas < 0) {
     delete h;
     return TB_EINVAL;
   }
@@ -759,6 +759,7 @@ struct Plan {
   std::vector<PassDesc> launch_passes;  // all passes, in launch order
   std::vector<int> launch_first;        // first pass index of each launch
   std::vector<int> launch_ctas;         // CTAs per launch
+  std::vector<int> launch_tile;         // pipelined plans: time tile k of set 0
   int max_ctas = 0;
 };
 
@@ -847,6 +848,88 @@ static int plan_sweep(tb_handle* h, int T, Plan* pl) {
   return TB_OK;
 }
 
+// Blocked sweep of K time tiles with the bands pipelined across time tiles.
+// Each launch fills up to `cap` CTAs: first with the rows of time tile k not
+// yet computed (a band of rows [y, y1), cut where the CTAs run out), then,
+// once tile k reaches the last row, with the first rows [0, c) of tile k + 1.
+// A pass owning rows [y0, y1) of tile k + 1 depends on rows
+// [0, y1 + T r) of tile k (T steps of reach r each); those must have been
+// owned by earlier launches, so c <= y - T r.  The same bound keeps tile
+// k + 1's writes (into the fields tile k reads) below every row that tile
+// k's band in the launch reads.  Rows a pass computes beyond what its owned
+// rows depend on may read fields in flight; they are never written out.  A
+// grid whose time tile fits one launch gets one launch per tile.
+static int plan_pipeline(tb_handle* h, int T, int K, Plan* pl) {
+  const int R = h->R;
+  SweepShape sh;
+  if (!sweep_shape(R, T, &sh, 0)) return fail(h, TB_EINVAL, "unsupported time tile %d", T);
+  int per_sm = 0;
+  cudaError_t e = sweep_max_ctas(R, T, &per_sm, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "occupancy");
+  if (per_sm < 1) return fail(h, TB_ECUDA, "sweep kernel does not fit on an SM");
+  int cap = per_sm * h->num_sms;
+  if (h->opt.band_ctas > 0) cap = std::min(cap, h->opt.band_ctas);
+  const int n0 = (int)h->n[0], n1 = (int)h->n[1], n2 = (int)h->n[2];
+  const int TY = sh.TY, TZ = 64;
+  const int ntz = (n2 + TZ - 1) / TZ;
+  const int halo = (T - 1) * R, reach = T * R;
+  const int tiles_cap = cap / ntz;  // tile rows per launch
+  auto make = [&](int set, int y0, int y1) {
+    PassDesc p{};
+    p.yo0 = y0;
+    p.yo1 = y1;
+    p.xo0 = 0;
+    p.xo1 = n0;
+    p.yb0 = std::max(0, y0 - halo);
+    p.nty = (std::min(n1, y1 + halo) - p.yb0 + TY - 1) / TY;
+    p.ntz = ntz;
+    p.xc0 = 0;
+    p.xc1 = n0;
+    p.set = set;
+    return p;
+  };
+  // the last row y1 <= n1 a pass from row y0 can own within `tiles` tile rows
+  auto last_row = [&](int y0, int tiles) {
+    const int cover = std::max(0, y0 - halo) + tiles * TY;
+    return cover >= n1 ? n1 : cover - halo;
+  };
+  pl->launch_passes.clear();
+  pl->launch_first.clear();
+  pl->launch_ctas.clear();
+  pl->launch_tile.clear();
+  pl->max_ctas = 0;
+  int k = 0, y = 0;  // rows [0, y) of time tile k are done
+  while (k < K) {
+    const int y1 = last_row(y, tiles_cap);
+    if (y1 <= y)
+      return fail(h, TB_EINVAL, "a blocked launch of %d CTAs cannot hold a band of this grid (%d tile columns)", cap,
+                  ntz);
+    pl->launch_first.push_back((int)pl->launch_passes.size());
+    pl->launch_tile.push_back(k);
+    PassDesc a = make(0, y, y1);
+    a.cta0 = 0;
+    int ctas = a.nty * ntz;
+    pl->launch_passes.push_back(a);
+    if (y1 < n1) {
+      y = y1;
+    } else {
+      int c = 0;
+      if (k + 1 < K && tiles_cap > a.nty) c = std::min(last_row(0, tiles_cap - a.nty), y - reach);
+      if (c > 0) {
+        PassDesc b = make(1, 0, c);
+        b.cta0 = ctas;
+        ctas += b.nty * ntz;
+        pl->launch_passes.push_back(b);
+      }
+      ++k;
+      y = std::max(c, 0);
+    }
+    pl->launch_ctas.push_back(ctas);
+    pl->max_ctas = std::max(pl->max_ctas, ctas);
+  }
+  return TB_OK;
+}
+
 static int ensure_capacity(tb_handle* h, int T, const Plan& pl, int nt, bool host_traces, int nrec,
                            cudaStream_t st) {
   SweepShape sh;
@@ -878,7 +961,9 @@ static int ensure_capacity(tb_handle* h, int T, const Plan& pl, int nt, bool hos
     h->pass_cap = (int)pl.launch_passes.size();
   }
   if (h->have_rec && h->rec.npts > 0) {
-    const int cap = std::max(16, T) / T * T;
+    // ring rows, a power of two: two time tiles in flight, plus slack
+    int cap = 16;
+    while (cap < 3 * T) cap *= 2;
     if (cap > h->rec_cap) {
       dfree(h->rec_dcmp, st);
       h->rec_dcmp = nullptr;
@@ -1109,10 +1194,15 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   float* dtr = host_traces ? nullptr : traces;
   const int T = schedule == TB_BLOCKED ? h->opt.time_tile : 1;
 
+  // blocked: bands pipelined across the K full time tiles unless the user
+  // fixed the decomposition (y_bands, x_chunks); the nt mod T remaining
+  // steps run one step per sweep
+  const int K = T > 1 ? nt / T : 0;
+  const bool pipelined = T > 1 && h->opt.y_bands == 0 && h->opt.x_chunks <= 1;
   Plan p1, pT;
   int s = plan_sweep(h, 1, &p1);
   if (s != TB_OK) return s;
-  if (T > 1 && (s = plan_sweep(h, T, &pT)) != TB_OK) return s;
+  if (T > 1 && (s = pipelined ? plan_pipeline(h, T, K, &pT) : plan_sweep(h, T, &pT)) != TB_OK) return s;
   if ((s = ensure_capacity(h, 1, p1, nt, host_traces, nrec, st)) != TB_OK) return s;
   if (T > 1 && (s = ensure_capacity(h, T, pT, nt, host_traces, nrec, st)) != TB_OK) return s;
   if (host_traces) dtr = h->traces_dev;
@@ -1177,9 +1267,12 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
                              cudaMemcpyHostToDevice, st));
 
   int cur = 0, prev = 1;  // field indices of u^n and u^{n-1}
-  int rec_base = 0, rec_fill = 0;
-  auto flush_receivers = [&]() -> int {
-    if (rec_on && rec_fill > 0 && dtr) {
+  // receiver samples of step n sit in ring row n mod rec_cap until the
+  // traces of steps [flushed, done) are finalised (done: every row complete)
+  int flushed = 0;
+  auto flush_receivers = [&](int done) -> int {
+    while (rec_on && dtr && flushed < done) {
+      const int row = flushed % h->rec_cap, cnt = std::min(done - flushed, h->rec_cap - row);
       cudaEvent_t a = nullptr, b = nullptr;
       if (h->opt.profile) {
         a = ev_next(h);
@@ -1187,62 +1280,93 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
         h->ev_kind.push_back(1);
         if (a) cudaEventRecord(a, st);
       }
-      cudaError_t e = finalize_traces(rec_fill, nrec, h->rec.corner_eid, h->rec.corner_w, h->rec_dcmp,
-                                      h->rec.npts, dtr + (size_t)rec_base * nrec, st);
+      cudaError_t e = finalize_traces(cnt, nrec, h->rec.corner_eid, h->rec.corner_w,
+                                      h->rec_dcmp + (size_t)row * h->rec.npts, h->rec.npts,
+                                      dtr + (size_t)flushed * nrec, st);
       if (h->opt.profile && b) cudaEventRecord(b, st);
       if (e != cudaSuccess) return cuda_fail(h, e, "receiver finalize");
+      flushed += cnt;
     }
-    rec_base += rec_fill;
-    rec_fill = 0;
+    flushed = done;
     return TB_OK;
   };
+  // before a launch recording steps below `hi` (steps below `done` complete)
+  auto make_room = [&](int done, int hi) -> int {
+    return rec_on && hi - flushed > h->rec_cap ? flush_receivers(done) : TB_OK;
+  };
+  P.rec_cap = h->rec_cap > 0 ? h->rec_cap : 1;
   P.lp_scales = h->lp_scales;
   P.lp_mx = h->lp_mx;
+  // set `i` of the launch: the time tile from step n reading (fld[c], fld[p])
+  auto set_fields = [&](int i, int c, int p, int out0, int out1, int step0) {
+    SweepSet& S = P.set[i];
+    S.u_cur = fld[c];
+    S.u_prev = fld[p];
+    S.tm_u = h->tm_box[c];
+    S.tm_p = h->tm_tile[p];
+    S.out0 = fld[out0];
+    S.out1 = out1 >= 0 ? fld[out1] : nullptr;
+    S.step0 = step0;
+  };
+  P.tm_c = h->tm_c2;
+  auto launch = [&](int TT, const Plan& pl, int pass_off, size_t L) -> int {
+    const int first = pl.launch_first[L];
+    const int last = L + 1 < pl.launch_first.size() ? pl.launch_first[L + 1] : (int)pl.launch_passes.size();
+    P.pass = h->d_pass + pass_off + first;
+    P.npass = last - first;
+    P.prog_base = h->prog_base;
+    int maxsteps = 0;
+    for (int i = first; i < last; ++i) {
+      const PassDesc& d = pl.launch_passes[i];
+      maxsteps = std::max(maxsteps, d.xo1 - 1 + (TT - 1) * h->R - d.xc0 + 1);
+    }
+    h->prog_base += (unsigned long long)maxsteps + 2;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (h->opt.profile) {
+      a = ev_next(h);
+      b = ev_next(h);
+      h->ev_kind.push_back(0);
+      if (a) cudaEventRecord(a, st);
+    }
+    cudaError_t e = sweep_launch(h->R, TT, P, pl.launch_ctas[L], TT > 1, st, TT == 1 ? h->sk : 0);
+    if (h->opt.profile && b) cudaEventRecord(b, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, TT > 1 ? "blocked sweep launch" : "one-step launch");
+    return TB_OK;
+  };
+  // every launch of a plan on the time tile (or step) from step n
   auto run = [&](int TT, const Plan& pl, int pass_off, int out0, int out1, int step0) -> int {
     if (h->sk) {  // the scale of u^{n+1}, from max |u^n| and the step's largest injection
       cudaError_t e = lowprec_scale(h->lp_scales, h->lp_mx, (h->have_src && h->src.npts > 0) ? h->lp_srcmax : nullptr,
                                     step0, st);
       if (e != cudaSuccess) return cuda_fail(h, e, "scale");
     }
-    P.u_cur = fld[cur];
-    P.u_prev = fld[prev];
-    P.tm_u = h->tm_box[cur];
-    P.tm_p = h->tm_tile[prev];
-    P.tm_c = h->tm_c2;
-    P.out0 = fld[out0];
-    P.out1 = out1 >= 0 ? fld[out1] : nullptr;
-    P.step0 = step0;
-    P.rec_base = rec_base;
+    set_fields(0, cur, prev, out0, out1, step0);
     for (size_t L = 0; L < pl.launch_first.size(); ++L) {
-      const int first = pl.launch_first[L];
-      const int last = L + 1 < pl.launch_first.size() ? pl.launch_first[L + 1] : (int)pl.launch_passes.size();
-      P.pass = h->d_pass + pass_off + first;
-      P.npass = last - first;
-      P.prog_base = h->prog_base;
-      int maxsteps = 0;
-      for (int i = first; i < last; ++i) {
-        const PassDesc& d = pl.launch_passes[i];
-        maxsteps = std::max(maxsteps, d.xo1 - 1 + (TT - 1) * h->R - d.xc0 + 1);
-      }
-      h->prog_base += (unsigned long long)maxsteps + 2;
-      cudaEvent_t a = nullptr, b = nullptr;
-      if (h->opt.profile) {
-        a = ev_next(h);
-        b = ev_next(h);
-        h->ev_kind.push_back(0);
-        if (a) cudaEventRecord(a, st);
-      }
-      cudaError_t e = sweep_launch(h->R, TT, P, pl.launch_ctas[L], TT > 1, st, TT == 1 ? h->sk : 0);
-      if (h->opt.profile && b) cudaEventRecord(b, st);
-      if (e != cudaSuccess) return cuda_fail(h, e, TT > 1 ? "blocked sweep launch" : "one-step launch");
+      int r = launch(TT, pl, pass_off, L);
+      if (r != TB_OK) return r;
     }
     return TB_OK;
   };
 
   int n = 0;
+  if (pipelined && K > 0) {
+    // time tile k reads fields (0, 1) for even k and (2, 3) for odd k and
+    // writes (u^{n+T}, u^{n+T-1}) into the other pair
+    for (size_t L = 0; L < pT.launch_first.size(); ++L) {
+      const int k = pT.launch_tile[L];
+      const int c = (k & 1) ? 2 : 0, o = 2 - c;
+      set_fields(0, c, c + 1, o, o + 1, k * T);
+      set_fields(1, o, o + 1, c, c + 1, (k + 1) * T);
+      if ((s = make_room(k * T, (k + 2) * T)) != TB_OK) return s;
+      if ((s = launch(T, pT, off_T, L)) != TB_OK) return s;
+    }
+    cur = (K & 1) ? 2 : 0;
+    prev = cur + 1;
+    n = K * T;
+  }
   while (n < nt) {
-    if (T > 1 && n + T <= nt) {
-      if (rec_on && rec_fill + T > h->rec_cap && (s = flush_receivers()) != TB_OK) return s;
+    if (T > 1 && !pipelined && n + T <= nt) {
+      if ((s = make_room(n, n + T)) != TB_OK) return s;
       // the two fields not holding (u^n, u^{n-1}) receive (u^{n+T}, u^{n+T-1})
       int free_idx[2], nf = 0;
       for (int i = 0; i < 4; ++i)
@@ -1250,17 +1374,15 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
       if ((s = run(T, pT, off_T, free_idx[0], free_idx[1], n)) != TB_OK) return s;
       cur = free_idx[0];
       prev = free_idx[1];
-      rec_fill += T;
       n += T;
     } else {
-      if (rec_on && rec_fill + 1 > h->rec_cap && (s = flush_receivers()) != TB_OK) return s;
+      if ((s = make_room(n, n + 1)) != TB_OK) return s;
       if ((s = run(1, p1, 0, prev, -1, n)) != TB_OK) return s;
       std::swap(cur, prev);
-      rec_fill += 1;
       n += 1;
     }
   }
-  if ((s = flush_receivers()) != TB_OK) return s;
+  if ((s = flush_receivers(nt)) != TB_OK) return s;
   h->cur_idx = cur;
   h->prev_idx = prev;
   if (h->sk) h->lp_cur = cur;
@@ -1426,15 +1548,16 @@ static int runner_init(tb_handle* h, StepRunner* r, cudaStream_t st) {
 // u^{step+1} over field[prev] from field[cur] = u^{step}, field[prev] = u^{step-1}
 static int runner_step(tb_handle* h, StepRunner* r, int cur, int prev, int step, cudaStream_t st) {
   SweepParams& P = r->P;
-  P.u_cur = h->field[cur];
-  P.u_prev = h->field[prev];
-  P.tm_u = h->tm_box[cur];
-  P.tm_p = h->tm_tile[prev];
+  SweepSet& S = P.set[0];
+  S.u_cur = h->field[cur];
+  S.u_prev = h->field[prev];
+  S.tm_u = h->tm_box[cur];
+  S.tm_p = h->tm_tile[prev];
+  S.out0 = h->field[prev];
+  S.out1 = nullptr;
+  S.step0 = step;
   P.tm_c = h->tm_c2;
-  P.out0 = h->field[prev];
-  P.out1 = nullptr;
-  P.step0 = step;
-  P.rec_base = 0;
+  P.rec_cap = 1;
   const Plan& pl = r->p1;
   for (size_t L = 0; L < pl.launch_first.size(); ++L) {
     const int first = pl.launch_first[L];

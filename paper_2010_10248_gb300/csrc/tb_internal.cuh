@@ -28,18 +28,27 @@ struct PassDesc {
   int yo0, yo1;  // rows whose results this pass owns (written out)
   int xc0, xc1;  // planes (axis 0) the first fused step computes
   int xo0, xo1;  // planes whose results this pass owns
+  int set;       // time tile of the pass: SweepParams::set[set]
 };
 
-// Launch parameters of one sweep (one-step or T fused steps).
-struct SweepParams {
+// The fields and first step of one time tile (T fused steps from step n).
+struct SweepSet {
   CUtensorMap tm_u;             // u^n: (TY+2r) x (64+2rp) boxes with halo
   CUtensorMap tm_p;             // u^{n-1}: TY x 64 tiles
-  CUtensorMap tm_c;             // c2: TY x 64 tiles
-  int n0, n1, n2, n2p;          // grid, and row pitch of the padded fields
   const float* u_cur;           // u^n
   const float* u_prev;          // u^{n-1}
   float* out0;                  // u^{n+T}   (one-step: may alias u_prev)
   float* out1;                  // u^{n+T-1} (T > 1)
+  int step0;                    // n
+};
+
+// Launch parameters of one sweep (one-step or T fused steps).  A launch may
+// hold passes of two consecutive time tiles (set[0]: tile k, set[1]: tile
+// k + 1) when bands of the blocked sweep are pipelined across time tiles.
+struct SweepParams {
+  SweepSet set[2];
+  CUtensorMap tm_c;             // c2: TY x 64 tiles
+  int n0, n1, n2, n2p;          // grid, and row pitch of the padded fields
   const float* c2;              // dt^2 vp^2 (padded layout)
   const float* damp_b;          // [n0 + n1 + n2] eta_d / (2 dt) per axis
   float2 w2[3][6];              // c_i / h_d^2 (i = 1..r) as (w, w) pairs
@@ -54,10 +63,10 @@ struct SweepParams {
   // grid-aligned receivers
   const int* r_colptr;
   const int2* r_ent;
-  float* rec_dcmp;              // [cap][nrpts], indexed by position in r_ent
+  float* rec_dcmp;              // [rec_cap][nrpts] ring: row = step mod rec_cap,
+                                // column = position in r_ent
   int64_t nrpts;
-  int rec_base;                 // step index stored in row 0 of rec_dcmp
-  int step0;                    // step index of the first fused step
+  int rec_cap;                  // a power of two
   // blocked-sweep coupling between CTAs
   float* ring;                  // per tile, per stage, per slot: halo strips
   unsigned long long* progress; // per CTA: completed steps (monotonic), kProgressStride apart

@@ -46,7 +46,10 @@
 // of u^{n+T}, u^{n+T-1}.  All CTAs of a pass stream in lockstep
 // (cooperative launch, co-resident); within a pass there is no redundant
 // computation, passes (bands along axis 1, chunks along axis 0) overlap by
-// (T-1) r rows or planes.
+// (T-1) r rows or planes.  A launch may hold passes of two consecutive time
+// tiles (SweepParams::set[0] and set[1]): the last band of tile k and the
+// first rows of tile k + 1, which depend only on rows of tile k finished by
+// earlier launches, so that every launch fills the GPU.
 //
 // Grid-aligned sparse operators (Sec. II-A).  Sources: each lane's column
 // pair has one range of planes that holds source points (built from the
@@ -55,7 +58,8 @@
 // in that range (Listing 5's fused injection, along the streamed axis); the
 // test is branch-light and stateless so that it does not split the step's
 // code.  Receivers: the receiver warp walks the per-column entries (x, id)
-// with one cursor per fused step and records u into rec_dcmp[step][rid].
+// with one cursor per fused step and records u into rec_dcmp[step mod
+// rec_cap][rid] (rec_cap a power of two).
 //
 // Rounding.  Every floating-point operation of the point update is an
 // explicit round-to-nearest operation, so each fused step and the one-step
@@ -338,6 +342,15 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
   for (int i = 1; i < P.npass; ++i)
     if (P.pass[i].cta0 <= b) pi = i;
   const PassDesc pd = P.pass[pi];
+  // the pass's time tile (selected field by field: constant-bank operands,
+  // no indexed access to the parameter block)
+  const bool s1 = T > 1 && pd.set != 0;
+  const int step0 = s1 ? P.set[1].step0 : P.set[0].step0;
+  float* const out0 = s1 ? P.set[1].out0 : P.set[0].out0;
+  float* const out1 = s1 ? P.set[1].out1 : P.set[0].out1;
+  const float* const u_cur = s1 ? P.set[1].u_cur : P.set[0].u_cur;
+  const CUtensorMap* const tm_u = s1 ? &P.set[1].tm_u : &P.set[0].tm_u;
+  const CUtensorMap* const tm_p = s1 ? &P.set[1].tm_p : &P.set[0].tm_p;
   const int tl = b - pd.cta0, ty = tl / pd.ntz, tz = tl - ty * pd.ntz;
   const int y0 = pd.yb0 + ty * TY, z0 = tz * TZ;
   const int jstart = pd.xc0;
@@ -374,14 +387,14 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
     {
       const int np = jstart + R - pu0;
       mbar_expect_tx(bar_pro, (unsigned)(np * C::PLANE * C::ESZ));
-      for (int p = pu0; p < jstart + R; ++p) tma_load_3d(u_slot(p), &P.tm_u, bar_pro, z0 - RP, y0 - R, p);
+      for (int p = pu0; p < jstart + R; ++p) tma_load_3d(u_slot(p), tm_u, bar_pro, z0 - RP, y0 - R, p);
     }
     // the data of stream step s: u^n plane s+R, u^{n-1} and c2 plane s
     auto issue = [&](int s) {
       uint64_t* bar = bar_dat + (s - jstart) % C::ND;
       mbar_expect_tx(bar, (unsigned)((C::PLANE + C::TILE) * C::ESZ + C::TILE * 4));
-      tma_load_3d(u_slot(s + R), &P.tm_u, bar, z0 - RP, y0 - R, s + R);
-      tma_load_3d(pring + ((s - jstart) % C::NP) * C::TILE, &P.tm_p, bar, z0, y0, s);
+      tma_load_3d(u_slot(s + R), tm_u, bar, z0 - RP, y0 - R, s + R);
+      tma_load_3d(pring + ((s - jstart) % C::NP) * C::TILE, tm_p, bar, z0, y0, s);
       tma_load_3d(cring + ((s - jstart) % C::NC) * C::TILE, &P.tm_c, bar, z0, y0, s);
     };
     int ns = jstart, ret = jstart - 1;
@@ -418,6 +431,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
     unsigned short* rcur = ccur;  // [T][col][NT]
     unsigned short* rlist = reinterpret_cast<unsigned short*>(smem + C::OFF_RL);
     int nlist = 0;
+    int xlo = 0x7fffffff, xhi = -1;  // planes holding the tile's receiver points
     for (int s0 = 0; s0 < 2 * NT; s0 += 32) {
       const int sl = s0 + lane, ci = sl / NT, t = sl - ci * NT;
       const int yy = y0 + (t >> 5), zz = z0 + 2 * (t & 31) + ci;
@@ -432,6 +446,8 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
           const int xf = __ldg(&P.r_ent[cb].x), xl = __ldg(&P.r_ent[ce - 1].x);
           cxf[sl] = (unsigned short)xf;
           dense = xl - xf + 1 == ce - cb;
+          xlo = min(xlo, xf);
+          xhi = max(xhi, xl);
           for (int k = 0; k < T; ++k) rcur[k * 2 * NT + sl] = 0;
         }
       }
@@ -440,12 +456,15 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
       nlist += __popc(m);
     }
     __syncwarp();
+    xlo = max(__reduce_min_sync(0xffffffffu, xlo), pd.xo0);
+    xhi = min(__reduce_max_sync(0xffffffffu, xhi), pd.xo1 - 1);
     const size_t ps = (size_t)P.n1 * P.n2p;
     // u at the receiver points of plane q of level n+kk+1 (fused step kk):
-    // from a staged plane, or from the sweep's output in global memory
+    // from a staged plane, or from the sweep's output in global memory (a
+    // plane without receiver points of the tile costs two compares)
     auto record = [&](int kk, int q, const float* plane) {
-      if (q < pd.xo0 || q >= pd.xo1 || nlist == 0) return;
-      float* rrow = P.rec_dcmp + (size_t)(P.step0 + kk - P.rec_base) * P.nrpts;
+      if (q < xlo || q > xhi) return;
+      float* rrow = P.rec_dcmp + (size_t)((step0 + kk) & (P.rec_cap - 1)) * P.nrpts;
       for (int e = lane; e < nlist; e += 32) {
         const int en = rlist[e], sl = en & 0x7fff, ci = sl / NT, t = sl - ci * NT;
         const int cn = rcnt[sl], cb = rbase[sl];
@@ -471,9 +490,9 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
           const int ww = t >> 5, ln = t & 31;
           const size_t go = (size_t)q * ps + (size_t)(y0 + ww) * P.n2p + z0 + 2 * ln + ci;
           if constexpr (SK != 0)  // one-step only: u^{n+1} is stored as u / s
-            rrow[pos] = __fmul_rn(ld1cg(reinterpret_cast<const ST*>(P.out0) + go), __ldg(P.lp_scales + P.step0 + 2));
+            rrow[pos] = __fmul_rn(ld1cg(reinterpret_cast<const ST*>(out0) + go), __ldg(P.lp_scales + step0 + 2));
           else
-            rrow[pos] = plane ? plane[(R + ww) * SW + RP + 2 * ln + ci] : __ldcg(P.out0 + go);
+            rrow[pos] = plane ? plane[(R + ww) * SW + RP + 2 * ln + ci] : __ldcg(out0 + go);
         }
       }
     };
@@ -707,7 +726,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
     for (int s = 0; s < C::Q; ++s) {
       const int plane = jstart - 1 - R + s;
       if (v0 && plane >= 0 && plane < P.n0) {
-        Q0[s] = ld2(reinterpret_cast<const ST*>(P.u_cur) + (size_t)plane * ps + coff);
+        Q0[s] = ld2(reinterpret_cast<const ST*>(u_cur) + (size_t)plane * ps + coff);
         if (!v1) Q0[s].y = 0.f;
       }
     }
@@ -726,8 +745,8 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
   float2 sc2 = make_float2(1.f, 1.f), sp2 = sc2, io2 = sc2;
   float vmax = 0.f;
   if constexpr (SK != 0) {
-    const float a = __ldg(P.lp_scales + P.step0 + 1), p = __ldg(P.lp_scales + P.step0),
-                o = 1.f / __ldg(P.lp_scales + P.step0 + 2);
+    const float a = __ldg(P.lp_scales + step0 + 1), p = __ldg(P.lp_scales + step0),
+                o = 1.f / __ldg(P.lp_scales + step0 + 2);
     sc2 = make_float2(a, a);
     sp2 = make_float2(p, p);
     io2 = make_float2(o, o);
@@ -739,7 +758,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
   // one step per stream step a column pair without sources skips it by a
   // branch; with several, the test stays branch-light so that the fused
   // steps' code is not split.
-  const float2* evrow = ev_n > 0 ? P.src_ev + (size_t)P.step0 * P.nev + ev_b : nullptr;
+  const float2* evrow = ev_n > 0 ? P.src_ev + (size_t)step0 * P.nev + ev_b : nullptr;
   auto inject = [&](int k, int q, float2& un) {
     if constexpr (T == 1)
       if (ev_n == 0) return;
@@ -825,9 +844,9 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
       if (act0 && own_row && j >= pd.xo0 && j < pd.xo1 && v0) {
         if constexpr (SK != 0) {
           vmax = fmaxf(vmax, fmaxf(fabsf(un0.x), v1 ? fabsf(un0.y) : 0.f));
-          st2cs(reinterpret_cast<ST*>(P.out0) + (size_t)j * ps + coff, __fmul2_rn(un0, io2));
+          st2cs(reinterpret_cast<ST*>(out0) + (size_t)j * ps + coff, __fmul2_rn(un0, io2));
         } else {
-          __stcs(reinterpret_cast<float2*>(P.out0 + (size_t)j * ps + coff), un0);
+          __stcs(reinterpret_cast<float2*>(out0 + (size_t)j * ps + coff), un0);
         }
       }
     } else {
@@ -903,8 +922,8 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
             if (strip_z >= 0) __stcg(reinterpret_cast<float2*>(rs + strip_z), un);
           }
         } else if (act && own_row && q >= pd.xo0 && q < pd.xo1 && v0) {
-          __stcs(reinterpret_cast<float2*>(P.out0 + (size_t)q * ps + coff), un);
-          __stcs(reinterpret_cast<float2*>(P.out1 + (size_t)q * ps + coff), Qs[T - 2][R]);
+          __stcs(reinterpret_cast<float2*>(out0 + (size_t)q * ps + coff), un);
+          __stcs(reinterpret_cast<float2*>(out1 + (size_t)q * ps + coff), Qs[T - 2][R]);
         }
       }
       mbar_arrive(bar_ctr + ((j + 1) & 1));
@@ -919,7 +938,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
   if constexpr (SK != 0) {  // max |u^{n+1}| over the grid, for the next step's scale
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    if (lane == 0 && vmax > 0.f) atomicMax(P.lp_mx + P.step0 + 2, __float_as_uint(vmax));
+    if (lane == 0 && vmax > 0.f) atomicMax(P.lp_mx + step0 + 2, __float_as_uint(vmax));
   }
   if (!ok) atomicExch(P.err, 2);
 }

@@ -76,6 +76,15 @@ def make_case(name):
         src = np.concatenate([line, cloud, edge])
         rec = wl.receiver_line(shape, h, 9, 16)
         return dict(shape=shape, h=h, so=8, nt=60, nbl=5, vp=vp, src=src, rec=rec, f0=55.0)
+    if name == "tall_so8":
+        # a grid tall along axis 1, so that with few CTAs per launch the
+        # blocked sweep's bands are pipelined across time tiles
+        shape, h = (30, 96, 70), (10.0, 10.0, 10.0)
+        vp = wl.layered_vp(shape, 43, nlayers=4, nblobs=3)
+        src = np.array([[150.3, 100.7, 340.2], [120.0, 830.0, 95.5], [41.0, 520.2, 600.9]])
+        rec = np.concatenate([wl.receiver_line(shape, h, 11, 24),
+                              np.array([[10.0, 945.0, 100.0], [250.0, 15.0, 680.0]])])
+        return dict(shape=shape, h=h, so=8, nt=61, nbl=5, vp=vp, src=src, rec=rec, f0=55.0)
     raise KeyError(name)
 
 
@@ -138,6 +147,31 @@ def test_blocked_bitwise_equals_onestep(tb, name, T, opts):
         np.testing.assert_array_equal(a, b)
     tr_o, u_o, _ = oracle_run(name, c, dt, wav)
     assert rel(got[1], u_o) <= TOL and rel(got[0], tr_o) <= TOL
+
+
+# Launches limited to a few CTAs: bands pipelined across time tiles, most
+# launches holding the last band of one time tile and the first rows of the
+# next (two time tiles in flight, receiver rows recorded out of step order).
+@pytest.mark.parametrize("name,T,band_ctas", [("tall_so8", 3, 10), ("tall_so8", 2, 8), ("tall_so8", 4, 10),
+                                              ("tall_so8", 3, 6), ("ragged_so4", 2, 9), ("ragged_so4", 4, 12)])
+def test_pipelined_bands_bitwise_equal_onestep(tb, name, T, band_ctas):
+    c, dt, wav = setup(name)
+    ref = gpu_run(tb, c, dt, wav, "onestep", x_chunks=1)
+    got = gpu_run(tb, c, dt, wav, "blocked", time_tile=T, band_ctas=band_ctas)
+    for a, b in zip(got, ref):
+        np.testing.assert_array_equal(a, b)
+    tr_o, u_o, _ = oracle_run(name, c, dt, wav)
+    assert rel(got[1], u_o) <= TOL and rel(got[0], tr_o) <= TOL
+
+
+def test_pipelined_launch_too_small_is_rejected(tb):
+    import torch
+    c, dt, wav = setup("tall_so8")
+    p = tb.Propagator(c["shape"], c["h"], c["so"], nbl=c["nbl"], time_tile=3, band_ctas=2)
+    p.set_model(torch.from_numpy(np.ascontiguousarray(c["vp"])).cuda(), dt=dt)
+    with pytest.raises(tb.TBError):
+        p.forward(6, schedule="blocked")
+    p.close()
 
 
 @pytest.mark.parametrize("opts", [dict(x_chunks=1), dict(x_chunks=5), dict(y_bands=2, x_chunks=2)])

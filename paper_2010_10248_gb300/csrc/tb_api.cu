@@ -2,6 +2,7 @@
 // setup arithmetic (FD weights, CFL, sponge, Ricker), pass planning for the
 // blocked sweep, and the time loop of tb_forward.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1314,6 +1315,9 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
     const int last = L + 1 < pl.launch_first.size() ? pl.launch_first[L + 1] : (int)pl.launch_passes.size();
     P.pass = h->d_pass + pass_off + first;
     P.npass = last - first;
+    P.set1_cta0 = INT_MAX;
+    for (int i = first; i < last; ++i)
+      if (pl.launch_passes[i].set != 0) P.set1_cta0 = std::min(P.set1_cta0, pl.launch_passes[i].cta0);
     P.prog_base = h->prog_base;
     int maxsteps = 0;
     for (int i = first; i < last; ++i) {
@@ -1558,6 +1562,7 @@ static int runner_step(tb_handle* h, StepRunner* r, int cur, int prev, int step,
   S.step0 = step;
   P.tm_c = h->tm_c2;
   P.rec_cap = 1;
+  P.set1_cta0 = INT_MAX;
   const Plan& pl = r->p1;
   for (size_t L = 0; L < pl.launch_first.size(); ++L) {
     const int first = pl.launch_first[L];

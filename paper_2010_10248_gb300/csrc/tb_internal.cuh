@@ -28,7 +28,8 @@ struct PassDesc {
   int yo0, yo1;  // rows whose results this pass owns (written out)
   int xc0, xc1;  // planes (axis 0) the first fused step computes
   int xo0, xo1;  // planes whose results this pass owns
-  int set;       // time tile of the pass: SweepParams::set[set]
+  int set;       // time tile of the pass: SweepParams::set[set] (set-1 passes
+                 // follow the set-0 passes of a launch)
 };
 
 // The fields and first step of one time tile (T fused steps from step n).
@@ -47,6 +48,8 @@ struct SweepSet {
 // k + 1) when bands of the blocked sweep are pipelined across time tiles.
 struct SweepParams {
   SweepSet set[2];
+  int set1_cta0;                // CTAs from this index on compute set[1]
+                                // (INT_MAX: the launch holds set[0] only)
   CUtensorMap tm_c;             // c2: TY x 64 tiles
   int n0, n1, n2, n2p;          // grid, and row pitch of the padded fields
   const float* c2;              // dt^2 vp^2 (padded layout)

@@ -313,7 +313,7 @@ __device__ __forceinline__ float2 pair_term2(float2 acc, float2 w2, float2 a, fl
 }
 
 // ----------------------------------------------------------------- kernel --
-template <int R, int T, int TY, int SK = 0>
+template <int R, int T, int TY, int SK = 0, bool TWO = false>
 __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 : 1)
     sweep_kernel(const __grid_constant__ SweepParams P) {
   using C = SweepCfg<R, T, TY, SK>;
@@ -342,9 +342,11 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
   for (int i = 1; i < P.npass; ++i)
     if (P.pass[i].cta0 <= b) pi = i;
   const PassDesc pd = P.pass[pi];
-  // the pass's time tile (selected field by field: constant-bank operands,
-  // no indexed access to the parameter block)
-  const bool s1 = T > 1 && pd.set != 0;
+  // the pass's time tile: launches holding two time tiles run the TWO
+  // instantiation, which selects the fields by the block index (the select
+  // costs ~2 % more instructions in the fused steps, so single-tile
+  // launches take the other one)
+  const bool s1 = TWO && b >= P.set1_cta0;
   const int step0 = s1 ? P.set[1].step0 : P.set[0].step0;
   float* const out0 = s1 ? P.set[1].out0 : P.set[0].out0;
   float* const out1 = s1 ? P.set[1].out1 : P.set[0].out1;
@@ -949,11 +951,11 @@ struct SweepTraits {
   using Cfg = SweepCfg<R, T, TY, SK>;
 };
 
-template <int R, int T, int SK>
+template <int R, int T, int SK, bool TWO>
 cudaError_t sweep_launch_t(const SweepParams& p, int nctas, bool cooperative, cudaStream_t st) {
   using Tr = SweepTraits<R, T, SK>;
   using Cf = typename Tr::Cfg;
-  auto fn = sweep_kernel<R, T, Tr::TY, SK>;
+  auto fn = sweep_kernel<R, T, Tr::TY, SK, TWO>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
@@ -969,11 +971,11 @@ cudaError_t sweep_launch_t(const SweepParams& p, int nctas, bool cooperative, cu
   return cudaGetLastError();
 }
 
-template <int R, int T, int SK>
+template <int R, int T, int SK, bool TWO>
 cudaError_t sweep_occupancy_t(int* per_sm) {
   using Tr = SweepTraits<R, T, SK>;
   using Cf = typename Tr::Cfg;
-  auto fn = sweep_kernel<R, T, Tr::TY, SK>;
+  auto fn = sweep_kernel<R, T, Tr::TY, SK, TWO>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, Cf::NTHREADS, Cf::SMEM);
@@ -999,8 +1001,21 @@ void sweep_shape_t(SweepShape* s) {
 template <int R, int T, int SK>
 cudaError_t sweep_do(int what, const SweepParams* p, int nctas, bool coop, cudaStream_t st, int* per_sm,
                      SweepShape* s) {
-  if (what == 0) return sweep_launch_t<R, T, SK>(*p, nctas, coop, st);
-  if (what == 1) return sweep_occupancy_t<R, T, SK>(per_sm);
+  constexpr bool kTwo = T > 1 && SK == 0;  // passes of two time tiles exist
+  if (what == 0) {
+    if constexpr (kTwo)
+      if (p->set1_cta0 < nctas) return sweep_launch_t<R, T, SK, true>(*p, nctas, coop, st);
+    return sweep_launch_t<R, T, SK, false>(*p, nctas, coop, st);
+  }
+  if (what == 1) {
+    cudaError_t e = sweep_occupancy_t<R, T, SK, false>(per_sm);
+    if constexpr (kTwo) {
+      int two = 0;
+      if (e == cudaSuccess) e = sweep_occupancy_t<R, T, SK, true>(&two);
+      if (e == cudaSuccess) *per_sm = *per_sm < two ? *per_sm : two;
+    }
+    return e;
+  }
   sweep_shape_t<R, T, SK>(s);
   return cudaSuccess;
 }

@@ -396,7 +396,8 @@ def run_native(args):
     flops_per_launch = fl * points_per_launch * T
     roof = {"bound": "alu", "achieved": upd_per_s * fl / 1e12, "peak": fpk, "unit": "TFLOP/s",
             "frac": upd_per_s * fl / 1e12 / fpk,
-            "traffic": counters.get("dram_bytes_per_launch_full_size"),
+            "traffic": (counters.get("dram_bytes_per_launch_full_size")
+                        if counters.get("grid_edge") == args.size else None),
             "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz",
             "kernel": f"sweep_kernel<R={w.so // 2},T={T}>", "flops_per_point_step": fl,
             "flops_per_launch": flops_per_launch, "bytes_per_launch": bytes_per_launch,

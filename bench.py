@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--adjoint", action="store_true",
                     help="vp gradient of the 256^3 so8 shot (800 steps, 32 checkpoints) instead")
+    ap.add_argument("--many-sources", action="store_true",
+                    help="blocked vs one-step with many sources on a plane and spread through the grid")
     ap.add_argument("--physics", default="acoustic", choices=["acoustic", "tti", "elastic"],
                     help="tti / elastic: the 384^3 so8 500-step TTI or elastic workload, one-step "
                          "schedule (the headline line is the acoustic one)")
@@ -701,6 +703,92 @@ def run_storage(args):
     prop.close()
 
 
+def run_many_sources(args):
+    """The 512^3 so8 benchmark grid with many sources (Sec. V-C): sources on a
+    horizontal plane (sparse) and uniformly spread through the grid (dense),
+    1 .. 32768 of them.  Per case: set_sources (inspector, decomposition,
+    event table) timed on the host, then the blocked (T = 3) and the one-step
+    schedule timed with CUDA events; the line's value is the blocked rate of
+    the densest case."""
+    import torch
+    import paper_2010_10248_gb300 as tb
+    from paper_2010_10248_gb300 import build as tbbuild
+    from paper_2010_10248_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    tbbuild.build()
+    tb.load()
+    nt = args.nt if args.nt != 1000 else 300
+    w = wl.acoustic_512_so8(shape=(args.size,) * 3, nt=nt)
+    N = int(np.prod(w.shape))
+    dev = torch.device("cuda", 0)
+    T = args.time_tile
+    prop = tb.Propagator(w.shape, w.spacing, w.so, nbl=w.nbl, time_tile=T, profile=True)
+    st = torch.cuda.current_stream()
+    prop.set_model(torch.from_numpy(w.vp).to(dev))
+    dt = prop.dt
+    prop.set_receivers(w.rec_xyz)
+    traces = torch.empty((nt, len(w.rec_xyz)), dtype=torch.float32, device=dev)
+    base_ws = None
+    cases = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = tb.tb_launch_count()
+    for layout in ("plane", "dense"):
+        for n in (1, 64, 1024, 8192, 32768):
+            if layout == "plane":
+                src = wl.source_plane(w.shape, w.spacing, 101, n, depth_cells=w.nbl + 10, margin_cells=w.nbl)
+            else:
+                src = wl.source_cloud(w.shape, w.spacing, 102, n, margin_cells=w.nbl)
+            wav = np.repeat(wl.ricker(w.f0, dt, nt)[None, :], n, axis=0).astype(np.float32)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            prop.set_sources(src, wav)
+            torch.cuda.synchronize()
+            set_s = time.perf_counter() - t0
+            ws = tb.tb_workspace_bytes(prop.h)
+            if base_ws is None:
+                base_ws = ws
+            rates = {}
+            for sched in ("blocked", "onestep"):
+                prop.forward(nt, traces, schedule=sched)
+                ts = []
+                for _ in range(max(1, args.steps // 2)):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    prop.forward(nt, traces, schedule=sched)
+                    e1.record(st)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                kn, kms = prop.kernel_time(0)
+                rates[sched] = N * nt / (min(ts) * 1e-3) / 1e9
+                rates[sched + "_kernel_ms_per_launch"] = kms / max(kn, 1)
+            cases.append({"layout": layout, "sources": n, "grid_points": int(tb.tb_get_source_points(prop.h)),
+                          "blocked": rates["blocked"], "onestep": rates["onestep"],
+                          "speedup": rates["blocked"] / rates["onestep"], "set_sources_s": set_s,
+                          "source_table_bytes": int(ws - base_ws)})
+    clk = clocks.stop()
+    worst = cases[-1]
+    fl = alg_flops(w.so)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fpk, mhz = fp32_peak_tflops(nsm)
+    line = {"metric": METRIC, "value": worst["blocked"], "unit": UNIT, "n_gpus": 1,
+            "steps": max(1, args.steps // 2), "warmup": 1, "ms_per_step": N * nt / (worst["blocked"] * 1e9) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{w.name}, many sources (plane / dense, 1..32768)", "grid": list(w.shape),
+                       "space_order": w.so, "nt": nt, "time_tile": T, "receivers": len(w.rec_xyz),
+                       "value_case": "dense, 32768 sources, blocked",
+                       "step": "forward(nt) (set_sources timed separately per case)"},
+            "gpu_launches": int(tb.tb_launch_count() - l0), "clocks": clk,
+            "roofline": {"bound": "alu", "achieved": worst["blocked"] * fl / 1e3, "peak": fpk, "unit": "TFLOP/s",
+                         "frac": worst["blocked"] * fl / 1e3 / fpk, "traffic": None,
+                         "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz",
+                         "note": "end-to-end forward rate x algorithmic flops"},
+            "cpu_baseline": None, "cases": cases}
+    print(json.dumps(line), flush=True)
+    prop.close()
+
+
 def run_adjoint(args):
     """vp gradient of the acoustic shot at 256^3 so8 (the 512^3 recipe), 800
     steps, 32 checkpoints: one step = tb_adjoint_gradient (forward with
@@ -823,6 +911,9 @@ def main():
         return
     if args.impl == "native" and args.adjoint:
         run_adjoint(args)
+        return
+    if args.impl == "native" and args.many_sources:
+        run_many_sources(args)
         return
     if args.impl == "reference":
         run_reference(args)

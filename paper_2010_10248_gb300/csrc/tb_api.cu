@@ -98,6 +98,7 @@ struct tb_handle {
   float2* src_ev = nullptr;     // [src_nt][nev]
   int64_t nev = 0;
   int npair = 0;
+  int ev_max_span = 0;          // longest plane range of a column pair
   bool have_src = false;
   // receivers
   PointTables rec;
@@ -660,6 +661,7 @@ extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int 
   dfree(h->src_ev, st);
   h->src_ev = nullptr;
   h->nev = 0;
+  h->ev_max_span = 0;
   h->src_nt = nsrc > 0 ? nt : 0;
   cudaError_t e = cudaSuccess;
   int* d_slot = nullptr;
@@ -699,6 +701,7 @@ extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int 
           while (g1 < np && key(ord[g1]).first == pr) ++g1;
           const int64_t xf = key(ord[g]).second, xl = key(ord[g1 - 1]).second, span = xl - xf + 1;
           evp[pr] = make_int2((int)(xf | (span << 16)), (int)base);
+          h->ev_max_span = std::max(h->ev_max_span, (int)span);
           for (int64_t i = g; i < g1; ++i)
             slot[ord[i]] = (int)(2 * (base + key(ord[i]).second - xf) + (lin[ord[i]] % n2) % 2);
           base += span;
@@ -1243,6 +1246,9 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   P.src_ev = h->src_ev;
   P.nev = h->nev;
   P.npair = h->npair;
+  // a column pair injecting over more than 8 planes loads in most of its
+  // stream steps: the blocked sweep then prefetches (a single source spans 2)
+  P.src_prefetch = src_on && h->ev_max_span > 8;
   const bool rec_on = h->have_rec && h->rec.npts > 0 && nrec > 0;
   P.r_colptr = rec_on ? h->rec.colptr : nullptr;
   P.r_ent = rec_on ? h->rec.ent : nullptr;

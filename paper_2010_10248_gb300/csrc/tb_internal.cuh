@@ -63,6 +63,8 @@ struct SweepParams {
   const float2* src_ev;         // [nt][nev]
   int64_t nev;
   int npair;
+  int src_prefetch;             // blocked sweep: load a stream step's injections
+                                // at its top (some pair spans many planes)
   // grid-aligned receivers
   const int* r_colptr;
   const int2* r_ent;

@@ -313,7 +313,7 @@ __device__ __forceinline__ float2 pair_term2(float2 acc, float2 w2, float2 a, fl
 }
 
 // ----------------------------------------------------------------- kernel --
-template <int R, int T, int TY, int SK = 0, bool TWO = false>
+template <int R, int T, int TY, int SK = 0, bool TWO = false, bool PRE = false>
 __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 : 1)
     sweep_kernel(const __grid_constant__ SweepParams P) {
   using C = SweepCfg<R, T, TY, SK>;
@@ -761,11 +761,22 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
   // branch; with several, the test stays branch-light so that the fused
   // steps' code is not split.
   const float2* evrow = ev_n > 0 ? P.src_ev + (size_t)step0 * P.nev + ev_b : nullptr;
+  // PRE (sources with long plane ranges): the T values of a stream step are
+  // loaded at its top (inj), so that their latency overlaps the steps'
+  // arithmetic instead of stalling the fused step that adds them (a column
+  // pair whose range spans many planes loads in every stream step, and its
+  // warp's stalls held back the whole lockstep band).  With short ranges
+  // (single sources) the in-step load is cheaper than the prefetch.
+  float2 inj[PRE ? T : 1];
   auto inject = [&](int k, int q, float2& un) {
     if constexpr (T == 1)
       if (ev_n == 0) return;
     const unsigned off = (unsigned)(q - ev_x);
-    if (off < (unsigned)ev_n) un = __fadd2_rn(un, __ldg(evrow + (size_t)k * P.nev + off));
+    if constexpr (PRE) {
+      if (off < (unsigned)ev_n) un = __fadd2_rn(un, inj[k]);
+    } else {
+      if (off < (unsigned)ev_n) un = __fadd2_rn(un, __ldg(evrow + (size_t)k * P.nev + off));
+    }
   };
 
   int su = (jstart - pu0) % C::NU;  // ring slot of u^n plane j
@@ -774,6 +785,13 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
 #pragma unroll 1
   for (int j = jstart; j <= jend && ok; ++j) {
     const bool act0 = j >= pd.xc0 && j < pd.xc1;
+    if constexpr (PRE) {
+#pragma unroll
+      for (int k = 0; k < T; ++k) {
+        const unsigned off = (unsigned)(j - k * R - ev_x);
+        inj[k] = off < (unsigned)ev_n ? __ldg(evrow + (size_t)k * P.nev + off) : make_float2(0.f, 0.f);
+      }
+    }
     const float bxc = bxn;
     bxn = __ldg(&P.damp_b[min(max(j + 1 - kl * R, 0), P.n0 - 1)]);
     int suR = su + R;
@@ -951,11 +969,11 @@ struct SweepTraits {
   using Cfg = SweepCfg<R, T, TY, SK>;
 };
 
-template <int R, int T, int SK, bool TWO>
+template <int R, int T, int SK, bool TWO, bool PRE>
 cudaError_t sweep_launch_t(const SweepParams& p, int nctas, bool cooperative, cudaStream_t st) {
   using Tr = SweepTraits<R, T, SK>;
   using Cf = typename Tr::Cfg;
-  auto fn = sweep_kernel<R, T, Tr::TY, SK, TWO>;
+  auto fn = sweep_kernel<R, T, Tr::TY, SK, TWO, PRE>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
@@ -971,11 +989,11 @@ cudaError_t sweep_launch_t(const SweepParams& p, int nctas, bool cooperative, cu
   return cudaGetLastError();
 }
 
-template <int R, int T, int SK, bool TWO>
+template <int R, int T, int SK, bool TWO, bool PRE>
 cudaError_t sweep_occupancy_t(int* per_sm) {
   using Tr = SweepTraits<R, T, SK>;
   using Cf = typename Tr::Cfg;
-  auto fn = sweep_kernel<R, T, Tr::TY, SK, TWO>;
+  auto fn = sweep_kernel<R, T, Tr::TY, SK, TWO, PRE>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, Cf::NTHREADS, Cf::SMEM);
@@ -1002,17 +1020,34 @@ template <int R, int T, int SK>
 cudaError_t sweep_do(int what, const SweepParams* p, int nctas, bool coop, cudaStream_t st, int* per_sm,
                      SweepShape* s) {
   constexpr bool kTwo = T > 1 && SK == 0;  // passes of two time tiles exist
+  // prefetched injections, where the registers allow (T - 1 axis-0 queues of
+  // 2r + 1 pairs up to 18 pairs; r = 4, T = 4 spilled)
+  constexpr bool kPre = kTwo && (T - 1) * (2 * R + 1) <= 18;
   if (what == 0) {
-    if constexpr (kTwo)
-      if (p->set1_cta0 < nctas) return sweep_launch_t<R, T, SK, true>(*p, nctas, coop, st);
-    return sweep_launch_t<R, T, SK, false>(*p, nctas, coop, st);
+    const bool two = p->set1_cta0 < nctas, pre = p->src_prefetch != 0;
+    if constexpr (kTwo) {
+      if constexpr (kPre) {
+        if (pre) return two ? sweep_launch_t<R, T, SK, true, true>(*p, nctas, coop, st)
+                            : sweep_launch_t<R, T, SK, false, true>(*p, nctas, coop, st);
+      }
+      if (two) return sweep_launch_t<R, T, SK, true, false>(*p, nctas, coop, st);
+    }
+    (void)two;
+    (void)pre;
+    return sweep_launch_t<R, T, SK, false, false>(*p, nctas, coop, st);
   }
   if (what == 1) {
-    cudaError_t e = sweep_occupancy_t<R, T, SK, false>(per_sm);
+    cudaError_t e = sweep_occupancy_t<R, T, SK, false, false>(per_sm);
+    int o = 0;
     if constexpr (kTwo) {
-      int two = 0;
-      if (e == cudaSuccess) e = sweep_occupancy_t<R, T, SK, true>(&two);
-      if (e == cudaSuccess) *per_sm = *per_sm < two ? *per_sm : two;
+      if (e == cudaSuccess) e = sweep_occupancy_t<R, T, SK, true, false>(&o);
+      if (e == cudaSuccess) *per_sm = *per_sm < o ? *per_sm : o;
+    }
+    if constexpr (kPre) {
+      if (e == cudaSuccess) e = sweep_occupancy_t<R, T, SK, false, true>(&o);
+      if (e == cudaSuccess) *per_sm = *per_sm < o ? *per_sm : o;
+      if (e == cudaSuccess) e = sweep_occupancy_t<R, T, SK, true, true>(&o);
+      if (e == cudaSuccess) *per_sm = *per_sm < o ? *per_sm : o;
     }
     return e;
   }

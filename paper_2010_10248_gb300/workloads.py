@@ -114,6 +114,30 @@ def receiver_plane(shape, spacing, seed: int, nx: int, ny: int, depth_cells: flo
     return np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], axis=1)
 
 
+def source_plane(shape, spacing, seed: int, n: int, depth_cells: float, margin_cells: float) -> np.ndarray:
+    """n sources on a horizontal plane (fixed axis-2 depth): a square lattice
+    over axes 0 and 1 inside the margin, each point with a seeded sub-cell
+    offset (the sparse many-source case of Sec. V-C)."""
+    g = rng(seed)
+    k = max(1, int(math.ceil(math.sqrt(n))))
+    lo0, hi0 = margin_cells, shape[0] - 2 - margin_cells
+    lo1, hi1 = margin_cells, shape[1] - 2 - margin_cells
+    X, Y = np.meshgrid(np.linspace(lo0, hi0, k), np.linspace(lo1, hi1, k), indexing="ij")
+    off = g.uniform(0.05, 0.95, size=(k * k, 3))
+    z = np.full(k * k, float(depth_cells))
+    pts = np.stack([np.floor(X.ravel()), np.floor(Y.ravel()), z], axis=1) + off
+    return pts[:n] * np.asarray(spacing, dtype=np.float64)
+
+
+def source_cloud(shape, spacing, seed: int, n: int, margin_cells: float) -> np.ndarray:
+    """n sources uniformly random in the box inside the margin (the dense
+    many-source case of Sec. V-C)."""
+    g = rng(seed)
+    lo = np.full(3, float(margin_cells))
+    hi = np.array([shape[d] - 1 - margin_cells for d in range(3)], dtype=np.float64)
+    return g.uniform(lo, hi, size=(n, 3)) * np.asarray(spacing, dtype=np.float64)
+
+
 @dataclass
 class Workload:
     """One propagation problem: grid, model, geometry and wavelet recipe."""

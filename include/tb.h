@@ -201,6 +201,21 @@ int tb_get_receiver_points(tb_handle* h, int64_t* npts, int64_t* lin, int32_t* c
 /* Device bytes held by the handle (fields, model, tables, scratch). */
 size_t tb_workspace_bytes(const tb_handle* h);
 
+/* Host-side schedule of the blocked sweep with bands pipelined across time
+ * tiles (the default when y_bands = 0 and x_chunks <= 1; Sec. II-B's temporal
+ * blocking, split into co-resident bands).  No GPU is needed.  For a grid of
+ * n1 x n2 points on axes 1 and 2, space order 4, 8 or 12, time_tile >= 2 fused
+ * steps, n_tiles time tiles and launches of at most `cap` CTAs (one 16 x 64
+ * tile each), writes up to max_passes passes to `passes` (caller-owned,
+ * 7 ints each, in launch order): launch index, time tile, first and end owned
+ * row of axis 1, first computed row, tile rows, first CTA in the launch.  A
+ * pass computes its owned rows plus (time_tile - 1) r rows on each side
+ * (clipped), with r = space_order / 2.  Returns the number of passes (which
+ * may exceed max_passes), or -TB_EINVAL for bad arguments or a cap too small
+ * for one band of the grid. */
+int tb_plan_pipeline(int n1, int n2, int space_order, int time_tile, int n_tiles, int cap, int* passes,
+                     int max_passes);
+
 /* With opt.profile = 1: number of propagator launches of the last
  * tb_forward and their summed device time in ms, measured with CUDA events
  * on the launching stream; kind 0 = propagator sweeps, 1 = receiver

@@ -67,6 +67,8 @@ _SIGS = {
     "tb_selftest_wait": (C.c_int, [C.c_double, _vp]),
     "tb_measure_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
     "tb_launch_count": (C.c_uint64, []),
+    "tb_plan_pipeline": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.POINTER(C.c_int), C.c_int]),
     "tb_inspect_points_noalloc": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int,
                                             _vp, _vp, _vp, _vp]),
 }
@@ -187,6 +189,21 @@ def tb_get_receiver_points(h, lin=None, corner_id=None, corner_w=None):
 
 def tb_workspace_bytes(h):
     return load().tb_workspace_bytes(h)
+
+
+def tb_plan_pipeline(n1, n2, space_order, time_tile, n_tiles, cap):
+    """The pipelined blocked sweep's passes as an int array [npass, 7]: launch,
+    time tile, first / end owned row, first computed row, tile rows, first
+    CTA (host only, no GPU)."""
+    import numpy as np
+    lib = load()
+    n = lib.tb_plan_pipeline(int(n1), int(n2), int(space_order), int(time_tile), int(n_tiles), int(cap), None, 0)
+    if n < 0:
+        raise TBError(-n, "tb_plan_pipeline: invalid arguments or cap too small")
+    out = np.zeros((max(n, 1), 7), dtype=np.int32)
+    lib.tb_plan_pipeline(int(n1), int(n2), int(space_order), int(time_tile), int(n_tiles), int(cap),
+                         out.ctypes.data_as(C.POINTER(C.c_int)), n)
+    return out[:n]
 
 
 def tb_kernel_time(h, kind=0):

@@ -863,18 +863,10 @@ static int plan_sweep(tb_handle* h, int T, Plan* pl) {
 // k's band in the launch reads.  Rows a pass computes beyond what its owned
 // rows depend on may read fields in flight; they are never written out.  A
 // grid whose time tile fits one launch gets one launch per tile.
-static int plan_pipeline(tb_handle* h, int T, int K, Plan* pl) {
-  const int R = h->R;
-  SweepShape sh;
-  if (!sweep_shape(R, T, &sh, 0)) return fail(h, TB_EINVAL, "unsupported time tile %d", T);
-  int per_sm = 0;
-  cudaError_t e = sweep_max_ctas(R, T, &per_sm, 0);
-  if (e != cudaSuccess) return cuda_fail(h, e, "occupancy");
-  if (per_sm < 1) return fail(h, TB_ECUDA, "sweep kernel does not fit on an SM");
-  int cap = per_sm * h->num_sms;
-  if (h->opt.band_ctas > 0) cap = std::min(cap, h->opt.band_ctas);
-  const int n0 = (int)h->n[0], n1 = (int)h->n[1], n2 = (int)h->n[2];
-  const int TY = sh.TY, TZ = 64;
+// The planner itself (host only): returns 0, or -1 when a launch of `cap`
+// CTAs cannot hold a band of the grid.
+static int pipeline_passes(int n0, int n1, int n2, int R, int T, int TY, int K, int cap, Plan* pl) {
+  const int TZ = 64;
   const int ntz = (n2 + TZ - 1) / TZ;
   const int halo = (T - 1) * R, reach = T * R;
   const int tiles_cap = cap / ntz;  // tile rows per launch
@@ -905,9 +897,7 @@ static int plan_pipeline(tb_handle* h, int T, int K, Plan* pl) {
   int k = 0, y = 0;  // rows [0, y) of time tile k are done
   while (k < K) {
     const int y1 = last_row(y, tiles_cap);
-    if (y1 <= y)
-      return fail(h, TB_EINVAL, "a blocked launch of %d CTAs cannot hold a band of this grid (%d tile columns)", cap,
-                  ntz);
+    if (y1 <= y) return -1;
     pl->launch_first.push_back((int)pl->launch_passes.size());
     pl->launch_tile.push_back(k);
     PassDesc a = make(0, y, y1);
@@ -931,7 +921,51 @@ static int plan_pipeline(tb_handle* h, int T, int K, Plan* pl) {
     pl->launch_ctas.push_back(ctas);
     pl->max_ctas = std::max(pl->max_ctas, ctas);
   }
+  return 0;
+}
+
+static int plan_pipeline(tb_handle* h, int T, int K, Plan* pl) {
+  SweepShape sh;
+  if (!sweep_shape(h->R, T, &sh, 0)) return fail(h, TB_EINVAL, "unsupported time tile %d", T);
+  int per_sm = 0;
+  cudaError_t e = sweep_max_ctas(h->R, T, &per_sm, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "occupancy");
+  if (per_sm < 1) return fail(h, TB_ECUDA, "sweep kernel does not fit on an SM");
+  int cap = per_sm * h->num_sms;
+  if (h->opt.band_ctas > 0) cap = std::min(cap, h->opt.band_ctas);
+  if (pipeline_passes((int)h->n[0], (int)h->n[1], (int)h->n[2], h->R, T, sh.TY, K, cap, pl) != 0)
+    return fail(h, TB_EINVAL, "a blocked launch of %d CTAs cannot hold a band of this grid (%d tile columns)", cap,
+                (int)((h->n[2] + 63) / 64));
   return TB_OK;
+}
+
+extern "C" int tb_plan_pipeline(int n1, int n2, int space_order, int time_tile, int n_tiles, int cap, int* passes,
+                                int max_passes) {
+  const int R = space_order / 2;
+  if ((space_order != 4 && space_order != 8 && space_order != 12) || time_tile < 2 || n1 < 1 || n2 < 1 ||
+      n_tiles < 0 || cap < 1 || max_passes < 0 || (max_passes > 0 && !passes))
+    return -TB_EINVAL;
+  SweepShape sh;
+  if (!sweep_shape(R, time_tile, &sh, 0)) return -TB_EINVAL;
+  Plan pl;
+  if (pipeline_passes(1, n1, n2, R, time_tile, sh.TY, n_tiles, cap, &pl) != 0) return -TB_EINVAL;
+  const int np = (int)pl.launch_passes.size();
+  for (int L = 0, i = 0; L < (int)pl.launch_first.size(); ++L) {
+    const int last = L + 1 < (int)pl.launch_first.size() ? pl.launch_first[L + 1] : np;
+    for (; i < last; ++i) {
+      if (i >= max_passes) continue;
+      const PassDesc& d = pl.launch_passes[i];
+      int* o = passes + 7 * (size_t)i;
+      o[0] = L;
+      o[1] = pl.launch_tile[L] + d.set;
+      o[2] = d.yo0;
+      o[3] = d.yo1;
+      o[4] = d.yb0;
+      o[5] = d.nty;
+      o[6] = d.cta0;
+    }
+  }
+  return np;
 }
 
 static int ensure_capacity(tb_handle* h, int T, const Plan& pl, int nt, bool host_traces, int nrec,

@@ -9,6 +9,7 @@
 // (the centred Laplacian is symmetric), and the gradient of <d, r> is
 //   d/dm(p) = sum_k lam^k(p) c2 [2 g (u^{k-1} - u^{k-2}) - c2 L u^{k-1}](p)
 //             / (dt^2 (1+g)^2)  -  sum_k lam^k(p) c2(p) S^{k-1}(p) c2(p)/dt^2,
+// evaluated through the recurrence from three stored states (k_adj_grad),
 //   d/dvp = d/dm * (-2/vp^3),  vp = sqrt(c2)/dt,
 // accumulated in FP64 (the per-step term in FP32).  One plane of columns per
 // block; a neighbour load tests only the coordinate it moves along.
@@ -106,10 +107,14 @@ __global__ void k_adj_step(PhysGrid g, LapW lw, const float* __restrict__ w, con
   lam0[i0] = __fadd_rn(l, div_sponge(__fmaf_rn(2.f, lam1[i0], __fmul_rn(__fsub_rn(gd, 1.f), lam2[i0])), opg));
 }
 
-// grad_m += lam^k c2 [2 g (u1 - u2) - c2 L u1] / (dt^2 (1+g)^2): the term in
-// FP32, the sum over steps in FP64
-template <int R>
-__global__ void k_adj_grad(PhysGrid g, LapW lw, float inv_dt2, const float* __restrict__ lam0,
+// grad_m += lam^k c2 [2 g (u^{k-1} - u^{k-2}) - c2 L u^{k-1}] / (dt^2 (1+g)^2).  By the
+// forward recurrence, (1+g) (u^k - c2 S^{k-1}) = c2 L u^{k-1} + 2 u^{k-1} - (1-g) u^{k-2},
+// the bracket equals -(1+g) [(u^k - c2 S^{k-1}) - 2 u^{k-1} + u^{k-2}]: the term is
+// -lam^k c2 [(u^k - u^{k-1}) - (u^{k-1} - u^{k-2})] / (dt^2 (1+g)), pointwise on three
+// stored states (no stencil), with the c2 S part added at the source points
+// (k_adj_grad_src).  The term in FP32 (the differences of neighbouring states
+// first), the sum over steps in FP64.
+__global__ void k_adj_grad(PhysGrid g, float inv_dt2, const float* __restrict__ lam0, const float* __restrict__ u0,
                            const float* __restrict__ u1, const float* __restrict__ u2, const float* __restrict__ c2,
                            const float* __restrict__ damp_b, double* __restrict__ gm) {
   const AdjCol c = adj_col(g);
@@ -118,23 +123,28 @@ __global__ void k_adj_grad(PhysGrid g, LapW lw, float inv_dt2, const float* __re
   const size_t i0 = aidx(g, x, c.y, c.z);
   const float cc = __ldg(c2 + i0);
   const float gd = damp_g(g, damp_b, cc, x, c.y, c.z);
-  const float lu = lap_at<R>(g, u1, lw, x, c.y, c.z);
-  const float opg = __fadd_rn(1.f, gd);
-  const float t = __fmaf_rn(__fmul_rn(2.f, gd), __fsub_rn(__ldg(u1 + i0), __ldg(u2 + i0)), -__fmul_rn(cc, lu));
-  const float dr = div_sponge(__fmul_rn(__fmul_rn(cc, t), inv_dt2), __fmul_rn(opg, opg));
-  gm[i0] += (double)__ldg(lam0 + i0) * (double)dr;
+  const float b1 = __ldg(u1 + i0);
+  const float d2 = __fsub_rn(__fsub_rn(__ldg(u0 + i0), b1), __fsub_rn(b1, __ldg(u2 + i0)));
+  const float dr = div_sponge(__fmul_rn(__fmul_rn(cc, d2), inv_dt2), __fadd_rn(1.f, gd));
+  gm[i0] -= (double)__ldg(lam0 + i0) * (double)dr;
 }
 
-// source term: grad_m(p_id) -= lam^k c2(p) src_dcmp[k-1][id] / dt^2  (src_dcmp = c2 S)
+// source points: the term of M = c2 (d(c2 S)/dm = -c2 (c2 S)/dt^2) and the c2 S
+// part of the imaging term, +lam^k c2 (c2 S) / (dt^2 (1+g)); together
+// grad_m(p_id) -= lam^k c2 (c2 S^{k-1}) g / (dt^2 (1+g))  (src_dcmp = c2 S; zero
+// outside the sponge)
 __global__ void k_adj_grad_src(PhysGrid g, int64_t npts, const int64_t* __restrict__ lin,
                                const float* __restrict__ dcmp_row, double inv_dt2, const float* __restrict__ lam0,
-                               const float* __restrict__ c2, double* __restrict__ gm) {
+                               const float* __restrict__ c2, const float* __restrict__ damp_b,
+                               double* __restrict__ gm) {
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= npts) return;
   const int64_t l = lin[id];
   const int z = (int)(l % g.n2), y = (int)((l / g.n2) % g.n1), x = (int)(l / ((int64_t)g.n1 * g.n2));
   const size_t i0 = aidx(g, x, y, z);
-  gm[i0] -= (double)lam0[i0] * (double)c2[i0] * (double)dcmp_row[id] * inv_dt2;
+  const float cc = c2[i0];
+  const double gd = (double)damp_g(g, damp_b, cc, x, y, z);
+  gm[i0] -= (double)lam0[i0] * (double)cc * (double)dcmp_row[id] * inv_dt2 * (gd / (1.0 + gd));
 }
 
 // source-wavelet gradient row: value at each source point of M lam = c2 lam
@@ -182,28 +192,18 @@ cudaError_t adjoint_step(int R, const PhysGrid& g, const LapW& lw, const float* 
   return cudaErrorInvalidValue;
 }
 
-template <int R>
-static cudaError_t adj_grad_r(const PhysGrid& g, const LapW& lw, double dt, const float* lam0, const float* u1,
-                              const float* u2, const float* c2, const float* damp_b, double* gm, cudaStream_t st) {
-  count_launch();
-  k_adj_grad<R><<<adj_grid(g), dim3(32, 8), 0, st>>>(g, lw, (float)(1.0 / (dt * dt)), lam0, u1, u2, c2, damp_b, gm);
-  return cudaGetLastError();
-}
-cudaError_t adjoint_grad(int R, const PhysGrid& g, const LapW& lw, double dt, const float* lam0, const float* u1,
+cudaError_t adjoint_grad(const PhysGrid& g, double dt, const float* lam0, const float* u0, const float* u1,
                          const float* u2, const float* c2, const float* damp_b, double* gm, cudaStream_t st) {
-  switch (R) {
-    case 2: return adj_grad_r<2>(g, lw, dt, lam0, u1, u2, c2, damp_b, gm, st);
-    case 4: return adj_grad_r<4>(g, lw, dt, lam0, u1, u2, c2, damp_b, gm, st);
-    case 6: return adj_grad_r<6>(g, lw, dt, lam0, u1, u2, c2, damp_b, gm, st);
-  }
-  return cudaErrorInvalidValue;
+  count_launch();
+  k_adj_grad<<<adj_grid(g), dim3(32, 8), 0, st>>>(g, (float)(1.0 / (dt * dt)), lam0, u0, u1, u2, c2, damp_b, gm);
+  return cudaGetLastError();
 }
 
 cudaError_t adjoint_grad_src(const PhysGrid& g, int64_t npts, const int64_t* lin, const float* dcmp_row, double dt,
-                             const float* lam0, const float* c2, double* gm, cudaStream_t st) {
+                             const float* lam0, const float* c2, const float* damp_b, double* gm, cudaStream_t st) {
   if (npts <= 0) return cudaSuccess;
   count_launch();
-  k_adj_grad_src<<<grid_for(npts, 128), 128, 0, st>>>(g, npts, lin, dcmp_row, 1.0 / (dt * dt), lam0, c2, gm);
+  k_adj_grad_src<<<grid_for(npts, 128), 128, 0, st>>>(g, npts, lin, dcmp_row, 1.0 / (dt * dt), lam0, c2, damp_b, gm);
   return cudaGetLastError();
 }
 

@@ -1636,8 +1636,9 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
   int s = runner_init(h, &run, st);
   if (s != TB_OK) return s;
   // scratch: checkpoints (u^{jK}, u^{jK-1}) of segments j >= 1, a segment of
-  // K+1 states, adjoint fields, D lam, the FP64 gradient, the decomposed
-  // residual and the source-gradient rows
+  // K+2 states (u^{k0-1} .. u^{k1}: the imaging term of step k reads u^k,
+  // u^{k-1}, u^{k-2}), adjoint fields, D lam, the FP64 gradient, the
+  // decomposed residual and the source-gradient rows
   std::vector<void*> bufs;
   auto alloc = [&](size_t bytes) -> void* {
     void* p = nullptr;
@@ -1650,7 +1651,7 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
     bufs.clear();
   };
   float* snap = (float*)alloc(fbytes * 2 * std::max(nseg - 1, 1));
-  float* seg = (float*)alloc(fbytes * (K + 1));
+  float* seg = (float*)alloc(fbytes * (K + 2));
   float* lam = (float*)alloc(fbytes * 3);
   float* wbuf = (float*)alloc(fbytes);
   double* gm = (double*)alloc(sizeof(double) * Np);
@@ -1709,7 +1710,7 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
   float* l2 = lam + 2 * Np;
   for (int j = nseg - 1; j >= 0 && e == cudaSuccess; --j) {
     const int k0 = j * K, k1 = std::min((j + 1) * K, nt);
-    // seg[s] = u^{k0 - 1 + s}, s = 0 .. k1 - k0
+    // seg[s] = u^{k0 - 1 + s}, s = 0 .. k1 - k0 + 1
     if (j == 0) {
       ok(cudaMemsetAsync(seg, 0, fbytes * 2, st));
     } else {
@@ -1720,7 +1721,7 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
     prev = 1;
     ok(cudaMemcpyAsync(h->field[cur], seg + Np, fbytes, cudaMemcpyDeviceToDevice, st));
     ok(cudaMemcpyAsync(h->field[prev], seg, fbytes, cudaMemcpyDeviceToDevice, st));
-    for (int n = k0; n <= k1 - 2 && e == cudaSuccess; ++n) {
+    for (int n = k0; n <= k1 - 1 && e == cudaSuccess; ++n) {
       if ((s = runner_step(h, &run, cur, prev, n, st)) != TB_OK) {
         cleanup();
         return s;
@@ -1732,9 +1733,11 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
       ok(adjoint_step(h->R, g, lw, l1, l2, l0, wbuf, h->c2, h->damp_b, st));
       if (nrp > 0) ok(inject_points(g, nrp, h->rec.lin, rdcmp + (size_t)(k - 1) * nrp, l0, nullptr, nullptr, st));
       if (grad_vp) {
-        ok(adjoint_grad(h->R, g, lw, h->dt, l0, seg + (size_t)(k - k0) * Np, seg + (size_t)(k - k0 - 1) * Np, h->c2,
-                        h->damp_b, gm, st));
-        if (nsp > 0) ok(adjoint_grad_src(g, nsp, h->src.lin, h->src_dcmp + (size_t)(k - 1) * nsp, h->dt, l0, h->c2, gm, st));
+        ok(adjoint_grad(g, h->dt, l0, seg + (size_t)(k - k0 + 1) * Np, seg + (size_t)(k - k0) * Np,
+                        seg + (size_t)(k - k0 - 1) * Np, h->c2, h->damp_b, gm, st));
+        if (nsp > 0)
+          ok(adjoint_grad_src(g, nsp, h->src.lin, h->src_dcmp + (size_t)(k - 1) * nsp, h->dt, l0, h->c2, h->damp_b,
+                              gm, st));
       }
       if (grad_src && nsp > 0) ok(adjoint_sample_src(g, nsp, h->src.ent, h->src.lin, l0, h->c2, srow + (size_t)(k - 1) * nsp, st));
       float* t = l2;

@@ -151,10 +151,12 @@ struct LapW {
 };
 cudaError_t adjoint_step(int R, const PhysGrid& g, const LapW& lw, const float* lam1, const float* lam2, float* lam0,
                          float* w, const float* c2, const float* damp_b, cudaStream_t st);
-cudaError_t adjoint_grad(int R, const PhysGrid& g, const LapW& lw, double dt, const float* lam0, const float* u1,
+// imaging term of step k from u^k, u^{k-1}, u^{k-2} (pointwise), and its
+// source-point part
+cudaError_t adjoint_grad(const PhysGrid& g, double dt, const float* lam0, const float* u0, const float* u1,
                          const float* u2, const float* c2, const float* damp_b, double* gm, cudaStream_t st);
 cudaError_t adjoint_grad_src(const PhysGrid& g, int64_t npts, const int64_t* lin, const float* dcmp_row, double dt,
-                             const float* lam0, const float* c2, double* gm, cudaStream_t st);
+                             const float* lam0, const float* c2, const float* damp_b, double* gm, cudaStream_t st);
 cudaError_t adjoint_sample_src(const PhysGrid& g, int64_t npts, const int2* ent, const int64_t* lin,
                                const float* lam0, const float* c2, float* row, cudaStream_t st);
 cudaError_t adjoint_finish(const PhysGrid& g, double dt, const double* gm, const float* c2, float* out,

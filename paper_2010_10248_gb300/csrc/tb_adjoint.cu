@@ -6,13 +6,18 @@
 //   D = c2/(1+g),  B = 2/(1+g),  C = (g-1)/(1+g),  M = c2,
 // receivers d[k-1] = P u^{k}.  Adjoint for residual traces r (backward):
 //   lam^{k} = L (D lam^{k+1}) + B lam^{k+1} + C lam^{k+2} + P^T r[k-1]
-// (the centred Laplacian is symmetric), and the gradient of <d, r> is
-//   d/dm(p) = sum_k lam^k(p) c2 [2 g (u^{k-1} - u^{k-2}) - c2 L u^{k-1}](p)
-//             / (dt^2 (1+g)^2)  -  sum_k lam^k(p) c2(p) S^{k-1}(p) c2(p)/dt^2,
-// evaluated through the recurrence from three stored states (k_adj_grad),
+// (the centred Laplacian is symmetric).  B, C and D are pointwise, so
+// mu = D lam obeys the forward recurrence itself, backward in time:
+//   mu^{k} = D L mu^{k+1} + B mu^{k+1} + C mu^{k+2} + D P^T r[k-1],
+// which the forward sweep kernel computes (the residual injected at the
+// receiver points, scaled by D).  The gradient of <d, r>,
+//   d/dm(p) = sum_k lam^k c2 [2 g (u^{k-1} - u^{k-2}) - c2 L u^{k-1}] / (dt^2 (1+g)^2)
+//             - sum_k lam^k c2 S^{k-1} c2 / dt^2,
+// becomes, with the forward recurrence for c2 L u^{k-1} (see k_adj_grad),
+//   d/dm(p) = -sum_k mu^k [(u^k - u^{k-1}) - (u^{k-1} - u^{k-2})] / dt^2
+//             - sum_k mu^k (c2 S^{k-1}) g / dt^2     (source points),
 //   d/dvp = d/dm * (-2/vp^3),  vp = sqrt(c2)/dt,
-// accumulated in FP64 (the per-step term in FP32).  One plane of columns per
-// block; a neighbour load tests only the coordinate it moves along.
+// accumulated in FP64 (the per-step term in FP32).
 #include <cstdint>
 
 #include "tb_internal.cuh"
@@ -36,105 +41,53 @@ __device__ __forceinline__ AdjCol adj_col(const PhysGrid& g) {
 __device__ __forceinline__ size_t aidx(const PhysGrid& g, int x, int y, int z) {
   return ((size_t)x * g.n1 + y) * g.n2p + z;
 }
-__device__ __forceinline__ float ldz(const PhysGrid& g, const float* __restrict__ f, int x, int y, int z) {
-  return (x >= 0 && x < g.n0 && y >= 0 && y < g.n1 && z >= 0 && z < g.n2) ? __ldg(f + aidx(g, x, y, z)) : 0.f;
-}
 // g = (sum of per-axis eta/(2 dt)) * c2
 __device__ __forceinline__ float damp_g(const PhysGrid& g, const float* __restrict__ damp_b, float c2, int x, int y,
                                         int z) {
   return __fmul_rn(__fadd_rn(__fadd_rn(__ldg(damp_b + x), __ldg(damp_b + g.n0 + y)), __ldg(damp_b + g.n0 + g.n1 + z)),
                    c2);
 }
-// neighbour at offset o along axis d of the in-grid point (x, y, z): only
-// that coordinate can leave the grid
-template <int D>
-__device__ __forceinline__ float ld_ax(const PhysGrid& g, const float* __restrict__ f, size_t i0, int x, int y, int z,
-                                       int o) {
-  const int c = D == 0 ? x : (D == 1 ? y : z);
-  const int n = D == 0 ? g.n0 : (D == 1 ? g.n1 : g.n2);
-  const ptrdiff_t st = D == 0 ? (ptrdiff_t)g.n1 * g.n2p : (D == 1 ? (ptrdiff_t)g.n2p : 1);
-  return (unsigned)(c + o) < (unsigned)n ? __ldg(f + (ptrdiff_t)i0 + o * st) : 0.f;
-}
-// centred Laplacian in differences form at the in-grid point (x, y, z)
-// (w2[d][i-1] = c_i / h_d^2)
-template <int R>
-__device__ __forceinline__ float lap_at(const PhysGrid& g, const float* __restrict__ f, const LapW& w, int x, int y,
-                                        int z) {
-  const size_t i0 = aidx(g, x, y, z);
-  const float u = __ldg(f + i0);
-  float l = 0.f;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    float s = 0.f;
-#pragma unroll
-    for (int i = 1; i <= R; ++i) {
-      const float a = d == 0 ? ld_ax<0>(g, f, i0, x, y, z, i) : (d == 1 ? ld_ax<1>(g, f, i0, x, y, z, i) : ld_ax<2>(g, f, i0, x, y, z, i));
-      const float b = d == 0 ? ld_ax<0>(g, f, i0, x, y, z, -i) : (d == 1 ? ld_ax<1>(g, f, i0, x, y, z, -i) : ld_ax<2>(g, f, i0, x, y, z, -i));
-      s = __fmaf_rn(w.c[d][i - 1], __fadd_rn(__fsub_rn(a, u), __fsub_rn(b, u)), s);
-    }
-    l = __fadd_rn(l, s);
-  }
-  return l;
-}
 // n / den, exact when den is 1 (outside the sponge) without a division
 __device__ __forceinline__ float div_sponge(float n, float den) { return den == 1.f ? n : __fdiv_rn(n, den); }
 }  // namespace
 
-// w = D lam^{k+1}
-__global__ void k_adj_scale(PhysGrid g, const float* __restrict__ lam1, const float* __restrict__ c2,
-                            const float* __restrict__ damp_b, float* __restrict__ w) {
-  const AdjCol c = adj_col(g);
-  if (!c.ok) return;
-  const int x = blockIdx.z;
-  const size_t i0 = aidx(g, x, c.y, c.z);
+// rows[t][id] *= D(p_id) = c2/(1+g): the residual injection of the mu recurrence
+__global__ void k_adj_scale_rows(PhysGrid g, int nt, int64_t npts, const int64_t* __restrict__ lin,
+                                 const float* __restrict__ c2, const float* __restrict__ damp_b,
+                                 float* __restrict__ rows) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nt * npts) return;
+  const int64_t l = lin[i % npts];
+  const int z = (int)(l % g.n2), y = (int)((l / g.n2) % g.n1), x = (int)(l / ((int64_t)g.n1 * g.n2));
+  const size_t i0 = aidx(g, x, y, z);
   const float cc = __ldg(c2 + i0);
-  const float gd = damp_g(g, damp_b, cc, x, c.y, c.z);
-  w[i0] = div_sponge(__fmul_rn(cc, lam1[i0]), __fadd_rn(1.f, gd));
-}
-
-// lam^{k} = L w + B lam^{k+1} + C lam^{k+2} (before the residual injection)
-template <int R>
-__global__ void k_adj_step(PhysGrid g, LapW lw, const float* __restrict__ w, const float* __restrict__ lam1,
-                           const float* __restrict__ lam2, const float* __restrict__ c2,
-                           const float* __restrict__ damp_b, float* __restrict__ lam0) {
-  const AdjCol c = adj_col(g);
-  if (!c.ok) return;
-  const int x = blockIdx.z;
-  const size_t i0 = aidx(g, x, c.y, c.z);
-  const float gd = damp_g(g, damp_b, __ldg(c2 + i0), x, c.y, c.z);
-  const float opg = __fadd_rn(1.f, gd);
-  const float l = lap_at<R>(g, w, lw, x, c.y, c.z);
-  lam0[i0] = __fadd_rn(l, div_sponge(__fmaf_rn(2.f, lam1[i0], __fmul_rn(__fsub_rn(gd, 1.f), lam2[i0])), opg));
+  rows[i] = div_sponge(__fmul_rn(cc, rows[i]), __fadd_rn(1.f, damp_g(g, damp_b, cc, x, y, z)));
 }
 
 // grad_m += lam^k c2 [2 g (u^{k-1} - u^{k-2}) - c2 L u^{k-1}] / (dt^2 (1+g)^2).  By the
 // forward recurrence, (1+g) (u^k - c2 S^{k-1}) = c2 L u^{k-1} + 2 u^{k-1} - (1-g) u^{k-2},
-// the bracket equals -(1+g) [(u^k - c2 S^{k-1}) - 2 u^{k-1} + u^{k-2}]: the term is
-// -lam^k c2 [(u^k - u^{k-1}) - (u^{k-1} - u^{k-2})] / (dt^2 (1+g)), pointwise on three
-// stored states (no stencil), with the c2 S part added at the source points
-// (k_adj_grad_src).  The term in FP32 (the differences of neighbouring states
-// first), the sum over steps in FP64.
-__global__ void k_adj_grad(PhysGrid g, float inv_dt2, const float* __restrict__ lam0, const float* __restrict__ u0,
-                           const float* __restrict__ u1, const float* __restrict__ u2, const float* __restrict__ c2,
-                           const float* __restrict__ damp_b, double* __restrict__ gm) {
+// the bracket equals -(1+g) [(u^k - c2 S^{k-1}) - 2 u^{k-1} + u^{k-2}], and with
+// lam = mu (1+g)/c2 the term is -mu^k [(u^k - u^{k-1}) - (u^{k-1} - u^{k-2})] / dt^2:
+// pointwise on three stored states, no stencil; the c2 S part is added at the
+// source points (k_adj_grad_src).  The term in FP32 (the differences of
+// neighbouring states first), the sum over steps in FP64.
+__global__ void k_adj_grad(PhysGrid g, float inv_dt2, const float* __restrict__ mu, const float* __restrict__ u0,
+                           const float* __restrict__ u1, const float* __restrict__ u2, double* __restrict__ gm) {
   const AdjCol c = adj_col(g);
   if (!c.ok) return;
   const int x = blockIdx.z;
   const size_t i0 = aidx(g, x, c.y, c.z);
-  const float cc = __ldg(c2 + i0);
-  const float gd = damp_g(g, damp_b, cc, x, c.y, c.z);
   const float b1 = __ldg(u1 + i0);
   const float d2 = __fsub_rn(__fsub_rn(__ldg(u0 + i0), b1), __fsub_rn(b1, __ldg(u2 + i0)));
-  const float dr = div_sponge(__fmul_rn(__fmul_rn(cc, d2), inv_dt2), __fadd_rn(1.f, gd));
-  gm[i0] -= (double)__ldg(lam0 + i0) * (double)dr;
+  gm[i0] -= (double)__ldg(mu + i0) * (double)__fmul_rn(d2, inv_dt2);
 }
 
 // source points: the term of M = c2 (d(c2 S)/dm = -c2 (c2 S)/dt^2) and the c2 S
 // part of the imaging term, +lam^k c2 (c2 S) / (dt^2 (1+g)); together
-// grad_m(p_id) -= lam^k c2 (c2 S^{k-1}) g / (dt^2 (1+g))  (src_dcmp = c2 S; zero
-// outside the sponge)
+// -lam^k c2 (c2 S^{k-1}) g / (dt^2 (1+g)) = -mu^k (c2 S^{k-1}) g / dt^2
+// (src_dcmp = c2 S; zero outside the sponge)
 __global__ void k_adj_grad_src(PhysGrid g, int64_t npts, const int64_t* __restrict__ lin,
-                               const float* __restrict__ dcmp_row, double inv_dt2, const float* __restrict__ lam0,
+                               const float* __restrict__ dcmp_row, double inv_dt2, const float* __restrict__ mu,
                                const float* __restrict__ c2, const float* __restrict__ damp_b,
                                double* __restrict__ gm) {
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -142,21 +95,21 @@ __global__ void k_adj_grad_src(PhysGrid g, int64_t npts, const int64_t* __restri
   const int64_t l = lin[id];
   const int z = (int)(l % g.n2), y = (int)((l / g.n2) % g.n1), x = (int)(l / ((int64_t)g.n1 * g.n2));
   const size_t i0 = aidx(g, x, y, z);
-  const float cc = c2[i0];
-  const double gd = (double)damp_g(g, damp_b, cc, x, y, z);
-  gm[i0] -= (double)lam0[i0] * (double)cc * (double)dcmp_row[id] * inv_dt2 * (gd / (1.0 + gd));
+  const double gd = (double)damp_g(g, damp_b, c2[i0], x, y, z);
+  gm[i0] -= (double)mu[i0] * (double)dcmp_row[id] * gd * inv_dt2;
 }
 
-// source-wavelet gradient row: value at each source point of M lam = c2 lam
+// source-wavelet gradient row: value at each source point of M lam = c2 lam = (1+g) mu
 __global__ void k_adj_sample_src(PhysGrid g, int64_t npts, const int2* __restrict__ ent,
-                                 const int64_t* __restrict__ lin, const float* __restrict__ lam0,
-                                 const float* __restrict__ c2, float* __restrict__ row) {
+                                 const int64_t* __restrict__ lin, const float* __restrict__ mu,
+                                 const float* __restrict__ c2, const float* __restrict__ damp_b,
+                                 float* __restrict__ row) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= npts) return;
   const int64_t l = lin[ent[e].y];
   const int z = (int)(l % g.n2), y = (int)((l / g.n2) % g.n1), x = (int)(l / ((int64_t)g.n1 * g.n2));
   const size_t i0 = aidx(g, x, y, z);
-  row[e] = __fmul_rn(c2[i0], lam0[i0]);
+  row[e] = __fmul_rn(__fadd_rn(1.f, damp_g(g, damp_b, c2[i0], x, y, z)), mu[i0]);
 }
 
 // grad_vp = grad_m * (-2 / vp^3), vp = sqrt(c2)/dt, into a dense [n0][n1][n2] array
@@ -174,44 +127,34 @@ static dim3 adj_grid(const PhysGrid& g) {
   return dim3((unsigned)((g.n2 + 31) / 32), (unsigned)((g.n1 + 7) / 8), (unsigned)g.n0);
 }
 
-template <int R>
-static cudaError_t adj_step_r(const PhysGrid& g, const LapW& lw, const float* lam1, const float* lam2, float* lam0,
-                              float* w, const float* c2, const float* damp_b, cudaStream_t st) {
-  count_launch(2);
-  k_adj_scale<<<adj_grid(g), dim3(32, 8), 0, st>>>(g, lam1, c2, damp_b, w);
-  k_adj_step<R><<<adj_grid(g), dim3(32, 8), 0, st>>>(g, lw, w, lam1, lam2, c2, damp_b, lam0);
+cudaError_t adjoint_scale_rows(const PhysGrid& g, int nt, int64_t npts, const int64_t* lin, const float* c2,
+                               const float* damp_b, float* rows, cudaStream_t st) {
+  if (npts <= 0 || nt <= 0) return cudaSuccess;
+  count_launch();
+  k_adj_scale_rows<<<grid_for((int64_t)nt * npts, 256), 256, 0, st>>>(g, nt, npts, lin, c2, damp_b, rows);
   return cudaGetLastError();
 }
-cudaError_t adjoint_step(int R, const PhysGrid& g, const LapW& lw, const float* lam1, const float* lam2, float* lam0,
-                         float* w, const float* c2, const float* damp_b, cudaStream_t st) {
-  switch (R) {
-    case 2: return adj_step_r<2>(g, lw, lam1, lam2, lam0, w, c2, damp_b, st);
-    case 4: return adj_step_r<4>(g, lw, lam1, lam2, lam0, w, c2, damp_b, st);
-    case 6: return adj_step_r<6>(g, lw, lam1, lam2, lam0, w, c2, damp_b, st);
-  }
-  return cudaErrorInvalidValue;
-}
 
-cudaError_t adjoint_grad(const PhysGrid& g, double dt, const float* lam0, const float* u0, const float* u1,
-                         const float* u2, const float* c2, const float* damp_b, double* gm, cudaStream_t st) {
+cudaError_t adjoint_grad(const PhysGrid& g, double dt, const float* mu, const float* u0, const float* u1,
+                         const float* u2, double* gm, cudaStream_t st) {
   count_launch();
-  k_adj_grad<<<adj_grid(g), dim3(32, 8), 0, st>>>(g, (float)(1.0 / (dt * dt)), lam0, u0, u1, u2, c2, damp_b, gm);
+  k_adj_grad<<<adj_grid(g), dim3(32, 8), 0, st>>>(g, (float)(1.0 / (dt * dt)), mu, u0, u1, u2, gm);
   return cudaGetLastError();
 }
 
 cudaError_t adjoint_grad_src(const PhysGrid& g, int64_t npts, const int64_t* lin, const float* dcmp_row, double dt,
-                             const float* lam0, const float* c2, const float* damp_b, double* gm, cudaStream_t st) {
+                             const float* mu, const float* c2, const float* damp_b, double* gm, cudaStream_t st) {
   if (npts <= 0) return cudaSuccess;
   count_launch();
-  k_adj_grad_src<<<grid_for(npts, 128), 128, 0, st>>>(g, npts, lin, dcmp_row, 1.0 / (dt * dt), lam0, c2, damp_b, gm);
+  k_adj_grad_src<<<grid_for(npts, 128), 128, 0, st>>>(g, npts, lin, dcmp_row, 1.0 / (dt * dt), mu, c2, damp_b, gm);
   return cudaGetLastError();
 }
 
 cudaError_t adjoint_sample_src(const PhysGrid& g, int64_t npts, const int2* ent, const int64_t* lin,
-                               const float* lam0, const float* c2, float* row, cudaStream_t st) {
+                               const float* mu, const float* c2, const float* damp_b, float* row, cudaStream_t st) {
   if (npts <= 0) return cudaSuccess;
   count_launch();
-  k_adj_sample_src<<<grid_for(npts, 128), 128, 0, st>>>(g, npts, ent, lin, lam0, c2, row);
+  k_adj_sample_src<<<grid_for(npts, 128), 128, 0, st>>>(g, npts, ent, lin, mu, c2, damp_b, row);
   return cudaGetLastError();
 }
 

@@ -1589,15 +1589,17 @@ static int runner_init(tb_handle* h, StepRunner* r, cudaStream_t st) {
   P.timeout_ns = (long long)(h->opt.wait_timeout_s * 1e9);
   return TB_OK;
 }
-// u^{step+1} over field[prev] from field[cur] = u^{step}, field[prev] = u^{step-1}
-static int runner_step(tb_handle* h, StepRunner* r, int cur, int prev, int step, cudaStream_t st) {
+// one step of the sweep over field fp (u^{step-1} in, u^{step+1} out) from
+// fc = u^{step}; box_c, tile_p: their TMA descriptors
+static int runner_step_on(tb_handle* h, StepRunner* r, float* fc, float* fp, const CUtensorMap& box_c,
+                          const CUtensorMap& tile_p, int step, cudaStream_t st) {
   SweepParams& P = r->P;
   SweepSet& S = P.set[0];
-  S.u_cur = h->field[cur];
-  S.u_prev = h->field[prev];
-  S.tm_u = h->tm_box[cur];
-  S.tm_p = h->tm_tile[prev];
-  S.out0 = h->field[prev];
+  S.u_cur = fc;
+  S.u_prev = fp;
+  S.tm_u = box_c;
+  S.tm_p = tile_p;
+  S.out0 = fp;
   S.out1 = nullptr;
   S.step0 = step;
   P.tm_c = h->tm_c2;
@@ -1610,9 +1612,13 @@ static int runner_step(tb_handle* h, StepRunner* r, int cur, int prev, int step,
     P.pass = h->d_pass + first;
     P.npass = last - first;
     cudaError_t e = sweep_launch(h->R, 1, P, pl.launch_ctas[L], false, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint forward launch");
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint sweep launch");
   }
   return TB_OK;
+}
+// u^{step+1} over field[prev] from field[cur] = u^{step}, field[prev] = u^{step-1}
+static int runner_step(tb_handle* h, StepRunner* r, int cur, int prev, int step, cudaStream_t st) {
+  return runner_step_on(h, r, h->field[cur], h->field[prev], h->tm_box[cur], h->tm_tile[prev], step, st);
 }
 
 extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, float* grad_vp, float* grad_src,
@@ -1637,8 +1643,8 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
   if (s != TB_OK) return s;
   // scratch: checkpoints (u^{jK}, u^{jK-1}) of segments j >= 1, a segment of
   // K+2 states (u^{k0-1} .. u^{k1}: the imaging term of step k reads u^k,
-  // u^{k-1}, u^{k-2}), adjoint fields, D lam, the FP64 gradient, the
-  // decomposed residual and the source-gradient rows
+  // u^{k-1}, u^{k-2}), the two adjoint fields mu = D lam, the FP64 gradient,
+  // the decomposed residual and the source-gradient rows
   std::vector<void*> bufs;
   auto alloc = [&](size_t bytes) -> void* {
     void* p = nullptr;
@@ -1652,8 +1658,7 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
   };
   float* snap = (float*)alloc(fbytes * 2 * std::max(nseg - 1, 1));
   float* seg = (float*)alloc(fbytes * (K + 2));
-  float* lam = (float*)alloc(fbytes * 3);
-  float* wbuf = (float*)alloc(fbytes);
+  float* lam = (float*)alloc(fbytes * 2);
   double* gm = (double*)alloc(sizeof(double) * Np);
   float* resT = (float*)alloc(sizeof(float) * (size_t)nt * std::max(nrec, 1));
   float* rdcmp = (float*)alloc(sizeof(float) * (size_t)nt * std::max<int64_t>(nrp, 1));
@@ -1662,15 +1667,12 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
   float* gvp_dev = nullptr;
   const bool gvp_host = grad_vp && !is_device_ptr(grad_vp);
   if (gvp_host) gvp_dev = (float*)alloc(sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n[2]);
-  if (!snap || !seg || !lam || !wbuf || !gm || !resT || !rdcmp || !srow || !gsrc || (gvp_host && !gvp_dev)) {
+  if (!snap || !seg || !lam || !gm || !resT || !rdcmp || !srow || !gsrc || (gvp_host && !gvp_dev)) {
     cleanup();
     cudaGetLastError();
     return fail(h, TB_ENOMEM, "adjoint scratch");
   }
   const PhysGrid g{(int)h->n[0], (int)h->n[1], (int)h->n[2], h->n2p};
-  LapW lw{};
-  for (int d = 0; d < 3; ++d)
-    for (int i = 1; i <= h->R; ++i) lw.c[d][i - 1] = (float)(h->c[i] / (h->h[d] * h->h[d]));
   cudaError_t e = cudaSuccess;
   auto ok = [&](cudaError_t x) {
     if (e == cudaSuccess && x != cudaSuccess) e = x;
@@ -1684,6 +1686,22 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
     if (tmp) bufs.push_back(tmp);
     ok(transpose_f32(nt, nrec, (const float*)dres, resT, st));
     if (nrp > 0) ok(decompose(&h->rec, nt, resT, nullptr, 1.0, (int)h->n[1], (int)h->n[2], h->n2p, rdcmp, st));
+    // injected into mu = D lam: scaled by D at each receiver point
+    if (nrp > 0) ok(adjoint_scale_rows(g, nt, nrp, h->rec.lin, h->c2, h->damp_b, rdcmp, st));
+  }
+  // the adjoint sweeps: the forward sweep kernel on the mu fields, without
+  // the sources (the residual is injected after each step)
+  StepRunner arun = run;
+  arun.P.ev_pair = nullptr;
+  float* mu[2] = {lam, lam + Np};
+  CUtensorMap mbox[2], mtile[2];
+  {
+    SweepShape sh;
+    if (!sweep_shape(h->R, 1, &sh, 0)) ok(cudaErrorInvalidValue);
+    for (int i = 0; i < 2; ++i) {
+      ok(make_tmap(&mbox[i], mu[i], h->n, h->n2p, sh.box_w, sh.box_h));
+      ok(make_tmap(&mtile[i], mu[i], h->n, h->n2p, 64, sh.TY));
+    }
   }
   // forward pass, keeping the checkpoints
   int cur = 0, prev = 1;
@@ -1703,11 +1721,9 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
     std::swap(cur, prev);
   }
   // backward over the segments, each recomputed once from its checkpoint
-  ok(cudaMemsetAsync(lam, 0, fbytes * 3, st));
+  ok(cudaMemsetAsync(lam, 0, fbytes * 2, st));
   ok(cudaMemsetAsync(gm, 0, sizeof(double) * Np, st));
-  float* l0 = lam;
-  float* l1 = lam + Np;
-  float* l2 = lam + 2 * Np;
+  int mc = 0, mp = 1;  // mu^{k+1} in mu[mc], mu^{k+2} in mu[mp]
   for (int j = nseg - 1; j >= 0 && e == cudaSuccess; --j) {
     const int k0 = j * K, k1 = std::min((j + 1) * K, nt);
     // seg[s] = u^{k0 - 1 + s}, s = 0 .. k1 - k0 + 1
@@ -1730,20 +1746,23 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
       ok(cudaMemcpyAsync(seg + (size_t)(n + 2 - k0) * Np, h->field[cur], fbytes, cudaMemcpyDeviceToDevice, st));
     }
     for (int k = k1; k >= k0 + 1 && e == cudaSuccess; --k) {
-      ok(adjoint_step(h->R, g, lw, l1, l2, l0, wbuf, h->c2, h->damp_b, st));
-      if (nrp > 0) ok(inject_points(g, nrp, h->rec.lin, rdcmp + (size_t)(k - 1) * nrp, l0, nullptr, nullptr, st));
+      // mu^k over mu^{k+2}, then + D P^T r[k-1]
+      if (e == cudaSuccess && (s = runner_step_on(h, &arun, mu[mc], mu[mp], mbox[mc], mtile[mp], nt - k, st)) != TB_OK) {
+        cleanup();
+        return s;
+      }
+      std::swap(mc, mp);
+      float* m0 = mu[mc];
+      if (nrp > 0) ok(inject_points(g, nrp, h->rec.lin, rdcmp + (size_t)(k - 1) * nrp, m0, nullptr, nullptr, st));
       if (grad_vp) {
-        ok(adjoint_grad(g, h->dt, l0, seg + (size_t)(k - k0 + 1) * Np, seg + (size_t)(k - k0) * Np,
-                        seg + (size_t)(k - k0 - 1) * Np, h->c2, h->damp_b, gm, st));
+        ok(adjoint_grad(g, h->dt, m0, seg + (size_t)(k - k0 + 1) * Np, seg + (size_t)(k - k0) * Np,
+                        seg + (size_t)(k - k0 - 1) * Np, gm, st));
         if (nsp > 0)
-          ok(adjoint_grad_src(g, nsp, h->src.lin, h->src_dcmp + (size_t)(k - 1) * nsp, h->dt, l0, h->c2, h->damp_b,
+          ok(adjoint_grad_src(g, nsp, h->src.lin, h->src_dcmp + (size_t)(k - 1) * nsp, h->dt, m0, h->c2, h->damp_b,
                               gm, st));
       }
-      if (grad_src && nsp > 0) ok(adjoint_sample_src(g, nsp, h->src.ent, h->src.lin, l0, h->c2, srow + (size_t)(k - 1) * nsp, st));
-      float* t = l2;
-      l2 = l1;
-      l1 = l0;
-      l0 = t;
+      if (grad_src && nsp > 0)
+        ok(adjoint_sample_src(g, nsp, h->src.ent, h->src.lin, m0, h->c2, h->damp_b, srow + (size_t)(k - 1) * nsp, st));
     }
   }
   if (grad_vp && e == cudaSuccess) {

@@ -146,19 +146,21 @@ cudaError_t sample_points(const PhysGrid& g, int64_t npts, const int2* ent, cons
                           const float* f1, const float* f2, float* row, cudaStream_t st);
 
 // Adjoint of the acoustic one-step recurrence and the vp gradient (tb_adjoint.cu).
+// The adjoint runs on mu = D lam (D = c2/(1+g)) with the forward sweep kernel.
 struct LapW {
   float c[3][6];  // c_i / h_d^2, i = 1..r
 };
-cudaError_t adjoint_step(int R, const PhysGrid& g, const LapW& lw, const float* lam1, const float* lam2, float* lam0,
-                         float* w, const float* c2, const float* damp_b, cudaStream_t st);
-// imaging term of step k from u^k, u^{k-1}, u^{k-2} (pointwise), and its
-// source-point part
-cudaError_t adjoint_grad(const PhysGrid& g, double dt, const float* lam0, const float* u0, const float* u1,
-                         const float* u2, const float* c2, const float* damp_b, double* gm, cudaStream_t st);
+// rows[t][id] *= D at the receiver point id (the residual injected into mu)
+cudaError_t adjoint_scale_rows(const PhysGrid& g, int nt, int64_t npts, const int64_t* lin, const float* c2,
+                               const float* damp_b, float* rows, cudaStream_t st);
+// imaging term of step k from mu^k and u^k, u^{k-1}, u^{k-2} (pointwise), and
+// its source-point part
+cudaError_t adjoint_grad(const PhysGrid& g, double dt, const float* mu, const float* u0, const float* u1,
+                         const float* u2, double* gm, cudaStream_t st);
 cudaError_t adjoint_grad_src(const PhysGrid& g, int64_t npts, const int64_t* lin, const float* dcmp_row, double dt,
-                             const float* lam0, const float* c2, const float* damp_b, double* gm, cudaStream_t st);
+                             const float* mu, const float* c2, const float* damp_b, double* gm, cudaStream_t st);
 cudaError_t adjoint_sample_src(const PhysGrid& g, int64_t npts, const int2* ent, const int64_t* lin,
-                               const float* lam0, const float* c2, float* row, cudaStream_t st);
+                               const float* mu, const float* c2, const float* damp_b, float* row, cudaStream_t st);
 cudaError_t adjoint_finish(const PhysGrid& g, double dt, const double* gm, const float* c2, float* out,
                            cudaStream_t st);
 cudaError_t transpose_f32(int64_t rows, int64_t cols, const float* in, float* out, cudaStream_t st);

@@ -306,14 +306,17 @@ int tb_inspect_points_noalloc(const int64_t n[3], const double h[3], int npt, co
  *             d<d, r>/d q (the adjoint of the wavelet-to-trace map);
  *   n_snapshots >= 1: the forward pass keeps a checkpoint (u^n, u^{n-1})
  *             every ceil(nt / n_snapshots) steps; the backward pass
- *             recomputes each segment once from its checkpoint into a
- *             buffer of ceil(nt / n_snapshots) + 1 states.
+ *             recomputes each segment once from its checkpoint (one step
+ *             into the next segment) into a buffer of
+ *             ceil(nt / n_snapshots) + 2 states.
  * The adjoint is the exact transpose of the discrete one-step recurrence:
  * lam^k = L(D lam^{k+1}) + B lam^{k+1} + C lam^{k+2} + P^T r[k-1] with
- * D = dt^2/(m + a), B = 2m/(m + a), C = (a - m)/(m + a), a = eta dt/2; the
- * gradient sums lam^k d(step k)/dm over the steps in FP64.  Device scratch
- * about (2 n_snapshots + ceil(nt / n_snapshots) + 7) fields, allocated and
- * freed by the call.  Synchronises `stream`.  Overwrites the handle's
+ * D = dt^2/(m + a), B = 2m/(m + a), C = (a - m)/(m + a), a = eta dt/2,
+ * computed as mu = D lam, which obeys the forward recurrence backward in
+ * time (the forward sweep kernel runs it); the gradient sums
+ * lam^k d(step k)/dm over the steps in FP64.  Device scratch about
+ * (2 n_snapshots + ceil(nt / n_snapshots) + 5) fields, allocated and freed
+ * by the call.  Synchronises `stream`.  Overwrites the handle's
  * wavefields (tb_get_field needs a new tb_forward).  Acoustic only.
  * Errors: TB_ESTATE, TB_EINVAL, TB_ENOMEM, TB_ECUDA, TB_ETIMEOUT. */
 int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, float* grad_vp, float* grad_src,

@@ -854,10 +854,10 @@ def run_adjoint(args):
     ms = e0.elapsed_time(e1) / args.steps
     value = N * nt / (ms * 1e-3) / 1e9
     # algorithmic bytes per point and step of the gradient: forward one-step
-    # (16) with checkpoints, recomputation (16) and its segment copy (8), the
+    # (16) with checkpoints, recomputation into the segment buffer (16), the
     # adjoint one-step sweep on mu = D lam (16), imaging condition (mu, u^k,
     # u^{k-1}, u^{k-2}: 16, + FP64 sum 16)
-    bpp = 16.0 + 16.0 + 8.0 + 16.0 + 32.0
+    bpp = 16.0 + 16.0 + 16.0 + 32.0
     peak, peak_kind = measured_peaks()
     achieved = bpp * N * nt / (ms * 1e-3) / 1e9
     finite = bool(torch.isfinite(gvp).all().item()) and float(gvp.abs().max()) > 0

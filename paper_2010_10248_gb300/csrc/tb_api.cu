@@ -1589,17 +1589,17 @@ static int runner_init(tb_handle* h, StepRunner* r, cudaStream_t st) {
   P.timeout_ns = (long long)(h->opt.wait_timeout_s * 1e9);
   return TB_OK;
 }
-// one step of the sweep over field fp (u^{step-1} in, u^{step+1} out) from
-// fc = u^{step}; box_c, tile_p: their TMA descriptors
+// one step of the sweep: u^{step+1} into out (fp when NULL) from fc = u^{step}
+// and fp = u^{step-1}; box_c, tile_p: their TMA descriptors
 static int runner_step_on(tb_handle* h, StepRunner* r, float* fc, float* fp, const CUtensorMap& box_c,
-                          const CUtensorMap& tile_p, int step, cudaStream_t st) {
+                          const CUtensorMap& tile_p, int step, cudaStream_t st, float* out = nullptr) {
   SweepParams& P = r->P;
   SweepSet& S = P.set[0];
   S.u_cur = fc;
   S.u_prev = fp;
   S.tm_u = box_c;
   S.tm_p = tile_p;
-  S.out0 = fp;
+  S.out0 = out ? out : fp;
   S.out1 = nullptr;
   S.step0 = step;
   P.tm_c = h->tm_c2;
@@ -1690,17 +1690,23 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
     if (nrp > 0) ok(adjoint_scale_rows(g, nt, nrp, h->rec.lin, h->c2, h->damp_b, rdcmp, st));
   }
   // the adjoint sweeps: the forward sweep kernel on the mu fields, without
-  // the sources (the residual is injected after each step)
+  // the sources (the residual is injected after each step); the
+  // recomputation writes each state straight into its segment slot
   StepRunner arun = run;
   arun.P.ev_pair = nullptr;
   float* mu[2] = {lam, lam + Np};
   CUtensorMap mbox[2], mtile[2];
+  std::vector<CUtensorMap> sbox(K + 2), stile(K + 2);
   {
     SweepShape sh;
     if (!sweep_shape(h->R, 1, &sh, 0)) ok(cudaErrorInvalidValue);
     for (int i = 0; i < 2; ++i) {
       ok(make_tmap(&mbox[i], mu[i], h->n, h->n2p, sh.box_w, sh.box_h));
       ok(make_tmap(&mtile[i], mu[i], h->n, h->n2p, 64, sh.TY));
+    }
+    for (int i = 0; i < K + 2; ++i) {
+      ok(make_tmap(&sbox[i], seg + (size_t)i * Np, h->n, h->n2p, sh.box_w, sh.box_h));
+      ok(make_tmap(&stile[i], seg + (size_t)i * Np, h->n, h->n2p, 64, sh.TY));
     }
   }
   // forward pass, keeping the checkpoints
@@ -1733,17 +1739,13 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
       ok(cudaMemcpyAsync(seg + Np, snap + (size_t)(2 * (j - 1)) * Np, fbytes, cudaMemcpyDeviceToDevice, st));
       ok(cudaMemcpyAsync(seg, snap + (size_t)(2 * (j - 1) + 1) * Np, fbytes, cudaMemcpyDeviceToDevice, st));
     }
-    cur = 0;
-    prev = 1;
-    ok(cudaMemcpyAsync(h->field[cur], seg + Np, fbytes, cudaMemcpyDeviceToDevice, st));
-    ok(cudaMemcpyAsync(h->field[prev], seg, fbytes, cudaMemcpyDeviceToDevice, st));
     for (int n = k0; n <= k1 - 1 && e == cudaSuccess; ++n) {
-      if ((s = runner_step(h, &run, cur, prev, n, st)) != TB_OK) {
+      const int sc = n - k0 + 1;  // slot of u^n
+      if ((s = runner_step_on(h, &run, seg + (size_t)sc * Np, seg + (size_t)(sc - 1) * Np, sbox[sc],
+                              stile[sc - 1], n, st, seg + (size_t)(sc + 1) * Np)) != TB_OK) {
         cleanup();
         return s;
       }
-      std::swap(cur, prev);
-      ok(cudaMemcpyAsync(seg + (size_t)(n + 2 - k0) * Np, h->field[cur], fbytes, cudaMemcpyDeviceToDevice, st));
     }
     for (int k = k1; k >= k0 + 1 && e == cudaSuccess; --k) {
       // mu^k over mu^{k+2}, then + D P^T r[k-1]

@@ -356,15 +356,16 @@ extern "C" int tb_destroy(tb_handle* h) {
 // the tensor, so cells past n2 read as zeros) with a box of bw x bh x 1.
 static cudaError_t make_tmap(CUtensorMap* m, void* base, const int64_t n[3], int n2p, int bw, int bh,
                              CUtensorMapDataType dtype = CU_TENSOR_MAP_DATA_TYPE_FLOAT32, int esz = 4) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // looked up once (a function-local static: safe with concurrent callers)
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                     cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-  }
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                           cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess) return nullptr;
+    return (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }();
+  if (!encode) return cudaErrorNotSupported;
   const cuuint64_t dims[3] = {(cuuint64_t)n[2], (cuuint64_t)n[1], (cuuint64_t)n[0]};
   const cuuint64_t strides[2] = {(cuuint64_t)n2p * esz, (cuuint64_t)n2p * esz * n[1]};
   const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};

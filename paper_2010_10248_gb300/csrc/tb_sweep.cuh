@@ -974,12 +974,11 @@ cudaError_t sweep_launch_t(const SweepParams& p, int nctas, bool cooperative, cu
   using Tr = SweepTraits<R, T, SK>;
   using Cf = typename Tr::Cfg;
   auto fn = sweep_kernel<R, T, Tr::TY, SK, TWO, PRE>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // once per process (a function-local static: initialised once even when
+  // several host threads launch at the same time)
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
+  if (attr != cudaSuccess) return attr;
   count_launch();
   if (cooperative) {
     void* args[] = {const_cast<SweepParams*>(&p)};

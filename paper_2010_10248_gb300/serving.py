@@ -141,13 +141,22 @@ class ShotServer:
     requests (arrival times in ``ShotRequest.arrival``, seconds from the start)
     and returns their results in completion order."""
 
-    def __init__(self, slots: int = 8, memory_budget: int | None = None, poll_s: float = 2e-4):
-        import torch
-        self.torch = torch
-        self.slots = [_Slot(torch) for _ in range(slots)]
-        if memory_budget is None:
-            free, _ = torch.cuda.mem_get_info()
-            memory_budget = int(free * 0.85)
+    def __init__(self, slots: int = 8, memory_budget: int | None = None, poll_s: float = 2e-4,
+                 slot_factory=None):
+        """``slot_factory`` (no arguments) makes the slots; by default a slot
+        is a CUDA stream with a propagator.  Any object with ``bytes``,
+        ``launch(req, t0)``, ``ready()`` and ``finish(t0)`` serves (the
+        scheduling logic is tested with host-only slots)."""
+        if slot_factory is None:
+            import torch
+            self.slots = [_Slot(torch) for _ in range(slots)]
+            if memory_budget is None:
+                free, _ = torch.cuda.mem_get_info()
+                memory_budget = int(free * 0.85)
+        else:
+            self.slots = [slot_factory() for _ in range(slots)]
+            if memory_budget is None:
+                raise ValueError("a memory budget is needed with a custom slot factory")
         self.budget = int(memory_budget)
         self.poll_s = poll_s
         self.stats = {"max_in_flight": 0, "max_bytes": 0}

@@ -201,6 +201,20 @@ int tb_get_receiver_points(tb_handle* h, int64_t* npts, int64_t* lin, int32_t* c
 /* Device bytes held by the handle (fields, model, tables, scratch). */
 size_t tb_workspace_bytes(const tb_handle* h);
 
+/* Host-side layout of the sweep kernel's source table (Sec. II-A's
+ * grid-aligned injection, as the blocked sweep reads it; no GPU needed).
+ * For npts grid points given by their unpadded linear indices lin[i] =
+ * (x n1 + y) n2 + z on a grid with n1 x n2 points on axes 1 and 2, the points
+ * of each column pair (y, 2p), (y, 2p + 1) share one range of planes
+ * [first, first + span): writes ev_pair[2 (y ceil(n2/2) + p) + 0] = first |
+ * span << 16 and [.. + 1] = base (caller-owned, 2 n1 ceil(n2/2) ints; zero
+ * for pairs without points), slot[i] = 2 (base + x - first) + (z mod 2) (the
+ * float offset of point i in every step's row of the table) and nev (the sum
+ * of the spans: a row holds 2 nev floats).  Errors: TB_EINVAL (bad
+ * arguments, a plane or span beyond 65535, more than 2^30 slots). */
+int tb_source_event_layout(int64_t npts, const int64_t* lin, int64_t n1, int64_t n2, int* ev_pair, int* slot,
+                           int64_t* nev);
+
 /* Host-side schedule of the blocked sweep with bands pipelined across time
  * tiles (the default when y_bands = 0 and x_chunks <= 1; Sec. II-B's temporal
  * blocking, split into co-resident bands).  No GPU is needed.  For a grid of

@@ -14,7 +14,7 @@ from ._tb import (TB_ACOUSTIC, TB_BF16, TB_BLOCKED, TB_ELASTIC, TB_F16, TB_F32, 
                   tb_create, tb_destroy, tb_fd_weights, tb_forward, tb_get_dt, tb_get_field,
                   tb_get_receiver_points, tb_get_source_points, tb_kernel_time, tb_last_error,
                   tb_launch_count, tb_measure_peaks, tb_ricker, tb_selftest_wait, tb_set_model, tb_set_receivers, tb_set_sources,
-                  tb_plan_pipeline, tb_sponge_profile, tb_workspace_bytes)
+                  tb_plan_pipeline, tb_source_event_layout, tb_sponge_profile, tb_workspace_bytes)
 
 __all__ = ["Propagator", "Options", "TBError", "load", "TB_ONESTEP", "TB_BLOCKED", "TB_ACOUSTIC",
            "TB_TTI", "TB_ELASTIC", "tb_tti_dt_max", "tb_elastic_dt_max", "tb_adjoint_gradient",
@@ -23,7 +23,7 @@ __all__ = ["Propagator", "Options", "TBError", "load", "TB_ONESTEP", "TB_BLOCKED
            "tb_set_receivers", "tb_forward", "tb_get_field", "tb_get_source_points",
            "tb_get_receiver_points", "tb_workspace_bytes", "tb_kernel_time", "tb_last_error",
            "tb_fd_weights", "tb_cfl_dt_max", "tb_sponge_profile", "tb_ricker", "tb_selftest_wait", "tb_measure_peaks",
-           "tb_launch_count", "tb_plan_pipeline"]
+           "tb_launch_count", "tb_plan_pipeline", "tb_source_event_layout"]
 
 
 class Propagator:

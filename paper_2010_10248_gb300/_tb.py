@@ -69,6 +69,8 @@ _SIGS = {
     "tb_launch_count": (C.c_uint64, []),
     "tb_plan_pipeline": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                    C.POINTER(C.c_int), C.c_int]),
+    "tb_source_event_layout": (C.c_int, [C.c_int64, _vp, C.c_int64, C.c_int64, _vp, _vp,
+                                         C.POINTER(C.c_int64)]),
     "tb_inspect_points_noalloc": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int,
                                             _vp, _vp, _vp, _vp]),
 }
@@ -189,6 +191,22 @@ def tb_get_receiver_points(h, lin=None, corner_id=None, corner_w=None):
 
 def tb_workspace_bytes(h):
     return load().tb_workspace_bytes(h)
+
+
+def tb_source_event_layout(lin, n1, n2):
+    """The sweep kernel's source table layout for grid points `lin` (host
+    only): (ev_pair [n1 * ceil(n2/2), 2] int32, slot [npts] int32, nev)."""
+    import numpy as np
+    lin = np.ascontiguousarray(lin, dtype=np.int64)
+    npair = (int(n2) + 1) // 2
+    ev = np.zeros((int(n1) * npair, 2), dtype=np.int32)
+    slot = np.zeros(max(len(lin), 1), dtype=np.int32)
+    nev = C.c_int64(0)
+    st = load().tb_source_event_layout(len(lin), lin.ctypes.data, int(n1), int(n2), ev.ctypes.data,
+                                       slot.ctypes.data, C.byref(nev))
+    if st != 0:
+        raise TBError(st, "tb_source_event_layout")
+    return ev, slot[:len(lin)], nev.value
 
 
 def tb_plan_pipeline(n1, n2, space_order, time_tile, n_tiles, cap):

@@ -628,6 +628,63 @@ extern "C" int tb_set_model(tb_handle* h, const float* vp, const float* aux, con
   return TB_OK;
 }
 
+// The sweep kernel's source event layout (host only): the points of each
+// column pair (y, 2p), (y, 2p + 1) share one range of planes [first, last];
+// ev_pair[y * npair + p] = (first | span << 16, base) and the injection of the
+// point at plane x of column 2p + c goes to slot 2 (base + x - first) + c of
+// every step's row (nev = the sum of the spans).  Returns TB_EINVAL when a
+// plane or span does not fit 16 bits or the rows exceed the int32 slot range.
+static int event_layout(const int64_t* lin, int64_t np, int64_t n1, int64_t n2, std::vector<int2>& evp,
+                        std::vector<int>& slot, int64_t* nev, int* max_span) {
+  const int64_t npair = (n2 + 1) / 2;
+  std::vector<int64_t> ord(np);
+  for (int64_t i = 0; i < np; ++i) ord[i] = i;
+  // points ordered by (row, pair, plane)
+  auto key = [&](int64_t i) {
+    const int64_t z = lin[i] % n2, y = (lin[i] / n2) % n1, x = lin[i] / (n1 * n2);
+    return std::make_pair(y * npair + z / 2, x);
+  };
+  std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
+  evp.assign((size_t)(n1 * npair), make_int2(0, 0));
+  slot.assign((size_t)np, 0);
+  int64_t base = 0;
+  int mspan = 0;
+  for (int64_t g = 0; g < np;) {
+    const int64_t pr = key(ord[g]).first;
+    int64_t g1 = g;
+    while (g1 < np && key(ord[g1]).first == pr) ++g1;
+    const int64_t xf = key(ord[g]).second, xl = key(ord[g1 - 1]).second, span = xl - xf + 1;
+    if (xf > 0xffff || span > 0xffff) return TB_EINVAL;
+    evp[pr] = make_int2((int)(xf | (span << 16)), (int)base);
+    mspan = std::max(mspan, (int)span);
+    for (int64_t i = g; i < g1; ++i) slot[ord[i]] = (int)(2 * (base + key(ord[i]).second - xf) + (lin[ord[i]] % n2) % 2);
+    base += span;
+    if (2 * base >= (int64_t)INT32_MAX) return TB_EINVAL;
+    g = g1;
+  }
+  *nev = base;
+  *max_span = mspan;
+  return TB_OK;
+}
+
+extern "C" int tb_source_event_layout(int64_t npts, const int64_t* lin, int64_t n1, int64_t n2, int* ev_pair,
+                                      int* slot, int64_t* nev) {
+  if (npts < 0 || n1 < 1 || n2 < 1 || (npts > 0 && (!lin || !slot)) || !ev_pair || !nev) return TB_EINVAL;
+  for (int64_t i = 0; i < npts; ++i)
+    if (lin[i] < 0) return TB_EINVAL;
+  std::vector<int2> evp;
+  std::vector<int> sl;
+  int mspan = 0;
+  const int s = event_layout(lin, npts, n1, n2, evp, sl, nev, &mspan);
+  if (s != TB_OK) return s;
+  for (size_t i = 0; i < evp.size(); ++i) {
+    ev_pair[2 * i] = evp[i].x;
+    ev_pair[2 * i + 1] = evp[i].y;
+  }
+  for (int64_t i = 0; i < npts; ++i) slot[i] = sl[(size_t)i];
+  return TB_OK;
+}
+
 extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int nt,
                               const float* wav, void* stream) {
   if (!h) return TB_EINVAL;
@@ -685,32 +742,8 @@ extern "C" int tb_set_sources(tb_handle* h, int nsrc, const double* coords, int 
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       std::vector<int> slot(np);
       std::vector<int2> evp;
-      if (e == cudaSuccess) {
-        // points ordered by (row, pair, plane)
-        std::vector<int64_t> ord(np);
-        for (int64_t i = 0; i < np; ++i) ord[i] = i;
-        auto key = [&](int64_t i) {
-          const int64_t z = lin[i] % n2, y = (lin[i] / n2) % n1, x = lin[i] / (n1 * n2);
-          return std::make_pair(y * h->npair + z / 2, x);
-        };
-        std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
-        evp.assign((size_t)n1 * h->npair, make_int2(0, 0));
-        int64_t base = 0;
-        for (int64_t g = 0; g < np;) {
-          const int64_t pr = key(ord[g]).first;
-          int64_t g1 = g;
-          while (g1 < np && key(ord[g1]).first == pr) ++g1;
-          const int64_t xf = key(ord[g]).second, xl = key(ord[g1 - 1]).second, span = xl - xf + 1;
-          evp[pr] = make_int2((int)(xf | (span << 16)), (int)base);
-          h->ev_max_span = std::max(h->ev_max_span, (int)span);
-          for (int64_t i = g; i < g1; ++i)
-            slot[ord[i]] = (int)(2 * (base + key(ord[i]).second - xf) + (lin[ord[i]] % n2) % 2);
-          base += span;
-          g = g1;
-        }
-        h->nev = base;
-        if (2 * base >= (int64_t)INT32_MAX) e = cudaErrorInvalidValue;
-      }
+      if (e == cudaSuccess && event_layout(lin.data(), np, n1, n2, evp, slot, &h->nev, &h->ev_max_span) != TB_OK)
+        e = cudaErrorInvalidValue;
       if (e == cudaSuccess) e = dmalloc(&h->ev_pair, sizeof(int2) * evp.size(), st);
       if (e == cudaSuccess) e = dmalloc(&h->src_ev, sizeof(float2) * (size_t)nt * h->nev, st);
       if (e == cudaSuccess) e = dmalloc(&d_slot, sizeof(int) * np, st);

@@ -3,6 +3,7 @@
 // blocked sweep, and the time loop of tb_forward.
 #include <algorithm>
 #include <climits>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -43,6 +44,30 @@ cudaError_t sweep_launch(int R, int T, const SweepParams& p, int nctas, bool coo
 }  // namespace tbi
 
 namespace tbi {
+cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = 4ull << 30;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
 static unsigned long long g_launches = 0;
 void count_launch(int n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
 }  // namespace tbi
@@ -166,7 +191,7 @@ static cudaError_t to_device(const void* src, size_t bytes, void** tmp, const vo
     *out = src;
     return cudaSuccess;
   }
-  cudaError_t e = cudaMallocAsync(tmp, bytes ? bytes : 1, st);
+  cudaError_t e = dmalloc(tmp, bytes, st);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(*tmp, src, bytes, cudaMemcpyHostToDevice, st);
   *out = *tmp;

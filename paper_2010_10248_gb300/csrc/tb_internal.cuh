@@ -165,11 +165,17 @@ cudaError_t adjoint_finish(const PhysGrid& g, double dt, const double* gm, const
                            cudaStream_t st);
 cudaError_t transpose_f32(int64_t rows, int64_t cols, const float* in, float* out, cudaStream_t st);
 
-// Stream-ordered device memory (cudaMallocAsync / cudaFreeAsync): creating,
-// reconfiguring or destroying a handle never synchronises the whole device,
-// so work of other handles on other streams keeps running meanwhile.
+// Stream-ordered device memory (cudaMallocFromPoolAsync / cudaFreeAsync):
+// creating, reconfiguring or destroying a handle never synchronises the whole
+// device, so work of other handles on other streams keeps running meanwhile.
+// The library's pool of the current device keeps up to 4 GiB of freed memory
+// mapped (the default pool returns it at once, and remapping the staging
+// buffer of a 512^3 model cost every shot), NULL if it cannot be made.
+cudaMemPool_t library_pool();
 template <class T>
 inline cudaError_t dmalloc(T** p, size_t bytes, cudaStream_t st) {
+  cudaMemPool_t pool = library_pool();
+  if (pool) return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), bytes ? bytes : 1, pool, st);
   return cudaMallocAsync(reinterpret_cast<void**>(p), bytes ? bytes : 1, st);
 }
 inline void dfree(void* p, cudaStream_t st) {

@@ -124,7 +124,9 @@ typedef struct {
 int tb_create(const int64_t n[3], const double h[3], int space_order, int physics,
               const tb_options* opt, tb_handle** out);
 
-/* Release every device allocation of the handle (NULL is accepted). */
+/* Release every device allocation of the handle and the handle itself
+ * (stream-ordered frees on the handle's last stream).  NULL is accepted.
+ * Returns TB_OK. */
 int tb_destroy(tb_handle* h);
 
 /* Set the velocity model (Eq. 1: m = 1/vp^2).  vp: field of P velocities in
@@ -142,7 +144,8 @@ int tb_destroy(tb_handle* h);
 int tb_set_model(tb_handle* h, const float* vp, const float* aux, const float* damp,
                  double dt, void* stream);
 
-/* Time step in use (after tb_set_model), or 0. */
+/* Time step in seconds in use after tb_set_model; 0 for a NULL handle or
+ * before tb_set_model. */
 double tb_get_dt(const tb_handle* h);
 
 /* Register nsrc off-grid sources and run the inspector on the device
@@ -182,23 +185,33 @@ int tb_forward(tb_handle* h, int nt, float* traces, int schedule, void* stream);
  * host or device).  Acoustic: which = 0 -> u^{nt}, 1 -> u^{nt-1}.  TTI:
  * 0 -> p^{nt}, 1 -> p^{nt-1}, 2 -> r^{nt}, 3 -> r^{nt-1}.  Elastic: 0..8 ->
  * vx, vy, vz (at nt - 1/2; vx at (i+1/2, j, k) etc.), txx, tyy, tzz, txy,
- * txz, tyz (at nt; txy at (i+1/2, j+1/2, k) etc.). */
+ * txz, tyz (at nt; txy at (i+1/2, j+1/2, k) etc.).  16-bit storage returns
+ * the stored value times its step's scale.  Ordered on `stream` (a host
+ * destination makes the call synchronous).  Errors: TB_EINVAL (NULL handle
+ * or out, `which` out of range), TB_ESTATE (no tb_forward yet, or the fields
+ * were overwritten by tb_adjoint_gradient), TB_ECUDA. */
 int tb_get_field(tb_handle* h, int which, float* out, void* stream);
 
 /* Inspector tables, for checking against an independent implementation.
  * Source points: *npts receives the number of affected points; lin (host,
  * may be NULL) receives their ascending linear indices (x n1 + y) n2 + z,
  * which is the paper's SID order; dcmp (host, may be NULL) receives
- * src_dcmp as [nt][npts] float.  Synchronous. */
+ * src_dcmp as [nt][npts] float (nt: the wavelet length given to
+ * tb_set_sources).  Caller-owned arrays; call first with lin = dcmp = NULL
+ * to size them.  Synchronous.  Errors: TB_EINVAL (NULL handle or npts),
+ * TB_ESTATE (no sources set), TB_ECUDA. */
 int tb_get_source_points(tb_handle* h, int64_t* npts, int64_t* lin, float* dcmp);
 
 /* Receiver points: *npts, ascending linear indices (host, may be NULL), and
  * per receiver its 8 corner point ids (-1 for a zero weight) and weights
- * (host arrays [nrec][8], may be NULL).  Synchronous. */
+ * (host arrays [nrec][8], may be NULL).  Caller-owned arrays.  Synchronous.
+ * Errors: TB_EINVAL (NULL handle or npts), TB_ESTATE (no receivers set),
+ * TB_ECUDA. */
 int tb_get_receiver_points(tb_handle* h, int64_t* npts, int64_t* lin, int32_t* corner_id,
                            float* corner_w);
 
-/* Device bytes held by the handle (fields, model, tables, scratch). */
+/* Device bytes held by the handle (fields, model, tables, scratch); 0 for a
+ * NULL handle.  Never fails. */
 size_t tb_workspace_bytes(const tb_handle* h);
 
 /* Host-side layout of the sweep kernel's source table (Sec. II-A's
@@ -233,10 +246,13 @@ int tb_plan_pipeline(int n1, int n2, int space_order, int time_tile, int n_tiles
 /* With opt.profile = 1: number of propagator launches of the last
  * tb_forward and their summed device time in ms, measured with CUDA events
  * on the launching stream; kind 0 = propagator sweeps, 1 = receiver
- * finalize.  Synchronises the stream of the last forward. */
+ * finalize.  Synchronises the stream of the last forward.  Errors: TB_EINVAL
+ * (NULL arguments), TB_ESTATE (profiling off). */
 int tb_kernel_time(tb_handle* h, int kind, int* launches, double* ms);
 
-/* Message of the last failing call on this handle ("" if none). */
+/* Message of the last failing call on this handle ("" if the last call
+ * succeeded; "null handle" for NULL).  Owned by the handle, valid until its
+ * next call. */
 const char* tb_last_error(const tb_handle* h);
 
 /* --- Setup arithmetic (host, FP64), exported for testing --------------- */
@@ -253,11 +269,13 @@ double tb_cfl_dt_max(int space_order, const double h[3], double vmax);
 
 /* Built-in sponge along one axis: eta[i] = eta_max (d/nbl)^2, d the
  * distance in cells into the layer (1..nbl), eta_max = 3 vmax ln(1000) /
- * (2 nbl h).  eta: host array of n doubles. */
+ * (2 nbl h) (Sec. IV-B).  eta: caller-owned host array of n doubles.
+ * Errors: TB_EINVAL (n < 1, nbl < 0, h <= 0, NULL eta). */
 int tb_sponge_profile(int64_t n, int nbl, double h, double vmax, double* eta);
 
 /* Ricker wavelet q(t_n) = (1 - 2 a) exp(-a), a = (pi f0 (n dt - t0))^2,
- * t0 = 1/f0 when t0 <= 0.  out: host array of nt floats. */
+ * t0 = 1/f0 when t0 <= 0.  out: caller-owned host array of nt floats.
+ * Errors: TB_EINVAL (f0 <= 0, nt < 0, NULL out). */
 int tb_ricker(double f0, double dt, int nt, double t0, float* out);
 
 /* --- Diagnostics ---------------------------------------------------- */

@@ -308,7 +308,8 @@ int tb_measure_peaks(double* hbm_gbs, double* fp32_tflops, void* stream);
  * fixed array of about 1.8 MB in device memory, which every GPU that loads
  * the library holds until the process exits.  (The paper has no
  * counterpart; it is an interface addition of this library.)
- *   n, h       grid shape and spacing, as for tb_create (host arrays).
+ *   n, h       grid shape and spacing (host arrays): 2 <= n_d <= 65535,
+ *              n0 n1 n2 < 2^40, h_d > 0, else TB_EINVAL.
  *   npt        number of points, 0..8192; more is rejected with TB_EINVAL.
  *   coords     device array [npt][3] of FP64 metres.
  *   lin        device array with room for 8 * npt int64 values; receives the
@@ -316,9 +317,12 @@ int tb_measure_peaks(double* hbm_gbs, double* fp32_tflops, void* stream);
  *              points (the paper's SID order).
  *   npts       device int64: receives their number, or -1 when a coordinate
  *              lies outside [0, (n_d - 1) h_d].
- * Asynchronous on `stream`.  The first call on each device looks up the
- * device address of the scratch array (with that device current); make
- * that first call before any stream capture.  Nothing in the array has to
+ * Asynchronous on `stream`, which must belong to the current device
+ * (TB_EINVAL otherwise; NULL is the current device's legacy stream).  The
+ * first call on each device looks up the device address of the scratch
+ * array (with that device current) and keeps it for the process: make that
+ * first call before any stream capture, and make no call on a device after
+ * a cudaDeviceReset of it.  Nothing in the array has to
  * start at zero: each call clears its own out-of-grid flag and overwrites
  * the rest before reading it.  Every call shares the one array and it keeps
  * the last call's contents: calls that overlap on the GPU

@@ -103,6 +103,7 @@ def _load():
             L.orc_elastic_forward.argtypes = [gp, dp, dp, dp, dp, C.c_int, dp, dp, C.c_int, dp, dp,
                                               dp, dp]
             L.orc_elastic_energy.argtypes = [gp, dp, dp, dp, dp, dp, dp]
+            L.orc_elastic_materials.argtypes = [gp, dp, dp, dp, dp]
             L.orc_elastic_energy.restype = C.c_double
             L.orc_acoustic_adjoint.argtypes = [gp, dp, dp, C.c_int, dp, dp, C.c_int, dp, dp, dp, dp]
         return _lib
@@ -338,6 +339,18 @@ def elastic_forward(shape, spacing, so, dt, nt, vp, vs, rho, *, nbl=0, eta=None,
                                      _dp(_f64(init)), _dp(out))
     _check(st, "elastic_forward")
     return traces[:, :nrec], out
+
+
+def elastic_materials(shape, spacing, so, vp, vs, rho):
+    """The staggered scheme's material arrays (R18), as the oracle builds them:
+    dict of bx, by, bz (buoyancy at half-nodes), lam, mu (nodes), mxy, mxz,
+    myz (harmonic shear modulus at edge centres), each of shape ``shape``."""
+    g = make_grid(shape, spacing, so, 1e-3, 1)
+    args = [_f64(np.broadcast_to(a, tuple(shape))) for a in (vp, vs, rho)]
+    out = np.zeros((8,) + tuple(shape))
+    _check(_load().orc_elastic_materials(C.byref(g), *[_dp(a) for a in args], _dp(out)),
+           "elastic_materials")
+    return dict(zip(("bx", "by", "bz", "lam", "mu", "mxy", "mxz", "myz"), out))
 
 
 def elastic_energy(shape, spacing, so, dt, vp, vs, rho, v_next, v_prev, tau, periodic=False):

@@ -27,7 +27,7 @@
  *   so/2 that is never updated).  A periodic mode exists only for the
  *   closed-form eigenmode pin in the tests.
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent, and the reading taken here:
  *   - affected points are the trilinear corners with FP64 weight != 0
  *     (structural, independent of the wavelet values; Sec. II-A.1);
  *   - the unique IDs of Sec. II-A.2 ascend with the linear index
@@ -1206,6 +1206,23 @@ static int ela_init(ela_t* E, const orc_grid* g, const double* vp, const double*
     for (int d = 0; d < 3; ++d) free(ea[d]);
   }
   return ORC_OK;
+}
+
+/* Test hook: the material arrays of the staggered scheme as ela_init builds
+ * them (R18's averaging), so that a test can restate them independently.
+ * out: [8][N] = bx, by, bz (half-nodes along x, y, z), lam, mu (nodes),
+ * mu_xy, mu_xz, mu_yz (edge centres). */
+int orc_elastic_materials(const orc_grid* g, const double* vp, const double* vs, const double* rho,
+                          double* out) {
+  ela_t E;
+  int st = ela_init(&E, g, vp, vs, rho, NULL);
+  if (st == ORC_OK) {
+    int64_t N = g->n[0] * g->n[1] * g->n[2];
+    const double* src[8] = {E.bx, E.by, E.bz, E.lam, E.mu, E.mxy, E.mxz, E.myz};
+    for (int i = 0; i < 8; ++i) memcpy(out + (int64_t)i * N, src[i], sizeof(double) * N);
+  }
+  ela_free(&E);
+  return st;
 }
 
 static inline int64_t ela_stride(const pad_t* p, int d) {

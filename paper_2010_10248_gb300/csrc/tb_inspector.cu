@@ -599,10 +599,21 @@ extern "C" int tb_inspect_points_noalloc(const int64_t n[3], const double h[3], 
   if (npt > 0 && (!coords || !lin)) return TB_EINVAL;
   for (int d = 0; d < 3; ++d)
     if (n[d] < 2 || n[d] > 65535 || !(h[d] > 0)) return TB_EINVAL;
+  // the sort key holds the linear index above 24 bits of corner number: the
+  // same grid-size limit as tb_create
+  if (n[0] * n[1] * n[2] >= (1ll << 40)) return TB_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return TB_ECUDA;
+  if (st) {  // the scratch address is per device: the stream must be the current device's
+    int sdev = -1;
+    if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+      cudaGetLastError();
+      return TB_EINVAL;
+    }
+    if (sdev != dev) return TB_EINVAL;
+  }
   unsigned char* base = (unsigned char*)noalloc_scratch(dev, &e);
   if (!base) {
     cudaGetLastError();

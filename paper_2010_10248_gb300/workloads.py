@@ -182,8 +182,10 @@ def acoustic_512_so8(seed: int = BASE_SEED + 1, shape=(512, 512, 512), nt: int =
     src = np.array([[(0.5 * (shape[0] - 1) + g.uniform(-0.5, 0.5)) * h[0],
                      (0.5 * (shape[1] - 1) + g.uniform(-0.5, 0.5)) * h[1],
                      (nbl + 10 + g.uniform(0.05, 0.95)) * h[2]]])
-    nrx = min(256, (shape[0] - 1) // 2)
-    nry = min(256, (shape[1] - 1) // 2)
+    # spacing 2h from a sub-cell offset < 1: n // 2 receivers fit in n - 1 cells
+    # (256 x 256 = 65,536 at 512^3)
+    nrx = min(256, shape[0] // 2)
+    nry = min(256, shape[1] // 2)
     rec = receiver_plane(shape, h, seed + 3, nrx, nry, depth_cells=nbl + 20)
     vp = layered_vp(shape, seed + 4)
     return Workload(f"acoustic {shape[0]}x{shape[1]}x{shape[2]} so8 {nt} steps", tuple(shape), h,

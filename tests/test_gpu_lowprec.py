@@ -39,9 +39,13 @@ def case():
     return w, dt, wav, tr, u
 
 
-# (storage, bound on rel-L2 vs FP64) -- the 16-bit bounds are loose ceilings;
-# the measured values are printed and recorded in the design notes
-LIMITS = {"TB_F32_PLAIN": 1e-4, "TB_F16": 2e-2, "TB_BF16": 2e-1}
+# (traces, field) bounds on rel-L2 against FP64: about 1.5x the errors measured
+# on GB300 (72 x 70 x 96, so8, 300 steps: plain FP32 4.2e-7 / 7.0e-7, FP16
+# 3.1e-3 / 5.0e-3, BF16 4.9e-2 / 5.8e-2), so that a scaling mistake that
+# doubles the error fails; the plain-FP32 variant also meets the 1e-4 bar
+LIMITS = {"TB_F32_PLAIN": (6.5e-7, 1.1e-6), "TB_F16": (4.7e-3, 7.5e-3), "TB_BF16": (7.4e-2, 8.7e-2)}
+# the ragged case (37 x 45 x 83, 80 steps): FP16 1.2e-3 / 2.1e-3, BF16 9.6e-3 / 1.7e-2
+LIMITS_RAGGED = {"TB_F16": (1.8e-3, 3.2e-3), "TB_BF16": (1.45e-2, 2.6e-2)}
 
 
 @pytest.mark.parametrize("storage", list(LIMITS))
@@ -56,7 +60,7 @@ def test_storage_error_against_oracle(tb, case, storage):
     u = p.field(0).cpu().numpy()
     e_tr, e_u = rel_l2(tr, tr_o), rel_l2(u, u_o)
     print(f"{storage}: traces rel-L2 {e_tr:.2e}, field rel-L2 {e_u:.2e} ({w.nt} steps)")
-    assert e_tr <= LIMITS[storage] and e_u <= LIMITS[storage]
+    assert e_tr <= LIMITS[storage][0] and e_u <= LIMITS[storage][1]
     with pytest.raises(tb.TBError):
         p.forward(4, schedule="blocked")
 
@@ -83,7 +87,7 @@ def test_storage_ragged_grid(tb, storage):
     u = p.field(0).cpu().numpy()
     e_tr, e_u = rel_l2(tr, tr_o), rel_l2(u, u_o)
     print(f"{storage} ragged: traces rel-L2 {e_tr:.2e}, field rel-L2 {e_u:.2e}")
-    assert e_tr <= LIMITS[storage] and e_u <= LIMITS[storage]
+    assert e_tr <= LIMITS_RAGGED[storage][0] and e_u <= LIMITS_RAGGED[storage][1]
 
 
 def test_workspace_counts_the_stored_fields(tb):

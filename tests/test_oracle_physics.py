@@ -277,3 +277,45 @@ def test_elastic_without_shear_is_the_staggered_acoustic_scheme(so):
     assert np.abs(u_b).max() > 1e-6
     np.testing.assert_allclose(st[5], u_b, rtol=0, atol=1e-11 * np.abs(u_b).max())
     np.testing.assert_allclose(tr, tr_b, rtol=0, atol=1e-11 * np.abs(tr_b).max())
+
+
+def test_elastic_material_averaging_restated():
+    """R18's averaging, restated in numpy and compared array by array with the
+    oracle's: b = 1/rho at a half-node is the mean of its two nodes, mu at an
+    edge centre the harmonic mean of its four nodes (0 when one is 0), and a
+    neighbour beyond the last node takes the last node's value (Sec. III-C,
+    Eq. 3 on the Virieux grid).  Every edge and corner of the grid is in the
+    comparison, so a change to the edge rule fails here."""
+    shape = (7, 6, 9)
+    g = np.random.Generator(np.random.PCG64(20101018))
+    vp = g.uniform(2000.0, 3000.0, shape)
+    vs = vp / g.uniform(1.6, 2.2, shape)
+    vs[g.uniform(size=shape) < 0.15] = 0.0          # fluid points: mu = 0
+    vs[-1, :, 2] = 0.0                              # on the upper x face
+    rho = g.uniform(1000.0, 2500.0, shape)
+    got = oracle.elastic_materials(shape, (10.0, 11.0, 12.0), 4, vp, vs, rho)
+
+    def nb(a, d):   # value at index + 1 along axis d, the last node repeated
+        return np.concatenate([np.take(a, np.arange(1, a.shape[d]), axis=d),
+                               np.take(a, [a.shape[d] - 1], axis=d)], axis=d)
+
+    mu = rho * vs ** 2
+    lam = rho * (vp ** 2 - 2.0 * vs ** 2)
+    b = 1.0 / rho
+
+    def harm(a, b_, c, d):
+        with np.errstate(divide="ignore"):
+            h = 4.0 / (1.0 / a + 1.0 / b_ + 1.0 / c + 1.0 / d)
+        return np.where((a > 0) & (b_ > 0) & (c > 0) & (d > 0), h, 0.0)
+
+    want = {
+        "lam": lam, "mu": mu,
+        "bx": 0.5 * (b + nb(b, 0)), "by": 0.5 * (b + nb(b, 1)), "bz": 0.5 * (b + nb(b, 2)),
+        "mxy": harm(mu, nb(mu, 0), nb(mu, 1), nb(nb(mu, 0), 1)),
+        "mxz": harm(mu, nb(mu, 0), nb(mu, 2), nb(nb(mu, 0), 2)),
+        "myz": harm(mu, nb(mu, 1), nb(mu, 2), nb(nb(mu, 1), 2)),
+    }
+    for k, v in want.items():
+        np.testing.assert_allclose(got[k], v, rtol=1e-14, atol=0.0, err_msg=k)
+    # the edge rule is visible: the last x-face's bx is that node's own 1/rho
+    np.testing.assert_allclose(got["bx"][-1], b[-1], rtol=1e-15)

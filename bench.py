@@ -238,6 +238,15 @@ def cpu_oracle_rate_physics(physics, mk, size, steps_a, steps_b):
     return N * (steps_b - steps_a) / dtime / 1e9, t[0] + t[1], threads, sample
 
 
+def bench_config(w, args, ws):
+    """The workload of the headline line (the same dict in both arms)."""
+    return {"workload": w.name, "grid": list(w.shape), "space_order": w.so, "nt": w.nt,
+            "time_tile": args.time_tile, "receivers": len(w.rec_xyz), "sources": len(w.src_xyz),
+            "schedule": "blocked", "parallelism": f"replicas x{ws}",
+            "l2": "inputs larger than L2 (512 MiB per field, 5 fields)",
+            "step": "set_model + set_sources + set_receivers + forward(nt)"}
+
+
 def oracle_full_runs():
     """Whole runs of the FP64 oracle (setup included) on one thread and on
     every host core: the 64^3 so4 100-step workload and the 512^3 recipe at
@@ -294,9 +303,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": float(np.mean(walls)) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "grid": list(w.shape), "space_order": w.so,
-                       "nt": w.nt, "receivers": len(w.rec_xyz),
-                       "sample_steps_per_bench_step": 4 + args.cpu_steps},
+            "config": bench_config(w, args, ws),
+            "sample_steps_per_bench_step": 4 + args.cpu_steps,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -482,11 +490,7 @@ def run_native(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": w.name, "grid": list(w.shape), "space_order": w.so,
-                           "nt": nt, "time_tile": T, "receivers": nrec, "sources": len(w.src_xyz),
-                           "schedule": "blocked", "parallelism": f"replicas x{ws}",
-                           "l2": "inputs larger than L2 (512 MiB per field, 5 fields)",
-                           "step": "set_model + set_sources + set_receivers + forward(nt)"},
+                "config": bench_config(w, args, ws),
                 "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
                 "cpu_baseline": cpu, **out}
         if out.get("onestep"):

@@ -358,6 +358,52 @@ int tb_inspect_points_noalloc(const int64_t n[3], const double h[3], int npt, co
 int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, float* grad_vp, float* grad_src,
                         int n_snapshots, void* stream);
 
+/* Checkpointing of tb_adjoint_gradient_ckpt. */
+enum { TB_CKPT_SEGMENTS = 0, TB_CKPT_BINOMIAL = 1 };
+
+/* tb_adjoint_gradient with a choice of how the backward pass gets the
+ * forward states it needs (same arguments and results otherwise; both give
+ * bit-identical gradients, every state being the same sequence of one-step
+ * sweeps from the zero initial condition):
+ *   TB_CKPT_SEGMENTS  as tb_adjoint_gradient: a checkpoint every
+ *     ceil(nt/S) steps and a segment buffer of ceil(nt/S) + 2 states; every
+ *     step is recomputed once (2 nt forward steps in all); device scratch
+ *     about (2 S + ceil(nt/S) + 5) fields;
+ *   TB_CKPT_BINOMIAL  exactly S = n_snapshots stored states (two fields
+ *     each) in Griewank's binomial schedule (tb_plan_checkpoints), the least
+ *     recomputation S states allow; device scratch (2 S + 3) fields plus
+ *     the adjoint's own 4 (two mu fields, the FP64 gradient sum), whatever
+ *     nt is.  1 <= n_snapshots <= 4096.
+ * tb_adjoint_stats reports the forward steps the call ran and its scratch.
+ * Errors: as tb_adjoint_gradient, TB_EINVAL for another checkpointing. */
+int tb_adjoint_gradient_ckpt(tb_handle* h, int nt, const float* residual, float* grad_vp, float* grad_src,
+                             int n_snapshots, int checkpointing, void* stream);
+
+/* Accounting of the last adjoint gradient of the handle: *forward_steps =
+ * the forward time steps (one-step sweeps) it ran, its reverse steps' own
+ * recomputations included (-1 before any), *scratch_bytes = the device
+ * bytes it allocated for its own use and freed before returning (states,
+ * adjoint fields, FP64 sum, tables).  Host outputs.  Errors: TB_EINVAL
+ * (NULL argument). */
+int tb_adjoint_stats(const tb_handle* h, int64_t* forward_steps, size_t* scratch_bytes);
+
+/* Host-side binomial checkpoint schedule (no GPU needed), the one
+ * TB_CKPT_BINOMIAL runs.  X_n = (u^n, u^{n-1}) is the forward state after n
+ * steps (X_0 = 0, never stored); reversing forward step n (adjoint step
+ * n + 1) needs X_n and runs that forward step once itself.  With
+ * n_snapshots = S storage slots, writes up to max_actions actions of 5 ints
+ * (kind, from, to, src, dst) in execution order (caller-owned):
+ *   kind 0, advance: compute X_to from X_from held at src into dst;
+ *   kind 1, reverse: reverse forward step `from` (= to) with X_from at src;
+ * locations: a slot 0 .. S-1, -1 the zero state X_0, -2 a work pair.  The
+ * reverse actions come in the order nt-1 .. 0.  *forward_steps (may be
+ * NULL) receives the forward steps of the schedule (advanced steps plus one
+ * per reverse action), the minimum for S slots: t l - C(S + t + 1, t - 1)
+ * advanced steps, t the least integer with C(S + 1 + t, t) >= nt.  Returns
+ * the number of actions (which may exceed max_actions), or -TB_EINVAL for
+ * nt < 1, S < 0 or S > 4096. */
+int tb_plan_checkpoints(int nt, int n_snapshots, int* actions, int max_actions, int64_t* forward_steps);
+
 /* Stability limits of the TTI and elastic schemes (seconds), -1 on bad
  * arguments.  TTI: 2 / (vmax sqrt(1 + 2 eps_max) sqrt(sum_d (S1/h_d)^2)),
  * S1 = max |2 sum a_i sin(i t)| over the centred first-derivative weights

@@ -9,8 +9,9 @@ from __future__ import annotations
 
 from . import _tb
 from ._tb import (TB_ACOUSTIC, TB_BF16, TB_BLOCKED, TB_ELASTIC, TB_F16, TB_F32, TB_F32_PLAIN, TB_ONESTEP,
-                  TB_TTI, Options, TBError, load,
-                  tb_adjoint_gradient, tb_cfl_dt_max, tb_elastic_dt_max, tb_tti_dt_max,
+                  TB_TTI, TB_CKPT_BINOMIAL, TB_CKPT_SEGMENTS, Options, TBError, load,
+                  tb_adjoint_gradient, tb_adjoint_gradient_ckpt, tb_adjoint_stats, tb_plan_checkpoints,
+                  tb_cfl_dt_max, tb_elastic_dt_max, tb_tti_dt_max,
                   tb_create, tb_destroy, tb_fd_weights, tb_forward, tb_get_dt, tb_get_field,
                   tb_get_receiver_points, tb_get_source_points, tb_kernel_time, tb_last_error,
                   tb_launch_count, tb_measure_peaks, tb_ricker, tb_selftest_wait, tb_set_model, tb_set_receivers, tb_set_sources,
@@ -18,6 +19,8 @@ from ._tb import (TB_ACOUSTIC, TB_BF16, TB_BLOCKED, TB_ELASTIC, TB_F16, TB_F32, 
 
 __all__ = ["Propagator", "Options", "TBError", "load", "TB_ONESTEP", "TB_BLOCKED", "TB_ACOUSTIC",
            "TB_TTI", "TB_ELASTIC", "tb_tti_dt_max", "tb_elastic_dt_max", "tb_adjoint_gradient",
+           "tb_adjoint_gradient_ckpt", "tb_adjoint_stats", "tb_plan_checkpoints", "TB_CKPT_SEGMENTS",
+           "TB_CKPT_BINOMIAL",
            "AcousticTraces", "TB_F32", "TB_F16", "TB_BF16", "TB_F32_PLAIN",
            "tb_create", "tb_destroy", "tb_set_model", "tb_get_dt", "tb_set_sources",
            "tb_set_receivers", "tb_forward", "tb_get_field", "tb_get_source_points",
@@ -134,12 +137,20 @@ class Propagator:
         tb_get_receiver_points(self.h, lin, cid, cw)
         return lin[:n], cid[: self.nrec], cw[: self.nrec]
 
-    def adjoint_gradient(self, nt, residual, grad_vp=None, grad_src=None, n_snapshots=32):
-        """d<traces, residual>/dvp (and /dq) for the current model and geometry."""
+    def adjoint_gradient(self, nt, residual, grad_vp=None, grad_src=None, n_snapshots=32,
+                         checkpointing="segments"):
+        """d<traces, residual>/dvp (and /dq) for the current model and geometry.
+        checkpointing: "segments" (checkpoints every ceil(nt/S) steps and a
+        segment buffer) or "binomial" (exactly S stored states)."""
         torch = self._torch
         residual = residual.to(dtype=torch.float32).contiguous() if hasattr(residual, "data_ptr") else residual
-        tb_adjoint_gradient(self.h, nt, residual, grad_vp, grad_src, n_snapshots, self._stream())
+        ck = {"segments": TB_CKPT_SEGMENTS, "binomial": TB_CKPT_BINOMIAL}[checkpointing]
+        tb_adjoint_gradient_ckpt(self.h, nt, residual, grad_vp, grad_src, n_snapshots, ck, self._stream())
         return grad_vp, grad_src
+
+    def adjoint_stats(self):
+        """(forward steps, device scratch bytes) of the last adjoint gradient."""
+        return tb_adjoint_stats(self.h)
 
     def kernel_time(self, kind=0):
         return tb_kernel_time(self.h, kind)

@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "TB_OK", 1: "TB_EINVAL", 2: "TB_ENOMEM", 3: "TB_ECUDA", 4: "T
 TB_ACOUSTIC, TB_TTI, TB_ELASTIC = 0, 1, 2
 TB_ONESTEP, TB_BLOCKED = 0, 1
 TB_F32, TB_F16, TB_BF16, TB_F32_PLAIN = 0, 1, 2, 3
+TB_CKPT_SEGMENTS, TB_CKPT_BINOMIAL = 0, 1
 
 
 class TBError(RuntimeError):
@@ -60,6 +61,10 @@ _SIGS = {
     "tb_cfl_dt_max": (C.c_double, [C.c_int, C.POINTER(C.c_double), C.c_double]),
     "tb_tti_dt_max": (C.c_double, [C.c_int, C.POINTER(C.c_double), C.c_double, C.c_double]),
     "tb_adjoint_gradient": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int, _vp]),
+    "tb_adjoint_gradient_ckpt": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int, C.c_int, _vp]),
+    "tb_adjoint_stats": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_size_t)]),
+    "tb_plan_checkpoints": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int,
+                                      C.POINTER(C.c_int64)]),
     "tb_elastic_dt_max": (C.c_double, [C.c_int, C.POINTER(C.c_double), C.c_double]),
     "tb_sponge_profile": (C.c_int, [C.c_int64, C.c_int, C.c_double, C.c_double,
                                     C.POINTER(C.c_double)]),
@@ -252,6 +257,34 @@ def tb_cfl_dt_max(space_order, spacing, vmax):
 def tb_adjoint_gradient(h, nt, residual, grad_vp=None, grad_src=None, n_snapshots=32, stream=None):
     _check(h, load().tb_adjoint_gradient(h, int(nt), _ptr(residual), _ptr(grad_vp), _ptr(grad_src),
                                          int(n_snapshots), _stream(stream)), "tb_adjoint_gradient")
+
+
+def tb_adjoint_gradient_ckpt(h, nt, residual, grad_vp=None, grad_src=None, n_snapshots=32,
+                             checkpointing=TB_CKPT_BINOMIAL, stream=None):
+    _check(h, load().tb_adjoint_gradient_ckpt(h, int(nt), _ptr(residual), _ptr(grad_vp), _ptr(grad_src),
+                                              int(n_snapshots), int(checkpointing), _stream(stream)),
+           "tb_adjoint_gradient_ckpt")
+
+
+def tb_adjoint_stats(h):
+    """(forward steps, scratch bytes) of the handle's last adjoint gradient."""
+    fs, sb = C.c_int64(0), C.c_size_t(0)
+    _check(h, load().tb_adjoint_stats(h, C.byref(fs), C.byref(sb)), "tb_adjoint_stats")
+    return int(fs.value), int(sb.value)
+
+
+def tb_plan_checkpoints(nt, n_snapshots):
+    """The binomial checkpoint schedule as an int array [nactions, 5] (kind,
+    from, to, src, dst) and its forward-step count (host only, no GPU)."""
+    import numpy as np
+    lib = load()
+    fs = C.c_int64(0)
+    n = lib.tb_plan_checkpoints(int(nt), int(n_snapshots), None, 0, C.byref(fs))
+    if n < 0:
+        raise TBError(-n, "tb_plan_checkpoints: invalid arguments")
+    out = np.zeros((max(n, 1), 5), dtype=np.int32)
+    lib.tb_plan_checkpoints(int(nt), int(n_snapshots), out.ctypes.data_as(C.POINTER(C.c_int)), n, C.byref(fs))
+    return out[:n], int(fs.value)
 
 
 def tb_tti_dt_max(space_order, spacing, vmax, eps_max):

@@ -143,6 +143,8 @@ struct tb_handle {
   size_t traces_cap = 0;
   // result of the last forward
   int last_nt = -1;
+  int64_t last_fwd_steps = -1;  // forward steps of the last adjoint gradient
+  size_t last_scratch = 0;      // device bytes it allocated
   int cur_idx = 0, prev_idx = 1;
   // profiling
   std::vector<cudaEvent_t> ev;
@@ -1680,43 +1682,69 @@ static int runner_step(tb_handle* h, StepRunner* r, int cur, int prev, int step,
   return runner_step_on(h, r, h->field[cur], h->field[prev], h->tm_box[cur], h->tm_tile[prev], step, st);
 }
 
-extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, float* grad_vp, float* grad_src,
-                                   int n_snapshots, void* stream) {
+// Adjoint-state gradient with one of two ways to provide the forward states
+// the backward pass needs (u^k, u^{k-1}, u^{k-2} at adjoint step k):
+//   TB_CKPT_SEGMENTS: a checkpoint every ceil(nt/S) steps and a segment
+//     buffer of ceil(nt/S) + 2 states, every step recomputed once;
+//   TB_CKPT_BINOMIAL: S stored states in Griewank's binomial schedule
+//     (tb_checkpoint.cu), the least recomputation S states allow.
+// Both give bit-identical gradients: every forward state is the same
+// sequence of one-step sweeps from the zero initial condition.
+static int adjoint_gradient_impl(tb_handle* h, int nt, const float* residual, float* grad_vp, float* grad_src,
+                                 int n_snapshots, int ckpt, cudaStream_t st) {
   if (!h) return TB_EINVAL;
   if (h->physics != TB_ACOUSTIC || h->storage != TB_F32)
     return fail(h, TB_EINVAL, "the adjoint is implemented for the FP32 acoustic equation");
   if (!h->have_model || !h->have_src || !h->have_rec)
     return fail(h, TB_ESTATE, "tb_set_model, tb_set_sources and tb_set_receivers must come first");
   if (nt <= 0 || !residual || n_snapshots < 1 || (!grad_vp && !grad_src)) return fail(h, TB_EINVAL, "bad arguments");
+  if (ckpt != TB_CKPT_SEGMENTS && ckpt != TB_CKPT_BINOMIAL) return fail(h, TB_EINVAL, "bad checkpointing");
+  if (ckpt == TB_CKPT_BINOMIAL && n_snapshots > 4096) return fail(h, TB_EINVAL, "n_snapshots > 4096");
   if (h->src.npts > 0 && nt > h->src_nt)
     return fail(h, TB_EINVAL, "nt = %d exceeds the wavelet length %d", nt, h->src_nt);
-  cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
   const int nrec = h->rec.npt, nsrc = h->src.npt;
   const int64_t nrp = h->rec.npts, nsp = h->src.npts;
   const size_t Np = (size_t)h->n[0] * h->n[1] * h->n2p, fbytes = sizeof(float) * Np;
-  const int K = (nt + n_snapshots - 1) / n_snapshots;  // steps per segment
+  const int K = (nt + n_snapshots - 1) / n_snapshots;  // segments: steps per segment
   const int nseg = (nt + K - 1) / K;
+  std::vector<CkptAction> plan;
+  int64_t fsteps = 0;
+  if (ckpt == TB_CKPT_BINOMIAL && plan_binomial(nt, n_snapshots, &plan, &fsteps) != TB_OK)
+    return fail(h, TB_EINVAL, "checkpoint schedule");
   StepRunner run;
   int s = runner_init(h, &run, st);
   if (s != TB_OK) return s;
-  // scratch: checkpoints (u^{jK}, u^{jK-1}) of segments j >= 1, a segment of
-  // K+2 states (u^{k0-1} .. u^{k1}: the imaging term of step k reads u^k,
-  // u^{k-1}, u^{k-2}), the two adjoint fields mu = D lam, the FP64 gradient,
-  // the decomposed residual and the source-gradient rows
   std::vector<void*> bufs;
+  size_t scratch = 0;
   auto alloc = [&](size_t bytes) -> void* {
     void* p = nullptr;
     if (dmalloc(&p, bytes ? bytes : 1, st) != cudaSuccess) return nullptr;
     bufs.push_back(p);
+    scratch += bytes ? bytes : 1;
     return p;
   };
   auto cleanup = [&]() {
     for (void* p : bufs) dfree(p, st);
     bufs.clear();
   };
-  float* snap = (float*)alloc(fbytes * 2 * std::max(nseg - 1, 1));
-  float* seg = (float*)alloc(fbytes * (K + 2));
+  // state storage.  Segments: checkpoints (u^{jK}, u^{jK-1}) of segments
+  // j >= 1 and a segment of K + 2 states (u^{k0-1} .. u^{k1}).  Binomial: S
+  // slots of two fields, a work pair, a zero field (X_0) and the handle's
+  // four wavefields as scratch of the advances and the reverse steps.
+  float* snap = nullptr;
+  float* seg = nullptr;
+  float* slots = nullptr;
+  float* work = nullptr;
+  float* zero = nullptr;
+  if (ckpt == TB_CKPT_SEGMENTS) {
+    snap = (float*)alloc(fbytes * 2 * std::max(nseg - 1, 1));
+    seg = (float*)alloc(fbytes * (K + 2));
+  } else {
+    slots = (float*)alloc(fbytes * 2 * n_snapshots);
+    work = (float*)alloc(fbytes * 2);
+    zero = (float*)alloc(fbytes);
+  }
   float* lam = (float*)alloc(fbytes * 2);
   double* gm = (double*)alloc(sizeof(double) * Np);
   float* resT = (float*)alloc(sizeof(float) * (size_t)nt * std::max(nrec, 1));
@@ -1726,7 +1754,8 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
   float* gvp_dev = nullptr;
   const bool gvp_host = grad_vp && !is_device_ptr(grad_vp);
   if (gvp_host) gvp_dev = (float*)alloc(sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n[2]);
-  if (!snap || !seg || !lam || !gm || !resT || !rdcmp || !srow || !gsrc || (gvp_host && !gvp_dev)) {
+  const bool have_states = ckpt == TB_CKPT_SEGMENTS ? (snap && seg) : (slots && work && zero);
+  if (!have_states || !lam || !gm || !resT || !rdcmp || !srow || !gsrc || (gvp_host && !gvp_dev)) {
     cleanup();
     cudaGetLastError();
     return fail(h, TB_ENOMEM, "adjoint scratch");
@@ -1742,89 +1771,136 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
     void* tmp = nullptr;
     const void* dres = nullptr;
     ok(to_device(residual, sizeof(float) * (size_t)nt * nrec, &tmp, &dres, st));
-    if (tmp) bufs.push_back(tmp);
+    if (tmp) {
+      bufs.push_back(tmp);
+      scratch += sizeof(float) * (size_t)nt * nrec;
+    }
     ok(transpose_f32(nt, nrec, (const float*)dres, resT, st));
     if (nrp > 0) ok(decompose(&h->rec, nt, resT, nullptr, 1.0, (int)h->n[1], (int)h->n[2], h->n2p, rdcmp, st));
     // injected into mu = D lam: scaled by D at each receiver point
     if (nrp > 0) ok(adjoint_scale_rows(g, nt, nrp, h->rec.lin, h->c2, h->damp_b, rdcmp, st));
   }
+  // TMA descriptors of every buffer a forward or adjoint step reads
+  SweepShape sh;
+  if (!sweep_shape(h->R, 1, &sh, 0)) ok(cudaErrorInvalidValue);
+  struct Buf {
+    float* p;
+    CUtensorMap box, tile;
+  };
+  auto mkbuf = [&](float* p) {
+    Buf b{p, {}, {}};
+    ok(make_tmap(&b.box, p, h->n, h->n2p, sh.box_w, sh.box_h));
+    ok(make_tmap(&b.tile, p, h->n, h->n2p, 64, sh.TY));
+    return b;
+  };
   // the adjoint sweeps: the forward sweep kernel on the mu fields, without
-  // the sources (the residual is injected after each step); the
-  // recomputation writes each state straight into its segment slot
+  // the sources (the residual is injected after each step)
   StepRunner arun = run;
   arun.P.ev_pair = nullptr;
-  float* mu[2] = {lam, lam + Np};
-  CUtensorMap mbox[2], mtile[2];
-  std::vector<CUtensorMap> sbox(K + 2), stile(K + 2);
-  {
-    SweepShape sh;
-    if (!sweep_shape(h->R, 1, &sh, 0)) ok(cudaErrorInvalidValue);
-    for (int i = 0; i < 2; ++i) {
-      ok(make_tmap(&mbox[i], mu[i], h->n, h->n2p, sh.box_w, sh.box_h));
-      ok(make_tmap(&mtile[i], mu[i], h->n, h->n2p, 64, sh.TY));
-    }
-    for (int i = 0; i < K + 2; ++i) {
-      ok(make_tmap(&sbox[i], seg + (size_t)i * Np, h->n, h->n2p, sh.box_w, sh.box_h));
-      ok(make_tmap(&stile[i], seg + (size_t)i * Np, h->n, h->n2p, 64, sh.TY));
-    }
-  }
-  // forward pass, keeping the checkpoints
-  int cur = 0, prev = 1;
-  ok(cudaMemsetAsync(h->field[0], 0, fbytes, st));
-  ok(cudaMemsetAsync(h->field[1], 0, fbytes, st));
-  ok(cudaMemsetAsync(h->err, 0, sizeof(int), st));
-  for (int n = 0; n < nt && e == cudaSuccess; ++n) {
-    if (n > 0 && n % K == 0) {
-      const int j = n / K;
-      ok(cudaMemcpyAsync(snap + (size_t)(2 * (j - 1)) * Np, h->field[cur], fbytes, cudaMemcpyDeviceToDevice, st));
-      ok(cudaMemcpyAsync(snap + (size_t)(2 * (j - 1) + 1) * Np, h->field[prev], fbytes, cudaMemcpyDeviceToDevice, st));
-    }
-    if ((s = runner_step(h, &run, cur, prev, n, st)) != TB_OK) {
-      cleanup();
-      return s;
-    }
-    std::swap(cur, prev);
-  }
-  // backward over the segments, each recomputed once from its checkpoint
+  Buf mub[2] = {mkbuf(lam), mkbuf(lam + Np)};
+  int mc = 0, mp = 1;  // mu^{k+1} in mub[mc], mu^{k+2} in mub[mp]
   ok(cudaMemsetAsync(lam, 0, fbytes * 2, st));
   ok(cudaMemsetAsync(gm, 0, sizeof(double) * Np, st));
-  int mc = 0, mp = 1;  // mu^{k+1} in mu[mc], mu^{k+2} in mu[mp]
-  for (int j = nseg - 1; j >= 0 && e == cudaSuccess; --j) {
-    const int k0 = j * K, k1 = std::min((j + 1) * K, nt);
-    // seg[s] = u^{k0 - 1 + s}, s = 0 .. k1 - k0 + 1
-    if (j == 0) {
-      ok(cudaMemsetAsync(seg, 0, fbytes * 2, st));
-    } else {
-      ok(cudaMemcpyAsync(seg + Np, snap + (size_t)(2 * (j - 1)) * Np, fbytes, cudaMemcpyDeviceToDevice, st));
-      ok(cudaMemcpyAsync(seg, snap + (size_t)(2 * (j - 1) + 1) * Np, fbytes, cudaMemcpyDeviceToDevice, st));
+  ok(cudaMemsetAsync(h->err, 0, sizeof(int), st));
+  // adjoint step k (k = nt .. 1, in that order) with the forward states
+  // u^k, u^{k-1}, u^{k-2}
+  auto adjoint_step = [&](int k, const float* uk, const float* uk1, const float* uk2) -> int {
+    // mu^k over mu^{k+2}, then + D P^T r[k-1]
+    int r = runner_step_on(h, &arun, mub[mc].p, mub[mp].p, mub[mc].box, mub[mp].tile, nt - k, st);
+    if (r != TB_OK) return r;
+    std::swap(mc, mp);
+    float* m0 = mub[mc].p;
+    if (nrp > 0) ok(inject_points(g, nrp, h->rec.lin, rdcmp + (size_t)(k - 1) * nrp, m0, nullptr, nullptr, st));
+    if (grad_vp) {
+      ok(adjoint_grad(g, h->dt, m0, uk, uk1, uk2, gm, st));
+      if (nsp > 0)
+        ok(adjoint_grad_src(g, nsp, h->src.lin, h->src_dcmp + (size_t)(k - 1) * nsp, h->dt, m0, h->c2, h->damp_b,
+                            gm, st));
     }
-    for (int n = k0; n <= k1 - 1 && e == cudaSuccess; ++n) {
-      const int sc = n - k0 + 1;  // slot of u^n
-      if ((s = runner_step_on(h, &run, seg + (size_t)sc * Np, seg + (size_t)(sc - 1) * Np, sbox[sc],
-                              stile[sc - 1], n, st, seg + (size_t)(sc + 1) * Np)) != TB_OK) {
-        cleanup();
-        return s;
+    if (grad_src && nsp > 0)
+      ok(adjoint_sample_src(g, nsp, h->src.ent, h->src.lin, m0, h->c2, h->damp_b, srow + (size_t)(k - 1) * nsp, st));
+    return TB_OK;
+  };
+  if (ckpt == TB_CKPT_SEGMENTS) {
+    // seg[s] = u^{k0 - 1 + s}; the recomputation writes each state straight
+    // into its segment slot
+    std::vector<Buf> sb;
+    for (int i = 0; i < K + 2; ++i) sb.push_back(mkbuf(seg + (size_t)i * Np));
+    // forward pass, keeping the checkpoints
+    int cur = 0, prev = 1;
+    ok(cudaMemsetAsync(h->field[0], 0, fbytes, st));
+    ok(cudaMemsetAsync(h->field[1], 0, fbytes, st));
+    for (int n = 0; n < nt && e == cudaSuccess; ++n) {
+      if (n > 0 && n % K == 0) {
+        const int j = n / K;
+        ok(cudaMemcpyAsync(snap + (size_t)(2 * (j - 1)) * Np, h->field[cur], fbytes, cudaMemcpyDeviceToDevice, st));
+        ok(cudaMemcpyAsync(snap + (size_t)(2 * (j - 1) + 1) * Np, h->field[prev], fbytes, cudaMemcpyDeviceToDevice,
+                           st));
+      }
+      if ((s = runner_step(h, &run, cur, prev, n, st)) != TB_OK) break;
+      std::swap(cur, prev);
+    }
+    // backward over the segments, each recomputed once from its checkpoint
+    for (int j = nseg - 1; j >= 0 && e == cudaSuccess && s == TB_OK; --j) {
+      const int k0 = j * K, k1 = std::min((j + 1) * K, nt);
+      if (j == 0) {
+        ok(cudaMemsetAsync(seg, 0, fbytes * 2, st));
+      } else {
+        ok(cudaMemcpyAsync(seg + Np, snap + (size_t)(2 * (j - 1)) * Np, fbytes, cudaMemcpyDeviceToDevice, st));
+        ok(cudaMemcpyAsync(seg, snap + (size_t)(2 * (j - 1) + 1) * Np, fbytes, cudaMemcpyDeviceToDevice, st));
+      }
+      for (int n = k0; n <= k1 - 1 && e == cudaSuccess && s == TB_OK; ++n) {
+        const int sc = n - k0 + 1;  // slot of u^n
+        s = runner_step_on(h, &run, sb[sc].p, sb[sc - 1].p, sb[sc].box, sb[sc - 1].tile, n, st, sb[sc + 1].p);
+      }
+      for (int k = k1; k >= k0 + 1 && e == cudaSuccess && s == TB_OK; --k)
+        s = adjoint_step(k, sb[k - k0 + 1].p, sb[k - k0].p, sb[k - k0 - 1].p);
+    }
+  } else {
+    // slot i holds a state X_n = (u^n, u^{n-1}) in fields 2i, 2i + 1
+    std::vector<Buf> sl;
+    for (int i = 0; i < 2 * n_snapshots; ++i) sl.push_back(mkbuf(slots + (size_t)i * Np));
+    Buf wk[2] = {mkbuf(work), mkbuf(work + Np)};
+    Buf zb = mkbuf(zero);
+    Buf hf[4];
+    for (int i = 0; i < 4; ++i) hf[i] = Buf{h->field[i], h->tm_box[i], h->tm_tile[i]};
+    ok(cudaMemsetAsync(zero, 0, fbytes, st));
+    auto loc = [&](int L, int which) -> Buf* {
+      if (L >= 0) return &sl[2 * L + which];
+      return L == kCkptWork ? &wk[which] : &zb;
+    };
+    for (size_t ai = 0; ai < plan.size() && e == cudaSuccess && s == TB_OK; ++ai) {
+      const CkptAction& a = plan[ai];
+      Buf* c = loc(a.src, 0);  // u^from
+      Buf* p = loc(a.src, 1);  // u^{from-1}
+      if (a.kind == kCkptAdvance) {
+        // X_to into dst: the last two states go to the destination's fields,
+        // the ones before them to a scratch wavefield that is neither input
+        Buf* d0 = loc(a.dst, 0);
+        Buf* d1 = loc(a.dst, 1);
+        if (a.to - a.from == 1) {
+          if (a.src == kCkptZero) ok(cudaMemsetAsync(d1->p, 0, fbytes, st));
+          else ok(cudaMemcpyAsync(d1->p, c->p, fbytes, cudaMemcpyDeviceToDevice, st));
+        }
+        for (int n = a.from; n < a.to && e == cudaSuccess && s == TB_OK; ++n) {
+          Buf* out = n + 1 == a.to ? d0 : (n + 1 == a.to - 1 ? d1 : nullptr);
+          for (int i = 0; i < 3 && !out; ++i)
+            if (hf[i].p != c->p && hf[i].p != p->p) out = &hf[i];
+          s = runner_step_on(h, &run, c->p, p->p, c->box, p->tile, n, st, out->p);
+          p = c;
+          c = out;
+        }
+      } else {
+        // reverse step `from`: u^{from+1} by one forward step, then the adjoint
+        // step k = from + 1 with u^k, u^{k-1}, u^{k-2}
+        s = runner_step_on(h, &run, c->p, p->p, c->box, p->tile, a.from, st, hf[3].p);
+        if (s == TB_OK) s = adjoint_step(a.from + 1, hf[3].p, c->p, p->p);
       }
     }
-    for (int k = k1; k >= k0 + 1 && e == cudaSuccess; --k) {
-      // mu^k over mu^{k+2}, then + D P^T r[k-1]
-      if (e == cudaSuccess && (s = runner_step_on(h, &arun, mu[mc], mu[mp], mbox[mc], mtile[mp], nt - k, st)) != TB_OK) {
-        cleanup();
-        return s;
-      }
-      std::swap(mc, mp);
-      float* m0 = mu[mc];
-      if (nrp > 0) ok(inject_points(g, nrp, h->rec.lin, rdcmp + (size_t)(k - 1) * nrp, m0, nullptr, nullptr, st));
-      if (grad_vp) {
-        ok(adjoint_grad(g, h->dt, m0, seg + (size_t)(k - k0 + 1) * Np, seg + (size_t)(k - k0) * Np,
-                        seg + (size_t)(k - k0 - 1) * Np, gm, st));
-        if (nsp > 0)
-          ok(adjoint_grad_src(g, nsp, h->src.lin, h->src_dcmp + (size_t)(k - 1) * nsp, h->dt, m0, h->c2, h->damp_b,
-                              gm, st));
-      }
-      if (grad_src && nsp > 0)
-        ok(adjoint_sample_src(g, nsp, h->src.ent, h->src.lin, m0, h->c2, h->damp_b, srow + (size_t)(k - 1) * nsp, st));
-    }
+  }
+  if (s != TB_OK) {
+    cleanup();
+    return s;
   }
   if (grad_vp && e == cudaSuccess) {
     ok(adjoint_finish(g, h->dt, gm, h->c2, gvp_host ? gvp_dev : grad_vp, st));
@@ -1848,7 +1924,28 @@ extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, 
   if (e != cudaSuccess) return cuda_fail(h, e, "tb_adjoint_gradient");
   if (err) return fail(h, TB_ETIMEOUT, "a sweep CTA timed out");
   h->last_nt = -1;  // the fields hold recomputation scratch now
+  h->last_fwd_steps = ckpt == TB_CKPT_BINOMIAL ? fsteps : 2 * (int64_t)nt;
+  h->last_scratch = scratch;
   h->msg[0] = 0;
+  return TB_OK;
+}
+
+extern "C" int tb_adjoint_gradient(tb_handle* h, int nt, const float* residual, float* grad_vp, float* grad_src,
+                                   int n_snapshots, void* stream) {
+  return adjoint_gradient_impl(h, nt, residual, grad_vp, grad_src, n_snapshots, TB_CKPT_SEGMENTS,
+                               (cudaStream_t)stream);
+}
+
+extern "C" int tb_adjoint_gradient_ckpt(tb_handle* h, int nt, const float* residual, float* grad_vp,
+                                        float* grad_src, int n_snapshots, int checkpointing, void* stream) {
+  return adjoint_gradient_impl(h, nt, residual, grad_vp, grad_src, n_snapshots, checkpointing,
+                               (cudaStream_t)stream);
+}
+
+extern "C" int tb_adjoint_stats(const tb_handle* h, int64_t* forward_steps, size_t* scratch_bytes) {
+  if (!h || !forward_steps || !scratch_bytes) return TB_EINVAL;
+  *forward_steps = h->last_fwd_steps;
+  *scratch_bytes = h->last_fwd_steps < 0 ? 0 : h->last_scratch;
   return TB_OK;
 }
 

@@ -225,4 +225,16 @@ cudaError_t unpad_copy(const float* src, float* dst, int n0, int n1, int n2, int
                        cudaStream_t st);
 cudaError_t count_nonfinite(const float* a, int64_t n, int* d_count, cudaStream_t st);
 
+// binomial checkpoint schedule of the adjoint gradient (tb_checkpoint.cu):
+// ADVANCE computes X_to from X_from held at src into dst; REVERSE runs the
+// adjoint step of forward step `from` with X_from held at src.  Locations:
+// a slot 0 .. S-1, kCkptZero (the zero state X_0) or kCkptWork (the work
+// pair).
+enum { kCkptAdvance = 0, kCkptReverse = 1 };
+enum { kCkptZero = -1, kCkptWork = -2 };
+struct CkptAction {
+  int kind, from, to, src, dst;
+};
+int plan_binomial(int nt, int S, std::vector<CkptAction>* out, int64_t* forward_steps);
+
 }  // namespace tbi

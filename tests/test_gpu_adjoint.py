@@ -118,3 +118,35 @@ def test_autograd_function(tb):
     p.adjoint_gradient(nt, (tr - d_obs).detach(), grad_vp=gvp, n_snapshots=8)
     np.testing.assert_array_equal(v.grad.cpu().numpy(), gvp.cpu().numpy())
     assert float(v.grad.abs().max()) > 0
+
+
+@pytest.mark.parametrize("S", [1, 3, 12])
+def test_binomial_schedule_equals_segments(tb, S):
+    """The binomial schedule (exactly S stored states) recomputes the same
+    forward states by the same one-step sweeps as the segment scheme: the
+    gradients in vp and in the wavelets are bit-identical; the forward-step
+    count is the planner's, and the scratch holds 2 S + 3 wavefields beside
+    the adjoint's own buffers, whatever nt is."""
+    import torch
+    h, so, nt, vp, damp, eta, src, rec, dt, g = case(nt=61)
+    wav = np.repeat(wl.ricker(35.0, dt, nt, t0=6 * dt)[None, :], 2, axis=0).astype(np.float32)
+    r = torch.from_numpy(g.standard_normal((nt, len(rec))).astype(np.float32)).cuda()
+    p = make_prop(tb, vp.shape, h, so, vp, damp, dt, src, wav, rec)
+    res = {}
+    for mode in ("segments", "binomial"):
+        gvp = torch.empty(vp.shape, device="cuda")
+        gsrc = torch.empty((2, nt), device="cuda")
+        p.adjoint_gradient(nt, r, grad_vp=gvp, grad_src=gsrc, n_snapshots=S, checkpointing=mode)
+        res[mode] = (gvp.cpu().numpy(), gsrc.cpu().numpy(), p.adjoint_stats())
+    np.testing.assert_array_equal(res["binomial"][0], res["segments"][0])
+    np.testing.assert_array_equal(res["binomial"][1], res["segments"][1])
+    assert float(np.abs(res["binomial"][0]).max()) > 0
+    _, fsteps = tb.tb_plan_checkpoints(nt, S)
+    assert res["binomial"][2][0] == fsteps
+    assert res["segments"][2][0] == 2 * nt
+    n2p = (vp.shape[2] + 3) // 4 * 4
+    field = 4 * vp.shape[0] * vp.shape[1] * n2p
+    states = (2 * S + 3) * field
+    own = 2 * field + 8 * vp.shape[0] * vp.shape[1] * n2p        # mu pair, FP64 sum
+    tables = res["binomial"][2][1] - states - own
+    assert 0 <= tables < field, (res["binomial"][2][1], states, own)

@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--serving", action="store_true",
                     help="Poisson stream of acoustic so8 shots of mixed sizes through the continuous-"
                          "batching server: p50/p99 shot latency and aggregate GPts/s")
-    ap.add_argument("--shots", type=int, default=48)
+    ap.add_argument("--shots", type=int, default=500)
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "plain"],
                     help="f16 / bf16 / plain: the 512^3 acoustic shot with 16-bit (or plain FP32) wavefield "
                          "storage in the streaming one-step kernel")
@@ -605,7 +605,8 @@ def serving_shots(n, seed):
         h = (10.0, 10.0, 10.0)
         ext = np.array([(shape[d] - 1) * h[d] for d in range(3)])
         nbl = 20
-        vp = wl.layered_vp(shape, seed + 1000 + i, nblobs=0)
+        # the layered model, built on the device when the shot is admitted
+        vp = _DeviceLayers(shape, wl.layered_profile(shape[2], seed + 1000 + i))
         nsrc = int(g.integers(1, 5))
         src = np.stack([g.uniform(0.3, 0.7, nsrc) * ext[0], g.uniform(0.3, 0.7, nsrc) * ext[1],
                         np.full(nsrc, (nbl + 5 + g.uniform(0.1, 0.9)) * h[2])], axis=1)
@@ -614,8 +615,21 @@ def serving_shots(n, seed):
                         np.full(nrec, (nbl + 8 + g.uniform(0.1, 0.9)) * h[2])], axis=1)
         storage = int(g.integers(0, 2))  # FP32 or FP16 wavefield storage, 50/50
         out.append(serving.ShotRequest(shape, h, 8, vp, src, 15.0, rec, nt=int(g.integers(300, 1501)), nbl=nbl,
-                                       time_tile=1, tag=i, storage=storage))
+                                       time_tile=0, tag=i, storage=storage))
     return out
+
+
+class _DeviceLayers:
+    """A layered velocity model (a depth profile repeated over x, y) made on
+    the device when called: 500 shots of up to 512^3 would not fit in host
+    memory made up front."""
+
+    def __init__(self, shape, profile):
+        self.shape, self.profile = tuple(shape), profile
+
+    def __call__(self):
+        import torch
+        return torch.from_numpy(self.profile).cuda()[None, None, :].expand(self.shape).contiguous()
 
 
 def run_serving(args):
@@ -628,20 +642,21 @@ def run_serving(args):
     tb.load()
     reqs = serving_shots(args.shots, 2010_10248 + 4)
     work = np.array([np.prod(r.shape) * r.nt for r in reqs], dtype=np.float64)
-    # capacity from two calibration shots run alone (after one untimed shot
-    # that takes the first-use costs: module loading, memory pool growth)
+    # capacity: the first ncal shots run one at a time, each alone on the GPU
+    # (blocked sweep for FP32 storage, one-step for FP16), after one untimed
+    # shot that takes the first-use costs (module loading, memory pool growth)
+    ncal = min(20, len(reqs))
     cal = serving.ShotServer(slots=1)
     cal.run([serving.ShotRequest(**{**reqs[2].__dict__, "tag": "warm"})])
     t0 = time.perf_counter()
-    cal.run([serving.ShotRequest(**{**reqs[0].__dict__, "tag": "cal0"}),
-             serving.ShotRequest(**{**reqs[1].__dict__, "tag": "cal1"})])
-    cap = (work[0] + work[1]) / (time.perf_counter() - t0)  # point updates / s, one at a time
-    rate = 0.8 * cap / work.mean()                           # shots / s at 80 % of that capacity
+    cal.run([serving.ShotRequest(**{**reqs[i].__dict__, "tag": f"cal{i}", "arrival": 0.0}) for i in range(ncal)])
+    cap = work[:ncal].sum() / (time.perf_counter() - t0)  # point updates / s, one at a time
+    rate = 0.8 * cap / work.mean()                         # shots / s at 80 % of that capacity
     g = np.random.Generator(np.random.PCG64(2010_10248 + 5))
     arr = np.cumsum(g.exponential(1.0 / rate, size=len(reqs)))
     for r, a in zip(reqs, arr):
         r.arrival = float(a - arr[0])
-    srv = serving.ShotServer(slots=args.slots)
+    srv = serving.ShotServer(slots=args.slots, batch_points=256 ** 3, batch_max=16, batch_chunk=32)
     clocks = ClockSampler(0)
     clocks.start()
     t0 = time.perf_counter()
@@ -655,12 +670,18 @@ def run_serving(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"serving: Poisson stream of {len(reqs)} acoustic so8 shots, grids 128^3-512^3 "
                                    "(multiples of 32), 300-1500 steps, 1-4 sources, 1k-64k receivers",
-                       "arrival_rate_per_s": rate, "slots": args.slots, "schedule": "onestep",
+                       "arrival_rate_per_s": rate, "slots": args.slots,
+                       "schedule": ("FP32 shots of at most 256^3 points: batch lane (one launch per step for "
+                                    "all shots in it, chunks of 32 steps); larger FP32 shots: blocked sweep "
+                                    "alone on a slot; FP16 shots: one-step sweep on a slot"),
                        "precision": "FP32 arithmetic; FP32 or FP16 wavefield storage per shot (50/50)",
-                       "fp16_shots": int(sum(1 for r in reqs if r.storage == 1))},
+                       "fp16_shots": int(sum(1 for r in reqs if r.storage == 1)),
+                       "batched_shots": int(sum(1 for r in reqs if r.storage == 0 and np.prod(r.shape) <= 256 ** 3)),
+                       "calibration_shots": ncal},
             "latency_s": {"p50": serving.percentile(lat, 50), "p99": serving.percentile(lat, 99),
                           "mean": float(np.mean(lat)), "max": float(np.max(lat))},
-            "capacity_alone_gpts": cap / 1e9, "max_in_flight": srv.stats["max_in_flight"],
+            "capacity_alone_gpts": cap / 1e9, "value_over_capacity": value / (cap / 1e9),
+            "lanes": srv.stats.get("lanes"), "max_in_flight": srv.stats["max_in_flight"],
             "max_bytes_in_flight": srv.stats["max_bytes"], "clocks": clk}
     print(json.dumps(line), flush=True)
 
@@ -874,41 +895,57 @@ def run_adjoint(args):
     d_obs = p.forward(nt, schedule="onestep").clone()
     geometry(vp)
     resid = (p.forward(nt, schedule="onestep") - d_obs).contiguous()
-    gvp = torch.empty_like(vp)
     st = torch.cuda.current_stream()
-
-    def step():
-        p.adjoint_gradient(nt, resid, grad_vp=gvp, n_snapshots=nsnap)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
     # the forward alone, for the cost of a gradient in forward runs
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(st)
-    p.forward(nt, schedule="onestep")
-    f1.record(st)
-    torch.cuda.synchronize()
+    for _ in range(2):
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(st)
+        p.forward(nt, schedule="onestep")
+        f1.record(st)
+        torch.cuda.synchronize()
     fwd_ms = f0.elapsed_time(f1)
+    peak, peak_kind = measured_peaks()
+    sched = {}
+    grads = {}
     clocks = ClockSampler(0)
     clocks.start()
     l0 = tb.tb_launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(args.steps):
-        step()
-    e1.record(st)
-    torch.cuda.synchronize()
+    for mode in ("segments", "binomial"):
+        gvp = torch.empty_like(vp)
+
+        def step():
+            p.adjoint_gradient(nt, resid, grad_vp=gvp, n_snapshots=nsnap, checkpointing=mode)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_m = e0.elapsed_time(e1) / args.steps
+        fsteps, scratch = p.adjoint_stats()
+        # algorithmic bytes per point and step of the gradient: the forward
+        # one-step sweeps (16 B each, fsteps of them for nt steps), the adjoint
+        # sweep on mu = D lam (16) and the imaging condition (mu, u^k, u^{k-1},
+        # u^{k-2}: 16, + FP64 sum 16)
+        bpp_m = 16.0 * fsteps / nt + 16.0 + 32.0
+        sched[mode] = {"value": N * nt / (ms_m * 1e-3) / 1e9, "ms_per_gradient": ms_m,
+                       "gradient_in_forward_runs": ms_m / fwd_ms, "forward_steps": fsteps,
+                       "forward_steps_per_nt": fsteps / nt, "scratch_bytes": scratch,
+                       "scratch_fields": scratch / (4.0 * N), "bytes_per_point_step": bpp_m,
+                       "hbm_frac": bpp_m * N * nt / (ms_m * 1e-3) / 1e9 / peak}
+        grads[mode] = gvp
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    value = N * nt / (ms * 1e-3) / 1e9
-    # algorithmic bytes per point and step of the gradient: forward one-step
-    # (16) with checkpoints, recomputation into the segment buffer (16), the
-    # adjoint one-step sweep on mu = D lam (16), imaging condition (mu, u^k,
-    # u^{k-1}, u^{k-2}: 16, + FP64 sum 16)
-    bpp = 16.0 + 16.0 + 16.0 + 32.0
-    peak, peak_kind = measured_peaks()
+    launches = tb.tb_launch_count() - l0
+    gvp = grads["binomial"]
+    ms = sched["binomial"]["ms_per_gradient"]
+    value = sched["binomial"]["value"]
+    bpp = sched["binomial"]["bytes_per_point_step"]
     achieved = bpp * N * nt / (ms * 1e-3) / 1e9
+    same = bool(torch.equal(grads["binomial"], grads["segments"]))
     finite = bool(torch.isfinite(gvp).all().item()) and float(gvp.abs().max()) > 0
     cpu = None
     if not args.no_cpu:
@@ -937,13 +974,14 @@ def run_adjoint(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"vp gradient, acoustic {size}^3 so8 {nt} steps", "grid": list(w.shape),
                        "space_order": w.so, "nt": nt, "snapshots": nsnap, "receivers": len(w.rec_xyz),
-                       "step": "tb_adjoint_gradient (forward with checkpoints + recomputation + adjoint)"},
-            "gpu_launches": int(tb.tb_launch_count() - l0), "clocks": clk,
+                       "checkpointing": "binomial (value); segments beside it",
+                       "step": "tb_adjoint_gradient_ckpt (forward states from the checkpoints + adjoint)"},
+            "gpu_launches": int(launches), "clocks": clk,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                          "kernel": "gradient step (all kernels of one time step)", "bytes_per_point_step": bpp},
-            "forward_ms": fwd_ms, "gradient_in_forward_runs": ms / fwd_ms,
-            "cpu_baseline": cpu, "gradient_finite": finite}
+            "forward_ms": fwd_ms, "gradient_in_forward_runs": ms / fwd_ms, "schedules": sched,
+            "binomial_equals_segments": same, "cpu_baseline": cpu, "gradient_finite": finite}
     print(json.dumps(line), flush=True)
     p.close()
 

@@ -413,6 +413,56 @@ int tb_plan_checkpoints(int nt, int n_snapshots, int* actions, int max_actions, 
 double tb_tti_dt_max(int space_order, const double h[3], double vmax, double eps_max);
 double tb_elastic_dt_max(int space_order, const double h[3], double vpmax);
 
+/* --- Batched small shots (continuous batching) ------------------------ */
+
+/* A batch advances several acoustic shots (FP32 storage, one space order)
+ * together: every time step of every shot in the batch is one launch of the
+ * one-step sweep (Sec. IV-C's spatially blocked kernel) whose CTAs take the
+ * (shot, tile) entries of a concatenated pass table and read each shot's
+ * fields, tensor maps and tables from device memory.  Shots join and leave
+ * between steps, so a serving loop admits new shots while others run
+ * (continuous batching); each shot gives the same traces and wavefields,
+ * bit for bit, as tb_forward(TB_ONESTEP) alone.  Large shots are better
+ * served alone with TB_BLOCKED.  A batch lives on the device that is current
+ * at tb_batch_create; use one stream for all calls on a batch and its
+ * shots, and keep a shot's handle alive and untouched (no other call on it)
+ * from tb_batch_add until tb_batch_finished returns it.  The paper has no
+ * counterpart; this is the serving path of the library. */
+typedef struct tb_batch tb_batch;
+
+/* Create a batch for at most max_shots (1..4096) shots at a time; allocates
+ * about 2.3 KB of device memory per shot.  Errors: TB_EINVAL, TB_ENOMEM. */
+int tb_batch_create(int max_shots, tb_batch** out);
+
+/* Release the batch (stream-ordered frees on its last stream); its shots'
+ * handles stay the caller's.  NULL is accepted.  Returns TB_OK. */
+int tb_batch_destroy(tb_batch* b);
+
+/* Admit a shot: handle h with tb_set_model done (sources and receivers
+ * optional, as for tb_forward), nt steps from zero initial conditions,
+ * traces: device [nt][nrec] float (caller-owned, may be NULL).  The shot's
+ * wavefields are zeroed on `stream`; its first step is the batch's next
+ * launch.  nt = 0 finishes at once.  Errors: TB_EINVAL (not acoustic FP32,
+ * a space order other than the batch's, host traces, nt beyond the wavelet
+ * length, the batch full, h already in it), TB_ESTATE (no model), TB_ECUDA. */
+int tb_batch_add(tb_batch* b, tb_handle* h, int nt, float* traces, void* stream);
+
+/* Advance every shot in the batch by up to nsteps steps (one launch per
+ * step; fewer when the batch empties), asynchronously on `stream`; a shot's
+ * receiver traces are finalised every 16 steps and at its last step, and a
+ * shot that reaches its nt leaves the batch (tb_batch_finished).  Errors:
+ * TB_EINVAL, TB_ENOMEM, TB_ECUDA. */
+int tb_batch_step(tb_batch* b, int nsteps, void* stream);
+
+/* Shots in the batch that have not finished. */
+int tb_batch_active(const tb_batch* b);
+
+/* Pop up to max_out finished shots' handles into out (caller-owned array),
+ * *n = how many.  Their traces and final wavefields (tb_get_field) are ready
+ * once the work enqueued so far on the batch's stream completes.  Errors:
+ * TB_EINVAL. */
+int tb_batch_finished(tb_batch* b, tb_handle** out, int max_out, int* n);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * handles, all devices), for accounting in benchmarks. */
 uint64_t tb_launch_count(void);

@@ -63,6 +63,12 @@ _SIGS = {
     "tb_adjoint_gradient": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int, _vp]),
     "tb_adjoint_gradient_ckpt": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int, C.c_int, _vp]),
     "tb_adjoint_stats": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_size_t)]),
+    "tb_batch_create": (C.c_int, [C.c_int, C.POINTER(_vp)]),
+    "tb_batch_destroy": (C.c_int, [_vp]),
+    "tb_batch_add": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp]),
+    "tb_batch_step": (C.c_int, [_vp, C.c_int, _vp]),
+    "tb_batch_active": (C.c_int, [_vp]),
+    "tb_batch_finished": (C.c_int, [_vp, C.POINTER(_vp), C.c_int, C.POINTER(C.c_int)]),
     "tb_plan_checkpoints": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int,
                                       C.POINTER(C.c_int64)]),
     "tb_elastic_dt_max": (C.c_double, [C.c_int, C.POINTER(C.c_double), C.c_double]),
@@ -285,6 +291,49 @@ def tb_plan_checkpoints(nt, n_snapshots):
     out = np.zeros((max(n, 1), 5), dtype=np.int32)
     lib.tb_plan_checkpoints(int(nt), int(n_snapshots), out.ctypes.data_as(C.POINTER(C.c_int)), n, C.byref(fs))
     return out[:n], int(fs.value)
+
+
+class Batch:
+    """Several small acoustic shots advanced together, one launch per time
+    step (tb_batch_*).  Shots are Propagator handles; traces device tensors."""
+
+    def __init__(self, max_shots=16):
+        lib = load()
+        b = _vp()
+        st = lib.tb_batch_create(int(max_shots), C.byref(b))
+        if st != TB_OK:
+            raise TBError(st, "tb_batch_create")
+        self.b = b
+
+    def add(self, h, nt, traces=None, stream=None):
+        _check(h, load().tb_batch_add(self.b, h, int(nt), _ptr(traces), _stream(stream)), "tb_batch_add")
+
+    def step(self, nsteps, stream=None):
+        st = load().tb_batch_step(self.b, int(nsteps), _stream(stream))
+        if st != TB_OK:
+            raise TBError(st, "tb_batch_step")
+
+    def active(self):
+        return int(load().tb_batch_active(self.b))
+
+    def finished(self, max_out=64):
+        arr = (_vp * max_out)()
+        n = C.c_int(0)
+        st = load().tb_batch_finished(self.b, arr, int(max_out), C.byref(n))
+        if st != TB_OK:
+            raise TBError(st, "tb_batch_finished")
+        return [arr[i] for i in range(n.value)]
+
+    def close(self):
+        if self.b:
+            load().tb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tb_tti_dt_max(space_order, spacing, vmax, eps_max):

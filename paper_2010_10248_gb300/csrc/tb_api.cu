@@ -22,6 +22,18 @@ cudaError_t sweep_dispatch_r4(int what, int T, int sk, const SweepParams* p, int
 cudaError_t sweep_dispatch_r6(int what, int T, int sk, const SweepParams* p, int nctas, bool coop,
                               cudaStream_t st, int* per_sm, SweepShape* s);
 
+cudaError_t sweep_batch_dispatch_r2(const BatchParams* p, int nctas, cudaStream_t st);
+cudaError_t sweep_batch_dispatch_r4(const BatchParams* p, int nctas, cudaStream_t st);
+cudaError_t sweep_batch_dispatch_r6(const BatchParams* p, int nctas, cudaStream_t st);
+cudaError_t sweep_batch_launch(int R, const BatchParams& p, int nctas, cudaStream_t st) {
+  switch (R) {
+    case 2: return sweep_batch_dispatch_r2(&p, nctas, st);
+    case 4: return sweep_batch_dispatch_r4(&p, nctas, st);
+    case 6: return sweep_batch_dispatch_r6(&p, nctas, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 static cudaError_t sweep_dispatch(int R, int what, int T, int sk, const SweepParams* p, int nctas, bool coop,
                                   cudaStream_t st, int* per_sm, SweepShape* s) {
   switch (R) {
@@ -1978,4 +1990,228 @@ extern "C" int tb_selftest_wait(double timeout_s, void* stream) {
     return TB_ECUDA;
   }
   return timed_out == 1 ? TB_ETIMEOUT : (timed_out == 0 ? TB_OK : TB_ECUDA);
+}
+
+// --------------------------------------------------------------- batch --
+// Several small acoustic shots advanced together, one launch per time step
+// for all of them (the one-step sweep over a concatenated pass table).
+struct tb_batch {
+  struct Shot {
+    tb_handle* h;
+    int nt, done, flushed, admit, slot;
+    float* traces;  // device [nt][nrec] or NULL
+    Plan p1;
+  };
+  int R = 0;
+  int max_shots = 0;
+  std::vector<Shot> active;
+  std::vector<tb_handle*> finished;
+  std::vector<char> slot_used;
+  SweepParams* d_params = nullptr;  // [2 max_shots]: even / odd steps of each slot
+  PassDesc* d_pass = nullptr;
+  int pass_cap = 0, npass = 0, nctas = 0;
+  bool dirty = true;
+  int step = 0;
+  cudaStream_t last_stream = nullptr;
+};
+
+extern "C" int tb_batch_create(int max_shots, tb_batch** out) {
+  if (!out || max_shots < 1 || max_shots > 4096) return TB_EINVAL;
+  *out = nullptr;
+  tb_batch* b = new (std::nothrow) tb_batch();
+  if (!b) return TB_ENOMEM;
+  b->max_shots = max_shots;
+  b->slot_used.assign(max_shots, 0);
+  if (dmalloc(&b->d_params, sizeof(SweepParams) * 2 * max_shots, nullptr) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return TB_ENOMEM;
+  }
+  *out = b;
+  return TB_OK;
+}
+
+extern "C" int tb_batch_destroy(tb_batch* b) {
+  if (!b) return TB_OK;
+  dfree(b->d_params, b->last_stream);
+  dfree(b->d_pass, b->last_stream);
+  delete b;
+  return TB_OK;
+}
+
+extern "C" int tb_batch_active(const tb_batch* b) { return b ? (int)b->active.size() : 0; }
+
+extern "C" int tb_batch_add(tb_batch* b, tb_handle* h, int nt, float* traces, void* stream) {
+  if (!b || !h) return TB_EINVAL;
+  if (h->physics != TB_ACOUSTIC || h->storage != TB_F32)
+    return fail(h, TB_EINVAL, "batched shots: FP32 acoustic propagation only");
+  if (!h->have_model) return fail(h, TB_ESTATE, "tb_set_model must come before tb_batch_add");
+  if (nt < 0) return fail(h, TB_EINVAL, "nt < 0");
+  if (h->have_src && h->src.npts > 0 && nt > h->src_nt)
+    return fail(h, TB_EINVAL, "nt = %d exceeds the wavelet length %d", nt, h->src_nt);
+  const int nrec = h->have_rec ? h->rec.npt : 0;
+  if (traces && nrec > 0 && !is_device_ptr(traces)) return fail(h, TB_EINVAL, "batched traces must be device memory");
+  if (b->R && b->R != h->R) return fail(h, TB_EINVAL, "a batch holds shots of one space order");
+  for (const auto& s : b->active)
+    if (s.h == h) return fail(h, TB_EINVAL, "the handle is already in the batch");
+  int slot = -1;
+  for (int i = 0; i < b->max_shots && slot < 0; ++i)
+    if (!b->slot_used[i]) slot = i;
+  if (slot < 0) return fail(h, TB_EINVAL, "the batch is full (%d shots)", b->max_shots);
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  b->last_stream = st;
+  tb_batch::Shot s{h, nt, 0, 0, b->step, slot, traces, Plan{}};
+  int r = plan_sweep(h, 1, &s.p1);
+  if (r != TB_OK) return r;
+  if ((r = ensure_capacity(h, 1, s.p1, nt, false, nrec, st)) != TB_OK) return r;
+  const size_t fbytes = sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n2p;
+  TB_CUDA(h, cudaMemsetAsync(h->field[0], 0, fbytes, st));
+  TB_CUDA(h, cudaMemsetAsync(h->field[1], 0, fbytes, st));
+  TB_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(int), st));
+  // the shot's parameters for even steps (u^n in field 0) and odd steps
+  SweepParams P[2] = {};
+  for (int par = 0; par < 2; ++par) {
+    SweepParams& Q = P[par];
+    const int c = par, p = 1 - par;
+    Q.n0 = (int)h->n[0];
+    Q.n1 = (int)h->n[1];
+    Q.n2 = (int)h->n[2];
+    Q.n2p = h->n2p;
+    Q.c2 = h->c2;
+    Q.damp_b = h->damp_b;
+    for (int d = 0; d < 3; ++d)
+      for (int i = 1; i <= h->R; ++i) {
+        const float wf = (float)(h->c[i] / (h->h[d] * h->h[d]));
+        Q.w2[d][i - 1] = make_float2(wf, wf);
+      }
+    const bool src_on = h->have_src && h->src.npts > 0;
+    Q.ev_pair = src_on ? h->ev_pair : nullptr;
+    Q.src_ev = h->src_ev;
+    Q.nev = h->nev;
+    Q.npair = h->npair;
+    const bool rec_on = h->have_rec && h->rec.npts > 0 && nrec > 0 && traces;
+    Q.r_colptr = rec_on ? h->rec.colptr : nullptr;
+    Q.r_ent = rec_on ? h->rec.ent : nullptr;
+    Q.rec_dcmp = h->rec_dcmp;
+    Q.nrpts = h->rec.npts;
+    Q.rec_cap = h->rec_cap > 0 ? h->rec_cap : 1;
+    Q.err = h->err;
+    Q.timeout_ns = (long long)(h->opt.wait_timeout_s * 1e9);
+    Q.set1_cta0 = INT_MAX;
+    Q.tm_c = h->tm_c2;
+    SweepSet& S = Q.set[0];
+    S.u_cur = h->field[c];
+    S.u_prev = h->field[p];
+    S.tm_u = h->tm_box[c];
+    S.tm_p = h->tm_tile[p];
+    S.out0 = h->field[p];  // u^{n+1} over u^{n-1}
+    S.out1 = nullptr;
+  }
+  TB_CUDA(h, cudaMemcpyAsync(b->d_params + 2 * slot, P, sizeof(P), cudaMemcpyHostToDevice, st));
+  b->slot_used[slot] = 1;
+  b->R = h->R;
+  h->last_nt = -1;
+  if (nt == 0) {
+    h->cur_idx = 0;
+    h->prev_idx = 1;
+    h->last_nt = 0;
+    b->slot_used[slot] = 0;
+    b->finished.push_back(h);
+  } else {
+    b->active.push_back(std::move(s));
+    b->dirty = true;
+  }
+  h->msg[0] = 0;
+  return TB_OK;
+}
+
+extern "C" int tb_batch_step(tb_batch* b, int nsteps, void* stream) {
+  if (!b || nsteps < 0) return TB_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  b->last_stream = st;
+  for (int k = 0; k < nsteps && !b->active.empty(); ++k) {
+    if (b->dirty) {
+      // the shots' passes, concatenated with running CTA offsets
+      std::vector<PassDesc> all;
+      int off = 0;
+      for (const auto& s : b->active) {
+        const Plan& pl = s.p1;
+        for (size_t L = 0; L < pl.launch_first.size(); ++L) {
+          const int first = pl.launch_first[L];
+          const int last = L + 1 < pl.launch_first.size() ? pl.launch_first[L + 1] : (int)pl.launch_passes.size();
+          for (int i = first; i < last; ++i) {
+            PassDesc d = pl.launch_passes[i];
+            d.cta0 += off;
+            d.shot = s.slot;
+            d.step_off = s.admit;
+            all.push_back(d);
+          }
+          off += pl.launch_ctas[L];
+        }
+      }
+      if ((int)all.size() > b->pass_cap) {
+        dfree(b->d_pass, st);
+        b->d_pass = nullptr;
+        b->pass_cap = 0;
+        if (dmalloc(&b->d_pass, sizeof(PassDesc) * all.size(), st) != cudaSuccess) {
+          cudaGetLastError();
+          return TB_ENOMEM;
+        }
+        b->pass_cap = (int)all.size();
+      }
+      if (cudaMemcpyAsync(b->d_pass, all.data(), sizeof(PassDesc) * all.size(), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        return TB_ECUDA;
+      }
+      // the pageable copy above is staged before it returns: `all` may go
+      b->npass = (int)all.size();
+      b->nctas = off;
+      b->dirty = false;
+    }
+    BatchParams L{b->d_pass, b->npass, b->d_params, b->step};
+    cudaError_t e = sweep_batch_launch(b->R, L, b->nctas, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return TB_ECUDA;
+    }
+    ++b->step;
+    for (size_t i = 0; i < b->active.size();) {
+      tb_batch::Shot& s = b->active[i];
+      tb_handle* h = s.h;
+      ++s.done;
+      const int nrec = h->have_rec ? h->rec.npt : 0;
+      const bool rec_on = h->have_rec && h->rec.npts > 0 && nrec > 0 && s.traces;
+      // receiver samples of steps [flushed, done) to traces before the ring wraps
+      if (rec_on && (s.done - s.flushed == h->rec_cap || s.done == s.nt)) {
+        const int row = s.flushed % h->rec_cap, cnt = s.done - s.flushed;
+        e = finalize_traces(cnt, nrec, h->rec.corner_eid, h->rec.corner_w, h->rec_dcmp + (size_t)row * h->rec.npts,
+                            h->rec.npts, s.traces + (size_t)s.flushed * nrec, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "batched receiver finalize");
+        s.flushed = s.done;
+      }
+      if (s.done == s.nt) {
+        h->cur_idx = s.nt & 1;
+        h->prev_idx = 1 - h->cur_idx;
+        h->last_nt = s.nt;
+        b->slot_used[s.slot] = 0;
+        b->finished.push_back(h);
+        b->active.erase(b->active.begin() + i);
+        b->dirty = true;
+      } else {
+        ++i;
+      }
+    }
+  }
+  return TB_OK;
+}
+
+extern "C" int tb_batch_finished(tb_batch* b, tb_handle** out, int max_out, int* n) {
+  if (!b || !n || max_out < 0 || (max_out > 0 && !out)) return TB_EINVAL;
+  const int k = std::min<int>(max_out, (int)b->finished.size());
+  for (int i = 0; i < k; ++i) out[i] = b->finished[i];
+  b->finished.erase(b->finished.begin(), b->finished.begin() + k);
+  *n = k;
+  return TB_OK;
 }

@@ -30,6 +30,8 @@ struct PassDesc {
   int xo0, xo1;  // planes whose results this pass owns
   int set;       // time tile of the pass: SweepParams::set[set] (set-1 passes
                  // follow the set-0 passes of a launch)
+  int shot;      // batched launches: the pass's shot (BatchParams::shots)
+  int step_off;  // batched launches: the launch at which the shot started
 };
 
 // The fields and first step of one time tile (T fused steps from step n).
@@ -86,6 +88,17 @@ struct SweepParams {
   unsigned* lp_mx;
 };
 
+// A batched one-step launch over several shots: pass table (sorted by
+// cta0), per shot two parameter sets (even and odd steps: u^n in field 0 or
+// 1) in device memory, and the launch's index (a shot's step is step -
+// pass.step_off).
+struct BatchParams {
+  const PassDesc* pass;
+  int npass;
+  const SweepParams* shots;
+  int step;
+};
+
 struct SweepShape {
   int R, T, TY;
   int threads;
@@ -102,6 +115,7 @@ bool sweep_shape(int R, int T, SweepShape* s, int sk = 0);
 cudaError_t sweep_max_ctas(int R, int T, int* per_sm, int sk = 0);
 cudaError_t sweep_launch(int R, int T, const SweepParams& p, int nctas, bool cooperative,
                          cudaStream_t st, int sk = 0);
+cudaError_t sweep_batch_launch(int R, const BatchParams& p, int nctas, cudaStream_t st);
 
 // Inspector and setup kernels (tb_inspector.cu).
 struct PointTables {

@@ -80,30 +80,6 @@ namespace tbi {
 template <int SK> struct StoreT { using type = float; };
 template <> struct StoreT<1> { using type = __half; };
 template <> struct StoreT<2> { using type = __nv_bfloat16; };
-// a column pair (two adjacent values) as FP32, and back with rounding to nearest
-__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
-__device__ __forceinline__ float2 ld2(const __half* p) { return __half22float2(*reinterpret_cast<const __half2*>(p)); }
-__device__ __forceinline__ float2 ld2(const __nv_bfloat16* p) {
-  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
-}
-__device__ __forceinline__ void st2cs(float* p, float2 v) { __stcs(reinterpret_cast<float2*>(p), v); }
-__device__ __forceinline__ void st2cs(__half* p, float2 v) {
-  const __half2 hv = __float22half2_rn(v);
-  __stcs(reinterpret_cast<unsigned*>(p), *reinterpret_cast<const unsigned*>(&hv));
-}
-__device__ __forceinline__ void st2cs(__nv_bfloat16* p, float2 v) {
-  const __nv_bfloat162 hv = __float22bfloat162_rn(v);
-  __stcs(reinterpret_cast<unsigned*>(p), *reinterpret_cast<const unsigned*>(&hv));
-}
-// one value from global memory through L2
-__device__ __forceinline__ float ld1cg(const float* p) { return __ldcg(p); }
-__device__ __forceinline__ float ld1cg(const __half* p) {
-  return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short*>(p))));
-}
-__device__ __forceinline__ float ld1cg(const __nv_bfloat16* p) {
-  return __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short*>(p))));
-}
-
 constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
 
 template <int R, int T, int TY, int SK = 0>
@@ -112,26 +88,37 @@ struct SweepCfg {
   static constexpr int ESZ = (int)sizeof(ST);  // bytes of a stored wavefield value
   static_assert(SK == 0 || T == 1, "16-bit storage: one-step kernel only");
   static constexpr int TZ = 64;
-  static constexpr int NT = 32 * TY;           // compute threads
+  static constexpr int NCOL = TY * TZ;         // columns of a tile
+  // compute lanes own CW adjacent columns of one tile row (CW / 2 packed
+  // f32x2 pairs).  The one-step kernel takes four (float4 accesses; a warp
+  // covers two rows; two CTAs per SM keep 16 compute warps on an SM); the
+  // blocked sweep, one CTA per SM whose fused steps form a long dependency
+  // chain per stream step, takes two so that 16 compute warps hide it.
+  static constexpr int CW = T == 1 ? 4 : 2;
+  static constexpr int NPAIR = CW / 2;
+  static constexpr int RPW = 32 * CW / TZ;   // tile rows per warp
+  static constexpr int NWC = TY / RPW;
+  static constexpr int NT = 32 * NWC;          // compute threads
   static constexpr bool HALO = T > 1;          // halo and publisher warps present
   // + producer, receiver (+ halo, publisher) warps
   static constexpr int NTHREADS = NT + 64 + (HALO ? 64 : 0);
-  static constexpr int WREC = TY + 1;                    // receiver warp
-  static constexpr int WHALO = TY + 2, WPUB = TY + 3;    // halo, publisher warps (T > 1)
-  // axis-2 halo width in shared memory; with 16-bit values 8 keeps the TMA
-  // box's first column z0 - RP on a 16-byte boundary
+  static constexpr int WPRO = NWC, WREC = NWC + 1;       // producer, receiver warps
+  static constexpr int WHALO = NWC + 2, WPUB = NWC + 3;  // halo, publisher warps (T > 1)
+  // axis-2 halo width in shared memory: a multiple of four values (16-byte
+  // rows for the float4 accesses); with 16-bit values 8 keeps the TMA box's
+  // first column z0 - RP on a 16-byte boundary
   static constexpr int RP = SK ? 8 : (R + 3) / 4 * 4;
-  static constexpr int SW = TZ + 2 * RP;       // plane row stride (floats)
+  static constexpr int SW = TZ + 2 * RP;       // plane row stride (values)
   static constexpr int SH = TY + 2 * R;
   static constexpr int PLANE = SW * SH;
   static constexpr int PSLOT = (int)(align128(PLANE * ESZ) / ESZ);
   static constexpr int TILE = TY * TZ;
-  static constexpr int Q = 2 * R + 1;                // queue length
+  static constexpr int Q = 2 * R + 1;                // queue length (planes around the centre)
   static constexpr int PF = 2;                       // planes of prefetch beyond need
-  // fused step 0 takes its axis-0 neighbours from a register queue when it
-  // is the only step (keeps the ring short: two CTAs per SM), else from the
-  // u^n ring (frees registers for the queues of the other fused steps)
+  // fused step 0 takes its axis-0 neighbours from a register queue where
+  // the registers allow (T queues of Q float4), else from the u^n ring
   static constexpr bool X0Q = T == 1;
+  static constexpr int NQ = X0Q ? T : T - 1;         // register queues
   static constexpr int NU = (X0Q ? R + 1 : 2 * R + 1) + PF;  // u^n box ring
   static constexpr int ULAG = X0Q ? 0 : R;           // plane p is last read at step p + ULAG
   static constexpr int NP = PF + 1;                  // u^{n-1} tile ring
@@ -142,6 +129,12 @@ struct SweepCfg {
   static_assert(NU - R - ULAG >= LEAD && NP >= LEAD && NC - (T - 1) * R >= LEAD && ND >= LEAD,
                 "ring depths must cover the prefetch distance");
   static constexpr int NDONE = 8;                    // step-retirement barriers
+  // helper warps' polls back off up to this many ns (their issue slots are
+  // the compute warps')
+  static constexpr unsigned kNapMax = 512;
+  // the stream loop is unrolled by the queue length, so that the axis-0
+  // register queues rotate by renaming; else they shift every step
+  static constexpr bool UNROLL = true;
   static constexpr int D = 2 * R + 2;                // halo ring slots per fused step (global)
   // halo strips of one tile and fused step in the global ring: the top and
   // bottom R rows with the plane's row pitch SW (so that each lands in
@@ -157,15 +150,15 @@ struct SweepCfg {
   static constexpr size_t OFF_C = OFF_P + align128((size_t)NP * TILE * ESZ);
   static constexpr size_t OFF_S = OFF_C + align128((size_t)NC * TILE * 4);
   static constexpr size_t OFF_BASE = OFF_S + align128((size_t)NSP * PSLOT * 4);
-  static constexpr size_t OFF_CNT = OFF_BASE + 4 * 2 * NT;
-  static constexpr size_t OFF_CUR = OFF_CNT + 2 * 2 * NT;
-  static constexpr size_t OFF_XF = OFF_CUR + 2 * T * 2 * NT;      // receiver columns' first x
-  static constexpr size_t OFF_RL = OFF_XF + 2 * 2 * NT;   // receiver warp: list of receiver columns
-  static constexpr size_t OFF_BAR = align128(OFF_RL + 2 * 2 * NT);
+  static constexpr size_t OFF_CNT = OFF_BASE + 4 * NCOL;
+  static constexpr size_t OFF_CUR = OFF_CNT + 2 * NCOL;
+  static constexpr size_t OFF_XF = OFF_CUR + 2 * T * NCOL;      // receiver columns' first x
+  static constexpr size_t OFF_RL = OFF_XF + 2 * NCOL;   // receiver warp: list of receiver columns
+  static constexpr size_t OFF_BAR = align128(OFF_RL + 2 * NCOL);
   static constexpr int NBAR = 1 + ND + 2 + NDONE;    // prologue, data, centre[2], done
   static constexpr size_t SMEM = OFF_BAR + 8 * NBAR + 128;    // + base alignment
   static_assert(R % 2 == 0, "radius must be even for aligned float2 access");
-  static_assert(TY >= R && TZ >= RP, "a halo must come from one neighbour tile");
+  static_assert(TY % 2 == 0 && TY >= R && TZ >= RP, "a halo must come from one neighbour tile");
   static_assert(SMEM <= 232448, "shared memory budget exceeded");
 };
 
@@ -282,43 +275,165 @@ __device__ __forceinline__ bool bounded_wait_ge(const unsigned long long* flag,
 __device__ __forceinline__ int j_mod(int j, int d) { return j % d; }
 
 // ------------------------------------------------------------ arithmetic --
+// A lane's CW = 2 NP adjacent columns as NP column pairs (packed f32x2
+// operands), moved as one float2 (NP = 1) or float4 (NP = 2).
+template <int NP>
+struct FV {
+  float2 p[NP];
+};
+template <int NP>
+__device__ __forceinline__ FV<NP> fvzero() {
+  FV<NP> v;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) v.p[i] = make_float2(0.f, 0.f);
+  return v;
+}
+template <int NP>
+__device__ __forceinline__ FV<NP> ldv(const float* p) {
+  FV<NP> v;
+  if constexpr (NP == 1) {
+    v.p[0] = *reinterpret_cast<const float2*>(p);
+  } else {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v.p[0] = make_float2(q.x, q.y);
+    v.p[1] = make_float2(q.z, q.w);
+  }
+  return v;
+}
+__device__ __forceinline__ float2 h2f(unsigned x) { return __half22float2(*reinterpret_cast<const __half2*>(&x)); }
+__device__ __forceinline__ float2 b2f(unsigned x) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&x));
+}
+template <int NP>
+__device__ __forceinline__ FV<NP> ldv(const __half* p) {
+  FV<NP> v;
+  if constexpr (NP == 1) {
+    v.p[0] = h2f(*reinterpret_cast<const unsigned*>(p));
+  } else {
+    const uint2 q = *reinterpret_cast<const uint2*>(p);
+    v.p[0] = h2f(q.x);
+    v.p[1] = h2f(q.y);
+  }
+  return v;
+}
+template <int NP>
+__device__ __forceinline__ FV<NP> ldv(const __nv_bfloat16* p) {
+  FV<NP> v;
+  if constexpr (NP == 1) {
+    v.p[0] = b2f(*reinterpret_cast<const unsigned*>(p));
+  } else {
+    const uint2 q = *reinterpret_cast<const uint2*>(p);
+    v.p[0] = b2f(q.x);
+    v.p[1] = b2f(q.y);
+  }
+  return v;
+}
+// stores: plain (shared memory), .cg (halo strips, kept in L2), .cs (outputs)
+template <int NP>
+__device__ __forceinline__ void stv(float* p, const FV<NP>& v) {
+  if constexpr (NP == 1)
+    *reinterpret_cast<float2*>(p) = v.p[0];
+  else
+    *reinterpret_cast<float4*>(p) = make_float4(v.p[0].x, v.p[0].y, v.p[1].x, v.p[1].y);
+}
+template <int NP>
+__device__ __forceinline__ void stvcg(float* p, const FV<NP>& v) {
+  if constexpr (NP == 1)
+    __stcg(reinterpret_cast<float2*>(p), v.p[0]);
+  else
+    __stcg(reinterpret_cast<float4*>(p), make_float4(v.p[0].x, v.p[0].y, v.p[1].x, v.p[1].y));
+}
+template <int NP>
+__device__ __forceinline__ void stvcs(float* p, const FV<NP>& v) {
+  if constexpr (NP == 1)
+    __stcs(reinterpret_cast<float2*>(p), v.p[0]);
+  else
+    __stcs(reinterpret_cast<float4*>(p), make_float4(v.p[0].x, v.p[0].y, v.p[1].x, v.p[1].y));
+}
+__device__ __forceinline__ unsigned f2h(float2 v) {
+  const __half2 h = __float22half2_rn(v);
+  return *reinterpret_cast<const unsigned*>(&h);
+}
+__device__ __forceinline__ unsigned f2b(float2 v) {
+  const __nv_bfloat162 h = __float22bfloat162_rn(v);
+  return *reinterpret_cast<const unsigned*>(&h);
+}
+template <int NP>
+__device__ __forceinline__ void stvcs(__half* p, const FV<NP>& v) {
+  if constexpr (NP == 1)
+    __stcs(reinterpret_cast<unsigned*>(p), f2h(v.p[0]));
+  else
+    __stcs(reinterpret_cast<uint2*>(p), make_uint2(f2h(v.p[0]), f2h(v.p[1])));
+}
+template <int NP>
+__device__ __forceinline__ void stvcs(__nv_bfloat16* p, const FV<NP>& v) {
+  if constexpr (NP == 1)
+    __stcs(reinterpret_cast<unsigned*>(p), f2b(v.p[0]));
+  else
+    __stcs(reinterpret_cast<uint2*>(p), make_uint2(f2b(v.p[0]), f2b(v.p[1])));
+}
+// one value from global memory through L2
+__device__ __forceinline__ float ld1cg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ float ld1cg(const __half* p) {
+  return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short*>(p))));
+}
+__device__ __forceinline__ float ld1cg(const __nv_bfloat16* p) {
+  return __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short*>(p))));
+}
+
 // Eq. 1 at one point: u^{n+1} = [dt^2 L u + m(2u - u_prev) + a u_prev]/(m + a)
 // rewritten with c2 = dt^2/m and g = a/m = (eta/(2 dt)) c2 as an increment:
 //   u^{n+1} = u + (c2 L u + (1 - g)(u - u_prev)) / (1 + g),
 // on a column pair with packed f32x2 round-to-nearest operations.  x - y is
 // formed as fma(y, -1, x) (the product is exact, so one rounding, as a
-// subtraction).  Branch-free: outside the sponge g = 0, 1 - g and 1 + g are
-// exactly 1, the reciprocal of 1 is exactly 1, and the result is
-// u + (c2 L u + (u - u_prev)) with the same roundings; inside, the quotient
-// is the reciprocal times the numerator (within 2 ulp of the correctly
-// rounded division).
-__device__ __forceinline__ float2 point_update2(float2 uc, float2 up, float2 lap, float2 c2,
-                                               float2 bsum) {
+// subtraction).  Inside the sponge the quotient is the reciprocal times the
+// numerator (within 2 ulp of the correctly rounded division); where g = 0
+// every operation reduces exactly to point_update2_free, so the choice
+// between the two never changes a result.
+__device__ __forceinline__ float2 point_update2(float2 uc, float2 up, float2 lap, float2 c2, float2 bsum) {
   const float2 m1 = make_float2(-1.f, -1.f), one = make_float2(1.f, 1.f);
   const float2 d = __ffma2_rn(up, m1, uc);
   const float2 g = __fmul2_rn(bsum, c2);
   const float2 inc = __ffma2_rn(c2, lap, __fmul2_rn(__ffma2_rn(g, m1, one), d));
   const float2 opg = __fadd2_rn(one, g);
-  return __fadd2_rn(uc, make_float2(__fdividef(inc.x, opg.x), __fdividef(inc.y, opg.y)));
+  // where g = 0 the quotient is inc itself, as in point_update2_free
+  return __fadd2_rn(uc, make_float2(g.x == 0.f ? inc.x : __fdividef(inc.x, opg.x),
+                                    g.y == 0.f ? inc.y : __fdividef(inc.y, opg.y)));
+}
+// The same update where no damping acts (g = 0): u + (c2 L u + (u - u_prev)).
+__device__ __forceinline__ float2 point_update2_free(float2 uc, float2 up, float2 lap, float2 c2) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  return __fadd2_rn(uc, __ffma2_rn(c2, lap, __ffma2_rn(up, m1, uc)));
 }
 
-// One neighbour pair of the Laplacian in differences form on a column pair,
-// acc + w ((a - u) + (b - u)).  The differences of close values are exact, so
+// Neighbour pairs of the Laplacian on a column pair.  The pairs with the two
+// largest weights (offsets 1 and 2) are taken in differences form,
+// acc + w ((a - u) + (b - u)): differences of close values are exact, so
 // the large centre term never cancels against the neighbour sum (in FP32
-// this keeps 1000-step runs ~40x closer to the FP64 result than the
-// c0 u + sum c_i (u_+i + u_-i) form).
-__device__ __forceinline__ float2 pair_term2(float2 acc, float2 w2, float2 a, float2 b, float2 u) {
+// the c0 u + sum c_i (u_+i + u_-i) form lost ~40x accuracy over 1000 steps).
+// The pairs further out (weights below 3 % of the nearest one at space order
+// 8 and 12) are summed directly, acc + w (a + b), and their centre term
+// -2 sum w u is added once per point: the cancellation there is against
+// values ~30x smaller than the centre term of the direct form.
+__device__ __forceinline__ float2 pair_diff2(float2 acc, float2 w2, float2 a, float2 b, float2 u) {
   const float2 m1 = make_float2(-1.f, -1.f);
   return __ffma2_rn(w2, __fadd2_rn(__ffma2_rn(u, m1, a), __ffma2_rn(u, m1, b)), acc);
 }
+__device__ __forceinline__ float2 pair_sum2(float2 acc, float2 w2, float2 a, float2 b) {
+  return __ffma2_rn(w2, __fadd2_rn(a, b), acc);
+}
+constexpr int kDiffPairs = 2;  // offsets taken in differences form
 
 // ----------------------------------------------------------------- kernel --
-template <int R, int T, int TY, int SK = 0, bool TWO = false, bool PRE = false>
-__global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 : 1)
-    sweep_kernel(const __grid_constant__ SweepParams P) {
+// The sweep of one CTA: pass pd (the CTA's place in the launch), block
+// index b within the launch, time tile s1 (launches holding two), first
+// step step0.  P holds the fields, tables and model of the propagation.
+template <int R, int T, int TY, int SK, bool TWO, bool PRE>
+__device__ __forceinline__ void sweep_body(const SweepParams& P, const PassDesc& pd, const int b, const bool s1,
+                                           const int step0) {
   using C = SweepCfg<R, T, TY, SK>;
   using ST = typename C::ST;
-  constexpr int TZ = C::TZ, NT = C::NT, SW = C::SW, RP = C::RP;
+  constexpr int TZ = C::TZ, NT = C::NT, SW = C::SW, RP = C::RP, NCOL = C::NCOL;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // TMA destinations need 128-byte alignment: align the base explicitly
   unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -331,23 +446,16 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
   uint64_t* bar_ctr = bar_dat + C::ND; // [2] centres and halos of stream step j in buffer j & 1
   uint64_t* bar_done = bar_ctr + 2;    // [NDONE] compute warps finished a stream step
   // per-column state of the grid-aligned receivers (receiver warp)
-  int* cbase = reinterpret_cast<int*>(smem + C::OFF_BASE);                      // [col][NT]
-  unsigned short* ccnt = reinterpret_cast<unsigned short*>(smem + C::OFF_CNT);  // [col][NT]
-  unsigned short* ccur = reinterpret_cast<unsigned short*>(smem + C::OFF_CUR);  // [T][col][NT]
-  unsigned short* cxf = reinterpret_cast<unsigned short*>(smem + C::OFF_XF);    // [col][NT]
+  int* cbase = reinterpret_cast<int*>(smem + C::OFF_BASE);                      // [NCOL]
+  unsigned short* ccnt = reinterpret_cast<unsigned short*>(smem + C::OFF_CNT);  // [NCOL]
+  unsigned short* ccur = reinterpret_cast<unsigned short*>(smem + C::OFF_CUR);  // [T][NCOL]
+  unsigned short* cxf = reinterpret_cast<unsigned short*>(smem + C::OFF_XF);    // [NCOL]
 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int b = blockIdx.x;
-  int pi = 0;
-  for (int i = 1; i < P.npass; ++i)
-    if (P.pass[i].cta0 <= b) pi = i;
-  const PassDesc pd = P.pass[pi];
   // the pass's time tile: launches holding two time tiles run the TWO
   // instantiation, which selects the fields by the block index (the select
   // costs ~2 % more instructions in the fused steps, so single-tile
   // launches take the other one)
-  const bool s1 = TWO && b >= P.set1_cta0;
-  const int step0 = s1 ? P.set[1].step0 : P.set[0].step0;
   float* const out0 = s1 ? P.set[1].out0 : P.set[0].out0;
   float* const out1 = s1 ? P.set[1].out1 : P.set[0].out1;
   const float* const u_cur = s1 ? P.set[1].u_cur : P.set[0].u_cur;
@@ -381,7 +489,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
   const int nb_lf = tz > 0 ? b - 1 : -1;
   const int nb_rt = tz + 1 < pd.ntz ? b + 1 : -1;
 
-  if (w == TY) {
+  if (w == C::WPRO) {
     // =========================== producer warp ===========================
     if (lane != 0) return;
     auto u_slot = [&](int p) { return uring + ((p - pu0) % C::NU) * C::PSLOT; };
@@ -406,7 +514,9 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
       // retire the next stream step (polled with a short back-off so the
       // refills above go out as soon as a step is done)
       const int s = ret + 1;
-      if (!mbar_poll(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo)) {
+      // (suspending on the barrier: a polling loop here took issue slots
+      // from the compute warps of the producer's sub-partition)
+      if (!mbar_wait(bar_done + (s - jstart) % C::NDONE, ((s - jstart) / C::NDONE) & 1, tmo)) {
         atomicExch(P.err, 2);
         ok = false;
         break;
@@ -430,13 +540,14 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
     // compact list of their slots (bit 15: entries contiguous in x)
     int* rbase = cbase;
     unsigned short* rcnt = ccnt;
-    unsigned short* rcur = ccur;  // [T][col][NT]
+    unsigned short* rcur = ccur;  // [T][NCOL]
     unsigned short* rlist = reinterpret_cast<unsigned short*>(smem + C::OFF_RL);
     int nlist = 0;
     int xlo = 0x7fffffff, xhi = -1;  // planes holding the tile's receiver points
-    for (int s0 = 0; s0 < 2 * NT; s0 += 32) {
-      const int sl = s0 + lane, ci = sl / NT, t = sl - ci * NT;
-      const int yy = y0 + (t >> 5), zz = z0 + 2 * (t & 31) + ci;
+    // tile column sl: row sl / TZ, column sl mod TZ
+    for (int s0 = 0; s0 < NCOL; s0 += 32) {
+      const int sl = s0 + lane;
+      const int yy = y0 + sl / TZ, zz = z0 + sl % TZ;
       bool has = false, dense = false;
       if (P.r_colptr && yy < P.n1 && zz < P.n2 && yy >= pd.yo0 && yy < pd.yo1) {
         const int c = yy * P.n2 + zz;
@@ -450,7 +561,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
           dense = xl - xf + 1 == ce - cb;
           xlo = min(xlo, xf);
           xhi = max(xhi, xl);
-          for (int k = 0; k < T; ++k) rcur[k * 2 * NT + sl] = 0;
+          for (int k = 0; k < T; ++k) rcur[k * NCOL + sl] = 0;
         }
       }
       const unsigned m = __ballot_sync(0xffffffffu, has);
@@ -468,14 +579,14 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
       if (q < xlo || q > xhi) return;
       float* rrow = P.rec_dcmp + (size_t)((step0 + kk) & (P.rec_cap - 1)) * P.nrpts;
       for (int e = lane; e < nlist; e += 32) {
-        const int en = rlist[e], sl = en & 0x7fff, ci = sl / NT, t = sl - ci * NT;
+        const int en = rlist[e], sl = en & 0x7fff, row = sl / TZ, col = sl % TZ;
         const int cn = rcnt[sl], cb = rbase[sl];
         int pos = -1;
         if (en & 0x8000) {
           const unsigned off = (unsigned)(q - (int)cxf[sl]);
           if (off < (unsigned)cn) pos = cb + (int)off;
         } else {
-          unsigned short* cp = &rcur[kk * 2 * NT + sl];
+          unsigned short* cp = &rcur[kk * NCOL + sl];
           int cc = *cp;
           while (cc < cn) {
             const int x = __ldg(&P.r_ent[cb + cc].x);
@@ -489,21 +600,22 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
           *cp = (unsigned short)cc;
         }
         if (pos >= 0) {
-          const int ww = t >> 5, ln = t & 31;
-          const size_t go = (size_t)q * ps + (size_t)(y0 + ww) * P.n2p + z0 + 2 * ln + ci;
+          const size_t go = (size_t)q * ps + (size_t)(y0 + row) * P.n2p + z0 + col;
           if constexpr (SK != 0)  // one-step only: u^{n+1} is stored as u / s
             rrow[pos] = __fmul_rn(ld1cg(reinterpret_cast<const ST*>(out0) + go), __ldg(P.lp_scales + step0 + 2));
           else
-            rrow[pos] = plane ? plane[(R + ww) * SW + RP + 2 * ln + ci] : __ldcg(out0 + go);
+            rrow[pos] = plane ? plane[(R + row) * SW + RP + col] : __ldcg(out0 + go);
         }
       }
     };
     // steps retired by the producer (its level-n+T planes are in global memory)
     auto wait_retired = [&](int jr) -> bool {
       const unsigned long long t0 = global_ns();
+      unsigned nap = 64;
       while (ld_acquire_cta_s32(&s_ret) < jr) {
         if ((long long)(global_ns() - t0) > tmo) return false;
-        __nanosleep(64);
+        __nanosleep(nap);
+        nap = nap < C::kNapMax ? 2 * nap : nap;
       }
       return true;
     };
@@ -545,6 +657,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
       // publishes the producer's latest retired step (it may skip steps
       // while a release is in flight: the counter is monotonic)
       if (lane != 0) return;
+      unsigned nap = 64;
       int pub = jstart - 1;
       unsigned long long t0 = global_ns();
       while (pub < jend) {
@@ -556,12 +669,14 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
           st_release_u64(&P.progress[(size_t)b * kProgressStride], P.prog_base + (unsigned long long)(r - jstart + 1));
           pub = r;
           t0 = global_ns();
+          nap = 64;
         } else {
           if ((long long)(global_ns() - t0) > tmo) {
             atomicExch(P.err, 2);
             break;
           }
-          __nanosleep(64);
+          __nanosleep(nap);
+          nap = nap < C::kNapMax ? 2 * nap : nap;
         }
       }
       return;
@@ -582,6 +697,7 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
         if (jn - R >= jstart) {
           const unsigned long long target = P.prog_base + (unsigned long long)(jn - R - jstart + 1);
           const unsigned long long t0 = global_ns();
+          unsigned nap = 32;  // back-off: the warp's polls take issue slots from the compute warps
           while (true) {
             if (nb >= 0 && seen < target) seen = ld_acquire_u64(&P.progress[(size_t)nb * kProgressStride]);
             if (__all_sync(0xffffffffu, nb < 0 || seen >= target)) break;
@@ -589,7 +705,8 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
               ok = false;
               break;
             }
-            __nanosleep(32);
+            __nanosleep(nap);
+            nap = nap < C::kNapMax ? 2 * nap : nap;
           }
           if (!ok) {
             atomicExch(P.err, 1);
@@ -680,56 +797,107 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
   }
 
   // ============================== compute warps ==============================
-  const int y = y0 + w, z = z0 + 2 * lane;
+  // A lane owns the CW adjacent columns c0 .. c0 + CW - 1 of tile row r: a
+  // warp covers RPW rows (lanes 0-15 and 16-31 with four columns each, or
+  // all 32 lanes of one row with two).
+  constexpr int CW = C::CW, NPR = C::NPAIR;
+  using V = FV<NPR>;
+  constexpr int LPR = TZ / CW;                    // lanes per tile row
+  const int r = C::RPW * w + lane / LPR, c0 = CW * (lane % LPR);
+  const int y = y0 + r, z = z0 + c0;
   const bool vrow = y < P.n1;
-  const bool v0 = vrow && z < P.n2, v1 = vrow && z + 1 < P.n2;
+  const bool vz = vrow && z < P.n2;               // the lane's first column is in the grid
   const bool own_row = y >= pd.yo0 && y < pd.yo1;
-  const size_t ps = (size_t)P.n1 * P.n2p;        // plane stride
-  const size_t coff = (size_t)y * P.n2p + z;     // column offset (valid if v0)
-  const int own = (R + w) * SW + RP + 2 * lane;  // own pair in a plane slot
-  const int own_t = w * TZ + 2 * lane;           // own pair in a tile slot
+  const size_t ps = (size_t)P.n1 * P.n2p;         // plane stride
+  const size_t coff = (size_t)y * P.n2p + z;      // column offset (valid if vz)
+  const int own = (R + r) * SW + RP + c0;         // own columns in a plane slot
+  const int own_t = r * TZ + c0;                  // own columns in a tile slot
   // this thread's place in the halo strips it publishes (-1: none)
-  const int strip_y = w < R ? w * SW + RP + 2 * lane
-                            : (w >= TY - R ? (R + w - (TY - R)) * SW + RP + 2 * lane : -1);
-  const int strip_z = 2 * lane < RP ? 2 * C::STRIP_Y + w * RP + 2 * lane
-                                    : (2 * lane >= TZ - RP ? 2 * C::STRIP_Y + TY * RP + w * RP + 2 * lane - (TZ - RP) : -1);
+  const int strip_y = r < R ? r * SW + RP + c0 : (r >= TY - R ? (R + r - (TY - R)) * SW + RP + c0 : -1);
+  const int strip_z = c0 < RP ? 2 * C::STRIP_Y + r * RP + c0
+                              : (c0 >= TZ - RP ? 2 * C::STRIP_Y + TY * RP + r * RP + c0 - (TZ - RP) : -1);
 
-  float2 byz = make_float2(0.f, 0.f);
-  if (v0) byz.x = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z]));
-  if (v1) byz.y = __fadd_rn(__ldg(&P.damp_b[P.n0 + y]), __ldg(&P.damp_b[P.n0 + P.n1 + z + 1]));
+  // damping along axes 1 and 2 of the lane's columns (zero outside the
+  // grid), and whether none acts anywhere in the warp's columns: then the
+  // update takes the undamped form wherever the plane is outside the axis-0
+  // sponge
+  float bzc[CW];
+#pragma unroll
+  for (int c = 0; c < CW; ++c) bzc[c] = 0.f;
+  if (vrow) {
+    const float by = __ldg(&P.damp_b[P.n0 + y]);
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+      if (z + c < P.n2) bzc[c] = __fadd_rn(by, __ldg(&P.damp_b[P.n0 + P.n1 + z + c]));
+  }
+  V byz;
+  bool nodamp = true;
+#pragma unroll
+  for (int p = 0; p < NPR; ++p) {
+    byz.p[p] = make_float2(bzc[2 * p], bzc[2 * p + 1]);
+    nodamp = nodamp && bzc[2 * p] == 0.f && bzc[2 * p + 1] == 0.f;
+  }
+  const bool yz_free = __all_sync(0xffffffffu, nodamp);
 
-  // The column pair's grid-aligned source points (Sec. II-A, Listing 5): the
+  // centre weight of the directly summed pairs, -2 sum_d sum_{i > 2} c_i / h_d^2
+  float2 wcen = make_float2(0.f, 0.f);
+  if constexpr (R > kDiffPairs) {
+    float s = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int i = kDiffPairs; i < R; ++i) s = __fadd_rn(s, P.w2[d][i].x);
+    wcen = make_float2(-2.f * s, -2.f * s);
+  }
+
+  // The column pairs' grid-aligned source points (Sec. II-A, Listing 5): the
   // planes ev_x .. ev_x + ev_n - 1 carry the pair's injections, read from
   // src_ev[step][ev_b + plane - ev_x] (zero for a column without a point at
   // that plane).  The check is a compare and a predicated load per fused
-  // step, with no loop, cursor or shared-memory store in the step's code.
-  int ev_x = 0, ev_n = 0, ev_b = 0;
-  if (v0 && P.ev_pair) {
-    const int2 d = __ldg(&P.ev_pair[(size_t)y * P.npair + (z >> 1)]);
-    ev_x = d.x & 0xffff;
-    ev_n = (int)((unsigned)d.x >> 16);
-    ev_b = d.y;
+  // step and pair, with no loop, cursor or shared-memory store in the step's
+  // code.
+  int ev_x[NPR], ev_n[NPR];
+  const float2* evrow[NPR];
+  bool any_src = false;
+#pragma unroll
+  for (int p = 0; p < NPR; ++p) {
+    ev_x[p] = 0;
+    ev_n[p] = 0;
+    evrow[p] = nullptr;
+    if (vz && P.ev_pair && z + 2 * p < P.n2) {
+      const int2 d = __ldg(&P.ev_pair[(size_t)y * P.npair + (z >> 1) + p]);
+      ev_x[p] = d.x & 0xffff;
+      ev_n[p] = (int)((unsigned)d.x >> 16);
+      if (ev_n[p] > 0) evrow[p] = P.src_ev + (size_t)step0 * P.nev + d.y;
+    }
+    any_src = any_src || ev_n[p] > 0;
   }
 
-  // Register queues: Q0 holds u^n around plane j (one-step kernel only);
-  // fused step k >= 1 uses Qs[k-1], level n+k around plane q_k.
-  constexpr int TQ = T > 1 ? T - 1 : 1;
-  float2 Qs[TQ][C::Q];
-  float2 Q0[C::X0Q ? C::Q : 1];
+  // Register queues along axis 0, rotated by renaming: the stream loop is
+  // unrolled by Q = 2r + 1, and at stream step j (phase i = (j - jstart) mod
+  // Q) logical entry s of a queue (plane centre - r + s) is register
+  // (i + s) mod Q.  Queue QI(k) holds level n+k around the plane of fused
+  // step k (level n only with X0Q).
+  constexpr int Q = C::Q, NQ = C::NQ;
+  auto QI = [](int k) { return C::X0Q ? k : k - 1; };
+  V qq[NQ][Q];
 #pragma unroll
-  for (int k = 0; k < TQ; ++k)
+  for (int k = 0; k < NQ; ++k)
 #pragma unroll
-    for (int s = 0; s < C::Q; ++s) Qs[k][s] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int s = 0; s < (C::X0Q ? C::Q : 1); ++s) Q0[s] = make_float2(0.f, 0.f);
+    for (int s = 0; s < Q; ++s) qq[k][s] = fvzero<NPR>();
   if constexpr (C::X0Q) {
-    // planes [jstart-1-R, jstart-1+R] of u^n before the first shift
+    // planes jstart - r .. jstart + r - 1 of u^n (logical 0 .. 2r - 1 at phase 0)
 #pragma unroll
-    for (int s = 0; s < C::Q; ++s) {
-      const int plane = jstart - 1 - R + s;
-      if (v0 && plane >= 0 && plane < P.n0) {
-        Q0[s] = ld2(reinterpret_cast<const ST*>(u_cur) + (size_t)plane * ps + coff);
-        if (!v1) Q0[s].y = 0.f;
+    for (int s = 0; s < 2 * R; ++s) {
+      const int plane = jstart - R + s;
+      if (vz && plane >= 0 && plane < P.n0) {
+        V v = ldv<NPR>(reinterpret_cast<const ST*>(u_cur) + (size_t)plane * ps + coff);
+#pragma unroll
+        for (int p = 0; p < NPR; ++p) {
+          if (z + 2 * p >= P.n2) v.p[p].x = 0.f;
+          if (z + 2 * p + 1 >= P.n2) v.p[p].y = 0.f;
+        }
+        qq[0][s] = v;
       }
     }
   }
@@ -754,206 +922,255 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
     io2 = make_float2(o, o);
   }
 
+  // Laplacian (differences form for the nearest pairs, direct sums further
+  // out, see pair_diff2) of the lane's columns at a plane slot `pl` (axes 1
+  // and 2) with centre uc; xn(d) gives the axis-0 neighbours at +d (d > 0)
+  // and -d (d < 0).  Every point's terms are summed in one fixed order, so
+  // every fused step and the one-step kernel round alike.
+  constexpr int NZ = (R + CW - 1) / CW;  // chunks of CW axis-2 neighbours on each side
+  auto laplacian = [&](const auto* pl, const V& uc, auto&& xn) -> V {
+    float zv[CW * (2 * NZ + 1)];
+#pragma unroll
+    for (int m = 0; m < NZ; ++m) {
+      const V lf = ldv<NPR>(pl + own - CW * (m + 1)), rt = ldv<NPR>(pl + own + CW * (m + 1));
+#pragma unroll
+      for (int p = 0; p < NPR; ++p) {
+        zv[CW * (NZ - 1 - m) + 2 * p] = lf.p[p].x;
+        zv[CW * (NZ - 1 - m) + 2 * p + 1] = lf.p[p].y;
+        zv[CW * (NZ + 1 + m) + 2 * p] = rt.p[p].x;
+        zv[CW * (NZ + 1 + m) + 2 * p + 1] = rt.p[p].y;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < NPR; ++p) {
+      zv[CW * NZ + 2 * p] = uc.p[p].x;
+      zv[CW * NZ + 2 * p + 1] = uc.p[p].y;
+    }
+    float2 lx[NPR], ly[NPR], lz[NPR];
+#pragma unroll
+    for (int d = 1; d <= R; ++d) {
+      const V xp = xn(d), xm = xn(-d);
+      const V yp = ldv<NPR>(pl + own + d * SW), ym = ldv<NPR>(pl + own - d * SW);
+#pragma unroll
+      for (int p = 0; p < NPR; ++p) {
+        const float2 u = uc.p[p];
+        const int c = CW * NZ + 2 * p;
+        const float2 cp = make_float2(zv[c + d], zv[c + 1 + d]), cm = make_float2(zv[c - d], zv[c + 1 - d]);
+        if (d == 1) {
+          const float2 m1 = make_float2(-1.f, -1.f);
+          lx[p] = __fmul2_rn(P.w2[0][0], __fadd2_rn(__ffma2_rn(u, m1, xp.p[p]), __ffma2_rn(u, m1, xm.p[p])));
+          ly[p] = __fmul2_rn(P.w2[1][0], __fadd2_rn(__ffma2_rn(u, m1, yp.p[p]), __ffma2_rn(u, m1, ym.p[p])));
+          lz[p] = __fmul2_rn(P.w2[2][0], __fadd2_rn(__ffma2_rn(u, m1, cp), __ffma2_rn(u, m1, cm)));
+        } else if (d <= kDiffPairs) {
+          lx[p] = pair_diff2(lx[p], P.w2[0][d - 1], xp.p[p], xm.p[p], u);
+          ly[p] = pair_diff2(ly[p], P.w2[1][d - 1], yp.p[p], ym.p[p], u);
+          lz[p] = pair_diff2(lz[p], P.w2[2][d - 1], cp, cm, u);
+        } else {
+          lx[p] = pair_sum2(lx[p], P.w2[0][d - 1], xp.p[p], xm.p[p]);
+          ly[p] = pair_sum2(ly[p], P.w2[1][d - 1], yp.p[p], ym.p[p]);
+          lz[p] = pair_sum2(lz[p], P.w2[2][d - 1], cp, cm);
+        }
+      }
+    }
+    V out;
+#pragma unroll
+    for (int p = 0; p < NPR; ++p) {
+      float2 l = __fadd2_rn(__fadd2_rn(lx[p], ly[p]), lz[p]);
+      if constexpr (R > kDiffPairs) l = __ffma2_rn(wcen, uc.p[p], l);
+      out.p[p] = l;
+    }
+    return out;
+  };
+  // Eq. 1's update of the lane's columns; `free` (warp-uniform): no damping
+  // at any of the warp's points
+  auto update = [&](const V& uc, const V& up, const V& lap, const V& c2v, float bx, bool free) -> V {
+    V o;
+    if (free) {
+#pragma unroll
+      for (int p = 0; p < NPR; ++p) o.p[p] = point_update2_free(uc.p[p], up.p[p], lap.p[p], c2v.p[p]);
+    } else {
+      const float2 bxx = make_float2(bx, bx);
+#pragma unroll
+      for (int p = 0; p < NPR; ++p)
+        o.p[p] = point_update2(uc.p[p], up.p[p], lap.p[p], c2v.p[p], __fadd2_rn(bxx, byz.p[p]));
+    }
+    return o;
+  };
+
   bool ok = mbar_wait(bar_pro, 0, tmo);  // u^n planes pu0 .. jstart+R-1
 
-  // fused grid-aligned injection of fused step k at plane q (Listing 5).  With
-  // one step per stream step a column pair without sources skips it by a
-  // branch; with several, the test stays branch-light so that the fused
-  // steps' code is not split.
-  const float2* evrow = ev_n > 0 ? P.src_ev + (size_t)step0 * P.nev + ev_b : nullptr;
+  // fused grid-aligned injection of fused step k at plane q (Listing 5).
   // PRE (sources with long plane ranges): the T values of a stream step are
   // loaded at its top (inj), so that their latency overlaps the steps'
-  // arithmetic instead of stalling the fused step that adds them (a column
-  // pair whose range spans many planes loads in every stream step, and its
-  // warp's stalls held back the whole lockstep band).  With short ranges
-  // (single sources) the in-step load is cheaper than the prefetch.
-  float2 inj[PRE ? T : 1];
-  auto inject = [&](int k, int q, float2& un) {
-    if constexpr (T == 1)
-      if (ev_n == 0) return;
-    const unsigned off = (unsigned)(q - ev_x);
-    if constexpr (PRE) {
-      if (off < (unsigned)ev_n) un = __fadd2_rn(un, inj[k]);
-    } else {
-      if (off < (unsigned)ev_n) un = __fadd2_rn(un, __ldg(evrow + (size_t)k * P.nev + off));
+  // arithmetic instead of stalling the fused step that adds them.
+  float2 inj[PRE ? T : 1][NPR];
+  auto inject = [&](int k, int q, V& un) {
+#pragma unroll
+    for (int p = 0; p < NPR; ++p) {
+      const unsigned off = (unsigned)(q - ev_x[p]);
+      if constexpr (PRE) {
+        if (off < (unsigned)ev_n[p]) un.p[p] = __fadd2_rn(un.p[p], inj[k][p]);
+      } else {
+        if (off < (unsigned)ev_n[p]) un.p[p] = __fadd2_rn(un.p[p], __ldg(evrow[p] + (size_t)k * P.nev + off));
+      }
     }
   };
 
   int su = (jstart - pu0) % C::NU;  // ring slot of u^n plane j
   int sp = 0, sc = 0;               // ring slots of u^{n-1}, c2 plane j
   int jd = j_mod(jstart, C::D);     // j mod D (halo ring slot of plane j)
+  float* const rs_base = P.ring + (size_t)b * (T > 1 ? (T - 1) * C::D * C::STRIP : 0);
+  constexpr int UNR = C::UNROLL ? Q : 1;
 #pragma unroll 1
-  for (int j = jstart; j <= jend && ok; ++j) {
-    const bool act0 = j >= pd.xc0 && j < pd.xc1;
-    if constexpr (PRE) {
+  for (int jb = jstart; jb <= jend && ok; jb += UNR) {
 #pragma unroll
-      for (int k = 0; k < T; ++k) {
-        const unsigned off = (unsigned)(j - k * R - ev_x);
-        inj[k] = off < (unsigned)ev_n ? __ldg(evrow + (size_t)k * P.nev + off) : make_float2(0.f, 0.f);
-      }
-    }
-    const float bxc = bxn;
-    bxn = __ldg(&P.damp_b[min(max(j + 1 - kl * R, 0), P.n0 - 1)]);
-    int suR = su + R;
-    suR -= suR >= C::NU ? C::NU : 0;
-    // u^n plane j+R, u^{n-1} and c2 plane j
-    ok = mbar_wait(bar_dat + (j - jstart) % C::ND, ((j - jstart) / C::ND) & 1, tmo);
-    if constexpr (T > 1) {
-      // centres and halo strips of this step, staged during the previous one;
-      // the phase also means every compute thread finished step j-1
-      if (j > jstart) ok = ok && mbar_wait(bar_ctr + (j & 1), ((j - jstart - 1) >> 1) & 1, tmo);
-    }
-    if (!ok) break;
-
-    // ---- fused step 0
-    const ST* ub = uring + su * C::PSLOT;
-    if constexpr (C::X0Q) {
-      const float2 nq = ld2(uring + suR * C::PSLOT + own);
+    for (int i = 0; i < UNR; ++i) {
+      const int j = jb + i;
+      if (j <= jend && ok) {
+        const bool act0 = j >= pd.xc0 && j < pd.xc1;
+        if constexpr (PRE) {
 #pragma unroll
-      for (int s = 0; s < C::Q - 1; ++s) Q0[s] = Q0[s + 1];
-      Q0[C::Q - 1] = nq;
-    }
-    float2 un0 = make_float2(0.f, 0.f);
-    if (act0) {
-      const float2 uc0 = C::X0Q ? Q0[R] : ld2(ub + own);
-      const float2 up = ld2(pring + sp * C::TILE + own_t);
-      const float2 c2v = *reinterpret_cast<const float2*>(cring + sc * C::TILE + own_t);
-      float2 zp[R + 1];
+          for (int k = 0; k < T; ++k)
 #pragma unroll
-      for (int m = 0; m <= R; ++m)
-        zp[m] = (m == R / 2) ? uc0 : ld2(&ub[own - R + 2 * m]);
-      float2 lx = make_float2(0.f, 0.f), ly = lx, lz = lx;
-#pragma unroll
-      for (int d = 1; d <= R; ++d) {
-        float2 xp, xm;
-        if constexpr (C::X0Q) {
-          xp = Q0[R + d];
-          xm = Q0[R - d];
-        } else {
-          int sf = su + d, sb = su - d;
-          sf -= sf >= C::NU ? C::NU : 0;
-          sb += sb < 0 ? C::NU : 0;
-          xp = ld2(uring + sf * C::PSLOT + own);
-          xm = ld2(uring + sb * C::PSLOT + own);
-        }
-        const float2 yp = ld2(&ub[own + d * SW]);
-        const float2 ym = ld2(&ub[own - d * SW]);
-        float2 zpl, zmi;
-        if (d % 2 == 0) {
-          zpl = zp[R / 2 + d / 2];
-          zmi = zp[R / 2 - d / 2];
-        } else {
-          zpl = make_float2(zp[R / 2 + (d - 1) / 2].y, zp[R / 2 + (d + 1) / 2].x);
-          zmi = make_float2(zp[R / 2 - (d + 1) / 2].y, zp[R / 2 - (d - 1) / 2].x);
-        }
-        lx = pair_term2(lx, P.w2[0][d - 1], xp, xm, uc0);
-        ly = pair_term2(ly, P.w2[1][d - 1], yp, ym, uc0);
-        lz = pair_term2(lz, P.w2[2][d - 1], zpl, zmi, uc0);
-      }
-      const float2 lap = __fadd2_rn(__fadd2_rn(lx, ly), lz);
-      const float bx = __shfl_sync(0xffffffffu, bxc, 0);
-      if constexpr (SK != 0)  // stored values are u / s: scale back (exact, s a power of two)
-        un0 = point_update2(__fmul2_rn(uc0, sc2), __fmul2_rn(up, sp2), __fmul2_rn(lap, sc2), c2v,
-                            __fadd2_rn(make_float2(bx, bx), byz));
-      else
-        un0 = point_update2(uc0, up, lap, c2v, __fadd2_rn(make_float2(bx, bx), byz));
-      inject(0, j, un0);
-    }
-
-    if constexpr (T == 1) {
-      if (act0 && own_row && j >= pd.xo0 && j < pd.xo1 && v0) {
-        if constexpr (SK != 0) {
-          vmax = fmaxf(vmax, fmaxf(fabsf(un0.x), v1 ? fabsf(un0.y) : 0.f));
-          st2cs(reinterpret_cast<ST*>(out0) + (size_t)j * ps + coff, __fmul2_rn(un0, io2));
-        } else {
-          __stcs(reinterpret_cast<float2*>(out0 + (size_t)j * ps + coff), un0);
-        }
-      }
-    } else {
-      float* rs_base = P.ring + (size_t)b * (T - 1) * C::D * C::STRIP;
-      const float* rdbuf = splane + (size_t)(j & 1) * (T - 1) * C::PSLOT;
-      float* wrbuf = splane + (size_t)((j + 1) & 1) * (T - 1) * C::PSLOT;
-      float2 un = un0;
-      bool act = act0;
-#pragma unroll
-      for (int k = 0; k < T; ++k) {
-        const int q = j - k * R;
-        if (k > 0) {
-          act = q >= pd.xc0 && q < pd.xc1;
-          un = make_float2(0.f, 0.f);
-          if (act) {
-            const float* pl = rdbuf + (k - 1) * C::PSLOT;
-            // u_prev of step k: level n+k-1 at plane q
-            float2 upv;
-            if (k == 1) {
-              int sq = su - R;
-              sq += sq < 0 ? C::NU : 0;
-              upv = ld2(uring + sq * C::PSLOT + own);
-            } else {
-              upv = Qs[k >= 2 ? k - 2 : 0][0];
+            for (int p = 0; p < NPR; ++p) {
+              const unsigned off = (unsigned)(j - k * R - ev_x[p]);
+              inj[k][p] = off < (unsigned)ev_n[p] ? __ldg(evrow[p] + (size_t)k * P.nev + off) : make_float2(0.f, 0.f);
             }
-            int scq = sc - k * R;
-            scq += scq < 0 ? C::NC : 0;
-            const float2 c2v = *reinterpret_cast<const float2*>(cring + scq * C::TILE + own_t);
-            const float2 uc = Qs[k - 1][R];
-            float2 zp[R + 1];
-#pragma unroll
-            for (int m = 0; m <= R; ++m)
-              zp[m] = (m == R / 2) ? uc : *reinterpret_cast<const float2*>(&pl[own - R + 2 * m]);
-            float2 lx = make_float2(0.f, 0.f), ly = lx, lz = lx;
-#pragma unroll
-            for (int d = 1; d <= R; ++d) {
-              const float2 yp = *reinterpret_cast<const float2*>(&pl[own + d * SW]);
-              const float2 ym = *reinterpret_cast<const float2*>(&pl[own - d * SW]);
-              float2 zpl, zmi;
-              if (d % 2 == 0) {
-                zpl = zp[R / 2 + d / 2];
-                zmi = zp[R / 2 - d / 2];
+        }
+        const float bxc = bxn;
+        bxn = __ldg(&P.damp_b[min(max(j + 1 - kl * R, 0), P.n0 - 1)]);
+        // u^n plane j+R, u^{n-1} and c2 plane j
+        ok = mbar_wait(bar_dat + (j - jstart) % C::ND, ((j - jstart) / C::ND) & 1, tmo);
+        if constexpr (T > 1) {
+          // centres and halo strips of this step, staged during the previous one;
+          // the phase also means every compute thread finished step j-1
+          if (j > jstart) ok = ok && mbar_wait(bar_ctr + (j & 1), ((j - jstart - 1) >> 1) & 1, tmo);
+        }
+        if (ok) {
+          const ST* ub = uring + su * C::PSLOT;
+          if constexpr (C::X0Q) {
+            int suR = su + R;
+            suR -= suR >= C::NU ? C::NU : 0;
+            qq[0][(i + 2 * R) % Q] = ldv<NPR>(uring + suR * C::PSLOT + own);
+          }
+          // ---- fused step 0
+          V un = fvzero<NPR>();
+          if (act0) {
+            const V uc = C::X0Q ? qq[0][(i + R) % Q] : ldv<NPR>(ub + own);
+            const V up = ldv<NPR>(pring + sp * C::TILE + own_t);
+            const V c2v = ldv<NPR>(cring + sc * C::TILE + own_t);
+            const V lap = laplacian(ub, uc, [&](int d) -> V {
+              if constexpr (C::X0Q) {
+                return qq[0][(i + R + d) % Q];
               } else {
-                zpl = make_float2(zp[R / 2 + (d - 1) / 2].y, zp[R / 2 + (d + 1) / 2].x);
-                zmi = make_float2(zp[R / 2 - (d + 1) / 2].y, zp[R / 2 - (d - 1) / 2].x);
+                int sf = su + d;
+                sf -= sf >= C::NU ? C::NU : 0;
+                sf += sf < 0 ? C::NU : 0;
+                return ldv<NPR>(uring + sf * C::PSLOT + own);
               }
-              lx = pair_term2(lx, P.w2[0][d - 1], Qs[k - 1][R + d], Qs[k - 1][R - d], uc);
-              ly = pair_term2(ly, P.w2[1][d - 1], yp, ym, uc);
-              lz = pair_term2(lz, P.w2[2][d - 1], zpl, zmi, uc);
-            }
-            const float2 lap = __fadd2_rn(__fadd2_rn(lx, ly), lz);
-            const float bx = __shfl_sync(0xffffffffu, bxc, k);
-            un = point_update2(uc, upv, lap, c2v, __fadd2_rn(make_float2(bx, bx), byz));
-            inject(k, q, un);
-          }
-        }
-        if (k + 1 < T) {
-          const int kq = k < T - 1 ? k : 0;  // queue of fused step k+1
-          // hand the new level to fused step k+1 ...
+            });
+            const float bx = __shfl_sync(0xffffffffu, bxc, 0);
+            if constexpr (SK != 0) {  // stored values are u / s: scale back (exact, s a power of two)
+              V ucs, ups, ls;
 #pragma unroll
-          for (int s = 0; s < C::Q - 1; ++s) Qs[kq][s] = Qs[kq][s + 1];
-          Qs[kq][C::Q - 1] = un;
-          // ... stage its centre for the next stream step ...
-          const int qn = j + 1 - (k + 1) * R;
-          if (qn >= pd.xc0 && qn < pd.xc1)
-            *reinterpret_cast<float2*>(wrbuf + (size_t)k * C::PSLOT + own) = Qs[kq][R + 1];
-          // ... and publish its halo strips for the neighbours
-          if (act && (strip_y >= 0 || strip_z >= 0)) {
-            int qd = jd - (k * R) % C::D;
-            qd += qd < 0 ? C::D : 0;
-            float* rs = rs_base + ((size_t)k * C::D + qd) * C::STRIP;
-            if (strip_y >= 0) __stcg(reinterpret_cast<float2*>(rs + strip_y), un);
-            if (strip_z >= 0) __stcg(reinterpret_cast<float2*>(rs + strip_z), un);
+              for (int p = 0; p < NPR; ++p) {
+                ucs.p[p] = __fmul2_rn(uc.p[p], sc2);
+                ups.p[p] = __fmul2_rn(up.p[p], sp2);
+                ls.p[p] = __fmul2_rn(lap.p[p], sc2);
+              }
+              un = update(ucs, ups, ls, c2v, bx, yz_free && bx == 0.f);
+            } else {
+              un = update(uc, up, lap, c2v, bx, yz_free && bx == 0.f);
+            }
+            if constexpr (T == 1) {
+              if (any_src) inject(0, j, un);
+            } else {
+              inject(0, j, un);
+            }
           }
-        } else if (act && own_row && q >= pd.xo0 && q < pd.xo1 && v0) {
-          __stcs(reinterpret_cast<float2*>(out0 + (size_t)q * ps + coff), un);
-          __stcs(reinterpret_cast<float2*>(out1 + (size_t)q * ps + coff), Qs[T - 2][R]);
+
+          if constexpr (T == 1) {
+            if (act0 && own_row && j >= pd.xo0 && j < pd.xo1 && vz) {
+              if constexpr (SK != 0) {
+                V sv;
+#pragma unroll
+                for (int p = 0; p < NPR; ++p) {
+                  vmax = fmaxf(vmax, fmaxf(fabsf(un.p[p].x), fabsf(un.p[p].y)));
+                  sv.p[p] = __fmul2_rn(un.p[p], io2);
+                }
+                stvcs<NPR>(reinterpret_cast<ST*>(out0) + (size_t)j * ps + coff, sv);
+              } else {
+                stvcs<NPR>(out0 + (size_t)j * ps + coff, un);
+              }
+            }
+          } else {
+            const float* rdbuf = splane + (size_t)(j & 1) * (T - 1) * C::PSLOT;
+            float* wrbuf = splane + (size_t)((j + 1) & 1) * (T - 1) * C::PSLOT;
+            bool act = act0;
+#pragma unroll
+            for (int k = 0; k < T; ++k) {
+              const int q = j - k * R;
+              if (k > 0) {
+                act = q >= pd.xc0 && q < pd.xc1;
+                un = fvzero<NPR>();
+                if (act) {
+                  const float* pl = rdbuf + (k - 1) * C::PSLOT;
+                  // u_prev of step k: level n+k-1 at plane q
+                  V upv;
+                  if (k == 1 && !C::X0Q) {
+                    int sq = su - R;
+                    sq += sq < 0 ? C::NU : 0;
+                    upv = ldv<NPR>(uring + sq * C::PSLOT + own);
+                  } else {
+                    upv = qq[QI(k - 1)][i % Q];
+                  }
+                  int scq = sc - k * R;
+                  scq += scq < 0 ? C::NC : 0;
+                  const V c2v = ldv<NPR>(cring + scq * C::TILE + own_t);
+                  const V uc = qq[QI(k)][(i + R) % Q];
+                  const V lap = laplacian(pl, uc, [&](int d) -> V { return qq[QI(k)][(i + R + d) % Q]; });
+                  const float bx = __shfl_sync(0xffffffffu, bxc, k);
+                  un = update(uc, upv, lap, c2v, bx, yz_free && bx == 0.f);
+                  inject(k, q, un);
+                }
+              }
+              if (k + 1 < T) {
+                // hand the new level to fused step k+1 ...
+                qq[QI(k + 1)][(i + 2 * R) % Q] = un;
+                // ... stage its centre for the next stream step ...
+                const int qn = j + 1 - (k + 1) * R;
+                if (qn >= pd.xc0 && qn < pd.xc1)
+                  stv<NPR>(wrbuf + (size_t)k * C::PSLOT + own, qq[QI(k + 1)][(i + R + 1) % Q]);
+                // ... and publish its halo strips for the neighbours
+                if (act && (strip_y >= 0 || strip_z >= 0)) {
+                  int qd = jd - (k * R) % C::D;
+                  qd += qd < 0 ? C::D : 0;
+                  float* rs = rs_base + ((size_t)k * C::D + qd) * C::STRIP;
+                  if (strip_y >= 0) stvcg<NPR>(rs + strip_y, un);
+                  if (strip_z >= 0) stvcg<NPR>(rs + strip_z, un);
+                }
+              } else if (act && own_row && q >= pd.xo0 && q < pd.xo1 && vz) {
+                stvcs<NPR>(out0 + (size_t)q * ps + coff, un);
+                stvcs<NPR>(out1 + (size_t)q * ps + coff, qq[QI(T - 1)][(i + R) % Q]);
+              }
+            }
+            mbar_arrive(bar_ctr + ((j + 1) & 1));
+          }
+          mbar_arrive(bar_done + (j - jstart) % C::NDONE);
+          if constexpr (!C::UNROLL) {  // the queues move one plane down
+#pragma unroll
+            for (int k = 0; k < NQ; ++k)
+#pragma unroll
+              for (int s2 = 0; s2 < Q - 1; ++s2) qq[k][s2] = qq[k][s2 + 1];
+          }
+          // advance the ring slots
+          su = su + 1 == C::NU ? 0 : su + 1;
+          sp = sp + 1 == C::NP ? 0 : sp + 1;
+          sc = sc + 1 == C::NC ? 0 : sc + 1;
+          jd = jd + 1 == C::D ? 0 : jd + 1;
         }
       }
-      mbar_arrive(bar_ctr + ((j + 1) & 1));
     }
-    mbar_arrive(bar_done + (j - jstart) % C::NDONE);
-    // advance the ring slots
-    su = su + 1 == C::NU ? 0 : su + 1;
-    sp = sp + 1 == C::NP ? 0 : sp + 1;
-    sc = sc + 1 == C::NC ? 0 : sc + 1;
-    jd = jd + 1 == C::D ? 0 : jd + 1;
   }
   if constexpr (SK != 0) {  // max |u^{n+1}| over the grid, for the next step's scale
 #pragma unroll
@@ -961,6 +1178,40 @@ __global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, T == 1 ? 2 :
     if (lane == 0 && vmax > 0.f) atomicMax(P.lp_mx + step0 + 2, __float_as_uint(vmax));
   }
   if (!ok) atomicExch(P.err, 2);
+}
+
+// two CTAs per SM for the one-step kernel where its register queue fits in
+// half the register file (r <= 4), else one
+template <int R, int T, int TY, int SK = 0, bool TWO = false, bool PRE = false>
+__global__ void __launch_bounds__(SweepCfg<R, T, TY, SK>::NTHREADS, (T == 1 && R <= 4) ? 2 : 1)
+    sweep_kernel(const __grid_constant__ SweepParams P) {
+  const int b = blockIdx.x;
+  int pi = 0;
+  for (int i = 1; i < P.npass; ++i)
+    if (P.pass[i].cta0 <= b) pi = i;
+  const PassDesc pd = P.pass[pi];
+  const bool s1 = TWO && b >= P.set1_cta0;
+  sweep_body<R, T, TY, SK, TWO, PRE>(P, pd, b, s1, s1 ? P.set[1].step0 : P.set[0].step0);
+}
+
+// One time step of several shots in one launch (the one-step sweep): the
+// launch's pass table concatenates the shots' passes, each naming its shot
+// and the launch at which the shot started, and the CTAs of a pass run the
+// sweep of that shot's step with the shot's parameters (fields, tensor
+// maps, tables), read from device memory: L.shots[2 s + parity of the step].
+template <int R>
+__global__ void __launch_bounds__(SweepCfg<R, 1, 16, 0>::NTHREADS, R <= 4 ? 2 : 1)
+    sweep_batch_kernel(const __grid_constant__ BatchParams L) {
+  const int b = blockIdx.x;
+  int lo = 0, hi = L.npass - 1;  // the last pass with cta0 <= b (sorted by cta0)
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (L.pass[mid].cta0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  const PassDesc pd = L.pass[lo];
+  const int step = L.step - pd.step_off;
+  sweep_body<R, 1, 16, 0, false, false>(L.shots[2 * pd.shot + (step & 1)], pd, b, false, step);
 }
 
 template <int R, int T, int SK = 0>
@@ -984,6 +1235,18 @@ cudaError_t sweep_launch_t(const SweepParams& p, int nctas, bool cooperative, cu
     void* args[] = {const_cast<SweepParams*>(&p)};
     return cudaLaunchCooperativeKernel((const void*)fn, dim3(nctas), dim3(Cf::NTHREADS), args, Cf::SMEM, st);
   }
+  fn<<<nctas, Cf::NTHREADS, Cf::SMEM, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t sweep_batch_launch_t(const BatchParams& p, int nctas, cudaStream_t st) {
+  using Cf = SweepCfg<R, 1, 16, 0>;
+  auto fn = sweep_batch_kernel<R>;
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
+  if (attr != cudaSuccess) return attr;
+  count_launch();
   fn<<<nctas, Cf::NTHREADS, Cf::SMEM, st>>>(p);
   return cudaGetLastError();
 }

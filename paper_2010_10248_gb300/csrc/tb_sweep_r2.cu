@@ -13,4 +13,7 @@ cudaError_t sweep_dispatch_r2(int what, int T, int sk, const SweepParams* p, int
   }
   return cudaErrorInvalidValue;
 }
+cudaError_t sweep_batch_dispatch_r2(const BatchParams* p, int nctas, cudaStream_t st) {
+  return sweep_batch_launch_t<2>(*p, nctas, st);
+}
 }  // namespace tbi

@@ -11,4 +11,7 @@ cudaError_t sweep_dispatch_r6(int what, int T, int sk, const SweepParams* p, int
   }
   return cudaErrorInvalidValue;
 }
+cudaError_t sweep_batch_dispatch_r6(const BatchParams* p, int nctas, cudaStream_t st) {
+  return sweep_batch_launch_t<6>(*p, nctas, st);
+}
 }  // namespace tbi

@@ -47,18 +47,27 @@ def constant_vp(shape, v: float) -> np.ndarray:
     return np.full(tuple(shape), v, dtype=np.float32)
 
 
+def _layers(n2, g, vmin, vmax, nlayers):
+    # interface depths: sorted seeded fractions of the depth axis
+    cuts = np.sort(g.uniform(0.05, 0.95, size=nlayers - 1)) * n2
+    vel = np.linspace(vmin, vmax, nlayers)
+    layer = np.searchsorted(cuts, np.arange(n2), side="right")
+    return vel[layer].astype(np.float32)
+
+
+def layered_profile(n2: int, seed: int, vmin: float = 1500.0, vmax: float = 4500.0, nlayers: int = 8) -> np.ndarray:
+    """The depth profile of layered_vp without perturbations (the model is
+    this profile along axis 2, the same at every (x, y))."""
+    return _layers(int(n2), rng(seed), vmin, vmax, nlayers)
+
+
 def layered_vp(shape, seed: int, vmin: float = 1500.0, vmax: float = 4500.0,
                nlayers: int = 8, nblobs: int = 16, blob_sigma=(20.0, 60.0),
                blob_amp: float = 0.05) -> np.ndarray:
     """Layered model along depth (axis 2) with smooth Gaussian perturbations."""
     n0, n1, n2 = (int(s) for s in shape)
     g = rng(seed)
-    # interface depths: sorted seeded fractions of the depth axis
-    cuts = np.sort(g.uniform(0.05, 0.95, size=nlayers - 1)) * n2
-    vel = np.linspace(vmin, vmax, nlayers)
-    z = np.arange(n2)
-    layer = np.searchsorted(cuts, z, side="right")
-    prof = vel[layer].astype(np.float32)
+    prof = _layers(n2, g, vmin, vmax, nlayers)
     vp = np.broadcast_to(prof[None, None, :], (n0, n1, n2)).copy()
     # sigma range is quoted for 512^3; scale it with the grid
     scale = min(n0, n1, n2) / 512.0

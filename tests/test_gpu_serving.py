@@ -47,8 +47,10 @@ def test_alone_and_in_the_mix_are_identical(serving):
         r0 = serving.ShotRequest(**{**r.__dict__, "arrival": 0.0})
         (res,) = solo.run([r0])
         alone[r.tag] = res.traces
-    mix = serving.ShotServer(slots=4)
+    # small FP32 shots go to batch lanes (one launch per step for all of them)
+    mix = serving.ShotServer(slots=4, batch_points=96 ** 3, batch_chunk=16)
     results = mix.run(reqs)
+    assert sum(ln["max_shots"] for ln in mix.stats["lanes"].values()) >= 2
     assert sorted(x.tag for x in results) == sorted(alone)
     for x in results:
         np.testing.assert_array_equal(x.traces, alone[x.tag])
@@ -68,3 +70,68 @@ def test_admission_respects_the_memory_budget(serving):
     too_big = serving.ShotServer(slots=2, memory_budget=big - 1)
     with pytest.raises(ValueError):
         too_big.run([max(reqs, key=serving.footprint_bytes)])
+
+
+def test_batched_shots_equal_alone_and_the_oracle(serving):
+    """Shots of different grids, lengths and geometries advanced together (one
+    launch per step for all of them), admitted at different steps: traces and
+    final wavefields bit-identical to each shot's one-step run alone, and the
+    first shot within the FP32 bar of the FP64 oracle."""
+    import torch
+
+    import oracle
+    import paper_2010_10248_gb300 as tb
+    g = np.random.default_rng(21)
+    cases = []
+    for shape, nt in (((40, 48, 70), 37), ((64, 64, 64), 60), ((33, 50, 90), 45)):
+        h = (10.0, 10.0, 10.0)
+        vp = wl.layered_vp(shape, int(g.integers(1000)), vmin=1600.0, vmax=3200.0, nlayers=3, nblobs=2)
+        ext = np.array([(shape[d] - 1) * h[d] for d in range(3)])
+        src = g.uniform(0.3, 0.7, size=(2, 3)) * ext
+        rec = np.concatenate([g.uniform(0.05, 0.95, size=(50, 3)) * ext, ext[None, :]])
+        dt = 0.8 * oracle.cfl_dt_max(8, h, float(vp.max()))
+        wav = np.repeat(wl.ricker(25.0, dt, nt, t0=5 * dt)[None, :], 2, axis=0).astype(np.float32)
+        cases.append((shape, h, vp, src, rec, dt, wav, nt))
+
+    def prop(c):
+        shape, h, vp, src, rec, dt, wav, nt = c
+        p = tb.Propagator(shape, h, 8, nbl=6)
+        p.set_model(torch.from_numpy(vp).cuda(), dt=dt)
+        p.set_sources(src, wav)
+        p.set_receivers(rec)
+        return p
+
+    alone = []
+    for c in cases:
+        p = prop(c)
+        tr = p.forward(c[7], schedule="onestep").clone()
+        alone.append((tr, p.field(0).clone(), p.field(1).clone()))
+        p.close()
+    st = torch.cuda.current_stream()
+    b = tb._tb.Batch(4)
+    props = [prop(c) for c in cases]
+    outs = [torch.full((c[7], len(c[4])), float("nan"), device="cuda") for c in cases]
+    b.add(props[0].h, cases[0][7], outs[0], st)
+    b.step(10, st)
+    b.add(props[1].h, cases[1][7], outs[1], st)
+    b.step(7, st)
+    b.add(props[2].h, cases[2][7], outs[2], st)
+    done = []
+    while b.active():
+        b.step(5, st)
+        done += b.finished()
+    torch.cuda.synchronize()
+    assert sorted(done) == sorted(p.h for p in props)
+    for p, o, (tr, u0, u1) in zip(props, outs, alone):
+        assert torch.equal(o, tr)
+        assert torch.equal(p.field(0), u0) and torch.equal(p.field(1), u1)
+        assert float(tr.abs().max()) > 0
+    shape, h, vp, src, rec, dt, wav, nt = cases[0]
+    tr_o, u_o, _ = oracle.acoustic_forward(shape, h, 8, dt, nt, vp.astype(np.float64), nbl=6, src_xyz=src,
+                                           src_wav=wav.astype(np.float64), rec_xyz=rec)
+    e_tr = np.linalg.norm(outs[0].cpu().numpy() - tr_o) / np.linalg.norm(tr_o)
+    e_u = np.linalg.norm(props[0].field(0).cpu().numpy() - u_o) / np.linalg.norm(u_o)
+    assert e_tr <= 1e-4 and e_u <= 1e-4, (e_tr, e_u)
+    for p in props:
+        p.close()
+    b.close()

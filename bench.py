@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--size", type=int, default=512, help="cube edge (512 = the benchmark)")
     ap.add_argument("--nt", type=int, default=1000)
     ap.add_argument("--time-tile", type=int, default=3)  # the fastest fused depth at 512^3 so8
+    ap.add_argument("--space-order", type=int, default=8, choices=[4, 8, 12],
+                    help="the benchmark model at another space order (the headline is so8)")
     ap.add_argument("--no-onestep", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -333,7 +335,7 @@ def run_native(args):
     tb.load()
     dev = torch.device("cuda", local)
 
-    w = wl.acoustic_512_so8(shape=(args.size,) * 3, nt=args.nt)
+    w = wl.acoustic_512_so8(shape=(args.size,) * 3, nt=args.nt, so=args.space_order)
     N = int(np.prod(w.shape))
     nt = w.nt
     vp_dev = torch.from_numpy(w.vp).to(dev)
@@ -480,7 +482,7 @@ def run_native(args):
         try:
             rate, secs, threads = cpu_oracle_rate(w, dt, 2, 2 + args.cpu_steps)
             cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-                   "sample": f"{w.shape[0]}^3 so8, {args.cpu_steps} steps (difference of a 2- "
+                   "sample": f"{w.shape[0]}^3 so{w.so}, {args.cpu_steps} steps (difference of a 2- "
                              f"and a {2 + args.cpu_steps}-step FP64 oracle run, {secs:.1f} s total)"}
         except Exception as e:  # the baseline is reported, not required
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
@@ -744,7 +746,7 @@ def run_storage(args):
         try:
             rate, secs, threads = cpu_oracle_rate(w, dt, 2, 2 + args.cpu_steps)
             cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-                   "sample": f"{w.shape[0]}^3 so8, {args.cpu_steps} steps (difference of a 2- "
+                   "sample": f"{w.shape[0]}^3 so{w.so}, {args.cpu_steps} steps (difference of a 2- "
                              f"and a {2 + args.cpu_steps}-step FP64 oracle run, {secs:.1f} s total)"}
         except Exception as e:  # the baseline is reported, not required
             cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {e}"}

@@ -180,12 +180,12 @@ def acoustic_64_so4(seed: int = BASE_SEED + 0) -> Workload:
 
 
 def acoustic_512_so8(seed: int = BASE_SEED + 1, shape=(512, 512, 512), nt: int = 1000,
-                     nbl: int = 40) -> Workload:
+                     nbl: int = 40, so: int = 8) -> Workload:
     """512^3, h = 10 m, so8, 1000 steps, 40-cell sponge, seeded layered vp
     1.5-4.5 km/s with Gaussian perturbations, one 15 Hz Ricker near the top,
     256 x 256 receiver plane (spacing 2h) at a fixed off-grid depth.
     ``shape`` / ``nt`` / ``nbl`` may be reduced for parity runs that keep
-    the same recipe."""
+    the same recipe; ``so`` selects another space order on the same model."""
     h = (10.0, 10.0, 10.0)
     g = rng(seed + 7)
     src = np.array([[(0.5 * (shape[0] - 1) + g.uniform(-0.5, 0.5)) * h[0],
@@ -197,8 +197,8 @@ def acoustic_512_so8(seed: int = BASE_SEED + 1, shape=(512, 512, 512), nt: int =
     nry = min(256, shape[1] // 2)
     rec = receiver_plane(shape, h, seed + 3, nrx, nry, depth_cells=nbl + 20)
     vp = layered_vp(shape, seed + 4)
-    return Workload(f"acoustic {shape[0]}x{shape[1]}x{shape[2]} so8 {nt} steps", tuple(shape), h,
-                    8, nt, nbl, 15.0, vp, src, rec)
+    return Workload(f"acoustic {shape[0]}x{shape[1]}x{shape[2]} so{so} {nt} steps", tuple(shape), h,
+                    so, nt, nbl, 15.0, vp, src, rec)
 
 
 def smooth_field(shape, seed: int, lo: float, hi: float, coarse: int = 6) -> np.ndarray:

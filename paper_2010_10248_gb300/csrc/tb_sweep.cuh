@@ -160,7 +160,9 @@ struct SweepCfg {
   static constexpr int NBAR = 1 + ND + 2 + NDONE;    // prologue, data, centre[2], done
   static constexpr size_t SMEM = OFF_BAR + 8 * NBAR + 128;    // + base alignment
   static_assert(R % 2 == 0, "radius must be even for aligned float2 access");
-  static_assert(TY % 2 == 0 && TY >= R && TZ >= RP, "a halo must come from one neighbour tile");
+  // a halo comes from one neighbour tile, and the top and bottom strips a tile
+  // publishes (its first and last r rows) must not overlap
+  static_assert(TY % 2 == 0 && TY >= 2 * R && TZ >= RP, "tile too small for the stencil radius");
   static_assert(SMEM <= 232448, "shared memory budget exceeded");
 };
 

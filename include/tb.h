@@ -89,7 +89,8 @@ typedef struct {
   int time_tile;   /* T: time steps fused per blocked sweep (Sec. II-B).
                       Supported: 1..4 (space order 4, 8), 1..2 (space order 12);
                       0 -> the fastest measured on GB300 at 512^3: 4 (space
-                      order 4), 3 (8), 2 (12).  TB_TTI, TB_ELASTIC: 0 or 1.  */
+                      order 4), 3 (8), 2 (12).  TB_TTI, TB_ELASTIC: 1..8
+                      steps per wavefront (below); 0 -> 4.                    */
   int nbl;         /* width in cells of the built-in sponge (Sec. IV-B); 0: none  */
   int y_bands;     /* blocked sweep: number of bands along axis 1, each time
                       tile split the same way; 0 -> bands pipelined across time
@@ -111,6 +112,9 @@ typedef struct {
                       max|source step n|)) - 8), set on the device each step     */
   int band_ctas;   /* pipelined blocked sweep: most CTAs per launch; 0 -> every
                       CTA that fits co-resident on the GPU (one per SM)          */
+  int slab_planes; /* TB_TTI / TB_ELASTIC blocked sweep: planes per slab of the
+                      wavefront along axis 0, >= space_order / 2 (else
+                      TB_EINVAL); 0 -> 32                                       */
 } tb_options;
 
 /* Create a propagator for a grid of shape n[3] with spacing h[3] (metres),
@@ -173,8 +177,13 @@ int tb_set_receivers(tb_handle* h, int nrec, const double* coords, void* stream)
  * NULL).  schedule: TB_ONESTEP (one launch per time step, spatial blocking
  * only) or TB_BLOCKED (opt.time_tile steps fused per sweep, Sec. II-B).
  * Both give bitwise-identical wavefields and traces.  TB_TTI and
- * TB_ELASTIC: TB_ONESTEP only (TB_BLOCKED gives TB_EINVAL); traces sample p
- * (TTI) or the mean normal stress at n+1 (elastic).  Source tables scale:
+ * TB_ELASTIC: each step is two sub-updates (TTI: fluxes, then divergence
+ * and leapfrog update; elastic: velocity, then stress, Fig. 7b); TB_BLOCKED
+ * runs opt.time_tile steps as one wavefront over slabs of opt.slab_planes
+ * planes along axis 0, sub-update u of slab s in launch s + 2u (the nt mod
+ * time_tile remaining steps one step per launch); traces sample p (TTI) or
+ * the mean normal stress at n+1 (elastic).  16-bit and plain storage:
+ * TB_ONESTEP only (TB_EINVAL).  Source tables scale:
  * dt^2/m (acoustic, TTI), dt (elastic).  nt must not exceed the
  * wavelet length given to tb_set_sources (when sources are set).
  * Device traces: asynchronous on `stream`.  Host traces: synchronous.
@@ -242,6 +251,15 @@ int tb_source_event_layout(int64_t npts, const int64_t* lin, int64_t n1, int64_t
  * for one band of the grid. */
 int tb_plan_pipeline(int n1, int n2, int space_order, int time_tile, int n_tiles, int cap, int* passes,
                      int max_passes);
+
+/* Host-side planner of the TTI / elastic wavefront (tb_forward with
+ * TB_BLOCKED, Sec. II-B): n0 planes along axis 0 in slabs of `slab` planes,
+ * `n_sub` sub-updates (2 per fused step).  Writes up to max_items items of 4
+ * ints (launch, sub-update u, first plane, end plane) into items (may be
+ * NULL to count), launches ascending; sub-update u of slab s is in launch
+ * s + 2u.  Returns the number of items, or -TB_EINVAL for n0 < 1, slab < 1,
+ * n_sub < 1 or too small a buffer. */
+int tb_plan_wavefront(int n0, int slab, int n_sub, int* items, int max_items);
 
 /* With opt.profile = 1: number of propagator launches of the last
  * tb_forward and their summed device time in ms, measured with CUDA events

@@ -15,7 +15,8 @@ from ._tb import (TB_ACOUSTIC, TB_BF16, TB_BLOCKED, TB_ELASTIC, TB_F16, TB_F32, 
                   tb_create, tb_destroy, tb_fd_weights, tb_forward, tb_get_dt, tb_get_field,
                   tb_get_receiver_points, tb_get_source_points, tb_kernel_time, tb_last_error,
                   tb_launch_count, tb_measure_peaks, tb_ricker, tb_selftest_wait, tb_set_model, tb_set_receivers, tb_set_sources,
-                  tb_plan_pipeline, tb_source_event_layout, tb_sponge_profile, tb_workspace_bytes)
+                  tb_plan_pipeline, tb_plan_wavefront, tb_source_event_layout, tb_sponge_profile,
+                  tb_workspace_bytes)
 
 __all__ = ["Propagator", "Options", "TBError", "load", "TB_ONESTEP", "TB_BLOCKED", "TB_ACOUSTIC",
            "TB_TTI", "TB_ELASTIC", "tb_tti_dt_max", "tb_elastic_dt_max", "tb_adjoint_gradient",
@@ -26,7 +27,7 @@ __all__ = ["Propagator", "Options", "TBError", "load", "TB_ONESTEP", "TB_BLOCKED
            "tb_set_receivers", "tb_forward", "tb_get_field", "tb_get_source_points",
            "tb_get_receiver_points", "tb_workspace_bytes", "tb_kernel_time", "tb_last_error",
            "tb_fd_weights", "tb_cfl_dt_max", "tb_sponge_profile", "tb_ricker", "tb_selftest_wait", "tb_measure_peaks",
-           "tb_launch_count", "tb_plan_pipeline", "tb_source_event_layout"]
+           "tb_launch_count", "tb_plan_pipeline", "tb_plan_wavefront", "tb_source_event_layout"]
 
 
 class Propagator:
@@ -39,12 +40,13 @@ class Propagator:
 
     def __init__(self, shape, spacing, space_order, *, physics=TB_ACOUSTIC, time_tile=0, nbl=0,
                  y_bands=0, x_chunks=0, profile=False, check_nan=False, wait_timeout_s=0.0,
-                 storage=TB_F32, band_ctas=0):
+                 storage=TB_F32, band_ctas=0, slab_planes=0):
         import torch
         self._torch = torch
         opt = Options(time_tile=time_tile, nbl=nbl, y_bands=y_bands, x_chunks=x_chunks,
                       profile=int(profile), check_nan=int(check_nan),
-                      wait_timeout_s=float(wait_timeout_s), storage=int(storage), band_ctas=int(band_ctas))
+                      wait_timeout_s=float(wait_timeout_s), storage=int(storage), band_ctas=int(band_ctas),
+                      slab_planes=int(slab_planes))
         self.shape = tuple(int(s) for s in shape)
         self.spacing = tuple(float(s) for s in spacing)
         self.space_order = int(space_order)
@@ -104,8 +106,9 @@ class Propagator:
         return self
 
     def forward(self, nt, traces=None, schedule=None):
-        """schedule: "blocked" (default for acoustic) or "onestep" (the only
-        one for TTI and elastic)."""
+        """schedule: "blocked" (time_tile steps fused per sweep; the default
+        for FP32 acoustic) or "onestep" (the default for TTI, elastic and
+        16-bit storage; 16-bit storage runs nothing else)."""
         torch = self._torch
         if schedule is None:
             schedule = "blocked" if self.physics == TB_ACOUSTIC and self.storage == TB_F32 else "onestep"

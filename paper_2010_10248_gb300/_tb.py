@@ -35,7 +35,8 @@ class TBError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("time_tile", C.c_int), ("nbl", C.c_int), ("y_bands", C.c_int),
                 ("x_chunks", C.c_int), ("profile", C.c_int), ("check_nan", C.c_int),
-                ("wait_timeout_s", C.c_double), ("storage", C.c_int), ("band_ctas", C.c_int)]
+                ("wait_timeout_s", C.c_double), ("storage", C.c_int), ("band_ctas", C.c_int),
+                ("slab_planes", C.c_int)]
 
 
 _lib = None
@@ -80,6 +81,7 @@ _SIGS = {
     "tb_launch_count": (C.c_uint64, []),
     "tb_plan_pipeline": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                    C.POINTER(C.c_int), C.c_int]),
+    "tb_plan_wavefront": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "tb_source_event_layout": (C.c_int, [C.c_int64, _vp, C.c_int64, C.c_int64, _vp, _vp,
                                          C.POINTER(C.c_int64)]),
     "tb_inspect_points_noalloc": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int,
@@ -232,6 +234,19 @@ def tb_plan_pipeline(n1, n2, space_order, time_tile, n_tiles, cap):
     out = np.zeros((max(n, 1), 7), dtype=np.int32)
     lib.tb_plan_pipeline(int(n1), int(n2), int(space_order), int(time_tile), int(n_tiles), int(cap),
                          out.ctypes.data_as(C.POINTER(C.c_int)), n)
+    return out[:n]
+
+
+def tb_plan_wavefront(n0, slab, n_sub):
+    """The TTI / elastic wavefront's items as an int array [nitem, 4]: launch,
+    sub-update, first plane, end plane (host only, no GPU)."""
+    import numpy as np
+    lib = load()
+    n = lib.tb_plan_wavefront(int(n0), int(slab), int(n_sub), None, 0)
+    if n < 0:
+        raise TBError(-n, "tb_plan_wavefront: invalid arguments")
+    out = np.zeros((max(n, 1), 4), dtype=np.int32)
+    lib.tb_plan_wavefront(int(n0), int(slab), int(n_sub), out.ctypes.data_as(C.POINTER(C.c_int)), n)
     return out[:n]
 
 

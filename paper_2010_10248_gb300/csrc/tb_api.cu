@@ -442,14 +442,18 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
     delete h;
     return TB_EINVAL;
   }
-  // more fused so12 steps exceed shared memory; TTI and elastic run one step per launch
-  const int tmax = (physics != TB_ACOUSTIC || h->storage != TB_F32) ? 1 : (so == 12 ? 2 : 4);
+  // more fused so12 steps exceed shared memory; 16-bit and plain storage run
+  // one step per launch; the TTI / elastic wavefront takes up to 8 steps
+  const int tmax = physics != TB_ACOUSTIC ? 8 : (h->storage != TB_F32 ? 1 : (so == 12 ? 2 : 4));
   // default: the fused depth measured fastest at 512^3 (so8: T = 3 computes
   // each level faster than T = 4, whose three register queues crowd the
-  // registers)
-  if (h->opt.time_tile == 0) h->opt.time_tile = (tmax > 1 && so == 8) ? 3 : tmax;
+  // registers); TTI / elastic: 4 (at 384^3 so8 the wavefront costs least
+  // per step at T = 4 among 2, 3, 4)
+  if (h->opt.time_tile == 0)
+    h->opt.time_tile = physics != TB_ACOUSTIC ? 4 : ((tmax > 1 && so == 8) ? 3 : tmax);
   if (h->opt.time_tile < 1 || h->opt.time_tile > tmax || h->opt.nbl < 0 || h->opt.y_bands < 0 ||
-      h->opt.x_chunks < 0 || h->opt.band_ctas < 0) {
+      h->opt.x_chunks < 0 || h->opt.band_ctas < 0 || h->opt.slab_planes < 0 ||
+      (h->opt.slab_planes > 0 && h->opt.slab_planes < so / 2)) {
     delete h;
     return TB_EINVAL;
   }
@@ -1012,6 +1016,17 @@ static int plan_pipeline(tb_handle* h, int T, int K, Plan* pl) {
   return TB_OK;
 }
 
+extern "C" int tb_plan_wavefront(int n0, int slab, int n_sub, int* items, int max_items) {
+  std::vector<int> v;
+  if (wave_plan(n0, slab, n_sub, &v) != 0) return -TB_EINVAL;
+  const int n = (int)(v.size() / 4);
+  if (items) {
+    if (max_items < n) return -TB_EINVAL;
+    std::copy(v.begin(), v.end(), items);
+  }
+  return n;
+}
+
 extern "C" int tb_plan_pipeline(int n1, int n2, int space_order, int time_tile, int n_tiles, int cap, int* passes,
                                 int max_passes) {
   const int R = space_order / 2;
@@ -1134,7 +1149,7 @@ static int ensure_scales(tb_handle* h, int nt, cudaStream_t st) {
   return TB_OK;
 }
 
-static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
+static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cudaStream_t st) {
   const int nrec = h->have_rec ? h->rec.npt : 0;
   const bool rec_on = h->have_rec && h->rec.npts > 0 && nrec > 0 && traces;
   const bool host_traces = traces && nrec > 0 && !is_device_ptr(traces);
@@ -1199,7 +1214,92 @@ static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
     fill = 0;
     return TB_OK;
   };
-  for (int n = 0; n < nt; ++n) {
+  // TTI / elastic blocked: T steps per wavefront over slabs of axis 0 (the
+  // nt mod T remaining steps one step per launch)
+  const int T = (!lowp && schedule == TB_BLOCKED) ? h->opt.time_tile : 1;
+  // 32-plane slabs: measured fastest at 384^3 among 4 .. 64 (thin slabs
+  // re-read 2r planes per slab to fill their register queues)
+  const int slab = h->opt.slab_planes > 0 ? h->opt.slab_planes : 32;
+  const bool src_on = h->have_src && h->src.npts > 0;
+  std::vector<int> plan;
+  if (T > 1 && wave_plan((int)h->n[0], slab, 2 * T, &plan) != 0) return fail(h, TB_EINVAL, "bad wavefront");
+  for (int n = 0; n < nt;) {
+    if (T > 1 && nt - n >= T) {
+      if (rec_on && fill + T > h->rec_cap) {
+        int s = flush();
+        if (s != TB_OK) return s;
+      }
+      // level k of the block: TTI fields p^{n+k} and p^{n+k-1} (their roles
+      // alternate with k), elastic fields in place
+      int pcur[2] = {pc, pp}, rcur[2] = {rc, rp};
+      WaveItems L{};
+      WavePosts P{};
+      for (size_t i = 0; i < plan.size(); i += 4) {
+        const int u = plan[i + 1], k = u / 2;
+        WaveItem& it = L.it[L.n++];
+        it.kind = u & 1;
+        it.x0 = plan[i + 2];
+        it.x1 = plan[i + 3];
+        if (h->physics == TB_TTI) {
+          it.a = h->field[pcur[k & 1]];
+          it.b = h->field[pcur[(k + 1) & 1]];
+          it.c = h->field[rcur[k & 1]];
+          it.d = h->field[rcur[(k + 1) & 1]];
+        }
+        if (it.kind == 1 && (src_on || rec_on)) {
+          WavePost& q = P.it[P.n++];
+          q.x0 = it.x0;
+          q.x1 = it.x1;
+          if (src_on) q.dcmp = h->src_dcmp + (size_t)(n + k) * h->src.npts;
+          if (h->physics == TB_TTI) {
+            q.f0 = it.b;  // p^{n+k+1}, r^{n+k+1}
+            q.f1 = it.d;
+            q.s0 = it.b;
+          } else {
+            q.f0 = h->efield + 3 * Np;
+            q.f1 = h->efield + 4 * Np;
+            q.f2 = h->efield + 5 * Np;
+            q.s0 = q.f0;
+            q.s1 = q.f1;
+            q.s2 = q.f2;
+          }
+          if (rec_on) q.row = h->rec_dcmp + (size_t)(fill + k) * h->rec.npts;
+        }
+        const bool last = i + 4 == plan.size() || plan[i + 4] != plan[i];
+        if (!last) continue;
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (h->opt.profile) {
+          ea = ev_next(h);
+          eb = ev_next(h);
+          h->ev_kind.push_back(0);
+          if (ea) cudaEventRecord(ea, st);
+        }
+        cudaError_t e = wave_launch(h->physics, h->R, g, w, (float)h->dt, L, h->c2, h->coef, h->nzb, h->damp_b,
+                                    h->flux, h->efield, h->emat, h->eta_dt, st);
+        if (h->opt.profile && eb) cudaEventRecord(eb, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "wavefront launch");
+        if (P.n > 0) {
+          e = wave_post(g, P, src_on ? h->src.npts : 0, h->src.lin, rec_on ? h->rec.npts : 0, h->rec.ent, h->rec.lin,
+                        st);
+          if (e != cudaSuccess) return cuda_fail(h, e, "wavefront injection / sampling");
+        }
+        L.n = 0;
+        P.n = 0;
+      }
+      if (T & 1) {
+        std::swap(pc, pp);
+        std::swap(rc, rp);
+      }
+      n += T;
+      if (rec_on) {
+        fill += T;
+        if (fill == h->rec_cap) {
+          int s = flush();
+          if (s != TB_OK) return s;
+        }
+      }
+      continue;
+    }
     cudaEvent_t ea = nullptr, eb = nullptr;
     if (h->opt.profile) {
       ea = ev_next(h);
@@ -1231,6 +1331,7 @@ static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
           if (s != TB_OK) return s;
         }
       }
+      ++n;
       continue;
     }
     if (h->physics == TB_TTI) {
@@ -1263,6 +1364,7 @@ static int forward_other(tb_handle* h, int nt, float* traces, cudaStream_t st) {
         if (s != TB_OK) return s;
       }
     }
+    ++n;
   }
   int s = flush();
   if (s != TB_OK) return s;
@@ -1293,12 +1395,13 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
     return fail(h, TB_EINVAL, "nt = %d exceeds the wavelet length %d", nt, h->src_nt);
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
-  if (h->physics != TB_ACOUSTIC || h->storage != TB_F32) {
+  if (h->physics != TB_ACOUSTIC) return forward_other(h, nt, traces, schedule, st);
+  if (h->storage != TB_F32) {
     if (schedule != TB_ONESTEP)
-      return fail(h, TB_EINVAL, "the blocked schedule is implemented for the FP32 acoustic equation only");
-    // FP16 / BF16 storage runs the one-step sweep below; TTI, elastic and
-    // plain-FP32 storage run their streaming kernels
-    if (!h->sk) return forward_other(h, nt, traces, st);
+      return fail(h, TB_EINVAL, "16-bit and plain storage run one step per launch (TB_ONESTEP)");
+    // FP16 / BF16 storage runs the one-step sweep below; plain-FP32 storage
+    // its streaming kernel
+    if (!h->sk) return forward_other(h, nt, traces, schedule, st);
   }
   const int nrec = h->have_rec ? h->rec.npt : 0;
   const bool host_traces = traces && nrec > 0 && !is_device_ptr(traces);

@@ -152,6 +152,42 @@ cudaError_t tti_coefficients(const PhysGrid& g, const float* aux, float* coef, f
                              int* d_bad, cudaStream_t st);
 cudaError_t elastic_step(int R, const PhysGrid& g, const DerivW& w, float dt, int nchunks, float* f, const float* mat,
                          const float* eta_dt, cudaStream_t st);
+// Wavefront schedule of the TTI / elastic sub-updates (tb_physics.cu): the
+// (sub-update, slab) items of one launch, and the injection / sampling of the
+// steps whose last sub-update finished a slab in it.
+constexpr int kWaveItemsMax = 16;  // 2 x the deepest time tile (8)
+constexpr int kWavePostsMax = 8;
+struct WaveItem {
+  int kind;   // 0: TTI flux / elastic velocity; 1: TTI update / elastic stress
+  int x0, x1;  // planes of the slab
+  const float* a;  // TTI: p^n (kind 0 and 1)
+  float* b;        // TTI: p^{n-1}, overwritten by p^{n+1} (kind 1)
+  const float* c;  // TTI: r^n
+  float* d;        // TTI: r^{n-1}, overwritten by r^{n+1}
+};
+struct WaveItems {
+  int n;
+  WaveItem it[kWaveItemsMax];
+};
+struct WavePost {
+  int x0, x1;
+  const float* dcmp;    // the step's injection table row (unused without sources)
+  float *f0, *f1, *f2;  // injected fields (TTI: p, r; elastic: txx, tyy, tzz)
+  float* row;           // the step's receiver row (unused without receivers)
+  const float *s0, *s1, *s2;  // sampled: s0 (TTI: p), or the mean of s0..s2 (elastic)
+};
+struct WavePosts {
+  int n;
+  WavePost it[kWavePostsMax];
+};
+cudaError_t wave_launch(int physics, int R, const PhysGrid& g, const DerivW& w, float dt, const WaveItems& L,
+                        const float* c2, const float* coef, const float* nz, const float* damp_b, float* flux,
+                        float* ef, const float* mat, const float* eta_dt, cudaStream_t st);
+cudaError_t wave_post(const PhysGrid& g, const WavePosts& P, int64_t nsrc_pts, const int64_t* src_lin,
+                      int64_t nrec_pts, const int2* rec_ent, const int64_t* rec_lin, cudaStream_t st);
+// items (launch, sub-update, x0, x1) of the wavefront over n0 planes in slabs
+// of `slab` planes for U sub-updates, launches in order; -1 on bad arguments
+int wave_plan(int n0, int slab, int U, std::vector<int>* items);
 cudaError_t elastic_material(const PhysGrid& g, const float* vp, const float* vs, const float* rho, float* mat,
                              int* d_bad, cudaStream_t st);
 cudaError_t inject_points(const PhysGrid& g, int64_t npts, const int64_t* lin, const float* dcmp_row, float* f0,

@@ -23,6 +23,7 @@
 // axis-1 and axis-2 neighbours come through the L1 cache.  Source injection
 // (grid-aligned table of Sec. II-A) and receiver sampling are separate small
 // kernels after the update of each step.
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 
@@ -96,19 +97,16 @@ __device__ __forceinline__ float dc_q(const float* q, const float* a) {  // q[R]
 }
 
 // pass 1: F = grad p - zbar (zbar . grad p), G = zbar (zbar . grad r) on
-// planes [x0, x1) of every column
+// planes [x0, x1) of column c.  Reads p, r on planes x0 - R .. x1 - 1 + R.
 template <int R>
-__global__ void __launch_bounds__(256) k_tti_flux(PhysGrid g, DerivW w, int nchunks, const float* __restrict__ p,
-                                                  const float* __restrict__ r, const float* __restrict__ nz,
-                                                  float* __restrict__ flux) {
-  const Col c = thread_col(g);
-  if (!c.ok) return;
-  int x0, x1;
-  chunk_planes(g, nchunks, x0, x1);
+__device__ __forceinline__ void tti_flux_cols(const PhysGrid& g, const DerivW& w, const Col& c, int x0, int x1,
+                                              const float* __restrict__ p, const float* __restrict__ r,
+                                              const float* __restrict__ nz, float* __restrict__ flux) {
   const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
   float qp[2 * R + 1], qr[2 * R + 1];
+  qp[0] = qr[0] = 0.f;  // shifted out before its first use
 #pragma unroll
-  for (int s = 0; s < 2 * R + 1; ++s) {  // planes x0-1-R .. x0-1+R before the first shift
+  for (int s = 1; s < 2 * R + 1; ++s) {  // planes x0-R .. x0+R-1 before the first shift
     qp[s] = ld0(g, p, x0 - 1 - R + s, c.y, c.z);
     qr[s] = ld0(g, r, x0 - 1 - R + s, c.y, c.z);
   }
@@ -136,24 +134,32 @@ __global__ void __launch_bounds__(256) k_tti_flux(PhysGrid g, DerivW w, int nchu
     flux[5 * Np + i0] = __fmul_rn(n2, sr);
   }
 }
-
-// pass 2: H_h p = div F, H_z r = div G; leapfrog update of p and r written
-// over p^{n-1}, r^{n-1}
 template <int R>
-__global__ void __launch_bounds__(256) k_tti_update(PhysGrid g, DerivW w, int nchunks, const float* __restrict__ flux,
-                                                    const float* __restrict__ pc, float* pp, const float* __restrict__ rc,
-                                                    float* rp, const float* __restrict__ c2,
-                                                    const float* __restrict__ coef, const float* __restrict__ damp_b) {
+__global__ void __launch_bounds__(256) k_tti_flux(PhysGrid g, DerivW w, int nchunks, const float* __restrict__ p,
+                                                  const float* __restrict__ r, const float* __restrict__ nz,
+                                                  float* __restrict__ flux) {
   const Col c = thread_col(g);
   if (!c.ok) return;
   int x0, x1;
   chunk_planes(g, nchunks, x0, x1);
+  tti_flux_cols<R>(g, w, c, x0, x1, p, r, nz, flux);
+}
+
+// pass 2: H_h p = div F, H_z r = div G; leapfrog update of p and r written
+// over p^{n-1}, r^{n-1} on planes [x0, x1) of column c.  Reads the fluxes on
+// planes x0 - R .. x1 - 1 + R.
+template <int R>
+__device__ __forceinline__ void tti_update_cols(const PhysGrid& g, const DerivW& w, const Col& c, int x0, int x1,
+                                                const float* __restrict__ flux, const float* __restrict__ pc, float* pp,
+                                                const float* __restrict__ rc, float* rp, const float* __restrict__ c2,
+                                                const float* __restrict__ coef, const float* __restrict__ damp_b) {
   const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
   const float* F0 = flux;
   const float* G0 = flux + 3 * Np;
   float qf[2 * R + 1], qg[2 * R + 1];
+  qf[0] = qg[0] = 0.f;
 #pragma unroll
-  for (int s = 0; s < 2 * R + 1; ++s) {
+  for (int s = 1; s < 2 * R + 1; ++s) {
     qf[s] = ld0(g, F0, x0 - 1 - R + s, c.y, c.z);
     qg[s] = ld0(g, G0, x0 - 1 - R + s, c.y, c.z);
   }
@@ -181,6 +187,17 @@ __global__ void __launch_bounds__(256) k_tti_update(PhysGrid g, DerivW w, int nc
     pp[i0] = __fadd_rn(up, div_sponge(__fmaf_rn(c2v, rhs_p, __fmul_rn(omg, __fsub_rn(up, upp))), opg));
     rp[i0] = __fadd_rn(ur, div_sponge(__fmaf_rn(c2v, rhs_r, __fmul_rn(omg, __fsub_rn(ur, urp))), opg));
   }
+}
+template <int R>
+__global__ void __launch_bounds__(256) k_tti_update(PhysGrid g, DerivW w, int nchunks, const float* __restrict__ flux,
+                                                    const float* __restrict__ pc, float* pp, const float* __restrict__ rc,
+                                                    float* rp, const float* __restrict__ c2,
+                                                    const float* __restrict__ coef, const float* __restrict__ damp_b) {
+  const Col c = thread_col(g);
+  if (!c.ok) return;
+  int x0, x1;
+  chunk_planes(g, nchunks, x0, x1);
+  tti_update_cols<R>(g, w, c, x0, x1, flux, pc, pp, rc, rp, c2, coef, damp_b);
 }
 
 // ------------------------------------------------------------- elastic --
@@ -218,19 +235,19 @@ __device__ __forceinline__ float dstag_q(const float* q, const float* cw, bool p
 // Each thread streams its column through the planes of one chunk; the axis-0
 // neighbours of the three fields it differentiates along axis 0 sit in
 // register queues of planes x-R .. x+R.
+// velocity update on planes [x0, x1) of column c; reads the stresses on
+// planes x0 - R .. x1 - 1 + R
 template <int R>
-__global__ void __launch_bounds__(256, 4) k_ela_velocity(PhysGrid g, DerivW w, float dt, int nchunks, float* __restrict__ f,
-                                                      const float* __restrict__ mat, const float* __restrict__ eta_dt) {
-  const Col c = thread_col(g);
-  if (!c.ok) return;
-  int x0, x1;
-  chunk_planes(g, nchunks, x0, x1);
+__device__ __forceinline__ void ela_velocity_cols(const PhysGrid& g, const DerivW& w, const Col& c, float dt, int x0,
+                                                  int x1, float* __restrict__ f, const float* __restrict__ mat,
+                                                  const float* __restrict__ eta_dt) {
   const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
   const float *txx = f + 3 * Np, *tyy = f + 4 * Np, *tzz = f + 5 * Np, *txy = f + 6 * Np, *txz = f + 7 * Np,
               *tyz = f + 8 * Np;
   float qa[2 * R + 1], qb[2 * R + 1], qc[2 * R + 1];  // txx, txy, txz
+  qa[0] = qb[0] = qc[0] = 0.f;
 #pragma unroll
-  for (int s = 0; s < 2 * R + 1; ++s) {
+  for (int s = 1; s < 2 * R + 1; ++s) {
     qa[s] = ld0(g, txx, x0 - 1 - R + s, c.y, c.z);
     qb[s] = ld0(g, txy, x0 - 1 - R + s, c.y, c.z);
     qc[s] = ld0(g, txz, x0 - 1 - R + s, c.y, c.z);
@@ -259,19 +276,28 @@ __global__ void __launch_bounds__(256, 4) k_ela_velocity(PhysGrid g, DerivW w, f
     f[2 * Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 2 * Np + i0)), fz, f[2 * Np + i0]), den);
   }
 }
-
 template <int R>
-__global__ void __launch_bounds__(256, 4) k_ela_stress(PhysGrid g, DerivW w, float dt, int nchunks, float* __restrict__ f,
-                                                    const float* __restrict__ mat, const float* __restrict__ eta_dt) {
+__global__ void __launch_bounds__(256, 4) k_ela_velocity(PhysGrid g, DerivW w, float dt, int nchunks, float* __restrict__ f,
+                                                      const float* __restrict__ mat, const float* __restrict__ eta_dt) {
   const Col c = thread_col(g);
   if (!c.ok) return;
   int x0, x1;
   chunk_planes(g, nchunks, x0, x1);
+  ela_velocity_cols<R>(g, w, c, dt, x0, x1, f, mat, eta_dt);
+}
+
+// stress update on planes [x0, x1) of column c; reads the velocities on
+// planes x0 - R .. x1 - 1 + R
+template <int R>
+__device__ __forceinline__ void ela_stress_cols(const PhysGrid& g, const DerivW& w, const Col& c, float dt, int x0,
+                                                int x1, float* __restrict__ f, const float* __restrict__ mat,
+                                                const float* __restrict__ eta_dt) {
   const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
   const float *vx = f, *vy = f + Np, *vz = f + 2 * Np;
   float qa[2 * R + 1], qb[2 * R + 1], qc[2 * R + 1];  // vx, vy, vz
+  qa[0] = qb[0] = qc[0] = 0.f;
 #pragma unroll
-  for (int s = 0; s < 2 * R + 1; ++s) {
+  for (int s = 1; s < 2 * R + 1; ++s) {
     qa[s] = ld0(g, vx, x0 - 1 - R + s, c.y, c.z);
     qb[s] = ld0(g, vy, x0 - 1 - R + s, c.y, c.z);
     qc[s] = ld0(g, vz, x0 - 1 - R + s, c.y, c.z);
@@ -305,6 +331,15 @@ __global__ void __launch_bounds__(256, 4) k_ela_stress(PhysGrid g, DerivW w, flo
     f[7 * Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 6 * Np + i0)), gxz, f[7 * Np + i0]), den);
     f[8 * Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, __ldg(mat + 7 * Np + i0)), gyz, f[8 * Np + i0]), den);
   }
+}
+template <int R>
+__global__ void __launch_bounds__(256, 4) k_ela_stress(PhysGrid g, DerivW w, float dt, int nchunks, float* __restrict__ f,
+                                                    const float* __restrict__ mat, const float* __restrict__ eta_dt) {
+  const Col c = thread_col(g);
+  if (!c.ok) return;
+  int x0, x1;
+  chunk_planes(g, nchunks, x0, x1);
+  ela_stress_cols<R>(g, w, c, dt, x0, x1, f, mat, eta_dt);
 }
 
 // material at the staggered positions from vp, vs, rho (dense [N]):
@@ -392,6 +427,73 @@ __global__ void k_sample(PhysGrid g, int64_t npts, const int2* __restrict__ ent,
   row[e] = v;
 }
 
+// ------------------------------------------------- wavefront sweeps --
+// Temporal blocking of the two-pass steps (Sec. II-B, Fig. 7b): T steps are
+// 2T sub-updates (TTI: flux, update; elastic: velocity, stress), each
+// reading the previous one's output within r planes along axis 0.  Axis 0
+// is cut into slabs of at least r planes and sub-update u of slab s runs in
+// launch s + 2u: every value a sub-update reads was written in an earlier
+// launch, and no value is overwritten before the launch after its last
+// reader, so the fields stay in place and every point sees the operands of
+// the one-step order.  One launch runs all of its (sub-update, slab) items,
+// blockIdx.z selecting the item; the per-point code is the one-step code.
+template <int R>
+__global__ void __launch_bounds__(256) k_tti_wave(PhysGrid g, DerivW w, WaveItems L, const float* __restrict__ c2,
+                                                  const float* __restrict__ coef, const float* __restrict__ nz,
+                                                  const float* __restrict__ damp_b, float* flux) {
+  const Col c = thread_col(g);
+  if (!c.ok) return;
+  const WaveItem it = L.it[blockIdx.z];
+  if (it.kind == 0) tti_flux_cols<R>(g, w, c, it.x0, it.x1, it.a, it.c, nz, flux);
+  else tti_update_cols<R>(g, w, c, it.x0, it.x1, flux, it.a, it.b, it.c, it.d, c2, coef, damp_b);
+}
+
+template <int R>
+__global__ void __launch_bounds__(256, 4) k_ela_wave(PhysGrid g, DerivW w, float dt, WaveItems L, float* f,
+                                                  const float* __restrict__ mat, const float* __restrict__ eta_dt) {
+  const Col c = thread_col(g);
+  if (!c.ok) return;
+  const WaveItem it = L.it[blockIdx.z];
+  if (it.kind == 0) ela_velocity_cols<R>(g, w, c, dt, it.x0, it.x1, f, mat, eta_dt);
+  else ela_stress_cols<R>(g, w, c, dt, it.x0, it.x1, f, mat, eta_dt);
+}
+
+__device__ __forceinline__ int point_plane(const PhysGrid& g, int64_t l) { return (int)(l / ((int64_t)g.n1 * g.n2)); }
+
+// grid-aligned injection of the steps whose last sub-update finished slabs
+// in this launch: item blockIdx.y adds its step's table row to the points on
+// its planes (the one-step injection, restricted to a slab)
+__global__ void k_wave_inject(PhysGrid g, int64_t npts, const int64_t* __restrict__ lin, WavePosts P) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= npts) return;
+  const WavePost q = P.it[blockIdx.y];
+  const int64_t l = lin[id];
+  const int x = point_plane(g, l);
+  if (x < q.x0 || x >= q.x1) return;
+  const int z = (int)(l % g.n2), y = (int)((l / g.n2) % g.n1);
+  const size_t i0 = pidx(g, x, y, z);
+  const float a = q.dcmp[id];
+  if (q.f0) q.f0[i0] = __fadd_rn(q.f0[i0], a);
+  if (q.f1) q.f1[i0] = __fadd_rn(q.f1[i0], a);
+  if (q.f2) q.f2[i0] = __fadd_rn(q.f2[i0], a);
+}
+
+// receiver sampling of the same steps on the same slabs (after injection)
+__global__ void k_wave_sample(PhysGrid g, int64_t npts, const int2* __restrict__ ent, const int64_t* __restrict__ lin,
+                              WavePosts P) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= npts) return;
+  const WavePost q = P.it[blockIdx.y];
+  const int64_t l = lin[ent[e].y];
+  const int x = point_plane(g, l);
+  if (x < q.x0 || x >= q.x1) return;
+  const int z = (int)(l % g.n2), y = (int)((l / g.n2) % g.n1);
+  const size_t i0 = pidx(g, x, y, z);
+  float v = q.s0[i0];
+  if (q.s1) v = __fdiv_rn(__fadd_rn(__fadd_rn(v, q.s1[i0]), q.s2[i0]), 3.f);
+  q.row[e] = v;
+}
+
 // ------------------------------------------------------------- launch --
 static dim3 col_grid(const PhysGrid& g, int nz_planes) {
   return dim3((unsigned)((g.n2 + 31) / 32), (unsigned)((g.n1 + 7) / 8), (unsigned)nz_planes);
@@ -439,6 +541,57 @@ cudaError_t elastic_step(int R, const PhysGrid& g, const DerivW& w, float dt, in
     case 6: return ela_step_r<6>(g, w, dt, nchunks, f, mat, eta_dt, st);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t wave_launch(int physics, int R, const PhysGrid& g, const DerivW& w, float dt, const WaveItems& L,
+                        const float* c2, const float* coef, const float* nz, const float* damp_b, float* flux,
+                        float* ef, const float* mat, const float* eta_dt, cudaStream_t st) {
+  if (L.n < 1 || L.n > kWaveItemsMax) return cudaErrorInvalidValue;
+  const dim3 grid = col_grid(g, L.n), blk(32, 8);
+  count_launch();
+  if (physics == TB_TTI) {
+    switch (R) {
+      case 2: k_tti_wave<2><<<grid, blk, 0, st>>>(g, w, L, c2, coef, nz, damp_b, flux); break;
+      case 4: k_tti_wave<4><<<grid, blk, 0, st>>>(g, w, L, c2, coef, nz, damp_b, flux); break;
+      case 6: k_tti_wave<6><<<grid, blk, 0, st>>>(g, w, L, c2, coef, nz, damp_b, flux); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    switch (R) {
+      case 2: k_ela_wave<2><<<grid, blk, 0, st>>>(g, w, dt, L, ef, mat, eta_dt); break;
+      case 4: k_ela_wave<4><<<grid, blk, 0, st>>>(g, w, dt, L, ef, mat, eta_dt); break;
+      case 6: k_ela_wave<6><<<grid, blk, 0, st>>>(g, w, dt, L, ef, mat, eta_dt); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaGetLastError();
+}
+
+int wave_plan(int n0, int slab, int U, std::vector<int>* items) {
+  if (n0 < 1 || slab < 1 || U < 1) return -1;
+  const int ns = (n0 + slab - 1) / slab;
+  items->clear();
+  for (int L = 0; L < ns + 2 * (U - 1); ++L)
+    for (int u = 0; u < U; ++u) {
+      const int sl = L - 2 * u;
+      if (sl < 0 || sl >= ns) continue;
+      items->insert(items->end(), {L, u, sl * slab, std::min(n0, (sl + 1) * slab)});
+    }
+  return 0;
+}
+
+cudaError_t wave_post(const PhysGrid& g, const WavePosts& P, int64_t nsrc_pts, const int64_t* src_lin,
+                      int64_t nrec_pts, const int2* rec_ent, const int64_t* rec_lin, cudaStream_t st) {
+  if (P.n < 1 || P.n > kWavePostsMax) return cudaErrorInvalidValue;
+  if (nsrc_pts > 0) {
+    count_launch();
+    k_wave_inject<<<dim3(grid_for(nsrc_pts, 128), P.n), 128, 0, st>>>(g, nsrc_pts, src_lin, P);
+  }
+  if (nrec_pts > 0) {
+    count_launch();
+    k_wave_sample<<<dim3(grid_for(nrec_pts, 128), P.n), 128, 0, st>>>(g, nrec_pts, rec_ent, rec_lin, P);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t elastic_material(const PhysGrid& g, const float* vp, const float* vs, const float* rho, float* mat,

@@ -1,5 +1,7 @@
 """GPU parity of the TTI (Sec. III-B, Eq. 2) and elastic (Sec. III-C, Eq. 3)
-one-step propagators against the FP64 oracle, through the C ABI.
+propagators against the FP64 oracle, through the C ABI: one step per launch,
+and the temporally blocked wavefront (Sec. II-B, Fig. 7b), which must equal
+the one-step path bit for bit.
 
 Tolerance: rel-L2 <= 1e-4 on receiver traces and wavefields (FP32 against
 FP64), as for the acoustic path."""
@@ -55,12 +57,13 @@ def tti_case(shape, so, seed, nt):
     return h, vp, (eps, delta, theta, phi), src, rec
 
 
+@pytest.mark.parametrize("schedule", ["onestep", "blocked"])
 @pytest.mark.parametrize("shape,so,nt", [((30, 33, 40), 4, 70), ((28, 31, 37), 8, 60),
                                          ((30, 29, 35), 12, 40)])
-def test_tti_matches_oracle(tb, shape, so, nt):
+def test_tti_matches_oracle(tb, shape, so, nt, schedule):
     import torch
     h, vp, aux, src, rec = tti_case(shape, so, 101 + so, nt)
-    p = tb.Propagator(shape, h, so, physics=tb.TB_TTI, nbl=5)
+    p = tb.Propagator(shape, h, so, physics=tb.TB_TTI, nbl=5, time_tile=3, slab_planes=so // 2)
     p.set_model(torch.from_numpy(vp).cuda(), aux=np.stack(aux))
     dt = p.dt
     assert dt == pytest.approx(0.8 * oracle.tti_dt_max(so, h, float(vp.max()), float(aux[0].max())),
@@ -68,14 +71,14 @@ def test_tti_matches_oracle(tb, shape, so, nt):
     wav = wl.ricker(30.0, dt, nt, t0=8 * dt)[None, :].astype(np.float32)
     p.set_sources(src, wav)
     p.set_receivers(rec)
-    tr = p.forward(nt).cpu().numpy()
+    tr = p.forward(nt, schedule=schedule).cpu().numpy()
     tr_o, st_o = oracle.tti_forward(shape, h, so, dt, nt, vp.astype(np.float64),
                                     *[a.astype(np.float64) for a in aux], nbl=5,
                                     src_xyz=src, src_wav=wav.astype(np.float64), rec_xyz=rec)
     e_tr = rel_l2(tr, tr_o)
     fields = [p.field(i).cpu().numpy() for i in range(4)]
     e_f = [rel_l2(f, st_o[i]) for i, f in enumerate(fields)]
-    print(f"TTI so{so}: traces rel-L2 {e_tr:.2e}, fields {[f'{x:.1e}' for x in e_f]}")
+    print(f"TTI so{so} {schedule}: traces rel-L2 {e_tr:.2e}, fields {[f'{x:.1e}' for x in e_f]}")
     assert np.abs(tr_o).max() > 0
     assert e_tr <= TOL
     assert max(e_f) <= TOL
@@ -90,31 +93,67 @@ def elastic_case(shape, so, seed):
     return h, vp, (vs, rho), src, rec
 
 
+@pytest.mark.parametrize("schedule", ["onestep", "blocked"])
 @pytest.mark.parametrize("shape,so,nt", [((30, 33, 40), 4, 70), ((28, 31, 37), 8, 60),
                                          ((30, 29, 35), 12, 40)])
-def test_elastic_matches_oracle(tb, shape, so, nt):
+def test_elastic_matches_oracle(tb, shape, so, nt, schedule):
     import torch
     h, vp, aux, src, rec = elastic_case(shape, so, 201 + so)
-    p = tb.Propagator(shape, h, so, physics=tb.TB_ELASTIC, nbl=5)
+    p = tb.Propagator(shape, h, so, physics=tb.TB_ELASTIC, nbl=5, time_tile=3, slab_planes=so // 2)
     p.set_model(torch.from_numpy(vp).cuda(), aux=np.stack(aux))
     dt = p.dt
     assert dt == pytest.approx(0.8 * oracle.elastic_dt_max(so, h, float(vp.max())), rel=1e-9)
     wav = wl.ricker(40.0, dt, nt, t0=8 * dt)[None, :].astype(np.float32)
     p.set_sources(src, wav)
     p.set_receivers(rec)
-    tr = p.forward(nt).cpu().numpy()
+    tr = p.forward(nt, schedule=schedule).cpu().numpy()
     tr_o, st_o = oracle.elastic_forward(shape, h, so, dt, nt, vp.astype(np.float64),
                                         *[a.astype(np.float64) for a in aux], nbl=5, src_xyz=src,
                                         src_wav=wav.astype(np.float64), rec_xyz=rec)
     e_tr = rel_l2(tr, tr_o)
     e_f = [rel_l2(p.field(i).cpu().numpy(), st_o[i]) for i in range(9)]
-    print(f"elastic so{so}: traces rel-L2 {e_tr:.2e}, fields {[f'{x:.1e}' for x in e_f]}")
+    print(f"elastic so{so} {schedule}: traces rel-L2 {e_tr:.2e}, fields {[f'{x:.1e}' for x in e_f]}")
     assert np.abs(tr_o).max() > 0
     assert e_tr <= TOL
     assert max(e_f) <= TOL
 
 
-def test_tti_and_elastic_reject_blocked_and_bad_models(tb):
+def _run(tb, physics, case, so, nt, schedule, **opt):
+    import torch
+    h, vp, aux, src, rec = case
+    p = tb.Propagator(vp.shape, h, so, physics=physics, nbl=4, **opt)
+    p.set_model(torch.from_numpy(vp).cuda(), aux=np.stack(aux))
+    wav = np.stack([wl.ricker(f, p.dt, nt, t0=(6 + i) * p.dt) for i, f in enumerate((35.0, 25.0, 45.0))])
+    g = np.random.default_rng(so + nt)
+    ext = np.array([(vp.shape[d] - 1) * h[d] for d in range(3)])
+    srcs = np.concatenate([src, g.uniform(0.05, 0.95, size=(2, 3)) * ext])
+    srcs[1, 0] = 0.0      # a source on the first plane
+    srcs[2, 0] = ext[0]   # and one on the last
+    p.set_sources(srcs, wav.astype(np.float32))
+    p.set_receivers(rec)
+    tr = p.forward(nt, schedule=schedule).cpu().numpy()
+    nf = 4 if physics == tb.TB_TTI else 9
+    return tr, [p.field(i).cpu().numpy() for i in range(nf)]
+
+
+@pytest.mark.parametrize("physics", ["tti", "elastic"])
+@pytest.mark.parametrize("shape,so,T,slab,nt", [((30, 33, 40), 4, 2, 0, 23), ((37, 31, 36), 8, 3, 4, 20),
+                                                ((29, 33, 35), 8, 2, 5, 17), ((41, 29, 35), 12, 2, 6, 15),
+                                                ((33, 30, 34), 4, 8, 3, 19), ((19, 30, 34), 8, 4, 0, 13)])
+def test_blocked_bitwise_equals_onestep(tb, physics, shape, so, T, slab, nt):
+    """Ragged slabs (n0 not a multiple of the slab), nt not a multiple of T
+    (the rest one step per launch), sources on the first and last planes."""
+    phys = tb.TB_TTI if physics == "tti" else tb.TB_ELASTIC
+    case = (tti_case(shape, so, 300 + so, nt) if physics == "tti" else elastic_case(shape, so, 400 + so))
+    ref_tr, ref_f = _run(tb, phys, case, so, nt, "onestep")
+    got_tr, got_f = _run(tb, phys, case, so, nt, "blocked", time_tile=T, slab_planes=slab)
+    assert np.abs(ref_tr).max() > 0
+    assert np.array_equal(got_tr, ref_tr)
+    for a, b in zip(got_f, ref_f):
+        assert np.array_equal(a, b)
+
+
+def test_tti_and_elastic_reject_bad_options_and_models(tb):
     import torch
     shape, h = (20, 20, 20), (10.0, 10.0, 10.0)
     vp = torch.full(shape, 2000.0, device="cuda")
@@ -126,17 +165,15 @@ def test_tti_and_elastic_reject_blocked_and_bad_models(tb):
     with pytest.raises(tb.TBError):  # aux required
         p.set_model(vp)
     p.set_model(vp, aux=np.stack([0.2 * one, 0.1 * one, 0 * one, 0 * one]))
-    with pytest.raises(tb.TBError) as e:
-        p.forward(4, schedule="blocked")
-    assert e.value.status == 1
     q = tb.Propagator(shape, h, 4, physics=tb.TB_ELASTIC)
     with pytest.raises(tb.TBError):  # vs too large (2 vs^2 > vp^2)
         q.set_model(vp, aux=np.stack([1500.0 * one, one]))
-    with pytest.raises(tb.TBError):  # time_tile > 1 is acoustic only
-        tb.Propagator(shape, h, 4, physics=tb.TB_ELASTIC, time_tile=2)
+    for opt in [dict(time_tile=9), dict(slab_planes=1), dict(slab_planes=-1)]:
+        with pytest.raises(tb.TBError):  # at most 8 fused steps; slabs of at least r planes
+            tb.Propagator(shape, h, 4, physics=tb.TB_ELASTIC, **opt)
 
 
-def _subbox_parity(tb, physics, w, nsteps, radius):
+def _subbox_parity(tb, physics, w, nsteps, radius, schedule="onestep"):
     """Full-size run in the benchmark's configuration (same kernels and
     launch shapes) for nsteps; the oracle runs on the sub-box around the
     source that holds the whole domain of dependence (radius cells), with the
@@ -151,7 +188,7 @@ def _subbox_parity(tb, physics, w, nsteps, radius):
     wav = wl.ricker(w.f0, dt, nt, t0=3 * dt)[None, :].astype(np.float32)
     p.set_sources(w.src_xyz, wav)
     p.set_receivers(w.rec_xyz)
-    tr = p.forward(nt).cpu().numpy()
+    tr = p.forward(nt, schedule=schedule).cpu().numpy()
     c = np.floor(w.src_xyz[0] / np.array(h)).astype(int)
     lo = np.maximum(c - radius, 0)
     hi = np.minimum(c + radius + 2, np.array(shape))
@@ -181,12 +218,41 @@ def _subbox_parity(tb, physics, w, nsteps, radius):
 
 
 @pytest.mark.slow
-def test_tti_full_size_subbox(tb):
+@pytest.mark.parametrize("schedule", ["onestep", "blocked"])
+def test_tti_full_size_subbox(tb, schedule):
     w = wl.tti_384_so8()
-    _subbox_parity(tb, tb.TB_TTI, w, nsteps=5, radius=5 * w.so + 4)
+    _subbox_parity(tb, tb.TB_TTI, w, nsteps=5, radius=5 * w.so + 4, schedule=schedule)
 
 
 @pytest.mark.slow
-def test_elastic_full_size_subbox(tb):
+@pytest.mark.parametrize("schedule", ["onestep", "blocked"])
+def test_elastic_full_size_subbox(tb, schedule):
     w = wl.elastic_384_so8()
-    _subbox_parity(tb, tb.TB_ELASTIC, w, nsteps=6, radius=6 * w.so + 4)
+    _subbox_parity(tb, tb.TB_ELASTIC, w, nsteps=6, radius=6 * w.so + 4, schedule=schedule)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("physics", ["tti", "elastic"])
+def test_full_size_blocked_bitwise_equals_onestep(tb, physics):
+    """The benchmark's grid, model and default wavefront (time tile 4, slabs
+    of 32 planes) over 26 steps (six wavefronts and two single steps): traces
+    and every field bit for bit."""
+    import torch
+    w = wl.tti_384_so8() if physics == "tti" else wl.elastic_384_so8()
+    phys = tb.TB_TTI if physics == "tti" else tb.TB_ELASTIC
+    out = []
+    for schedule in ("onestep", "blocked"):
+        p = tb.Propagator(w.shape, w.spacing, w.so, physics=phys, nbl=w.nbl)
+        p.set_model(torch.from_numpy(w.vp).cuda(), aux=torch.from_numpy(np.stack(w.meta["aux"])).cuda())
+        nt = 26
+        wav = wl.ricker(w.f0, p.dt, nt, t0=3 * p.dt)[None, :].astype(np.float32)
+        p.set_sources(w.src_xyz, wav)
+        p.set_receivers(w.rec_xyz)
+        tr = p.forward(nt, schedule=schedule)
+        fields = [p.field(i) for i in range(4 if physics == "tti" else 9)]
+        out.append((tr, fields))
+        p.close()
+    (a_tr, a_f), (b_tr, b_f) = out
+    assert torch.equal(a_tr, b_tr) and bool(a_tr.abs().max() > 0)
+    for a, b in zip(a_f, b_f):
+        assert torch.equal(a, b)

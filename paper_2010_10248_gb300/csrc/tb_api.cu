@@ -532,7 +532,8 @@ extern "C" size_t tb_workspace_bytes(const tb_handle* h) {
   if (!h) return 0;
   const size_t fbytes = sizeof(float) * (size_t)h->n[0] * h->n[1] * h->n2p;
   // wavefields (four FP32 buffers, or two stored 16-bit / plain-FP32 ones) and c2
-  const size_t wave = h->storage == TB_F32 ? 4 * fbytes : 2 * (h->storage == TB_F32_PLAIN ? 1 : 2) * (fbytes / 4);
+  // (fbytes / 4 is one value per padded point)
+  const size_t wave = h->storage == TB_F32 ? 4 * fbytes : 2 * (h->storage == TB_F32_PLAIN ? 4 : 2) * (fbytes / 4);
   size_t b = wave + fbytes + sizeof(float) * (h->n[0] + h->n[1] + h->n[2]) + sizeof(int) * 4;
   if (h->storage != TB_F32) b += 2 * sizeof(float) * h->lp_cap;
   if (h->physics == TB_TTI) b += 11 * fbytes;

@@ -135,3 +135,67 @@ def test_batched_shots_equal_alone_and_the_oracle(serving):
     for p in props:
         p.close()
     b.close()
+
+
+@pytest.mark.parametrize("kind", ["blocked", "onestep", "f16"])
+def test_footprint_bounds_the_library_bytes(serving, kind):
+    """The admission estimate holds what the library reports for the shot
+    (tb_workspace_bytes after its forward) plus the device trace tensor, and
+    is not far above it."""
+    import torch
+    from paper_2010_10248_gb300 import _tb
+    g = np.random.default_rng(11)
+    shape, h = (80, 64, 96), (10.0, 10.0, 10.0)
+    vp = wl.layered_vp(shape, 3, vmin=1500.0, vmax=3000.0, nlayers=4, nblobs=2)
+    ext = np.array([(shape[d] - 1) * h[d] for d in range(3)])
+    src = g.uniform(0.3, 0.7, size=(3, 3)) * ext
+    rec = g.uniform(0.05, 0.95, size=(250, 3)) * ext
+    req = serving.ShotRequest(shape, h, 8, vp, src, 12.0, rec, nt=200, nbl=8,
+                              time_tile=0 if kind == "blocked" else 1, storage=1 if kind == "f16" else 0)
+    st = torch.cuda.current_stream()
+    p, dt, keep = serving._setup(torch, req, st, req.time_tile if req.storage == 0 else 1)
+    tr = torch.empty((req.nt, len(rec)), dtype=torch.float32, device="cuda")
+    _tb.tb_forward(p.h, req.nt, tr, _tb.TB_BLOCKED if kind == "blocked" else _tb.TB_ONESTEP, st)
+    torch.cuda.synchronize()
+    used = p.workspace_bytes() + 4 * tr.numel()
+    est = serving.footprint_bytes(req)
+    print(f"{kind}: library {used / 2**20:.1f} MiB, estimate {est / 2**20:.1f} MiB")
+    assert used <= est <= 1.3 * used + (16 << 20)
+    p.close()
+
+
+_ALLOC_PROBE = """
+import json, sys, torch
+import paper_2010_10248_gb300 as tb
+tb.load()
+opt = {"f32": {}, "f16": {"storage": tb.TB_F16}, "plain": {"storage": tb.TB_F32_PLAIN},
+       "tti": {"physics": tb.TB_TTI}, "elastic": {"physics": tb.TB_ELASTIC}}[sys.argv[1]]
+torch.cuda.init()
+tb.Propagator((32, 32, 32), (10.0, 10.0, 10.0), 8, **opt).close()  # first-use costs of the allocator
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+p = tb.Propagator((320, 320, 320), (10.0, 10.0, 10.0), 8, **opt)
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+print(json.dumps([free0 - free1, p.workspace_bytes()]))
+"""
+
+
+@pytest.mark.parametrize("kind", ["f32", "f16", "plain", "tti", "elastic"])
+def test_workspace_bytes_match_device_allocations(serving, kind):
+    """tb_workspace_bytes after tb_create against the drop in free device
+    memory around it, in a fresh process (its allocation pool holds only a
+    small handle's memory), to the pool's growth granularity."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _ALLOC_PROBE, kind], cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    drop, reported = json.loads(r.stdout.strip().splitlines()[-1])
+    field = 4 * 320 ** 3
+    print(f"{kind}: free memory dropped {drop / 2**20:.1f} MiB, reported {reported / 2**20:.1f} MiB")
+    assert reported >= 2 * field  # at least two FP32 wavefields' worth
+    assert abs(drop - reported) <= 64 << 20

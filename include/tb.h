@@ -113,8 +113,15 @@ typedef struct {
   int band_ctas;   /* pipelined blocked sweep: most CTAs per launch; 0 -> every
                       CTA that fits co-resident on the GPU (one per SM)          */
   int slab_planes; /* TB_TTI / TB_ELASTIC blocked sweep: planes per slab of the
-                      wavefront along axis 0, >= space_order / 2 (else
-                      TB_EINVAL); 0 -> 32                                       */
+                      wavefront along axis 0, at least the reach of one
+                      sub-update: space_order / 2, or space_order for TTI with
+                      tti_fused, else TB_EINVAL; 0 -> 32                         */
+  int tti_fused;   /* TB_TTI: 0 (default) a flux kernel writing the six flux
+                      fields and an update kernel reading them; 1: both passes
+                      of a step in one kernel, the fluxes kept on chip (the
+                      same values bit for bit, 6 fields less device memory,
+                      48 B less memory traffic per point and step, slower on
+                      GB300: one CTA per SM with two barriers per plane)        */
 } tb_options;
 
 /* Create a propagator for a grid of shape n[3] with spacing h[3] (metres),
@@ -123,7 +130,7 @@ typedef struct {
  * every axis.  `opt` may be NULL (defaults).  Allocates the wavefields and
  * model buffers on the current CUDA device (acoustic: 5 x n0 n1 n2 floats,
  * with TB_F16 / TB_BF16 storage two 16-bit wavefields and one float field;
- * TTI: 16; elastic: 18).  Errors: TB_EINVAL (also: 16-bit or plain storage
+ * TTI: 16, 10 with opt.tti_fused; elastic: 18).  Errors: TB_EINVAL (also: 16-bit or plain storage
  * with TTI or elastic physics), TB_ENOMEM, TB_ECUDA. */
 int tb_create(const int64_t n[3], const double h[3], int space_order, int physics,
               const tb_options* opt, tb_handle** out);
@@ -177,11 +184,12 @@ int tb_set_receivers(tb_handle* h, int nrec, const double* coords, void* stream)
  * NULL).  schedule: TB_ONESTEP (one launch per time step, spatial blocking
  * only) or TB_BLOCKED (opt.time_tile steps fused per sweep, Sec. II-B).
  * Both give bitwise-identical wavefields and traces.  TB_TTI and
- * TB_ELASTIC: each step is two sub-updates (TTI: fluxes, then divergence
- * and leapfrog update; elastic: velocity, then stress, Fig. 7b); TB_BLOCKED
- * runs opt.time_tile steps as one wavefront over slabs of opt.slab_planes
- * planes along axis 0, sub-update u of slab s in launch s + 2u (the nt mod
- * time_tile remaining steps one step per launch); traces sample p (TTI) or
+ * TB_ELASTIC: each step is two sub-updates (elastic: velocity, then
+ * stress, Fig. 7b; TTI: fluxes, then divergence and leapfrog update) or one
+ * (TTI with opt.tti_fused); TB_BLOCKED runs opt.time_tile steps as
+ * one wavefront over slabs of opt.slab_planes planes along axis 0,
+ * sub-update u of slab s in launch s + 2u (the nt mod time_tile remaining
+ * steps one step per launch); traces sample p (TTI) or
  * the mean normal stress at n+1 (elastic).  16-bit and plain storage:
  * TB_ONESTEP only (TB_EINVAL).  Source tables scale:
  * dt^2/m (acoustic, TTI), dt (elastic).  nt must not exceed the

@@ -453,7 +453,8 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
     h->opt.time_tile = physics != TB_ACOUSTIC ? 4 : ((tmax > 1 && so == 8) ? 3 : tmax);
   if (h->opt.time_tile < 1 || h->opt.time_tile > tmax || h->opt.nbl < 0 || h->opt.y_bands < 0 ||
       h->opt.x_chunks < 0 || h->opt.band_ctas < 0 || h->opt.slab_planes < 0 ||
-      (h->opt.slab_planes > 0 && h->opt.slab_planes < so / 2)) {
+      (h->opt.slab_planes > 0 &&
+       h->opt.slab_planes < ((physics == TB_TTI && h->opt.tti_fused) ? so : so / 2))) {
     delete h;
     return TB_EINVAL;
   }
@@ -488,8 +489,8 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   if (physics == TB_TTI) {
     if (e == cudaSuccess) e = dmalloc(&h->coef, 2 * fbytes, st);
     if (e == cudaSuccess) e = dmalloc(&h->nzb, 3 * fbytes, st);
-    if (e == cudaSuccess) e = dmalloc(&h->flux, 6 * fbytes, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->flux, 0, 6 * fbytes, st);
+    if (e == cudaSuccess && !h->opt.tti_fused) e = dmalloc(&h->flux, 6 * fbytes, st);
+    if (e == cudaSuccess && !h->opt.tti_fused) e = cudaMemsetAsync(h->flux, 0, 6 * fbytes, st);
   } else if (physics == TB_ELASTIC) {
     if (e == cudaSuccess) e = dmalloc(&h->efield, 9 * fbytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->efield, 0, 9 * fbytes, st);
@@ -536,7 +537,7 @@ extern "C" size_t tb_workspace_bytes(const tb_handle* h) {
   const size_t wave = h->storage == TB_F32 ? 4 * fbytes : 2 * (h->storage == TB_F32_PLAIN ? 4 : 2) * (fbytes / 4);
   size_t b = wave + fbytes + sizeof(float) * (h->n[0] + h->n[1] + h->n[2]) + sizeof(int) * 4;
   if (h->storage != TB_F32) b += 2 * sizeof(float) * h->lp_cap;
-  if (h->physics == TB_TTI) b += 11 * fbytes;
+  if (h->physics == TB_TTI) b += (h->opt.tti_fused ? 5 : 11) * fbytes;
   if (h->physics == TB_ELASTIC) b += 17 * fbytes - 4 * fbytes + sizeof(float) * (h->n[0] + h->n[1] + h->n[2]);
   b += h->src.bytes + h->rec.bytes;
   b += sizeof(float) * (size_t)h->src_nt * std::max<int64_t>(h->src.npts, 0);
@@ -1222,8 +1223,18 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
   // re-read 2r planes per slab to fill their register queues)
   const int slab = h->opt.slab_planes > 0 ? h->opt.slab_planes : 32;
   const bool src_on = h->have_src && h->src.npts > 0;
+  // TTI with tti_fused: both passes of a step in one kernel (a step is one
+  // sub-update of reach 2r)
+  const bool fused = h->physics == TB_TTI && h->opt.tti_fused;
+  const int per_step = fused ? 1 : 2;
   std::vector<int> plan;
-  if (T > 1 && wave_plan((int)h->n[0], slab, 2 * T, &plan) != 0) return fail(h, TB_EINVAL, "bad wavefront");
+  if (T > 1 && wave_plan((int)h->n[0], slab, per_step * T, &plan) != 0) return fail(h, TB_EINVAL, "bad wavefront");
+  // fused TTI: chunks along axis 0 for about four CTAs per SM in all (one
+  // CTA per SM fits), no chunk shorter than 8r planes (each computes the
+  // fluxes of 2r planes beyond it)
+  const int64_t ftiles = ((h->n[2] + 31) / 32) * ((h->n[1] + 7) / 8);
+  const int fchunks = (int)std::max<int64_t>(
+      1, std::min<int64_t>(h->n[0] / (8 * h->R), (4 * (int64_t)h->num_sms + ftiles - 1) / ftiles));
   for (int n = 0; n < nt;) {
     if (T > 1 && nt - n >= T) {
       if (rec_on && fill + T > h->rec_cap) {
@@ -1236,9 +1247,9 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
       WaveItems L{};
       WavePosts P{};
       for (size_t i = 0; i < plan.size(); i += 4) {
-        const int u = plan[i + 1], k = u / 2;
+        const int u = plan[i + 1], k = u / per_step;
         WaveItem& it = L.it[L.n++];
-        it.kind = u & 1;
+        it.kind = fused ? 1 : (u & 1);
         it.x0 = plan[i + 2];
         it.x1 = plan[i + 3];
         if (h->physics == TB_TTI) {
@@ -1275,8 +1286,10 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
           h->ev_kind.push_back(0);
           if (ea) cudaEventRecord(ea, st);
         }
-        cudaError_t e = wave_launch(h->physics, h->R, g, w, (float)h->dt, L, h->c2, h->coef, h->nzb, h->damp_b,
-                                    h->flux, h->efield, h->emat, h->eta_dt, st);
+        cudaError_t e = fused ? tti_fused(h->R, g, w, 0, &L, nullptr, nullptr, nullptr, nullptr, h->c2, h->coef,
+                                          h->nzb, h->damp_b, st)
+                              : wave_launch(h->physics, h->R, g, w, (float)h->dt, L, h->c2, h->coef, h->nzb,
+                                            h->damp_b, h->flux, h->efield, h->emat, h->eta_dt, st);
         if (h->opt.profile && eb) cudaEventRecord(eb, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "wavefront launch");
         if (P.n > 0) {
@@ -1336,8 +1349,10 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
       continue;
     }
     if (h->physics == TB_TTI) {
-      e = tti_step(h->R, g, w, nchunks, h->field[pc], h->field[pp], h->field[rc], h->field[rp], h->c2, h->coef,
-                   h->nzb, h->damp_b, h->flux, st);
+      e = fused ? tti_fused(h->R, g, w, fchunks, nullptr, h->field[pc], h->field[pp], h->field[rc], h->field[rp],
+                            h->c2, h->coef, h->nzb, h->damp_b, st)
+                : tti_step(h->R, g, w, nchunks, h->field[pc], h->field[pp], h->field[rc], h->field[rp], h->c2,
+                           h->coef, h->nzb, h->damp_b, h->flux, st);
       std::swap(pc, pp);
       std::swap(rc, rp);
       f0 = h->field[pc];

@@ -185,6 +185,11 @@ cudaError_t wave_launch(int physics, int R, const PhysGrid& g, const DerivW& w, 
                         float* ef, const float* mat, const float* eta_dt, cudaStream_t st);
 cudaError_t wave_post(const PhysGrid& g, const WavePosts& P, int64_t nsrc_pts, const int64_t* src_lin,
                       int64_t nrec_pts, const int2* rec_ent, const int64_t* rec_lin, cudaStream_t st);
+// One TTI step with both passes fused on chip (no flux fields in memory):
+// chunks along axis 0 (L null), or the items of one wavefront launch.
+cudaError_t tti_fused(int R, const PhysGrid& g, const DerivW& w, int nchunks, const WaveItems* L, const float* pc,
+                      float* pp, const float* rc, float* rp, const float* c2, const float* coef, const float* nz,
+                      const float* damp_b, cudaStream_t st);
 // items (launch, sub-update, x0, x1) of the wavefront over n0 planes in slabs
 // of `slab` planes for U sub-updates, launches in order; -1 on bad arguments
 int wave_plan(int n0, int slab, int U, std::vector<int>* items);

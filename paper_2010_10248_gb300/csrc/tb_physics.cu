@@ -200,6 +200,226 @@ __global__ void __launch_bounds__(256) k_tti_update(PhysGrid g, DerivW w, int nc
   tti_update_cols<R>(g, w, c, x0, x1, flux, pc, pp, rc, rp, c2, coef, damp_b);
 }
 
+// ------------------------------------------------------- fused TTI step --
+// Both passes of a TTI step in one kernel.  A CTA owns a tile of kFY x TZ
+// columns and streams a chunk of planes; one thread per column of the tile
+// widened by r on each side along axes 1 and 2.  At flux plane x every
+// thread takes p, r of its column from register queues (planes x - r ..
+// x + r) and the axis-1/2 neighbours from shared planes that reach 2r beyond
+// the tile, and computes F, G there: F0, G0 stay in the owning thread's
+// register queue (planes x - 2r .. x), F1, G1 (rows -r .. kFY + r) and F2,
+// G2 (columns -r .. TZ + r) go into a ring of r + 1 shared planes.  The
+// update of plane x - r then reads all six fluxes on chip.  Every operation
+// is that of k_tti_flux and k_tti_update in the same order (fluxes zero
+// outside the grid), so the step equals the two-kernel step bit for bit,
+// and the fluxes never reach memory (per point and step: p, r, p^{n-1},
+// r^{n-1}, the six coefficients read, p, r written).
+constexpr int kFY = 8;
+template <int R>
+struct TtiFusedCfg {
+  static constexpr int TZ = R == 2 ? 32 : 24;               // tile columns (about 512-720 threads)
+  static constexpr int EH = kFY + 2 * R, EW = TZ + 2 * R;   // thread columns
+  static constexpr int NT = EH * EW;
+  static constexpr int PH = kFY + 4 * R, PW = TZ + 4 * R;   // shared p, r planes
+  static constexpr int NFAR = 2 * R * (kFY + TZ);          // plane cells read beyond the thread columns
+  static constexpr int NRING = R + 1;                      // flux planes kept for the divergence
+  static constexpr int FYS = EH * TZ, FZS = kFY * EW;     // F1 / G1 and F2 / G2 plane sizes
+  static constexpr int SMEM = (int)sizeof(float) * (2 * PH * PW + NRING * 2 * (FYS + FZS));
+  static_assert(NFAR <= NT && NT <= 1024, "thread columns");
+};
+
+// d/dy, d/dz of a shared plane with row pitch `pitch` at index c: the sums
+// of dc_y / dc_z (offsets r .. 1, zeros outside the grid already stored)
+template <int R>
+__device__ __forceinline__ float dcs(const float* f, int c, int step, const float* a) {
+  float s = 0.f;
+#pragma unroll
+  for (int i = R; i >= 1; --i) s = __fmaf_rn(a[i - 1], __fsub_rn(f[c + i * step], f[c - i * step]), s);
+  return s;
+}
+
+// Every global value a step needs (p, r at plane x + r, the far cells at x,
+// the frame at x, the update's operands at x - r) is loaded one step ahead,
+// so that a step's loads are in flight during the previous step's work.
+template <int R>
+__device__ __forceinline__ void tti_fused_tile(const PhysGrid& g, const DerivW& w, int y0, int z0, int x0, int x1,
+                                               const float* __restrict__ pc, float* pp, const float* __restrict__ rc,
+                                               float* rp, const float* __restrict__ c2, const float* __restrict__ coef,
+                                               const float* __restrict__ nz, const float* __restrict__ damp_b,
+                                               float* sm) {
+  using C = TtiFusedCfg<R>;
+  constexpr int TZ = C::TZ;
+  const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
+  const int t = threadIdx.x;
+  const int ey = t / C::EW - R, ez = t % C::EW - R;  // column relative to the tile
+  const int y = y0 + ey, z = z0 + ez;
+  const bool in_yz = (unsigned)y < (unsigned)g.n1 && (unsigned)z < (unsigned)g.n2;
+  const bool ycross = ez >= 0 && ez < TZ;   // F1, G1 wanted here
+  const bool zcross = ey >= 0 && ey < kFY;  // F2, G2 wanted here
+  const bool own = ycross && zcross;
+  const bool flux_col = in_yz && (ycross || zcross);
+  const bool upd_col = own && in_yz;
+  float* sp = sm;
+  float* sr = sm + C::PH * C::PW;
+  float* ring = sm + 2 * C::PH * C::PW;  // [NRING][F1 | G1 | F2 | G2]
+  const int cs = (ey + 2 * R) * C::PW + ez + 2 * R;  // this column in the shared planes
+  // the far cell of this thread: 2r rows beyond the thread rows at the tile's
+  // columns, 2r columns beyond the thread columns at the tile's rows
+  int fy = 0, fz = 0;
+  const bool far = t < C::NFAR;
+  if (far) {
+    if (t < 2 * R * TZ) {
+      const int row = t / TZ;
+      fy = row < R ? row - 2 * R : kFY + row;
+      fz = t % TZ;
+    } else {
+      const int f = t - 2 * R * TZ, col = f % (2 * R);
+      fy = f / (2 * R);
+      fz = col < R ? col - 2 * R : TZ + col;
+    }
+  }
+  const int fyg = y0 + fy, fzg = z0 + fz;
+  const bool far_in = far && (unsigned)fyg < (unsigned)g.n1 && (unsigned)fzg < (unsigned)g.n2;
+  const int cf = (fy + 2 * R) * C::PW + fz + 2 * R;
+  const size_t col = (size_t)(in_yz ? y : 0) * g.n2p + (in_yz ? z : 0);
+  const size_t colf = (size_t)(far_in ? fyg : 0) * g.n2p + (far_in ? fzg : 0);
+  const size_t plane = (size_t)g.n1 * g.n2p;
+  auto ldx = [&](const float* f, size_t c, bool ok, int x) -> float {
+    return (ok && (unsigned)x < (unsigned)g.n0) ? __ldg(f + (size_t)x * plane + c) : 0.f;
+  };
+  float qp[2 * R + 1], qr[2 * R + 1], qf[2 * R + 1], qg[2 * R + 1];
+  const int xs = x0 - R, xe = x1 + R;  // flux planes
+  qp[0] = qr[0] = 0.f;  // shifted out before its first use
+#pragma unroll
+  for (int s = 1; s < 2 * R + 1; ++s) {  // planes xs - r .. xs + r - 1
+    qp[s] = ldx(pc, col, in_yz, xs - 1 - R + s);
+    qr[s] = ldx(rc, col, in_yz, xs - 1 - R + s);
+  }
+#pragma unroll
+  for (int s = 0; s < 2 * R + 1; ++s) qf[s] = qg[s] = 0.f;
+  const float byz = upd_col ? __fadd_rn(__ldg(damp_b + g.n0 + y), __ldg(damp_b + g.n0 + g.n1 + z)) : 0.f;
+  // values of the coming step, loaded one step ahead
+  float np_ = 0.f, nr_ = 0.f, fp_ = 0.f, fr_ = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f;
+  float o_pp = 0.f, o_rp = 0.f, o_c2 = 0.f, o_cp = 0.f, o_cr = 0.f;
+  auto prefetch = [&](int x) {
+    np_ = ldx(pc, col, in_yz, x + R);
+    nr_ = ldx(rc, col, in_yz, x + R);
+    if (far) {
+      fp_ = ldx(pc, colf, far_in, x);
+      fr_ = ldx(rc, colf, far_in, x);
+    }
+    if (flux_col && (unsigned)x < (unsigned)g.n0) {
+      const size_t i0 = (size_t)x * plane + col;
+      m0 = __ldg(nz + i0);
+      m1 = __ldg(nz + Np + i0);
+      m2 = __ldg(nz + 2 * Np + i0);
+    }
+    const int u = x - R;
+    if (upd_col && u >= x0 && u < x1) {
+      const size_t i0 = (size_t)u * plane + col;
+      o_pp = pp[i0];
+      o_rp = rp[i0];
+      o_c2 = __ldg(c2 + i0);
+      o_cp = __ldg(coef + i0);
+      o_cr = __ldg(coef + Np + i0);
+    }
+  };
+  prefetch(xs);
+  for (int x = xs; x < xe; ++x) {
+#pragma unroll
+    for (int s = 0; s < 2 * R; ++s) {
+      qp[s] = qp[s + 1];
+      qr[s] = qr[s + 1];
+    }
+    qp[2 * R] = np_;
+    qr[2 * R] = nr_;
+    sp[cs] = qp[R];
+    sr[cs] = qr[R];
+    if (far) {
+      sp[cf] = fp_;
+      sr[cf] = fr_;
+    }
+    const bool pin = flux_col && (unsigned)x < (unsigned)g.n0;
+    const float n0 = m0, n1 = m1, n2 = m2;
+    const float upp = o_pp, urp = o_rp, c2v = o_c2, cpp = o_cp, cpr = o_cr;
+    if (x + 1 < xe) prefetch(x + 1);
+    __syncthreads();
+    float F0 = 0.f, F1 = 0.f, F2 = 0.f, G0 = 0.f, G1 = 0.f, G2 = 0.f;
+    if (pin) {
+      const float gp0 = dc_q<R>(qp, w.a[0]), gp1 = dcs<R>(sp, cs, C::PW, w.a[1]), gp2 = dcs<R>(sp, cs, 1, w.a[2]);
+      const float gr0 = dc_q<R>(qr, w.a[0]), gr1 = dcs<R>(sr, cs, C::PW, w.a[1]), gr2 = dcs<R>(sr, cs, 1, w.a[2]);
+      const float spn = __fmaf_rn(n2, gp2, __fmaf_rn(n1, gp1, __fmul_rn(n0, gp0)));
+      const float srn = __fmaf_rn(n2, gr2, __fmaf_rn(n1, gr1, __fmul_rn(n0, gr0)));
+      F0 = __fmaf_rn(-n0, spn, gp0);
+      F1 = __fmaf_rn(-n1, spn, gp1);
+      F2 = __fmaf_rn(-n2, spn, gp2);
+      G0 = __fmul_rn(n0, srn);
+      G1 = __fmul_rn(n1, srn);
+      G2 = __fmul_rn(n2, srn);
+    }
+    float* slot = ring + ((x - xs) % C::NRING) * 2 * (C::FYS + C::FZS);
+    if (ycross) {
+      slot[(ey + R) * TZ + ez] = F1;
+      slot[C::FYS + (ey + R) * TZ + ez] = G1;
+    }
+    if (zcross) {
+      slot[2 * C::FYS + ey * C::EW + ez + R] = F2;
+      slot[2 * C::FYS + C::FZS + ey * C::EW + ez + R] = G2;
+    }
+#pragma unroll
+    for (int s = 0; s < 2 * R; ++s) {
+      qf[s] = qf[s + 1];
+      qg[s] = qg[s + 1];
+    }
+    qf[2 * R] = F0;
+    qg[2 * R] = G0;
+    __syncthreads();
+    const int u = x - R;  // the plane updated at this step
+    if (upd_col && u >= x0) {
+      const float* su = ring + ((u - xs) % C::NRING) * 2 * (C::FYS + C::FZS);
+      const int cy = (ey + R) * TZ + ez, cz = ey * C::EW + ez + R;
+      const float hh = __fadd_rn(__fadd_rn(dc_q<R>(qf, w.a[0]), dcs<R>(su, cy, TZ, w.a[1])),
+                                 dcs<R>(su + 2 * C::FYS, cz, 1, w.a[2]));
+      const float hz = __fadd_rn(__fadd_rn(dc_q<R>(qg, w.a[0]), dcs<R>(su + C::FYS, cy, TZ, w.a[1])),
+                                 dcs<R>(su + 2 * C::FYS + C::FZS, cz, 1, w.a[2]));
+      const size_t i0 = (size_t)u * plane + col;
+      const float rhs_p = __fmaf_rn(cpp, hh, __fmul_rn(cpr, hz));
+      const float rhs_r = __fmaf_rn(cpr, hh, hz);
+      const float gdamp = __fmul_rn(__fadd_rn(__ldg(damp_b + u), byz), c2v);
+      const float opg = __fadd_rn(1.f, gdamp), omg = __fsub_rn(1.f, gdamp);
+      const float up = qp[0], ur = qr[0];
+      pp[i0] = __fadd_rn(up, div_sponge(__fmaf_rn(c2v, rhs_p, __fmul_rn(omg, __fsub_rn(up, upp))), opg));
+      rp[i0] = __fadd_rn(ur, div_sponge(__fmaf_rn(c2v, rhs_r, __fmul_rn(omg, __fsub_rn(ur, urp))), opg));
+    }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(TtiFusedCfg<R>::NT, 1)
+    k_tti_fused(PhysGrid g, DerivW w, int nchunks, const float* __restrict__ pc, float* pp,
+                const float* __restrict__ rc, float* rp, const float* __restrict__ c2,
+                const float* __restrict__ coef, const float* __restrict__ nz, const float* __restrict__ damp_b) {
+  extern __shared__ float4 tti_smem4[];
+  int x0, x1;
+  chunk_planes(g, nchunks, x0, x1);
+  tti_fused_tile<R>(g, w, blockIdx.y * kFY, blockIdx.x * TtiFusedCfg<R>::TZ, x0, x1, pc, pp, rc, rp, c2, coef, nz,
+                    damp_b,
+                    reinterpret_cast<float*>(tti_smem4));
+}
+
+// wavefront form: item blockIdx.z is one fused step on one slab (a: p^n,
+// b: p^{n-1} -> p^{n+1}, c: r^n, d: r^{n-1} -> r^{n+1})
+template <int R>
+__global__ void __launch_bounds__(TtiFusedCfg<R>::NT, 1)
+    k_tti_fused_wave(PhysGrid g, DerivW w, WaveItems L, const float* __restrict__ c2, const float* __restrict__ coef,
+                     const float* __restrict__ nz, const float* __restrict__ damp_b) {
+  extern __shared__ float4 tti_smem4[];
+  const WaveItem it = L.it[blockIdx.z];
+  tti_fused_tile<R>(g, w, blockIdx.y * kFY, blockIdx.x * TtiFusedCfg<R>::TZ, it.x0, it.x1, it.a, it.b, it.c, it.d,
+                    c2, coef, nz,
+                    damp_b, reinterpret_cast<float*>(tti_smem4));
+}
+
 // ------------------------------------------------------------- elastic --
 // node -> half-node: sum_k c_k (f[i+k] - f[i-k+1]); half-node -> node:
 // sum_k c_k (f[i+k-1] - f[i-k]), along axis d at (x, y, z)
@@ -510,6 +730,41 @@ static cudaError_t tti_step_r(const PhysGrid& g, const DerivW& w, int nchunks, c
   k_tti_flux<R><<<col_grid(g, nchunks), blk, 0, st>>>(g, w, nchunks, pc, rc, nz, flux);
   k_tti_update<R><<<col_grid(g, nchunks), blk, 0, st>>>(g, w, nchunks, flux, pc, pp, rc, rp, c2, coef, damp_b);
   return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t tti_fused_r(const PhysGrid& g, const DerivW& w, int nchunks, const WaveItems* L, const float* pc,
+                               float* pp, const float* rc, float* rp, const float* c2, const float* coef,
+                               const float* nz, const float* damp_b, cudaStream_t st) {
+  using C = TtiFusedCfg<R>;
+  static bool attr = false;  // shared memory above 48 KB (r = 6) needs the opt-in
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tti_fused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tti_fused_wave<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const unsigned gz = (unsigned)((g.n2 + C::TZ - 1) / C::TZ), gy = (unsigned)((g.n1 + kFY - 1) / kFY);
+  count_launch();
+  if (L)
+    k_tti_fused_wave<R><<<dim3(gz, gy, L->n), C::NT, C::SMEM, st>>>(g, w, *L, c2, coef, nz, damp_b);
+  else
+    k_tti_fused<R><<<dim3(gz, gy, nchunks), C::NT, C::SMEM, st>>>(g, w, nchunks, pc, pp, rc, rp, c2, coef, nz,
+                                                                    damp_b);
+  return cudaGetLastError();
+}
+
+cudaError_t tti_fused(int R, const PhysGrid& g, const DerivW& w, int nchunks, const WaveItems* L, const float* pc,
+                      float* pp, const float* rc, float* rp, const float* c2, const float* coef, const float* nz,
+                      const float* damp_b, cudaStream_t st) {
+  if (L && (L->n < 1 || L->n > kWaveItemsMax)) return cudaErrorInvalidValue;
+  switch (R) {
+    case 2: return tti_fused_r<2>(g, w, nchunks, L, pc, pp, rc, rp, c2, coef, nz, damp_b, st);
+    case 4: return tti_fused_r<4>(g, w, nchunks, L, pc, pp, rc, rp, c2, coef, nz, damp_b, st);
+    case 6: return tti_fused_r<6>(g, w, nchunks, L, pc, pp, rc, rp, c2, coef, nz, damp_b, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t tti_step(int R, const PhysGrid& g, const DerivW& w, int nchunks, const float* pc, float* pp,

@@ -63,7 +63,7 @@ def tti_case(shape, so, seed, nt):
 def test_tti_matches_oracle(tb, shape, so, nt, schedule):
     import torch
     h, vp, aux, src, rec = tti_case(shape, so, 101 + so, nt)
-    p = tb.Propagator(shape, h, so, physics=tb.TB_TTI, nbl=5, time_tile=3, slab_planes=so // 2)
+    p = tb.Propagator(shape, h, so, physics=tb.TB_TTI, nbl=5, time_tile=3, slab_planes=so)
     p.set_model(torch.from_numpy(vp).cuda(), aux=np.stack(aux))
     dt = p.dt
     assert dt == pytest.approx(0.8 * oracle.tti_dt_max(so, h, float(vp.max()), float(aux[0].max())),
@@ -136,17 +136,36 @@ def _run(tb, physics, case, so, nt, schedule, **opt):
     return tr, [p.field(i).cpu().numpy() for i in range(nf)]
 
 
-@pytest.mark.parametrize("physics", ["tti", "elastic"])
+@pytest.mark.parametrize("physics", ["tti", "tti_fused", "elastic"])
 @pytest.mark.parametrize("shape,so,T,slab,nt", [((30, 33, 40), 4, 2, 0, 23), ((37, 31, 36), 8, 3, 4, 20),
                                                 ((29, 33, 35), 8, 2, 5, 17), ((41, 29, 35), 12, 2, 6, 15),
                                                 ((33, 30, 34), 4, 8, 3, 19), ((19, 30, 34), 8, 4, 0, 13)])
 def test_blocked_bitwise_equals_onestep(tb, physics, shape, so, T, slab, nt):
     """Ragged slabs (n0 not a multiple of the slab), nt not a multiple of T
-    (the rest one step per launch), sources on the first and last planes."""
-    phys = tb.TB_TTI if physics == "tti" else tb.TB_ELASTIC
-    case = (tti_case(shape, so, 300 + so, nt) if physics == "tti" else elastic_case(shape, so, 400 + so))
-    ref_tr, ref_f = _run(tb, phys, case, so, nt, "onestep")
-    got_tr, got_f = _run(tb, phys, case, so, nt, "blocked", time_tile=T, slab_planes=slab)
+    (the rest one step per launch), sources on the first and last planes.
+    The fused TTI step reaches 2r planes, so its slabs are at least so."""
+    phys = tb.TB_ELASTIC if physics == "elastic" else tb.TB_TTI
+    fused = physics == "tti_fused"
+    if fused and slab:
+        slab = max(slab, so)
+    case = (elastic_case(shape, so, 400 + so) if physics == "elastic" else tti_case(shape, so, 300 + so, nt))
+    ref_tr, ref_f = _run(tb, phys, case, so, nt, "onestep", tti_fused=fused)
+    got_tr, got_f = _run(tb, phys, case, so, nt, "blocked", time_tile=T, slab_planes=slab, tti_fused=fused)
+    assert np.abs(ref_tr).max() > 0
+    assert np.array_equal(got_tr, ref_tr)
+    for a, b in zip(got_f, ref_f):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("shape,so", [((30, 33, 40), 4), ((70, 19, 71), 8), ((45, 26, 33), 12), ((96, 40, 66), 8)])
+def test_tti_fused_step_equals_two_pass(tb, shape, so):
+    """The fused TTI step (fluxes on chip, tiles of 8 x 32 columns, chunks
+    along axis 0) against the flux and update kernels: traces and fields bit
+    for bit, on grids with ragged tiles and several chunks."""
+    nt = 21
+    case = tti_case(shape, so, 500 + so, nt)
+    ref_tr, ref_f = _run(tb, tb.TB_TTI, case, so, nt, "onestep")
+    got_tr, got_f = _run(tb, tb.TB_TTI, case, so, nt, "onestep", tti_fused=True)
     assert np.abs(ref_tr).max() > 0
     assert np.array_equal(got_tr, ref_tr)
     for a, b in zip(got_f, ref_f):
@@ -171,6 +190,9 @@ def test_tti_and_elastic_reject_bad_options_and_models(tb):
     for opt in [dict(time_tile=9), dict(slab_planes=1), dict(slab_planes=-1)]:
         with pytest.raises(tb.TBError):  # at most 8 fused steps; slabs of at least r planes
             tb.Propagator(shape, h, 4, physics=tb.TB_ELASTIC, **opt)
+    with pytest.raises(tb.TBError):  # the fused TTI step reaches 2r planes
+        tb.Propagator(shape, h, 8, physics=tb.TB_TTI, slab_planes=7, tti_fused=True)
+    tb.Propagator(shape, h, 8, physics=tb.TB_TTI, slab_planes=4).close()
 
 
 def _subbox_parity(tb, physics, w, nsteps, radius, schedule="onestep"):

@@ -31,6 +31,12 @@ def accesses(physics, u, x0, x1, n0, r):
     """(reads, writes) of sub-update u on planes [x0, x1): sets of (buffer, plane)."""
     near = range(max(0, x0 - r), min(n0, x1 + r))
     own = range(x0, x1)
+    if physics == "tti_fused":  # one sub-update per step, reaching 2r planes
+        cur, prev = u % 2, (u + 1) % 2
+        near2 = range(max(0, x0 - 2 * r), min(n0, x1 + 2 * r))
+        reads = {(f"{b}{cur}", x) for b in "PR" for x in near2} | {(f"{b}{prev}", x) for b in "PR" for x in own}
+        writes = {(f"{b}{prev}", x) for b in "PR" for x in own}
+        return reads, writes
     k, second = divmod(u, 2)
     if physics == "tti":
         cur, prev = k % 2, (k + 1) % 2
@@ -52,8 +58,8 @@ def accesses(physics, u, x0, x1, n0, r):
 
 def post_accesses(physics, u, x0, x1):
     """injection (read-modify-write) and sampling of the step's output"""
-    k = u // 2
-    bufs = [f"P{(k + 1) % 2}", f"R{(k + 1) % 2}"] if physics == "tti" else ["S"]
+    k = u if physics == "tti_fused" else u // 2
+    bufs = [f"P{(k + 1) % 2}", f"R{(k + 1) % 2}"] if physics.startswith("tti") else ["S"]
     rw = {(b, x) for b in bufs for x in range(x0, x1)}
     return rw, rw
 
@@ -69,7 +75,7 @@ def run_onestep(physics, n0, r, U):
         for x, (_, wr) in enumerate(ops):
             for a in wr:
                 ver[a] = ("op", u, a[1])
-        if u % 2:
+        if u % 2 or physics == "tti_fused":
             for x in range(n0):
                 rd, wr = post_accesses(physics, u, x, x + 1)
                 seen[("post", u, x)] = {a: ver.get(a) for a in rd}
@@ -96,7 +102,7 @@ def run_wave(physics, items, n0, r, U):
         for (_, u, x0, x1), (_, wr) in zip(grp, acc):
             for a in wr:
                 ver[a] = ("op", u, a[1])
-        posts = [(u, x0, x1) for _, u, x0, x1 in grp if u % 2]
+        posts = [(u, x0, x1) for _, u, x0, x1 in grp if u % 2 or physics == "tti_fused"]
         pacc = [post_accesses(physics, u, x0, x1) for u, x0, x1 in posts]
         for i, j in itertools.permutations(range(len(posts)), 2):
             assert not (pacc[i][1] & (pacc[j][0] | pacc[j][1]))
@@ -126,6 +132,22 @@ def test_wavefront_replays_the_onestep_order(lib, physics, n0, r, slab, T):
     assert got.keys() == ref.keys()
     for key in ref:
         assert got[key] == ref[key], key
+
+
+@pytest.mark.parametrize("n0,r,slab,T", [(37, 2, 4, 3), (50, 4, 8, 4), (41, 6, 12, 2), (61, 4, 9, 8), (7, 4, 8, 3)])
+def test_fused_tti_wavefront_replays_the_onestep_order(lib, n0, r, slab, T):
+    """The fused TTI step is one sub-update per step reading p, r within 2r
+    planes: slabs of at least 2r planes keep the same rules."""
+    items = [tuple(map(int, it)) for it in _tb.tb_plan_wavefront(n0, slab, T)]
+    ref = run_onestep("tti_fused", n0, r, T)
+    got = run_wave("tti_fused", items, n0, r, T)
+    assert got == ref
+
+
+def test_fused_tti_slabs_thinner_than_its_reach_would_race(lib):
+    items = [tuple(map(int, it)) for it in _tb.tb_plan_wavefront(40, 6, 4)]  # r = 4 reaches 8 planes
+    with pytest.raises(AssertionError):
+        run_wave("tti_fused", items, 40, 4, 4)
 
 
 def test_skew_one_would_race(lib):

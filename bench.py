@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--wave-tile", type=int, default=4, help="TTI / elastic: steps per wavefront")
     ap.add_argument("--slab", type=int, default=0, help="TTI / elastic: planes per wavefront slab (0: auto)")
     ap.add_argument("--tti-fused", action="store_true", help="TTI: both passes of a step in one kernel")
+    ap.add_argument("--elastic-plain", action="store_true", help="elastic: the L1 streaming kernels")
     ap.add_argument("--physics", default="acoustic", choices=["acoustic", "tti", "elastic"],
                     help="tti / elastic: the 384^3 so8 500-step TTI or elastic workload, one-step "
                          "schedule (the headline line is the acoustic one)")
@@ -147,7 +148,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("tb_sweep.cuh",):
+    for f in ("tb_sweep.cuh", "tb_async.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2010_10248_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -537,7 +538,7 @@ def run_physics(args):
     vp = torch.from_numpy(w.vp).to(dev)
     aux = torch.from_numpy(np.stack(w.meta["aux"])).to(dev)
     prop = tb.Propagator(w.shape, w.spacing, w.so, physics=phys, nbl=w.nbl, profile=True, time_tile=T,
-                         slab_planes=args.slab, tti_fused=args.tti_fused)
+                         slab_planes=args.slab, tti_fused=args.tti_fused, elastic_plain=args.elastic_plain)
     st = torch.cuda.current_stream()
     prop.set_model(vp, aux=aux)
     dt = prop.dt
@@ -600,6 +601,8 @@ def run_physics(args):
                        "receivers": len(w.rec_xyz), "schedule": "blocked", "time_tile": T,
                        "slab_planes": args.slab or 32,
                        "tti_step": ("fused" if args.tti_fused else "two kernels") if args.physics == "tti" else None,
+                       "elastic_step": ("L1 streaming" if args.elastic_plain else "TMA-staged")
+                       if args.physics == "elastic" else None,
                        "l2": "inputs larger than L2",
                        "step": "set_model + set_sources + set_receivers + forward(nt)"},
             "gpu_launches": launches_b, "clocks": clk,

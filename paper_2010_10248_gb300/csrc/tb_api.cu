@@ -103,6 +103,7 @@ struct tb_handle {
   CUtensorMap tm_box[4];   // u^n boxes with halo, per field buffer
   CUtensorMap tm_tile[4];  // own tiles, per field buffer
   CUtensorMap tm_c2;       // own tiles of c2
+  ElaMaps ela_maps;        // elastic fields and material for the TMA-staged updates
   float* damp_b = nullptr;
   // other physics (Sec. III-B/C): physics id, TTI coefficients [2][Np]
   // (1+2eps, sqrt(1+2delta)), symmetry axis [3][Np], fluxes [6][Np];
@@ -415,6 +416,28 @@ static cudaError_t make_tmap(CUtensorMap* m, void* base, const int64_t n[3], int
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// [nf][n0][n1][n2p] floats as a 4-D tensor (axis 2 innermost), bw x bh boxes of one plane of one field
+static cudaError_t make_tmap4(CUtensorMap* m, void* base, const int64_t n[3], int n2p, int nf, int bw, int bh) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                           cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess) return nullptr;
+    return (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }();
+  if (!encode) return cudaErrorNotSupported;
+  const cuuint64_t dims[4] = {(cuuint64_t)n[2], (cuuint64_t)n[1], (cuuint64_t)n[0], (cuuint64_t)nf};
+  const cuuint64_t row = (cuuint64_t)n2p * 4;
+  const cuuint64_t strides[3] = {row, row * n[1], row * n[1] * n[0]};
+  const cuuint32_t box[4] = {(cuuint32_t)bw, (cuuint32_t)bh, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int physics,
                          const tb_options* opt, tb_handle** out) {
   if (!out || !n || !hsp) return TB_EINVAL;
@@ -496,6 +519,11 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
     if (e == cudaSuccess) e = cudaMemsetAsync(h->efield, 0, 9 * fbytes, st);
     if (e == cudaSuccess) e = dmalloc(&h->emat, 8 * fbytes, st);
     if (e == cudaSuccess) e = dmalloc(&h->eta_dt, sizeof(float) * (n[0] + n[1] + n[2]), st);
+    const int rz = (so / 2 + 3) / 4 * 4;
+    if (e == cudaSuccess && !h->opt.elastic_plain)
+      e = make_tmap4(&h->ela_maps.fh, h->efield, n, h->n2p, 9, kEZ + 2 * rz, kEY + so);
+    if (e == cudaSuccess && !h->opt.elastic_plain) e = make_tmap4(&h->ela_maps.fo, h->efield, n, h->n2p, 9, kEZ, kEY);
+    if (e == cudaSuccess && !h->opt.elastic_plain) e = make_tmap4(&h->ela_maps.mo, h->emat, n, h->n2p, 8, kEZ, kEY);
   }
   if (e == cudaSuccess) e = dmalloc(&h->c2, fbytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->c2, 0, fbytes, st);
@@ -1232,6 +1260,15 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
   // fused TTI: chunks along axis 0 for about four CTAs per SM in all (one
   // CTA per SM fits), no chunk shorter than 8r planes (each computes the
   // fluxes of 2r planes beyond it)
+  // elastic: the TMA-staged updates (chunks for about twelve CTAs per SM
+  // in all, three fit at once; chunks no shorter than 4r planes), unless the
+  // L1 streaming kernels are asked for
+  const bool ela_tma = h->physics == TB_ELASTIC && !h->opt.elastic_plain;
+  const long long tmo = (long long)(h->opt.wait_timeout_s * 1e9);
+  const int64_t etiles = ((h->n[2] + kEZ - 1) / kEZ) * ((h->n[1] + kEY - 1) / kEY);
+  const int echunks = (int)std::max<int64_t>(
+      1, std::min<int64_t>(h->n[0] / (4 * h->R), (12 * (int64_t)h->num_sms + etiles - 1) / etiles));
+  if (ela_tma) TB_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(int), st));
   const int64_t ftiles = ((h->n[2] + 31) / 32) * ((h->n[1] + 7) / 8);
   const int fchunks = (int)std::max<int64_t>(
       1, std::min<int64_t>(h->n[0] / (8 * h->R), (4 * (int64_t)h->num_sms + ftiles - 1) / ftiles));
@@ -1288,8 +1325,10 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
         }
         cudaError_t e = fused ? tti_fused(h->R, g, w, 0, &L, nullptr, nullptr, nullptr, nullptr, h->c2, h->coef,
                                           h->nzb, h->damp_b, st)
-                              : wave_launch(h->physics, h->R, g, w, (float)h->dt, L, h->c2, h->coef, h->nzb,
-                                            h->damp_b, h->flux, h->efield, h->emat, h->eta_dt, st);
+                        : ela_tma ? elastic_tma(h->R, g, w, (float)h->dt, h->ela_maps, 0, 0, &L, h->efield,
+                                                h->eta_dt, tmo, h->err, st)
+                                  : wave_launch(h->physics, h->R, g, w, (float)h->dt, L, h->c2, h->coef, h->nzb,
+                                                h->damp_b, h->flux, h->efield, h->emat, h->eta_dt, st);
         if (h->opt.profile && eb) cudaEventRecord(eb, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "wavefront launch");
         if (P.n > 0) {
@@ -1358,7 +1397,15 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
       f0 = h->field[pc];
       f1 = h->field[rc];
     } else {
-      e = elastic_step(h->R, g, w, (float)h->dt, nchunks, h->efield, h->emat, h->eta_dt, st);
+      if (ela_tma) {
+        e = elastic_tma(h->R, g, w, (float)h->dt, h->ela_maps, 0, echunks, nullptr, h->efield, h->eta_dt, tmo,
+                        h->err, st);
+        if (e == cudaSuccess)
+          e = elastic_tma(h->R, g, w, (float)h->dt, h->ela_maps, 1, echunks, nullptr, h->efield, h->eta_dt, tmo,
+                          h->err, st);
+      } else {
+        e = elastic_step(h->R, g, w, (float)h->dt, nchunks, h->efield, h->emat, h->eta_dt, st);
+      }
       f0 = h->efield + 3 * Np;
       f1 = h->efield + 4 * Np;
       f2 = h->efield + 5 * Np;
@@ -1387,6 +1434,12 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
   h->cur_idx = pc;
   h->prev_idx = pp;
   h->last_nt = nt;
+  if (ela_tma && nt > 0) {
+    int err = 0;
+    TB_CUDA(h, cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TB_CUDA(h, cudaStreamSynchronize(st));
+    if (err) return fail(h, TB_ETIMEOUT, "an elastic update CTA timed out waiting for its staged operands");
+  }
   if (host_traces) {
     TB_CUDA(h, cudaMemcpyAsync(traces, h->traces_dev, sizeof(float) * (size_t)nt * nrec, cudaMemcpyDeviceToHost, st));
     TB_CUDA(h, cudaStreamSynchronize(st));

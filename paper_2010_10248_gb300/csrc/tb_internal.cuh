@@ -190,6 +190,19 @@ cudaError_t wave_post(const PhysGrid& g, const WavePosts& P, int64_t nsrc_pts, c
 cudaError_t tti_fused(int R, const PhysGrid& g, const DerivW& w, int nchunks, const WaveItems* L, const float* pc,
                       float* pp, const float* rc, float* rp, const float* c2, const float* coef, const float* nz,
                       const float* damp_b, cudaStream_t st);
+// Elastic velocity (kind 0) / stress (kind 1) update with TMA-staged
+// operands (tb_physics.cu): kEY x kEZ tiles, chunks along axis 0 (L null)
+// or the items of one wavefront launch.  A stalled copy sets *err after
+// `tmo` ns.
+constexpr int kEY = 8, kEZ = 32;
+struct ElaMaps {
+  CUtensorMap fh;  // the nine fields [9][n0][n1][n2p], (kEZ + 2 rz) x (kEY + 2r) boxes, rz = r rounded up to 4
+  CUtensorMap fo;  // the nine fields, kEZ x kEY boxes
+  CUtensorMap mo;  // the eight material fields, kEZ x kEY boxes
+};
+cudaError_t elastic_tma(int R, const PhysGrid& g, const DerivW& w, float dt, const ElaMaps& M, int kind,
+                        int nchunks, const WaveItems* L, float* f, const float* eta_dt, long long tmo, int* err,
+                        cudaStream_t st);
 // items (launch, sub-update, x0, x1) of the wavefront over n0 planes in slabs
 // of `slab` planes for U sub-updates, launches in order; -1 on bad arguments
 int wave_plan(int n0, int slab, int U, std::vector<int>* items);

@@ -27,6 +27,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "tb_async.cuh"
 #include "tb_internal.cuh"
 
 namespace tbi {
@@ -562,6 +563,233 @@ __global__ void __launch_bounds__(256, 4) k_ela_stress(PhysGrid g, DerivW w, flo
   ela_stress_cols<R>(g, w, c, dt, x0, x1, f, mat, eta_dt);
 }
 
+// ------------------------------------------------- elastic, TMA-staged --
+// The velocity and stress updates with every operand staged by TMA: a CTA
+// owns a kEY x kEZ tile (one compute thread per column) and streams a range
+// of planes; a producer warp loads, per plane x, the planes the axis-1/2
+// derivatives read (with an r-cell halo, zeros outside the grid), the
+// plane x + r of the three fields differentiated along axis 0 (the head of
+// each column's register queue), the fields updated in place and the
+// material, into a ring of stages several planes ahead of the compute
+// warps.  The per-point arithmetic is that of k_ela_velocity / k_ela_stress
+// (same operations in the same order), so the results are bit for bit
+// those of the plain kernels.
+template <int R>
+struct ElaCfg {
+  static constexpr int RZ = (R + 3) / 4 * 4;  // axis-2 halo rounded to 16 bytes (TMA)
+  static constexpr int HH = kEY + 2 * R, HW = kEZ + 2 * RZ;
+  static constexpr int HALO = HH * HW, OWN = kEY * kEZ;
+  // velocity: halo planes txy tyy tyz txz tzz (x); own planes txx txy txz
+  // (x + r), vx vy vz, bx by bz (x).  Stress: halo planes vx vy vz (x); own
+  // planes vx vy vz (x + r), txx .. tyz, lam mu mxy mxz myz (x).
+  static constexpr int NHV = 5, NOV = 9, NHS = 3, NOS = 14;
+  static constexpr int SV = NHV * HALO + NOV * OWN, SS = NHS * HALO + NOS * OWN;
+  static constexpr int STAGE = SV > SS ? SV : SS;  // floats
+  static constexpr int NST = 3;                    // stages in flight
+  static constexpr int NT = kEY * kEZ + 32;        // compute warps + producer warp
+  static constexpr int MINB = R <= 4 ? 3 : 2;      // CTAs per SM the shared memory allows
+  static constexpr int SMEM = 4 * NST * STAGE + 16 * NST + 128;  // + alignment of the ring to 128 B
+  static_assert(HALO % 32 == 0 && OWN % 32 == 0 && STAGE % 32 == 0, "128-byte aligned TMA boxes");
+  static constexpr unsigned BYTES_V = 4u * SV, BYTES_S = 4u * SS;
+};
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// staggered derivative along axis 1 or 2 of a shared plane (pitch `step`
+// between neighbours): the sums of dstag<R, 1 | 2>
+template <int R>
+__device__ __forceinline__ float dstag_s(const float* f, int c, int step, const float* cw, bool plus) {
+  float s = 0.f;
+#pragma unroll
+  for (int k = R; k >= 1; --k) {
+    const int hi = plus ? k : k - 1, lo = plus ? -(k - 1) : -k;
+    s = __fmaf_rn(cw[k - 1], __fsub_rn(f[c + hi * step], f[c + lo * step]), s);
+  }
+  return s;
+}
+
+// kind 0: velocity, 1: stress, on planes [x0, x1) of the tile at (y0, z0)
+template <int R>
+__device__ __forceinline__ void ela_tma_tile(const PhysGrid& g, const DerivW& w, float dt, const ElaMaps& M,
+                                             int kind, int y0, int z0, int x0, int x1, float* __restrict__ f,
+                                             const float* __restrict__ eta_dt, float* ring, uint64_t* full,
+                                             uint64_t* empty, long long tmo, int* err) {
+  using C = ElaCfg<R>;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int nsteps = x1 - x0;
+  if (warp == kEY) {
+    // ============================ producer warp ============================
+    if (lane != 0) return;
+    int issued = 0;
+    bool ok = true;
+    for (int i = 0; i < nsteps && ok; ++i) {
+      const int st = i % C::NST, x = x0 + i;
+      if (i >= C::NST && !mbar_wait(&empty[st], ((i / C::NST) - 1) & 1, tmo)) {
+        atomicExch(err, 1);
+        ok = false;
+        break;
+      }
+      float* base = ring + (size_t)st * C::STAGE;
+      uint64_t* bar = &full[st];
+      if (kind == 0) {
+        mbar_expect_tx(bar, C::BYTES_V);
+        const int hf[5] = {6, 4, 8, 7, 5};  // txy tyy tyz txz tzz
+#pragma unroll
+        for (int k = 0; k < 5; ++k) tma_load_4d(base + k * C::HALO, &M.fh, bar, z0 - C::RZ, y0 - R, x, hf[k]);
+        float* own = base + C::NHV * C::HALO;
+        const int qf[3] = {3, 6, 7};  // txx txy txz at x + r
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tma_load_4d(own + k * C::OWN, &M.fo, bar, z0, y0, x + R, qf[k]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tma_load_4d(own + (3 + k) * C::OWN, &M.fo, bar, z0, y0, x, k);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tma_load_4d(own + (6 + k) * C::OWN, &M.mo, bar, z0, y0, x, k);
+      } else {
+        mbar_expect_tx(bar, C::BYTES_S);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tma_load_4d(base + k * C::HALO, &M.fh, bar, z0 - C::RZ, y0 - R, x, k);
+        float* own = base + C::NHS * C::HALO;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tma_load_4d(own + k * C::OWN, &M.fo, bar, z0, y0, x + R, k);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) tma_load_4d(own + (3 + k) * C::OWN, &M.fo, bar, z0, y0, x, 3 + k);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) tma_load_4d(own + (9 + k) * C::OWN, &M.mo, bar, z0, y0, x, 3 + k);
+      }
+      issued = i + 1;
+    }
+    // copies still in flight complete on their stages' full barriers
+    for (int i = (issued > C::NST ? issued - C::NST : 0); i < issued; ++i)
+      mbar_wait(&full[i % C::NST], (i / C::NST) & 1, tmo);
+    return;
+  }
+  // ============================= compute warps =============================
+  const int ey = warp, ez = lane;
+  const int y = y0 + ey, z = z0 + ez;
+  const bool in = y < g.n1 && z < g.n2;
+  const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
+  const size_t col = (size_t)(in ? y : 0) * g.n2p + (in ? z : 0);
+  const int ch = (ey + R) * C::HW + ez + C::RZ, co = ey * kEZ + ez;
+  // axis-0 queues (planes x - r .. x + r) of txx txy txz (velocity) or vx vy vz (stress)
+  const float* q0 = f + (kind == 0 ? 3 * Np : 0);
+  const float* q1 = f + (kind == 0 ? 6 * Np : Np);
+  const float* q2 = f + (kind == 0 ? 7 * Np : 2 * Np);
+  float qa[2 * R + 1], qb[2 * R + 1], qc[2 * R + 1];
+  qa[0] = qb[0] = qc[0] = 0.f;  // shifted out before its first use
+  const int yc = in ? y : 0, zc = in ? z : 0;
+#pragma unroll
+  for (int s = 1; s < 2 * R + 1; ++s) {  // planes x0 - r .. x0 + r - 1 before the first shift
+    qa[s] = in ? ld0(g, q0, x0 - 1 - R + s, yc, zc) : 0.f;
+    qb[s] = in ? ld0(g, q1, x0 - 1 - R + s, yc, zc) : 0.f;
+    qc[s] = in ? ld0(g, q2, x0 - 1 - R + s, yc, zc) : 0.f;
+  }
+  const float eyz_y = __ldg(eta_dt + g.n0 + (in ? y : 0)), eyz_z = __ldg(eta_dt + g.n0 + g.n1 + (in ? z : 0));
+  for (int i = 0; i < nsteps; ++i) {
+    const int st = i % C::NST, x = x0 + i;
+    const bool ok = mbar_wait(&full[st], (i / C::NST) & 1, tmo);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) atomicExch(err, 1);
+      break;
+    }
+    const float* base = ring + (size_t)st * C::STAGE;
+#pragma unroll
+    for (int s = 0; s < 2 * R; ++s) {
+      qa[s] = qa[s + 1];
+      qb[s] = qb[s + 1];
+      qc[s] = qc[s + 1];
+    }
+    const float den = __fadd_rn(1.f, __fadd_rn(__fadd_rn(__ldg(eta_dt + x), eyz_y), eyz_z));
+    const size_t i0 = (size_t)x * g.n1 * g.n2p + col;
+    if (kind == 0) {
+      const float* own = base + C::NHV * C::HALO;
+      qa[2 * R] = own[co];
+      qb[2 * R] = own[C::OWN + co];
+      qc[2 * R] = own[2 * C::OWN + co];
+      const float *txy = base, *tyy = base + C::HALO, *tyz = base + 2 * C::HALO, *txz = base + 3 * C::HALO,
+                  *tzz = base + 4 * C::HALO;
+      const float fx = __fadd_rn(__fadd_rn(dstag_q<R>(qa, w.a[0], true), dstag_s<R>(txy, ch, C::HW, w.a[1], false)),
+                                 dstag_s<R>(txz, ch, 1, w.a[2], false));
+      const float fy = __fadd_rn(__fadd_rn(dstag_q<R>(qb, w.a[0], false), dstag_s<R>(tyy, ch, C::HW, w.a[1], true)),
+                                 dstag_s<R>(tyz, ch, 1, w.a[2], false));
+      const float fz = __fadd_rn(__fadd_rn(dstag_q<R>(qc, w.a[0], false), dstag_s<R>(tyz, ch, C::HW, w.a[1], false)),
+                                 dstag_s<R>(tzz, ch, 1, w.a[2], true));
+      const float vx = own[3 * C::OWN + co], vy = own[4 * C::OWN + co], vz = own[5 * C::OWN + co];
+      const float bx = own[6 * C::OWN + co], by = own[7 * C::OWN + co], bz = own[8 * C::OWN + co];
+      if (in) {
+        f[i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, bx), fx, vx), den);
+        f[Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, by), fy, vy), den);
+        f[2 * Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, bz), fz, vz), den);
+      }
+    } else {
+      const float* own = base + C::NHS * C::HALO;
+      qa[2 * R] = own[co];
+      qb[2 * R] = own[C::OWN + co];
+      qc[2 * R] = own[2 * C::OWN + co];
+      const float *vxp = base, *vyp = base + C::HALO, *vzp = base + 2 * C::HALO;
+      const float exx = dstag_q<R>(qa, w.a[0], false);
+      const float eyy = dstag_s<R>(vyp, ch, C::HW, w.a[1], false);
+      const float ezz = dstag_s<R>(vzp, ch, 1, w.a[2], false);
+      const float gxy = __fadd_rn(dstag_s<R>(vxp, ch, C::HW, w.a[1], true), dstag_q<R>(qb, w.a[0], true));
+      const float gxz = __fadd_rn(dstag_s<R>(vxp, ch, 1, w.a[2], true), dstag_q<R>(qc, w.a[0], true));
+      const float gyz = __fadd_rn(dstag_s<R>(vyp, ch, 1, w.a[2], true), dstag_s<R>(vzp, ch, C::HW, w.a[1], true));
+      const float lam = own[9 * C::OWN + co], mu = own[10 * C::OWN + co];
+      const float ltr = __fmul_rn(lam, __fadd_rn(__fadd_rn(exx, eyy), ezz));
+      const float mu2 = __fmul_rn(2.f, mu);
+      const float sxx = own[3 * C::OWN + co], syy = own[4 * C::OWN + co], szz = own[5 * C::OWN + co];
+      const float sxy = own[6 * C::OWN + co], sxz = own[7 * C::OWN + co], syz = own[8 * C::OWN + co];
+      const float mxy = own[11 * C::OWN + co], mxz = own[12 * C::OWN + co], myz = own[13 * C::OWN + co];
+      if (in) {
+        f[3 * Np + i0] = div_sponge(__fmaf_rn(dt, __fmaf_rn(mu2, exx, ltr), sxx), den);
+        f[4 * Np + i0] = div_sponge(__fmaf_rn(dt, __fmaf_rn(mu2, eyy, ltr), syy), den);
+        f[5 * Np + i0] = div_sponge(__fmaf_rn(dt, __fmaf_rn(mu2, ezz, ltr), szz), den);
+        f[6 * Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, mxy), gxy, sxy), den);
+        f[7 * Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, mxz), gxz, sxz), den);
+        f[8 * Np + i0] = div_sponge(__fmaf_rn(__fmul_rn(dt, myz), gyz, syz), den);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+  }
+}
+
+// one-step (L.n == 0: `kind` over nchunks chunks of planes) or wavefront items
+template <int R>
+__global__ void __launch_bounds__(ElaCfg<R>::NT, ElaCfg<R>::MINB)
+    k_ela_tma(PhysGrid g, DerivW w, float dt, const __grid_constant__ ElaMaps M, int kind, int nchunks,
+              const WaveItems L, float* f, const float* __restrict__ eta_dt, long long tmo, int* err) {
+  using C = ElaCfg<R>;
+  extern __shared__ float4 ela_smem4[];
+  float* ring = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(ela_smem4) + 127) & ~uintptr_t(127));
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)C::NST * C::STAGE);
+  uint64_t* empty = full + C::NST;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < C::NST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kEY);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int x0, x1;
+  if (L.n == 0) {
+    chunk_planes(g, nchunks, x0, x1);
+  } else {
+    const WaveItem& it = L.it[blockIdx.z];
+    kind = it.kind;
+    x0 = it.x0;
+    x1 = it.x1;
+  }
+  ela_tma_tile<R>(g, w, dt, M, kind, blockIdx.y * kEY, blockIdx.x * kEZ, x0, x1, f, eta_dt, ring, full, empty, tmo,
+                  err);
+}
+
 // material at the staggered positions from vp, vs, rho (dense [N]):
 // b = 1/rho at half-nodes (mean of two nodes), lam, mu at nodes, mu at edge
 // centres (harmonic mean of four nodes, 0 if one is 0); a neighbour past
@@ -847,6 +1075,37 @@ cudaError_t wave_post(const PhysGrid& g, const WavePosts& P, int64_t nsrc_pts, c
     k_wave_sample<<<dim3(grid_for(nrec_pts, 128), P.n), 128, 0, st>>>(g, nrec_pts, rec_ent, rec_lin, P);
   }
   return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t ela_tma_r(const PhysGrid& g, const DerivW& w, float dt, const ElaMaps& M, int kind, int nchunks,
+                             const WaveItems* L, float* f, const float* eta_dt, long long tmo, int* err,
+                             cudaStream_t st) {
+  using C = ElaCfg<R>;
+  static bool attr = false;  // more than 48 KB of shared memory needs the opt-in
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_ela_tma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  WaveItems none{};
+  const dim3 grid((unsigned)((g.n2 + kEZ - 1) / kEZ), (unsigned)((g.n1 + kEY - 1) / kEY),
+                  (unsigned)(L ? L->n : nchunks));
+  count_launch();
+  k_ela_tma<R><<<grid, C::NT, C::SMEM, st>>>(g, w, dt, M, kind, nchunks, L ? *L : none, f, eta_dt, tmo, err);
+  return cudaGetLastError();
+}
+
+cudaError_t elastic_tma(int R, const PhysGrid& g, const DerivW& w, float dt, const ElaMaps& M, int kind,
+                        int nchunks, const WaveItems* L, float* f, const float* eta_dt, long long tmo, int* err,
+                        cudaStream_t st) {
+  if (L && (L->n < 1 || L->n > kWaveItemsMax)) return cudaErrorInvalidValue;
+  switch (R) {
+    case 2: return ela_tma_r<2>(g, w, dt, M, kind, nchunks, L, f, eta_dt, tmo, err, st);
+    case 4: return ela_tma_r<4>(g, w, dt, M, kind, nchunks, L, f, eta_dt, tmo, err, st);
+    case 6: return ela_tma_r<6>(g, w, dt, M, kind, nchunks, L, f, eta_dt, tmo, err, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t elastic_material(const PhysGrid& g, const float* vp, const float* vs, const float* rho, float* mat,

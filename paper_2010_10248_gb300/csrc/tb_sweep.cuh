@@ -70,6 +70,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "tb_async.cuh"
 #include "tb_internal.cuh"
 
 namespace tbi {
@@ -165,116 +166,6 @@ struct SweepCfg {
   static_assert(TY % 2 == 0 && TY >= 2 * R && TZ >= RP, "tile too small for the stencil radius");
   static_assert(SMEM <= 232448, "shared memory budget exceeded");
 };
-
-// ---------------------------------------------------------------- PTX ----
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ void st_release_cta_s32(int* p, int v) {
-  asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
-}
-__device__ __forceinline__ int ld_acquire_cta_s32(const int* p) {
-  int v;
-  asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
-  return v;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-// raise the phase's expected transaction bytes without arriving
-__device__ __forceinline__ void mbar_expect_tx_only(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-// try_wait suspends the warp until the phase completes or ~20 us pass, so a
-// waiting warp sleeps instead of spending issue slots on polling.
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait on an mbarrier phase; false when the time limit ran out.
-// The first try is inline; the polling loop is kept out of the hot path.
-static __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, unsigned parity, long long timeout_ns) {
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if ((long long)(global_ns() - t0) > timeout_ns) return false;
-  return true;
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long timeout_ns) {
-  return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, timeout_ns);
-}
-// Poll without suspending (one thread; a nanosleep between tries).
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_poll(uint64_t* bar, unsigned parity, long long timeout_ns) {
-  if (mbar_test(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_test(bar, parity)) {
-    if ((long long)(global_ns() - t0) > timeout_ns) return false;
-    __nanosleep(20);
-  }
-  return true;
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
-                                            int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-      : "memory");
-}
-// Non-tensor bulk copy global -> shared (16-byte aligned, size multiple of 16).
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Spin (one thread) until *flag >= target, at most timeout_ns after t0 and
-// at most 2^26 polls.  Returns false when the limit ran out.
-__device__ __forceinline__ bool bounded_wait_ge(const unsigned long long* flag,
-                                                unsigned long long target, unsigned long long t0,
-                                                long long timeout_ns) {
-  long long spins = 0;
-  while (ld_acquire_u64(flag) < target) {
-    if (++spins > (1ll << 26) || (long long)(global_ns() - t0) > timeout_ns) return false;
-    __nanosleep(32);
-  }
-  return true;
-}
 
 __device__ __forceinline__ int j_mod(int j, int d) { return j % d; }
 

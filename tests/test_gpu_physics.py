@@ -136,7 +136,7 @@ def _run(tb, physics, case, so, nt, schedule, **opt):
     return tr, [p.field(i).cpu().numpy() for i in range(nf)]
 
 
-@pytest.mark.parametrize("physics", ["tti", "tti_fused", "elastic"])
+@pytest.mark.parametrize("physics", ["tti", "tti_fused", "elastic", "elastic_plain"])
 @pytest.mark.parametrize("shape,so,T,slab,nt", [((30, 33, 40), 4, 2, 0, 23), ((37, 31, 36), 8, 3, 4, 20),
                                                 ((29, 33, 35), 8, 2, 5, 17), ((41, 29, 35), 12, 2, 6, 15),
                                                 ((33, 30, 34), 4, 8, 3, 19), ((19, 30, 34), 8, 4, 0, 13)])
@@ -144,13 +144,14 @@ def test_blocked_bitwise_equals_onestep(tb, physics, shape, so, T, slab, nt):
     """Ragged slabs (n0 not a multiple of the slab), nt not a multiple of T
     (the rest one step per launch), sources on the first and last planes.
     The fused TTI step reaches 2r planes, so its slabs are at least so."""
-    phys = tb.TB_ELASTIC if physics == "elastic" else tb.TB_TTI
-    fused = physics == "tti_fused"
-    if fused and slab:
+    ela = physics.startswith("elastic")
+    phys = tb.TB_ELASTIC if ela else tb.TB_TTI
+    opt = dict(tti_fused=physics == "tti_fused", elastic_plain=physics == "elastic_plain")
+    if opt["tti_fused"] and slab:
         slab = max(slab, so)
-    case = (elastic_case(shape, so, 400 + so) if physics == "elastic" else tti_case(shape, so, 300 + so, nt))
-    ref_tr, ref_f = _run(tb, phys, case, so, nt, "onestep", tti_fused=fused)
-    got_tr, got_f = _run(tb, phys, case, so, nt, "blocked", time_tile=T, slab_planes=slab, tti_fused=fused)
+    case = (elastic_case(shape, so, 400 + so) if ela else tti_case(shape, so, 300 + so, nt))
+    ref_tr, ref_f = _run(tb, phys, case, so, nt, "onestep", **opt)
+    got_tr, got_f = _run(tb, phys, case, so, nt, "blocked", time_tile=T, slab_planes=slab, **opt)
     assert np.abs(ref_tr).max() > 0
     assert np.array_equal(got_tr, ref_tr)
     for a, b in zip(got_f, ref_f):
@@ -166,6 +167,22 @@ def test_tti_fused_step_equals_two_pass(tb, shape, so):
     case = tti_case(shape, so, 500 + so, nt)
     ref_tr, ref_f = _run(tb, tb.TB_TTI, case, so, nt, "onestep")
     got_tr, got_f = _run(tb, tb.TB_TTI, case, so, nt, "onestep", tti_fused=True)
+    assert np.abs(ref_tr).max() > 0
+    assert np.array_equal(got_tr, ref_tr)
+    for a, b in zip(got_f, ref_f):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("shape,so", [((30, 33, 40), 4), ((70, 19, 71), 8), ((45, 26, 33), 12), ((96, 40, 66), 8)])
+def test_elastic_tma_equals_plain(tb, shape, so):
+    """The TMA-staged elastic updates (8 x 32 tiles, chunks along axis 0,
+    halos and out-of-grid cells filled by the copy engine) against the L1
+    streaming kernels: traces and every field bit for bit, on grids with
+    ragged tiles and several chunks."""
+    nt = 21
+    case = elastic_case(shape, so, 600 + so)
+    ref_tr, ref_f = _run(tb, tb.TB_ELASTIC, case, so, nt, "onestep", elastic_plain=True)
+    got_tr, got_f = _run(tb, tb.TB_ELASTIC, case, so, nt, "onestep")
     assert np.abs(ref_tr).max() > 0
     assert np.array_equal(got_tr, ref_tr)
     for a, b in zip(got_f, ref_f):

@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--wave-tile", type=int, default=4, help="TTI / elastic: steps per wavefront")
     ap.add_argument("--slab", type=int, default=0, help="TTI / elastic: planes per wavefront slab (0: auto)")
     ap.add_argument("--tti-fused", action="store_true", help="TTI: both passes of a step in one kernel")
-    ap.add_argument("--elastic-plain", action="store_true", help="elastic: the L1 streaming kernels")
+    ap.add_argument("--stream-l1", action="store_true", help="TTI / elastic: the L1 streaming kernels")
     ap.add_argument("--physics", default="acoustic", choices=["acoustic", "tti", "elastic"],
                     help="tti / elastic: the 384^3 so8 500-step TTI or elastic workload, one-step "
                          "schedule (the headline line is the acoustic one)")
@@ -538,7 +538,7 @@ def run_physics(args):
     vp = torch.from_numpy(w.vp).to(dev)
     aux = torch.from_numpy(np.stack(w.meta["aux"])).to(dev)
     prop = tb.Propagator(w.shape, w.spacing, w.so, physics=phys, nbl=w.nbl, profile=True, time_tile=T,
-                         slab_planes=args.slab, tti_fused=args.tti_fused, elastic_plain=args.elastic_plain)
+                         slab_planes=args.slab, tti_fused=args.tti_fused, stream_l1=args.stream_l1)
     st = torch.cuda.current_stream()
     prop.set_model(vp, aux=aux)
     dt = prop.dt
@@ -600,9 +600,8 @@ def run_physics(args):
             "config": {"workload": w.name, "grid": list(w.shape), "space_order": w.so, "nt": nt,
                        "receivers": len(w.rec_xyz), "schedule": "blocked", "time_tile": T,
                        "slab_planes": args.slab or 32,
-                       "tti_step": ("fused" if args.tti_fused else "two kernels") if args.physics == "tti" else None,
-                       "elastic_step": ("L1 streaming" if args.elastic_plain else "TMA-staged")
-                       if args.physics == "elastic" else None,
+                       "passes": "fused (TTI)" if args.tti_fused else ("L1 streaming" if args.stream_l1
+                                                                       else "TMA-staged"),
                        "l2": "inputs larger than L2",
                        "step": "set_model + set_sources + set_receivers + forward(nt)"},
             "gpu_launches": launches_b, "clocks": clk,

@@ -122,7 +122,7 @@ typedef struct {
                       same values bit for bit, 6 fields less device memory,
                       48 B less memory traffic per point and step, slower on
                       GB300: one CTA per SM with two barriers per plane)        */
-  int elastic_plain; /* TB_ELASTIC: 0 (default) velocity and stress updates with
+  int stream_l1;   /* TB_TTI (two-pass) / TB_ELASTIC: 0 (default) passes with
                       every operand staged in shared memory by TMA; 1: the
                       streaming kernels that read axis-1/2 neighbours through
                       the L1 cache (the same values bit for bit)                */

@@ -40,14 +40,14 @@ class Propagator:
 
     def __init__(self, shape, spacing, space_order, *, physics=TB_ACOUSTIC, time_tile=0, nbl=0,
                  y_bands=0, x_chunks=0, profile=False, check_nan=False, wait_timeout_s=0.0,
-                 storage=TB_F32, band_ctas=0, slab_planes=0, tti_fused=False, elastic_plain=False):
+                 storage=TB_F32, band_ctas=0, slab_planes=0, tti_fused=False, stream_l1=False):
         import torch
         self._torch = torch
         opt = Options(time_tile=time_tile, nbl=nbl, y_bands=y_bands, x_chunks=x_chunks,
                       profile=int(profile), check_nan=int(check_nan),
                       wait_timeout_s=float(wait_timeout_s), storage=int(storage), band_ctas=int(band_ctas),
                       slab_planes=int(slab_planes), tti_fused=int(tti_fused),
-                      elastic_plain=int(elastic_plain))
+                      stream_l1=int(stream_l1))
         self.shape = tuple(int(s) for s in shape)
         self.spacing = tuple(float(s) for s in spacing)
         self.space_order = int(space_order)

@@ -37,7 +37,7 @@ class Options(C.Structure):
                 ("x_chunks", C.c_int), ("profile", C.c_int), ("check_nan", C.c_int),
                 ("wait_timeout_s", C.c_double), ("storage", C.c_int), ("band_ctas", C.c_int),
                 ("slab_planes", C.c_int), ("tti_fused", C.c_int),
-                ("elastic_plain", C.c_int)]
+                ("stream_l1", C.c_int)]
 
 
 _lib = None

@@ -104,6 +104,7 @@ struct tb_handle {
   CUtensorMap tm_tile[4];  // own tiles, per field buffer
   CUtensorMap tm_c2;       // own tiles of c2
   ElaMaps ela_maps;        // elastic fields and material for the TMA-staged updates
+  TtiMaps tti_maps;        // TTI fields, fluxes and coefficients for the TMA-staged passes
   float* damp_b = nullptr;
   // other physics (Sec. III-B/C): physics id, TTI coefficients [2][Np]
   // (1+2eps, sqrt(1+2delta)), symmetry axis [3][Np], fluxes [6][Np];
@@ -520,13 +521,26 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
     if (e == cudaSuccess) e = dmalloc(&h->emat, 8 * fbytes, st);
     if (e == cudaSuccess) e = dmalloc(&h->eta_dt, sizeof(float) * (n[0] + n[1] + n[2]), st);
     const int rz = (so / 2 + 3) / 4 * 4;
-    if (e == cudaSuccess && !h->opt.elastic_plain)
+    if (e == cudaSuccess && !h->opt.stream_l1)
       e = make_tmap4(&h->ela_maps.fh, h->efield, n, h->n2p, 9, kEZ + 2 * rz, kEY + so);
-    if (e == cudaSuccess && !h->opt.elastic_plain) e = make_tmap4(&h->ela_maps.fo, h->efield, n, h->n2p, 9, kEZ, kEY);
-    if (e == cudaSuccess && !h->opt.elastic_plain) e = make_tmap4(&h->ela_maps.mo, h->emat, n, h->n2p, 8, kEZ, kEY);
+    if (e == cudaSuccess && !h->opt.stream_l1) e = make_tmap4(&h->ela_maps.fo, h->efield, n, h->n2p, 9, kEZ, kEY);
+    if (e == cudaSuccess && !h->opt.stream_l1) e = make_tmap4(&h->ela_maps.mo, h->emat, n, h->n2p, 8, kEZ, kEY);
   }
   if (e == cudaSuccess) e = dmalloc(&h->c2, fbytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->c2, 0, fbytes, st);
+  if (physics == TB_TTI && !h->opt.tti_fused && !h->opt.stream_l1) {
+    const int rz = (so / 2 + 3) / 4 * 4;
+    TtiMaps& M = h->tti_maps;
+    for (int i = 0; i < nfield && e == cudaSuccess; ++i) {
+      e = make_tmap(&M.bh[i], h->field[i], n, h->n2p, kEZ + 2 * rz, kEY + so);
+      if (e == cudaSuccess) e = make_tmap(&M.bo[i], h->field[i], n, h->n2p, kEZ, kEY);
+    }
+    if (e == cudaSuccess) e = make_tmap4(&M.fh, h->flux, n, h->n2p, 6, kEZ + 2 * rz, kEY + so);
+    if (e == cudaSuccess) e = make_tmap4(&M.fo, h->flux, n, h->n2p, 6, kEZ, kEY);
+    if (e == cudaSuccess) e = make_tmap4(&M.nzo, h->nzb, n, h->n2p, 3, kEZ, kEY);
+    if (e == cudaSuccess) e = make_tmap(&M.co, h->c2, n, h->n2p, kEZ, kEY);
+    if (e == cudaSuccess) e = make_tmap4(&M.ko, h->coef, n, h->n2p, 2, kEZ, kEY);
+  }
   if (e == cudaSuccess) e = dmalloc(&h->damp_b, sizeof(float) * (n[0] + n[1] + n[2]), st);
   if (e == cudaSuccess) e = dmalloc(&h->err, sizeof(int) * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int) * 4, st);
@@ -1263,12 +1277,13 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
   // elastic: the TMA-staged updates (chunks for about twelve CTAs per SM
   // in all, three fit at once; chunks no shorter than 4r planes), unless the
   // L1 streaming kernels are asked for
-  const bool ela_tma = h->physics == TB_ELASTIC && !h->opt.elastic_plain;
+  const bool ela_tma = h->physics == TB_ELASTIC && !h->opt.stream_l1;
+  const bool tti_tma_on = h->physics == TB_TTI && !h->opt.stream_l1 && !h->opt.tti_fused;
   const long long tmo = (long long)(h->opt.wait_timeout_s * 1e9);
   const int64_t etiles = ((h->n[2] + kEZ - 1) / kEZ) * ((h->n[1] + kEY - 1) / kEY);
   const int echunks = (int)std::max<int64_t>(
       1, std::min<int64_t>(h->n[0] / (4 * h->R), (12 * (int64_t)h->num_sms + etiles - 1) / etiles));
-  if (ela_tma) TB_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(int), st));
+  if (ela_tma || tti_tma_on) TB_CUDA(h, cudaMemsetAsync(h->err, 0, sizeof(int), st));
   const int64_t ftiles = ((h->n[2] + 31) / 32) * ((h->n[1] + 7) / 8);
   const int fchunks = (int)std::max<int64_t>(
       1, std::min<int64_t>(h->n[0] / (8 * h->R), (4 * (int64_t)h->num_sms + ftiles - 1) / ftiles));
@@ -1290,10 +1305,14 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
         it.x0 = plan[i + 2];
         it.x1 = plan[i + 3];
         if (h->physics == TB_TTI) {
-          it.a = h->field[pcur[k & 1]];
-          it.b = h->field[pcur[(k + 1) & 1]];
-          it.c = h->field[rcur[k & 1]];
-          it.d = h->field[rcur[(k + 1) & 1]];
+          it.ia = pcur[k & 1];
+          it.ib = pcur[(k + 1) & 1];
+          it.ic = rcur[k & 1];
+          it.id = rcur[(k + 1) & 1];
+          it.a = h->field[it.ia];
+          it.b = h->field[it.ib];
+          it.c = h->field[it.ic];
+          it.d = h->field[it.id];
         }
         if (it.kind == 1 && (src_on || rec_on)) {
           WavePost& q = P.it[P.n++];
@@ -1327,6 +1346,8 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
                                           h->nzb, h->damp_b, st)
                         : ela_tma ? elastic_tma(h->R, g, w, (float)h->dt, h->ela_maps, 0, 0, &L, h->efield,
                                                 h->eta_dt, tmo, h->err, st)
+                        : tti_tma_on ? tti_tma(h->R, g, w, h->tti_maps, 0, nullptr, &L, h->flux, h->damp_b, tmo,
+                                               h->err, st)
                                   : wave_launch(h->physics, h->R, g, w, (float)h->dt, L, h->c2, h->coef, h->nzb,
                                                 h->damp_b, h->flux, h->efield, h->emat, h->eta_dt, st);
         if (h->opt.profile && eb) cudaEventRecord(eb, st);
@@ -1388,10 +1409,27 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
       continue;
     }
     if (h->physics == TB_TTI) {
-      e = fused ? tti_fused(h->R, g, w, fchunks, nullptr, h->field[pc], h->field[pp], h->field[rc], h->field[rp],
-                            h->c2, h->coef, h->nzb, h->damp_b, st)
-                : tti_step(h->R, g, w, nchunks, h->field[pc], h->field[pp], h->field[rc], h->field[rp], h->c2,
-                           h->coef, h->nzb, h->damp_b, h->flux, st);
+      if (fused) {
+        e = tti_fused(h->R, g, w, fchunks, nullptr, h->field[pc], h->field[pp], h->field[rc], h->field[rp], h->c2,
+                      h->coef, h->nzb, h->damp_b, st);
+      } else if (tti_tma_on) {
+        WaveItem one{};
+        one.ia = pc;
+        one.ib = pp;
+        one.ic = rc;
+        one.id = rp;
+        one.a = h->field[pc];
+        one.b = h->field[pp];
+        one.c = h->field[rc];
+        one.d = h->field[rp];
+        e = tti_tma(h->R, g, w, h->tti_maps, echunks, &one, nullptr, h->flux, h->damp_b, tmo, h->err, st);
+        one.kind = 1;
+        if (e == cudaSuccess)
+          e = tti_tma(h->R, g, w, h->tti_maps, echunks, &one, nullptr, h->flux, h->damp_b, tmo, h->err, st);
+      } else {
+        e = tti_step(h->R, g, w, nchunks, h->field[pc], h->field[pp], h->field[rc], h->field[rp], h->c2, h->coef,
+                     h->nzb, h->damp_b, h->flux, st);
+      }
       std::swap(pc, pp);
       std::swap(rc, rp);
       f0 = h->field[pc];
@@ -1434,11 +1472,11 @@ static int forward_other(tb_handle* h, int nt, float* traces, int schedule, cuda
   h->cur_idx = pc;
   h->prev_idx = pp;
   h->last_nt = nt;
-  if (ela_tma && nt > 0) {
+  if ((ela_tma || tti_tma_on) && nt > 0) {
     int err = 0;
     TB_CUDA(h, cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     TB_CUDA(h, cudaStreamSynchronize(st));
-    if (err) return fail(h, TB_ETIMEOUT, "an elastic update CTA timed out waiting for its staged operands");
+    if (err) return fail(h, TB_ETIMEOUT, "a TTI / elastic CTA timed out waiting for its staged operands");
   }
   if (host_traces) {
     TB_CUDA(h, cudaMemcpyAsync(traces, h->traces_dev, sizeof(float) * (size_t)nt * nrec, cudaMemcpyDeviceToHost, st));

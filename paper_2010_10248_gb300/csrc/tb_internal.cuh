@@ -164,6 +164,7 @@ struct WaveItem {
   float* b;        // TTI: p^{n-1}, overwritten by p^{n+1} (kind 1)
   const float* c;  // TTI: r^n
   float* d;        // TTI: r^{n-1}, overwritten by r^{n+1}
+  int ia, ib, ic, id;  // TTI: the field buffers (0..3) of a, b, c, d, for their tensor maps
 };
 struct WaveItems {
   int n;
@@ -203,6 +204,20 @@ struct ElaMaps {
 cudaError_t elastic_tma(int R, const PhysGrid& g, const DerivW& w, float dt, const ElaMaps& M, int kind,
                         int nchunks, const WaveItems* L, float* f, const float* eta_dt, long long tmo, int* err,
                         cudaStream_t st);
+// TTI flux (kind 0) / update (kind 1) passes with TMA-staged operands, same
+// tiles; one-step (L null: the buffers of WaveItem `one` over nchunks chunks)
+// or the items of one wavefront launch.
+struct TtiMaps {
+  CUtensorMap bh[4];  // the four p, r buffers, (kEZ + 2 rz) x (kEY + 2r) boxes
+  CUtensorMap bo[4];  // the four p, r buffers, kEZ x kEY boxes
+  CUtensorMap fh;     // fluxes [6][n0][n1][n2p], halo boxes
+  CUtensorMap fo;     // fluxes, own boxes
+  CUtensorMap nzo;    // frame [3][..], own boxes
+  CUtensorMap co;     // c2, own boxes
+  CUtensorMap ko;     // coef [2][..], own boxes
+};
+cudaError_t tti_tma(int R, const PhysGrid& g, const DerivW& w, const TtiMaps& M, int nchunks, const WaveItem* one,
+                    const WaveItems* L, float* flux, const float* damp_b, long long tmo, int* err, cudaStream_t st);
 // items (launch, sub-update, x0, x1) of the wavefront over n0 planes in slabs
 // of `slab` planes for U sub-updates, launches in order; -1 on bad arguments
 int wave_plan(int n0, int slab, int U, std::vector<int>* items);

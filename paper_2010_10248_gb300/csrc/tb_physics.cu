@@ -790,6 +790,190 @@ __global__ void __launch_bounds__(ElaCfg<R>::NT, ElaCfg<R>::MINB)
                   err);
 }
 
+// ----------------------------------------------------- TTI, TMA-staged --
+// The flux and update passes with every operand staged by TMA, as the
+// elastic updates above: per plane x the producer warp loads the planes the
+// axis-1/2 derivatives read (p, r for the fluxes; F1, G1, F2, G2 for the
+// divergence) with an r-cell halo, the axis-0 queue heads at x + r (p, r;
+// F0, G0) and the point's other operands.  Same arithmetic as k_tti_flux /
+// k_tti_update, so bit for bit their results.
+template <int R>
+struct TtiCfg {
+  static constexpr int RZ = (R + 3) / 4 * 4;
+  static constexpr int HH = kEY + 2 * R, HW = kEZ + 2 * RZ;
+  static constexpr int HALO = HH * HW, OWN = kEY * kEZ;
+  // flux: halo p r (x); own p r (x + r), n0 n1 n2 (x).  Update: halo F1 G1
+  // F2 G2 (x); own F0 G0 (x + r), p^n p^{n-1} r^n r^{n-1} c2 coef0 coef1 (x).
+  static constexpr int NHF = 2, NOF = 5, NHU = 4, NOU = 9;
+  static constexpr int SF = NHF * HALO + NOF * OWN, SU = NHU * HALO + NOU * OWN;
+  static constexpr int STAGE = SF > SU ? SF : SU;
+  static constexpr int NST = 3;
+  static constexpr int NT = kEY * kEZ + 32;
+  static constexpr int MINB = R <= 4 ? 3 : 2;
+  static constexpr int SMEM = 4 * NST * STAGE + 16 * NST + 128;
+  static constexpr unsigned BYTES_F = 4u * SF, BYTES_U = 4u * SU;
+  static_assert(HALO % 32 == 0 && OWN % 32 == 0 && STAGE % 32 == 0, "128-byte aligned TMA boxes");
+};
+
+template <int R>
+__device__ __forceinline__ void tti_tma_tile(const PhysGrid& g, const DerivW& w, const TtiMaps& M,
+                                             const WaveItem& it, int y0, int z0, int x0, int x1,
+                                             float* __restrict__ flux, const float* __restrict__ damp_b, float* ring,
+                                             uint64_t* full, uint64_t* empty, long long tmo, int* err) {
+  using C = TtiCfg<R>;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int nsteps = x1 - x0, kind = it.kind;
+  if (warp == kEY) {
+    // ============================ producer warp ============================
+    if (lane != 0) return;
+    int issued = 0;
+    for (int i = 0; i < nsteps; ++i) {
+      const int st = i % C::NST, x = x0 + i;
+      if (i >= C::NST && !mbar_wait(&empty[st], ((i / C::NST) - 1) & 1, tmo)) {
+        atomicExch(err, 1);
+        break;
+      }
+      float* base = ring + (size_t)st * C::STAGE;
+      uint64_t* bar = &full[st];
+      if (kind == 0) {
+        mbar_expect_tx(bar, C::BYTES_F);
+        tma_load_3d(base, &M.bh[it.ia], bar, z0 - C::RZ, y0 - R, x);
+        tma_load_3d(base + C::HALO, &M.bh[it.ic], bar, z0 - C::RZ, y0 - R, x);
+        float* own = base + C::NHF * C::HALO;
+        tma_load_3d(own, &M.bo[it.ia], bar, z0, y0, x + R);
+        tma_load_3d(own + C::OWN, &M.bo[it.ic], bar, z0, y0, x + R);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tma_load_4d(own + (2 + k) * C::OWN, &M.nzo, bar, z0, y0, x, k);
+      } else {
+        mbar_expect_tx(bar, C::BYTES_U);
+        const int hf[4] = {1, 4, 2, 5};  // F1 G1 F2 G2
+#pragma unroll
+        for (int k = 0; k < 4; ++k) tma_load_4d(base + k * C::HALO, &M.fh, bar, z0 - C::RZ, y0 - R, x, hf[k]);
+        float* own = base + C::NHU * C::HALO;
+        tma_load_4d(own, &M.fo, bar, z0, y0, x + R, 0);            // F0
+        tma_load_4d(own + C::OWN, &M.fo, bar, z0, y0, x + R, 3);  // G0
+        tma_load_3d(own + 2 * C::OWN, &M.bo[it.ia], bar, z0, y0, x);
+        tma_load_3d(own + 3 * C::OWN, &M.bo[it.ib], bar, z0, y0, x);
+        tma_load_3d(own + 4 * C::OWN, &M.bo[it.ic], bar, z0, y0, x);
+        tma_load_3d(own + 5 * C::OWN, &M.bo[it.id], bar, z0, y0, x);
+        tma_load_3d(own + 6 * C::OWN, &M.co, bar, z0, y0, x);
+        tma_load_4d(own + 7 * C::OWN, &M.ko, bar, z0, y0, x, 0);
+        tma_load_4d(own + 8 * C::OWN, &M.ko, bar, z0, y0, x, 1);
+      }
+      issued = i + 1;
+    }
+    for (int i = (issued > C::NST ? issued - C::NST : 0); i < issued; ++i)
+      mbar_wait(&full[i % C::NST], (i / C::NST) & 1, tmo);
+    return;
+  }
+  // ============================= compute warps =============================
+  const int ey = warp, ez = lane;
+  const int y = y0 + ey, z = z0 + ez;
+  const bool in = y < g.n1 && z < g.n2;
+  const size_t Np = (size_t)g.n0 * g.n1 * g.n2p;
+  const size_t col = (size_t)(in ? y : 0) * g.n2p + (in ? z : 0);
+  const int yc = in ? y : 0, zc = in ? z : 0;
+  const int ch = (ey + R) * C::HW + ez + C::RZ, co = ey * kEZ + ez;
+  const float* q0 = kind == 0 ? it.a : flux;           // p^n or F0
+  const float* q1 = kind == 0 ? it.c : flux + 3 * Np;  // r^n or G0
+  float qa[2 * R + 1], qb[2 * R + 1];
+  qa[0] = qb[0] = 0.f;  // shifted out before its first use
+#pragma unroll
+  for (int s = 1; s < 2 * R + 1; ++s) {
+    qa[s] = in ? ld0(g, q0, x0 - 1 - R + s, yc, zc) : 0.f;
+    qb[s] = in ? ld0(g, q1, x0 - 1 - R + s, yc, zc) : 0.f;
+  }
+  const float byz = in ? __fadd_rn(__ldg(damp_b + g.n0 + y), __ldg(damp_b + g.n0 + g.n1 + z)) : 0.f;
+  for (int i = 0; i < nsteps; ++i) {
+    const int st = i % C::NST, x = x0 + i;
+    const bool ok = mbar_wait(&full[st], (i / C::NST) & 1, tmo);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) atomicExch(err, 1);
+      break;
+    }
+    const float* base = ring + (size_t)st * C::STAGE;
+#pragma unroll
+    for (int s = 0; s < 2 * R; ++s) {
+      qa[s] = qa[s + 1];
+      qb[s] = qb[s + 1];
+    }
+    const size_t i0 = (size_t)x * g.n1 * g.n2p + col;
+    if (kind == 0) {
+      const float* own = base + C::NHF * C::HALO;
+      qa[2 * R] = own[co];
+      qb[2 * R] = own[C::OWN + co];
+      const float* hp = base;
+      const float* hr = base + C::HALO;
+      const float gp0 = dc_q<R>(qa, w.a[0]), gp1 = dcs<R>(hp, ch, C::HW, w.a[1]), gp2 = dcs<R>(hp, ch, 1, w.a[2]);
+      const float gr0 = dc_q<R>(qb, w.a[0]), gr1 = dcs<R>(hr, ch, C::HW, w.a[1]), gr2 = dcs<R>(hr, ch, 1, w.a[2]);
+      const float n0 = own[2 * C::OWN + co], n1 = own[3 * C::OWN + co], n2 = own[4 * C::OWN + co];
+      const float sp = __fmaf_rn(n2, gp2, __fmaf_rn(n1, gp1, __fmul_rn(n0, gp0)));
+      const float sr = __fmaf_rn(n2, gr2, __fmaf_rn(n1, gr1, __fmul_rn(n0, gr0)));
+      if (in) {
+        flux[i0] = __fmaf_rn(-n0, sp, gp0);
+        flux[Np + i0] = __fmaf_rn(-n1, sp, gp1);
+        flux[2 * Np + i0] = __fmaf_rn(-n2, sp, gp2);
+        flux[3 * Np + i0] = __fmul_rn(n0, sr);
+        flux[4 * Np + i0] = __fmul_rn(n1, sr);
+        flux[5 * Np + i0] = __fmul_rn(n2, sr);
+      }
+    } else {
+      const float* own = base + C::NHU * C::HALO;
+      qa[2 * R] = own[co];
+      qb[2 * R] = own[C::OWN + co];
+      const float *hF1 = base, *hG1 = base + C::HALO, *hF2 = base + 2 * C::HALO, *hG2 = base + 3 * C::HALO;
+      const float hh = __fadd_rn(__fadd_rn(dc_q<R>(qa, w.a[0]), dcs<R>(hF1, ch, C::HW, w.a[1])),
+                                 dcs<R>(hF2, ch, 1, w.a[2]));
+      const float hz = __fadd_rn(__fadd_rn(dc_q<R>(qb, w.a[0]), dcs<R>(hG1, ch, C::HW, w.a[1])),
+                                 dcs<R>(hG2, ch, 1, w.a[2]));
+      const float up = own[2 * C::OWN + co], upp = own[3 * C::OWN + co];
+      const float ur = own[4 * C::OWN + co], urp = own[5 * C::OWN + co];
+      const float c2v = own[6 * C::OWN + co], cpp = own[7 * C::OWN + co], cpr = own[8 * C::OWN + co];
+      const float rhs_p = __fmaf_rn(cpp, hh, __fmul_rn(cpr, hz));
+      const float rhs_r = __fmaf_rn(cpr, hh, hz);
+      const float gdamp = __fmul_rn(__fadd_rn(__ldg(damp_b + x), byz), c2v);
+      const float opg = __fadd_rn(1.f, gdamp), omg = __fsub_rn(1.f, gdamp);
+      if (in) {
+        it.b[i0] = __fadd_rn(up, div_sponge(__fmaf_rn(c2v, rhs_p, __fmul_rn(omg, __fsub_rn(up, upp))), opg));
+        it.d[i0] = __fadd_rn(ur, div_sponge(__fmaf_rn(c2v, rhs_r, __fmul_rn(omg, __fsub_rn(ur, urp))), opg));
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(TtiCfg<R>::NT, TtiCfg<R>::MINB)
+    k_tti_tma(PhysGrid g, DerivW w, const __grid_constant__ TtiMaps M, int nchunks, const WaveItem one,
+              const WaveItems L, float* flux, const float* __restrict__ damp_b, long long tmo, int* err) {
+  using C = TtiCfg<R>;
+  extern __shared__ float4 tti_tma_smem4[];
+  float* ring = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tti_tma_smem4) + 127) & ~uintptr_t(127));
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)C::NST * C::STAGE);
+  uint64_t* empty = full + C::NST;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < C::NST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kEY);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int x0, x1;
+  WaveItem it;
+  if (L.n == 0) {
+    it = one;
+    chunk_planes(g, nchunks, x0, x1);
+  } else {
+    it = L.it[blockIdx.z];
+    x0 = it.x0;
+    x1 = it.x1;
+  }
+  tti_tma_tile<R>(g, w, M, it, blockIdx.y * kEY, blockIdx.x * kEZ, x0, x1, flux, damp_b, ring, full, empty, tmo,
+                  err);
+}
+
 // material at the staggered positions from vp, vs, rho (dense [N]):
 // b = 1/rho at half-nodes (mean of two nodes), lam, mu at nodes, mu at edge
 // centres (harmonic mean of four nodes, 0 if one is 0); a neighbour past
@@ -1104,6 +1288,38 @@ cudaError_t elastic_tma(int R, const PhysGrid& g, const DerivW& w, float dt, con
     case 2: return ela_tma_r<2>(g, w, dt, M, kind, nchunks, L, f, eta_dt, tmo, err, st);
     case 4: return ela_tma_r<4>(g, w, dt, M, kind, nchunks, L, f, eta_dt, tmo, err, st);
     case 6: return ela_tma_r<6>(g, w, dt, M, kind, nchunks, L, f, eta_dt, tmo, err, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int R>
+static cudaError_t tti_tma_r(const PhysGrid& g, const DerivW& w, const TtiMaps& M, int nchunks, const WaveItem* one,
+                             const WaveItems* L, float* flux, const float* damp_b, long long tmo, int* err,
+                             cudaStream_t st) {
+  using C = TtiCfg<R>;
+  static bool attr = false;  // more than 48 KB of shared memory needs the opt-in
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_tti_tma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  WaveItems none{};
+  WaveItem nil{};
+  const dim3 grid((unsigned)((g.n2 + kEZ - 1) / kEZ), (unsigned)((g.n1 + kEY - 1) / kEY),
+                  (unsigned)(L ? L->n : nchunks));
+  count_launch();
+  k_tti_tma<R><<<grid, C::NT, C::SMEM, st>>>(g, w, M, nchunks, one ? *one : nil, L ? *L : none, flux, damp_b, tmo,
+                                             err);
+  return cudaGetLastError();
+}
+
+cudaError_t tti_tma(int R, const PhysGrid& g, const DerivW& w, const TtiMaps& M, int nchunks, const WaveItem* one,
+                    const WaveItems* L, float* flux, const float* damp_b, long long tmo, int* err, cudaStream_t st) {
+  if (L ? (L->n < 1 || L->n > kWaveItemsMax) : !one) return cudaErrorInvalidValue;
+  switch (R) {
+    case 2: return tti_tma_r<2>(g, w, M, nchunks, one, L, flux, damp_b, tmo, err, st);
+    case 4: return tti_tma_r<4>(g, w, M, nchunks, one, L, flux, damp_b, tmo, err, st);
+    case 6: return tti_tma_r<6>(g, w, M, nchunks, one, L, flux, damp_b, tmo, err, st);
   }
   return cudaErrorInvalidValue;
 }

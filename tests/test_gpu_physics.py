@@ -136,7 +136,7 @@ def _run(tb, physics, case, so, nt, schedule, **opt):
     return tr, [p.field(i).cpu().numpy() for i in range(nf)]
 
 
-@pytest.mark.parametrize("physics", ["tti", "tti_fused", "elastic", "elastic_plain"])
+@pytest.mark.parametrize("physics", ["tti", "tti_l1", "tti_fused", "elastic", "elastic_l1"])
 @pytest.mark.parametrize("shape,so,T,slab,nt", [((30, 33, 40), 4, 2, 0, 23), ((37, 31, 36), 8, 3, 4, 20),
                                                 ((29, 33, 35), 8, 2, 5, 17), ((41, 29, 35), 12, 2, 6, 15),
                                                 ((33, 30, 34), 4, 8, 3, 19), ((19, 30, 34), 8, 4, 0, 13)])
@@ -146,7 +146,7 @@ def test_blocked_bitwise_equals_onestep(tb, physics, shape, so, T, slab, nt):
     The fused TTI step reaches 2r planes, so its slabs are at least so."""
     ela = physics.startswith("elastic")
     phys = tb.TB_ELASTIC if ela else tb.TB_TTI
-    opt = dict(tti_fused=physics == "tti_fused", elastic_plain=physics == "elastic_plain")
+    opt = dict(tti_fused=physics == "tti_fused", stream_l1=physics.endswith("_l1"))
     if opt["tti_fused"] and slab:
         slab = max(slab, so)
     case = (elastic_case(shape, so, 400 + so) if ela else tti_case(shape, so, 300 + so, nt))
@@ -174,15 +174,29 @@ def test_tti_fused_step_equals_two_pass(tb, shape, so):
 
 
 @pytest.mark.parametrize("shape,so", [((30, 33, 40), 4), ((70, 19, 71), 8), ((45, 26, 33), 12), ((96, 40, 66), 8)])
-def test_elastic_tma_equals_plain(tb, shape, so):
+def test_elastic_tma_equals_l1(tb, shape, so):
     """The TMA-staged elastic updates (8 x 32 tiles, chunks along axis 0,
     halos and out-of-grid cells filled by the copy engine) against the L1
     streaming kernels: traces and every field bit for bit, on grids with
     ragged tiles and several chunks."""
     nt = 21
     case = elastic_case(shape, so, 600 + so)
-    ref_tr, ref_f = _run(tb, tb.TB_ELASTIC, case, so, nt, "onestep", elastic_plain=True)
+    ref_tr, ref_f = _run(tb, tb.TB_ELASTIC, case, so, nt, "onestep", stream_l1=True)
     got_tr, got_f = _run(tb, tb.TB_ELASTIC, case, so, nt, "onestep")
+    assert np.abs(ref_tr).max() > 0
+    assert np.array_equal(got_tr, ref_tr)
+    for a, b in zip(got_f, ref_f):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("shape,so", [((30, 33, 40), 4), ((70, 19, 71), 8), ((45, 26, 33), 12), ((96, 40, 66), 8)])
+def test_tti_tma_equals_l1(tb, shape, so):
+    """The TMA-staged TTI passes against the L1 streaming kernels: traces and
+    every field bit for bit, ragged tiles and several chunks."""
+    nt = 21
+    case = tti_case(shape, so, 700 + so, nt)
+    ref_tr, ref_f = _run(tb, tb.TB_TTI, case, so, nt, "onestep", stream_l1=True)
+    got_tr, got_f = _run(tb, tb.TB_TTI, case, so, nt, "onestep")
     assert np.abs(ref_tr).max() > 0
     assert np.array_equal(got_tr, ref_tr)
     for a, b in zip(got_f, ref_f):

@@ -767,6 +767,9 @@ __device__ __forceinline__ void sweep_body(const SweepParams& P, const PassDesc&
     }
     any_src = any_src || ev_n[p] > 0;
   }
+  // warp-uniform: the fused steps of a warp without source points skip the
+  // check (1 % of the blocked sweep's time with one source)
+  const bool any_src_w = __any_sync(0xffffffffu, any_src);
 
   // Register queues along axis 0, rotated by renaming: the stream loop is
   // unrolled by Q = 2r + 1, and at stream step j (phase i = (j - jstart) mod
@@ -980,7 +983,7 @@ __device__ __forceinline__ void sweep_body(const SweepParams& P, const PassDesc&
             if constexpr (T == 1) {
               if (any_src) inject(0, j, un);
             } else {
-              inject(0, j, un);
+              if (any_src_w) inject(0, j, un);
             }
           }
 
@@ -1026,7 +1029,7 @@ __device__ __forceinline__ void sweep_body(const SweepParams& P, const PassDesc&
                   const V lap = laplacian(pl, uc, [&](int d) -> V { return qq[QI(k)][(i + R + d) % Q]; });
                   const float bx = __shfl_sync(0xffffffffu, bxc, k);
                   un = update(uc, upv, lap, c2v, bx, CW == 4 && yz_free && bx == 0.f);
-                  inject(k, q, un);
+                  if (any_src_w) inject(k, q, un);
                 }
               }
               if (k + 1 < T) {

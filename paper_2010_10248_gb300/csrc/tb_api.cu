@@ -1621,6 +1621,7 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   P.rec_cap = h->rec_cap > 0 ? h->rec_cap : 1;
   P.lp_scales = h->lp_scales;
   P.lp_mx = h->lp_mx;
+  P.lp_srcmax = (h->have_src && h->src.npts > 0) ? h->lp_srcmax : nullptr;
   // set `i` of the launch: the time tile from step n reading (fld[c], fld[p])
   auto set_fields = [&](int i, int c, int p, int out0, int out1, int step0) {
     SweepSet& S = P.set[i];
@@ -1662,11 +1663,6 @@ extern "C" int tb_forward(tb_handle* h, int nt, float* traces, int schedule, voi
   };
   // every launch of a plan on the time tile (or step) from step n
   auto run = [&](int TT, const Plan& pl, int pass_off, int out0, int out1, int step0) -> int {
-    if (h->sk) {  // the scale of u^{n+1}, from max |u^n| and the step's largest injection
-      cudaError_t e = lowprec_scale(h->lp_scales, h->lp_mx, (h->have_src && h->src.npts > 0) ? h->lp_srcmax : nullptr,
-                                    step0, st);
-      if (e != cudaSuccess) return cuda_fail(h, e, "scale");
-    }
     set_fields(0, cur, prev, out0, out1, step0);
     for (size_t L = 0; L < pl.launch_first.size(); ++L) {
       int r = launch(TT, pl, pass_off, L);

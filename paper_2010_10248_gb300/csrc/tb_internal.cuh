@@ -83,10 +83,27 @@ struct SweepParams {
   const PassDesc* pass;         // device copy of the pass table
   int npass;
   // 16-bit storage (one-step kernel): scales[n] of u^{n-1} (stored = u / s),
-  // running max |u| per step (float bits)
-  const float* lp_scales;
+  // running max |u| per step (float bits), the steps' largest injections
+  // (may be null); the sweep of step n sets scales[n + 2] (lp_next_scale)
+  float* lp_scales;
   unsigned* lp_mx;
+  const float* lp_srcmax;
 };
+
+// Scale of u^{n+1} with 16-bit storage, s = 2^(ceil(log2(4 max|u^n| + max
+// |src step n|)) - 8) (a power of two, exact to multiply by), from the
+// running maximum mx[n + 1] of |u^n| and the step's largest injection.
+// Every thread of the step's launch computes it (no separate launch); the
+// same arithmetic everywhere, so every reader gets the same value.
+__device__ __forceinline__ float lp_next_scale(const unsigned* mx, const float* srcmax, int n) {
+  const float bound = 4.f * __uint_as_float(mx[n + 1]) + (srcmax ? srcmax[n] : 0.f);
+  int e = 0;
+  if (bound > 0.f) {
+    frexpf(bound, &e);  // bound = f 2^e, f in [0.5, 1)
+    e -= 8;
+  }
+  return ldexpf(1.f, max(min(e, 100), -100));
+}
 
 // A batched one-step launch over several shots: pass table (sorted by
 // cta0), per shot two parameter sets (even and odd steps: u^n in field 0 or
@@ -271,10 +288,9 @@ inline void dfree(void* p, cudaStream_t st) {
 // best of 5) and packed-FP32 FMA throughput (TFLOP/s), with this build's
 // kernels (tb_selftest.cu).  Synchronises st.
 cudaError_t measure_peaks(double* hbm_gbs, double* fp32_tflops, cudaStream_t st);
-// scales[n + 2] (of u^{n+1}) from max |u^n| and the step's largest injection
-cudaError_t lowprec_scale(float* scales, const unsigned* mx, const float* srcmax, int n, cudaStream_t st);
+// one step; the step's kernel also sets scales[n + 2] (lp_next_scale)
 cudaError_t lowprec_step(int storage, int R, const PhysGrid& g, const LapW& w, int nchunks, const void* uc, void* up,
-                         const float* c2, const float* damp_b, const float* scales, const float* srcmax, int n,
+                         const float* c2, const float* damp_b, float* scales, const float* srcmax, int n,
                          unsigned* mx, cudaStream_t st);
 cudaError_t lowprec_inject(int storage, const PhysGrid& g, int64_t npts, const int64_t* lin, const float* dcmp_row,
                            void* u, const float* scales, int n, unsigned* mx, cudaStream_t st);

@@ -63,13 +63,16 @@ __device__ __forceinline__ void atomic_max_warp(unsigned* dst, float v) {
 template <class ST, int R>
 __global__ void __launch_bounds__(256) k_ac_lp(PhysGrid g, LapW w, int nchunks, const ST* __restrict__ uc,
                                                ST* up, const float* __restrict__ c2,
-                                               const float* __restrict__ damp_b, const float* __restrict__ scales,
-                                               int n, unsigned* __restrict__ mx) {
+                                               const float* __restrict__ damp_b, float* scales,
+                                               const float* __restrict__ srcmax, int n, unsigned* __restrict__ mx) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
   const bool ok = z < g.n2 && y < g.n1;
   // planes [x0, x1) of chunk blockIdx.z (all chunks of a step in one launch)
   const int x0 = (int)((int64_t)g.n0 * blockIdx.z / nchunks), x1 = (int)((int64_t)g.n0 * (blockIdx.z + 1) / nchunks);
-  const float s_cur = scales[n + 1], s_prev = scales[n], inv_out = 1.0f / scales[n + 2];  // powers of two
+  const float s_out = lp_next_scale(mx, srcmax, n);
+  const float s_cur = scales[n + 1], s_prev = scales[n], inv_out = 1.0f / s_out;  // powers of two
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    scales[n + 2] = s_out;  // for the kernels after the step
   float q[2 * R + 1];
 #pragma unroll
   for (int s = 0; s < 2 * R + 1; ++s) q[s] = ok ? lz(g, uc, x0 - 1 - R + s, y, z, s_cur) : 0.f;
@@ -105,17 +108,6 @@ __global__ void __launch_bounds__(256) k_ac_lp(PhysGrid g, LapW w, int nchunks, 
     vmax = fmaxf(vmax, fabsf(un));
   }
   atomic_max_warp(mx + n + 2, vmax);
-}
-
-// s_{n+1} from max |u^n| and the largest source increment of step n
-__global__ void k_lp_scale(float* scales, const unsigned* mx, const float* srcmax, int n) {
-  const float bound = 4.f * __uint_as_float(mx[n + 1]) + (srcmax ? srcmax[n] : 0.f);
-  int e = 0;
-  if (bound > 0.f) {
-    frexpf(bound, &e);  // bound = f 2^e, f in [0.5, 1)
-    e -= 8;
-  }
-  scales[n + 2] = ldexpf(1.f, max(min(e, 100), -100));
 }
 
 // u^{n+1}(p_id) += dcmp[id], in the stored scale; updates the running max
@@ -168,39 +160,32 @@ __global__ void k_lp_unpack(PhysGrid g, const ST* __restrict__ u, float s, float
 // ------------------------------------------------------------- launch --
 template <class ST, int R>
 static cudaError_t lp_step_t(const PhysGrid& g, const LapW& w, int nchunks, const void* uc, void* up, const float* c2,
-                             const float* damp_b, const float* scales, int n, unsigned* mx, cudaStream_t st) {
+                             const float* damp_b, float* scales, const float* srcmax, int n, unsigned* mx,
+                             cudaStream_t st) {
   const dim3 blk(32, 8), grd((unsigned)((g.n2 + 31) / 32), (unsigned)((g.n1 + 7) / 8), (unsigned)nchunks);
   count_launch();
-  k_ac_lp<ST, R><<<grd, blk, 0, st>>>(g, w, nchunks, (const ST*)uc, (ST*)up, c2, damp_b, scales, n, mx);
+  k_ac_lp<ST, R><<<grd, blk, 0, st>>>(g, w, nchunks, (const ST*)uc, (ST*)up, c2, damp_b, scales, srcmax, n, mx);
   return cudaGetLastError();
 }
 template <class ST>
 static cudaError_t lp_step_st(int R, const PhysGrid& g, const LapW& w, int nchunks, const void* uc, void* up,
-                              const float* c2, const float* damp_b, const float* scales, int n, unsigned* mx,
-                              cudaStream_t st) {
+                              const float* c2, const float* damp_b, float* scales, const float* srcmax, int n,
+                              unsigned* mx, cudaStream_t st) {
   switch (R) {
-    case 2: return lp_step_t<ST, 2>(g, w, nchunks, uc, up, c2, damp_b, scales, n, mx, st);
-    case 4: return lp_step_t<ST, 4>(g, w, nchunks, uc, up, c2, damp_b, scales, n, mx, st);
-    case 6: return lp_step_t<ST, 6>(g, w, nchunks, uc, up, c2, damp_b, scales, n, mx, st);
+    case 2: return lp_step_t<ST, 2>(g, w, nchunks, uc, up, c2, damp_b, scales, srcmax, n, mx, st);
+    case 4: return lp_step_t<ST, 4>(g, w, nchunks, uc, up, c2, damp_b, scales, srcmax, n, mx, st);
+    case 6: return lp_step_t<ST, 6>(g, w, nchunks, uc, up, c2, damp_b, scales, srcmax, n, mx, st);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t lowprec_scale(float* scales, const unsigned* mx, const float* srcmax, int n, cudaStream_t st) {
-  count_launch();
-  k_lp_scale<<<1, 1, 0, st>>>(scales, mx, srcmax, n);
-  return cudaGetLastError();
-}
-
 cudaError_t lowprec_step(int storage, int R, const PhysGrid& g, const LapW& w, int nchunks, const void* uc, void* up,
-                         const float* c2, const float* damp_b, const float* scales, const float* srcmax, int n,
+                         const float* c2, const float* damp_b, float* scales, const float* srcmax, int n,
                          unsigned* mx, cudaStream_t st) {
-  count_launch();
-  k_lp_scale<<<1, 1, 0, st>>>((float*)scales, mx, srcmax, n);
   switch (storage) {
-    case 1: return lp_step_st<__half>(R, g, w, nchunks, uc, up, c2, damp_b, scales, n, mx, st);
-    case 2: return lp_step_st<__nv_bfloat16>(R, g, w, nchunks, uc, up, c2, damp_b, scales, n, mx, st);
-    case 3: return lp_step_st<float>(R, g, w, nchunks, uc, up, c2, damp_b, scales, n, mx, st);
+    case 1: return lp_step_st<__half>(R, g, w, nchunks, uc, up, c2, damp_b, scales, srcmax, n, mx, st);
+    case 2: return lp_step_st<__nv_bfloat16>(R, g, w, nchunks, uc, up, c2, damp_b, scales, srcmax, n, mx, st);
+    case 3: return lp_step_st<float>(R, g, w, nchunks, uc, up, c2, damp_b, scales, srcmax, n, mx, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -497,7 +497,8 @@ __device__ __forceinline__ void sweep_body(const SweepParams& P, const PassDesc&
         if (pos >= 0) {
           const size_t go = (size_t)q * ps + (size_t)(y0 + row) * P.n2p + z0 + col;
           if constexpr (SK != 0)  // one-step only: u^{n+1} is stored as u / s
-            rrow[pos] = __fmul_rn(ld1cg(reinterpret_cast<const ST*>(out0) + go), __ldg(P.lp_scales + step0 + 2));
+            rrow[pos] = __fmul_rn(ld1cg(reinterpret_cast<const ST*>(out0) + go),
+                                  lp_next_scale(P.lp_mx, P.lp_srcmax, step0));
           else
             rrow[pos] = plane ? plane[(R + row) * SW + RP + col] : __ldcg(out0 + go);
         }
@@ -813,8 +814,9 @@ __device__ __forceinline__ void sweep_body(const SweepParams& P, const PassDesc&
   float2 sc2 = make_float2(1.f, 1.f), sp2 = sc2, io2 = sc2;
   float vmax = 0.f;
   if constexpr (SK != 0) {
-    const float a = __ldg(P.lp_scales + step0 + 1), p = __ldg(P.lp_scales + step0),
-                o = 1.f / __ldg(P.lp_scales + step0 + 2);
+    const float so = lp_next_scale(P.lp_mx, P.lp_srcmax, step0);
+    const float a = __ldg(P.lp_scales + step0 + 1), p = __ldg(P.lp_scales + step0), o = 1.f / so;
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.lp_scales[step0 + 2] = so;  // for the kernels after the step
     sc2 = make_float2(a, a);
     sp2 = make_float2(p, p);
     io2 = make_float2(o, o);

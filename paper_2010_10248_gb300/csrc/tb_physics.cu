@@ -691,8 +691,11 @@ __device__ __forceinline__ void ela_tma_tile(const PhysGrid& g, const DerivW& w,
     qc[s] = in ? ld0(g, q2, x0 - 1 - R + s, yc, zc) : 0.f;
   }
   const float eyz_y = __ldg(eta_dt + g.n0 + (in ? y : 0)), eyz_z = __ldg(eta_dt + g.n0 + g.n1 + (in ? z : 0));
+  float eta_next = nsteps > 0 ? __ldg(eta_dt + x0) : 0.f;  // the plane's damping, loaded a step ahead
   for (int i = 0; i < nsteps; ++i) {
     const int st = i % C::NST, x = x0 + i;
+    const float eta_x = eta_next;
+    if (i + 1 < nsteps) eta_next = __ldg(eta_dt + x + 1);
     const bool ok = mbar_wait(&full[st], (i / C::NST) & 1, tmo);
     if (!__all_sync(0xffffffffu, ok)) {
       if (lane == 0) atomicExch(err, 1);
@@ -705,7 +708,7 @@ __device__ __forceinline__ void ela_tma_tile(const PhysGrid& g, const DerivW& w,
       qb[s] = qb[s + 1];
       qc[s] = qc[s + 1];
     }
-    const float den = __fadd_rn(1.f, __fadd_rn(__fadd_rn(__ldg(eta_dt + x), eyz_y), eyz_z));
+    const float den = __fadd_rn(1.f, __fadd_rn(__fadd_rn(eta_x, eyz_y), eyz_z));
     const size_t i0 = (size_t)x * g.n1 * g.n2p + col;
     if (kind == 0) {
       const float* own = base + C::NHV * C::HALO;
@@ -884,8 +887,11 @@ __device__ __forceinline__ void tti_tma_tile(const PhysGrid& g, const DerivW& w,
     qb[s] = in ? ld0(g, q1, x0 - 1 - R + s, yc, zc) : 0.f;
   }
   const float byz = in ? __fadd_rn(__ldg(damp_b + g.n0 + y), __ldg(damp_b + g.n0 + g.n1 + z)) : 0.f;
+  float bx_next = nsteps > 0 ? __ldg(damp_b + x0) : 0.f;  // the plane's damping, loaded a step ahead
   for (int i = 0; i < nsteps; ++i) {
     const int st = i % C::NST, x = x0 + i;
+    const float bx_x = bx_next;
+    if (i + 1 < nsteps) bx_next = __ldg(damp_b + x + 1);
     const bool ok = mbar_wait(&full[st], (i / C::NST) & 1, tmo);
     if (!__all_sync(0xffffffffu, ok)) {
       if (lane == 0) atomicExch(err, 1);
@@ -931,7 +937,7 @@ __device__ __forceinline__ void tti_tma_tile(const PhysGrid& g, const DerivW& w,
       const float c2v = own[6 * C::OWN + co], cpp = own[7 * C::OWN + co], cpr = own[8 * C::OWN + co];
       const float rhs_p = __fmaf_rn(cpp, hh, __fmul_rn(cpr, hz));
       const float rhs_r = __fmaf_rn(cpr, hh, hz);
-      const float gdamp = __fmul_rn(__fadd_rn(__ldg(damp_b + x), byz), c2v);
+      const float gdamp = __fmul_rn(__fadd_rn(bx_x, byz), c2v);
       const float opg = __fadd_rn(1.f, gdamp), omg = __fsub_rn(1.f, gdamp);
       if (in) {
         it.b[i0] = __fadd_rn(up, div_sponge(__fmaf_rn(c2v, rhs_p, __fmul_rn(omg, __fsub_rn(up, upp))), opg));
@@ -1149,14 +1155,15 @@ static cudaError_t tti_fused_r(const PhysGrid& g, const DerivW& w, int nchunks, 
                                float* pp, const float* rc, float* rp, const float* c2, const float* coef,
                                const float* nz, const float* damp_b, cudaStream_t st) {
   using C = TtiFusedCfg<R>;
-  static bool attr = false;  // shared memory above 48 KB (r = 6) needs the opt-in
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tti_fused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_tti_fused_wave<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // shared memory above 48 KB (r = 6) needs the opt-in; once per process (a
+  // function-local static is initialised once even with concurrent callers)
+  static const cudaError_t attr = [] {
+    const cudaError_t e = cudaFuncSetAttribute(k_tti_fused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    return e != cudaSuccess
+               ? e
+               : cudaFuncSetAttribute(k_tti_fused_wave<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  }();
+  if (attr != cudaSuccess) return attr;
   const unsigned gz = (unsigned)((g.n2 + C::TZ - 1) / C::TZ), gy = (unsigned)((g.n1 + kFY - 1) / kFY);
   count_launch();
   if (L)
@@ -1266,12 +1273,10 @@ static cudaError_t ela_tma_r(const PhysGrid& g, const DerivW& w, float dt, const
                              const WaveItems* L, float* f, const float* eta_dt, long long tmo, int* err,
                              cudaStream_t st) {
   using C = ElaCfg<R>;
-  static bool attr = false;  // more than 48 KB of shared memory needs the opt-in
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_ela_tma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // more than 48 KB of shared memory needs the opt-in; once per process
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_ela_tma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  if (attr != cudaSuccess) return attr;
   WaveItems none{};
   const dim3 grid((unsigned)((g.n2 + kEZ - 1) / kEZ), (unsigned)((g.n1 + kEY - 1) / kEY),
                   (unsigned)(L ? L->n : nchunks));
@@ -1297,12 +1302,10 @@ static cudaError_t tti_tma_r(const PhysGrid& g, const DerivW& w, const TtiMaps& 
                              const WaveItems* L, float* flux, const float* damp_b, long long tmo, int* err,
                              cudaStream_t st) {
   using C = TtiCfg<R>;
-  static bool attr = false;  // more than 48 KB of shared memory needs the opt-in
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_tti_tma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // more than 48 KB of shared memory needs the opt-in; once per process
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(k_tti_tma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  if (attr != cudaSuccess) return attr;
   WaveItems none{};
   WaveItem nil{};
   const dim3 grid((unsigned)((g.n2 + kEZ - 1) / kEZ), (unsigned)((g.n1 + kEY - 1) / kEY),

@@ -322,9 +322,9 @@ def test_elastic_full_size_subbox(tb, schedule):
 @pytest.mark.slow
 @pytest.mark.parametrize("physics", ["tti", "elastic"])
 def test_full_size_blocked_bitwise_equals_onestep(tb, physics):
-    """The benchmark's grid, model and default wavefront (time tile 4, slabs
-    of 32 planes) over 26 steps (six wavefronts and two single steps): traces
-    and every field bit for bit."""
+    """The benchmark's grid, model and default wavefront (time tile 8, slabs
+    of 32 planes) over 26 steps (three wavefronts and two single steps):
+    traces and every field bit for bit."""
     import torch
     w = wl.tti_384_so8() if physics == "tti" else wl.elastic_384_so8()
     phys = tb.TB_TTI if physics == "tti" else tb.TB_ELASTIC

@@ -238,6 +238,38 @@ __device__ __forceinline__ void stvcg(float* p, const FV<NP>& v) {
   else
     __stcg(reinterpret_cast<float4*>(p), make_float4(v.p[0].x, v.p[0].y, v.p[1].x, v.p[1].y));
 }
+// Stores of v to p where `on`, each one predicated instruction: a fused
+// step's conditional stores (halo strips, staged centres, the sweep's output)
+// then leave its code one block the compiler schedules across (branches
+// around them cost the blocked sweep 10 % at T = 3).  Global with .cg (to L2)
+// and .cs (streaming), or shared.
+template <int NP>
+__device__ __forceinline__ void st_pred_cg(bool on, float* p, const FV<NP>& v) {
+  if constexpr (NP == 1)
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.global.cg.v2.f32 [%1], {%2, %3};\n}" ::"r"((int)on),
+                 "l"(p), "f"(v.p[0].x), "f"(v.p[0].y));
+  else
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.global.cg.v4.f32 [%1], {%2, %3, %4, %5};\n}" ::"r"((int)on),
+                 "l"(p), "f"(v.p[0].x), "f"(v.p[0].y), "f"(v.p[1].x), "f"(v.p[1].y));
+}
+template <int NP>
+__device__ __forceinline__ void st_pred_sh(bool on, float* p, const FV<NP>& v) {
+  if constexpr (NP == 1)
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.shared.v2.f32 [%1], {%2, %3};\n}" ::"r"((int)on),
+                 "r"(smem_u32(p)), "f"(v.p[0].x), "f"(v.p[0].y));
+  else
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.shared.v4.f32 [%1], {%2, %3, %4, %5};\n}" ::"r"((int)on),
+                 "r"(smem_u32(p)), "f"(v.p[0].x), "f"(v.p[0].y), "f"(v.p[1].x), "f"(v.p[1].y));
+}
+template <int NP>
+__device__ __forceinline__ void st_pred_cs(bool on, float* p, const FV<NP>& v) {
+  if constexpr (NP == 1)
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.global.cs.v2.f32 [%1], {%2, %3};\n}" ::"r"((int)on),
+                 "l"(p), "f"(v.p[0].x), "f"(v.p[0].y));
+  else
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %0, 0;\n @q st.global.cs.v4.f32 [%1], {%2, %3, %4, %5};\n}" ::"r"((int)on),
+                 "l"(p), "f"(v.p[0].x), "f"(v.p[0].y), "f"(v.p[1].x), "f"(v.p[1].y));
+}
 template <int NP>
 __device__ __forceinline__ void stvcs(float* p, const FV<NP>& v) {
   if constexpr (NP == 1)
@@ -1039,19 +1071,21 @@ __device__ __forceinline__ void sweep_body(const SweepParams& P, const PassDesc&
                 qq[QI(k + 1)][(i + 2 * R) % Q] = un;
                 // ... stage its centre for the next stream step ...
                 const int qn = j + 1 - (k + 1) * R;
-                if (qn >= pd.xc0 && qn < pd.xc1)
-                  stv<NPR>(wrbuf + (size_t)k * C::PSLOT + own, qq[QI(k + 1)][(i + R + 1) % Q]);
+                st_pred_sh<NPR>(qn >= pd.xc0 && qn < pd.xc1, wrbuf + (size_t)k * C::PSLOT + own,
+                                qq[QI(k + 1)][(i + R + 1) % Q]);
                 // ... and publish its halo strips for the neighbours
-                if (act && (strip_y >= 0 || strip_z >= 0)) {
+                {
                   int qd = jd - (k * R) % C::D;
                   qd += qd < 0 ? C::D : 0;
                   float* rs = rs_base + ((size_t)k * C::D + qd) * C::STRIP;
-                  if (strip_y >= 0) stvcg<NPR>(rs + strip_y, un);
-                  if (strip_z >= 0) stvcg<NPR>(rs + strip_z, un);
+                  st_pred_cg<NPR>(act && strip_y >= 0, rs + (strip_y >= 0 ? strip_y : 0), un);
+                  st_pred_cg<NPR>(act && strip_z >= 0, rs + (strip_z >= 0 ? strip_z : 0), un);
                 }
-              } else if (act && own_row && q >= pd.xo0 && q < pd.xo1 && vz) {
-                stvcs<NPR>(out0 + (size_t)q * ps + coff, un);
-                stvcs<NPR>(out1 + (size_t)q * ps + coff, qq[QI(T - 1)][(i + R) % Q]);
+              } else {
+                const bool st_out = act && own_row && q >= pd.xo0 && q < pd.xo1 && vz;
+                const size_t qo = (size_t)(st_out ? q : 0) * ps + coff;
+                st_pred_cs<NPR>(st_out, out0 + qo, un);
+                st_pred_cs<NPR>(st_out, out1 + qo, qq[QI(T - 1)][(i + R) % Q]);
               }
             }
             mbar_arrive(bar_ctr + ((j + 1) & 1));

@@ -60,7 +60,7 @@ def parse():
                     help="vp gradient of the 256^3 so8 shot (800 steps, 32 checkpoints) instead")
     ap.add_argument("--many-sources", action="store_true",
                     help="blocked vs one-step with many sources on a plane and spread through the grid")
-    ap.add_argument("--wave-tile", type=int, default=8, help="TTI / elastic: steps per wavefront")
+    ap.add_argument("--wave-tile", type=int, default=16, help="TTI / elastic: steps per wavefront")
     ap.add_argument("--slab", type=int, default=0, help="TTI / elastic: planes per wavefront slab (0: auto)")
     ap.add_argument("--tti-fused", action="store_true", help="TTI: both passes of a step in one kernel")
     ap.add_argument("--stream-l1", action="store_true", help="TTI / elastic: the L1 streaming kernels")

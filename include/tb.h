@@ -89,8 +89,8 @@ typedef struct {
   int time_tile;   /* T: time steps fused per blocked sweep (Sec. II-B).
                       Supported: 1..4 (space order 4, 8), 1..2 (space order 12);
                       0 -> the fastest measured on GB300 at 512^3: 4 (space
-                      order 4), 3 (8), 2 (12).  TB_TTI, TB_ELASTIC: 1..8
-                      steps per wavefront (below); 0 -> 8.                    */
+                      order 4), 3 (8), 2 (12).  TB_TTI, TB_ELASTIC: 1..16
+                      steps per wavefront (below); 0 -> 16.                   */
   int nbl;         /* width in cells of the built-in sponge (Sec. IV-B); 0: none  */
   int y_bands;     /* blocked sweep: number of bands along axis 1, each time
                       tile split the same way; 0 -> bands pipelined across time

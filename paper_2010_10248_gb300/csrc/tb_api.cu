@@ -468,13 +468,13 @@ extern "C" int tb_create(const int64_t n[3], const double hsp[3], int so, int ph
   }
   // more fused so12 steps exceed shared memory; 16-bit and plain storage run
   // one step per launch; the TTI / elastic wavefront takes up to 8 steps
-  const int tmax = physics != TB_ACOUSTIC ? 8 : (h->storage != TB_F32 ? 1 : (so == 12 ? 2 : 4));
+  const int tmax = physics != TB_ACOUSTIC ? 16 : (h->storage != TB_F32 ? 1 : (so == 12 ? 2 : 4));
   // default: the fused depth measured fastest at 512^3 (so8: T = 3 computes
   // each level faster than T = 4, whose three register queues crowd the
-  // registers); TTI / elastic: 8 (at 384^3 so8 the deepest wavefront costs
+  // registers); TTI / elastic: 16 (at 384^3 so8 the deepest wavefront costs
   // least per step: fewer ramp launches per step)
   if (h->opt.time_tile == 0)
-    h->opt.time_tile = physics != TB_ACOUSTIC ? 8 : ((tmax > 1 && so == 8) ? 3 : tmax);
+    h->opt.time_tile = physics != TB_ACOUSTIC ? 16 : ((tmax > 1 && so == 8) ? 3 : tmax);
   if (h->opt.time_tile < 1 || h->opt.time_tile > tmax || h->opt.nbl < 0 || h->opt.y_bands < 0 ||
       h->opt.x_chunks < 0 || h->opt.band_ctas < 0 || h->opt.slab_planes < 0 ||
       (h->opt.slab_planes > 0 &&

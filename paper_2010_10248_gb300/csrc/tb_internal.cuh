@@ -172,8 +172,8 @@ cudaError_t elastic_step(int R, const PhysGrid& g, const DerivW& w, float dt, in
 // Wavefront schedule of the TTI / elastic sub-updates (tb_physics.cu): the
 // (sub-update, slab) items of one launch, and the injection / sampling of the
 // steps whose last sub-update finished a slab in it.
-constexpr int kWaveItemsMax = 16;  // 2 x the deepest time tile (8)
-constexpr int kWavePostsMax = 8;
+constexpr int kWaveItemsMax = 32;  // 2 x the deepest time tile (16)
+constexpr int kWavePostsMax = 16;
 struct WaveItem {
   int kind;   // 0: TTI flux / elastic velocity; 1: TTI update / elastic stress
   int x0, x1;  // planes of the slab

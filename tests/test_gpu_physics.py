@@ -139,7 +139,8 @@ def _run(tb, physics, case, so, nt, schedule, **opt):
 @pytest.mark.parametrize("physics", ["tti", "tti_l1", "tti_fused", "elastic", "elastic_l1"])
 @pytest.mark.parametrize("shape,so,T,slab,nt", [((30, 33, 40), 4, 2, 0, 23), ((37, 31, 36), 8, 3, 4, 20),
                                                 ((29, 33, 35), 8, 2, 5, 17), ((41, 29, 35), 12, 2, 6, 15),
-                                                ((33, 30, 34), 4, 8, 3, 19), ((19, 30, 34), 8, 4, 0, 13)])
+                                                ((33, 30, 34), 4, 8, 3, 19), ((19, 30, 34), 8, 4, 0, 13),
+                                                ((70, 28, 33), 4, 16, 2, 37)])
 def test_blocked_bitwise_equals_onestep(tb, physics, shape, so, T, slab, nt):
     """Ragged slabs (n0 not a multiple of the slab), nt not a multiple of T
     (the rest one step per launch), sources on the first and last planes.
@@ -253,8 +254,8 @@ def test_tti_and_elastic_reject_bad_options_and_models(tb):
     q = tb.Propagator(shape, h, 4, physics=tb.TB_ELASTIC)
     with pytest.raises(tb.TBError):  # vs too large (2 vs^2 > vp^2)
         q.set_model(vp, aux=np.stack([1500.0 * one, one]))
-    for opt in [dict(time_tile=9), dict(slab_planes=1), dict(slab_planes=-1)]:
-        with pytest.raises(tb.TBError):  # at most 8 fused steps; slabs of at least r planes
+    for opt in [dict(time_tile=17), dict(slab_planes=1), dict(slab_planes=-1)]:
+        with pytest.raises(tb.TBError):  # at most 16 fused steps; slabs of at least r planes
             tb.Propagator(shape, h, 4, physics=tb.TB_ELASTIC, **opt)
     with pytest.raises(tb.TBError):  # the fused TTI step reaches 2r planes
         tb.Propagator(shape, h, 8, physics=tb.TB_TTI, slab_planes=7, tti_fused=True)
@@ -322,8 +323,8 @@ def test_elastic_full_size_subbox(tb, schedule):
 @pytest.mark.slow
 @pytest.mark.parametrize("physics", ["tti", "elastic"])
 def test_full_size_blocked_bitwise_equals_onestep(tb, physics):
-    """The benchmark's grid, model and default wavefront (time tile 8, slabs
-    of 32 planes) over 26 steps (three wavefronts and two single steps):
+    """The benchmark's grid, model and default wavefront (time tile 16, slabs
+    of 32 planes) over 26 steps (one wavefront and ten single steps):
     traces and every field bit for bit."""
     import torch
     w = wl.tti_384_so8() if physics == "tti" else wl.elastic_384_so8()
